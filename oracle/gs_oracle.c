@@ -1,0 +1,614 @@
+/*
+ * FP64 CPU oracle for the GS-LIVO differentiable Gaussian-splatting path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the plain, slow, obviously correct
+ * restatement of what the renderer computes.  Only the test suite, the smoke
+ * check and the benchmark's CPU-baseline leg call it.  It shares no code,
+ * header, constant table or helper with the CUDA library and includes nothing
+ * from it.
+ *
+ * Everything is double precision.  Each function cites the passage of the
+ * paper it restates:
+ *   - Sec. II-B.1, Eq. 3dgs:        Sigma3 = (R S)(R S)^T
+ *   - Sec. II-B.1, Eq. q:           q_i = pi(T_CW p_W)
+ *   - Sec. II-B.1, Eq. spat:        Sigma2 = (J W) Sigma3 (J W)^T, W = R_CW
+ *   - Sec. II-B.2, Eq. raster:      front-to-back alpha compositing
+ *   - Sec. II-B.2, Eq. gaussian_optimization and Sec. II-D,
+ *     Eq. minimization:             photometric loss, minimised over the
+ *                                   Gaussian parameters and over the pose
+ *   - Appendix A, perturbation model: left perturbation of T_CW
+ *   - Sec. II-B.2 ("Adam optimizer"): Kingma-Ba Adam with bias correction.
+ *
+ * Readings taken where the paper is silent (the same ones the CUDA path uses):
+ *   - alpha_i(x) = sigma_i G_i(x), every G evaluated at the pixel x;
+ *   - alpha is clamped to alpha_max; a Gaussian with alpha < alpha_min is
+ *     skipped; compositing stops before the Gaussian that would take the
+ *     transmittance below T_min;
+ *   - a low-pass blur b is added to the diagonal of Sigma2;
+ *   - pixel (u, v) is sampled at (u + 0.5, v + 0.5);
+ *   - depth ties are ordered by Gaussian index;
+ *   - colour = max(0, C0 k0 + C1 (-d_y k1 + d_z k2 - d_x k3) + 0.5) with d the
+ *     unit view direction from the camera centre, C0, C1 the real spherical
+ *     harmonic normalisations of degree 0 and 1;
+ *   - opacity sigma = sigmoid(logit); scale = exp(log-scale);
+ *   - clamps contribute zero derivative; culling is locally constant.
+ * With alpha_min = 0, alpha_max = 1, T_min = 0 ("exact mode") the compositing
+ * is literally Eq. raster over every Gaussian in front of the camera.
+ *
+ * cfg[] layout (doubles): alpha_min, alpha_max, T_min, blur, z_near,
+ *                         bg_r, bg_g, bg_b.
+ * cam[] layout (doubles): R_CW (9, row-major), t_CW (3), fx, fy, cx, cy.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_PI 3.14159265358979323846
+
+/* Real spherical-harmonic normalisations: Y_00 = 1 / (2 sqrt(pi)),
+ * |Y_1m| prefactor = sqrt(3) / (2 sqrt(pi)). */
+static double sh_c0(void) { return 0.5 / sqrt(ORC_PI); }
+static double sh_c1(void) { return 0.5 * sqrt(3.0) / sqrt(ORC_PI); }
+
+/* ---------- small dense helpers (3x3, row-major) ---------- */
+static void mat3_mul(const double* A, const double* B, double* C) {
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double s = 0.0;
+            for (int k = 0; k < 3; ++k) s += A[3 * i + k] * B[3 * k + j];
+            C[3 * i + j] = s;
+        }
+}
+
+/* Rotation of the unit quaternion (w, x, y, z): the textbook formula. */
+static void quat_to_R(const double* qh, double* R) {
+    double w = qh[0], x = qh[1], y = qh[2], z = qh[3];
+    R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z);     R[2] = 2 * (x * z + w * y);
+    R[3] = 2 * (x * y + w * z);     R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
+    R[6] = 2 * (x * z - w * y);     R[7] = 2 * (y * z + w * x);     R[8] = 1 - 2 * (x * x + y * y);
+}
+
+/* Everything the forward projection of one Gaussian produces, kept so that the
+ * backward pass can walk the same chain in reverse. */
+typedef struct {
+    int valid;
+    double qn;        /* |quat| */
+    double qh[4];     /* unit quaternion */
+    double R[9];      /* R(qh) */
+    double sc[3];     /* exp(log-scale) */
+    double M[9];      /* R S */
+    double S3[9];     /* Sigma3 = M M^T */
+    double pc[3];     /* camera-frame mean */
+    double J[6];      /* 2x3 projection Jacobian */
+    double T[6];      /* J W */
+    double S2[3];     /* Sigma2 = T Sigma3 T^T + b I: (a, b, c) */
+    double conic[3];  /* Sigma2^-1: (A, B, C) */
+    double q[2];      /* projected mean (pixels) */
+    double sigma;     /* opacity */
+    double dvec[3];   /* mu - campos */
+    double dlen;
+    double dir[3];    /* unit view direction */
+    double raw[3];    /* colour before the clamp */
+    double colour[3];
+} orc_proj;
+
+/* Projection of Gaussian i into camera `cam` (Eqs. 3dgs, q, spat). */
+static void project_one(const double* mu, const double* ls, const double* quat, double ologit,
+                        const double* sh, int sh_degree, const double* cam, const double* cfg,
+                        orc_proj* P) {
+    const double* W = cam;       /* R_CW */
+    const double* t = cam + 9;   /* t_CW */
+    double fx = cam[12], fy = cam[13], cx = cam[14], cy = cam[15];
+    double blur = cfg[3], z_near = cfg[4];
+    memset(P, 0, sizeof(*P));
+
+    /* Sigma3 = (R S)(R S)^T with S = diag(exp(s)) (Eq. 3dgs). */
+    P->qn = sqrt(quat[0] * quat[0] + quat[1] * quat[1] + quat[2] * quat[2] + quat[3] * quat[3]);
+    for (int k = 0; k < 4; ++k) P->qh[k] = quat[k] / P->qn;
+    quat_to_R(P->qh, P->R);
+    for (int k = 0; k < 3; ++k) P->sc[k] = exp(ls[k]);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) P->M[3 * i + j] = P->R[3 * i + j] * P->sc[j];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double s = 0.0;
+            for (int k = 0; k < 3; ++k) s += P->M[3 * i + k] * P->M[3 * j + k];
+            P->S3[3 * i + j] = s;
+        }
+
+    /* Camera-frame mean p_C = R_CW p_W + t_CW (Eq. q). */
+    for (int i = 0; i < 3; ++i)
+        P->pc[i] = W[3 * i] * mu[0] + W[3 * i + 1] * mu[1] + W[3 * i + 2] * mu[2] + t[i];
+    double x = P->pc[0], y = P->pc[1], z = P->pc[2];
+    if (!(z > z_near)) { P->valid = 0; return; }
+
+    /* Pinhole projection pi and its Jacobian J (Eq. q, Eq. spat). */
+    P->q[0] = fx * x / z + cx;
+    P->q[1] = fy * y / z + cy;
+    P->J[0] = fx / z; P->J[1] = 0.0;    P->J[2] = -fx * x / (z * z);
+    P->J[3] = 0.0;    P->J[4] = fy / z; P->J[5] = -fy * y / (z * z);
+    for (int r = 0; r < 2; ++r)
+        for (int c = 0; c < 3; ++c) {
+            double s = 0.0;
+            for (int k = 0; k < 3; ++k) s += P->J[3 * r + k] * W[3 * k + c];
+            P->T[3 * r + c] = s;
+        }
+    /* Sigma2 = T Sigma3 T^T + b I (Eq. spat plus the low-pass blur). */
+    double S2f[4];
+    for (int r = 0; r < 2; ++r)
+        for (int c = 0; c < 2; ++c) {
+            double s = 0.0;
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) s += P->T[3 * r + i] * P->S3[3 * i + j] * P->T[3 * c + j];
+            S2f[2 * r + c] = s;
+        }
+    P->S2[0] = S2f[0] + blur;
+    P->S2[1] = 0.5 * (S2f[1] + S2f[2]);
+    P->S2[2] = S2f[3] + blur;
+    double det = P->S2[0] * P->S2[2] - P->S2[1] * P->S2[1];
+    if (!(det > 0.0)) { P->valid = 0; return; }
+    P->conic[0] = P->S2[2] / det;
+    P->conic[1] = -P->S2[1] / det;
+    P->conic[2] = P->S2[0] / det;
+
+    P->sigma = 1.0 / (1.0 + exp(-ologit));
+
+    /* Colour from SH of degree 0 or 1 along the view direction. */
+    double campos[3];
+    for (int i = 0; i < 3; ++i) campos[i] = -(W[i] * t[0] + W[3 + i] * t[1] + W[6 + i] * t[2]);
+    for (int i = 0; i < 3; ++i) P->dvec[i] = mu[i] - campos[i];
+    P->dlen = sqrt(P->dvec[0] * P->dvec[0] + P->dvec[1] * P->dvec[1] + P->dvec[2] * P->dvec[2]);
+    for (int i = 0; i < 3; ++i) P->dir[i] = P->dvec[i] / P->dlen;
+    for (int ch = 0; ch < 3; ++ch) {
+        double v = sh_c0() * sh[ch] + 0.5;
+        if (sh_degree >= 1)
+            v += sh_c1() * (-P->dir[1] * sh[3 + ch] + P->dir[2] * sh[6 + ch] - P->dir[0] * sh[9 + ch]);
+        P->raw[ch] = v;
+        P->colour[ch] = v > 0.0 ? v : 0.0;
+    }
+    P->valid = 1;
+}
+
+/* Public projection: per Gaussian of one view, the quantities the compositing
+ * uses.  Arrays are [n, k] row-major; `valid` is 0 for culled Gaussians. */
+int orc_project(long n, const double* means, const double* log_scales, const double* quats,
+                const double* opacity, const double* sh, int sh_degree, const double* cam,
+                const double* cfg, int* valid, double* pc, double* q, double* sigma2,
+                double* conic, double* opac, double* colour, double* raw_colour) {
+    int K = (sh_degree + 1) * (sh_degree + 1);
+    for (long i = 0; i < n; ++i) {
+        orc_proj P;
+        project_one(means + 3 * i, log_scales + 3 * i, quats + 4 * i, opacity[i], sh + 3 * K * i,
+                    sh_degree, cam, cfg, &P);
+        valid[i] = P.valid;
+        for (int k = 0; k < 3; ++k) pc[3 * i + k] = P.pc[k];
+        q[2 * i] = P.q[0]; q[2 * i + 1] = P.q[1];
+        for (int k = 0; k < 3; ++k) {
+            sigma2[3 * i + k] = P.S2[k];
+            conic[3 * i + k] = P.conic[k];
+            colour[3 * i + k] = P.colour[k];
+            raw_colour[3 * i + k] = P.raw[k];
+        }
+        opac[i] = P.sigma;
+    }
+    return 0;
+}
+
+/* ---------- compositing (Eq. raster) ---------- */
+
+typedef struct { double z; long i; } orc_key;
+
+static int key_cmp(const void* a, const void* b) {
+    const orc_key* x = (const orc_key*)a;
+    const orc_key* y = (const orc_key*)b;
+    if (x->z < y->z) return -1;
+    if (x->z > y->z) return 1;
+    return (x->i < y->i) ? -1 : (x->i > y->i);
+}
+
+/* Valid Gaussians ordered front to back by (depth, index). */
+static long depth_order(long n, const int* valid, const double* depth, long* order) {
+    orc_key* keys = (orc_key*)malloc(sizeof(orc_key) * (n > 0 ? n : 1));
+    long m = 0;
+    for (long i = 0; i < n; ++i)
+        if (valid[i]) { keys[m].z = depth[i]; keys[m].i = i; ++m; }
+    qsort(keys, m, sizeof(orc_key), key_cmp);
+    for (long k = 0; k < m; ++k) order[k] = keys[k].i;
+    free(keys);
+    return m;
+}
+
+/* One fragment of the per-pixel list: Gaussian index, its alpha, the
+ * unclamped sigma*G, G, the pixel offset d = x - q, and the transmittance
+ * in front of it. */
+typedef struct { long i; double alpha, araw, G, dx, dy, Tin; } orc_frag;
+
+#define REL_BORDER 1e-5
+
+/* Front-to-back compositing at pixel centre (px, py): fills `frags` with the
+ * contributing fragments, returns their count; *Tout is the final
+ * transmittance.  *border is set when a threshold decision lies within
+ * REL_BORDER (relative) of its cut, so FP32 may decide it the other way. */
+static long composite_pixel(double px, double py, long m, const long* order, const double* q,
+                            const double* conic, const double* opac, const double* depth,
+                            const double* cfg, orc_frag* frags, double* Tout, int* border,
+                            long* n_considered) {
+    double amin = cfg[0], amax = cfg[1], Tmin = cfg[2];
+    double T = 1.0;
+    long nf = 0;
+    int bd = 0;
+    double zprev = -1.0;
+    long k;
+    for (k = 0; k < m; ++k) {
+        long i = order[k];
+        double dx = px - q[2 * i], dy = py - q[2 * i + 1];
+        double A = conic[3 * i], B = conic[3 * i + 1], C = conic[3 * i + 2];
+        double power = -0.5 * (A * dx * dx + 2.0 * B * dx * dy + C * dy * dy);
+        double G = exp(power);
+        double araw = opac[i] * G;
+        double alpha = araw < amax ? araw : amax;
+        if (amin > 0.0 && fabs(araw - amin) <= REL_BORDER * amin) bd = 1;
+        if (fabs(araw - amax) <= REL_BORDER * amax) bd = 1;
+        if (alpha < amin) continue;
+        if (zprev >= 0.0 && fabs(depth[i] - zprev) <= REL_BORDER * depth[i]) bd = 1;
+        zprev = depth[i];
+        double Tnext = T * (1.0 - alpha);
+        if (Tmin > 0.0 && fabs(Tnext - Tmin) <= REL_BORDER * Tmin) bd = 1;
+        if (Tnext < Tmin) { ++k; break; }
+        frags[nf].i = i; frags[nf].alpha = alpha; frags[nf].araw = araw; frags[nf].G = G;
+        frags[nf].dx = dx; frags[nf].dy = dy; frags[nf].Tin = T;
+        ++nf;
+        T = Tnext;
+    }
+    *Tout = T;
+    *border = bd;
+    if (n_considered) *n_considered = k;
+    return nf;
+}
+
+/* Renders one view.  rgb is [3, H, W]; T_final, n_contrib and borderline are
+ * [H, W].  n_contrib counts the contributing Gaussians. */
+int orc_render(int W, int H, long n, const int* valid, const double* q, const double* conic,
+               const double* opac, const double* colour, const double* depth, const double* cfg,
+               double* rgb, double* T_final, int* n_contrib, unsigned char* borderline,
+               int n_threads) {
+    long* order = (long*)malloc(sizeof(long) * (n > 0 ? n : 1));
+    long m = depth_order(n, valid, depth, order);
+    const double* bg = cfg + 5;
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#pragma omp parallel
+#endif
+    {
+        orc_frag* frags = (orc_frag*)malloc(sizeof(orc_frag) * (m > 0 ? m : 1));
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 1)
+#endif
+        for (int v = 0; v < H; ++v) {
+            for (int u = 0; u < W; ++u) {
+                double T;
+                int bd;
+                long nf = composite_pixel(u + 0.5, v + 0.5, m, order, q, conic, opac, depth, cfg,
+                                          frags, &T, &bd, NULL);
+                double C[3] = {0.0, 0.0, 0.0};
+                for (long f = 0; f < nf; ++f) {
+                    long i = frags[f].i;
+                    for (int ch = 0; ch < 3; ++ch)
+                        C[ch] += colour[3 * i + ch] * frags[f].alpha * frags[f].Tin;
+                }
+                long pix = (long)v * W + u;
+                for (int ch = 0; ch < 3; ++ch) rgb[(long)ch * W * H + pix] = C[ch] + T * bg[ch];
+                T_final[pix] = T;
+                n_contrib[pix] = (int)nf;
+                borderline[pix] = (unsigned char)bd;
+            }
+        }
+        free(frags);
+    }
+    free(order);
+    return 0;
+}
+
+/* Gradient of the loss with respect to the per-Gaussian 2D quantities of one
+ * view, given dL/d(rgb) [3, H, W].  Outputs (accumulated, [n, k]):
+ *   g_q [n,2]      dL/dq (pixel-space mean)
+ *   g_conic [n,3]  dL/d(A, B, C) where the exponent is
+ *                  -1/2 (A dx^2 + 2 B dx dy + C dy^2)
+ *   g_opac [n]     dL/dsigma
+ *   g_colour [n,3] dL/dc
+ *   g_border [n]   set to 1 for Gaussians active at a borderline pixel.
+ * Written from the chain rule on Eq. raster: with T_k the transmittance in
+ * front of fragment k and S_k the light composited behind it (including the
+ * background through T_final),
+ *   dI/dc_k = alpha_k T_k,  dI/dalpha_k = c_k T_k - S_k / (1 - alpha_k). */
+int orc_render_backward(int W, int H, long n, const int* valid, const double* q,
+                        const double* conic, const double* opac, const double* colour,
+                        const double* depth, const double* cfg, const double* dL_drgb,
+                        double* g_q, double* g_conic, double* g_opac, double* g_colour,
+                        unsigned char* g_border, int n_threads) {
+    long* order = (long*)malloc(sizeof(long) * (n > 0 ? n : 1));
+    long m = depth_order(n, valid, depth, order);
+    const double* bg = cfg + 5;
+    double amax = cfg[1], amin = cfg[0];
+    int nt = 1;
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+    nt = omp_get_max_threads();
+#endif
+    /* Per-thread accumulators, summed at the end. */
+    double* acc = (double*)calloc((size_t)nt * (n > 0 ? n : 1) * 9, sizeof(double));
+    unsigned char* bacc = (unsigned char*)calloc((size_t)nt * (n > 0 ? n : 1), 1);
+#ifdef _OPENMP
+#pragma omp parallel
+#endif
+    {
+        int tid = 0;
+#ifdef _OPENMP
+        tid = omp_get_thread_num();
+#endif
+        double* a = acc + (size_t)tid * n * 9;
+        unsigned char* ba = bacc + (size_t)tid * n;
+        orc_frag* frags = (orc_frag*)malloc(sizeof(orc_frag) * (m > 0 ? m : 1));
+        double* S = (double*)malloc(sizeof(double) * 3 * (m > 0 ? m : 1));
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 1)
+#endif
+        for (int v = 0; v < H; ++v) {
+            for (int u = 0; u < W; ++u) {
+                double T;
+                int bd;
+                long ncons;
+                long nf = composite_pixel(u + 0.5, v + 0.5, m, order, q, conic, opac, depth, cfg,
+                                          frags, &T, &bd, &ncons);
+                long pix = (long)v * W + u;
+                double g[3];
+                for (int ch = 0; ch < 3; ++ch) g[ch] = dL_drgb[(long)ch * W * H + pix];
+                if (bd) {
+                    /* Every Gaussian that could be active here is unreliable. */
+                    for (long k = 0; k < ncons && k < m; ++k) {
+                        long i = order[k];
+                        double dx = u + 0.5 - q[2 * i], dy = v + 0.5 - q[2 * i + 1];
+                        double pw = -0.5 * (conic[3 * i] * dx * dx + 2.0 * conic[3 * i + 1] * dx * dy +
+                                            conic[3 * i + 2] * dy * dy);
+                        if (opac[i] * exp(pw) >= amin * (1.0 - REL_BORDER)) ba[i] = 1;
+                    }
+                }
+                /* S_k = sum_{j>k} c_j alpha_j T_j + T_final bg, from the back. */
+                double run[3] = {T * bg[0], T * bg[1], T * bg[2]};
+                for (long f = nf - 1; f >= 0; --f) {
+                    for (int ch = 0; ch < 3; ++ch) S[3 * f + ch] = run[ch];
+                    long i = frags[f].i;
+                    for (int ch = 0; ch < 3; ++ch)
+                        run[ch] += colour[3 * i + ch] * frags[f].alpha * frags[f].Tin;
+                }
+                for (long f = 0; f < nf; ++f) {
+                    long i = frags[f].i;
+                    double al = frags[f].alpha, Tk = frags[f].Tin;
+                    double dLda = 0.0;
+                    for (int ch = 0; ch < 3; ++ch) {
+                        a[9 * i + 6 + ch] += al * Tk * g[ch];
+                        dLda += g[ch] * (colour[3 * i + ch] * Tk - S[3 * f + ch] / (1.0 - al));
+                    }
+                    if (frags[f].araw < amax) {
+                        /* alpha = sigma G, G = exp(power). */
+                        double G = frags[f].G, sg = opac[i];
+                        double dx = frags[f].dx, dy = frags[f].dy;
+                        double A = conic[3 * i], B = conic[3 * i + 1], C = conic[3 * i + 2];
+                        double dLdpow = dLda * sg * G;
+                        a[9 * i + 5] += dLda * G;
+                        /* power = -1/2 (A dx^2 + 2 B dx dy + C dy^2), dx = px - q_x. */
+                        a[9 * i + 0] += dLdpow * (A * dx + B * dy);
+                        a[9 * i + 1] += dLdpow * (B * dx + C * dy);
+                        a[9 * i + 2] += dLdpow * (-0.5 * dx * dx);
+                        a[9 * i + 3] += dLdpow * (-dx * dy);
+                        a[9 * i + 4] += dLdpow * (-0.5 * dy * dy);
+                    }
+                }
+            }
+        }
+        free(S);
+        free(frags);
+    }
+    for (int tt = 0; tt < nt; ++tt) {
+        const double* a = acc + (size_t)tt * n * 9;
+        const unsigned char* ba = bacc + (size_t)tt * n;
+        for (long i = 0; i < n; ++i) {
+            g_q[2 * i] += a[9 * i]; g_q[2 * i + 1] += a[9 * i + 1];
+            for (int k = 0; k < 3; ++k) g_conic[3 * i + k] += a[9 * i + 2 + k];
+            g_opac[i] += a[9 * i + 5];
+            for (int k = 0; k < 3; ++k) g_colour[3 * i + k] += a[9 * i + 6 + k];
+            if (ba[i]) g_border[i] = 1;
+        }
+    }
+    free(acc);
+    free(bacc);
+    free(order);
+    return 0;
+}
+
+/* ---------- projection backward and pose gradient ---------- */
+
+/* Chains dL/d(q, conic, sigma, colour) of one view back to the Gaussian
+ * parameters (accumulated into g_*) and to the camera pose (accumulated
+ * into g_pose[6] = dL/d(dphi, dt) for the left perturbation
+ * T_CW <- Exp(dphi, dt) T_CW of the Appendix perturbation model).
+ * g_border_colour is set to 1 where a colour channel sits within REL_BORDER of
+ * its clamp. */
+int orc_project_backward(long n, const double* means, const double* log_scales,
+                         const double* quats, const double* opacity, const double* sh,
+                         int sh_degree, const double* cam, const double* cfg,
+                         const double* g_q, const double* g_conic, const double* g_opac,
+                         const double* g_colour, double* g_means, double* g_log_scales,
+                         double* g_quats, double* g_opacity, double* g_sh, double* g_pose,
+                         unsigned char* g_border_colour) {
+    int K = (sh_degree + 1) * (sh_degree + 1);
+    const double* W = cam;
+    double fx = cam[12], fy = cam[13];
+    for (long i = 0; i < n; ++i) {
+        orc_proj P;
+        const double* shi = sh + 3 * K * i;
+        project_one(means + 3 * i, log_scales + 3 * i, quats + 4 * i, opacity[i], shi, sh_degree,
+                    cam, cfg, &P);
+        if (!P.valid) continue;
+        double gmu[3] = {0, 0, 0}, gp[3] = {0, 0, 0};
+
+        /* Colour: c = max(0, raw). */
+        double graw[3];
+        for (int ch = 0; ch < 3; ++ch) {
+            graw[ch] = P.raw[ch] > 0.0 ? g_colour[3 * i + ch] : 0.0;
+            if (fabs(P.raw[ch]) <= REL_BORDER) g_border_colour[i] = 1;
+        }
+        for (int ch = 0; ch < 3; ++ch) g_sh[3 * K * i + ch] += sh_c0() * graw[ch];
+        double gd[3] = {0, 0, 0};
+        if (sh_degree >= 1) {
+            double gdir[3] = {0, 0, 0};
+            for (int ch = 0; ch < 3; ++ch) {
+                g_sh[3 * K * i + 3 + ch] += -sh_c1() * P.dir[1] * graw[ch];
+                g_sh[3 * K * i + 6 + ch] += sh_c1() * P.dir[2] * graw[ch];
+                g_sh[3 * K * i + 9 + ch] += -sh_c1() * P.dir[0] * graw[ch];
+                gdir[0] += -sh_c1() * shi[9 + ch] * graw[ch];
+                gdir[1] += -sh_c1() * shi[3 + ch] * graw[ch];
+                gdir[2] += sh_c1() * shi[6 + ch] * graw[ch];
+            }
+            /* dir = d / |d|: g_d = (g_dir - dir (dir . g_dir)) / |d|. */
+            double dotv = P.dir[0] * gdir[0] + P.dir[1] * gdir[1] + P.dir[2] * gdir[2];
+            for (int k = 0; k < 3; ++k) gd[k] = (gdir[k] - P.dir[k] * dotv) / P.dlen;
+            for (int k = 0; k < 3; ++k) gmu[k] += gd[k];
+        }
+
+        /* Opacity: sigma = 1 / (1 + exp(-o)). */
+        g_opacity[i] += g_opac[i] * P.sigma * (1.0 - P.sigma);
+
+        /* Conic = Sigma2^-1.  With G = [[gA, gB/2], [gB/2, gC]] the gradient as
+         * a symmetric matrix, dL/dSigma2 = -Q G Q. */
+        double Q[4] = {P.conic[0], P.conic[1], P.conic[1], P.conic[2]};
+        double Gm[4] = {g_conic[3 * i], 0.5 * g_conic[3 * i + 1], 0.5 * g_conic[3 * i + 1],
+                        g_conic[3 * i + 2]};
+        double QG[4], G2[4];
+        for (int r = 0; r < 2; ++r)
+            for (int c = 0; c < 2; ++c) QG[2 * r + c] = Q[2 * r] * Gm[c] + Q[2 * r + 1] * Gm[2 + c];
+        for (int r = 0; r < 2; ++r)
+            for (int c = 0; c < 2; ++c) G2[2 * r + c] = -(QG[2 * r] * Q[c] + QG[2 * r + 1] * Q[2 + c]);
+
+        /* Sigma2 = T Sigma3 T^T: dL/dSigma3 = T^T G2 T, dL/dT = 2 G2 T Sigma3. */
+        double G3[9], gT[6];
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+                double s = 0.0;
+                for (int r = 0; r < 2; ++r)
+                    for (int c = 0; c < 2; ++c) s += P.T[3 * r + a] * G2[2 * r + c] * P.T[3 * c + b];
+                G3[3 * a + b] = s;
+            }
+        for (int r = 0; r < 2; ++r)
+            for (int b = 0; b < 3; ++b) {
+                double s = 0.0;
+                for (int c = 0; c < 2; ++c)
+                    for (int k = 0; k < 3; ++k) s += G2[2 * r + c] * P.T[3 * c + k] * P.S3[3 * k + b];
+                gT[3 * r + b] = 2.0 * s;
+            }
+        /* T = J W: dL/dJ = dL/dT W^T, dL/dW = J^T dL/dT. */
+        double gJ[6], gW[9];
+        for (int r = 0; r < 2; ++r)
+            for (int k = 0; k < 3; ++k) {
+                double s = 0.0;
+                for (int c = 0; c < 3; ++c) s += gT[3 * r + c] * W[3 * k + c];
+                gJ[3 * r + k] = s;
+            }
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) gW[3 * a + b] = P.J[a] * gT[b] + P.J[3 + a] * gT[3 + b];
+
+        /* J(p_C) and q(p_C). */
+        double x = P.pc[0], y = P.pc[1], z = P.pc[2];
+        double z2 = z * z, z3 = z2 * z;
+        gp[0] += gJ[2] * (-fx / z2);
+        gp[1] += gJ[5] * (-fy / z2);
+        gp[2] += gJ[0] * (-fx / z2) + gJ[2] * (2.0 * fx * x / z3) + gJ[4] * (-fy / z2) +
+                 gJ[5] * (2.0 * fy * y / z3);
+        double gqx = g_q[2 * i], gqy = g_q[2 * i + 1];
+        gp[0] += gqx * fx / z;
+        gp[1] += gqy * fy / z;
+        gp[2] += -gqx * fx * x / z2 - gqy * fy * y / z2;
+
+        /* p_C = W mu + t. */
+        for (int k = 0; k < 3; ++k) gmu[k] += W[k] * gp[0] + W[3 + k] * gp[1] + W[6 + k] * gp[2];
+
+        /* Sigma3 = M M^T: dL/dM = 2 G3 M; M = R S. */
+        double gM[9];
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+                double s = 0.0;
+                for (int k = 0; k < 3; ++k) s += G3[3 * a + k] * P.M[3 * k + b];
+                gM[3 * a + b] = 2.0 * s;
+            }
+        double gR[9];
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) gR[3 * a + b] = gM[3 * a + b] * P.sc[b];
+        for (int b = 0; b < 3; ++b) {
+            double gS = 0.0;
+            for (int a = 0; a < 3; ++a) gS += gM[3 * a + b] * P.R[3 * a + b];
+            g_log_scales[3 * i + b] += gS * P.sc[b];
+        }
+        /* R(qh): partial derivatives of each entry of the textbook formula. */
+        double w = P.qh[0], qx = P.qh[1], qy = P.qh[2], qz = P.qh[3];
+        double gqh[4] = {0, 0, 0, 0};
+        gqh[0] = gR[1] * (-2 * qz) + gR[2] * (2 * qy) + gR[3] * (2 * qz) + gR[5] * (-2 * qx) +
+                 gR[6] * (-2 * qy) + gR[7] * (2 * qx);
+        gqh[1] = gR[1] * (2 * qy) + gR[2] * (2 * qz) + gR[3] * (2 * qy) + gR[4] * (-4 * qx) +
+                 gR[5] * (-2 * w) + gR[6] * (2 * qz) + gR[7] * (2 * w) + gR[8] * (-4 * qx);
+        gqh[2] = gR[0] * (-4 * qy) + gR[1] * (2 * qx) + gR[2] * (2 * w) + gR[3] * (2 * qx) +
+                 gR[5] * (2 * qz) + gR[6] * (-2 * w) + gR[7] * (2 * qz) + gR[8] * (-4 * qy);
+        gqh[3] = gR[0] * (-4 * qz) + gR[1] * (-2 * w) + gR[2] * (2 * qx) + gR[3] * (2 * w) +
+                 gR[4] * (-4 * qz) + gR[5] * (2 * qy) + gR[6] * (2 * qx) + gR[7] * (2 * qy);
+        /* qh = quat / |quat|. */
+        double dq = gqh[0] * P.qh[0] + gqh[1] * P.qh[1] + gqh[2] * P.qh[2] + gqh[3] * P.qh[3];
+        for (int k = 0; k < 4; ++k) g_quats[4 * i + k] += (gqh[k] - P.qh[k] * dq) / P.qn;
+
+        for (int k = 0; k < 3; ++k) g_means[3 * i + k] += gmu[k];
+
+        /* Pose, left perturbation: p_C <- p_C + dphi x p_C + dt, W <- W + [dphi]x W,
+         * campos <- campos - W^T dt. */
+        if (g_pose) {
+            double gW_Wt[9];
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) {
+                    double s = 0.0;
+                    for (int k = 0; k < 3; ++k) s += gW[3 * a + k] * W[3 * b + k];
+                    gW_Wt[3 * a + b] = s;
+                }
+            g_pose[0] += (P.pc[1] * gp[2] - P.pc[2] * gp[1]) + (gW_Wt[7] - gW_Wt[5]);
+            g_pose[1] += (P.pc[2] * gp[0] - P.pc[0] * gp[2]) + (gW_Wt[2] - gW_Wt[6]);
+            g_pose[2] += (P.pc[0] * gp[1] - P.pc[1] * gp[0]) + (gW_Wt[3] - gW_Wt[1]);
+            for (int k = 0; k < 3; ++k)
+                g_pose[3 + k] += gp[k] + (W[3 * k] * gd[0] + W[3 * k + 1] * gd[1] + W[3 * k + 2] * gd[2]);
+        }
+    }
+    return 0;
+}
+
+/* ---------- Adam (Sec. II-B.2) ---------- */
+
+/* Kingma & Ba (2015) with bias correction, in the form torch.optim.Adam uses:
+ * m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;
+ * p -= lr / (1 - b1^t) * m / (sqrt(v) / sqrt(1 - b2^t) + eps). */
+void orc_adam(long n, double* p, const double* g, double* m, double* v, double lr, double b1,
+              double b2, double eps, long step) {
+    double bc1 = 1.0 - pow(b1, (double)step);
+    double bc2 = 1.0 - pow(b2, (double)step);
+    for (long i = 0; i < n; ++i) {
+        m[i] = b1 * m[i] + (1.0 - b1) * g[i];
+        v[i] = b2 * v[i] + (1.0 - b2) * g[i] * g[i];
+        double denom = sqrt(v[i]) / sqrt(bc2) + eps;
+        p[i] -= (lr / bc1) * m[i] / denom;
+    }
+}
+
+int orc_num_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

@@ -1,0 +1,194 @@
+"""FP64 CPU oracle for the Gaussian-splatting path (test infrastructure only).
+
+Only the tests, the smoke check and the benchmark's CPU-baseline leg may use
+this module.  It wraps the plain C implementation in `gs_oracle.c` (compiled
+with gcc, loaded with ctypes) and adds the loss in numpy.  It imports nothing
+from the CUDA package.
+
+Functions, with the passage each restates:
+  project        Sec. II-B.1, Eqs. 3dgs, q, spat
+  render         Sec. II-B.2, Eq. raster (per pixel, front to back)
+  l1_loss_grad   Sec. II-B.2, Eq. gaussian_optimization with the L1 norm
+  backward       chain rule through all of the above, to the Gaussian
+                 parameters and to the left-perturbed camera pose
+                 (Appendix A, perturbation model)
+  adam           Sec. II-B.2 ("Adam optimizer"), Kingma & Ba with bias
+                 correction
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "gs_oracle.c")
+_LIB = os.path.join(_HERE, "libgs_oracle.so")
+_lib = None
+
+# Truncated-mode defaults (the reading of the 3D-GS rasteriser constants).
+DEFAULT_CFG = dict(alpha_min=1.0 / 255.0, alpha_max=0.99, T_min=1e-4, blur=0.3, z_near=0.2,
+                   bg=(0.0, 0.0, 0.0))
+# Exact mode: Eq. raster literally, every Gaussian at every pixel.
+EXACT_CFG = dict(alpha_min=0.0, alpha_max=1.0, T_min=0.0, blur=0.3, z_near=0.2, bg=(0.0, 0.0, 0.0))
+
+
+def build(force=False):
+    """Compile gs_oracle.c into libgs_oracle.so next to it."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-shared", "-fPIC", _SRC, "-o", _LIB, "-lm"]
+        subprocess.run(cmd, check=True)
+    return _LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB)
+        P = ctypes.c_void_p
+        L.orc_project.argtypes = [ctypes.c_long] + [P] * 5 + [ctypes.c_int] + [P] * 10
+        L.orc_render.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_long] + [P] * 11 + [ctypes.c_int]
+        L.orc_render_backward.argtypes = ([ctypes.c_int, ctypes.c_int, ctypes.c_long] + [P] * 13 +
+                                          [ctypes.c_int])
+        L.orc_project_backward.argtypes = ([ctypes.c_long] + [P] * 5 + [ctypes.c_int] + [P] * 2 +
+                                           [P] * 4 + [P] * 7)
+        L.orc_adam.argtypes = [ctypes.c_long, P, P, P, P, ctypes.c_double, ctypes.c_double,
+                               ctypes.c_double, ctypes.c_double, ctypes.c_long]
+        L.orc_adam.restype = None
+        L.orc_num_threads.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+
+
+def _f64(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def cfg_array(cfg):
+    c = dict(DEFAULT_CFG)
+    c.update(cfg or {})
+    return np.array([c["alpha_min"], c["alpha_max"], c["T_min"], c["blur"], c["z_near"],
+                     *c["bg"]], dtype=np.float64)
+
+
+def cam_array(view):
+    R = np.asarray(view["R"], np.float64).reshape(9)
+    t = np.asarray(view["t"], np.float64).reshape(3)
+    return np.concatenate([R, t, [view["fx"], view["fy"], view["cx"], view["cy"]]]).astype(np.float64)
+
+
+def _slice(params, view):
+    b = int(view.get("g_begin", 0))
+    e = int(view.get("g_end", 0)) or params["means"].shape[0]
+    return b, e
+
+
+def _params64(params, b, e):
+    return (_f64(params["means"][b:e]), _f64(params["log_scales"][b:e]), _f64(params["quats"][b:e]),
+            _f64(params["opacity"][b:e]), _f64(params["sh"][b:e]))
+
+
+def project(params, view, cfg=None):
+    """Per-Gaussian projection of one view (Eqs. 3dgs, q, spat)."""
+    b, e = _slice(params, view)
+    n = e - b
+    mu, ls, qt, op, sh = _params64(params, b, e)
+    out = dict(valid=np.zeros(n, np.int32), pc=np.zeros((n, 3)), q=np.zeros((n, 2)),
+               sigma2=np.zeros((n, 3)), conic=np.zeros((n, 3)), opac=np.zeros(n),
+               colour=np.zeros((n, 3)), raw_colour=np.zeros((n, 3)))
+    lib().orc_project(n, _p(mu), _p(ls), _p(qt), _p(op), _p(sh), int(params["sh_degree"]),
+                      _p(cam_array(view)), _p(cfg_array(cfg)), _p(out["valid"]), _p(out["pc"]),
+                      _p(out["q"]), _p(out["sigma2"]), _p(out["conic"]), _p(out["opac"]),
+                      _p(out["colour"]), _p(out["raw_colour"]))
+    out["depth"] = out["pc"][:, 2].copy()
+    return out
+
+
+def render_view(params, view, cfg=None, n_threads=0, proj=None):
+    """Eq. raster for one view: returns rgb [3,H,W], T_final [H,W], contributor
+    count [H,W] and the borderline-pixel mask [H,W]."""
+    W, H = int(view["W"]), int(view["H"])
+    pr = proj if proj is not None else project(params, view, cfg)
+    n = pr["valid"].shape[0]
+    rgb = np.zeros((3, H, W))
+    T = np.zeros((H, W))
+    nc = np.zeros((H, W), np.int32)
+    bd = np.zeros((H, W), np.uint8)
+    lib().orc_render(W, H, n, _p(pr["valid"]), _p(pr["q"]), _p(pr["conic"]), _p(pr["opac"]),
+                     _p(pr["colour"]), _p(pr["depth"]), _p(cfg_array(cfg)), _p(rgb), _p(T), _p(nc),
+                     _p(bd), int(n_threads))
+    return dict(rgb=rgb, T=T, n_contrib=nc, border=bd.astype(bool))
+
+
+def render(params, views, cfg=None, n_threads=0):
+    return [render_view(params, v, cfg, n_threads) for v in views]
+
+
+def l1_loss_grad(rgbs, targets):
+    """L = (1/V) sum_v mean |I_hat - I| and dL/dI_hat = sign(I_hat - I)/(3HW V),
+    sign(0) = 0 (Eq. gaussian_optimization with the L1 norm)."""
+    V = len(rgbs)
+    L = 0.0
+    grads = []
+    for r, t in zip(rgbs, targets):
+        d = np.asarray(r, np.float64) - np.asarray(t, np.float64)
+        L += np.abs(d).mean() / V
+        grads.append(np.sign(d) / (d.size * V))
+    return L, grads
+
+
+def backward(params, views, dL_drgbs, cfg=None, n_threads=0):
+    """Gradients of a loss with dL/d(rgb) given per view, with respect to every
+    Gaussian parameter (summed over views) and to each view's pose
+    (dL/d(dphi, dt) for T_CW <- Exp(dphi, dt) T_CW).  Also returns a per-Gaussian
+    mask of gradients that FP32 may legitimately decide differently."""
+    N = params["means"].shape[0]
+    K = params["sh"].shape[1]
+    g = dict(means=np.zeros((N, 3)), log_scales=np.zeros((N, 3)), quats=np.zeros((N, 4)),
+             opacity=np.zeros(N), sh=np.zeros((N, K, 3)))
+    pose = np.zeros((len(views), 6))
+    border = np.zeros(N, bool)
+    ca = cfg_array(cfg)
+    for vi, view in enumerate(views):
+        b, e = _slice(params, view)
+        n = e - b
+        pr = project(params, view, cfg)
+        gq = np.zeros((n, 2)); gc = np.zeros((n, 3)); go = np.zeros(n); gcol = np.zeros((n, 3))
+        gb = np.zeros(n, np.uint8)
+        dl = _f64(dL_drgbs[vi])
+        W, H = int(view["W"]), int(view["H"])
+        lib().orc_render_backward(W, H, n, _p(pr["valid"]), _p(pr["q"]), _p(pr["conic"]),
+                                  _p(pr["opac"]), _p(pr["colour"]), _p(pr["depth"]), _p(ca), _p(dl),
+                                  _p(gq), _p(gc), _p(go), _p(gcol), _p(gb), int(n_threads))
+        mu, ls, qt, op, sh = _params64(params, b, e)
+        gm = np.zeros((n, 3)); gl = np.zeros((n, 3)); gqt = np.zeros((n, 4)); gop = np.zeros(n)
+        gsh = np.zeros((n, K, 3)); gpose = np.zeros(6); gbc = np.zeros(n, np.uint8)
+        lib().orc_project_backward(n, _p(mu), _p(ls), _p(qt), _p(op), _p(sh), int(params["sh_degree"]),
+                                   _p(cam_array(view)), _p(ca), _p(gq), _p(gc), _p(go), _p(gcol),
+                                   _p(gm), _p(gl), _p(gqt), _p(gop), _p(gsh), _p(gpose), _p(gbc))
+        g["means"][b:e] += gm
+        g["log_scales"][b:e] += gl
+        g["quats"][b:e] += gqt
+        g["opacity"][b:e] += gop
+        g["sh"][b:e] += gsh
+        pose[vi] = gpose
+        border[b:e] |= (gb != 0) | (gbc != 0)
+    return g, pose, border
+
+
+def adam(p, g, m, v, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8, step=1):
+    """One Adam step in place on float64 arrays."""
+    for a in (p, g, m, v):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    lib().orc_adam(p.size, _p(p), _p(g), _p(m), _p(v), lr, b1, b2, eps, int(step))
+
+
+def num_threads():
+    return int(lib().orc_num_threads())

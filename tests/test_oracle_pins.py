@@ -1,0 +1,426 @@
+"""Pins of the FP64 oracle against things other than itself.
+
+Closed forms of Eq. raster, textbook rotations and real spherical harmonics
+from scipy, numerical Jacobians, central finite differences, torch.optim.Adam,
+and the pose/Gaussian adjoint identity.  No GPU is used.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg
+import scipy.special
+from scipy.spatial.transform import Rotation
+
+from paper_2501_08672_b300 import scenes
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def one_gaussian(mu, log_scale, quat, logit, sh, sh_degree=0):
+    K = (sh_degree + 1) ** 2
+    sh = np.asarray(sh, np.float64).reshape(1, K, 3)
+    return dict(means=np.asarray([mu], np.float64), log_scales=np.asarray([log_scale], np.float64),
+                quats=np.asarray([quat], np.float64), opacity=np.asarray([logit], np.float64),
+                sh=sh, sh_degree=sh_degree)
+
+
+def stack(*gs):
+    out = {k: np.concatenate([g[k] for g in gs]) for k in ("means", "log_scales", "quats", "opacity", "sh")}
+    out["sh_degree"] = gs[0]["sh_degree"]
+    return out
+
+
+def k0_for(c):
+    # degree-0 coefficient that gives colour c: c = k0 / (2 sqrt(pi)) + 0.5
+    return (np.asarray(c, np.float64) - 0.5) * 2.0 * math.sqrt(math.pi)
+
+
+def view(W, H, f, cx=None, cy=None, R=None, t=None):
+    return dict(R=np.eye(3) if R is None else R, t=np.zeros(3) if t is None else t, fx=f, fy=f,
+                cx=W / 2 if cx is None else cx, cy=H / 2 if cy is None else cy, W=W, H=H,
+                g_begin=0, g_end=0)
+
+
+# ---------------------------------------------------------------- projection
+
+@pytest.mark.parametrize("axis", ["x", "y", "z"])
+def test_quarter_turns_are_textbook(orc, axis):
+    """90-degree turns about each axis permute the scales (Eq. 3dgs); on the
+    optical axis J = diag(f/z, f/z) so Sigma2 = (f/z)^2 Sigma3[:2,:2] + b I."""
+    s = np.array([0.1, 0.2, 0.3])
+    z, f = 5.0, 100.0
+    q = {"x": [math.cos(math.pi / 4), math.sin(math.pi / 4), 0, 0],
+         "y": [math.cos(math.pi / 4), 0, math.sin(math.pi / 4), 0],
+         "z": [math.cos(math.pi / 4), 0, 0, math.sin(math.pi / 4)]}[axis]
+    # Rx(90): (x, y, z) scales -> diag(sx^2, sz^2, sy^2); Ry: (sz, sy, sx); Rz: (sy, sx, sz)
+    perm = {"x": (0, 2), "y": (2, 1), "z": (1, 0)}[axis]
+    p = one_gaussian([0, 0, z], np.log(s), q, 0.0, k0_for([0.5] * 3))
+    pr = orc.project(p, view(64, 64, f), dict(blur=0.3))
+    expect = np.array([(f / z) ** 2 * s[perm[0]] ** 2 + 0.3, 0.0, (f / z) ** 2 * s[perm[1]] ** 2 + 0.3])
+    np.testing.assert_allclose(pr["sigma2"][0], expect, rtol=1e-13, atol=1e-13)
+    np.testing.assert_allclose(pr["q"][0], [32.0, 32.0], rtol=0, atol=1e-13)
+
+
+def test_random_rotation_matches_scipy(orc):
+    """Sigma3 = R S^2 R^T with R from scipy's quaternion convention (Eq. 3dgs)."""
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        q = rng.standard_normal(4) * rng.uniform(0.5, 2.0)  # deliberately not unit
+        s = rng.uniform(0.05, 0.4, 3)
+        R = Rotation.from_quat([q[1], q[2], q[3], q[0]]).as_matrix()  # scipy is scalar-last
+        S3 = R @ np.diag(s ** 2) @ R.T
+        z, f = 4.0, 150.0
+        p = one_gaussian([0, 0, z], np.log(s), q, 0.0, k0_for([0.5] * 3))
+        pr = orc.project(p, view(64, 64, f), dict(blur=0.0))
+        e = (f / z) ** 2 * S3[:2, :2]
+        np.testing.assert_allclose(pr["sigma2"][0], [e[0, 0], e[0, 1], e[1, 1]], rtol=1e-12, atol=1e-14)
+
+
+def _pi(p, fx, fy, cx, cy):
+    return np.array([fx * p[0] / p[2] + cx, fy * p[1] / p[2] + cy])
+
+
+def test_offaxis_ewa_uses_exact_projection_jacobian(orc):
+    """Eq. spat with J the Jacobian of pi, checked against a numerical
+    Jacobian of the pinhole map and a posed camera."""
+    rng = np.random.default_rng(4)
+    R = Rotation.from_rotvec([0.3, -0.2, 0.5]).as_matrix()
+    t = np.array([0.2, -0.1, 1.0])
+    fx, fy, cx, cy = 300.0, 280.0, 161.0, 121.0
+    for _ in range(10):
+        mu = rng.uniform(-1, 1, 3) + np.array([0, 0, 4.0])
+        mu = R.T @ (mu - t)  # world point that lands in front of the camera
+        q = rng.standard_normal(4)
+        s = rng.uniform(0.02, 0.3, 3)
+        p = one_gaussian(mu, np.log(s), q, 0.0, k0_for([0.5] * 3))
+        v = dict(R=R, t=t, fx=fx, fy=fy, cx=cx, cy=cy, W=320, H=240, g_begin=0, g_end=0)
+        pr = orc.project(p, v, dict(blur=0.3))
+        pc = R @ mu + t
+        h = 1e-6
+        Jn = np.zeros((2, 3))
+        for k in range(3):
+            e = np.zeros(3); e[k] = h
+            Jn[:, k] = (_pi(pc + e, fx, fy, cx, cy) - _pi(pc - e, fx, fy, cx, cy)) / (2 * h)
+        Rq = Rotation.from_quat([q[1], q[2], q[3], q[0]]).as_matrix()
+        S3 = Rq @ np.diag(s ** 2) @ Rq.T
+        S2 = Jn @ R @ S3 @ R.T @ Jn.T + 0.3 * np.eye(2)
+        np.testing.assert_allclose(pr["sigma2"][0], [S2[0, 0], S2[0, 1], S2[1, 1]], rtol=1e-7)
+        np.testing.assert_allclose(pr["q"][0], _pi(pc, fx, fy, cx, cy), rtol=1e-13)
+
+
+def test_ewa_matches_monte_carlo_for_small_gaussians(orc):
+    """Second moment of projected samples approaches Sigma2 - b I as the
+    Gaussian shrinks relative to its depth (the local-affine approximation)."""
+    rng = np.random.default_rng(5)
+    R = Rotation.from_rotvec([0.1, 0.2, -0.1]).as_matrix()
+    t = np.array([0.0, 0.0, 0.5])
+    mu = np.array([0.4, -0.3, 5.0])
+    q = np.array([0.8, 0.1, -0.3, 0.5])
+    s = np.array([0.01, 0.02, 0.005])
+    p = one_gaussian(mu, np.log(s), q, 0.0, k0_for([0.5] * 3))
+    v = dict(R=R, t=t, fx=500.0, fy=500.0, cx=0.0, cy=0.0, W=8, H=8, g_begin=0, g_end=0)
+    pr = orc.project(p, v, dict(blur=0.0))
+    Rq = Rotation.from_quat([q[1], q[2], q[3], q[0]]).as_matrix()
+    x = mu + (rng.standard_normal((400_000, 3)) * s) @ Rq.T
+    pc = x @ R.T + t
+    uv = np.stack([500 * pc[:, 0] / pc[:, 2], 500 * pc[:, 1] / pc[:, 2]], 1)
+    C = np.cov(uv.T)
+    np.testing.assert_allclose(pr["sigma2"][0], [C[0, 0], C[0, 1], C[1, 1]], rtol=0.02, atol=0.02 * C[0, 0])
+
+
+def test_degree_one_colour_is_real_sh(orc):
+    """Colour = C0 k0 - k1 Y_{1,-1} + k2 Y_{1,0} - k3 Y_{1,1} + 0.5 with the
+    real harmonics built from scipy's complex ones (the degree-1 reading)."""
+    rng = np.random.default_rng(6)
+    for _ in range(10):
+        d = rng.standard_normal(3)
+        d /= np.linalg.norm(d)
+        if d[2] < 0.2:
+            d[2] = 0.2 + abs(d[2])
+            d /= np.linalg.norm(d)
+        mu = 5.0 * d
+        sh = rng.normal(0, 0.3, (4, 3))
+        sh[0] = 1.0
+        theta = math.acos(d[2])
+        phi = math.atan2(d[1], d[0])
+        Y = lambda l, m: scipy.special.sph_harm_y(l, m, theta, phi)  # noqa: E731
+        y00 = Y(0, 0).real
+        # real harmonics: Y_{1,-1} = -sqrt(2) Im Y_1^1, Y_{1,0} = Y_1^0, Y_{1,1} = -sqrt(2) Re Y_1^1
+        y1m1 = -math.sqrt(2) * Y(1, 1).imag
+        y10 = Y(1, 0).real
+        y11 = -math.sqrt(2) * Y(1, 1).real
+        np.testing.assert_allclose([y1m1, y10, y11], math.sqrt(3 / (4 * math.pi)) * d[[1, 2, 0]], rtol=1e-12)
+        expect = y00 * sh[0] - y1m1 * sh[1] + y10 * sh[2] - y11 * sh[3] + 0.5
+        p = one_gaussian(mu, np.log([0.1] * 3), [1, 0, 0, 0], 0.0, sh, sh_degree=1)
+        pr = orc.project(p, view(64, 64, 50.0), dict(blur=0.3))
+        np.testing.assert_allclose(pr["raw_colour"][0], expect, rtol=1e-12, atol=1e-13)
+
+
+# ---------------------------------------------------------------- compositing
+
+def test_single_isotropic_gaussian_closed_form(orc):
+    """Exact mode, one isotropic Gaussian on the axis:
+    I(x) = c sigma exp(-r^2 / (2 (f^2 s^2 / z^2 + b)))."""
+    f, z, s, b = 120.0, 3.0, 0.08, 0.3
+    c = np.array([0.9, 0.4, 0.2])
+    p = one_gaussian([0, 0, z], np.log([s] * 3), [0.3, 0.5, -0.2, 0.7], 0.4, k0_for(c))
+    W, H = 40, 30
+    v = view(W, H, f, cx=17.3, cy=14.1)
+    out = orc.render_view(p, v, dict(orc.EXACT_CFG, blur=b))
+    u, w = np.meshgrid(np.arange(W) + 0.5, np.arange(H) + 0.5)
+    r2 = (u - 17.3) ** 2 + (w - 14.1) ** 2
+    sig = 1 / (1 + math.exp(-0.4))
+    prof = sig * np.exp(-r2 / (2 * (f * f * s * s / (z * z) + b)))
+    for ch in range(3):
+        np.testing.assert_allclose(out["rgb"][ch], c[ch] * prof, rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(out["T"], 1 - prof, rtol=1e-12, atol=1e-14)
+
+
+def test_cocentred_stack_golden(orc):
+    g = json.load(open(os.path.join(GOLDEN, "cocentred_stack.json")))
+    gs = []
+    # inputs listed back to front so the oracle must sort by depth
+    for sg, c, z in reversed(list(zip(g["sigma"], g["colour"], g["depth"]))):
+        gs.append(one_gaussian([0, 0, z], np.log([0.05] * 3), [1, 0, 0, 0], math.log(sg / (1 - sg)),
+                               k0_for([c] * 3)))
+    p = stack(*gs)
+    v = view(9, 9, 50.0, cx=4.5, cy=4.5)
+    out = orc.render_view(p, v, dict(orc.EXACT_CFG))
+    assert abs(out["T"][4, 4] - g["T_final"]) < 1e-13
+    for ch in range(3):
+        assert abs(out["rgb"][ch, 4, 4] - g["intensity"]) < 1e-13
+
+
+def test_stack_product_and_termination(orc):
+    """Random co-centred stacks: T_final = prod(1 - sigma_j) and
+    I = sum c_j sigma_j prod_{k<j}(1 - sigma_k); with T_min the compositing
+    stops before the Gaussian that would take T below T_min."""
+    rng = np.random.default_rng(7)
+    for trial in range(10):
+        n = 12
+        sig = rng.uniform(0.2, 0.6, n)
+        col = rng.uniform(0.1, 0.9, n)
+        zs = rng.permutation(np.linspace(2.0, 9.0, n))
+        p = stack(*[one_gaussian([0, 0, zs[i]], np.log([0.05] * 3), [1, 0, 0, 0],
+                                 math.log(sig[i] / (1 - sig[i])), k0_for([col[i]] * 3)) for i in range(n)])
+        order = np.argsort(zs)
+        Tmin = 10 ** rng.uniform(-4, -2)
+        T, I = 1.0, 0.0
+        for j in order:
+            if T * (1 - sig[j]) < Tmin:
+                break
+            I += col[j] * sig[j] * T
+            T *= 1 - sig[j]
+        v = view(9, 9, 50.0, cx=4.5, cy=4.5)
+        out = orc.render_view(p, v, dict(alpha_min=0.0, alpha_max=1.0, T_min=Tmin))
+        assert abs(out["T"][4, 4] - T) < 1e-13
+        assert abs(out["rgb"][0, 4, 4] - I) < 1e-13
+        full = orc.render_view(p, v, dict(orc.EXACT_CFG))
+        assert abs(full["T"][4, 4] - np.prod(1 - sig)) < 1e-13
+
+
+def test_alpha_clamp_and_skip(orc):
+    """alpha = min(alpha_max, sigma G); Gaussians below alpha_min are skipped."""
+    v = view(9, 9, 50.0, cx=4.5, cy=4.5)
+    strong = one_gaussian([0, 0, 3.0], np.log([0.05] * 3), [1, 0, 0, 0], 8.0, k0_for([1.0] * 3))
+    out = orc.render_view(strong, v, dict(alpha_min=1 / 255, alpha_max=0.99, T_min=0.0))
+    assert abs(out["T"][4, 4] - 0.01) < 1e-14
+    faint = one_gaussian([0, 0, 2.0], np.log([0.05] * 3), [1, 0, 0, 0], math.log(0.003 / 0.997),
+                         k0_for([0.3] * 3))
+    both = orc.render_view(stack(strong, faint), v, dict(alpha_min=1 / 255, alpha_max=0.99, T_min=0.0))
+    np.testing.assert_array_equal(both["rgb"], out["rgb"])
+
+
+def test_permutation_invariance(orc):
+    p = scenes.frustum_scene(600, seed=11)
+    v = scenes.identity_view(64, 48, 60.0)
+    a = orc.render_view(p, v)
+    perm = np.random.default_rng(1).permutation(600)
+    q = {k: (p[k][perm] if isinstance(p[k], np.ndarray) else p[k]) for k in p}
+    b = orc.render_view(q, v)
+    np.testing.assert_allclose(a["rgb"], b["rgb"], rtol=0, atol=1e-13)
+
+
+def test_truncated_close_to_exact(orc):
+    """Truncation (alpha_min, T_min) moves each pixel by at most the light
+    it drops: skipped fragments (< alpha_min each) and the tail behind the
+    stop (< T_min / (1 - alpha_max))."""
+    p = scenes.frustum_scene(300, seed=12)
+    p["opacity"][:] = np.clip(p["opacity"], -3, 3)
+    v = scenes.identity_view(48, 40, 50.0)
+    ex = orc.render_view(p, v, dict(orc.EXACT_CFG, alpha_max=0.99))
+    tr = orc.render_view(p, v, dict(alpha_min=1 / 255, alpha_max=0.99, T_min=1e-4))
+    bound = 300 * (1 / 255) * 1.0 + 1e-4 / 0.01
+    assert np.abs(ex["rgb"] - tr["rgb"]).max() < bound
+    assert np.abs(ex["rgb"] - tr["rgb"]).mean() < 0.05
+
+
+# ---------------------------------------------------------------- gradients
+
+def _tiny_scene(seed, n=5, sh_degree=1):
+    rng = np.random.default_rng(seed)
+    K = (sh_degree + 1) ** 2
+    mu = np.stack([rng.uniform(-0.4, 0.4, n), rng.uniform(-0.3, 0.3, n), rng.uniform(2.0, 3.5, n)], 1)
+    sh = rng.normal(0, 0.3, (n, K, 3))
+    sh[:, 0, :] = k0_for(rng.uniform(0.4, 0.9, (n, 3)))
+    return dict(means=mu, log_scales=rng.normal(-2.2, 0.3, (n, 3)), quats=rng.standard_normal((n, 4)),
+                opacity=rng.normal(0, 0.8, n), sh=sh, sh_degree=sh_degree)
+
+
+def _posed_view(W=24, H=20):
+    R = Rotation.from_rotvec([0.05, -0.08, 0.03]).as_matrix()
+    return dict(R=R, t=np.array([0.05, -0.02, 0.1]), fx=40.0, fy=42.0, cx=W / 2 + 0.3, cy=H / 2 - 0.2,
+                W=W, H=H, g_begin=0, g_end=0)
+
+
+def _loss(orc, p, views, w, cfg):
+    outs = [orc.render_view(p, v, cfg) for v in views]
+    return sum(float(np.sum(o["rgb"] * wi)) for o, wi in zip(outs, w))
+
+
+@pytest.mark.parametrize("sh_degree", [0, 1])
+def test_gaussian_gradients_match_central_differences(orc, sh_degree):
+    """Exact mode, smooth loss L = sum w * I: analytic backward vs central
+    differences for every parameter of every Gaussian, two views."""
+    p = _tiny_scene(21 + sh_degree, sh_degree=sh_degree)
+    views = [_posed_view(), view(24, 20, 38.0, cx=11.7, cy=10.2)]
+    cfg = dict(orc.EXACT_CFG)
+    rng = np.random.default_rng(2)
+    w = [rng.standard_normal((3, v["H"], v["W"])) for v in views]
+    g, pose, _ = orc.backward(p, views, w, cfg)
+    h = 1e-6
+    for key in ("means", "log_scales", "quats", "opacity", "sh"):
+        flat = p[key].reshape(-1)
+        num = np.zeros_like(flat)
+        for k in range(flat.size):
+            old = flat[k]
+            flat[k] = old + h
+            lp = _loss(orc, p, views, w, cfg)
+            flat[k] = old - h
+            lm = _loss(orc, p, views, w, cfg)
+            flat[k] = old
+            num[k] = (lp - lm) / (2 * h)
+        ana = g[key].reshape(-1)
+        err = np.linalg.norm(ana - num) / max(np.linalg.norm(num), 1e-30)
+        assert err < 1e-6, (key, err)
+
+
+def _se3_exp(xi):
+    """Exp of xi = (dphi, dt) through the 4x4 matrix exponential (scipy)."""
+    X = np.zeros((4, 4))
+    wx, wy, wz = xi[:3]
+    X[:3, :3] = [[0, -wz, wy], [wz, 0, -wx], [-wy, wx, 0]]
+    X[:3, 3] = xi[3:]
+    return scipy.linalg.expm(X)
+
+
+def _perturb(v, xi):
+    T = np.eye(4)
+    T[:3, :3] = v["R"]
+    T[:3, 3] = v["t"]
+    Tp = _se3_exp(xi) @ T
+    out = dict(v)
+    out["R"] = Tp[:3, :3]
+    out["t"] = Tp[:3, 3]
+    return out
+
+
+@pytest.mark.parametrize("loss", ["weighted", "l1"])
+def test_pose_gradient_matches_central_differences(orc, loss):
+    """dL/d(dphi, dt) for T_CW <- Exp(xi) T_CW (Appendix A perturbation model),
+    against central differences through scipy's matrix exponential."""
+    p = _tiny_scene(31, sh_degree=1)
+    v = _posed_view(28, 22)
+    cfg = dict(orc.EXACT_CFG)
+    rng = np.random.default_rng(3)
+    if loss == "weighted":
+        w = rng.standard_normal((3, v["H"], v["W"]))
+        lossf = lambda vv: float(np.sum(orc.render_view(p, vv, cfg)["rgb"] * w))  # noqa: E731
+        dl = [w]
+    else:
+        base = orc.render_view(p, v, cfg)["rgb"]
+        target = base + np.where(rng.uniform(size=base.shape) < 0.5, -1, 1) * rng.uniform(0.2, 0.4, base.shape)
+        lossf = lambda vv: orc.l1_loss_grad([orc.render_view(p, vv, cfg)["rgb"]], [target])[0]  # noqa: E731
+        dl = orc.l1_loss_grad([base], [target])[1]
+    _, pose, _ = orc.backward(p, [v], dl, cfg)
+    h = 1e-6
+    num = np.zeros(6)
+    for k in range(6):
+        e = np.zeros(6); e[k] = h
+        num[k] = (lossf(_perturb(v, e)) - lossf(_perturb(v, -e))) / (2 * h)
+    np.testing.assert_allclose(pose[0], num, rtol=2e-6, atol=1e-9 * np.abs(num).max())
+
+
+def test_pose_gradient_adjoint_identity(orc):
+    """Degree-0 colour: moving the camera by Exp(xi) equals moving every
+    Gaussian rigidly by T_CW^-1 Exp(xi) T_CW, so the pose gradient equals
+    dt: W sum_i g_mu_i;  dphi: sum_i p_C,i x (W g_mu_i) + W g_omega_i with
+    g_omega the gradient of a left rotation of the Gaussian's quaternion."""
+    p = _tiny_scene(41, n=6, sh_degree=0)
+    v = _posed_view(30, 26)
+    cfg = dict(orc.EXACT_CFG)
+    w = np.random.default_rng(4).standard_normal((3, v["H"], v["W"]))
+    g, pose, _ = orc.backward(p, [v], [w], cfg)
+    Wm = np.asarray(v["R"], np.float64)
+    pc = p["means"] @ Wm.T + v["t"]
+    gt = Wm @ g["means"].sum(0)
+    gphi = np.zeros(3)
+    for i in range(p["means"].shape[0]):
+        gphi += np.cross(pc[i], Wm @ g["means"][i])
+        qw, qv = p["quats"][i, 0], p["quats"][i, 1:]
+        gw, gv = g["quats"][i, 0], g["quats"][i, 1:]
+        gomega = 0.5 * (qw * gv - gw * qv + np.cross(qv, gv))
+        gphi += Wm @ gomega
+    np.testing.assert_allclose(pose[0], np.concatenate([gphi, gt]), rtol=1e-9, atol=1e-12)
+
+
+def test_l1_gradient_matches_differences(orc):
+    """Eq. gaussian_optimization with the L1 norm: the gradient of the
+    per-Gaussian path under L1 (residuals bounded away from zero)."""
+    p = _tiny_scene(51, sh_degree=1)
+    v = _posed_view()
+    cfg = dict(orc.EXACT_CFG)
+    base = orc.render_view(p, v, cfg)["rgb"]
+    rng = np.random.default_rng(5)
+    target = base + np.where(rng.uniform(size=base.shape) < 0.5, -1, 1) * rng.uniform(0.2, 0.4, base.shape)
+    L, dl = orc.l1_loss_grad([base], [target])
+    assert abs(L - np.abs(base - target).mean()) < 1e-15
+    g, _, _ = orc.backward(p, [v], dl, cfg)
+    h = 1e-6
+    flat = p["means"].reshape(-1)
+    for k in range(flat.size):
+        old = flat[k]
+        flat[k] = old + h
+        lp = orc.l1_loss_grad([orc.render_view(p, v, cfg)["rgb"]], [target])[0]
+        flat[k] = old - h
+        lm = orc.l1_loss_grad([orc.render_view(p, v, cfg)["rgb"]], [target])[0]
+        flat[k] = old
+        assert abs((lp - lm) / (2 * h) - g["means"].reshape(-1)[k]) < 1e-7 * max(1.0, abs(g["means"]).max())
+
+
+# ---------------------------------------------------------------- Adam
+
+def test_adam_matches_torch(orc):
+    import torch
+    rng = np.random.default_rng(9)
+    n = 257
+    p0 = rng.standard_normal(n)
+    p = p0.copy(); m = np.zeros(n); v = np.zeros(n)
+    tp = torch.tensor(p0.copy(), dtype=torch.float64, requires_grad=True)
+    opt = torch.optim.Adam([tp], lr=1e-3, betas=(0.9, 0.999), eps=1e-8, foreach=False)
+    for step in range(1, 8):
+        g = rng.standard_normal(n) * 10 ** rng.uniform(-3, 1)
+        tp.grad = torch.tensor(g, dtype=torch.float64)
+        opt.step()
+        orc.adam(p, np.ascontiguousarray(g), m, v, 1e-3, 0.9, 0.999, 1e-8, step)
+        np.testing.assert_allclose(p, tp.detach().numpy(), rtol=1e-14, atol=1e-15)
+
+
+def test_borderline_pixels_are_rare(orc):
+    p = scenes.frustum_scene(3000, seed=0)
+    v = scenes.identity_view(160, 128, 150.0)
+    out = orc.render_view(p, v)
+    assert out["border"].mean() < 1e-3
