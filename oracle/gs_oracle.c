@@ -53,16 +53,6 @@
 static double sh_c0(void) { return 0.5 / sqrt(ORC_PI); }
 static double sh_c1(void) { return 0.5 * sqrt(3.0) / sqrt(ORC_PI); }
 
-/* ---------- small dense helpers (3x3, row-major) ---------- */
-static void mat3_mul(const double* A, const double* B, double* C) {
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) {
-            double s = 0.0;
-            for (int k = 0; k < 3; ++k) s += A[3 * i + k] * B[3 * k + j];
-            C[3 * i + j] = s;
-        }
-}
-
 /* Rotation of the unit quaternion (w, x, y, z): the textbook formula. */
 static void quat_to_R(const double* qh, double* R) {
     double w = qh[0], x = qh[1], y = qh[2], z = qh[3];
@@ -227,6 +217,10 @@ static long depth_order(long n, const int* valid, const double* depth, long* ord
 typedef struct { long i; double alpha, araw, G, dx, dy, Tin; } orc_frag;
 
 #define REL_BORDER 1e-5
+/* Two contributors closer in depth than this (relative) may be ordered the
+ * other way by an FP32 camera transform: its rounding error is a few ulp of
+ * the largest term, a few 1e-7 relative for the scenes used here. */
+#define REL_DEPTH 2e-6
 
 /* Front-to-back compositing at pixel centre (px, py): fills `frags` with the
  * contributing fragments, returns their count; *Tout is the final
@@ -253,7 +247,7 @@ static long composite_pixel(double px, double py, long m, const long* order, con
         if (amin > 0.0 && fabs(araw - amin) <= REL_BORDER * amin) bd = 1;
         if (fabs(araw - amax) <= REL_BORDER * amax) bd = 1;
         if (alpha < amin) continue;
-        if (zprev >= 0.0 && fabs(depth[i] - zprev) <= REL_BORDER * depth[i]) bd = 1;
+        if (zprev >= 0.0 && fabs(depth[i] - zprev) <= REL_DEPTH * depth[i]) bd = 1;
         zprev = depth[i];
         double Tnext = T * (1.0 - alpha);
         if (Tmin > 0.0 && fabs(Tnext - Tmin) <= REL_BORDER * Tmin) bd = 1;
@@ -312,32 +306,130 @@ int orc_render(int W, int H, long n, const int* valid, const double* q, const do
     return 0;
 }
 
+/* Eq. raster at a list of pixels (px[k], py[k]) of one view: rgb [n_pix, 3],
+ * T_final [n_pix], n_contrib [n_pix], borderline [n_pix].  The same
+ * per-pixel compositing as orc_render, for sampled checks of large images. */
+int orc_render_pixels(long n_pix, const int* px, const int* py, long n, const int* valid,
+                      const double* q, const double* conic, const double* opac,
+                      const double* colour, const double* depth, const double* cfg, double* rgb,
+                      double* T_final, int* n_contrib, unsigned char* borderline, int n_threads) {
+    long* order = (long*)malloc(sizeof(long) * (n > 0 ? n : 1));
+    long m = depth_order(n, valid, depth, order);
+    const double* bg = cfg + 5;
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#pragma omp parallel
+#endif
+    {
+        orc_frag* frags = (orc_frag*)malloc(sizeof(orc_frag) * (m > 0 ? m : 1));
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 16)
+#endif
+        for (long k = 0; k < n_pix; ++k) {
+            double T;
+            int bd;
+            long nf = composite_pixel(px[k] + 0.5, py[k] + 0.5, m, order, q, conic, opac, depth, cfg,
+                                      frags, &T, &bd, NULL);
+            double C[3] = {0.0, 0.0, 0.0};
+            for (long f = 0; f < nf; ++f) {
+                long i = frags[f].i;
+                for (int ch = 0; ch < 3; ++ch)
+                    C[ch] += colour[3 * i + ch] * frags[f].alpha * frags[f].Tin;
+            }
+            for (int ch = 0; ch < 3; ++ch) rgb[3 * k + ch] = C[ch] + T * bg[ch];
+            T_final[k] = T;
+            n_contrib[k] = (int)nf;
+            borderline[k] = (unsigned char)bd;
+        }
+        free(frags);
+    }
+    free(order);
+    return 0;
+}
+
+/* Backward of Eq. raster at one pixel centre (px, py) with dL/dI = g[3]:
+ * accumulates into a[9 i + k] (dq_x, dq_y, dA, dB, dC, dsigma, dc_r, dc_g,
+ * dc_b) and flags ba[i] for Gaussians active at a borderline pixel.
+ * Written from the chain rule on Eq. raster: with T_k the transmittance in
+ * front of fragment k and S_k the light composited behind it (including the
+ * background through T_final),
+ *   dI/dc_k = alpha_k T_k,  dI/dalpha_k = c_k T_k - S_k / (1 - alpha_k),
+ * alpha_k = sigma_k G_k (unless clamped), G = exp(power),
+ * power = -1/2 (A dx^2 + 2 B dx dy + C dy^2), dx = px - q_x. */
+static void backward_pixel(double px, double py, const double* g, long m, const long* order,
+                           const double* q, const double* conic, const double* opac,
+                           const double* colour, const double* depth, const double* cfg,
+                           orc_frag* frags, double* S, double* a, unsigned char* ba) {
+    const double* bg = cfg + 5;
+    double amax = cfg[1], amin = cfg[0];
+    double T;
+    int bd;
+    long ncons;
+    long nf = composite_pixel(px, py, m, order, q, conic, opac, depth, cfg, frags, &T, &bd, &ncons);
+    if (bd) {
+        /* Every Gaussian that could be active here is unreliable. */
+        for (long k = 0; k < ncons && k < m; ++k) {
+            long i = order[k];
+            double dx = px - q[2 * i], dy = py - q[2 * i + 1];
+            double pw = -0.5 * (conic[3 * i] * dx * dx + 2.0 * conic[3 * i + 1] * dx * dy +
+                                conic[3 * i + 2] * dy * dy);
+            if (opac[i] * exp(pw) >= amin * (1.0 - REL_BORDER)) ba[i] = 1;
+        }
+    }
+    /* S_k = sum_{j>k} c_j alpha_j T_j + T_final bg, from the back. */
+    double run[3] = {T * bg[0], T * bg[1], T * bg[2]};
+    for (long f = nf - 1; f >= 0; --f) {
+        for (int ch = 0; ch < 3; ++ch) S[3 * f + ch] = run[ch];
+        long i = frags[f].i;
+        for (int ch = 0; ch < 3; ++ch) run[ch] += colour[3 * i + ch] * frags[f].alpha * frags[f].Tin;
+    }
+    for (long f = 0; f < nf; ++f) {
+        long i = frags[f].i;
+        double al = frags[f].alpha, Tk = frags[f].Tin;
+        double dLda = 0.0;
+        for (int ch = 0; ch < 3; ++ch) {
+            a[9 * i + 6 + ch] += al * Tk * g[ch];
+            dLda += g[ch] * (colour[3 * i + ch] * Tk - S[3 * f + ch] / (1.0 - al));
+        }
+        if (frags[f].araw < amax) {
+            double G = frags[f].G, sg = opac[i];
+            double dx = frags[f].dx, dy = frags[f].dy;
+            double A = conic[3 * i], B = conic[3 * i + 1], C = conic[3 * i + 2];
+            double dLdpow = dLda * sg * G;
+            a[9 * i + 5] += dLda * G;
+            a[9 * i + 0] += dLdpow * (A * dx + B * dy);
+            a[9 * i + 1] += dLdpow * (B * dx + C * dy);
+            a[9 * i + 2] += dLdpow * (-0.5 * dx * dx);
+            a[9 * i + 3] += dLdpow * (-dx * dy);
+            a[9 * i + 4] += dLdpow * (-0.5 * dy * dy);
+        }
+    }
+}
+
 /* Gradient of the loss with respect to the per-Gaussian 2D quantities of one
- * view, given dL/d(rgb) [3, H, W].  Outputs (accumulated, [n, k]):
+ * view, over the pixels listed in (px, py) (n_pix >= 0) or, when px is NULL,
+ * over every pixel of the W x H image.  dL_drgb is [3, H, W] for the full
+ * image and [n_pix, 3] for a pixel list.  Outputs (accumulated, [n, k]):
  *   g_q [n,2]      dL/dq (pixel-space mean)
  *   g_conic [n,3]  dL/d(A, B, C) where the exponent is
  *                  -1/2 (A dx^2 + 2 B dx dy + C dy^2)
  *   g_opac [n]     dL/dsigma
  *   g_colour [n,3] dL/dc
- *   g_border [n]   set to 1 for Gaussians active at a borderline pixel.
- * Written from the chain rule on Eq. raster: with T_k the transmittance in
- * front of fragment k and S_k the light composited behind it (including the
- * background through T_final),
- *   dI/dc_k = alpha_k T_k,  dI/dalpha_k = c_k T_k - S_k / (1 - alpha_k). */
-int orc_render_backward(int W, int H, long n, const int* valid, const double* q,
-                        const double* conic, const double* opac, const double* colour,
-                        const double* depth, const double* cfg, const double* dL_drgb,
-                        double* g_q, double* g_conic, double* g_opac, double* g_colour,
-                        unsigned char* g_border, int n_threads) {
+ *   g_border [n]   set to 1 for Gaussians active at a borderline pixel. */
+static int render_backward_impl(int W, int H, long n_pix, const int* pxs, const int* pys, long n,
+                                const int* valid, const double* q, const double* conic,
+                                const double* opac, const double* colour, const double* depth,
+                                const double* cfg, const double* dL_drgb, double* g_q,
+                                double* g_conic, double* g_opac, double* g_colour,
+                                unsigned char* g_border, int n_threads) {
     long* order = (long*)malloc(sizeof(long) * (n > 0 ? n : 1));
     long m = depth_order(n, valid, depth, order);
-    const double* bg = cfg + 5;
-    double amax = cfg[1], amin = cfg[0];
     int nt = 1;
 #ifdef _OPENMP
     if (n_threads > 0) omp_set_num_threads(n_threads);
     nt = omp_get_max_threads();
 #endif
+    long total = pxs ? n_pix : (long)W * H;
     /* Per-thread accumulators, summed at the end. */
     double* acc = (double*)calloc((size_t)nt * (n > 0 ? n : 1) * 9, sizeof(double));
     unsigned char* bacc = (unsigned char*)calloc((size_t)nt * (n > 0 ? n : 1), 1);
@@ -354,60 +446,18 @@ int orc_render_backward(int W, int H, long n, const int* valid, const double* q,
         orc_frag* frags = (orc_frag*)malloc(sizeof(orc_frag) * (m > 0 ? m : 1));
         double* S = (double*)malloc(sizeof(double) * 3 * (m > 0 ? m : 1));
 #ifdef _OPENMP
-#pragma omp for schedule(dynamic, 1)
+#pragma omp for schedule(dynamic, 64)
 #endif
-        for (int v = 0; v < H; ++v) {
-            for (int u = 0; u < W; ++u) {
-                double T;
-                int bd;
-                long ncons;
-                long nf = composite_pixel(u + 0.5, v + 0.5, m, order, q, conic, opac, depth, cfg,
-                                          frags, &T, &bd, &ncons);
-                long pix = (long)v * W + u;
-                double g[3];
-                for (int ch = 0; ch < 3; ++ch) g[ch] = dL_drgb[(long)ch * W * H + pix];
-                if (bd) {
-                    /* Every Gaussian that could be active here is unreliable. */
-                    for (long k = 0; k < ncons && k < m; ++k) {
-                        long i = order[k];
-                        double dx = u + 0.5 - q[2 * i], dy = v + 0.5 - q[2 * i + 1];
-                        double pw = -0.5 * (conic[3 * i] * dx * dx + 2.0 * conic[3 * i + 1] * dx * dy +
-                                            conic[3 * i + 2] * dy * dy);
-                        if (opac[i] * exp(pw) >= amin * (1.0 - REL_BORDER)) ba[i] = 1;
-                    }
-                }
-                /* S_k = sum_{j>k} c_j alpha_j T_j + T_final bg, from the back. */
-                double run[3] = {T * bg[0], T * bg[1], T * bg[2]};
-                for (long f = nf - 1; f >= 0; --f) {
-                    for (int ch = 0; ch < 3; ++ch) S[3 * f + ch] = run[ch];
-                    long i = frags[f].i;
-                    for (int ch = 0; ch < 3; ++ch)
-                        run[ch] += colour[3 * i + ch] * frags[f].alpha * frags[f].Tin;
-                }
-                for (long f = 0; f < nf; ++f) {
-                    long i = frags[f].i;
-                    double al = frags[f].alpha, Tk = frags[f].Tin;
-                    double dLda = 0.0;
-                    for (int ch = 0; ch < 3; ++ch) {
-                        a[9 * i + 6 + ch] += al * Tk * g[ch];
-                        dLda += g[ch] * (colour[3 * i + ch] * Tk - S[3 * f + ch] / (1.0 - al));
-                    }
-                    if (frags[f].araw < amax) {
-                        /* alpha = sigma G, G = exp(power). */
-                        double G = frags[f].G, sg = opac[i];
-                        double dx = frags[f].dx, dy = frags[f].dy;
-                        double A = conic[3 * i], B = conic[3 * i + 1], C = conic[3 * i + 2];
-                        double dLdpow = dLda * sg * G;
-                        a[9 * i + 5] += dLda * G;
-                        /* power = -1/2 (A dx^2 + 2 B dx dy + C dy^2), dx = px - q_x. */
-                        a[9 * i + 0] += dLdpow * (A * dx + B * dy);
-                        a[9 * i + 1] += dLdpow * (B * dx + C * dy);
-                        a[9 * i + 2] += dLdpow * (-0.5 * dx * dx);
-                        a[9 * i + 3] += dLdpow * (-dx * dy);
-                        a[9 * i + 4] += dLdpow * (-0.5 * dy * dy);
-                    }
-                }
+        for (long k = 0; k < total; ++k) {
+            double px, py, g[3];
+            if (pxs) {
+                px = pxs[k] + 0.5; py = pys[k] + 0.5;
+                for (int ch = 0; ch < 3; ++ch) g[ch] = dL_drgb[3 * k + ch];
+            } else {
+                px = (double)(k % W) + 0.5; py = (double)(k / W) + 0.5;
+                for (int ch = 0; ch < 3; ++ch) g[ch] = dL_drgb[(long)ch * W * H + k];
             }
+            backward_pixel(px, py, g, m, order, q, conic, opac, colour, depth, cfg, frags, S, a, ba);
         }
         free(S);
         free(frags);
@@ -427,6 +477,24 @@ int orc_render_backward(int W, int H, long n, const int* valid, const double* q,
     free(bacc);
     free(order);
     return 0;
+}
+
+int orc_render_backward(int W, int H, long n, const int* valid, const double* q,
+                        const double* conic, const double* opac, const double* colour,
+                        const double* depth, const double* cfg, const double* dL_drgb,
+                        double* g_q, double* g_conic, double* g_opac, double* g_colour,
+                        unsigned char* g_border, int n_threads) {
+    return render_backward_impl(W, H, 0, NULL, NULL, n, valid, q, conic, opac, colour, depth, cfg,
+                                dL_drgb, g_q, g_conic, g_opac, g_colour, g_border, n_threads);
+}
+
+int orc_render_backward_pixels(long n_pix, const int* px, const int* py, long n, const int* valid,
+                               const double* q, const double* conic, const double* opac,
+                               const double* colour, const double* depth, const double* cfg,
+                               const double* dL_drgb, double* g_q, double* g_conic, double* g_opac,
+                               double* g_colour, unsigned char* g_border, int n_threads) {
+    return render_backward_impl(0, 0, n_pix, px, py, n, valid, q, conic, opac, colour, depth, cfg,
+                                dL_drgb, g_q, g_conic, g_opac, g_colour, g_border, n_threads);
 }
 
 /* ---------- projection backward and pose gradient ---------- */

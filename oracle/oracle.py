@@ -51,8 +51,11 @@ def lib():
         P = ctypes.c_void_p
         L.orc_project.argtypes = [ctypes.c_long] + [P] * 5 + [ctypes.c_int] + [P] * 10
         L.orc_render.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_long] + [P] * 11 + [ctypes.c_int]
+        L.orc_render_pixels.argtypes = ([ctypes.c_long, P, P, ctypes.c_long] + [P] * 11 + [ctypes.c_int])
         L.orc_render_backward.argtypes = ([ctypes.c_int, ctypes.c_int, ctypes.c_long] + [P] * 13 +
                                           [ctypes.c_int])
+        L.orc_render_backward_pixels.argtypes = ([ctypes.c_long, P, P, ctypes.c_long] + [P] * 13 +
+                                                 [ctypes.c_int])
         L.orc_project_backward.argtypes = ([ctypes.c_long] + [P] * 5 + [ctypes.c_int] + [P] * 2 +
                                            [P] * 4 + [P] * 7)
         L.orc_adam.argtypes = [ctypes.c_long, P, P, P, P, ctypes.c_double, ctypes.c_double,
@@ -127,6 +130,24 @@ def render_view(params, view, cfg=None, n_threads=0, proj=None):
     return dict(rgb=rgb, T=T, n_contrib=nc, border=bd.astype(bool))
 
 
+def render_pixels(params, view, px, py, cfg=None, n_threads=0, proj=None):
+    """Eq. raster at the listed pixels of one view (same per-pixel compositing
+    as render_view): rgb [n,3], T_final [n], contributor count [n], border [n]."""
+    pr = proj if proj is not None else project(params, view, cfg)
+    n = pr["valid"].shape[0]
+    px = np.ascontiguousarray(px, np.int32)
+    py = np.ascontiguousarray(py, np.int32)
+    k = px.size
+    rgb = np.zeros((k, 3))
+    T = np.zeros(k)
+    nc = np.zeros(k, np.int32)
+    bd = np.zeros(k, np.uint8)
+    lib().orc_render_pixels(k, _p(px), _p(py), n, _p(pr["valid"]), _p(pr["q"]), _p(pr["conic"]),
+                            _p(pr["opac"]), _p(pr["colour"]), _p(pr["depth"]), _p(cfg_array(cfg)), _p(rgb),
+                            _p(T), _p(nc), _p(bd), int(n_threads))
+    return dict(rgb=rgb, T=T, n_contrib=nc, border=bd.astype(bool))
+
+
 def render(params, views, cfg=None, n_threads=0):
     return [render_view(params, v, cfg, n_threads) for v in views]
 
@@ -144,11 +165,15 @@ def l1_loss_grad(rgbs, targets):
     return L, grads
 
 
-def backward(params, views, dL_drgbs, cfg=None, n_threads=0):
+def backward(params, views, dL_drgbs, cfg=None, n_threads=0, pixels=None):
     """Gradients of a loss with dL/d(rgb) given per view, with respect to every
     Gaussian parameter (summed over views) and to each view's pose
     (dL/d(dphi, dt) for T_CW <- Exp(dphi, dt) T_CW).  Also returns a per-Gaussian
-    mask of gradients that FP32 may legitimately decide differently."""
+    mask of gradients that FP32 may legitimately decide differently.
+
+    pixels: None (dL_drgbs[v] is [3,H,W]) or a list of (px, py) index arrays
+    per view, with dL_drgbs[v] of shape [len(px), 3]: the loss then depends
+    only on those pixels."""
     N = params["means"].shape[0]
     K = params["sh"].shape[1]
     g = dict(means=np.zeros((N, 3)), log_scales=np.zeros((N, 3)), quats=np.zeros((N, 4)),
@@ -163,10 +188,18 @@ def backward(params, views, dL_drgbs, cfg=None, n_threads=0):
         gq = np.zeros((n, 2)); gc = np.zeros((n, 3)); go = np.zeros(n); gcol = np.zeros((n, 3))
         gb = np.zeros(n, np.uint8)
         dl = _f64(dL_drgbs[vi])
-        W, H = int(view["W"]), int(view["H"])
-        lib().orc_render_backward(W, H, n, _p(pr["valid"]), _p(pr["q"]), _p(pr["conic"]),
-                                  _p(pr["opac"]), _p(pr["colour"]), _p(pr["depth"]), _p(ca), _p(dl),
-                                  _p(gq), _p(gc), _p(go), _p(gcol), _p(gb), int(n_threads))
+        if pixels is None:
+            W, H = int(view["W"]), int(view["H"])
+            lib().orc_render_backward(W, H, n, _p(pr["valid"]), _p(pr["q"]), _p(pr["conic"]),
+                                      _p(pr["opac"]), _p(pr["colour"]), _p(pr["depth"]), _p(ca), _p(dl),
+                                      _p(gq), _p(gc), _p(go), _p(gcol), _p(gb), int(n_threads))
+        else:
+            px = np.ascontiguousarray(pixels[vi][0], np.int32)
+            py = np.ascontiguousarray(pixels[vi][1], np.int32)
+            lib().orc_render_backward_pixels(px.size, _p(px), _p(py), n, _p(pr["valid"]), _p(pr["q"]),
+                                             _p(pr["conic"]), _p(pr["opac"]), _p(pr["colour"]),
+                                             _p(pr["depth"]), _p(ca), _p(dl), _p(gq), _p(gc), _p(go),
+                                             _p(gcol), _p(gb), int(n_threads))
         mu, ls, qt, op, sh = _params64(params, b, e)
         gm = np.zeros((n, 3)); gl = np.zeros((n, 3)); gqt = np.zeros((n, 4)); gop = np.zeros(n)
         gsh = np.zeros((n, K, 3)); gpose = np.zeros(6); gbc = np.zeros(n, np.uint8)
