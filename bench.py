@@ -1,0 +1,354 @@
+#!/usr/bin/env python
+"""Benchmark of the sliding-window optimisation step of GS-LIVO's Gaussian map
+(Sec. II-B.2): one step renders every keyframe of the window (projection,
+tile binning, compositing), takes the L1 photometric loss, back-propagates to
+every Gaussian parameter and applies Adam.
+
+Workload: a box-room window of 200,000 planar Gaussians (SH degree 1) seen by
+8 keyframes at 640x512 on a 2 m arc, FP32, Adam lr 1e-3; seeded synthetic
+data shaped like the paper's LiDAR-seeded windows (its datasets are not
+available).  Prints one JSON line.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl b300|reference]
+
+--impl reference times the FP64 CPU oracle on a bounded pixel sample of the
+same workload (the method has no other reference implementation).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, HERE)
+
+METRIC = "fwd+bwd window-opt iters/s at 200k Gaussians×8 views 640×512; % of roofline"
+UNIT = "it/s"
+N_GAUSS = 200_000
+N_VIEWS = 8
+W_IMG, H_IMG = 640, 512
+FOCAL = 600.0
+LR = 1e-3
+WORKLOAD = "box-room sliding window: 200k planar Gaussians (SH degree 1), 8 keyframes 640x512 on a 2 m arc"
+
+# Algorithmic FP32 work per visited fragment (FMA counted as 2 FLOP, the ex2 /
+# rcp of the special-function unit not counted): forward = offset (2), exponent
+# quadratic form (2 mul + 3 fma = 8), alpha clamp (1), 1-alpha and T update
+# (2), weight (1), colour accumulation (3 fma = 6) -> 20; backward = the same
+# exponent (10) and clamp (1), transmittance recovery (2), weight and colour
+# gradient (1 + 3), light-behind difference and alpha gradient (3 + 6),
+# light-behind update (3 fma = 6), opacity/exponent gradient (2), mean and
+# conic gradients (2 x 3 + 5) -> 45.
+FLOP_PER_FRAGMENT = {"raster_fwd": 20.0, "raster_bwd": 45.0}
+SM_COUNT = 148
+FP32_LANES = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
+    ap.add_argument("--cpu-pixels", type=int, default=128, help="oracle pixels sampled per view")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--tile-size", type=int, default=16)
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def workload(seed=0):
+    from paper_2501_08672_b300 import scenes
+    params = scenes.box_room_scene(N_GAUSS, seed=seed, sh_degree=1)
+    views = scenes.arc_views(N_VIEWS, W_IMG, H_IMG, FOCAL, n_gaussians=N_GAUSS)
+    return params, views
+
+
+def peaks():
+    try:
+        with open(os.path.join(HERE, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_oracle_iteration(params, views, pixels_per_view, seed=1):
+    """Times the FP64 oracle on a pixel sample of one window iteration and
+    scales the per-pixel parts to the full images.  Returns (seconds per
+    iteration estimate, threads, description)."""
+    from oracle import oracle as O
+    rng = np.random.default_rng(seed)
+    t_fixed = 0.0
+    t_pix = 0.0
+    n_pix_total = 0
+    for v in views:
+        W, H = int(v["W"]), int(v["H"])
+        px = rng.integers(0, W, pixels_per_view)
+        py = rng.integers(0, H, pixels_per_view)
+        t0 = time.perf_counter()
+        pr = O.project(params, v)
+        t1 = time.perf_counter()
+        O.render_pixels(params, v, px, py, proj=pr)
+        t2 = time.perf_counter()
+        dl = [rng.standard_normal((pixels_per_view, 3)) * 1e-6]
+        O.backward(params, [v], dl, pixels=[(px, py)])
+        t3 = time.perf_counter()
+        O.backward(params, [v], [np.zeros((0, 3))], pixels=[(px[:0], py[:0])])
+        t4 = time.perf_counter()
+        scale = (W * H) / float(pixels_per_view)
+        t_fixed += (t1 - t0) + (t4 - t3)
+        t_pix += ((t2 - t1) + max(0.0, (t3 - t2) - (t4 - t3))) * scale
+        n_pix_total += pixels_per_view
+    n = sum(int(params[k].size) for k in ("means", "log_scales", "quats", "opacity", "sh"))
+    p = rng.standard_normal(n)
+    g = rng.standard_normal(n)
+    m = np.zeros(n)
+    vv = np.zeros(n)
+    t0 = time.perf_counter()
+    O.adam(p, g, m, vv, LR, 0.9, 0.999, 1e-8, 1)
+    t_adam = time.perf_counter() - t0
+    desc = ("oracle FP64 on %d random pixels per view (%d of %d), projection and projection backward over all "
+            "Gaussians, Adam over all %d parameters; per-pixel time scaled to the full images"
+            % (pixels_per_view, n_pix_total, sum(int(v["W"]) * int(v["H"]) for v in views), n))
+    return t_fixed + t_pix + t_adam, O.num_threads(), desc
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    params, views = workload()
+    ppv = 4
+    for _ in range(args.warmup):
+        cpu_oracle_iteration(params, views[:1], ppv)
+    times = []
+    threads = 1
+    desc = ""
+    for k in range(args.steps):
+        t, threads, desc = cpu_oracle_iteration(params, views, ppv, seed=100 + k)
+        times.append(t)
+    sec = float(np.mean(times))
+    val = 1.0 / sec
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_gaussians": N_GAUSS, "views": N_VIEWS, "image": [W_IMG, H_IMG]},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_b300(args, world, rank, local):
+    import torch
+    import torch.distributed as dist
+    from paper_2501_08672_b300 import binding as B
+    from paper_2501_08672_b300 import scenes
+    from paper_2501_08672_b300.render import GaussianWindow, Renderer, WindowOptimizer
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    params, views = workload(seed=rank)
+    # target keyframes: render of a perturbed copy of the window
+    q = scenes.perturbed_copy(params, seed=1000 + rank)
+    rt = Renderer(views, local, args.tile_size)
+    wq = GaussianWindow(q, local)
+    rt.forward(wq.struct())
+    target = rt.rgb.clone()
+    del rt, wq
+
+    opt = WindowOptimizer(params, views, target, lr=LR, device=local, tile_size=args.tile_size)
+    ctx = opt.r.ctx
+    opt.step(count=True)  # sizes the pair workspace
+    cap0 = opt.r.cap
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    # warm-up, with every kernel family timed once to find the dominant one
+    ctx.profile(B.KERNEL_FAMILIES)
+    for _ in range(max(args.warmup, 3)):
+        opt.step(count=False)
+    prof_all = ctx.profile_collect()
+    rc, need = opt.r.check_status()
+    if rc != B.GS_OK:
+        raise RuntimeError("pair capacity exceeded during warm-up (%d needed, %d reserved)" % (need, cap0))
+    dominant = max(prof_all, key=lambda k: prof_all[k][1])
+    ctx.profile([dominant])
+
+    K = args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    sampler = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
+    barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    launches0 = ctx.launch_count()
+    for k in range(K):
+        flush.zero_()  # L2 flush (256 MB write) outside the timed events
+        ev[k][0].record()
+        opt.step(count=False)
+        ev[k][1].record()
+    torch.cuda.synchronize()
+    barrier()
+    launches = ctx.launch_count() - launches0
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = float(sum(step_ms))
+    prof = ctx.profile_collect()
+    rc, need = opt.r.check_status()
+    if rc != B.GS_OK:
+        raise RuntimeError("pair capacity exceeded in the timed region (%d needed)" % need)
+    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    max_ms = float(t.item())
+    value = world * K / (max_ms / 1e3)
+
+    # roofline of the dominant kernel
+    dom_launches, dom_ms = prof.get(dominant, (0, 0.0))
+    avg_ms = dom_ms / max(dom_launches, 1)
+    hbm, hbm_kind = peaks()
+    fragments = float(opt.r.n_contrib.double().sum().item())
+    if dominant in FLOP_PER_FRAGMENT:
+        clk = 2032.0
+        peak = SM_COUNT * FP32_LANES * 2 * clk * 1e6 / 1e12
+        achieved = fragments * FLOP_PER_FRAGMENT[dominant] / (avg_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "avg_launch_ms": avg_ms,
+                "fragments_per_launch": fragments,
+                "peak_basis": "FP32 FMA peak: 148 SMs x 128 lanes x 2 FLOP x 2032 MHz (maximum SM clock)"}
+    else:
+        roof = {"bound": "hbm", "kernel": dominant, "achieved": None, "peak": hbm, "unit": "GB/s",
+                "frac": None, "traffic": None, "avg_launch_ms": avg_ms, "peak_kind": hbm_kind}
+
+    # end to end through the public API with host buffers: per step the window
+    # parameters and the keyframe targets go host->device from pinned memory,
+    # the loss and updated parameters come back device->host
+    host_params = opt.win.flat.detach().cpu().pin_memory()
+    host_target = target.cpu().pin_memory()
+    back_params = torch.empty_like(host_params).pin_memory()
+    back_loss = torch.empty(1, dtype=torch.float32).pin_memory()
+    ctx.profile([])
+    e_s, e_e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    E = args.e2e_steps
+    e_s.record()
+    for _ in range(E):
+        opt.win.flat.copy_(host_params, non_blocking=True)
+        target.copy_(host_target, non_blocking=True)
+        loss = opt.step(count=False)
+        back_loss.copy_(loss, non_blocking=True)
+        back_params.copy_(opt.win.flat, non_blocking=True)
+    e_e.record()
+    torch.cuda.synchronize()
+    e2e_ms = e_s.elapsed_time(e_e) / E
+    h2d = host_params.numel() * 4 + host_target.numel() * 4
+    d2h = back_params.numel() * 4 + 4
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        sec, threads, desc = cpu_oracle_iteration(params, views, args.cpu_pixels)
+        cpu = {"value": 1.0 / sec, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc}
+
+    if rank == 0:
+        mpix = world * K * N_VIEWS * W_IMG * H_IMG / (max_ms / 1e3) / 1e6
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+                "warmup": args.warmup, "ms_per_step": max_ms / K, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "n_gaussians": N_GAUSS, "views": N_VIEWS,
+                           "image": [W_IMG, H_IMG], "tile_size": args.tile_size, "sh_degree": 1, "lr": LR,
+                           "l2": "flushed between steps (256 MB write outside the timed events)",
+                           "pairs_per_step": int(opt.r.last_pairs), "parallelism": "replicas" if world > 1 else "1 GPU",
+                           "mpix_per_s": mpix},
+                "roofline": roof,
+                "kernel_ms_per_step": {k: v[1] / max(1, len(range(max(args.warmup, 3)))) for k, v in prof_all.items()},
+                "cpu_baseline": cpu,
+                "e2e": {"value": 1e3 / e2e_ms, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                        "d2h_bytes_per_step": int(d2h)},
+                "gpu_launches": int(launches), "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_b300(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,322 @@
+/*
+ * gs.h - C ABI of the B300 (sm_103a) differentiable Gaussian-splatting path
+ * of GS-LIVO (arXiv 2501.08672).
+ *
+ * The library renders a sliding window of 3D Gaussians into one or more
+ * keyframe views and back-propagates a photometric loss to the Gaussian
+ * attributes (window map optimisation, Sec. II-B.2) and to the camera pose
+ * (photometric pose update, Sec. II-D and Appendix A).  One iteration is
+ *
+ *   gs_project -> gs_bin -> gs_render_fwd -> gs_l1_loss -> gs_render_bwd
+ *   -> gs_adam_step
+ *
+ * and the odometry form replaces the last two by gs_pose_grad.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Pointers named *_dev, and every array pointer inside gs_gaussians,
+ *   gs_grads and gs_workspace, are DEVICE pointers on the context's device.
+ *   gs_view arrays and gs_config are HOST memory, read during the call only.
+ * - Every call is asynchronous and stream-ordered on the given stream
+ *   (a cudaStream_t; NULL is the legacy default stream).  No call allocates
+ *   device memory, synchronises or copies to the host, except
+ *   gs_context_create / gs_context_destroy (allocate / free a small status
+ *   block), gs_sync_status and gs_bin with a non-NULL pairs_needed (both
+ *   synchronise the stream).  Hence a whole iteration can be captured in a
+ *   CUDA graph once gs_workspace_query has sized the workspace.
+ * - The caller owns every buffer it passes.  A context is not thread-safe;
+ *   use one context per host thread.
+ * - Return value: GS_OK (0) or a negative gs_status.  Argument errors are
+ *   detected on the host before anything is launched.  Errors found on the
+ *   device (pair-capacity overflow) are latched in the context and reported
+ *   by gs_sync_status.  No C++ exception crosses this interface and nothing
+ *   aborts the process.  gs_last_error returns a message for the last error.
+ *
+ * Geometry (Sec. II-B.1, Eqs. 3dgs, q, spat)
+ * ------------------------------------------
+ * - Camera: p_C = R_CW p_W + t_CW; x right, y down, z forward; pinhole
+ *   q = (fx x/z + cx, fy y/z + cy); pixel (u, v) is sampled at its centre
+ *   (u + 0.5, v + 0.5).
+ * - Gaussian: mean p_W; Sigma3 = R(q) S S^T R(q)^T with S = diag(exp(s)) and
+ *   R(q) the rotation of the normalised quaternion (w, x, y, z);
+ *   Sigma2 = J R_CW Sigma3 R_CW^T J^T + blur I with J the Jacobian of the
+ *   pinhole map; opacity sigmoid(o); colour from real spherical harmonics of
+ *   degree 0 or 1 along the unit direction from the camera centre to the
+ *   mean: c = max(0, C0 k0 + C1 (-d_y k1 + d_z k2 - d_x k3) + 0.5).
+ * - Compositing (Eq. raster): per pixel, front to back over the Gaussians
+ *   ordered by (depth, index): alpha = min(alpha_max, sigma G(x)); skip if
+ *   alpha < alpha_min; stop before the Gaussian that would take the
+ *   transmittance below T_min; C += c alpha T; T *= 1 - alpha.  Output
+ *   C + T bg.  The set of Gaussians tested at a pixel is every Gaussian
+ *   whose alpha can reach alpha_min there, so the image does not depend on
+ *   the tile size.
+ */
+#ifndef GS_B300_GS_H
+#define GS_B300_GS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Symbols of this interface are exported; everything else in the library is
+ * hidden. */
+#if defined(__GNUC__)
+#define GS_API __attribute__((visibility("default")))
+#else
+#define GS_API
+#endif
+
+/* Opaque CUDA stream handle (a cudaStream_t). */
+typedef struct CUstream_st* gs_stream;
+
+typedef enum gs_status {
+    GS_OK = 0,
+    GS_ERR_INVALID_ARG = -1, /* bad pointer, size, dtype, view or config */
+    GS_ERR_CUDA = -2,        /* a CUDA runtime call or launch failed */
+    GS_ERR_OOM = -3,         /* context status block could not be allocated */
+    GS_ERR_CAPACITY = -4,    /* more (Gaussian, tile) pairs than the workspace holds */
+    GS_ERR_TIMEOUT = -5,     /* reserved: a bounded device wait expired */
+    GS_ERR_NONFINITE = -6,   /* a camera or intrinsic value is not finite */
+    GS_ERR_UNSUPPORTED = -7  /* option not built into this library */
+} gs_status;
+
+typedef enum gs_dtype { GS_F32 = 0, GS_F16 = 1, GS_BF16 = 2 } gs_dtype;
+
+#define GS_MAX_VIEWS 64
+
+/* Rasteriser constants.  gs_config_default fills the defaults in brackets
+ * (the constants of the 3D-GS tile rasteriser the paper builds on,
+ * Sec. II-C).  alpha_min = 0, alpha_max = 1, T_min = 0 gives Eq. raster
+ * literally ("exact mode"). */
+typedef struct gs_config {
+    int32_t tile_size; /* 8, 16 or 32 [16] */
+    float alpha_min;   /* [1/255] */
+    float alpha_max;   /* [0.99] */
+    float T_min;       /* [1e-4] */
+    float blur;        /* low-pass term added to the diagonal of Sigma2, px^2 [0.3] */
+    float z_near;      /* Gaussians with camera depth <= z_near are culled, m [0.2] */
+    float bg[3];       /* background colour [0, 0, 0] */
+} gs_config;
+
+GS_API void gs_config_default(gs_config* cfg);
+
+typedef struct gs_ctx gs_ctx;
+
+/* Creates a context on CUDA device `device` (made current for the call).
+ * cfg may be NULL for the defaults.  Allocates a small device status block.
+ * Errors: GS_ERR_INVALID_ARG (out NULL, bad config), GS_ERR_CUDA, GS_ERR_OOM. */
+GS_API int gs_context_create(gs_ctx** out, int device, const gs_config* cfg);
+/* Frees the context and its status block.  NULL is accepted. */
+GS_API int gs_context_destroy(gs_ctx* ctx);
+/* Message of the last error on this context ("" if none); valid until the
+ * next call on the context. */
+GS_API const char* gs_last_error(const gs_ctx* ctx);
+/* Copies the context's configuration into *cfg. */
+GS_API int gs_get_config(const gs_ctx* ctx, gs_config* cfg);
+
+/* One keyframe view (host memory).  The view renders the contiguous Gaussian
+ * range [g_begin, g_end) of the window, mirroring the paper's contiguous GPU
+ * Gaussian buffer (Sec. II-C); 0 <= g_begin < g_end <= n is required.  Views are
+ * packed one after another in every per-pixel and per-record buffer in the
+ * order given: view v's pixels start at pixel offset sum_{u<v} W_u H_u, its
+ * projected records at sum_{u<v} (g_end_u - g_begin_u). */
+typedef struct gs_view {
+    float R_cw[9]; /* camera-from-world rotation, row-major */
+    float t_cw[3]; /* camera-from-world translation */
+    float fx, fy, cx, cy;
+    int32_t width, height;
+    int64_t g_begin, g_end;
+} gs_view;
+
+/* The Gaussian window (device memory, structure of arrays, row-major).
+ * means is always FP32; the other fields may be stored in FP16 or BF16
+ * (all arithmetic is FP32). */
+typedef struct gs_gaussians {
+    const float* means;     /* [N,3] world metres */
+    const void* log_scales; /* [N,3] log of the standard deviations */
+    const void* quats;      /* [N,4] (w, x, y, z), need not be normalised */
+    const void* opacity;    /* [N] logit of the opacity */
+    const void* sh;         /* [N,K,3], K = (sh_degree+1)^2, coefficient-major */
+    int32_t scale_dtype, rot_dtype, opacity_dtype, sh_dtype; /* gs_dtype */
+    int64_t n;
+    int32_t sh_degree; /* 0 or 1 */
+} gs_gaussians;
+
+/* Gradients (device memory, FP32, same shapes as gs_gaussians).  Every entry
+ * is overwritten, including Gaussians that no view sees (zero). */
+typedef struct gs_grads {
+    float* means;
+    float* log_scales;
+    float* quats;
+    float* opacity;
+    float* sh;
+} gs_grads;
+
+/* Caller-allocated device workspace holding the projected records, the
+ * sorted (tile, depth) pairs, the per-tile ranges and the per-record 2D
+ * gradients of one batch of views.  `bytes` must be at least what
+ * gs_workspace_query returned for the same views and max_pairs; the base
+ * pointer must be 256-byte aligned (cudaMalloc and torch allocations are). */
+typedef struct gs_workspace {
+    void* ptr;
+    size_t bytes;
+    int64_t max_pairs; /* capacity for (Gaussian, tile) pairs */
+} gs_workspace;
+
+/* Byte offsets of the workspace arrays, for inspection and tests. */
+typedef struct gs_ws_layout {
+    size_t records;       /* float[M][12]: qx, qy, A', B', C', log2(opacity), r, g, b, depth, 0, 0 */
+    size_t rects;         /* int32[M][4]: x0|y0<<16, x1|y1<<16, first tile id of the view, tiles_x */
+    size_t tiles_touched; /* uint32[M] */
+    size_t depth_keys;    /* uint32[M] sorted depth bits (two buffers) */
+    size_t depth_vals;    /* uint32[M] record indices in front-to-back order */
+    size_t pair_offsets;  /* uint64[M] */
+    size_t pair_keys;     /* uint32[max_pairs] x 2 */
+    size_t pair_vals;     /* uint32[max_pairs] x 2 */
+    size_t sorted_vals;   /* the buffer holding the sorted record index per pair */
+    size_t tile_ranges;   /* uint32[T][2] [start, end) into sorted_vals */
+    size_t grad2d;        /* float[M][9] per-record 2D gradients */
+    size_t counters;      /* uint64[8]: [0] pairs needed */
+    size_t total;         /* bytes */
+    int64_t n_records;    /* M */
+    int32_t n_tiles;      /* T */
+    int64_t n_pixels;
+} gs_ws_layout;
+
+/* Workspace size for `n_views` views and a pair capacity max_pairs.
+ * Errors: GS_ERR_INVALID_ARG. */
+GS_API int gs_workspace_query(const gs_ctx* ctx, const gs_view* views, int n_views, int64_t max_pairs,
+                       size_t* bytes);
+GS_API int gs_workspace_layout(const gs_ctx* ctx, const gs_view* views, int n_views, int64_t max_pairs,
+                        gs_ws_layout* out);
+
+/* a1: EWA projection of every (view, Gaussian) pair (Sec. II-B.1, Eqs. 3dgs,
+ * q, spat; colour from SH; opacity sigmoid).  Writes the projected records,
+ * tile rectangles and tiles-touched counts into the workspace.
+ * Errors: GS_ERR_INVALID_ARG, GS_ERR_NONFINITE, GS_ERR_CUDA. */
+GS_API int gs_project(gs_ctx* ctx, const gs_gaussians* g, const gs_view* views, int n_views,
+               const gs_workspace* ws, gs_stream stream);
+
+/* a2: tile binning.  Orders the records front to back (radix sort of the
+ * FP32 depth bits, stable in record index), expands each record into one
+ * pair per tile its footprint touches, and stably radix-sorts the pairs by
+ * global tile id, so each tile's list is ordered by (depth, index): the
+ * order a radix sort of 64-bit (tile << 32 | depth) keys gives.  Then
+ * extracts each tile's [start, end) range.  The tile sort is implied by the
+ * 3D-GS rasteriser the paper relies on (Sec. II-C).
+ * pairs_needed: NULL (fully asynchronous) or a host pointer that receives
+ * the number of pairs after a stream synchronisation.
+ * Errors: GS_ERR_INVALID_ARG, GS_ERR_CUDA; with pairs_needed non-NULL also
+ * GS_ERR_CAPACITY when the pairs exceed ws->max_pairs (the render is then
+ * incomplete; call again with a larger workspace). */
+GS_API int gs_bin(gs_ctx* ctx, const gs_view* views, int n_views, const gs_workspace* ws,
+           uint64_t* pairs_needed, gs_stream stream);
+
+/* a3: front-to-back alpha compositing (Sec. II-B.2, Eq. raster), one CTA per
+ * tile over the tile's sorted list, staged in shared memory, stopping early
+ * once every pixel's transmittance is below T_min.
+ * Outputs (device, packed over views): rgb [sum 3 H W] (view v planar
+ * [3,H,W]), T_final [sum H W], n_contrib [sum H W] (1 + position in the
+ * tile's list of the last contributing Gaussian, 0 if none; consumed by
+ * gs_render_bwd).  Errors: GS_ERR_INVALID_ARG, GS_ERR_CUDA. */
+GS_API int gs_render_fwd(gs_ctx* ctx, const gs_view* views, int n_views, const gs_workspace* ws,
+                  float* rgb, float* T_final, uint32_t* n_contrib, gs_stream stream);
+
+/* a4: photometric loss (Eq. gaussian_optimization, L1 norm):
+ * L = (1/V) sum_v mean_{3 H_v W_v} |rgb - target| written to loss_dev[0], and
+ * dL/drgb = sign(rgb - target) / (3 H_v W_v V) written to dL_drgb (sign(0) = 0).
+ * loss_dev may be NULL.  Errors: GS_ERR_INVALID_ARG, GS_ERR_CUDA. */
+GS_API int gs_l1_loss(gs_ctx* ctx, const gs_view* views, int n_views, const gs_workspace* ws,
+               const float* rgb, const float* target, float* dL_drgb, float* loss_dev,
+               gs_stream stream);
+
+/* a5 + a6 (+ a7): backward of the compositing (reverse order from n_contrib,
+ * alpha recomputed, transmittance recovered by division) into per-record 2D
+ * gradients, then backward of the projection to every Gaussian parameter
+ * (summed over views) and, if dL_dpose_dev is non-NULL, to each view's pose.
+ * dL_dpose_dev: [n_views][6] = dL/d(dphi_x, dphi_y, dphi_z, dt_x, dt_y, dt_z)
+ * for the left perturbation T_CW <- Exp(dphi, dt) T_CW (Appendix A,
+ * perturbation model).  grads may be NULL only when dL_dpose_dev is not.
+ * Clamped alpha and colour, culling and the footprint are locally constant.
+ * Errors: GS_ERR_INVALID_ARG, GS_ERR_CUDA. */
+GS_API int gs_render_bwd(gs_ctx* ctx, const gs_gaussians* g, const gs_view* views, int n_views,
+                  const gs_workspace* ws, const float* T_final, const uint32_t* n_contrib,
+                  const float* dL_drgb, const gs_grads* grads, float* dL_dpose_dev,
+                  gs_stream stream);
+
+/* a7: photometric pose gradient only (Sec. II-D, Eq. minimization; the
+ * derivative chain of Eqs. grad_meani_rcw to grad_covi_tcw restricted to the
+ * camera pose): gs_render_bwd with grads = NULL.  dL_dpose_dev is required. */
+GS_API int gs_pose_grad(gs_ctx* ctx, const gs_gaussians* g, const gs_view* views, int n_views,
+                 const gs_workspace* ws, const float* T_final, const uint32_t* n_contrib,
+                 const float* dL_drgb, float* dL_dpose_dev, gs_stream stream);
+
+/* Optional low-precision render copy written by gs_adam_step: elements
+ * [begin, end) of the FP32 parameter vector are also stored, converted to
+ * `dtype`, at dst[i - begin]. */
+typedef struct gs_lowp_segment {
+    int64_t begin, end;
+    int32_t dtype; /* GS_F16 or GS_BF16 */
+    void* dst;
+} gs_lowp_segment;
+
+/* a8: one Adam step (Sec. II-B.2, "Adam optimizer"; Kingma & Ba with bias
+ * correction, the update rule of torch.optim.Adam) over n FP32 parameters in
+ * place: m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;
+ * p -= lr / (1 - b1^step) * m / (sqrt(v) / sqrt(1 - b2^step) + eps).
+ * step >= 1.  segs: up to 8 low-precision copies (may be NULL).
+ * Errors: GS_ERR_INVALID_ARG, GS_ERR_CUDA. */
+GS_API int gs_adam_step(gs_ctx* ctx, float* param, const float* grad, float* m, float* v, int64_t n,
+                 float lr, float b1, float b2, float eps, int64_t step,
+                 const gs_lowp_segment* segs, int n_segs, gs_stream stream);
+
+/* Synchronises `stream`, returns and clears the latched device status
+ * (GS_OK or GS_ERR_CAPACITY); pairs_needed (nullable, host) receives the
+ * pair count of the last gs_bin on this context. */
+GS_API int gs_sync_status(gs_ctx* ctx, gs_stream stream, uint64_t* pairs_needed);
+
+/* Kernel families, for profiling (bit i of a mask selects family i). */
+typedef enum gs_kernel_family {
+    GS_KF_PROJECT = 0,     /* a1 projection */
+    GS_KF_DEPTH_SORT = 1,  /* a2 radix sort of record depths */
+    GS_KF_TILE_SCAN = 2,   /* a2 scan of tiles touched */
+    GS_KF_EMIT = 3,        /* a2 pair emission */
+    GS_KF_TILE_SORT = 4,   /* a2 radix sort of pairs by tile */
+    GS_KF_RANGES = 5,      /* a2 tile ranges */
+    GS_KF_RASTER_FWD = 6,  /* a3 compositing */
+    GS_KF_L1 = 7,          /* a4 loss */
+    GS_KF_RASTER_BWD = 8,  /* a5 compositing backward */
+    GS_KF_PROJECT_BWD = 9, /* a6/a7 projection backward and pose reduction */
+    GS_KF_ADAM = 10,       /* a8 Adam */
+    GS_KF_COUNT = 11
+} gs_kernel_family;
+
+typedef struct gs_profile_entry {
+    int32_t family;   /* gs_kernel_family */
+    int32_t launches; /* timed launches since the last collect */
+    double total_ms;  /* summed CUDA-event time of those launches */
+} gs_profile_entry;
+
+/* Tracing: when bit f of family_mask is set, every launch of family f is
+ * bracketed by CUDA events on its stream (events are created on first use,
+ * outside any stream capture; disable profiling before capturing a graph).
+ * 0 disables.  Errors: GS_ERR_INVALID_ARG. */
+GS_API int gs_profile_enable(gs_ctx* ctx, uint32_t family_mask);
+/* Synchronises `stream`, writes one entry per family with timed launches
+ * (at most max_entries) and clears the record.  *n_out receives the count. */
+GS_API int gs_profile_collect(gs_ctx* ctx, gs_stream stream, gs_profile_entry* out, int max_entries,
+                              int* n_out);
+/* Number of kernel launches (and memset nodes) this context has issued. */
+GS_API int64_t gs_launch_count(const gs_ctx* ctx);
+
+/* Library version string. */
+GS_API const char* gs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GS_B300_GS_H */

@@ -1,0 +1,334 @@
+"""ctypes binding of libgs_b300.so (include/gs.h): argument marshalling only.
+
+Every step of the path runs in the library's CUDA kernels; this module builds
+the C structs from torch tensors and view dicts and checks return codes.  It
+raises if the library is missing: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import numpy as np
+import torch  # noqa: F401  (loads the CUDA runtime the library links against)
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgs_b300.so")
+
+GS_OK = 0
+GS_ERR_INVALID_ARG = -1
+GS_ERR_CUDA = -2
+GS_ERR_OOM = -3
+GS_ERR_CAPACITY = -4
+GS_ERR_TIMEOUT = -5
+GS_ERR_NONFINITE = -6
+GS_ERR_UNSUPPORTED = -7
+GS_F32, GS_F16, GS_BF16 = 0, 1, 2
+GS_MAX_VIEWS = 64
+
+_DTYPE = {torch.float32: GS_F32, torch.float16: GS_F16, torch.bfloat16: GS_BF16}
+
+EXPORTED = ["gs_config_default", "gs_version", "gs_context_create", "gs_context_destroy", "gs_last_error",
+            "gs_get_config", "gs_workspace_query", "gs_workspace_layout", "gs_project", "gs_bin",
+            "gs_render_fwd", "gs_l1_loss", "gs_render_bwd", "gs_pose_grad", "gs_adam_step", "gs_sync_status",
+            "gs_profile_enable", "gs_profile_collect", "gs_launch_count"]
+
+KERNEL_FAMILIES = ["project", "depth_sort", "tile_scan", "emit", "tile_sort", "ranges", "raster_fwd", "l1",
+                   "raster_bwd", "project_bwd", "adam"]
+
+
+class GsError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("gs status %d: %s" % (code, msg))
+        self.code = code
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("tile_size", ctypes.c_int32), ("alpha_min", ctypes.c_float), ("alpha_max", ctypes.c_float),
+                ("T_min", ctypes.c_float), ("blur", ctypes.c_float), ("z_near", ctypes.c_float),
+                ("bg", ctypes.c_float * 3)]
+
+
+class View(ctypes.Structure):
+    _fields_ = [("R_cw", ctypes.c_float * 9), ("t_cw", ctypes.c_float * 3), ("fx", ctypes.c_float),
+                ("fy", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float),
+                ("width", ctypes.c_int32), ("height", ctypes.c_int32), ("g_begin", ctypes.c_int64),
+                ("g_end", ctypes.c_int64)]
+
+
+class Gaussians(ctypes.Structure):
+    _fields_ = [("means", ctypes.c_void_p), ("log_scales", ctypes.c_void_p), ("quats", ctypes.c_void_p),
+                ("opacity", ctypes.c_void_p), ("sh", ctypes.c_void_p), ("scale_dtype", ctypes.c_int32),
+                ("rot_dtype", ctypes.c_int32), ("opacity_dtype", ctypes.c_int32), ("sh_dtype", ctypes.c_int32),
+                ("n", ctypes.c_int64), ("sh_degree", ctypes.c_int32)]
+
+
+class Grads(ctypes.Structure):
+    _fields_ = [("means", ctypes.c_void_p), ("log_scales", ctypes.c_void_p), ("quats", ctypes.c_void_p),
+                ("opacity", ctypes.c_void_p), ("sh", ctypes.c_void_p)]
+
+
+class Workspace(ctypes.Structure):
+    _fields_ = [("ptr", ctypes.c_void_p), ("bytes", ctypes.c_size_t), ("max_pairs", ctypes.c_int64)]
+
+
+class WsLayout(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_size_t) for n in ("records", "rects", "tiles_touched", "depth_keys", "depth_vals",
+                                               "pair_offsets", "pair_keys", "pair_vals", "sorted_vals",
+                                               "tile_ranges", "grad2d", "counters", "total")] + [
+        ("n_records", ctypes.c_int64), ("n_tiles", ctypes.c_int32), ("n_pixels", ctypes.c_int64)]
+
+
+class ProfileEntry(ctypes.Structure):
+    _fields_ = [("family", ctypes.c_int32), ("launches", ctypes.c_int32), ("total_ms", ctypes.c_double)]
+
+
+class LowpSegment(ctypes.Structure):
+    _fields_ = [("begin", ctypes.c_int64), ("end", ctypes.c_int64), ("dtype", ctypes.c_int32),
+                ("dst", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def lib():
+    """Loads libgs_b300.so; raises if it is missing (build it with
+    `python -m paper_2501_08672_b300.build`)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libgs_b300.so not found at %s: build it with "
+                               "`python -m paper_2501_08672_b300.build`" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        P, I, I64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
+        L.gs_config_default.argtypes = [ctypes.POINTER(Config)]
+        L.gs_config_default.restype = None
+        L.gs_version.restype = ctypes.c_char_p
+        L.gs_context_create.argtypes = [ctypes.POINTER(P), I, ctypes.POINTER(Config)]
+        L.gs_context_destroy.argtypes = [P]
+        L.gs_last_error.argtypes = [P]
+        L.gs_last_error.restype = ctypes.c_char_p
+        L.gs_get_config.argtypes = [P, ctypes.POINTER(Config)]
+        L.gs_workspace_query.argtypes = [P, ctypes.POINTER(View), I, I64, ctypes.POINTER(ctypes.c_size_t)]
+        L.gs_workspace_layout.argtypes = [P, ctypes.POINTER(View), I, I64, ctypes.POINTER(WsLayout)]
+        L.gs_project.argtypes = [P, ctypes.POINTER(Gaussians), ctypes.POINTER(View), I, ctypes.POINTER(Workspace), P]
+        L.gs_bin.argtypes = [P, ctypes.POINTER(View), I, ctypes.POINTER(Workspace), ctypes.POINTER(ctypes.c_uint64), P]
+        L.gs_render_fwd.argtypes = [P, ctypes.POINTER(View), I, ctypes.POINTER(Workspace), P, P, P, P]
+        L.gs_l1_loss.argtypes = [P, ctypes.POINTER(View), I, ctypes.POINTER(Workspace), P, P, P, P, P]
+        L.gs_render_bwd.argtypes = [P, ctypes.POINTER(Gaussians), ctypes.POINTER(View), I, ctypes.POINTER(Workspace),
+                                    P, P, P, ctypes.POINTER(Grads), P, P]
+        L.gs_pose_grad.argtypes = [P, ctypes.POINTER(Gaussians), ctypes.POINTER(View), I, ctypes.POINTER(Workspace),
+                                   P, P, P, P, P]
+        L.gs_adam_step.argtypes = [P, P, P, P, P, I64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                   ctypes.c_float, I64, ctypes.POINTER(LowpSegment), I, P]
+        L.gs_sync_status.argtypes = [P, P, ctypes.POINTER(ctypes.c_uint64)]
+        L.gs_profile_enable.argtypes = [P, ctypes.c_uint32]
+        L.gs_profile_collect.argtypes = [P, P, ctypes.POINTER(ProfileEntry), I, ctypes.POINTER(ctypes.c_int)]
+        L.gs_launch_count.argtypes = [P]
+        L.gs_launch_count.restype = ctypes.c_int64
+        _lib = L
+    return _lib
+
+
+def default_config(**kw):
+    c = Config()
+    lib().gs_config_default(ctypes.byref(c))
+    for k, v in kw.items():
+        if k == "bg":
+            for i in range(3):
+                c.bg[i] = float(v[i])
+        else:
+            setattr(c, k, v)
+    return c
+
+
+def make_views(views):
+    """Host array of gs_view from view dicts (R, t, fx, fy, cx, cy, W, H,
+    g_begin, g_end)."""
+    arr = (View * len(views))()
+    for i, v in enumerate(views):
+        R = np.asarray(v["R"], np.float32).reshape(9)
+        t = np.asarray(v["t"], np.float32).reshape(3)
+        for k in range(9):
+            arr[i].R_cw[k] = float(R[k])
+        for k in range(3):
+            arr[i].t_cw[k] = float(t[k])
+        arr[i].fx, arr[i].fy, arr[i].cx, arr[i].cy = float(v["fx"]), float(v["fy"]), float(v["cx"]), float(v["cy"])
+        arr[i].width, arr[i].height = int(v["W"]), int(v["H"])
+        arr[i].g_begin, arr[i].g_end = int(v["g_begin"]), int(v["g_end"])
+    return arr
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _check_dev(t, name, dtype=None, numel=None):
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous()):
+        raise ValueError("%s must be a contiguous CUDA tensor" % name)
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError("%s must be %s, got %s" % (name, dtype, t.dtype))
+    if numel is not None and t.numel() != numel:
+        raise ValueError("%s must have %d elements, got %d" % (name, numel, t.numel()))
+
+
+def gaussians_struct(means, log_scales, quats, opacity, sh, sh_degree):
+    n = means.shape[0]
+    K = (sh_degree + 1) ** 2
+    _check_dev(means, "means", torch.float32, 3 * n)
+    _check_dev(log_scales, "log_scales", None, 3 * n)
+    _check_dev(quats, "quats", None, 4 * n)
+    _check_dev(opacity, "opacity", None, n)
+    _check_dev(sh, "sh", None, 3 * K * n)
+    g = Gaussians()
+    g.means, g.log_scales, g.quats = means.data_ptr(), log_scales.data_ptr(), quats.data_ptr()
+    g.opacity, g.sh = opacity.data_ptr(), sh.data_ptr()
+    g.scale_dtype, g.rot_dtype = _DTYPE[log_scales.dtype], _DTYPE[quats.dtype]
+    g.opacity_dtype, g.sh_dtype = _DTYPE[opacity.dtype], _DTYPE[sh.dtype]
+    g.n = n
+    g.sh_degree = sh_degree
+    return g
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Context:
+    """One gs_ctx: configuration, status block, and the C-ABI calls."""
+
+    def __init__(self, device=0, **cfg):
+        self.cfg = default_config(**cfg)
+        self.device = device
+        h = ctypes.c_void_p()
+        rc = lib().gs_context_create(ctypes.byref(h), int(device), ctypes.byref(self.cfg))
+        if rc != GS_OK:
+            raise GsError(rc, "gs_context_create failed")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().gs_context_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _ck(self, rc):
+        if rc != GS_OK:
+            raise GsError(rc, lib().gs_last_error(self.h).decode())
+        return rc
+
+    def workspace_bytes(self, views, max_pairs):
+        n = ctypes.c_size_t()
+        self._ck(lib().gs_workspace_query(self.h, views, len(views), int(max_pairs), ctypes.byref(n)))
+        return n.value
+
+    def layout(self, views, max_pairs):
+        L = WsLayout()
+        self._ck(lib().gs_workspace_layout(self.h, views, len(views), int(max_pairs), ctypes.byref(L)))
+        return L
+
+    @staticmethod
+    def ws_struct(ws_tensor, max_pairs):
+        w = Workspace()
+        w.ptr, w.bytes, w.max_pairs = ws_tensor.data_ptr(), ws_tensor.numel(), int(max_pairs)
+        return w
+
+    def project(self, g, views, ws, stream=None):
+        self._ck(lib().gs_project(self.h, ctypes.byref(g), views, len(views), ctypes.byref(ws), _stream(stream)))
+
+    def bin(self, views, ws, want_count=False, stream=None):
+        """Returns the pair count (synchronising) when want_count, else None.
+        Raises GsError(GS_ERR_CAPACITY) when want_count and the workspace is
+        too small."""
+        if want_count:
+            n = ctypes.c_uint64()
+            rc = lib().gs_bin(self.h, views, len(views), ctypes.byref(ws), ctypes.byref(n), _stream(stream))
+            if rc == GS_ERR_CAPACITY:
+                err = GsError(rc, lib().gs_last_error(self.h).decode())
+                err.pairs_needed = n.value
+                # clear the latched device status as well
+                lib().gs_sync_status(self.h, _stream(stream), None)
+                raise err
+            self._ck(rc)
+            return n.value
+        self._ck(lib().gs_bin(self.h, views, len(views), ctypes.byref(ws), None, _stream(stream)))
+        return None
+
+    def render_fwd(self, views, ws, rgb, T_final, n_contrib, stream=None):
+        self._ck(lib().gs_render_fwd(self.h, views, len(views), ctypes.byref(ws), _ptr(rgb), _ptr(T_final),
+                                     _ptr(n_contrib), _stream(stream)))
+
+    def l1_loss(self, views, ws, rgb, target, dL_drgb, loss=None, stream=None):
+        self._ck(lib().gs_l1_loss(self.h, views, len(views), ctypes.byref(ws), _ptr(rgb), _ptr(target),
+                                  _ptr(dL_drgb), _ptr(loss), _stream(stream)))
+
+    def render_bwd(self, g, views, ws, T_final, n_contrib, dL_drgb, grads=None, dL_dpose=None, stream=None):
+        gr = None
+        if grads is not None:
+            gr = Grads()
+            gr.means, gr.log_scales, gr.quats, gr.opacity, gr.sh = [t.data_ptr() for t in grads]
+        self._ck(lib().gs_render_bwd(self.h, ctypes.byref(g), views, len(views), ctypes.byref(ws), _ptr(T_final),
+                                     _ptr(n_contrib), _ptr(dL_drgb), ctypes.byref(gr) if gr is not None else None,
+                                     _ptr(dL_dpose), _stream(stream)))
+
+    def pose_grad(self, g, views, ws, T_final, n_contrib, dL_drgb, dL_dpose, stream=None):
+        self._ck(lib().gs_pose_grad(self.h, ctypes.byref(g), views, len(views), ctypes.byref(ws), _ptr(T_final),
+                                    _ptr(n_contrib), _ptr(dL_drgb), _ptr(dL_dpose), _stream(stream)))
+
+    def adam_step(self, param, grad, m, v, lr, b1, b2, eps, step, segments=(), stream=None):
+        segs = None
+        ns = len(segments)
+        if ns:
+            segs = (LowpSegment * ns)()
+            for k, (b, e, dst) in enumerate(segments):
+                segs[k].begin, segs[k].end, segs[k].dtype, segs[k].dst = int(b), int(e), _DTYPE[dst.dtype], dst.data_ptr()
+        self._ck(lib().gs_adam_step(self.h, _ptr(param), _ptr(grad), _ptr(m), _ptr(v), param.numel(), float(lr),
+                                    float(b1), float(b2), float(eps), int(step), segs, ns, _stream(stream)))
+
+    def profile(self, families):
+        """Times every launch of the named kernel families with CUDA events."""
+        mask = 0
+        for f in families:
+            mask |= 1 << KERNEL_FAMILIES.index(f)
+        self._ck(lib().gs_profile_enable(self.h, mask))
+
+    def profile_collect(self, stream=None):
+        """{family: (launches, total_ms)} since the last collect (synchronises)."""
+        out = (ProfileEntry * len(KERNEL_FAMILIES))()
+        n = ctypes.c_int()
+        self._ck(lib().gs_profile_collect(self.h, _stream(stream), out, len(KERNEL_FAMILIES), ctypes.byref(n)))
+        return {KERNEL_FAMILIES[out[k].family]: (out[k].launches, out[k].total_ms) for k in range(n.value)}
+
+    def launch_count(self):
+        return int(lib().gs_launch_count(self.h))
+
+    def sync_status(self, stream=None):
+        n = ctypes.c_uint64()
+        rc = lib().gs_sync_status(self.h, _stream(stream), ctypes.byref(n))
+        return rc, n.value
+
+
+def pixel_counts(views):
+    return [int(v["W"]) * int(v["H"]) for v in views]
+
+
+def unpack_images(flat, views, channels=3):
+    """Splits a packed per-view buffer into a list of [C,H,W] (or [H,W]) views."""
+    out, off = [], 0
+    for v in views:
+        n = int(v["W"]) * int(v["H"]) * channels
+        t = flat[off:off + n]
+        out.append(t.view(channels, int(v["H"]), int(v["W"])) if channels > 1 else t.view(int(v["H"]), int(v["W"])))
+        off += n
+    return out
+
+
+def suggest_capacity(n_pairs, headroom=1.25):
+    return int(math.ceil(max(n_pairs, 1024) * headroom))

@@ -1,0 +1,114 @@
+// Adam step over the flat FP32 parameter vector of the window (Sec. II-B.2,
+// "Adam optimizer"; Kingma & Ba with bias correction as in torch.optim.Adam).
+// HBM-bound: reads p, g, m, v and writes p, m, v (28 B per parameter), plus
+// 2 B per parameter for an optional FP16/BF16 render copy.
+#include "gs_internal.cuh"
+
+namespace gsb {
+
+namespace {
+
+struct SegTable {
+    long long begin[8], end[8];
+    void* dst[8];
+    int dtype[8];
+    int n;
+};
+
+__device__ __forceinline__ void store_lowp(const SegTable& st, long long i, float x) {
+    for (int s = 0; s < st.n; ++s) {
+        if (i >= st.begin[s] && i < st.end[s]) {
+            const long long o = i - st.begin[s];
+            if (st.dtype[s] == GS_F16)
+                static_cast<__half*>(st.dst[s])[o] = __float2half_rn(x);
+            else
+                static_cast<__nv_bfloat16*>(st.dst[s])[o] = __float2bfloat16_rn(x);
+        }
+    }
+}
+
+__device__ __forceinline__ float adam1(float& p, float g, float& m, float& v, float b1, float b2,
+                                       float eps, float step_size, float inv_sqrt_bc2) {
+    m = fmaf(b1, m, (1.f - b1) * g);
+    v = fmaf(b2, v, (1.f - b2) * g * g);
+    const float denom = sqrtf(v) * inv_sqrt_bc2 + eps;
+    p = p - step_size * (m / denom);
+    return p;
+}
+
+__global__ void __launch_bounds__(256) k_adam4(float4* __restrict__ p, const float4* __restrict__ g,
+                                               float4* __restrict__ m, float4* __restrict__ v,
+                                               long long n4, float b1, float b2, float eps,
+                                               float step_size, float inv_sqrt_bc2, SegTable st) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n4;
+         i += (long long)gridDim.x * blockDim.x) {
+        float4 pp = p[i], gg = g[i], mm = m[i], vv = v[i];
+        adam1(pp.x, gg.x, mm.x, vv.x, b1, b2, eps, step_size, inv_sqrt_bc2);
+        adam1(pp.y, gg.y, mm.y, vv.y, b1, b2, eps, step_size, inv_sqrt_bc2);
+        adam1(pp.z, gg.z, mm.z, vv.z, b1, b2, eps, step_size, inv_sqrt_bc2);
+        adam1(pp.w, gg.w, mm.w, vv.w, b1, b2, eps, step_size, inv_sqrt_bc2);
+        p[i] = pp;
+        m[i] = mm;
+        v[i] = vv;
+        if (st.n) {
+            store_lowp(st, 4 * i + 0, pp.x);
+            store_lowp(st, 4 * i + 1, pp.y);
+            store_lowp(st, 4 * i + 2, pp.z);
+            store_lowp(st, 4 * i + 3, pp.w);
+        }
+    }
+}
+
+__global__ void k_adam_tail(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                            float* __restrict__ v, long long start, long long n, float b1, float b2,
+                            float eps, float step_size, float inv_sqrt_bc2, SegTable st) {
+    for (long long i = start + (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        float pp = p[i], mm = m[i], vv = v[i];
+        adam1(pp, g[i], mm, vv, b1, b2, eps, step_size, inv_sqrt_bc2);
+        p[i] = pp;
+        m[i] = mm;
+        v[i] = vv;
+        if (st.n) store_lowp(st, i, pp);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_adam(float* p, const float* g, float* m, float* v, long long n,
+                        float b1, float b2, float eps, float step_size, float inv_sqrt_bc2,
+                        const gs_lowp_segment* segs, int n_segs, cudaStream_t s, Prof& pf) {
+    SegTable st{};
+    st.n = n_segs;
+    for (int k = 0; k < n_segs && k < 8; ++k) {
+        st.begin[k] = segs[k].begin;
+        st.end[k] = segs[k].end;
+        st.dst[k] = segs[k].dst;
+        st.dtype[k] = segs[k].dtype;
+    }
+    const bool aligned = ((reinterpret_cast<uintptr_t>(p) | reinterpret_cast<uintptr_t>(g) |
+                           reinterpret_cast<uintptr_t>(m) | reinterpret_cast<uintptr_t>(v)) & 15) == 0;
+    long long n4 = aligned ? n / 4 : 0;
+    const int pi = pf.begin(GS_KF_ADAM, s, (n4 > 0) + (4 * n4 < n));
+    if (n4 > 0) {
+        int dev = 0, sms = 148;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        long long blocks = (n4 + 255) / 256;
+        const long long cap = (long long)sms * 8;
+        if (blocks > cap) blocks = cap;
+        k_adam4<<<(unsigned)blocks, 256, 0, s>>>(reinterpret_cast<float4*>(p), reinterpret_cast<const float4*>(g),
+                                                 reinterpret_cast<float4*>(m), reinterpret_cast<float4*>(v), n4, b1,
+                                                 b2, eps, step_size, inv_sqrt_bc2, st);
+    }
+    if (4 * n4 < n) {
+        const long long rest = n - 4 * n4;
+        const long long blocks = rest < 256 * 1184 ? (rest + 255) / 256 : 1184;
+        k_adam_tail<<<(unsigned)blocks, 256, 0, s>>>(p, g, m, v, 4 * n4, n, b1, b2, eps, step_size,
+                                                     inv_sqrt_bc2, st);
+    }
+    pf.end(pi, s);
+    return cudaGetLastError();
+}
+
+}  // namespace gsb

@@ -1,0 +1,632 @@
+// C ABI of libgs_b300: argument validation, workspace layout, view tables and
+// kernel orchestration.  Every entry point validates on the host, launches on
+// the caller's stream and returns a gs_status; nothing here synchronises or
+// allocates except context creation/destruction and gs_sync_status (and
+// gs_bin when the caller asks for the pair count).
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+
+#include "gs_internal.cuh"
+
+struct gs_ctx {
+    int device;
+    gs_config cfg;
+    int sm_count;
+    gsb::Prof prof;
+    unsigned int* d_status;           // [0] latched status (negated gs_status), [2..3] pair count
+    unsigned long long* d_pairs;      // points into d_status
+    char err[512];
+};
+
+namespace gsb {
+
+int Prof::begin(int fam, cudaStream_t s, int n) {
+    launches += n;
+    if (!(mask & (1u << fam))) return -1;
+    if (pool_used + 2 > pool_size) {
+        const int grow = pool_size ? pool_size : 256;
+        cudaEvent_t* np = static_cast<cudaEvent_t*>(realloc(pool, sizeof(cudaEvent_t) * (pool_size + grow)));
+        if (!np) return -1;
+        pool = np;
+        for (int k = 0; k < grow; ++k)
+            if (cudaEventCreate(&pool[pool_size + k]) != cudaSuccess) {
+                cudaGetLastError();
+                return -1;
+            }
+        pool_size += grow;
+    }
+    if (n_recs == cap_recs) {
+        const int nc = cap_recs ? 2 * cap_recs : 128;
+        Rec* nr = static_cast<Rec*>(realloc(recs, sizeof(Rec) * nc));
+        if (!nr) return -1;
+        recs = nr;
+        cap_recs = nc;
+    }
+    Rec& r = recs[n_recs];
+    r.fam = fam;
+    r.a = pool[pool_used++];
+    r.b = pool[pool_used++];
+    cudaEventRecord(r.a, s);
+    return n_recs++;
+}
+
+void Prof::end(int idx, cudaStream_t s) {
+    if (idx >= 0) cudaEventRecord(recs[idx].b, s);
+}
+
+void Prof::release() {
+    for (int k = 0; k < pool_size; ++k) cudaEventDestroy(pool[k]);
+    free(pool);
+    free(recs);
+    pool = nullptr;
+    recs = nullptr;
+    pool_size = pool_used = n_recs = cap_recs = 0;
+}
+
+}  // namespace gsb
+
+namespace {
+
+using namespace gsb;
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+int fail(gs_ctx* ctx, int code, const char* fmt, ...) {
+    if (ctx) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(ctx->err, sizeof(ctx->err), fmt, ap);
+        va_end(ap);
+    }
+    return code;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) { ok = false; prev = -1; return; }
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+int tile_key_bits(int total_tiles) {
+    int b = 1;
+    while ((1ll << b) < (long long)total_tiles) ++b;
+    return b;
+}
+
+int sorted_buffer(int total_tiles) {
+    const int bits = tile_key_bits(total_tiles);
+    const int passes = (bits + 7) / 8;
+    return passes % 2;
+}
+
+struct Layout {
+    gs_ws_layout pub;
+    size_t scan_part, dkeys1, dvals1, pkeys1, pvals1, hist, partials;
+    int radix_grid, scan_blocks;
+    long long max_g_end;
+};
+
+int l1_blocks_x(long long max_px) { return (int)((3 * max_px + 1023) / 1024); }
+
+// Validates the views (host) and computes the workspace layout.
+int make_layout(gs_ctx* ctx, const gs_config& cfg, const gs_view* views, int n_views,
+                int64_t max_pairs, Layout& L) {
+    if (!views) return fail(ctx, GS_ERR_INVALID_ARG, "views is NULL");
+    if (n_views < 1 || n_views > GS_MAX_VIEWS)
+        return fail(ctx, GS_ERR_INVALID_ARG, "n_views=%d outside [1, %d]", n_views, GS_MAX_VIEWS);
+    if (max_pairs < 0 || max_pairs > 0x7FFFFFFFll)
+        return fail(ctx, GS_ERR_INVALID_ARG, "max_pairs=%lld outside [0, 2^31)", (long long)max_pairs);
+    const int ts = cfg.tile_size;
+    long long M = 0, P = 0, T = 0, max_px = 0, max_g_end = 0;
+    for (int v = 0; v < n_views; ++v) {
+        const gs_view& V = views[v];
+        if (V.width <= 0 || V.height <= 0 || V.width > 32768 || V.height > 32768)
+            return fail(ctx, GS_ERR_INVALID_ARG, "view %d: size %dx%d outside [1, 32768]", v, V.width, V.height);
+        if (V.g_begin < 0 || V.g_end <= V.g_begin)
+            return fail(ctx, GS_ERR_INVALID_ARG, "view %d: empty or negative Gaussian range [%lld, %lld)", v,
+                        (long long)V.g_begin, (long long)V.g_end);
+        for (int k = 0; k < 9; ++k)
+            if (!isfinite(V.R_cw[k])) return fail(ctx, GS_ERR_NONFINITE, "view %d: R_cw not finite", v);
+        for (int k = 0; k < 3; ++k)
+            if (!isfinite(V.t_cw[k])) return fail(ctx, GS_ERR_NONFINITE, "view %d: t_cw not finite", v);
+        if (!isfinite(V.fx) || !isfinite(V.fy) || !isfinite(V.cx) || !isfinite(V.cy))
+            return fail(ctx, GS_ERR_NONFINITE, "view %d: intrinsics not finite", v);
+        if (!(V.fx > 0.f) || !(V.fy > 0.f))
+            return fail(ctx, GS_ERR_INVALID_ARG, "view %d: focal lengths must be positive", v);
+        M += V.g_end - V.g_begin;
+        const long long tx = (V.width + ts - 1) / ts, ty = (V.height + ts - 1) / ts;
+        T += tx * ty;
+        P += (long long)V.width * V.height;
+        if ((long long)V.width * V.height > max_px) max_px = (long long)V.width * V.height;
+        if (V.g_end > max_g_end) max_g_end = V.g_end;
+    }
+    if (M >= 0xFFFFFFFFll) return fail(ctx, GS_ERR_INVALID_ARG, "too many (view, Gaussian) records: %lld", M);
+    if (T >= 0x7FFFFFFFll) return fail(ctx, GS_ERR_INVALID_ARG, "too many tiles: %lld", T);
+
+    const long long cap = max_pairs;
+    long long big = M > cap ? M : cap;
+    long long G = (big + 2047) / 2048;
+    if (G < 1) G = 1;
+    if (G > 592) G = 592;
+    L.radix_grid = (int)G;
+    L.scan_blocks = (int)((M + 4095) / 4096);
+    L.max_g_end = max_g_end;
+    const long long pose_blocks = (max_g_end + 255) / 256;
+    long long partials = (long long)n_views * pose_blocks * 6;
+    const long long l1 = (long long)n_views * l1_blocks_x(max_px);
+    if (l1 > partials) partials = l1;
+
+    size_t off = 0;
+    auto take = [&](size_t bytes) { const size_t o = off; off = align_up(off + bytes); return o; };
+    gs_ws_layout& W = L.pub;
+    memset(&W, 0, sizeof(W));
+    W.records = take(sizeof(float) * kRecFloats * (size_t)M);
+    W.rects = take(sizeof(int4) * (size_t)M);
+    W.tiles_touched = take(sizeof(uint32_t) * (size_t)M);
+    W.depth_keys = take(sizeof(uint32_t) * (size_t)M);
+    L.dkeys1 = take(sizeof(uint32_t) * (size_t)M);
+    W.depth_vals = take(sizeof(uint32_t) * (size_t)M);
+    L.dvals1 = take(sizeof(uint32_t) * (size_t)M);
+    W.pair_offsets = take(sizeof(unsigned long long) * (size_t)M);
+    L.scan_part = take(sizeof(unsigned long long) * (size_t)(L.scan_blocks + 1));
+    W.pair_keys = take(sizeof(uint32_t) * (size_t)cap);
+    L.pkeys1 = take(sizeof(uint32_t) * (size_t)cap);
+    W.pair_vals = take(sizeof(uint32_t) * (size_t)cap);
+    L.pvals1 = take(sizeof(uint32_t) * (size_t)cap);
+    L.hist = take(sizeof(uint32_t) * 256 * (size_t)G);
+    W.tile_ranges = take(sizeof(uint2) * (size_t)T);
+    W.grad2d = take(sizeof(float) * kGrad2D * (size_t)M);
+    W.counters = take(sizeof(unsigned long long) * 8);
+    L.partials = take(sizeof(float) * (size_t)partials);
+    W.total = off;
+    W.sorted_vals = sorted_buffer((int)T) ? L.pvals1 : W.pair_vals;
+    W.n_records = M;
+    W.n_tiles = (int32_t)T;
+    W.n_pixels = P;
+    return GS_OK;
+}
+
+int check_ws(gs_ctx* ctx, const gs_view* views, int n_views, const gs_workspace* ws, Layout& L) {
+    if (!ws || !ws->ptr) return fail(ctx, GS_ERR_INVALID_ARG, "workspace is NULL");
+    if (reinterpret_cast<uintptr_t>(ws->ptr) % kAlign)
+        return fail(ctx, GS_ERR_INVALID_ARG, "workspace base is not 256-byte aligned");
+    int rc = make_layout(ctx, ctx->cfg, views, n_views, ws->max_pairs, L);
+    if (rc) return rc;
+    if (ws->bytes < L.pub.total)
+        return fail(ctx, GS_ERR_INVALID_ARG, "workspace has %zu bytes, needs %zu", ws->bytes, L.pub.total);
+    return GS_OK;
+}
+
+WsPtrs ws_ptrs(const gs_workspace* ws, const Layout& L, int total_tiles) {
+    char* b = static_cast<char*>(ws->ptr);
+    WsPtrs p{};
+    p.rec = reinterpret_cast<float4*>(b + L.pub.records);
+    p.rect = reinterpret_cast<int4*>(b + L.pub.rects);
+    p.tiles_touched = reinterpret_cast<uint32_t*>(b + L.pub.tiles_touched);
+    p.dkeys[0] = reinterpret_cast<uint32_t*>(b + L.pub.depth_keys);
+    p.dkeys[1] = reinterpret_cast<uint32_t*>(b + L.dkeys1);
+    p.dvals[0] = reinterpret_cast<uint32_t*>(b + L.pub.depth_vals);
+    p.dvals[1] = reinterpret_cast<uint32_t*>(b + L.dvals1);
+    p.offsets = reinterpret_cast<unsigned long long*>(b + L.pub.pair_offsets);
+    p.scan_part = reinterpret_cast<unsigned long long*>(b + L.scan_part);
+    p.pkeys[0] = reinterpret_cast<uint32_t*>(b + L.pub.pair_keys);
+    p.pkeys[1] = reinterpret_cast<uint32_t*>(b + L.pkeys1);
+    p.pvals[0] = reinterpret_cast<uint32_t*>(b + L.pub.pair_vals);
+    p.pvals[1] = reinterpret_cast<uint32_t*>(b + L.pvals1);
+    p.hist = reinterpret_cast<uint32_t*>(b + L.hist);
+    p.ranges = reinterpret_cast<uint2*>(b + L.pub.tile_ranges);
+    p.grad2d = reinterpret_cast<float*>(b + L.pub.grad2d);
+    p.counters = reinterpret_cast<unsigned long long*>(b + L.pub.counters);
+    p.partials = reinterpret_cast<float*>(b + L.partials);
+    p.cap = ws->max_pairs;
+    p.radix_grid = L.radix_grid;
+    p.scan_blocks = L.scan_blocks;
+    p.sorted_buf = sorted_buffer(total_tiles);
+    return p;
+}
+
+void make_batch(const gs_config& cfg, const gs_view* views, int n_views, BatchParam& bp) {
+    memset(&bp, 0, sizeof(bp));
+    bp.n_views = n_views;
+    bp.tile_size = cfg.tile_size;
+    long long rec = 0, pix = 0;
+    int tiles = 0, maxc = 0;
+    for (int v = 0; v < n_views; ++v) {
+        const gs_view& S = views[v];
+        ViewParam& V = bp.v[v];
+        memcpy(V.R, S.R_cw, sizeof(V.R));
+        memcpy(V.t, S.t_cw, sizeof(V.t));
+        V.fx = S.fx; V.fy = S.fy; V.cx = S.cx; V.cy = S.cy;
+        for (int k = 0; k < 3; ++k) {  // camera centre -R^T t
+            const double c = -((double)S.R_cw[k] * S.t_cw[0] + (double)S.R_cw[3 + k] * S.t_cw[1] +
+                               (double)S.R_cw[6 + k] * S.t_cw[2]);
+            V.campos[k] = (float)c;
+        }
+        V.W = S.width; V.H = S.height;
+        V.tiles_x = (S.width + cfg.tile_size - 1) / cfg.tile_size;
+        V.tiles_y = (S.height + cfg.tile_size - 1) / cfg.tile_size;
+        V.tile_off = tiles;
+        V.g_begin = S.g_begin; V.g_end = S.g_end;
+        V.rec_off = rec;
+        V.pix_off = pix;
+        tiles += V.tiles_x * V.tiles_y;
+        rec += S.g_end - S.g_begin;
+        pix += (long long)S.width * S.height;
+        if (S.g_end - S.g_begin > maxc) maxc = (int)(S.g_end - S.g_begin);
+    }
+    bp.total_tiles = tiles;
+    bp.total_recs = rec;
+    bp.total_px = pix;
+    bp.max_count = maxc;
+}
+
+RenderConst make_rc(const gs_config& c) {
+    RenderConst r;
+    r.alpha_min = c.alpha_min;
+    r.alpha_max = c.alpha_max;
+    r.T_min = c.T_min;
+    r.blur = c.blur;
+    r.z_near = c.z_near;
+    r.log2_alpha_min = c.alpha_min > 0.f ? log2f(c.alpha_min) : -INFINITY;
+    for (int k = 0; k < 3; ++k) r.bg[k] = c.bg[k];
+    return r;
+}
+
+int check_gaussians(gs_ctx* ctx, const gs_gaussians* g, const gs_view* views, int n_views, GaussPtrs& out) {
+    if (!g) return fail(ctx, GS_ERR_INVALID_ARG, "gaussians is NULL");
+    if (!g->means || !g->log_scales || !g->quats || !g->opacity || !g->sh)
+        return fail(ctx, GS_ERR_INVALID_ARG, "a Gaussian attribute pointer is NULL");
+    if (g->n <= 0) return fail(ctx, GS_ERR_INVALID_ARG, "n=%lld must be positive", (long long)g->n);
+    if (g->sh_degree < 0 || g->sh_degree > 1)
+        return fail(ctx, GS_ERR_INVALID_ARG, "sh_degree=%d not in {0, 1}", g->sh_degree);
+    const int dts[4] = {g->scale_dtype, g->rot_dtype, g->opacity_dtype, g->sh_dtype};
+    for (int k = 0; k < 4; ++k)
+        if (dts[k] < GS_F32 || dts[k] > GS_BF16) return fail(ctx, GS_ERR_INVALID_ARG, "bad dtype %d", dts[k]);
+    for (int v = 0; v < n_views; ++v)
+        if (views[v].g_end > g->n)
+            return fail(ctx, GS_ERR_INVALID_ARG, "view %d: g_end=%lld exceeds n=%lld", v,
+                        (long long)views[v].g_end, (long long)g->n);
+    out.means = g->means;
+    out.log_scales = g->log_scales;
+    out.quats = g->quats;
+    out.opacity = g->opacity;
+    out.sh = g->sh;
+    out.scale_dtype = g->scale_dtype;
+    out.rot_dtype = g->rot_dtype;
+    out.opacity_dtype = g->opacity_dtype;
+    out.sh_dtype = g->sh_dtype;
+    out.sh_degree = g->sh_degree;
+    out.n = g->n;
+    return GS_OK;
+}
+
+int cuda_fail(gs_ctx* ctx, cudaError_t e, const char* where) {
+    return fail(ctx, GS_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+int check_config(const gs_config& c, char* msg, size_t n) {
+    if (c.tile_size != 8 && c.tile_size != 16 && c.tile_size != 32) {
+        snprintf(msg, n, "tile_size=%d not in {8, 16, 32}", c.tile_size);
+        return GS_ERR_INVALID_ARG;
+    }
+    if (!(c.alpha_min >= 0.f) || !(c.alpha_max > c.alpha_min) || !(c.alpha_max <= 1.f) || !(c.T_min >= 0.f) ||
+        !(c.T_min < 1.f) || !(c.blur >= 0.f) || !(c.z_near > 0.f)) {
+        snprintf(msg, n, "config constants out of range");
+        return GS_ERR_INVALID_ARG;
+    }
+    for (int k = 0; k < 3; ++k)
+        if (!isfinite(c.bg[k])) {
+            snprintf(msg, n, "background not finite");
+            return GS_ERR_INVALID_ARG;
+        }
+    return GS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void gs_config_default(gs_config* cfg) {
+    if (!cfg) return;
+    cfg->tile_size = 16;
+    cfg->alpha_min = 1.0f / 255.0f;
+    cfg->alpha_max = 0.99f;
+    cfg->T_min = 1e-4f;
+    cfg->blur = 0.3f;
+    cfg->z_near = 0.2f;
+    cfg->bg[0] = cfg->bg[1] = cfg->bg[2] = 0.f;
+}
+
+const char* gs_version(void) { return "gs_b300 0.1 (sm_103a)"; }
+
+int gs_context_create(gs_ctx** out, int device, const gs_config* cfg) {
+    if (!out) return GS_ERR_INVALID_ARG;
+    *out = nullptr;
+    gs_config c;
+    gs_config_default(&c);
+    if (cfg) c = *cfg;
+    char msg[256];
+    if (check_config(c, msg, sizeof(msg)) != GS_OK) return GS_ERR_INVALID_ARG;
+    gs_ctx* ctx = new (std::nothrow) gs_ctx();
+    if (!ctx) return GS_ERR_OOM;
+    ctx->device = device;
+    ctx->cfg = c;
+    ctx->err[0] = 0;
+    DeviceGuard dg(device);
+    if (!dg.ok) { delete ctx; return GS_ERR_CUDA; }
+    if (cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+        delete ctx;
+        return GS_ERR_CUDA;
+    }
+    if (cudaMalloc(&ctx->d_status, 64) != cudaSuccess) {
+        cudaGetLastError();
+        delete ctx;
+        return GS_ERR_OOM;
+    }
+    ctx->d_pairs = reinterpret_cast<unsigned long long*>(ctx->d_status + 2);
+    if (cudaMemset(ctx->d_status, 0, 64) != cudaSuccess) {
+        cudaFree(ctx->d_status);
+        delete ctx;
+        return GS_ERR_CUDA;
+    }
+    *out = ctx;
+    return GS_OK;
+}
+
+int gs_context_destroy(gs_ctx* ctx) {
+    if (!ctx) return GS_OK;
+    {
+        DeviceGuard dg(ctx->device);
+        if (ctx->d_status) cudaFree(ctx->d_status);
+        ctx->prof.release();
+    }
+    delete ctx;
+    return GS_OK;
+}
+
+const char* gs_last_error(const gs_ctx* ctx) { return ctx ? ctx->err : "context is NULL"; }
+
+int gs_get_config(const gs_ctx* ctx, gs_config* cfg) {
+    if (!ctx || !cfg) return GS_ERR_INVALID_ARG;
+    *cfg = ctx->cfg;
+    return GS_OK;
+}
+
+int gs_workspace_query(const gs_ctx* ctx, const gs_view* views, int n_views, int64_t max_pairs,
+                       size_t* bytes) {
+    if (!ctx || !bytes) return GS_ERR_INVALID_ARG;
+    Layout L;
+    const int rc = make_layout(const_cast<gs_ctx*>(ctx), ctx->cfg, views, n_views, max_pairs, L);
+    if (rc) return rc;
+    *bytes = L.pub.total;
+    return GS_OK;
+}
+
+int gs_workspace_layout(const gs_ctx* ctx, const gs_view* views, int n_views, int64_t max_pairs,
+                        gs_ws_layout* out) {
+    if (!ctx || !out) return GS_ERR_INVALID_ARG;
+    Layout L;
+    const int rc = make_layout(const_cast<gs_ctx*>(ctx), ctx->cfg, views, n_views, max_pairs, L);
+    if (rc) return rc;
+    *out = L.pub;
+    return GS_OK;
+}
+
+int gs_project(gs_ctx* ctx, const gs_gaussians* g, const gs_view* views, int n_views,
+               const gs_workspace* ws, gs_stream stream) {
+    if (!ctx) return GS_ERR_INVALID_ARG;
+    Layout L;
+    int rc = check_ws(ctx, views, n_views, ws, L);
+    if (rc) return rc;
+    GaussPtrs gp;
+    if ((rc = check_gaussians(ctx, g, views, n_views, gp))) return rc;
+    DeviceGuard dg(ctx->device);
+    BatchParam bp;
+    make_batch(ctx->cfg, views, n_views, bp);
+    const WsPtrs wp = ws_ptrs(ws, L, bp.total_tiles);
+    cudaError_t e = launch_project(bp, gp, make_rc(ctx->cfg), wp, reinterpret_cast<cudaStream_t>(stream), ctx->prof);
+    return e == cudaSuccess ? GS_OK : cuda_fail(ctx, e, "gs_project");
+}
+
+int gs_bin(gs_ctx* ctx, const gs_view* views, int n_views, const gs_workspace* ws,
+           uint64_t* pairs_needed, gs_stream stream) {
+    if (!ctx) return GS_ERR_INVALID_ARG;
+    Layout L;
+    int rc = check_ws(ctx, views, n_views, ws, L);
+    if (rc) return rc;
+    DeviceGuard dg(ctx->device);
+    BatchParam bp;
+    make_batch(ctx->cfg, views, n_views, bp);
+    WsPtrs wp = ws_ptrs(ws, L, bp.total_tiles);
+    const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = launch_bin(bp, wp, ctx->d_status, ctx->d_pairs, s, ctx->prof);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "gs_bin");
+    if (wp.sorted_buf != sorted_buffer(bp.total_tiles))
+        return fail(ctx, GS_ERR_CUDA, "gs_bin: sorted buffer parity mismatch");
+    if (pairs_needed) {
+        unsigned long long n = 0;
+        if ((e = cudaMemcpyAsync(&n, wp.counters, sizeof(n), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(s)) != cudaSuccess)
+            return cuda_fail(ctx, e, "gs_bin (pair count)");
+        *pairs_needed = n;
+        if ((long long)n > ws->max_pairs)
+            return fail(ctx, GS_ERR_CAPACITY, "gs_bin: %llu pairs exceed the capacity %lld", n,
+                        (long long)ws->max_pairs);
+    }
+    return GS_OK;
+}
+
+int gs_render_fwd(gs_ctx* ctx, const gs_view* views, int n_views, const gs_workspace* ws, float* rgb,
+                  float* T_final, uint32_t* n_contrib, gs_stream stream) {
+    if (!ctx) return GS_ERR_INVALID_ARG;
+    if (!rgb || !T_final || !n_contrib) return fail(ctx, GS_ERR_INVALID_ARG, "an output pointer is NULL");
+    Layout L;
+    int rc = check_ws(ctx, views, n_views, ws, L);
+    if (rc) return rc;
+    DeviceGuard dg(ctx->device);
+    BatchParam bp;
+    make_batch(ctx->cfg, views, n_views, bp);
+    const WsPtrs wp = ws_ptrs(ws, L, bp.total_tiles);
+    cudaError_t e = launch_render_fwd(bp, make_rc(ctx->cfg), wp, rgb, T_final, n_contrib,
+                                      reinterpret_cast<cudaStream_t>(stream), ctx->prof);
+    return e == cudaSuccess ? GS_OK : cuda_fail(ctx, e, "gs_render_fwd");
+}
+
+int gs_l1_loss(gs_ctx* ctx, const gs_view* views, int n_views, const gs_workspace* ws, const float* rgb,
+               const float* target, float* dL_drgb, float* loss_dev, gs_stream stream) {
+    if (!ctx) return GS_ERR_INVALID_ARG;
+    if (!rgb || !target || !dL_drgb) return fail(ctx, GS_ERR_INVALID_ARG, "an image pointer is NULL");
+    Layout L;
+    int rc = check_ws(ctx, views, n_views, ws, L);
+    if (rc) return rc;
+    DeviceGuard dg(ctx->device);
+    BatchParam bp;
+    make_batch(ctx->cfg, views, n_views, bp);
+    const WsPtrs wp = ws_ptrs(ws, L, bp.total_tiles);
+    cudaError_t e = launch_l1(bp, wp, rgb, target, dL_drgb, loss_dev, reinterpret_cast<cudaStream_t>(stream), ctx->prof);
+    return e == cudaSuccess ? GS_OK : cuda_fail(ctx, e, "gs_l1_loss");
+}
+
+int gs_render_bwd(gs_ctx* ctx, const gs_gaussians* g, const gs_view* views, int n_views, const gs_workspace* ws,
+                  const float* T_final, const uint32_t* n_contrib, const float* dL_drgb, const gs_grads* grads,
+                  float* dL_dpose_dev, gs_stream stream) {
+    if (!ctx) return GS_ERR_INVALID_ARG;
+    if (!T_final || !n_contrib || !dL_drgb) return fail(ctx, GS_ERR_INVALID_ARG, "an image pointer is NULL");
+    if (!grads && !dL_dpose_dev) return fail(ctx, GS_ERR_INVALID_ARG, "grads and dL_dpose are both NULL");
+    if (grads && (!grads->means || !grads->log_scales || !grads->quats || !grads->opacity || !grads->sh))
+        return fail(ctx, GS_ERR_INVALID_ARG, "a gradient pointer is NULL");
+    Layout L;
+    int rc = check_ws(ctx, views, n_views, ws, L);
+    if (rc) return rc;
+    GaussPtrs gp;
+    if ((rc = check_gaussians(ctx, g, views, n_views, gp))) return rc;
+    DeviceGuard dg(ctx->device);
+    BatchParam bp;
+    make_batch(ctx->cfg, views, n_views, bp);
+    const WsPtrs wp = ws_ptrs(ws, L, bp.total_tiles);
+    const RenderConst rcst = make_rc(ctx->cfg);
+    const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = launch_render_bwd(bp, rcst, wp, T_final, n_contrib, dL_drgb, s, ctx->prof);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "gs_render_bwd (raster)");
+    GradPtrs gr;
+    if (grads) {
+        gr.means = grads->means;
+        gr.log_scales = grads->log_scales;
+        gr.quats = grads->quats;
+        gr.opacity = grads->opacity;
+        gr.sh = grads->sh;
+    }
+    e = launch_project_bwd(bp, gp, rcst, wp, grads ? &gr : nullptr, dL_dpose_dev, s, ctx->prof);
+    return e == cudaSuccess ? GS_OK : cuda_fail(ctx, e, "gs_render_bwd (projection)");
+}
+
+int gs_pose_grad(gs_ctx* ctx, const gs_gaussians* g, const gs_view* views, int n_views, const gs_workspace* ws,
+                 const float* T_final, const uint32_t* n_contrib, const float* dL_drgb, float* dL_dpose_dev,
+                 gs_stream stream) {
+    if (!ctx) return GS_ERR_INVALID_ARG;
+    if (!dL_dpose_dev) return fail(ctx, GS_ERR_INVALID_ARG, "dL_dpose is NULL");
+    return gs_render_bwd(ctx, g, views, n_views, ws, T_final, n_contrib, dL_drgb, nullptr, dL_dpose_dev, stream);
+}
+
+int gs_adam_step(gs_ctx* ctx, float* param, const float* grad, float* m, float* v, int64_t n, float lr, float b1,
+                 float b2, float eps, int64_t step, const gs_lowp_segment* segs, int n_segs, gs_stream stream) {
+    if (!ctx) return GS_ERR_INVALID_ARG;
+    if (!param || !grad || !m || !v) return fail(ctx, GS_ERR_INVALID_ARG, "an Adam buffer is NULL");
+    if (n < 0) return fail(ctx, GS_ERR_INVALID_ARG, "n=%lld is negative", (long long)n);
+    if (step < 1) return fail(ctx, GS_ERR_INVALID_ARG, "step=%lld must be >= 1", (long long)step);
+    if (!(lr >= 0.f) || !(b1 >= 0.f && b1 < 1.f) || !(b2 >= 0.f && b2 < 1.f) || !(eps > 0.f))
+        return fail(ctx, GS_ERR_INVALID_ARG, "Adam hyper-parameters out of range");
+    if (n_segs < 0 || n_segs > 8 || (n_segs > 0 && !segs))
+        return fail(ctx, GS_ERR_INVALID_ARG, "n_segs=%d outside [0, 8]", n_segs);
+    for (int k = 0; k < n_segs; ++k) {
+        if (!segs[k].dst || segs[k].begin < 0 || segs[k].end > n || segs[k].end < segs[k].begin ||
+            (segs[k].dtype != GS_F16 && segs[k].dtype != GS_BF16))
+            return fail(ctx, GS_ERR_INVALID_ARG, "low-precision segment %d is invalid", k);
+    }
+    if (n == 0) return GS_OK;
+    DeviceGuard dg(ctx->device);
+    const double bc1 = 1.0 - pow((double)b1, (double)step);
+    const double bc2 = 1.0 - pow((double)b2, (double)step);
+    const float step_size = (float)(lr / bc1);
+    const float inv_sqrt_bc2 = (float)(1.0 / sqrt(bc2));
+    cudaError_t e = launch_adam(param, grad, m, v, n, b1, b2, eps, step_size, inv_sqrt_bc2, segs, n_segs,
+                                reinterpret_cast<cudaStream_t>(stream), ctx->prof);
+    return e == cudaSuccess ? GS_OK : cuda_fail(ctx, e, "gs_adam_step");
+}
+
+int gs_sync_status(gs_ctx* ctx, gs_stream stream, uint64_t* pairs_needed) {
+    if (!ctx) return GS_ERR_INVALID_ARG;
+    DeviceGuard dg(ctx->device);
+    const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    unsigned int host[16];
+    cudaError_t e = cudaMemcpyAsync(host, ctx->d_status, 64, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "gs_sync_status");
+    unsigned long long pairs;
+    memcpy(&pairs, host + 2, sizeof(pairs));
+    if (pairs_needed) *pairs_needed = pairs;
+    const unsigned int code = host[0];
+    if (code) {
+        e = cudaMemsetAsync(ctx->d_status, 0, sizeof(unsigned int), s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "gs_sync_status (clear)");
+        return fail(ctx, -(int)code, "device status %d (pairs needed %llu)", -(int)code, pairs);
+    }
+    return GS_OK;
+}
+
+int gs_profile_enable(gs_ctx* ctx, uint32_t family_mask) {
+    if (!ctx) return GS_ERR_INVALID_ARG;
+    if (family_mask >> GS_KF_COUNT) return fail(ctx, GS_ERR_INVALID_ARG, "family mask 0x%x has unknown bits", family_mask);
+    ctx->prof.mask = family_mask;
+    return GS_OK;
+}
+
+int gs_profile_collect(gs_ctx* ctx, gs_stream stream, gs_profile_entry* out, int max_entries, int* n_out) {
+    if (!ctx || (max_entries > 0 && !out) || max_entries < 0) return GS_ERR_INVALID_ARG;
+    DeviceGuard dg(ctx->device);
+    Prof& pf = ctx->prof;
+    cudaError_t e = cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "gs_profile_collect");
+    double ms[GS_KF_COUNT] = {0};
+    int cnt[GS_KF_COUNT] = {0};
+    for (int k = 0; k < pf.n_recs; ++k) {
+        float t = 0.f;
+        if ((e = cudaEventSynchronize(pf.recs[k].b)) != cudaSuccess ||
+            (e = cudaEventElapsedTime(&t, pf.recs[k].a, pf.recs[k].b)) != cudaSuccess)
+            return cuda_fail(ctx, e, "gs_profile_collect (event)");
+        ms[pf.recs[k].fam] += t;
+        cnt[pf.recs[k].fam] += 1;
+    }
+    pf.n_recs = 0;
+    pf.pool_used = 0;
+    int n = 0;
+    for (int f = 0; f < GS_KF_COUNT; ++f) {
+        if (!cnt[f]) continue;
+        if (n < max_entries) {
+            out[n].family = f;
+            out[n].launches = cnt[f];
+            out[n].total_ms = ms[f];
+        }
+        ++n;
+    }
+    if (n_out) *n_out = n < max_entries ? n : max_entries;
+    return GS_OK;
+}
+
+int64_t gs_launch_count(const gs_ctx* ctx) { return ctx ? (int64_t)ctx->prof.launches : -1; }
+
+}  // extern "C"

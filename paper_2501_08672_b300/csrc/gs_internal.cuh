@@ -1,0 +1,157 @@
+// Internal declarations shared by the CUDA translation units of libgs_b300.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/gs.h"
+
+namespace gsb {
+
+constexpr int kMaxViews = GS_MAX_VIEWS;
+constexpr int kRecFloats = 12;   // projected record: 3 x float4
+constexpr int kGrad2D = 9;       // per-record 2D gradient
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kLn2 = 0.6931471805599453f;
+
+// Per-view data passed by value to kernels (kernel parameter space).
+struct ViewParam {
+    float R[9];
+    float t[3];
+    float fx, fy, cx, cy;
+    float campos[3];
+    int W, H;
+    int tiles_x, tiles_y;
+    int tile_off;        // first global tile id of the view
+    int pad_;
+    long long g_begin, g_end;
+    long long rec_off;   // first record of the view
+    long long pix_off;   // first pixel of the view
+};
+
+struct BatchParam {
+    int n_views;
+    int total_tiles;
+    long long total_recs;
+    long long total_px;
+    int max_count;       // largest g_end - g_begin over views
+    int tile_size;
+    ViewParam v[kMaxViews];
+};
+
+struct RenderConst {
+    float alpha_min, alpha_max, T_min, blur, z_near;
+    float log2_alpha_min;   // -inf when alpha_min == 0
+    float bg[3];
+};
+
+struct GaussPtrs {
+    const float* means;
+    const void* log_scales;
+    const void* quats;
+    const void* opacity;
+    const void* sh;
+    int scale_dtype, rot_dtype, opacity_dtype, sh_dtype;
+    int sh_degree;
+    long long n;
+};
+
+struct GradPtrs {
+    float* means;
+    float* log_scales;
+    float* quats;
+    float* opacity;
+    float* sh;
+};
+
+// Device-side pointers into the caller's workspace.
+struct WsPtrs {
+    float4* rec;             // [M][3]
+    int4* rect;              // [M]
+    uint32_t* tiles_touched; // [M]
+    uint32_t* dkeys[2];      // [M]
+    uint32_t* dvals[2];      // [M]
+    unsigned long long* offsets; // [M]
+    unsigned long long* scan_part; // [scan blocks]
+    uint32_t* pkeys[2];      // [cap]
+    uint32_t* pvals[2];      // [cap]
+    uint32_t* hist;          // [256 * radix grid]
+    uint2* ranges;           // [T]
+    float* grad2d;           // [M][9]
+    unsigned long long* counters; // [8]
+    float* partials;         // reduction scratch
+    long long cap;
+    int radix_grid;
+    int scan_blocks;
+    int sorted_buf;          // which pvals buffer holds the sorted pairs
+};
+
+// ---- small device helpers --------------------------------------------------
+
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float load_as_float(const void* p, int dtype, long long i) {
+    if (dtype == GS_F32) return static_cast<const float*>(p)[i];
+    if (dtype == GS_F16) return __half2float(static_cast<const __half*>(p)[i]);
+    return __bfloat162float(static_cast<const __nv_bfloat16*>(p)[i]);
+}
+
+__device__ __forceinline__ int find_view_by_tile(const BatchParam& bp, int tile) {
+    int lo = 0, hi = bp.n_views - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (bp.v[mid].tile_off <= tile) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// ---- host-side launch accounting and optional event timing ---------------
+
+struct Prof {
+    uint32_t mask = 0;
+    long long launches = 0;
+    struct Rec {
+        int fam;
+        cudaEvent_t a, b;
+    };
+    Rec* recs = nullptr;     // pending timed launches
+    int n_recs = 0, cap_recs = 0;
+    cudaEvent_t* pool = nullptr;
+    int pool_size = 0, pool_used = 0;
+
+    // Counts `n` launches of family `fam`; returns a record index when the
+    // family is timed (the start event is recorded on `s`), else -1.
+    int begin(int fam, cudaStream_t s, int n = 1);
+    void count(int n) { launches += n; }
+    void end(int idx, cudaStream_t s);
+    void release();
+};
+
+// ---- launch wrappers (host), one per kernel family ------------------------
+
+cudaError_t launch_project(const BatchParam& bp, const GaussPtrs& g, const RenderConst& rc,
+                           const WsPtrs& ws, cudaStream_t s, Prof& pf);
+cudaError_t launch_bin(const BatchParam& bp, WsPtrs& ws, unsigned int* status,
+                       unsigned long long* status_pairs, cudaStream_t s, Prof& pf);
+cudaError_t launch_render_fwd(const BatchParam& bp, const RenderConst& rc, const WsPtrs& ws,
+                              float* rgb, float* T_final, uint32_t* n_contrib, cudaStream_t s,
+                              Prof& pf);
+cudaError_t launch_render_bwd(const BatchParam& bp, const RenderConst& rc, const WsPtrs& ws,
+                              const float* T_final, const uint32_t* n_contrib,
+                              const float* dL_drgb, cudaStream_t s, Prof& pf);
+cudaError_t launch_project_bwd(const BatchParam& bp, const GaussPtrs& g, const RenderConst& rc,
+                               const WsPtrs& ws, const GradPtrs* grads, float* dL_dpose,
+                               cudaStream_t s, Prof& pf);
+cudaError_t launch_l1(const BatchParam& bp, const WsPtrs& ws, const float* rgb,
+                      const float* target, float* dL_drgb, float* loss, cudaStream_t s, Prof& pf);
+cudaError_t launch_adam(float* p, const float* g, float* m, float* v, long long n,
+                        float b1, float b2, float eps, float step_size, float inv_sqrt_bc2,
+                        const gs_lowp_segment* segs, int n_segs, cudaStream_t s, Prof& pf);
+
+}  // namespace gsb

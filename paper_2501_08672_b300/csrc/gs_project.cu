@@ -1,0 +1,436 @@
+// EWA projection of (view, Gaussian) pairs and its backward pass.
+//
+// Forward (Sec. II-B.1): Sigma3 = (R S)(R S)^T (Eq. 3dgs), q = pi(T_CW p_W)
+// (Eq. q), Sigma2 = (J W) Sigma3 (J W)^T + blur I (Eq. spat), opacity
+// sigmoid(logit), colour from real SH of degree 0/1.  One thread per
+// (view, Gaussian); grid.y is the view so all view parameters are uniform in
+// a block.  HBM-bound: ~92 B read per Gaussian per view (FP32, degree 1),
+// 48 B record + 16 B rectangle + 12 B keys written.
+//
+// Backward: one thread per Gaussian walks the views that contain it,
+// rebuilds the forward quantities, chains the per-record 2D gradients
+// (written by the compositing backward) to the parameters, and (optionally)
+// reduces the pose gradient of the left perturbation T_CW <- Exp(dphi, dt)
+// T_CW (Appendix A) per block into a partials buffer.
+#include <math.h>
+
+#include "gs_internal.cuh"
+
+namespace gsb {
+
+namespace {
+
+constexpr float kShC0 = 0.28209479177387814f;  // 1 / (2 sqrt(pi))
+constexpr float kShC1 = 0.48860251190291992f;  // sqrt(3) / (2 sqrt(pi))
+
+struct Proj {
+    float qh[4];     // unit quaternion
+    float inv_qn;    // 1 / |quat|
+    float R[9];
+    float s[3];      // exp(log-scale)
+    float M[9];      // R S
+    float S3[6];     // Sigma3: xx, xy, xz, yy, yz, zz
+    float pc[3];
+    float Tm[6];     // J W, row-major 2x3
+    float a, b, c;   // Sigma2 with blur
+    float A, B, C;   // conic
+    float sigma;
+    float dir[3];
+    float inv_len;
+    float raw[3];
+};
+
+__device__ __forceinline__ void quat_rot(const float* q, float* R) {
+    const float w = q[0], x = q[1], y = q[2], z = q[3];
+    R[0] = 1.f - 2.f * (y * y + z * z); R[1] = 2.f * (x * y - w * z);       R[2] = 2.f * (x * z + w * y);
+    R[3] = 2.f * (x * y + w * z);       R[4] = 1.f - 2.f * (x * x + z * z); R[5] = 2.f * (y * z - w * x);
+    R[6] = 2.f * (x * z - w * y);       R[7] = 2.f * (y * z + w * x);       R[8] = 1.f - 2.f * (x * x + y * y);
+}
+
+// Loads Gaussian i and computes the view-independent part (Sigma3).
+__device__ __forceinline__ void load_gaussian(const GaussPtrs& g, long long i, float* mu, Proj& P,
+                                              float& ologit) {
+    mu[0] = g.means[3 * i + 0];
+    mu[1] = g.means[3 * i + 1];
+    mu[2] = g.means[3 * i + 2];
+    float q[4];
+    for (int k = 0; k < 4; ++k) q[k] = load_as_float(g.quats, g.rot_dtype, 4 * i + k);
+    const float qn2 = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
+    P.inv_qn = 1.f / sqrtf(qn2);
+    for (int k = 0; k < 4; ++k) P.qh[k] = q[k] * P.inv_qn;
+    quat_rot(P.qh, P.R);
+    for (int k = 0; k < 3; ++k) P.s[k] = expf(load_as_float(g.log_scales, g.scale_dtype, 3 * i + k));
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) P.M[3 * a + b] = P.R[3 * a + b] * P.s[b];
+    // Sigma3 = M M^T (symmetric, 6 entries)
+    const int ia[6] = {0, 0, 0, 1, 1, 2};
+    const int ib[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+    for (int e = 0; e < 6; ++e) {
+        const float* ra = P.M + 3 * ia[e];
+        const float* rb = P.M + 3 * ib[e];
+        P.S3[e] = ra[0] * rb[0] + ra[1] * rb[1] + ra[2] * rb[2];
+    }
+    ologit = load_as_float(g.opacity, g.opacity_dtype, i);
+}
+
+__device__ __forceinline__ float s3(const float* S, int a, int b) {
+    // symmetric 3x3 accessor over (xx, xy, xz, yy, yz, zz)
+    const int lut[9] = {0, 1, 2, 1, 3, 4, 2, 4, 5};
+    return S[lut[3 * a + b]];
+}
+
+// View-dependent part.  Returns false when culled (z <= z_near or a
+// degenerate Sigma2).
+__device__ __forceinline__ bool project_view(const ViewParam& V, const RenderConst& rc,
+                                             const float* mu, Proj& P) {
+    for (int r = 0; r < 3; ++r)
+        P.pc[r] = V.R[3 * r] * mu[0] + V.R[3 * r + 1] * mu[1] + V.R[3 * r + 2] * mu[2] + V.t[r];
+    const float x = P.pc[0], y = P.pc[1], z = P.pc[2];
+    if (!(z > rc.z_near)) return false;
+    const float iz = 1.f / z;
+    const float j00 = V.fx * iz, j02 = -V.fx * x * iz * iz;
+    const float j11 = V.fy * iz, j12 = -V.fy * y * iz * iz;
+    for (int c = 0; c < 3; ++c) {
+        P.Tm[c] = j00 * V.R[c] + j02 * V.R[6 + c];
+        P.Tm[3 + c] = j11 * V.R[3 + c] + j12 * V.R[6 + c];
+    }
+    // Sigma2 = T Sigma3 T^T
+    float u0[3], u1[3];
+    for (int a = 0; a < 3; ++a) {
+        u0[a] = s3(P.S3, a, 0) * P.Tm[0] + s3(P.S3, a, 1) * P.Tm[1] + s3(P.S3, a, 2) * P.Tm[2];
+        u1[a] = s3(P.S3, a, 0) * P.Tm[3] + s3(P.S3, a, 1) * P.Tm[4] + s3(P.S3, a, 2) * P.Tm[5];
+    }
+    P.a = P.Tm[0] * u0[0] + P.Tm[1] * u0[1] + P.Tm[2] * u0[2] + rc.blur;
+    P.b = P.Tm[3] * u0[0] + P.Tm[4] * u0[1] + P.Tm[5] * u0[2];
+    P.c = P.Tm[3] * u1[0] + P.Tm[4] * u1[1] + P.Tm[5] * u1[2] + rc.blur;
+    const float det = P.a * P.c - P.b * P.b;
+    if (!(det > 0.f)) return false;
+    const float idet = 1.f / det;
+    P.A = P.c * idet;
+    P.B = -P.b * idet;
+    P.C = P.a * idet;
+    return true;
+}
+
+__device__ __forceinline__ void view_colour(const ViewParam& V, const GaussPtrs& g, long long i,
+                                            const float* mu, Proj& P, float* col) {
+    float d[3] = {mu[0] - V.campos[0], mu[1] - V.campos[1], mu[2] - V.campos[2]};
+    P.inv_len = 1.f / sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    for (int k = 0; k < 3; ++k) P.dir[k] = d[k] * P.inv_len;
+    const int K = (g.sh_degree + 1) * (g.sh_degree + 1);
+    const long long base = i * K * 3;
+    for (int ch = 0; ch < 3; ++ch) {
+        float v = kShC0 * load_as_float(g.sh, g.sh_dtype, base + ch) + 0.5f;
+        if (g.sh_degree >= 1) {
+            const float k1 = load_as_float(g.sh, g.sh_dtype, base + 3 + ch);
+            const float k2 = load_as_float(g.sh, g.sh_dtype, base + 6 + ch);
+            const float k3 = load_as_float(g.sh, g.sh_dtype, base + 9 + ch);
+            v += kShC1 * (-P.dir[1] * k1 + P.dir[2] * k2 - P.dir[0] * k3);
+        }
+        P.raw[ch] = v;
+        col[ch] = fmaxf(v, 0.f);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_project(const __grid_constant__ BatchParam bp, GaussPtrs g,
+                                                 RenderConst rc, WsPtrs ws) {
+    const ViewParam& V = bp.v[blockIdx.y];
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long cnt = V.g_end - V.g_begin;
+    if (k >= cnt) return;
+    const long long i = V.g_begin + k;
+    const long long r = V.rec_off + k;
+
+    float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0;
+    int4 rect = make_int4(0, 0, V.tile_off, V.tiles_x);
+    uint32_t touched = 0;
+    uint32_t key = 0xFFFFFFFFu;
+
+    Proj P;
+    float mu[3], ologit;
+    load_gaussian(g, i, mu, P, ologit);
+    bool ok = project_view(V, rc, mu, P);
+    float sigma = 0.f;
+    if (ok) {
+        sigma = 1.f / (1.f + expf(-ologit));
+        ok = sigma > rc.alpha_min;
+    }
+    if (ok) {
+        const float iz = 1.f / P.pc[2];
+        const float qx = V.fx * P.pc[0] * iz + V.cx;
+        const float qy = V.fy * P.pc[1] * iz + V.cy;
+        float col[3];
+        view_colour(V, g, i, mu, P, col);
+        // Pixel box containing every pixel centre where sigma G >= alpha_min:
+        // the ellipse d^T Sigma2^-1 d <= 2 ln(sigma / alpha_min) has half-widths
+        // sqrt(r2 Sigma2_xx), sqrt(r2 Sigma2_yy).  The small margin only adds
+        // pixels where alpha < alpha_min.
+        float lo_x = 0.f, hi_x = (float)(V.W - 1), lo_y = 0.f, hi_y = (float)(V.H - 1);
+        if (rc.alpha_min > 0.f) {
+            const float r2 = 2.f * logf(sigma / rc.alpha_min) * 1.001f;
+            const float ex = sqrtf(r2 * P.a), ey = sqrtf(r2 * P.c);
+            lo_x = fmaxf(ceilf(qx - ex - 0.5f), 0.f);
+            hi_x = fminf(floorf(qx + ex - 0.5f), (float)(V.W - 1));
+            lo_y = fmaxf(ceilf(qy - ey - 0.5f), 0.f);
+            hi_y = fminf(floorf(qy + ey - 0.5f), (float)(V.H - 1));
+        }
+        r0 = make_float4(qx, qy, -0.5f * kLog2e * P.A, -kLog2e * P.B);
+        r1 = make_float4(-0.5f * kLog2e * P.C, log2f(sigma), col[0], col[1]);
+        r2 = make_float4(col[2], P.pc[2], 0.f, 0.f);
+        if (lo_x <= hi_x && lo_y <= hi_y) {
+            const int ts = bp.tile_size;
+            const int tx0 = (int)lo_x / ts, tx1 = (int)hi_x / ts + 1;
+            const int ty0 = (int)lo_y / ts, ty1 = (int)hi_y / ts + 1;
+            rect.x = tx0 | (ty0 << 16);
+            rect.y = tx1 | (ty1 << 16);
+            touched = (uint32_t)((tx1 - tx0) * (ty1 - ty0));
+            key = __float_as_uint(P.pc[2]);
+        }
+    }
+    ws.rec[3 * r + 0] = r0;
+    ws.rec[3 * r + 1] = r1;
+    ws.rec[3 * r + 2] = r2;
+    ws.rect[r] = rect;
+    ws.tiles_touched[r] = touched;
+    ws.dkeys[0][r] = key;
+    ws.dvals[0][r] = (uint32_t)r;
+}
+
+// ---------------------------------------------------------------------------
+// Backward
+
+__global__ void __launch_bounds__(256) k_project_bwd(const __grid_constant__ BatchParam bp,
+                                                     GaussPtrs g, RenderConst rc, WsPtrs ws,
+                                                     GradPtrs gr, int want_params, int want_pose,
+                                                     int pose_blocks) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = i < g.n;
+    const int K = (g.sh_degree + 1) * (g.sh_degree + 1);
+
+    Proj P;
+    float mu[3] = {0.f, 0.f, 0.f}, ologit = 0.f;
+    if (live) load_gaussian(g, i, mu, P, ologit);
+
+    float gmu[3] = {0.f, 0.f, 0.f};
+    float gS3[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // dL/dSigma3 (symmetric, full-matrix gradient)
+    float gop = 0.f;
+    float gsh[16 * 3];
+    for (int e = 0; e < K * 3; ++e) gsh[e] = 0.f;
+
+    __shared__ float s_red[8][6];
+
+    for (int vi = 0; vi < bp.n_views; ++vi) {
+        const ViewParam& V = bp.v[vi];
+        float pose[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        bool inview = live && i >= V.g_begin && i < V.g_end;
+        const long long r = V.rec_off + (i - V.g_begin);
+        float acc[kGrad2D];
+        if (inview) {
+            bool any = false;
+            for (int e = 0; e < kGrad2D; ++e) {
+                acc[e] = ws.grad2d[r * kGrad2D + e];
+                any |= acc[e] != 0.f;
+            }
+            inview = any && project_view(V, rc, mu, P);
+        }
+        if (inview) {
+            const float sigma = 1.f / (1.f + expf(-ologit));
+            // record-space gradients -> natural parameters (see k_render_bwd):
+            const float gqx = kLn2 * acc[0], gqy = kLn2 * acc[1];
+            const float gA = -0.5f * acc[2], gB = -acc[3], gC = -0.5f * acc[4];
+            const float gsig = acc[5] / sigma;
+            float col[3];
+            view_colour(V, g, i, mu, P, col);
+            // colour -> SH (+ view direction)
+            float gd[3] = {0.f, 0.f, 0.f};
+            {
+                float gdir[3] = {0.f, 0.f, 0.f};
+                const long long base = i * K * 3;
+                for (int ch = 0; ch < 3; ++ch) {
+                    const float graw = P.raw[ch] > 0.f ? acc[6 + ch] : 0.f;
+                    gsh[ch] += kShC0 * graw;
+                    if (g.sh_degree >= 1) {
+                        gsh[3 + ch] += -kShC1 * P.dir[1] * graw;
+                        gsh[6 + ch] += kShC1 * P.dir[2] * graw;
+                        gsh[9 + ch] += -kShC1 * P.dir[0] * graw;
+                        gdir[0] += -kShC1 * load_as_float(g.sh, g.sh_dtype, base + 9 + ch) * graw;
+                        gdir[1] += -kShC1 * load_as_float(g.sh, g.sh_dtype, base + 3 + ch) * graw;
+                        gdir[2] += kShC1 * load_as_float(g.sh, g.sh_dtype, base + 6 + ch) * graw;
+                    }
+                }
+                if (g.sh_degree >= 1) {
+                    const float dd = P.dir[0] * gdir[0] + P.dir[1] * gdir[1] + P.dir[2] * gdir[2];
+                    for (int k = 0; k < 3; ++k) {
+                        gd[k] = (gdir[k] - P.dir[k] * dd) * P.inv_len;
+                        gmu[k] += gd[k];
+                    }
+                }
+            }
+            gop += gsig * sigma * (1.f - sigma);
+
+            // conic Q = Sigma2^-1, dL/dSigma2 = -Q G Q with G = [[gA, gB/2], [gB/2, gC]]
+            const float hB = 0.5f * gB;
+            const float m00 = P.A * gA + P.B * hB, m01 = P.A * hB + P.B * gC;
+            const float m10 = P.B * gA + P.C * hB, m11 = P.B * hB + P.C * gC;
+            const float G00 = -(m00 * P.A + m01 * P.B);
+            const float G01 = -(m00 * P.B + m01 * P.C);
+            const float G11 = -(m10 * P.B + m11 * P.C);
+            // Sigma2 = T Sigma3 T^T: dL/dSigma3 += T^T G2 T ; dL/dT = 2 G2 T Sigma3
+            const float* T0 = P.Tm;
+            const float* T1 = P.Tm + 3;
+            {
+                const int ia[6] = {0, 0, 0, 1, 1, 2};
+                const int ib[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+                for (int e = 0; e < 6; ++e) {
+                    const int a = ia[e], b = ib[e];
+                    gS3[e] += G00 * T0[a] * T0[b] + G01 * (T0[a] * T1[b] + T1[a] * T0[b]) +
+                              G11 * T1[a] * T1[b];
+                }
+            }
+            float TS0[3], TS1[3];  // T Sigma3 rows
+            for (int b = 0; b < 3; ++b) {
+                TS0[b] = T0[0] * s3(P.S3, 0, b) + T0[1] * s3(P.S3, 1, b) + T0[2] * s3(P.S3, 2, b);
+                TS1[b] = T1[0] * s3(P.S3, 0, b) + T1[1] * s3(P.S3, 1, b) + T1[2] * s3(P.S3, 2, b);
+            }
+            float gT0[3], gT1[3];
+            for (int b = 0; b < 3; ++b) {
+                gT0[b] = 2.f * (G00 * TS0[b] + G01 * TS1[b]);
+                gT1[b] = 2.f * (G01 * TS0[b] + G11 * TS1[b]);
+            }
+            // T = J W: dL/dJ = dL/dT W^T (only J00, J02, J11, J12 are non-zero)
+            const float gJ00 = gT0[0] * V.R[0] + gT0[1] * V.R[1] + gT0[2] * V.R[2];
+            const float gJ02 = gT0[0] * V.R[6] + gT0[1] * V.R[7] + gT0[2] * V.R[8];
+            const float gJ11 = gT1[0] * V.R[3] + gT1[1] * V.R[4] + gT1[2] * V.R[5];
+            const float gJ12 = gT1[0] * V.R[6] + gT1[1] * V.R[7] + gT1[2] * V.R[8];
+            const float x = P.pc[0], y = P.pc[1], z = P.pc[2];
+            const float iz = 1.f / z, iz2 = iz * iz, iz3 = iz2 * iz;
+            float gp[3];
+            gp[0] = gJ02 * (-V.fx * iz2) + gqx * V.fx * iz;
+            gp[1] = gJ12 * (-V.fy * iz2) + gqy * V.fy * iz;
+            gp[2] = gJ00 * (-V.fx * iz2) + gJ02 * (2.f * V.fx * x * iz3) + gJ11 * (-V.fy * iz2) +
+                    gJ12 * (2.f * V.fy * y * iz3) - (gqx * V.fx * x + gqy * V.fy * y) * iz2;
+            // p_C = W mu + t
+            for (int k = 0; k < 3; ++k)
+                gmu[k] += V.R[k] * gp[0] + V.R[3 + k] * gp[1] + V.R[6 + k] * gp[2];
+            if (want_pose) {
+                // dL/dW (through T = J W) = J^T dL/dT; J rows: (j00, 0, j02), (0, j11, j12)
+                const float j00 = V.fx * iz, j02 = -V.fx * x * iz2;
+                const float j11 = V.fy * iz, j12 = -V.fy * y * iz2;
+                float gW[9];
+                for (int b = 0; b < 3; ++b) {
+                    gW[b] = j00 * gT0[b];
+                    gW[3 + b] = j11 * gT1[b];
+                    gW[6 + b] = j02 * gT0[b] + j12 * gT1[b];
+                }
+                // M = gW W^T ; dphi += vee-like terms (M21 - M12, M02 - M20, M10 - M01)
+                float Mw[9];
+                for (int a = 0; a < 3; ++a)
+                    for (int b = 0; b < 3; ++b)
+                        Mw[3 * a + b] = gW[3 * a] * V.R[3 * b] + gW[3 * a + 1] * V.R[3 * b + 1] +
+                                        gW[3 * a + 2] * V.R[3 * b + 2];
+                pose[0] = (y * gp[2] - z * gp[1]) + (Mw[7] - Mw[5]);
+                pose[1] = (z * gp[0] - x * gp[2]) + (Mw[2] - Mw[6]);
+                pose[2] = (x * gp[1] - y * gp[0]) + (Mw[3] - Mw[1]);
+                for (int k = 0; k < 3; ++k)
+                    pose[3 + k] = gp[k] + V.R[3 * k] * gd[0] + V.R[3 * k + 1] * gd[1] + V.R[3 * k + 2] * gd[2];
+            }
+        }
+        if (want_pose) {
+            // Block reduction of the 6 pose components for this view.
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                float v = pose[k];
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                pose[k] = v;
+            }
+            const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+            if (lane == 0)
+                for (int k = 0; k < 6; ++k) s_red[w][k] = pose[k];
+            __syncthreads();
+            if (threadIdx.x < 6 && (int)blockIdx.x < pose_blocks) {
+                float v = 0.f;
+                for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) v += s_red[ww][threadIdx.x];
+                ws.partials[((long long)vi * pose_blocks + blockIdx.x) * 6 + threadIdx.x] = v;
+            }
+            __syncthreads();
+        }
+    }
+
+    if (!live || !want_params) return;
+    // Sigma3 = M M^T with G3 = dL/dSigma3 as a full symmetric matrix
+    // (gS3 holds its upper triangle): dL/dM = 2 G3 M.
+    float G3[9];
+    G3[0] = gS3[0]; G3[4] = gS3[3]; G3[8] = gS3[5];
+    G3[1] = G3[3] = gS3[1];
+    G3[2] = G3[6] = gS3[2];
+    G3[5] = G3[7] = gS3[4];
+    float gM[9];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b)
+            gM[3 * a + b] = 2.f * (G3[3 * a] * P.M[b] + G3[3 * a + 1] * P.M[3 + b] + G3[3 * a + 2] * P.M[6 + b]);
+    float gR[9];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) gR[3 * a + b] = gM[3 * a + b] * P.s[b];
+    for (int b = 0; b < 3; ++b)
+        gr.log_scales[3 * i + b] = (gM[b] * P.R[b] + gM[3 + b] * P.R[3 + b] + gM[6 + b] * P.R[6 + b]) * P.s[b];
+    const float w = P.qh[0], x = P.qh[1], y = P.qh[2], z = P.qh[3];
+    float gq[4];
+    gq[0] = 2.f * (-z * gR[1] + y * gR[2] + z * gR[3] - x * gR[5] - y * gR[6] + x * gR[7]);
+    gq[1] = 2.f * (y * gR[1] + z * gR[2] + y * gR[3] - 2.f * x * gR[4] - w * gR[5] + z * gR[6] + w * gR[7] -
+                   2.f * x * gR[8]);
+    gq[2] = 2.f * (-2.f * y * gR[0] + x * gR[1] + w * gR[2] + x * gR[3] + z * gR[5] - w * gR[6] + z * gR[7] -
+                   2.f * y * gR[8]);
+    gq[3] = 2.f * (-2.f * z * gR[0] - w * gR[1] + x * gR[2] + w * gR[3] - 2.f * z * gR[4] + y * gR[5] +
+                   x * gR[6] + y * gR[7]);
+    const float dq = gq[0] * P.qh[0] + gq[1] * P.qh[1] + gq[2] * P.qh[2] + gq[3] * P.qh[3];
+    for (int k = 0; k < 4; ++k) gr.quats[4 * i + k] = (gq[k] - P.qh[k] * dq) * P.inv_qn;
+    for (int k = 0; k < 3; ++k) gr.means[3 * i + k] = gmu[k];
+    gr.opacity[i] = gop;
+    for (int e = 0; e < K * 3; ++e) gr.sh[i * K * 3 + e] = gsh[e];
+}
+
+__global__ void k_pose_finish(const float* partials, int nblocks, int n_views, float* dL_dpose) {
+    // one warp per (view, component): fixed-order sum for determinism
+    const int item = blockIdx.x;
+    if (item >= n_views * 6) return;
+    const int vi = item / 6, k = item % 6;
+    float s = 0.f;
+    for (int b = threadIdx.x; b < nblocks; b += 32) s += partials[((long long)vi * nblocks + b) * 6 + k];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) dL_dpose[vi * 6 + k] = s;
+}
+
+}  // namespace
+
+cudaError_t launch_project(const BatchParam& bp, const GaussPtrs& g, const RenderConst& rc,
+                           const WsPtrs& ws, cudaStream_t s, Prof& pf) {
+    if (bp.max_count <= 0) return cudaSuccess;
+    dim3 grid((unsigned)((bp.max_count + 255) / 256), (unsigned)bp.n_views);
+    const int pi = pf.begin(GS_KF_PROJECT, s);
+    k_project<<<grid, 256, 0, s>>>(bp, g, rc, ws);
+    pf.end(pi, s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_project_bwd(const BatchParam& bp, const GaussPtrs& g, const RenderConst& rc,
+                               const WsPtrs& ws, const GradPtrs* grads, float* dL_dpose,
+                               cudaStream_t s, Prof& pf) {
+    if (g.n <= 0) return cudaSuccess;
+    const int nblk = (int)((g.n + 255) / 256);
+    long long max_g_end = 0;
+    for (int v = 0; v < bp.n_views; ++v)
+        if (bp.v[v].g_end > max_g_end) max_g_end = bp.v[v].g_end;
+    // Blocks past the last Gaussian any view renders contribute no pose
+    // gradient; the partials buffer is sized for the others.
+    const int pose_blocks = (int)((max_g_end + 255) / 256);
+    GradPtrs gr = grads ? *grads : GradPtrs{nullptr, nullptr, nullptr, nullptr, nullptr};
+    const int pi = pf.begin(GS_KF_PROJECT_BWD, s, dL_dpose ? 2 : 1);
+    k_project_bwd<<<nblk, 256, 0, s>>>(bp, g, rc, ws, gr, grads != nullptr, dL_dpose != nullptr, pose_blocks);
+    if (dL_dpose) k_pose_finish<<<bp.n_views * 6, 32, 0, s>>>(ws.partials, pose_blocks, bp.n_views, dL_dpose);
+    pf.end(pi, s);
+    return cudaGetLastError();
+}
+
+}  // namespace gsb

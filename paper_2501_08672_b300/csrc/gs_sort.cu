@@ -1,0 +1,348 @@
+// Tile binning: the (tile, depth) sort the 3D-GS tile rasteriser relies on
+// (Sec. II-C mentions its tile-based depth sorting).
+//
+// A least-significant-digit radix sort of 64-bit keys (tile << 32 | depth
+// bits) first sorts on the depth digits, which are identical for every pair
+// a Gaussian emits.  So the depth digits are sorted once per record (M keys)
+// instead of once per pair (P keys): records are radix-sorted by depth bits
+// (stable in record index), expanded into pairs in that order, and the pairs
+// are stably radix-sorted by tile id only (ceil(log2 T) bits).  The result is
+// the order of the full 64-bit sort with ties broken by record index.
+//
+// Every kernel reads counts from device memory, so the whole binning step
+// needs no host synchronisation and can be captured in a CUDA graph; the
+// pair capacity is fixed by the workspace and overflow is latched.
+#include "gs_internal.cuh"
+
+namespace gsb {
+
+namespace {
+
+constexpr int kRadixThreads = 256;
+constexpr int kRadixWarps = kRadixThreads / 32;
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanChunk = kScanThreads * kScanItems;
+
+__device__ __forceinline__ unsigned long long clamp_n(unsigned long long n_host,
+                                                      const unsigned long long* n_dev) {
+    if (!n_dev) return n_host;
+    const unsigned long long d = *n_dev;
+    return d < n_host ? d : n_host;
+}
+
+__device__ __forceinline__ void chunk_of(unsigned long long n, int G, int b, unsigned long long& begin,
+                                         unsigned long long& end) {
+    unsigned long long per = (n + G - 1) / G;
+    per = (per + kRadixThreads - 1) / kRadixThreads * kRadixThreads;
+    begin = per * b;
+    end = begin + per;
+    if (begin > n) begin = n;
+    if (end > n) end = n;
+}
+
+// Per-block digit histogram: hist[digit * G + block].
+__global__ void __launch_bounds__(kRadixThreads) k_radix_hist(const uint32_t* __restrict__ keys,
+                                                              unsigned long long n_host,
+                                                              const unsigned long long* n_dev,
+                                                              int shift, int bits,
+                                                              uint32_t* __restrict__ hist) {
+    __shared__ uint32_t h[256];
+    const int t = threadIdx.x, G = gridDim.x, b = blockIdx.x;
+    h[t] = 0;
+    __syncthreads();
+    const unsigned long long n = clamp_n(n_host, n_dev);
+    unsigned long long begin, end;
+    chunk_of(n, G, b, begin, end);
+    const uint32_t mask = (1u << bits) - 1u;
+    for (unsigned long long i = begin + t; i < end; i += kRadixThreads)
+        atomicAdd(&h[(keys[i] >> shift) & mask], 1u);
+    __syncthreads();
+    hist[(size_t)t * G + b] = h[t];
+}
+
+// Exclusive scan of the digit-major histogram (256 x G entries), one block.
+__global__ void __launch_bounds__(1024) k_radix_scan(uint32_t* hist, int total) {
+    __shared__ uint32_t s[1024];
+    const int t = threadIdx.x;
+    const int per = (total + 1023) / 1024;
+    const int b0 = t * per;
+    uint32_t sum = 0;
+    for (int k = 0; k < per; ++k)
+        if (b0 + k < total) sum += hist[b0 + k];
+    s[t] = sum;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        uint32_t v = t >= o ? s[t - o] : 0u;
+        __syncthreads();
+        s[t] += v;
+        __syncthreads();
+    }
+    uint32_t run = s[t] - sum;  // exclusive prefix of this thread's segment
+    for (int k = 0; k < per; ++k)
+        if (b0 + k < total) {
+            const uint32_t v = hist[b0 + k];
+            hist[b0 + k] = run;
+            run += v;
+        }
+}
+
+// Stable scatter: each block walks its chunk 256 keys at a time; the rank of
+// a key among equal digits is (keys of that digit in earlier warps of the
+// tile) + (equal-digit lanes below it in its warp, via match.any).
+__global__ void __launch_bounds__(kRadixThreads) k_radix_scatter(
+    const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
+    uint32_t* __restrict__ vout, unsigned long long n_host, const unsigned long long* n_dev,
+    int shift, int bits, const uint32_t* __restrict__ hist) {
+    __shared__ uint32_t s_base[256];
+    __shared__ uint32_t s_wc[kRadixWarps][256];
+    const int t = threadIdx.x, G = gridDim.x, b = blockIdx.x;
+    const int w = t >> 5, lane = t & 31;
+    s_base[t] = hist[(size_t)t * G + b];
+    const unsigned long long n = clamp_n(n_host, n_dev);
+    unsigned long long begin, end;
+    chunk_of(n, G, b, begin, end);
+    const uint32_t mask = (1u << bits) - 1u;
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    for (unsigned long long base = begin; base < end; base += kRadixThreads) {
+#pragma unroll
+        for (int ww = 0; ww < kRadixWarps; ++ww) s_wc[ww][t] = 0u;
+        __syncthreads();
+        const unsigned long long i = base + t;
+        const bool valid = i < end;
+        const uint32_t k = valid ? kin[i] : 0u;
+        const uint32_t v = valid ? vin[i] : 0u;
+        const uint32_t d = valid ? ((k >> shift) & mask) : 0x100u;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t rank = __popc(peers & lt_mask);
+        if (valid && rank == 0) s_wc[w][d] = __popc(peers);
+        __syncthreads();
+        {
+            uint32_t run = s_base[t];
+#pragma unroll
+            for (int ww = 0; ww < kRadixWarps; ++ww) {
+                const uint32_t c = s_wc[ww][t];
+                s_wc[ww][t] = run;
+                run += c;
+            }
+            s_base[t] = run;
+        }
+        __syncthreads();
+        if (valid) {
+            const uint32_t pos = s_wc[w][d] + rank;
+            kout[pos] = k;
+            vout[pos] = v;
+        }
+        __syncthreads();
+    }
+}
+
+// ---- tiles-touched scan in depth order ------------------------------------
+
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t& total) {
+    __shared__ uint32_t s_w[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_w[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        const int nw = blockDim.x >> 5;
+        uint32_t y = lane < nw ? s_w[lane] : 0u;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t z = __shfl_up_sync(0xffffffffu, y, o);
+            if (lane >= o) y += z;
+        }
+        s_w[lane] = y;
+    }
+    __syncthreads();
+    total = s_w[(blockDim.x >> 5) - 1];
+    const uint32_t wprefix = w > 0 ? s_w[w - 1] : 0u;
+    __syncthreads();
+    return wprefix + x - v;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* __restrict__ order,
+                                                              const uint32_t* __restrict__ touched,
+                                                              long long M,
+                                                              unsigned long long* __restrict__ part) {
+    const long long base = (long long)blockIdx.x * kScanChunk + threadIdx.x * kScanItems;
+    uint32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k)
+        if (base + k < M) s += touched[order[base + k]];
+    uint32_t total;
+    block_exclusive_scan(s, total);
+    if (threadIdx.x == 0) part[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_top(unsigned long long* part, int nparts,
+                                                   unsigned long long* counters, long long cap,
+                                                   unsigned int* status,
+                                                   unsigned long long* status_pairs) {
+    __shared__ unsigned long long s[1024];
+    const int t = threadIdx.x;
+    const int per = (nparts + 1023) / 1024;
+    const int b0 = t * per;
+    unsigned long long sum = 0;
+    for (int k = 0; k < per; ++k)
+        if (b0 + k < nparts) sum += part[b0 + k];
+    s[t] = sum;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        unsigned long long v = t >= o ? s[t - o] : 0ull;
+        __syncthreads();
+        s[t] += v;
+        __syncthreads();
+    }
+    unsigned long long run = s[t] - sum;
+    for (int k = 0; k < per; ++k)
+        if (b0 + k < nparts) {
+            const unsigned long long v = part[b0 + k];
+            part[b0 + k] = run;
+            run += v;
+        }
+    if (t == 1023) {
+        const unsigned long long total = s[1023];
+        counters[0] = total;
+        if (status_pairs) *status_pairs = total;
+        if (total > (unsigned long long)cap && status) atomicCAS(status, 0u, (unsigned int)(-GS_ERR_CAPACITY));
+    }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(const uint32_t* __restrict__ order,
+                                                             const uint32_t* __restrict__ touched,
+                                                             long long M,
+                                                             const unsigned long long* __restrict__ part,
+                                                             unsigned long long* __restrict__ offsets) {
+    const long long base = (long long)blockIdx.x * kScanChunk + threadIdx.x * kScanItems;
+    uint32_t v[kScanItems];
+    uint32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        v[k] = base + k < M ? touched[order[base + k]] : 0u;
+        s += v[k];
+    }
+    uint32_t total;
+    const uint32_t ex = block_exclusive_scan(s, total);
+    unsigned long long run = part[blockIdx.x] + ex;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k)
+        if (base + k < M) {
+            offsets[base + k] = run;
+            run += v[k];
+        }
+}
+
+// One thread per record in depth order writes its pairs (global tile id,
+// record index) at its scanned offset, row-major over its tile rectangle.
+__global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ order,
+                                              const uint32_t* __restrict__ touched,
+                                              const int4* __restrict__ rects,
+                                              const unsigned long long* __restrict__ offsets, long long M,
+                                              long long cap, uint32_t* __restrict__ pkeys,
+                                              uint32_t* __restrict__ pvals) {
+    const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= M) return;
+    const uint32_t r = order[j];
+    const uint32_t tt = touched[r];
+    if (tt == 0) return;
+    const int4 rc = rects[r];
+    const int tx0 = rc.x & 0xFFFF, ty0 = (rc.x >> 16) & 0xFFFF;
+    const int tx1 = rc.y & 0xFFFF, ty1 = (rc.y >> 16) & 0xFFFF;
+    unsigned long long o = offsets[j];
+    for (int ty = ty0; ty < ty1; ++ty) {
+        const uint32_t row = (uint32_t)rc.z + (uint32_t)ty * (uint32_t)rc.w;
+        for (int tx = tx0; tx < tx1; ++tx, ++o) {
+            if (o < (unsigned long long)cap) {
+                pkeys[o] = row + (uint32_t)tx;
+                pvals[o] = r;
+            }
+        }
+    }
+}
+
+// Tile ranges over the sorted pair keys.
+__global__ void k_ranges(const uint32_t* __restrict__ keys, long long cap,
+                         const unsigned long long* __restrict__ n_dev, uint2* __restrict__ ranges) {
+    const unsigned long long n = clamp_n((unsigned long long)cap, n_dev);
+    for (unsigned long long j = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+         j += (unsigned long long)gridDim.x * blockDim.x) {
+        const uint32_t k = keys[j];
+        if (j == 0 || keys[j - 1] != k) ranges[k].x = (uint32_t)j;
+        if (j + 1 == n || keys[j + 1] != k) ranges[k].y = (uint32_t)(j + 1);
+    }
+}
+
+cudaError_t radix_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, uint32_t* hist,
+                       unsigned long long n_host, const unsigned long long* n_dev, int key_bits,
+                       int G, int* result_buf, cudaStream_t s, Prof& pf, int fam) {
+    const int passes = key_bits <= 0 ? 0 : (key_bits + 7) / 8;
+    const int pi = pf.begin(fam, s, 3 * passes);
+    const int dbits = passes ? (key_bits + passes - 1) / passes : 0;
+    uint32_t* kin = k0;
+    uint32_t* vin = v0;
+    uint32_t* kout = k1;
+    uint32_t* vout = v1;
+    for (int p = 0; p < passes; ++p) {
+        const int shift = p * dbits;
+        const int bits = key_bits - shift < dbits ? key_bits - shift : dbits;
+        k_radix_hist<<<G, kRadixThreads, 0, s>>>(kin, n_host, n_dev, shift, bits, hist);
+        k_radix_scan<<<1, 1024, 0, s>>>(hist, 256 * G);
+        k_radix_scatter<<<G, kRadixThreads, 0, s>>>(kin, vin, kout, vout, n_host, n_dev, shift, bits, hist);
+        uint32_t* tk = kin; kin = kout; kout = tk;
+        uint32_t* tv = vin; vin = vout; vout = tv;
+    }
+    pf.end(pi, s);
+    *result_buf = passes % 2;
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_bin(const BatchParam& bp, WsPtrs& ws, unsigned int* status,
+                       unsigned long long* status_pairs, cudaStream_t s, Prof& pf) {
+    const long long M = bp.total_recs;
+    cudaError_t e;
+    if (M <= 0) return cudaSuccess;
+    // 1. front-to-back order of records: 32-bit depth keys, stable in index
+    int dbuf = 0;
+    e = radix_sort(ws.dkeys[0], ws.dvals[0], ws.dkeys[1], ws.dvals[1], ws.hist,
+                   (unsigned long long)M, nullptr, 32, ws.radix_grid, &dbuf, s, pf, GS_KF_DEPTH_SORT);
+    if (e != cudaSuccess) return e;
+    const uint32_t* order = ws.dvals[dbuf];
+    // 2. exclusive scan of tiles-touched in that order
+    const int nb = (int)((M + kScanChunk - 1) / kScanChunk);
+    int pi = pf.begin(GS_KF_TILE_SCAN, s, 3);
+    k_scan_reduce<<<nb, kScanThreads, 0, s>>>(order, ws.tiles_touched, M, ws.scan_part);
+    k_scan_top<<<1, 1024, 0, s>>>(ws.scan_part, nb, ws.counters, ws.cap, status, status_pairs);
+    k_scan_apply<<<nb, kScanThreads, 0, s>>>(order, ws.tiles_touched, M, ws.scan_part, ws.offsets);
+    pf.end(pi, s);
+    // 3. expand records into (tile, record) pairs
+    pi = pf.begin(GS_KF_EMIT, s);
+    k_emit<<<(unsigned)((M + 255) / 256), 256, 0, s>>>(order, ws.tiles_touched, ws.rect, ws.offsets, M,
+                                                       ws.cap, ws.pkeys[0], ws.pvals[0]);
+    pf.end(pi, s);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // 4. stable sort of pairs by global tile id
+    int tile_bits = 1;
+    while ((1ll << tile_bits) < (long long)bp.total_tiles) ++tile_bits;
+    int pbuf = 0;
+    e = radix_sort(ws.pkeys[0], ws.pvals[0], ws.pkeys[1], ws.pvals[1], ws.hist,
+                   (unsigned long long)ws.cap, ws.counters, tile_bits, ws.radix_grid, &pbuf, s, pf,
+                   GS_KF_TILE_SORT);
+    if (e != cudaSuccess) return e;
+    ws.sorted_buf = pbuf;
+    // 5. per-tile [start, end)
+    pi = pf.begin(GS_KF_RANGES, s, 2);
+    e = cudaMemsetAsync(ws.ranges, 0, sizeof(uint2) * (size_t)bp.total_tiles, s);
+    if (e != cudaSuccess) return e;
+    k_ranges<<<1184, 256, 0, s>>>(ws.pkeys[pbuf], ws.cap, ws.counters, ws.ranges);
+    pf.end(pi, s);
+    return cudaGetLastError();
+}
+
+}  // namespace gsb

@@ -1,0 +1,284 @@
+"""High-level API over the C ABI: a renderer for a batch of keyframe views, a
+torch.autograd.Function, the sliding-window optimisation step (Sec. II-B.2)
+and the photometric pose-gradient step (Sec. II-D).
+
+Torch provides device memory and streams only; every computation is a call
+into libgs_b300.so.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import binding as B
+
+
+class Renderer:
+    """Renders a fixed batch of views (layout fixed, poses may change via
+    `set_views`) and owns the image buffers and the workspace."""
+
+    def __init__(self, views, device=0, tile_size=16, capacity=None, **cfg):
+        self.device = torch.device("cuda", device)
+        self.ctx = B.Context(device, tile_size=tile_size, **cfg)
+        self.view_dicts = [dict(v) for v in views]
+        self.views = B.make_views(self.view_dicts)
+        self.n_views = len(views)
+        self.npx = sum(B.pixel_counts(self.view_dicts))
+        dev = self.device
+        self.rgb = torch.empty(3 * self.npx, device=dev, dtype=torch.float32)
+        self.T = torch.empty(self.npx, device=dev, dtype=torch.float32)
+        self.n_contrib = torch.empty(self.npx, device=dev, dtype=torch.int32)
+        self.dL_drgb = torch.empty(3 * self.npx, device=dev, dtype=torch.float32)
+        self.loss = torch.zeros(1, device=dev, dtype=torch.float32)
+        self.dL_dpose = torch.zeros(self.n_views * 6, device=dev, dtype=torch.float32)
+        self.cap = 0
+        self.ws = None
+        self.ws_struct = None
+        self._counted = False
+        self.ensure_capacity(capacity or 1 << 16)
+
+    def set_views(self, views):
+        """Replaces camera poses / intrinsics; the layout (sizes, ranges) must
+        not change."""
+        for old, new in zip(self.view_dicts, views):
+            for k in ("W", "H", "g_begin", "g_end"):
+                if int(old[k]) != int(new[k]):
+                    raise ValueError("set_views may not change the view layout")
+        self.view_dicts = [dict(v) for v in views]
+        self.views = B.make_views(self.view_dicts)
+
+    def ensure_capacity(self, pairs):
+        if pairs <= self.cap and self.ws is not None:
+            return False
+        self.cap = B.suggest_capacity(pairs)
+        nbytes = self.ctx.workspace_bytes(self.views, self.cap)
+        self.ws = torch.empty(nbytes, device=self.device, dtype=torch.uint8)
+        self.ws_struct = B.Context.ws_struct(self.ws, self.cap)
+        return True
+
+    def layout(self):
+        return self.ctx.layout(self.views, self.cap)
+
+    def forward(self, g, count=None):
+        """project + bin + composite into self.rgb / self.T / self.n_contrib.
+        count: True synchronises to read the pair count and grows the workspace
+        if needed (default: only on the first call)."""
+        if count is None:
+            count = not self._counted
+        self.ctx.project(g, self.views, self.ws_struct)
+        if count:
+            while True:
+                try:
+                    n = self.ctx.bin(self.views, self.ws_struct, want_count=True)
+                    break
+                except B.GsError as e:
+                    if e.code != B.GS_ERR_CAPACITY:
+                        raise
+                    self.ensure_capacity(e.pairs_needed)
+                    self.ctx.project(g, self.views, self.ws_struct)
+            self._counted = True
+            self.last_pairs = n
+        else:
+            self.ctx.bin(self.views, self.ws_struct)
+        self.ctx.render_fwd(self.views, self.ws_struct, self.rgb, self.T, self.n_contrib)
+
+    def l1(self, target):
+        self.ctx.l1_loss(self.views, self.ws_struct, self.rgb, target, self.dL_drgb, self.loss)
+
+    def backward(self, g, dL_drgb, grads=None, want_pose=False):
+        self.ctx.render_bwd(g, self.views, self.ws_struct, self.T, self.n_contrib, dL_drgb, grads,
+                            self.dL_dpose if want_pose else None)
+
+    def pose_grad(self, g, dL_drgb):
+        self.ctx.pose_grad(g, self.views, self.ws_struct, self.T, self.n_contrib, dL_drgb, self.dL_dpose)
+
+    def images(self, flat=None):
+        return B.unpack_images(self.rgb if flat is None else flat, self.view_dicts, 3)
+
+    def check_status(self):
+        rc, n = self.ctx.sync_status()
+        if rc == B.GS_ERR_CAPACITY:
+            self.ensure_capacity(n)
+        return rc, n
+
+
+class GaussianWindow:
+    """The window's parameters as one flat FP32 master vector (Adam runs over
+    it in one launch) with per-group views, gradients, Adam moments and
+    optional FP16/BF16 render copies of the non-mean groups."""
+
+    GROUPS = ("means", "log_scales", "quats", "opacity", "sh")
+
+    def __init__(self, params, device=0, storage=None):
+        self.device = torch.device("cuda", device)
+        self.sh_degree = int(params["sh_degree"])
+        self.K = (self.sh_degree + 1) ** 2
+        self.n = int(params["means"].shape[0])
+        n, K = self.n, self.K
+        self.sizes = dict(means=3 * n, log_scales=3 * n, quats=4 * n, opacity=n, sh=3 * K * n)
+        self.shapes = dict(means=(n, 3), log_scales=(n, 3), quats=(n, 4), opacity=(n,), sh=(n, K, 3))
+        self.offsets = {}
+        off = 0
+        for k in self.GROUPS:
+            self.offsets[k] = off
+            off += self.sizes[k]
+            off = (off + 3) // 4 * 4  # keep each group 16-byte aligned
+        self.total = off
+        dev = self.device
+        self.flat = torch.zeros(self.total, device=dev, dtype=torch.float32)
+        self.gflat = torch.zeros(self.total, device=dev, dtype=torch.float32)
+        self.m = torch.zeros(self.total, device=dev, dtype=torch.float32)
+        self.v = torch.zeros(self.total, device=dev, dtype=torch.float32)
+        self.step_count = 0
+        for k in self.GROUPS:
+            self.group(k).copy_(torch.as_tensor(np.ascontiguousarray(params[k], np.float32)).view(self.shapes[k]))
+        self.storage = dict(storage or {})
+        self.lowp = {}
+        for k, dt in self.storage.items():
+            if k == "means":
+                raise ValueError("means are always FP32")
+            self.lowp[k] = self.group(k).to(dt).contiguous()
+
+    def group(self, k, flat=None):
+        f = self.flat if flat is None else flat
+        o = self.offsets[k]
+        return f[o:o + self.sizes[k]].view(self.shapes[k])
+
+    def grad(self, k):
+        return self.group(k, self.gflat)
+
+    def render_tensors(self):
+        return [self.lowp.get(k, self.group(k)) for k in self.GROUPS]
+
+    def struct(self):
+        t = self.render_tensors()
+        return B.gaussians_struct(*t, self.sh_degree)
+
+    def grad_tensors(self):
+        return [self.grad(k) for k in self.GROUPS]
+
+    def segments(self):
+        return [(self.offsets[k], self.offsets[k] + self.sizes[k], self.lowp[k]) for k in self.lowp]
+
+    def numpy(self, use_render_copy=False):
+        out = {}
+        for k in self.GROUPS:
+            t = self.lowp[k] if (use_render_copy and k in self.lowp) else self.group(k)
+            out[k] = t.float().cpu().numpy()
+        out["sh_degree"] = self.sh_degree
+        return out
+
+
+class WindowOptimizer:
+    """One sliding-window optimisation iteration (Sec. II-B.2): render every
+    keyframe, L1 photometric loss, backward to the Gaussians, Adam."""
+
+    def __init__(self, params, views, targets, lr=1e-3, betas=(0.9, 0.999), eps=1e-8, device=0,
+                 tile_size=16, storage=None, **cfg):
+        self.win = GaussianWindow(params, device, storage)
+        self.r = Renderer(views, device, tile_size, **cfg)
+        self.targets = targets
+        self.lr, self.betas, self.eps = lr, betas, eps
+        self._g = self.win.struct()
+        self._grads = self.win.grad_tensors()
+        self._segs = self.win.segments()
+
+    def step(self, count=None):
+        w, r = self.win, self.r
+        r.forward(self._g, count=count)
+        r.l1(self.targets)
+        r.backward(self._g, r.dL_drgb, grads=self._grads)
+        w.step_count += 1
+        r.ctx.adam_step(w.flat, w.gflat, w.m, w.v, self.lr, self.betas[0], self.betas[1], self.eps,
+                        w.step_count, self._segs)
+        return r.loss
+
+
+class _Rasterize(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, renderer, sh_degree, means, log_scales, quats, opacity, sh):
+        g = B.gaussians_struct(means, log_scales, quats, opacity, sh, sh_degree)
+        renderer.forward(g)
+        ctx.renderer = renderer
+        ctx.sh_degree = sh_degree
+        ctx.save_for_backward(means, log_scales, quats, opacity, sh)
+        rgb = renderer.rgb.clone()
+        T = renderer.T.clone()
+        ctx.mark_non_differentiable(T)
+        return rgb, T
+
+    @staticmethod
+    def backward(ctx, dL_drgb, _dT):
+        means, log_scales, quats, opacity, sh = ctx.saved_tensors
+        r = ctx.renderer
+        g = B.gaussians_struct(means, log_scales, quats, opacity, sh, ctx.sh_degree)
+        grads = [torch.empty(t.shape, device=t.device, dtype=torch.float32) for t in
+                 (means, log_scales, quats, opacity, sh)]
+        r.backward(g, dL_drgb.contiguous().float(), grads=grads)
+        out = [gr.to(t.dtype) for gr, t in zip(grads, (means, log_scales, quats, opacity, sh))]
+        return (None, None, *out)
+
+
+def rasterize(renderer, means, log_scales, quats, opacity, sh, sh_degree):
+    """Differentiable render of the renderer's views.  Returns the packed rgb
+    ([sum 3 H W]) and the final transmittance ([sum H W], not differentiable).
+    Alpha is recomputed in the backward pass from the saved bins: call
+    backward before the next forward on the same renderer."""
+    return _Rasterize.apply(renderer, int(sh_degree), means.contiguous(), log_scales.contiguous(),
+                            quats.contiguous(), opacity.contiguous(), sh.contiguous())
+
+
+def se3_exp(xi):
+    """4x4 Exp of xi = (dphi, dt) (closed form, float64)."""
+    phi = np.asarray(xi[:3], np.float64)
+    rho = np.asarray(xi[3:], np.float64)
+    th = float(np.linalg.norm(phi))
+    K = np.array([[0, -phi[2], phi[1]], [phi[2], 0, -phi[0]], [-phi[1], phi[0], 0]])
+    if th < 1e-12:
+        R = np.eye(3) + K
+        V = np.eye(3) + 0.5 * K
+    else:
+        R = np.eye(3) + np.sin(th) / th * K + (1 - np.cos(th)) / th ** 2 * (K @ K)
+        V = np.eye(3) + (1 - np.cos(th)) / th ** 2 * K + (th - np.sin(th)) / th ** 3 * (K @ K)
+    T = np.eye(4)
+    T[:3, :3] = R
+    T[:3, 3] = V @ rho
+    return T
+
+
+def apply_left(view, xi):
+    """View with T_CW <- Exp(xi) T_CW."""
+    T = np.eye(4)
+    T[:3, :3] = np.asarray(view["R"], np.float64)
+    T[:3, 3] = np.asarray(view["t"], np.float64)
+    Tn = se3_exp(xi) @ T
+    out = dict(view)
+    out["R"] = Tn[:3, :3].astype(np.float32)
+    out["t"] = Tn[:3, 3].astype(np.float32)
+    return out
+
+
+class PoseTracker:
+    """Photometric pose update (Sec. II-D, Eq. minimization) for fixed
+    Gaussians: render at the current pose, L1 against the frame, pose-only
+    backward, then a host step T <- Exp(-eta g) T (the paper feeds the
+    gradient to its IESKF instead; the step rule does not change the GPU
+    work)."""
+
+    def __init__(self, params, view, device=0, tile_size=16, step_sizes=(2e-2, 2e-2), **cfg):
+        self.win = GaussianWindow(params, device)
+        self.r = Renderer([view], device, tile_size, **cfg)
+        self.g = self.win.struct()
+        self.eta_rot, self.eta_trans = step_sizes
+
+    def iterate(self, view, target):
+        self.r.set_views([view])
+        self.r.forward(self.g)
+        self.r.l1(target)
+        self.r.pose_grad(self.g, self.r.dL_drgb)
+        return self.r.dL_dpose
+
+    def step(self, view, target):
+        gpose = self.iterate(view, target).double().cpu().numpy()
+        xi = np.concatenate([-self.eta_rot * gpose[:3], -self.eta_trans * gpose[3:]])
+        return apply_left(view, xi), gpose

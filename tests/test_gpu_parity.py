@@ -1,0 +1,388 @@
+"""CUDA path (through the C ABI) against the FP64 oracle.
+
+Forward images must match within 1e-4 max abs and gradients within 1e-3
+relative L2 per parameter group, over pixels / Gaussians whose threshold
+decisions are not borderline (the oracle flags those; their share is
+asserted small).
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from paper_2501_08672_b300 import binding as B  # noqa: E402
+from paper_2501_08672_b300 import scenes  # noqa: E402
+from paper_2501_08672_b300.render import GaussianWindow, Renderer, WindowOptimizer, rasterize  # noqa: E402
+
+FWD_TOL = 1e-4
+GRAD_TOL = 1e-3
+LOG2E = 1.4426950408889634
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    torch.cuda.init()
+
+
+def gpu_forward(params, views, tile_size=16, storage=None, **cfg):
+    win = GaussianWindow(params, 0, storage)
+    r = Renderer(views, 0, tile_size, **cfg)
+    r.forward(win.struct())
+    torch.cuda.synchronize()
+    return win, r
+
+
+def ragged_views(n):
+    v0 = scenes.identity_view(200, 136, 160.0, 0, n)
+    v1 = scenes.lookat_view((0.6, -0.4, -1.0), (0.0, 0.0, 5.0), 150, 100, 120.0, 0, n, up=(0, -1, 0))
+    return [v0, v1]
+
+
+def ws_view(r, offset, dtype, count):
+    nbytes = np.dtype(dtype).itemsize * count
+    return r.ws[offset:offset + nbytes].view(torch.uint8).cpu().numpy().view(dtype)
+
+
+def compare_images(orc_out, gpu_img, gpu_T, tol=FWD_TOL):
+    ok = ~orc_out["border"]
+    frac = 1.0 - ok.mean()
+    assert frac < 1e-3, "borderline pixel share %.2e" % frac
+    err = np.abs(gpu_img - orc_out["rgb"])[:, ok].max()
+    errT = np.abs(gpu_T - orc_out["T"])[ok].max()
+    assert err <= tol, "image max abs err %.3e" % err
+    assert errT <= tol, "T_final max abs err %.3e" % errT
+    return err, frac
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+
+
+def compare_grads(win, orc_g, border, tol=GRAD_TOL, pose=None, orc_pose=None):
+    ok = ~border
+    assert border.mean() < 0.02, "borderline Gaussian share %.3f" % border.mean()
+    errs = {}
+    for k in GaussianWindow.GROUPS:
+        a = win.grad(k).detach().cpu().numpy().astype(np.float64)[ok].reshape(-1)
+        b = orc_g[k][ok].reshape(-1)
+        errs[k] = rel_l2(a, b)
+    bad = {k: e for k, e in errs.items() if not e <= tol}
+    assert not bad, "gradient rel L2 errors %s" % errs
+    if pose is not None:
+        for v in range(orc_pose.shape[0]):
+            e = rel_l2(pose[v], orc_pose[v])
+            assert e <= tol, "pose grad of view %d rel err %.3e (%s vs %s)" % (v, e, pose[v], orc_pose[v])
+    return errs
+
+
+def test_library_exports_and_version():
+    lib = B.lib()
+    for name in B.EXPORTED:
+        assert hasattr(lib, name)
+    assert b"sm_103a" in lib.gs_version()
+
+
+def test_projection_records_match_oracle(orc):
+    p = scenes.frustum_scene(3000, seed=1)
+    p["sh"] = np.concatenate([p["sh"], np.random.default_rng(0).normal(0, 0.2, (3000, 3, 3)).astype(np.float32)], 1)
+    p["sh_degree"] = 1
+    views = ragged_views(3000)
+    win, r = gpu_forward(p, views)
+    L = r.layout()
+    M = L.n_records
+    rec = ws_view(r, L.records, np.float32, 12 * M).reshape(M, 12)
+    touched = ws_view(r, L.tiles_touched, np.uint32, M)
+    off = 0
+    for v in views:
+        o = orc.project(p, v)
+        n = v["g_end"] - v["g_begin"]
+        R = rec[off:off + n]
+        vis = (o["valid"] == 1) & (o["opac"] > 1 / 255) & (touched[off:off + n] > 0)
+        np.testing.assert_allclose(R[vis, 0], o["q"][vis, 0], rtol=2e-6, atol=2e-4)
+        np.testing.assert_allclose(R[vis, 1], o["q"][vis, 1], rtol=2e-6, atol=2e-4)
+        A = R[vis, 2] / (-0.5 * LOG2E)
+        Bc = R[vis, 3] / (-LOG2E)
+        C = R[vis, 4] / (-0.5 * LOG2E)
+        scale = np.abs(o["conic"][vis]).max(1)
+        for got, k in ((A, 0), (Bc, 1), (C, 2)):
+            assert np.max(np.abs(got - o["conic"][vis, k]) / scale) < 2e-4
+        np.testing.assert_allclose(2.0 ** R[vis, 5], o["opac"][vis], rtol=2e-6)
+        np.testing.assert_allclose(R[vis][:, [6, 7, 8]], o["colour"][vis], atol=2e-6)
+        np.testing.assert_allclose(R[vis, 9], o["depth"][vis], rtol=2e-6)
+        # culled by the oracle -> no tiles on the GPU
+        assert np.all(touched[off:off + n][o["valid"] == 0] == 0)
+        off += n
+
+
+@pytest.mark.parametrize("ts", [8, 16, 32])
+def test_forward_matches_oracle_ragged_multiview(orc, ts):
+    p = scenes.frustum_scene(3000, seed=2)
+    views = ragged_views(3000)
+    win, r = gpu_forward(p, views, tile_size=ts)
+    imgs = r.images()
+    Ts = B.unpack_images(r.T, views, 1)
+    for v, img, T in zip(views, imgs, Ts):
+        o = orc.render_view(p, v)
+        compare_images(o, img.cpu().numpy(), T.cpu().numpy())
+
+
+def test_forward_is_tile_size_invariant():
+    p = scenes.frustum_scene(4000, seed=3)
+    views = ragged_views(4000)
+    outs = []
+    for ts in (8, 16, 32):
+        _, r = gpu_forward(p, views, tile_size=ts)
+        outs.append((r.rgb.clone(), r.T.clone()))
+    for rgb, T in outs[1:]:
+        assert torch.equal(rgb, outs[0][0])
+        assert torch.equal(T, outs[0][1])
+
+
+def test_bins_are_sorted_and_complete():
+    """Each tile list holds exactly the records whose tile rectangle contains
+    the tile, ordered by (depth bits, record index)."""
+    p = scenes.frustum_scene(2500, seed=4)
+    views = ragged_views(2500)
+    _, r = gpu_forward(p, views, tile_size=16)
+    L = r.layout()
+    M, T = L.n_records, L.n_tiles
+    rect = ws_view(r, L.rects, np.int32, 4 * M).reshape(M, 4)
+    touched = ws_view(r, L.tiles_touched, np.uint32, M)
+    rec = ws_view(r, L.records, np.float32, 12 * M).reshape(M, 12)
+    ranges = ws_view(r, L.tile_ranges, np.uint32, 2 * T).reshape(T, 2)
+    npairs = int(r.last_pairs)
+    sv = ws_view(r, L.sorted_vals, np.uint32, npairs)
+    assert int(touched.sum()) == npairs
+    expect = [[] for _ in range(T)]
+    for i in np.nonzero(touched)[0]:
+        x0, y0 = rect[i, 0] & 0xFFFF, rect[i, 0] >> 16
+        x1, y1 = rect[i, 1] & 0xFFFF, rect[i, 1] >> 16
+        for ty in range(y0, y1):
+            for tx in range(x0, x1):
+                expect[rect[i, 2] + ty * rect[i, 3] + tx].append(i)
+    depth_bits = rec[:, 9].view(np.uint32)
+    for t in range(T):
+        got = sv[ranges[t, 0]:ranges[t, 1]].tolist()
+        want = sorted(expect[t], key=lambda i: (int(depth_bits[i]), i))
+        assert got == want, "tile %d" % t
+
+
+def l1_target(params, views, seed=5):
+    """Target images: render of a perturbed copy (oracle, FP64)."""
+    from oracle import oracle as O
+    q = scenes.perturbed_copy(params, seed=seed)
+    return [O.render_view(q, v)["rgb"] for v in views]
+
+
+def gpu_loss_backward(win, r, targets_np):
+    tgt = torch.cat([torch.as_tensor(t, dtype=torch.float32).reshape(-1) for t in targets_np]).cuda()
+    r.l1(tgt)
+    grads = win.grad_tensors()
+    r.backward(win.struct(), r.dL_drgb, grads=grads, want_pose=True)
+    torch.cuda.synchronize()
+    return tgt
+
+
+def oracle_l1_backward(orc, params, views, targets_np, r):
+    """dL/drgb from the GPU image's sign pattern (identical almost everywhere
+    to the oracle's), fed to the oracle backward."""
+    imgs = [im.cpu().numpy().astype(np.float64) for im in r.images()]
+    # use the oracle's own forward for the residual sign, away from zero residuals
+    outs = [orc.render_view(params, v) for v in views]
+    L, dl = orc.l1_loss_grad([o["rgb"] for o in outs], targets_np)
+    sign_gpu = [np.sign(i - t) for i, t in zip(imgs, targets_np)]
+    agree = np.mean(np.concatenate([(np.sign(o["rgb"] - t) == s).reshape(-1)
+                                    for o, t, s in zip(outs, targets_np, sign_gpu)]))
+    assert agree > 0.999
+    # use exactly the GPU's sign pattern so both sides differentiate the same loss
+    n_views = len(views)
+    dl = [s / (s.size * n_views) for s in sign_gpu]
+    g, pose, border = orc.backward(params, views, dl)
+    return L, g, pose, border, outs
+
+
+def test_backward_matches_oracle_multiview(orc):
+    p = scenes.frustum_scene(1500, seed=6)
+    views = ragged_views(1500)
+    win, r = gpu_forward(p, views)
+    tg = l1_target(p, views)
+    gpu_loss_backward(win, r, tg)
+    L, g, pose, border, outs = oracle_l1_backward(orc, p, views, tg, r)
+    assert abs(float(r.loss.item()) - L) < 1e-5
+    compare_grads(win, g, border, pose=r.dL_dpose.view(-1, 6).cpu().numpy().astype(np.float64), orc_pose=pose)
+
+
+def test_plain_single_view_fp32_10k(orc):
+    """Configuration: 10k Gaussians in a 4x4x(2..8) m box, 320x256, fx=fy=300,
+    16x16 tiles, SH degree 0, target = render of a perturbed copy, L1."""
+    p = scenes.frustum_scene(10_000, seed=0)
+    views = [scenes.identity_view(320, 256, 300.0, 0, 10_000)]
+    win, r = gpu_forward(p, views)
+    o = orc.render_view(p, views[0])
+    compare_images(o, r.images()[0].cpu().numpy(), B.unpack_images(r.T, views, 1)[0].cpu().numpy())
+    tg = l1_target(p, views)
+    gpu_loss_backward(win, r, tg)
+    L, g, pose, border, _ = oracle_l1_backward(orc, p, views, tg, r)
+    compare_grads(win, g, border, pose=r.dL_dpose.view(-1, 6).cpu().numpy().astype(np.float64), orc_pose=pose)
+
+
+def test_box_room_window_degree1(orc):
+    """Box-room window (planar Gaussians, SH degree 1) seen by three uneven
+    keyframes, forward and backward."""
+    n = 20_000
+    p = scenes.box_room_scene(n, seed=7)
+    views = scenes.arc_views(3, 192, 160, 180.0, n_gaussians=n)
+    views[1] = dict(views[1], W=176, H=144, cx=88.0, cy=72.0)
+    win, r = gpu_forward(p, views)
+    tg = l1_target(p, views)
+    for v, img, T in zip(views, r.images(), B.unpack_images(r.T, views, 1)):
+        compare_images(orc.render_view(p, v), img.cpu().numpy(), T.cpu().numpy())
+    gpu_loss_backward(win, r, tg)
+    L, g, pose, border, _ = oracle_l1_backward(orc, p, views, tg, r)
+    compare_grads(win, g, border, pose=r.dL_dpose.view(-1, 6).cpu().numpy().astype(np.float64), orc_pose=pose)
+
+
+def test_uneven_gaussian_ranges(orc):
+    """Each view renders its own contiguous range of the window."""
+    n = 6000
+    p = scenes.frustum_scene(n, seed=8)
+    views = [scenes.identity_view(128, 96, 100.0, 0, 2500), scenes.identity_view(96, 128, 90.0, 2000, 6000),
+             scenes.identity_view(64, 64, 60.0, 1000, 1001)]
+    win, r = gpu_forward(p, views)
+    for v, img, T in zip(views, r.images(), B.unpack_images(r.T, views, 1)):
+        compare_images(orc.render_view(p, v), img.cpu().numpy(), T.cpu().numpy())
+    tg = l1_target(p, views)
+    gpu_loss_backward(win, r, tg)
+    L, g, pose, border, _ = oracle_l1_backward(orc, p, views, tg, r)
+    compare_grads(win, g, border, pose=r.dL_dpose.view(-1, 6).cpu().numpy().astype(np.float64), orc_pose=pose)
+
+
+def test_exact_mode_matches_oracle(orc):
+    """alpha_min = 0, alpha_max = 1, T_min = 0: every Gaussian at every pixel."""
+    p = scenes.frustum_scene(300, seed=9)
+    p["opacity"] = np.clip(p["opacity"], -4, 3).astype(np.float32)
+    views = [scenes.identity_view(72, 56, 60.0, 0, 300)]
+    cfg = dict(alpha_min=0.0, alpha_max=1.0, T_min=0.0)
+    win, r = gpu_forward(p, views, **cfg)
+    o = orc.render_view(p, views[0], dict(orc.EXACT_CFG))
+    compare_images(o, r.images()[0].cpu().numpy(), B.unpack_images(r.T, views, 1)[0].cpu().numpy())
+
+
+def test_background_colour(orc):
+    p = scenes.frustum_scene(800, seed=10)
+    views = [scenes.identity_view(80, 64, 70.0, 0, 800)]
+    bg = (0.2, 0.5, 0.9)
+    win, r = gpu_forward(p, views, bg=bg)
+    o = orc.render_view(p, views[0], dict(bg=bg))
+    compare_images(o, r.images()[0].cpu().numpy(), B.unpack_images(r.T, views, 1)[0].cpu().numpy())
+
+
+def test_adam_matches_oracle(orc):
+    rng = np.random.default_rng(11)
+    n = 10_003  # ragged tail after the float4 body
+    p = rng.standard_normal(n)
+    m = np.zeros(n); v = np.zeros(n)
+    ctx = B.Context(0)
+    tp = torch.tensor(p, dtype=torch.float32, device="cuda")
+    tm = torch.zeros(n, device="cuda"); tv = torch.zeros(n, device="cuda")
+    lowp = torch.empty(4000, dtype=torch.bfloat16, device="cuda")
+    for step in range(1, 6):
+        g = rng.standard_normal(n) * 10 ** rng.uniform(-3, 0)
+        tg = torch.tensor(g, dtype=torch.float32, device="cuda")
+        ctx.adam_step(tp, tg, tm, tv, 1e-3, 0.9, 0.999, 1e-8, step, segments=[(5000, 9000, lowp)])
+        orc.adam(p, np.ascontiguousarray(tg.cpu().numpy().astype(np.float64)), m, v, 1e-3, 0.9, 0.999, 1e-8, step)
+    got = tp.cpu().numpy().astype(np.float64)
+    np.testing.assert_allclose(got, p, rtol=0, atol=2e-6)
+    np.testing.assert_allclose(lowp.float().cpu().numpy(), got[5000:9000], rtol=1e-2)
+
+
+def test_autograd_function_matches_direct_calls():
+    p = scenes.frustum_scene(2000, seed=12)
+    views = ragged_views(2000)
+    win = GaussianWindow(p, 0)
+    r = Renderer(views, 0, 16)
+    ts = [win.group(k).detach().clone().requires_grad_(True) for k in GaussianWindow.GROUPS]
+    rgb, T = rasterize(r, *ts, sh_degree=0)
+    w = torch.randn_like(rgb)
+    (rgb * w).sum().backward()
+    r2 = Renderer(views, 0, 16)
+    r2.forward(win.struct())
+    assert torch.equal(r2.rgb, rgb.detach())
+    grads = win.grad_tensors()
+    r2.backward(win.struct(), w.contiguous(), grads=grads)
+    for t, g in zip(ts, grads):
+        assert torch.allclose(t.grad, g, rtol=1e-5, atol=1e-7)
+
+
+def test_capacity_overflow_is_reported_and_recovered():
+    p = scenes.frustum_scene(3000, seed=13)
+    views = ragged_views(3000)
+    win = GaussianWindow(p, 0)
+    r = Renderer(views, 0, 16, capacity=100)
+    assert r.cap < 1000
+    r.forward(win.struct())  # grows the workspace after GS_ERR_CAPACITY
+    assert r.cap >= r.last_pairs > 100
+    _, ref = gpu_forward(p, views)
+    assert torch.equal(r.rgb, ref.rgb)
+    # async path: a too-small workspace latches the status, reported later
+    r3 = Renderer(views, 0, 16, capacity=100)
+    r3._counted = True
+    r3.forward(win.struct())
+    rc, need = r3.ctx.sync_status()
+    assert rc == B.GS_ERR_CAPACITY and need == r.last_pairs
+    rc, _ = r3.ctx.sync_status()
+    assert rc == B.GS_OK
+
+
+def test_invalid_arguments_are_rejected():
+    ctx = B.Context(0)
+    v = B.make_views([scenes.identity_view(64, 48, 50.0, 0, 10)])
+    size = ctypes_size = ctx.workspace_bytes(v, 1000)
+    assert size > 0 and ctypes_size == size
+    bad = B.make_views([scenes.identity_view(64, 48, 50.0, 5, 5)])
+    with pytest.raises(B.GsError) as e:
+        ctx.workspace_bytes(bad, 1000)
+    assert e.value.code == B.GS_ERR_INVALID_ARG
+    nanv = scenes.identity_view(64, 48, 50.0, 0, 10)
+    nanv["t"] = np.array([0, math.nan, 0], np.float32)
+    with pytest.raises(B.GsError) as e:
+        ctx.workspace_bytes(B.make_views([nanv]), 1000)
+    assert e.value.code == B.GS_ERR_NONFINITE
+    with pytest.raises(B.GsError) as e:
+        B.Context(0, tile_size=12)
+    assert e.value.code == B.GS_ERR_INVALID_ARG
+
+
+def test_mixed_precision_storage_matches_oracle_on_dequantised(orc):
+    """FP16 opacity/SH and BF16 scale/rotation storage, FP32 arithmetic: the
+    error against the oracle on the dequantised values is compute error."""
+    n = 8000
+    p = scenes.box_room_scene(n, seed=14)
+    views = scenes.arc_views(2, 160, 128, 150.0, n_gaussians=n)
+    storage = dict(log_scales=torch.bfloat16, quats=torch.bfloat16, opacity=torch.float16, sh=torch.float16)
+    win, r = gpu_forward(p, views, storage=storage)
+    deq = win.numpy(use_render_copy=True)
+    for v, img, T in zip(views, r.images(), B.unpack_images(r.T, views, 1)):
+        compare_images(orc.render_view(deq, v), img.cpu().numpy(), T.cpu().numpy())
+    tg = l1_target(deq, views)
+    gpu_loss_backward(win, r, tg)
+    L, g, pose, border, _ = oracle_l1_backward(orc, deq, views, tg, r)
+    compare_grads(win, g, border, pose=r.dL_dpose.view(-1, 6).cpu().numpy().astype(np.float64), orc_pose=pose)
+
+
+def test_window_optimizer_step_reduces_loss():
+    n = 20_000
+    p = scenes.box_room_scene(n, seed=15)
+    views = scenes.arc_views(4, 160, 128, 150.0, n_gaussians=n)
+    q = scenes.perturbed_copy(p, seed=3)
+    _, rt = gpu_forward(q, views)
+    target = rt.rgb.clone()
+    opt = WindowOptimizer(p, views, target, lr=1e-3)
+    losses = [float(opt.step().item()) for _ in range(30)]
+    assert losses[-1] < losses[0]
