@@ -48,6 +48,14 @@
 
 #define ORC_PI 3.14159265358979323846
 
+/* Unit roundoff of binary32.  Depth order is decided on the camera depth
+ * R_CW[2] . p_W + t_CW[2] of binary32 inputs evaluated as a compensated dot
+ * product in binary32 arithmetic ("Dot2", Ogita, Rump and Oishi 2005), whose
+ * unevaluated result errs by at most gamma_4^2 sum |terms| with
+ * gamma_n = n u / (1 - n u).  Two contributors closer in depth than the sum
+ * of their bounds may be ordered either way. */
+#define U32 (1.0 / 16777216.0)
+
 /* Real spherical-harmonic normalisations: Y_00 = 1 / (2 sqrt(pi)),
  * |Y_1m| prefactor = sqrt(3) / (2 sqrt(pi)). */
 static double sh_c0(void) { return 0.5 / sqrt(ORC_PI); }
@@ -72,6 +80,7 @@ typedef struct {
     double M[9];      /* R S */
     double S3[9];     /* Sigma3 = M M^T */
     double pc[3];     /* camera-frame mean */
+    double zerr;      /* bound on the FP32 rounding error of pc[2] */
     double J[6];      /* 2x3 projection Jacobian */
     double T[6];      /* J W */
     double S2[3];     /* Sigma2 = T Sigma3 T^T + b I: (a, b, c) */
@@ -112,6 +121,10 @@ static void project_one(const double* mu, const double* ls, const double* quat, 
     /* Camera-frame mean p_C = R_CW p_W + t_CW (Eq. q). */
     for (int i = 0; i < 3; ++i)
         P->pc[i] = W[3 * i] * mu[0] + W[3 * i + 1] * mu[1] + W[3 * i + 2] * mu[2] + t[i];
+    {
+        double g4 = 4.0 * U32 / (1.0 - 4.0 * U32);
+        P->zerr = g4 * g4 * (fabs(W[6] * mu[0]) + fabs(W[7] * mu[1]) + fabs(W[8] * mu[2]) + fabs(t[2]));
+    }
     double x = P->pc[0], y = P->pc[1], z = P->pc[2];
     if (!(z > z_near)) { P->valid = 0; return; }
 
@@ -167,7 +180,8 @@ static void project_one(const double* mu, const double* ls, const double* quat, 
 int orc_project(long n, const double* means, const double* log_scales, const double* quats,
                 const double* opacity, const double* sh, int sh_degree, const double* cam,
                 const double* cfg, int* valid, double* pc, double* q, double* sigma2,
-                double* conic, double* opac, double* colour, double* raw_colour) {
+                double* conic, double* opac, double* colour, double* raw_colour,
+                double* depth_err) {
     int K = (sh_degree + 1) * (sh_degree + 1);
     for (long i = 0; i < n; ++i) {
         orc_proj P;
@@ -183,6 +197,7 @@ int orc_project(long n, const double* means, const double* log_scales, const dou
             raw_colour[3 * i + k] = P.raw[k];
         }
         opac[i] = P.sigma;
+        depth_err[i] = P.zerr;
     }
     return 0;
 }
@@ -217,10 +232,6 @@ static long depth_order(long n, const int* valid, const double* depth, long* ord
 typedef struct { long i; double alpha, araw, G, dx, dy, Tin; } orc_frag;
 
 #define REL_BORDER 1e-5
-/* Two contributors closer in depth than this (relative) may be ordered the
- * other way by an FP32 camera transform: its rounding error is a few ulp of
- * the largest term, a few 1e-7 relative for the scenes used here. */
-#define REL_DEPTH 2e-6
 
 /* Front-to-back compositing at pixel centre (px, py): fills `frags` with the
  * contributing fragments, returns their count; *Tout is the final
@@ -228,13 +239,13 @@ typedef struct { long i; double alpha, araw, G, dx, dy, Tin; } orc_frag;
  * REL_BORDER (relative) of its cut, so FP32 may decide it the other way. */
 static long composite_pixel(double px, double py, long m, const long* order, const double* q,
                             const double* conic, const double* opac, const double* depth,
-                            const double* cfg, orc_frag* frags, double* Tout, int* border,
-                            long* n_considered) {
+                            const double* zerr, const double* cfg, orc_frag* frags, double* Tout,
+                            int* border, long* n_considered) {
     double amin = cfg[0], amax = cfg[1], Tmin = cfg[2];
     double T = 1.0;
     long nf = 0;
     int bd = 0;
-    double zprev = -1.0;
+    double zprev = -1.0, eprev = 0.0;
     long k;
     for (k = 0; k < m; ++k) {
         long i = order[k];
@@ -247,8 +258,9 @@ static long composite_pixel(double px, double py, long m, const long* order, con
         if (amin > 0.0 && fabs(araw - amin) <= REL_BORDER * amin) bd = 1;
         if (fabs(araw - amax) <= REL_BORDER * amax) bd = 1;
         if (alpha < amin) continue;
-        if (zprev >= 0.0 && fabs(depth[i] - zprev) <= REL_DEPTH * depth[i]) bd = 1;
+        if (zprev >= 0.0 && fabs(depth[i] - zprev) <= zerr[i] + eprev) bd = 1;
         zprev = depth[i];
+        eprev = zerr[i];
         double Tnext = T * (1.0 - alpha);
         if (Tmin > 0.0 && fabs(Tnext - Tmin) <= REL_BORDER * Tmin) bd = 1;
         if (Tnext < Tmin) { ++k; break; }
@@ -266,7 +278,8 @@ static long composite_pixel(double px, double py, long m, const long* order, con
 /* Renders one view.  rgb is [3, H, W]; T_final, n_contrib and borderline are
  * [H, W].  n_contrib counts the contributing Gaussians. */
 int orc_render(int W, int H, long n, const int* valid, const double* q, const double* conic,
-               const double* opac, const double* colour, const double* depth, const double* cfg,
+               const double* opac, const double* colour, const double* depth,
+               const double* depth_err, const double* cfg,
                double* rgb, double* T_final, int* n_contrib, unsigned char* borderline,
                int n_threads) {
     long* order = (long*)malloc(sizeof(long) * (n > 0 ? n : 1));
@@ -285,7 +298,7 @@ int orc_render(int W, int H, long n, const int* valid, const double* q, const do
             for (int u = 0; u < W; ++u) {
                 double T;
                 int bd;
-                long nf = composite_pixel(u + 0.5, v + 0.5, m, order, q, conic, opac, depth, cfg,
+                long nf = composite_pixel(u + 0.5, v + 0.5, m, order, q, conic, opac, depth, depth_err, cfg,
                                           frags, &T, &bd, NULL);
                 double C[3] = {0.0, 0.0, 0.0};
                 for (long f = 0; f < nf; ++f) {
@@ -311,7 +324,8 @@ int orc_render(int W, int H, long n, const int* valid, const double* q, const do
  * per-pixel compositing as orc_render, for sampled checks of large images. */
 int orc_render_pixels(long n_pix, const int* px, const int* py, long n, const int* valid,
                       const double* q, const double* conic, const double* opac,
-                      const double* colour, const double* depth, const double* cfg, double* rgb,
+                      const double* colour, const double* depth, const double* depth_err,
+                      const double* cfg, double* rgb,
                       double* T_final, int* n_contrib, unsigned char* borderline, int n_threads) {
     long* order = (long*)malloc(sizeof(long) * (n > 0 ? n : 1));
     long m = depth_order(n, valid, depth, order);
@@ -328,7 +342,7 @@ int orc_render_pixels(long n_pix, const int* px, const int* py, long n, const in
         for (long k = 0; k < n_pix; ++k) {
             double T;
             int bd;
-            long nf = composite_pixel(px[k] + 0.5, py[k] + 0.5, m, order, q, conic, opac, depth, cfg,
+            long nf = composite_pixel(px[k] + 0.5, py[k] + 0.5, m, order, q, conic, opac, depth, depth_err, cfg,
                                       frags, &T, &bd, NULL);
             double C[3] = {0.0, 0.0, 0.0};
             for (long f = 0; f < nf; ++f) {
@@ -358,14 +372,15 @@ int orc_render_pixels(long n_pix, const int* px, const int* py, long n, const in
  * power = -1/2 (A dx^2 + 2 B dx dy + C dy^2), dx = px - q_x. */
 static void backward_pixel(double px, double py, const double* g, long m, const long* order,
                            const double* q, const double* conic, const double* opac,
-                           const double* colour, const double* depth, const double* cfg,
+                           const double* colour, const double* depth, const double* depth_err,
+                           const double* cfg,
                            orc_frag* frags, double* S, double* a, unsigned char* ba) {
     const double* bg = cfg + 5;
     double amax = cfg[1], amin = cfg[0];
     double T;
     int bd;
     long ncons;
-    long nf = composite_pixel(px, py, m, order, q, conic, opac, depth, cfg, frags, &T, &bd, &ncons);
+    long nf = composite_pixel(px, py, m, order, q, conic, opac, depth, depth_err, cfg, frags, &T, &bd, &ncons);
     if (bd) {
         /* Every Gaussian that could be active here is unreliable. */
         for (long k = 0; k < ncons && k < m; ++k) {
@@ -419,7 +434,8 @@ static void backward_pixel(double px, double py, const double* g, long m, const 
 static int render_backward_impl(int W, int H, long n_pix, const int* pxs, const int* pys, long n,
                                 const int* valid, const double* q, const double* conic,
                                 const double* opac, const double* colour, const double* depth,
-                                const double* cfg, const double* dL_drgb, double* g_q,
+                                const double* depth_err, const double* cfg, const double* dL_drgb,
+                                double* g_q,
                                 double* g_conic, double* g_opac, double* g_colour,
                                 unsigned char* g_border, int n_threads) {
     long* order = (long*)malloc(sizeof(long) * (n > 0 ? n : 1));
@@ -457,7 +473,8 @@ static int render_backward_impl(int W, int H, long n_pix, const int* pxs, const 
                 px = (double)(k % W) + 0.5; py = (double)(k / W) + 0.5;
                 for (int ch = 0; ch < 3; ++ch) g[ch] = dL_drgb[(long)ch * W * H + k];
             }
-            backward_pixel(px, py, g, m, order, q, conic, opac, colour, depth, cfg, frags, S, a, ba);
+            backward_pixel(px, py, g, m, order, q, conic, opac, colour, depth, depth_err, cfg, frags, S,
+                           a, ba);
         }
         free(S);
         free(frags);
@@ -481,20 +498,23 @@ static int render_backward_impl(int W, int H, long n_pix, const int* pxs, const 
 
 int orc_render_backward(int W, int H, long n, const int* valid, const double* q,
                         const double* conic, const double* opac, const double* colour,
-                        const double* depth, const double* cfg, const double* dL_drgb,
-                        double* g_q, double* g_conic, double* g_opac, double* g_colour,
-                        unsigned char* g_border, int n_threads) {
-    return render_backward_impl(W, H, 0, NULL, NULL, n, valid, q, conic, opac, colour, depth, cfg,
-                                dL_drgb, g_q, g_conic, g_opac, g_colour, g_border, n_threads);
+                        const double* depth, const double* depth_err, const double* cfg,
+                        const double* dL_drgb, double* g_q, double* g_conic, double* g_opac,
+                        double* g_colour, unsigned char* g_border, int n_threads) {
+    return render_backward_impl(W, H, 0, NULL, NULL, n, valid, q, conic, opac, colour, depth,
+                                depth_err, cfg, dL_drgb, g_q, g_conic, g_opac, g_colour, g_border,
+                                n_threads);
 }
 
 int orc_render_backward_pixels(long n_pix, const int* px, const int* py, long n, const int* valid,
                                const double* q, const double* conic, const double* opac,
-                               const double* colour, const double* depth, const double* cfg,
-                               const double* dL_drgb, double* g_q, double* g_conic, double* g_opac,
-                               double* g_colour, unsigned char* g_border, int n_threads) {
-    return render_backward_impl(0, 0, n_pix, px, py, n, valid, q, conic, opac, colour, depth, cfg,
-                                dL_drgb, g_q, g_conic, g_opac, g_colour, g_border, n_threads);
+                               const double* colour, const double* depth, const double* depth_err,
+                               const double* cfg, const double* dL_drgb, double* g_q,
+                               double* g_conic, double* g_opac, double* g_colour,
+                               unsigned char* g_border, int n_threads) {
+    return render_backward_impl(0, 0, n_pix, px, py, n, valid, q, conic, opac, colour, depth,
+                                depth_err, cfg, dL_drgb, g_q, g_conic, g_opac, g_colour, g_border,
+                                n_threads);
 }
 
 /* ---------- projection backward and pose gradient ---------- */

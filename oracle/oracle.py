@@ -49,12 +49,12 @@ def lib():
         build()
         L = ctypes.CDLL(_LIB)
         P = ctypes.c_void_p
-        L.orc_project.argtypes = [ctypes.c_long] + [P] * 5 + [ctypes.c_int] + [P] * 10
-        L.orc_render.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_long] + [P] * 11 + [ctypes.c_int]
-        L.orc_render_pixels.argtypes = ([ctypes.c_long, P, P, ctypes.c_long] + [P] * 11 + [ctypes.c_int])
-        L.orc_render_backward.argtypes = ([ctypes.c_int, ctypes.c_int, ctypes.c_long] + [P] * 13 +
+        L.orc_project.argtypes = [ctypes.c_long] + [P] * 5 + [ctypes.c_int] + [P] * 11
+        L.orc_render.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_long] + [P] * 12 + [ctypes.c_int]
+        L.orc_render_pixels.argtypes = ([ctypes.c_long, P, P, ctypes.c_long] + [P] * 12 + [ctypes.c_int])
+        L.orc_render_backward.argtypes = ([ctypes.c_int, ctypes.c_int, ctypes.c_long] + [P] * 14 +
                                           [ctypes.c_int])
-        L.orc_render_backward_pixels.argtypes = ([ctypes.c_long, P, P, ctypes.c_long] + [P] * 13 +
+        L.orc_render_backward_pixels.argtypes = ([ctypes.c_long, P, P, ctypes.c_long] + [P] * 14 +
                                                  [ctypes.c_int])
         L.orc_project_backward.argtypes = ([ctypes.c_long] + [P] * 5 + [ctypes.c_int] + [P] * 2 +
                                            [P] * 4 + [P] * 7)
@@ -105,11 +105,11 @@ def project(params, view, cfg=None):
     mu, ls, qt, op, sh = _params64(params, b, e)
     out = dict(valid=np.zeros(n, np.int32), pc=np.zeros((n, 3)), q=np.zeros((n, 2)),
                sigma2=np.zeros((n, 3)), conic=np.zeros((n, 3)), opac=np.zeros(n),
-               colour=np.zeros((n, 3)), raw_colour=np.zeros((n, 3)))
+               colour=np.zeros((n, 3)), raw_colour=np.zeros((n, 3)), depth_err=np.zeros(n))
     lib().orc_project(n, _p(mu), _p(ls), _p(qt), _p(op), _p(sh), int(params["sh_degree"]),
                       _p(cam_array(view)), _p(cfg_array(cfg)), _p(out["valid"]), _p(out["pc"]),
                       _p(out["q"]), _p(out["sigma2"]), _p(out["conic"]), _p(out["opac"]),
-                      _p(out["colour"]), _p(out["raw_colour"]))
+                      _p(out["colour"]), _p(out["raw_colour"]), _p(out["depth_err"]))
     out["depth"] = out["pc"][:, 2].copy()
     return out
 
@@ -125,7 +125,7 @@ def render_view(params, view, cfg=None, n_threads=0, proj=None):
     nc = np.zeros((H, W), np.int32)
     bd = np.zeros((H, W), np.uint8)
     lib().orc_render(W, H, n, _p(pr["valid"]), _p(pr["q"]), _p(pr["conic"]), _p(pr["opac"]),
-                     _p(pr["colour"]), _p(pr["depth"]), _p(cfg_array(cfg)), _p(rgb), _p(T), _p(nc),
+                     _p(pr["colour"]), _p(pr["depth"]), _p(pr["depth_err"]), _p(cfg_array(cfg)), _p(rgb), _p(T), _p(nc),
                      _p(bd), int(n_threads))
     return dict(rgb=rgb, T=T, n_contrib=nc, border=bd.astype(bool))
 
@@ -143,7 +143,7 @@ def render_pixels(params, view, px, py, cfg=None, n_threads=0, proj=None):
     nc = np.zeros(k, np.int32)
     bd = np.zeros(k, np.uint8)
     lib().orc_render_pixels(k, _p(px), _p(py), n, _p(pr["valid"]), _p(pr["q"]), _p(pr["conic"]),
-                            _p(pr["opac"]), _p(pr["colour"]), _p(pr["depth"]), _p(cfg_array(cfg)), _p(rgb),
+                            _p(pr["opac"]), _p(pr["colour"]), _p(pr["depth"]), _p(pr["depth_err"]), _p(cfg_array(cfg)), _p(rgb),
                             _p(T), _p(nc), _p(bd), int(n_threads))
     return dict(rgb=rgb, T=T, n_contrib=nc, border=bd.astype(bool))
 
@@ -191,14 +191,15 @@ def backward(params, views, dL_drgbs, cfg=None, n_threads=0, pixels=None):
         if pixels is None:
             W, H = int(view["W"]), int(view["H"])
             lib().orc_render_backward(W, H, n, _p(pr["valid"]), _p(pr["q"]), _p(pr["conic"]),
-                                      _p(pr["opac"]), _p(pr["colour"]), _p(pr["depth"]), _p(ca), _p(dl),
+                                      _p(pr["opac"]), _p(pr["colour"]), _p(pr["depth"]), _p(pr["depth_err"]), _p(ca), _p(dl),
                                       _p(gq), _p(gc), _p(go), _p(gcol), _p(gb), int(n_threads))
         else:
             px = np.ascontiguousarray(pixels[vi][0], np.int32)
             py = np.ascontiguousarray(pixels[vi][1], np.int32)
             lib().orc_render_backward_pixels(px.size, _p(px), _p(py), n, _p(pr["valid"]), _p(pr["q"]),
                                              _p(pr["conic"]), _p(pr["opac"]), _p(pr["colour"]),
-                                             _p(pr["depth"]), _p(ca), _p(dl), _p(gq), _p(gc), _p(go),
+                                             _p(pr["depth"]), _p(pr["depth_err"]), _p(ca), _p(dl), _p(gq),
+                                             _p(gc), _p(go),
                                              _p(gcol), _p(gb), int(n_threads))
         mu, ls, qt, op, sh = _params64(params, b, e)
         gm = np.zeros((n, 3)); gl = np.zeros((n, 3)); gqt = np.zeros((n, 4)); gop = np.zeros(n)

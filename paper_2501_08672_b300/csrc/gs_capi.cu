@@ -114,8 +114,8 @@ int sorted_buffer(int total_tiles) {
 
 struct Layout {
     gs_ws_layout pub;
-    size_t scan_part, dkeys1, dvals1, pkeys1, pvals1, hist, partials;
-    int radix_grid, scan_blocks;
+    size_t scan_part, dkeys1, dvals1, pkeys1, pvals1, hist, hist_part, partials;
+    int scan_blocks;
     long long max_g_end;
 };
 
@@ -157,11 +157,9 @@ int make_layout(gs_ctx* ctx, const gs_config& cfg, const gs_view* views, int n_v
     if (T >= 0x7FFFFFFFll) return fail(ctx, GS_ERR_INVALID_ARG, "too many tiles: %lld", T);
 
     const long long cap = max_pairs;
-    long long big = M > cap ? M : cap;
-    long long G = (big + 2047) / 2048;
-    if (G < 1) G = 1;
-    if (G > 592) G = 592;
-    L.radix_grid = (int)G;
+    const long long big = M > cap ? M : cap;
+    const long long radix_tiles = (big + 4095) / 4096;      // tiles of the radix sort passes
+    const long long hist_parts = (256 * radix_tiles + 4095) / 4096;
     L.scan_blocks = (int)((M + 4095) / 4096);
     L.max_g_end = max_g_end;
     const long long pose_blocks = (max_g_end + 255) / 256;
@@ -178,6 +176,7 @@ int make_layout(gs_ctx* ctx, const gs_config& cfg, const gs_view* views, int n_v
     W.tiles_touched = take(sizeof(uint32_t) * (size_t)M);
     W.depth_keys = take(sizeof(uint32_t) * (size_t)M);
     L.dkeys1 = take(sizeof(uint32_t) * (size_t)M);
+    W.depth_hi = take(sizeof(uint32_t) * (size_t)M);
     W.depth_vals = take(sizeof(uint32_t) * (size_t)M);
     L.dvals1 = take(sizeof(uint32_t) * (size_t)M);
     W.pair_offsets = take(sizeof(unsigned long long) * (size_t)M);
@@ -186,7 +185,8 @@ int make_layout(gs_ctx* ctx, const gs_config& cfg, const gs_view* views, int n_v
     L.pkeys1 = take(sizeof(uint32_t) * (size_t)cap);
     W.pair_vals = take(sizeof(uint32_t) * (size_t)cap);
     L.pvals1 = take(sizeof(uint32_t) * (size_t)cap);
-    L.hist = take(sizeof(uint32_t) * 256 * (size_t)G);
+    L.hist = take(sizeof(uint32_t) * 256 * (size_t)(radix_tiles > 0 ? radix_tiles : 1));
+    L.hist_part = take(sizeof(uint32_t) * (size_t)(hist_parts + 1));
     W.tile_ranges = take(sizeof(uint2) * (size_t)T);
     W.grad2d = take(sizeof(float) * kGrad2D * (size_t)M);
     W.counters = take(sizeof(unsigned long long) * 8);
@@ -220,6 +220,7 @@ WsPtrs ws_ptrs(const gs_workspace* ws, const Layout& L, int total_tiles) {
     p.dkeys[1] = reinterpret_cast<uint32_t*>(b + L.dkeys1);
     p.dvals[0] = reinterpret_cast<uint32_t*>(b + L.pub.depth_vals);
     p.dvals[1] = reinterpret_cast<uint32_t*>(b + L.dvals1);
+    p.dhi = reinterpret_cast<uint32_t*>(b + L.pub.depth_hi);
     p.offsets = reinterpret_cast<unsigned long long*>(b + L.pub.pair_offsets);
     p.scan_part = reinterpret_cast<unsigned long long*>(b + L.scan_part);
     p.pkeys[0] = reinterpret_cast<uint32_t*>(b + L.pub.pair_keys);
@@ -227,12 +228,12 @@ WsPtrs ws_ptrs(const gs_workspace* ws, const Layout& L, int total_tiles) {
     p.pvals[0] = reinterpret_cast<uint32_t*>(b + L.pub.pair_vals);
     p.pvals[1] = reinterpret_cast<uint32_t*>(b + L.pvals1);
     p.hist = reinterpret_cast<uint32_t*>(b + L.hist);
+    p.hist_part = reinterpret_cast<uint32_t*>(b + L.hist_part);
     p.ranges = reinterpret_cast<uint2*>(b + L.pub.tile_ranges);
     p.grad2d = reinterpret_cast<float*>(b + L.pub.grad2d);
     p.counters = reinterpret_cast<unsigned long long*>(b + L.pub.counters);
     p.partials = reinterpret_cast<float*>(b + L.partials);
     p.cap = ws->max_pairs;
-    p.radix_grid = L.radix_grid;
     p.scan_blocks = L.scan_blocks;
     p.sorted_buf = sorted_buffer(total_tiles);
     return p;

@@ -71,19 +71,20 @@ struct WsPtrs {
     float4* rec;             // [M][3]
     int4* rect;              // [M]
     uint32_t* tiles_touched; // [M]
-    uint32_t* dkeys[2];      // [M]
+    uint32_t* dkeys[2];      // [M] low depth-key words, then scratch
     uint32_t* dvals[2];      // [M]
+    uint32_t* dhi;           // [M] high depth-key words
     unsigned long long* offsets; // [M]
     unsigned long long* scan_part; // [scan blocks]
     uint32_t* pkeys[2];      // [cap]
     uint32_t* pvals[2];      // [cap]
-    uint32_t* hist;          // [256 * radix grid]
+    uint32_t* hist;          // [256 * radix tiles]
+    uint32_t* hist_part;     // [radix scan blocks]
     uint2* ranges;           // [T]
     float* grad2d;           // [M][9]
     unsigned long long* counters; // [8]
     float* partials;         // reduction scratch
     long long cap;
-    int radix_grid;
     int scan_blocks;
     int sorted_buf;          // which pvals buffer holds the sorted pairs
 };

@@ -28,11 +28,12 @@ struct Proj {
     float inv_qn;    // 1 / |quat|
     float R[9];
     float s[3];      // exp(log-scale)
-    float M[9];      // R S
-    float S3[6];     // Sigma3: xx, xy, xz, yy, yz, zz
+    float M[9];      // R S, so Sigma3 = M M^T
     float pc[3];
     float Tm[6];     // J W, row-major 2x3
+    float U[6];      // T M, row-major 2x3, so Sigma2 = U U^T + blur I
     float a, b, c;   // Sigma2 with blur
+    float det;
     float A, B, C;   // conic
     float sigma;
     float dir[3];
@@ -60,30 +61,22 @@ __device__ __forceinline__ void load_gaussian(const GaussPtrs& g, long long i, f
     for (int k = 0; k < 4; ++k) P.qh[k] = q[k] * P.inv_qn;
     quat_rot(P.qh, P.R);
     for (int k = 0; k < 3; ++k) P.s[k] = expf(load_as_float(g.log_scales, g.scale_dtype, 3 * i + k));
-    for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 3; ++b) P.M[3 * a + b] = P.R[3 * a + b] * P.s[b];
-    // Sigma3 = M M^T (symmetric, 6 entries)
-    const int ia[6] = {0, 0, 0, 1, 1, 2};
-    const int ib[6] = {0, 1, 2, 1, 2, 2};
 #pragma unroll
-    for (int e = 0; e < 6; ++e) {
-        const float* ra = P.M + 3 * ia[e];
-        const float* rb = P.M + 3 * ib[e];
-        P.S3[e] = ra[0] * rb[0] + ra[1] * rb[1] + ra[2] * rb[2];
-    }
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) P.M[3 * a + b] = P.R[3 * a + b] * P.s[b];
     ologit = load_as_float(g.opacity, g.opacity_dtype, i);
 }
 
-__device__ __forceinline__ float s3(const float* S, int a, int b) {
-    // symmetric 3x3 accessor over (xx, xy, xz, yy, yz, zz)
-    const int lut[9] = {0, 1, 2, 1, 3, 4, 2, 4, 5};
-    return S[lut[3 * a + b]];
-}
-
 // View-dependent part.  Returns false when culled (z <= z_near or a
-// degenerate Sigma2).
+// degenerate Sigma2).  Sigma2 is formed from U = J W R S as U U^T + blur I
+// (entries a and c are sums of squares) and its determinant by the
+// Cauchy-Binet sum of squared 2x2 minors of U plus the blur terms: every term
+// is non-negative, so the determinant keeps full FP32 relative accuracy even
+// for long thin footprints, where a c - b^2 would cancel.
 __device__ __forceinline__ bool project_view(const ViewParam& V, const RenderConst& rc,
                                              const float* mu, Proj& P) {
+#pragma unroll
     for (int r = 0; r < 3; ++r)
         P.pc[r] = V.R[3 * r] * mu[0] + V.R[3 * r + 1] * mu[1] + V.R[3 * r + 2] * mu[2] + V.t[r];
     const float x = P.pc[0], y = P.pc[1], z = P.pc[2];
@@ -91,22 +84,29 @@ __device__ __forceinline__ bool project_view(const ViewParam& V, const RenderCon
     const float iz = 1.f / z;
     const float j00 = V.fx * iz, j02 = -V.fx * x * iz * iz;
     const float j11 = V.fy * iz, j12 = -V.fy * y * iz * iz;
+#pragma unroll
     for (int c = 0; c < 3; ++c) {
         P.Tm[c] = j00 * V.R[c] + j02 * V.R[6 + c];
         P.Tm[3 + c] = j11 * V.R[3 + c] + j12 * V.R[6 + c];
     }
-    // Sigma2 = T Sigma3 T^T
-    float u0[3], u1[3];
-    for (int a = 0; a < 3; ++a) {
-        u0[a] = s3(P.S3, a, 0) * P.Tm[0] + s3(P.S3, a, 1) * P.Tm[1] + s3(P.S3, a, 2) * P.Tm[2];
-        u1[a] = s3(P.S3, a, 0) * P.Tm[3] + s3(P.S3, a, 1) * P.Tm[4] + s3(P.S3, a, 2) * P.Tm[5];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        P.U[k] = P.Tm[0] * P.M[k] + P.Tm[1] * P.M[3 + k] + P.Tm[2] * P.M[6 + k];
+        P.U[3 + k] = P.Tm[3] * P.M[k] + P.Tm[4] * P.M[3 + k] + P.Tm[5] * P.M[6 + k];
     }
-    P.a = P.Tm[0] * u0[0] + P.Tm[1] * u0[1] + P.Tm[2] * u0[2] + rc.blur;
-    P.b = P.Tm[3] * u0[0] + P.Tm[4] * u0[1] + P.Tm[5] * u0[2];
-    P.c = P.Tm[3] * u1[0] + P.Tm[4] * u1[1] + P.Tm[5] * u1[2] + rc.blur;
-    const float det = P.a * P.c - P.b * P.b;
-    if (!(det > 0.f)) return false;
-    const float idet = 1.f / det;
+    const float* u0 = P.U;
+    const float* u1 = P.U + 3;
+    const float a0 = u0[0] * u0[0] + u0[1] * u0[1] + u0[2] * u0[2];
+    const float c0 = u1[0] * u1[0] + u1[1] * u1[1] + u1[2] * u1[2];
+    P.a = a0 + rc.blur;
+    P.b = u0[0] * u1[0] + u0[1] * u1[1] + u0[2] * u1[2];
+    P.c = c0 + rc.blur;
+    const float m01 = fmaf(u0[0], u1[1], -u0[1] * u1[0]);
+    const float m02 = fmaf(u0[0], u1[2], -u0[2] * u1[0]);
+    const float m12 = fmaf(u0[1], u1[2], -u0[2] * u1[1]);
+    P.det = (m01 * m01 + m02 * m02 + m12 * m12) + rc.blur * (a0 + c0) + rc.blur * rc.blur;
+    if (!(P.det > 0.f) || !(P.det < 3.0e38f)) return false;
+    const float idet = 1.f / P.det;
     P.A = P.c * idet;
     P.B = -P.b * idet;
     P.C = P.a * idet;
@@ -133,6 +133,42 @@ __device__ __forceinline__ void view_colour(const ViewParam& V, const GaussPtrs&
     }
 }
 
+// Camera depth R_CW[2] . p_W + t_CW[2] as an unevaluated sum hi + lo of two
+// floats (the compensated dot product "Dot2" of Ogita, Rump and Oishi, 2005,
+// built from the error-free transformations TwoProduct (via fma) and TwoSum):
+// as accurate as a dot product evaluated in twice the FP32 precision.  The
+// 64-bit key (bits(hi) << 32 | ordered(lo)) orders records by this value, so
+// nearly coplanar Gaussians are ordered as in exact arithmetic.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+__device__ __forceinline__ void depth_dot2(const ViewParam& V, const float* mu, float& hi, float& lo) {
+    float p = V.R[6] * mu[0];
+    float s = fmaf(V.R[6], mu[0], -p);
+    float h, r, q;
+    h = V.R[7] * mu[1];
+    r = fmaf(V.R[7], mu[1], -h);
+    two_sum(p, h, p, q);
+    s = s + (q + r);
+    h = V.R[8] * mu[2];
+    r = fmaf(V.R[8], mu[2], -h);
+    two_sum(p, h, p, q);
+    s = s + (q + r);
+    two_sum(p, V.t[2], p, q);
+    s = s + q;
+    hi = p + s;                // renormalise (|s| is far below |p| here)
+    lo = s - (hi - p);
+    lo = lo + 0.0f;            // -0 -> +0 so equal values give equal keys
+}
+
+__device__ __forceinline__ uint32_t ordered_bits(float x) {
+    const uint32_t u = __float_as_uint(x);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
 __global__ void __launch_bounds__(256) k_project(const __grid_constant__ BatchParam bp, GaussPtrs g,
                                                  RenderConst rc, WsPtrs ws) {
     const ViewParam& V = bp.v[blockIdx.y];
@@ -145,7 +181,7 @@ __global__ void __launch_bounds__(256) k_project(const __grid_constant__ BatchPa
     float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0;
     int4 rect = make_int4(0, 0, V.tile_off, V.tiles_x);
     uint32_t touched = 0;
-    uint32_t key = 0xFFFFFFFFu;
+    uint32_t key_hi = 0xFFFFFFFFu, key_lo = 0xFFFFFFFFu;
 
     Proj P;
     float mu[3], ologit;
@@ -175,9 +211,22 @@ __global__ void __launch_bounds__(256) k_project(const __grid_constant__ BatchPa
             lo_y = fmaxf(ceilf(qy - ey - 0.5f), 0.f);
             hi_y = fminf(floorf(qy + ey - 0.5f), (float)(V.H - 1));
         }
-        r0 = make_float4(qx, qy, -0.5f * kLog2e * P.A, -kLog2e * P.B);
-        r1 = make_float4(-0.5f * kLog2e * P.C, log2f(sigma), col[0], col[1]);
-        r2 = make_float4(col[2], P.pc[2], 0.f, 0.f);
+        // Exponent in eigen form: log2(sigma G) = l - (d.v1)^2 - (d.v2)^2 with
+        // v_k = e_k sqrt(log2(e) / (2 lambda_k)); its FP32 error grows with the
+        // square root of the footprint's condition number instead of linearly
+        // as for A dx^2 + 2B dx dy + C dy^2.
+        const float hsum = 0.5f * (P.a + P.c);
+        const float hdif = 0.5f * (P.a - P.c);
+        const float l1 = hsum + sqrtf(hdif * hdif + P.b * P.b);
+        const float l2 = P.det / l1;
+        float ex0, ex1;  // major eigenvector
+        if (P.a >= P.c) { ex0 = l1 - P.c; ex1 = P.b; } else { ex0 = P.b; ex1 = l1 - P.a; }
+        const float en = sqrtf(ex0 * ex0 + ex1 * ex1);
+        if (en > 0.f) { ex0 /= en; ex1 /= en; } else { ex0 = 1.f; ex1 = 0.f; }
+        const float s1 = sqrtf(0.5f * kLog2e / l1), s2 = sqrtf(0.5f * kLog2e / l2);
+        r0 = make_float4(qx, qy, ex0 * s1, ex1 * s1);
+        r1 = make_float4(-ex1 * s2, ex0 * s2, log2f(sigma), col[0]);
+        r2 = make_float4(col[1], col[2], P.pc[2], 0.f);
         if (lo_x <= hi_x && lo_y <= hi_y) {
             const int ts = bp.tile_size;
             const int tx0 = (int)lo_x / ts, tx1 = (int)hi_x / ts + 1;
@@ -185,7 +234,10 @@ __global__ void __launch_bounds__(256) k_project(const __grid_constant__ BatchPa
             rect.x = tx0 | (ty0 << 16);
             rect.y = tx1 | (ty1 << 16);
             touched = (uint32_t)((tx1 - tx0) * (ty1 - ty0));
-            key = __float_as_uint(P.pc[2]);
+            float zhi, zlo;
+            depth_dot2(V, mu, zhi, zlo);
+            key_hi = ordered_bits(zhi);
+            key_lo = ordered_bits(zlo);
         }
     }
     ws.rec[3 * r + 0] = r0;
@@ -193,7 +245,8 @@ __global__ void __launch_bounds__(256) k_project(const __grid_constant__ BatchPa
     ws.rec[3 * r + 2] = r2;
     ws.rect[r] = rect;
     ws.tiles_touched[r] = touched;
-    ws.dkeys[0][r] = key;
+    ws.dkeys[0][r] = key_lo;
+    ws.dhi[r] = key_hi;
     ws.dvals[0][r] = (uint32_t)r;
 }
 
@@ -213,7 +266,7 @@ __global__ void __launch_bounds__(256) k_project_bwd(const __grid_constant__ Bat
     if (live) load_gaussian(g, i, mu, P, ologit);
 
     float gmu[3] = {0.f, 0.f, 0.f};
-    float gS3[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // dL/dSigma3 (symmetric, full-matrix gradient)
+    float gM[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // dL/d(R S)
     float gop = 0.f;
     float gsh[16 * 3];
     for (int e = 0; e < K * 3; ++e) gsh[e] = 0.f;
@@ -276,29 +329,24 @@ __global__ void __launch_bounds__(256) k_project_bwd(const __grid_constant__ Bat
             const float G00 = -(m00 * P.A + m01 * P.B);
             const float G01 = -(m00 * P.B + m01 * P.C);
             const float G11 = -(m10 * P.B + m11 * P.C);
-            // Sigma2 = T Sigma3 T^T: dL/dSigma3 += T^T G2 T ; dL/dT = 2 G2 T Sigma3
-            const float* T0 = P.Tm;
-            const float* T1 = P.Tm + 3;
-            {
-                const int ia[6] = {0, 0, 0, 1, 1, 2};
-                const int ib[6] = {0, 1, 2, 1, 2, 2};
+            // Sigma2 = U U^T + blur I with U = T M: dL/dU = 2 G2 U, dL/dT = dL/dU M^T,
+            // dL/dM += T^T dL/dU (accumulated over views).
+            float gU0[3], gU1[3];
 #pragma unroll
-                for (int e = 0; e < 6; ++e) {
-                    const int a = ia[e], b = ib[e];
-                    gS3[e] += G00 * T0[a] * T0[b] + G01 * (T0[a] * T1[b] + T1[a] * T0[b]) +
-                              G11 * T1[a] * T1[b];
-                }
-            }
-            float TS0[3], TS1[3];  // T Sigma3 rows
-            for (int b = 0; b < 3; ++b) {
-                TS0[b] = T0[0] * s3(P.S3, 0, b) + T0[1] * s3(P.S3, 1, b) + T0[2] * s3(P.S3, 2, b);
-                TS1[b] = T1[0] * s3(P.S3, 0, b) + T1[1] * s3(P.S3, 1, b) + T1[2] * s3(P.S3, 2, b);
+            for (int k = 0; k < 3; ++k) {
+                gU0[k] = 2.f * (G00 * P.U[k] + G01 * P.U[3 + k]);
+                gU1[k] = 2.f * (G01 * P.U[k] + G11 * P.U[3 + k]);
             }
             float gT0[3], gT1[3];
-            for (int b = 0; b < 3; ++b) {
-                gT0[b] = 2.f * (G00 * TS0[b] + G01 * TS1[b]);
-                gT1[b] = 2.f * (G01 * TS0[b] + G11 * TS1[b]);
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                gT0[j] = gU0[0] * P.M[3 * j] + gU0[1] * P.M[3 * j + 1] + gU0[2] * P.M[3 * j + 2];
+                gT1[j] = gU1[0] * P.M[3 * j] + gU1[1] * P.M[3 * j + 1] + gU1[2] * P.M[3 * j + 2];
             }
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+#pragma unroll
+                for (int k = 0; k < 3; ++k) gM[3 * j + k] += P.Tm[j] * gU0[k] + P.Tm[3 + j] * gU1[k];
             // T = J W: dL/dJ = dL/dT W^T (only J00, J02, J11, J12 are non-zero)
             const float gJ00 = gT0[0] * V.R[0] + gT0[1] * V.R[1] + gT0[2] * V.R[2];
             const float gJ02 = gT0[0] * V.R[6] + gT0[1] * V.R[7] + gT0[2] * V.R[8];
@@ -359,17 +407,6 @@ __global__ void __launch_bounds__(256) k_project_bwd(const __grid_constant__ Bat
     }
 
     if (!live || !want_params) return;
-    // Sigma3 = M M^T with G3 = dL/dSigma3 as a full symmetric matrix
-    // (gS3 holds its upper triangle): dL/dM = 2 G3 M.
-    float G3[9];
-    G3[0] = gS3[0]; G3[4] = gS3[3]; G3[8] = gS3[5];
-    G3[1] = G3[3] = gS3[1];
-    G3[2] = G3[6] = gS3[2];
-    G3[5] = G3[7] = gS3[4];
-    float gM[9];
-    for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 3; ++b)
-            gM[3 * a + b] = 2.f * (G3[3 * a] * P.M[b] + G3[3 * a + 1] * P.M[3 + b] + G3[3 * a + 2] * P.M[6 + b]);
     float gR[9];
     for (int a = 0; a < 3; ++a)
         for (int b = 0; b < 3; ++b) gR[3 * a + b] = gM[3 * a + b] * P.s[b];

@@ -1,17 +1,20 @@
 // Per-tile compositing (Eq. raster), its backward pass, and the L1
 // photometric loss (Eq. gaussian_optimization).
 //
-// One CTA per screen tile of TS x TS pixels, one pixel per thread.  The
+// One CTA per screen tile of TS x TS pixels, PPT pixels per thread.  The
 // tile's depth-sorted Gaussian list is staged through shared memory in
-// batches of TS*TS records (every thread loads one record, every thread
-// reads all of them: broadcast reads, no bank conflicts).
+// batches of 256 records (every thread reads all of them: broadcast reads,
+// no bank conflicts).
 //
-// The fragment test is done in the log2 domain: with the record holding
-// A' = -A/2 log2(e), B' = -B log2(e), C' = -C/2 log2(e) and l = log2(sigma),
-//   p = A' dx^2 + B' dx dy + C' dy^2 + l  =  log2(sigma G(x)),
+// The fragment test is done in the log2 domain: with the record holding the
+// scaled principal axes v1, v2 of the footprint (v_k = e_k sqrt(log2(e) /
+// (2 lambda_k)), e_k, lambda_k the eigenpairs of Sigma2) and l = log2(sigma),
+//   p = l - (d.v1)^2 - (d.v2)^2  =  log2(sigma G(x)),   d = x - q,
 // so alpha_raw = 2^p (one ex2) and alpha < alpha_min is p < log2(alpha_min).
-// Forward and backward evaluate p and alpha with the same function, so both
-// passes make identical decisions.
+// Record layout (3 x float4): (qx, qy, v1x, v1y), (v2x, v2y, l, r), (g, b,
+// depth, 0).
+// Forward and backward evaluate p and alpha with the same operations in the
+// same order, so both passes make identical decisions.
 //
 // Unit of work: the visited fragment (pixel, Gaussian) pair.  These kernels
 // are bound by FP32/MUFU issue, not by HBM.
@@ -21,81 +24,108 @@ namespace gsb {
 
 namespace {
 
-__device__ __forceinline__ float frag_log2_alpha(const float4 a, const float4 b, float fx, float fy,
-                                                 float& dx, float& dy) {
-    dx = fx - a.x;
-    dy = fy - a.y;
-    return fmaf(fmaf(a.z, dx, a.w * dy), dx, fmaf(b.x * dy, dy, b.y));
-}
+// Thread layout: a TS x TS tile is covered by TS*TS/PPT threads; thread t
+// owns column t % TS and the PPT consecutive rows starting at (t / TS) * PPT,
+// so a warp covers a compact block of rows.  Records are staged kBatch at a
+// time (each thread loads kBatch / threads of them).
+constexpr int kBatch = 256;
 
-template <int TS>
-__global__ void __launch_bounds__(TS * TS) k_render_fwd(const __grid_constant__ BatchParam bp,
-                                                        RenderConst rc,
-                                                        const float4* __restrict__ rec,
-                                                        const uint2* __restrict__ ranges,
-                                                        const uint32_t* __restrict__ svals,
-                                                        float* __restrict__ rgb,
-                                                        float* __restrict__ T_final,
-                                                        uint32_t* __restrict__ n_contrib) {
-    constexpr int NT = TS * TS;
-    __shared__ float4 s_a[NT];
-    __shared__ float4 s_b[NT];
-    __shared__ float s_c[NT];
+template <int TS, int PPT>
+__global__ void __launch_bounds__(TS * TS / PPT) k_render_fwd(const __grid_constant__ BatchParam bp,
+                                                              RenderConst rc,
+                                                              const float4* __restrict__ rec,
+                                                              const uint2* __restrict__ ranges,
+                                                              const uint32_t* __restrict__ svals,
+                                                              float* __restrict__ rgb,
+                                                              float* __restrict__ T_final,
+                                                              uint32_t* __restrict__ n_contrib) {
+    constexpr int NT = TS * TS / PPT;
+    __shared__ float4 s_a[kBatch];
+    __shared__ float4 s_b[kBatch];
+    __shared__ float2 s_c[kBatch];
     const int t = threadIdx.x;
     const int tile = blockIdx.x;
     const ViewParam& V = bp.v[find_view_by_tile(bp, tile)];
     const int lt = tile - V.tile_off;
     const int ty = lt / V.tiles_x, tx = lt - ty * V.tiles_x;
-    const int px = tx * TS + (t % TS), py = ty * TS + (t / TS);
-    const bool inside = px < V.W && py < V.H;
-    const float fx = px + 0.5f, fy = py + 0.5f;
+    const int px = tx * TS + (t % TS);
+    const int py0 = ty * TS + (t / TS) * PPT;
+    const float fx = px + 0.5f;
+    float fy[PPT], T[PPT], C0[PPT], C1[PPT], C2[PPT];
+    uint32_t last[PPT];
+    bool done[PPT];
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        fy[k] = py0 + k + 0.5f;
+        T[k] = 1.f;
+        C0[k] = C1[k] = C2[k] = 0.f;
+        last[k] = 0;
+        done[k] = !(px < V.W && py0 + k < V.H);
+    }
     const uint2 rg = ranges[tile];
 
-    float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
-    uint32_t last = 0;
-    bool done = !inside;
-    for (uint32_t start = rg.x; start < rg.y; start += NT) {
-        if (__syncthreads_count(done) == NT) break;
-        const uint32_t idx = start + t;
-        if (idx < rg.y) {
-            const uint32_t r = svals[idx];
-            s_a[t] = rec[3 * r];
-            s_b[t] = rec[3 * r + 1];
-            s_c[t] = rec[3 * r + 2].x;
+    for (uint32_t start = rg.x; start < rg.y; start += kBatch) {
+        bool all = true;
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) all = all && done[k];
+        if (__syncthreads_count(all) == NT) break;
+#pragma unroll
+        for (int q = 0; q < kBatch / NT; ++q) {
+            const int slot = q * NT + t;
+            const uint32_t idx = start + slot;
+            if (idx < rg.y) {
+                const uint32_t r = svals[idx];
+                s_a[slot] = rec[3 * r];
+                s_b[slot] = rec[3 * r + 1];
+                const float4 c = rec[3 * r + 2];
+                s_c[slot] = make_float2(c.x, c.y);
+            }
         }
         __syncthreads();
-        const int cnt = min((uint32_t)NT, rg.y - start);
-        if (!done) {
+        if (!all) {
+            const int cnt = min((uint32_t)kBatch, rg.y - start);
             for (int j = 0; j < cnt; ++j) {
                 const float4 a = s_a[j];
                 const float4 b = s_b[j];
-                float dx, dy;
-                const float p = frag_log2_alpha(a, b, fx, fy, dx, dy);
-                if (p < rc.log2_alpha_min) continue;
-                const float alpha = fminf(rc.alpha_max, ex2_approx(p));
-                const float Tn = T * (1.f - alpha);
-                if (Tn < rc.T_min) {
-                    done = true;
-                    break;
+                const float2 c = s_c[j];
+                const float dx = fx - a.x;
+                const float u1 = dx * a.z, u2 = dx * b.x;
+#pragma unroll
+                for (int k = 0; k < PPT; ++k) {
+                    if (done[k]) continue;
+                    const float dy = fy[k] - a.y;
+                    const float t1 = fmaf(dy, a.w, u1);
+                    const float t2 = fmaf(dy, b.y, u2);
+                    const float p = fmaf(-t1, t1, fmaf(-t2, t2, b.z));
+                    if (p < rc.log2_alpha_min) continue;
+                    const float alpha = fminf(rc.alpha_max, ex2_approx(p));
+                    const float Tn = T[k] * (1.f - alpha);
+                    if (Tn < rc.T_min) {
+                        done[k] = true;
+                        continue;
+                    }
+                    const float w = alpha * T[k];
+                    C0[k] = fmaf(b.w, w, C0[k]);
+                    C1[k] = fmaf(c.x, w, C1[k]);
+                    C2[k] = fmaf(c.y, w, C2[k]);
+                    T[k] = Tn;
+                    last[k] = start - rg.x + j + 1;
                 }
-                const float w = alpha * T;
-                C0 = fmaf(b.z, w, C0);
-                C1 = fmaf(b.w, w, C1);
-                C2 = fmaf(s_c[j], w, C2);
-                T = Tn;
-                last = start - rg.x + j + 1;
             }
         }
     }
-    if (inside) {
-        const long long hw = (long long)V.W * V.H;
-        const long long pl = (long long)py * V.W + px;
-        float* out = rgb + 3 * V.pix_off;
-        out[pl] = C0 + T * rc.bg[0];
-        out[hw + pl] = C1 + T * rc.bg[1];
-        out[2 * hw + pl] = C2 + T * rc.bg[2];
-        T_final[V.pix_off + pl] = T;
-        n_contrib[V.pix_off + pl] = last;
+    const long long hw = (long long)V.W * V.H;
+    float* out = rgb + 3 * V.pix_off;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        if (px < V.W && py0 + k < V.H) {
+            const long long pl = (long long)(py0 + k) * V.W + px;
+            out[pl] = C0[k] + T[k] * rc.bg[0];
+            out[hw + pl] = C1[k] + T[k] * rc.bg[1];
+            out[2 * hw + pl] = C2[k] + T[k] * rc.bg[2];
+            T_final[V.pix_off + pl] = T[k];
+            n_contrib[V.pix_off + pl] = last[k];
+        }
     }
 }
 
@@ -104,25 +134,26 @@ __global__ void __launch_bounds__(TS * TS) k_render_fwd(const __grid_constant__ 
 // fragment j and R the light composited behind it (normalised by T),
 //   T_j = T_{j+1} / (1 - alpha_j),   dL/dc_j = alpha_j T_j g,
 //   dL/dalpha_j = T_j g . (c_j - R_j),  R_{j-1} = R_j + alpha_j (c_j - R_j),
-// with R = bg behind the last contributor.  Per-record accumulators (9
-// floats, see grad2d in gs.h) are reduced over the warp and added with one
-// atomic per warp and component; the factor ln 2 and the conversion to the
-// natural conic happen in the projection backward.
-template <int TS>
-__global__ void __launch_bounds__(TS * TS) k_render_bwd(const __grid_constant__ BatchParam bp,
-                                                        RenderConst rc,
-                                                        const float4* __restrict__ rec,
-                                                        const uint2* __restrict__ ranges,
-                                                        const uint32_t* __restrict__ svals,
-                                                        const float* __restrict__ T_final,
-                                                        const uint32_t* __restrict__ n_contrib,
-                                                        const float* __restrict__ dL_drgb,
-                                                        float* __restrict__ grad2d) {
-    constexpr int NT = TS * TS;
-    __shared__ float4 s_a[NT];
-    __shared__ float4 s_b[NT];
-    __shared__ float s_c[NT];
-    __shared__ uint32_t s_r[NT];
+// with R = bg behind the last contributor.  A thread sums its PPT pixels'
+// contributions to the 9 per-record accumulators (see grad2d in gs.h), the
+// warp reduces them, and lane 0 adds them with one atomic per component;
+// the factor ln 2 and the conversion to the natural conic happen in the
+// projection backward.
+template <int TS, int PPT>
+__global__ void __launch_bounds__(TS * TS / PPT) k_render_bwd(const __grid_constant__ BatchParam bp,
+                                                              RenderConst rc,
+                                                              const float4* __restrict__ rec,
+                                                              const uint2* __restrict__ ranges,
+                                                              const uint32_t* __restrict__ svals,
+                                                              const float* __restrict__ T_final,
+                                                              const uint32_t* __restrict__ n_contrib,
+                                                              const float* __restrict__ dL_drgb,
+                                                              float* __restrict__ grad2d) {
+    constexpr int NT = TS * TS / PPT;
+    __shared__ float4 s_a[kBatch];
+    __shared__ float4 s_b[kBatch];
+    __shared__ float2 s_c[kBatch];
+    __shared__ uint32_t s_r[kBatch];
     __shared__ uint32_t s_maxnc;
     const int t = threadIdx.x;
     const int lane = t & 31;
@@ -130,90 +161,117 @@ __global__ void __launch_bounds__(TS * TS) k_render_bwd(const __grid_constant__ 
     const ViewParam& V = bp.v[find_view_by_tile(bp, tile)];
     const int lt = tile - V.tile_off;
     const int ty = lt / V.tiles_x, tx = lt - ty * V.tiles_x;
-    const int px = tx * TS + (t % TS), py = ty * TS + (t / TS);
-    const bool inside = px < V.W && py < V.H;
-    const float fx = px + 0.5f, fy = py + 0.5f;
+    const int px = tx * TS + (t % TS);
+    const int py0 = ty * TS + (t / TS) * PPT;
+    const float fx = px + 0.5f;
     const uint2 rg = ranges[tile];
-
     const long long hw = (long long)V.W * V.H;
-    const long long pl = (long long)py * V.W + px;
-    float T = 1.f, g0 = 0.f, g1 = 0.f, g2 = 0.f;
-    uint32_t nc = 0;
-    if (inside) {
-        T = T_final[V.pix_off + pl];
-        nc = n_contrib[V.pix_off + pl];
-        const float* gp = dL_drgb + 3 * V.pix_off;
-        g0 = gp[pl];
-        g1 = gp[hw + pl];
-        g2 = gp[2 * hw + pl];
+    const float* gimg = dL_drgb + 3 * V.pix_off;
+
+    float fy[PPT], T[PPT], g0[PPT], g1[PPT], g2[PPT], R0[PPT], R1[PPT], R2[PPT];
+    int nc[PPT];
+    uint32_t mine = 0;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        fy[k] = py0 + k + 0.5f;
+        T[k] = 1.f;
+        g0[k] = g1[k] = g2[k] = 0.f;
+        nc[k] = 0;
+        if (px < V.W && py0 + k < V.H) {
+            const long long pl = (long long)(py0 + k) * V.W + px;
+            T[k] = T_final[V.pix_off + pl];
+            nc[k] = (int)n_contrib[V.pix_off + pl];
+            g0[k] = gimg[pl];
+            g1[k] = gimg[hw + pl];
+            g2[k] = gimg[2 * hw + pl];
+        }
+        R0[k] = rc.bg[0];
+        R1[k] = rc.bg[1];
+        R2[k] = rc.bg[2];
+        mine = max(mine, (uint32_t)nc[k]);
     }
-    float R0 = rc.bg[0], R1 = rc.bg[1], R2 = rc.bg[2];
     if (t == 0) s_maxnc = 0;
     __syncthreads();
-    if (nc) atomicMax(&s_maxnc, nc);
+    if (mine) atomicMax(&s_maxnc, mine);
     __syncthreads();
     // n_contrib never exceeds the tile's list length when it comes from the
-    // forward pass over the same bins; clamp so other inputs cannot read
-    // past the list.
+    // forward pass over the same bins; clamp so other inputs cannot read past
+    // the list.
     const int maxnc = min((int)s_maxnc, (int)(rg.y - rg.x));
 
-    for (int hi = maxnc; hi > 0; hi -= NT) {
-        const int lo = hi - NT > 0 ? hi - NT : 0;
+    for (int hi = maxnc; hi > 0; hi -= kBatch) {
+        const int lo = hi - kBatch > 0 ? hi - kBatch : 0;
         const int cnt = hi - lo;
         __syncthreads();
-        if (t < cnt) {
-            const uint32_t r = svals[rg.x + hi - 1 - t];
-            s_r[t] = r;
-            s_a[t] = rec[3 * r];
-            s_b[t] = rec[3 * r + 1];
-            s_c[t] = rec[3 * r + 2].x;
+#pragma unroll
+        for (int q = 0; q < kBatch / NT; ++q) {
+            const int slot = q * NT + t;
+            if (slot < cnt) {
+                const uint32_t r = svals[rg.x + hi - 1 - slot];
+                s_r[slot] = r;
+                s_a[slot] = rec[3 * r];
+                s_b[slot] = rec[3 * r + 1];
+                const float4 c = rec[3 * r + 2];
+                s_c[slot] = make_float2(c.x, c.y);
+            }
         }
         __syncthreads();
         for (int j = 0; j < cnt; ++j) {
             const int rel = hi - 1 - j;
             const float4 a = s_a[j];
             const float4 b = s_b[j];
-            float dx, dy;
-            const float p = frag_log2_alpha(a, b, fx, fy, dx, dy);
-            const bool act = rel < (int)nc && p >= rc.log2_alpha_min;
+            const float2 c = s_c[j];
+            const float dx = fx - a.x;
+            const float u1 = dx * a.z, u2 = dx * b.x;
             float v[kGrad2D];
 #pragma unroll
-            for (int k = 0; k < kGrad2D; ++k) v[k] = 0.f;
-            if (act) {
+            for (int e = 0; e < kGrad2D; ++e) v[e] = 0.f;
+            bool any = false;
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) {
+                if (rel >= nc[k]) continue;
+                const float dy = fy[k] - a.y;
+                const float t1 = fmaf(dy, a.w, u1);
+                const float t2 = fmaf(dy, b.y, u2);
+                const float p = fmaf(-t1, t1, fmaf(-t2, t2, b.z));
+                if (p < rc.log2_alpha_min) continue;
+                any = true;
                 const float araw = ex2_approx(p);
                 const float alpha = fminf(rc.alpha_max, araw);
-                T = __fdividef(T, 1.f - alpha);
-                const float w = alpha * T;
-                const float c2 = s_c[j];
-                v[6] = w * g0;
-                v[7] = w * g1;
-                v[8] = w * g2;
-                const float d0 = b.z - R0, d1 = b.w - R1, d2 = c2 - R2;
-                const float dalpha = T * (g0 * d0 + g1 * d1 + g2 * d2);
-                R0 = fmaf(alpha, d0, R0);
-                R1 = fmaf(alpha, d1, R1);
-                R2 = fmaf(alpha, d2, R2);
+                T[k] = __fdividef(T[k], 1.f - alpha);
+                const float w = alpha * T[k];
+                v[6] = fmaf(w, g0[k], v[6]);
+                v[7] = fmaf(w, g1[k], v[7]);
+                v[8] = fmaf(w, g2[k], v[8]);
+                const float d0 = b.w - R0[k], d1 = c.x - R1[k], d2 = c.y - R2[k];
+                const float dalpha = T[k] * (g0[k] * d0 + g1[k] * d1 + g2[k] * d2);
+                R0[k] = fmaf(alpha, d0, R0[k]);
+                R1[k] = fmaf(alpha, d1, R1[k]);
+                R2[k] = fmaf(alpha, d2, R2[k]);
                 const float ga = araw < rc.alpha_max ? dalpha * araw : 0.f;
-                v[0] = -ga * fmaf(2.f * a.z, dx, a.w * dy);
-                v[1] = -ga * fmaf(a.w, dx, 2.f * b.x * dy);
+                // dp/dq = 2 ((d.v1) v1 + (d.v2) v2)
+                const float gg = 2.f * ga;
+                v[0] = fmaf(gg, fmaf(t1, a.z, t2 * b.x), v[0]);
+                v[1] = fmaf(gg, fmaf(t1, a.w, t2 * b.y), v[1]);
                 const float gdx = ga * dx;
-                v[2] = gdx * dx;
-                v[3] = gdx * dy;
-                v[4] = ga * dy * dy;
-                v[5] = ga;
+                v[2] = fmaf(gdx, dx, v[2]);
+                v[3] = fmaf(gdx, dy, v[3]);
+                v[4] = fmaf(ga * dy, dy, v[4]);
+                v[5] += ga;
             }
-            if (__any_sync(0xffffffffu, act)) {
+            if (__any_sync(0xffffffffu, any)) {
 #pragma unroll
-                for (int k = 0; k < kGrad2D; ++k) {
-                    float x = v[k];
+                for (int e = 0; e < kGrad2D; ++e) {
+                    float x = v[e];
+#pragma unroll
                     for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-                    v[k] = x;
+                    v[e] = x;
                 }
                 if (lane == 0) {
                     float* dst = grad2d + (size_t)s_r[j] * kGrad2D;
 #pragma unroll
-                    for (int k = 0; k < kGrad2D; ++k)
-                        if (v[k] != 0.f) atomicAdd(dst + k, v[k]);
+                    for (int e = 0; e < kGrad2D; ++e)
+                        if (v[e] != 0.f) atomicAdd(dst + e, v[e]);
                 }
             }
         }
@@ -279,13 +337,13 @@ cudaError_t launch_render_fwd(const BatchParam& bp, const RenderConst& rc, const
     const int pi = pf.begin(GS_KF_RASTER_FWD, s);
     switch (bp.tile_size) {
         case 8:
-            k_render_fwd<8><<<bp.total_tiles, 64, 0, s>>>(bp, rc, ws.rec, ws.ranges, svals, rgb, T_final, n_contrib);
+            k_render_fwd<8, 2><<<bp.total_tiles, 32, 0, s>>>(bp, rc, ws.rec, ws.ranges, svals, rgb, T_final, n_contrib);
             break;
         case 16:
-            k_render_fwd<16><<<bp.total_tiles, 256, 0, s>>>(bp, rc, ws.rec, ws.ranges, svals, rgb, T_final, n_contrib);
+            k_render_fwd<16, 4><<<bp.total_tiles, 64, 0, s>>>(bp, rc, ws.rec, ws.ranges, svals, rgb, T_final, n_contrib);
             break;
         case 32:
-            k_render_fwd<32><<<bp.total_tiles, 1024, 0, s>>>(bp, rc, ws.rec, ws.ranges, svals, rgb, T_final, n_contrib);
+            k_render_fwd<32, 4><<<bp.total_tiles, 256, 0, s>>>(bp, rc, ws.rec, ws.ranges, svals, rgb, T_final, n_contrib);
             break;
         default:
             return cudaErrorInvalidValue;
@@ -304,13 +362,13 @@ cudaError_t launch_render_bwd(const BatchParam& bp, const RenderConst& rc, const
     const int pi = pf.begin(GS_KF_RASTER_BWD, s);
     switch (bp.tile_size) {
         case 8:
-            k_render_bwd<8><<<bp.total_tiles, 64, 0, s>>>(bp, rc, ws.rec, ws.ranges, svals, T_final, n_contrib, dL_drgb, ws.grad2d);
+            k_render_bwd<8, 2><<<bp.total_tiles, 32, 0, s>>>(bp, rc, ws.rec, ws.ranges, svals, T_final, n_contrib, dL_drgb, ws.grad2d);
             break;
         case 16:
-            k_render_bwd<16><<<bp.total_tiles, 256, 0, s>>>(bp, rc, ws.rec, ws.ranges, svals, T_final, n_contrib, dL_drgb, ws.grad2d);
+            k_render_bwd<16, 4><<<bp.total_tiles, 64, 0, s>>>(bp, rc, ws.rec, ws.ranges, svals, T_final, n_contrib, dL_drgb, ws.grad2d);
             break;
         case 32:
-            k_render_bwd<32><<<bp.total_tiles, 1024, 0, s>>>(bp, rc, ws.rec, ws.ranges, svals, T_final, n_contrib, dL_drgb, ws.grad2d);
+            k_render_bwd<32, 4><<<bp.total_tiles, 256, 0, s>>>(bp, rc, ws.rec, ws.ranges, svals, T_final, n_contrib, dL_drgb, ws.grad2d);
             break;
         default:
             return cudaErrorInvalidValue;

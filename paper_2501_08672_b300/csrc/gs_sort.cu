@@ -31,110 +31,237 @@ __device__ __forceinline__ unsigned long long clamp_n(unsigned long long n_host,
     return d < n_host ? d : n_host;
 }
 
-__device__ __forceinline__ void chunk_of(unsigned long long n, int G, int b, unsigned long long& begin,
-                                         unsigned long long& end) {
-    unsigned long long per = (n + G - 1) / G;
-    per = (per + kRadixThreads - 1) / kRadixThreads * kRadixThreads;
-    begin = per * b;
-    end = begin + per;
-    if (begin > n) begin = n;
-    if (end > n) end = n;
+// ---- LSD radix sort pass --------------------------------------------------
+//
+// One pass sorts on `bits` (<= 8) bits starting at `shift`.  The keys are cut
+// into tiles of kRTile = 4096 consecutive keys, one tile per block:
+//   upsweep:   per-tile digit histogram -> hist[digit * nblk + tile]
+//   scan:      device-wide exclusive scan of hist (digit-major), so the entry
+//              is the first output position of that digit from that tile
+//   downsweep: the tile ranks its keys stably (16 rounds of 256 keys; within
+//              a round, match.any ranks lanes of a warp and per-warp counts
+//              order the warps), stages them digit-sorted in shared memory,
+//              and writes each digit run to consecutive global positions.
+// The key count may live in device memory (n_dev), so the grid is sized by
+// the capacity and tiles past the count do nothing.
+
+constexpr int kRItems = 16;
+constexpr int kRTile = kRadixThreads * kRItems;
+
+__device__ __forceinline__ uint32_t lane_lt_mask() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
 }
 
-// Per-block digit histogram: hist[digit * G + block].
-__global__ void __launch_bounds__(kRadixThreads) k_radix_hist(const uint32_t* __restrict__ keys,
-                                                              unsigned long long n_host,
-                                                              const unsigned long long* n_dev,
-                                                              int shift, int bits,
-                                                              uint32_t* __restrict__ hist) {
-    __shared__ uint32_t h[256];
-    const int t = threadIdx.x, G = gridDim.x, b = blockIdx.x;
-    h[t] = 0;
+__global__ void __launch_bounds__(kRadixThreads) k_radix_upsweep(const uint32_t* __restrict__ keys,
+                                                                 unsigned long long n_host,
+                                                                 const unsigned long long* n_dev,
+                                                                 int shift, int bits,
+                                                                 uint32_t* __restrict__ hist) {
+    __shared__ uint32_t wh[kRadixWarps][256];
+    const int t = threadIdx.x, w = t >> 5;
+#pragma unroll
+    for (int k = 0; k < kRadixWarps; ++k) wh[k][t] = 0u;
     __syncthreads();
     const unsigned long long n = clamp_n(n_host, n_dev);
-    unsigned long long begin, end;
-    chunk_of(n, G, b, begin, end);
+    const unsigned long long base = (unsigned long long)blockIdx.x * kRTile;
     const uint32_t mask = (1u << bits) - 1u;
-    for (unsigned long long i = begin + t; i < end; i += kRadixThreads)
-        atomicAdd(&h[(keys[i] >> shift) & mask], 1u);
-    __syncthreads();
-    hist[(size_t)t * G + b] = h[t];
-}
-
-// Exclusive scan of the digit-major histogram (256 x G entries), one block.
-__global__ void __launch_bounds__(1024) k_radix_scan(uint32_t* hist, int total) {
-    __shared__ uint32_t s[1024];
-    const int t = threadIdx.x;
-    const int per = (total + 1023) / 1024;
-    const int b0 = t * per;
-    uint32_t sum = 0;
-    for (int k = 0; k < per; ++k)
-        if (b0 + k < total) sum += hist[b0 + k];
-    s[t] = sum;
-    __syncthreads();
-    for (int o = 1; o < 1024; o <<= 1) {
-        uint32_t v = t >= o ? s[t - o] : 0u;
-        __syncthreads();
-        s[t] += v;
-        __syncthreads();
+    const uint32_t lt = lane_lt_mask();
+#pragma unroll 4
+    for (int k = 0; k < kRItems; ++k) {
+        const unsigned long long i = base + (unsigned long long)k * kRadixThreads + t;
+        const bool valid = i < n;
+        const uint32_t d = valid ? ((keys[i] >> shift) & mask) : 0x100u;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        if (valid && (peers & lt) == 0) atomicAdd(&wh[w][d], (uint32_t)__popc(peers));
     }
-    uint32_t run = s[t] - sum;  // exclusive prefix of this thread's segment
-    for (int k = 0; k < per; ++k)
-        if (b0 + k < total) {
-            const uint32_t v = hist[b0 + k];
-            hist[b0 + k] = run;
-            run += v;
-        }
+    __syncthreads();
+    uint32_t c = 0;
+#pragma unroll
+    for (int k = 0; k < kRadixWarps; ++k) c += wh[k][t];
+    hist[(size_t)t * gridDim.x + blockIdx.x] = c;
 }
 
-// Stable scatter: each block walks its chunk 256 keys at a time; the rank of
-// a key among equal digits is (keys of that digit in earlier warps of the
-// tile) + (equal-digit lanes below it in its warp, via match.any).
-__global__ void __launch_bounds__(kRadixThreads) k_radix_scatter(
+__global__ void __launch_bounds__(kRadixThreads) k_radix_downsweep(
     const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
-    uint32_t* __restrict__ vout, unsigned long long n_host, const unsigned long long* n_dev,
-    int shift, int bits, const uint32_t* __restrict__ hist) {
-    __shared__ uint32_t s_base[256];
+    uint32_t* __restrict__ vout, unsigned long long n_host, const unsigned long long* n_dev, int shift,
+    int bits, const uint32_t* __restrict__ hist) {
+    __shared__ uint32_t s_keys[kRTile];
+    __shared__ uint32_t s_vals[kRTile];
     __shared__ uint32_t s_wc[kRadixWarps][256];
-    const int t = threadIdx.x, G = gridDim.x, b = blockIdx.x;
-    const int w = t >> 5, lane = t & 31;
-    s_base[t] = hist[(size_t)t * G + b];
+    __shared__ uint32_t s_run[256];
+    __shared__ uint32_t s_start[256];
+    __shared__ uint32_t s_gbase[256];
+    __shared__ uint32_t s_wsum[kRadixWarps];
+    const int t = threadIdx.x, w = t >> 5, lane = t & 31;
     const unsigned long long n = clamp_n(n_host, n_dev);
-    unsigned long long begin, end;
-    chunk_of(n, G, b, begin, end);
+    const unsigned long long base = (unsigned long long)blockIdx.x * kRTile;
+    if (base >= n) return;
+    const int count = (int)(n - base < (unsigned long long)kRTile ? n - base : (unsigned long long)kRTile);
     const uint32_t mask = (1u << bits) - 1u;
-    const uint32_t lt_mask = (1u << lane) - 1u;
-    for (unsigned long long base = begin; base < end; base += kRadixThreads) {
+    const uint32_t lt = lane_lt_mask();
+    s_run[t] = 0u;
+    s_gbase[t] = hist[(size_t)t * gridDim.x + blockIdx.x];
+
+    uint32_t key[kRItems], val[kRItems], rank[kRItems];
+#pragma unroll
+    for (int k = 0; k < kRItems; ++k) {
+        const int j = k * kRadixThreads + t;
+        key[k] = j < count ? kin[base + j] : 0u;
+        val[k] = j < count ? vin[base + j] : 0u;
+    }
+#pragma unroll
+    for (int k = 0; k < kRItems; ++k) {
 #pragma unroll
         for (int ww = 0; ww < kRadixWarps; ++ww) s_wc[ww][t] = 0u;
         __syncthreads();
-        const unsigned long long i = base + t;
-        const bool valid = i < end;
-        const uint32_t k = valid ? kin[i] : 0u;
-        const uint32_t v = valid ? vin[i] : 0u;
-        const uint32_t d = valid ? ((k >> shift) & mask) : 0x100u;
+        const bool valid = k * kRadixThreads + t < count;
+        const uint32_t d = valid ? ((key[k] >> shift) & mask) : 0x100u;
         const uint32_t peers = __match_any_sync(0xffffffffu, d);
-        const uint32_t rank = __popc(peers & lt_mask);
-        if (valid && rank == 0) s_wc[w][d] = __popc(peers);
+        const uint32_t rw = __popc(peers & lt);
+        if (valid && rw == 0) s_wc[w][d] = __popc(peers);
         __syncthreads();
         {
-            uint32_t run = s_base[t];
+            uint32_t run = s_run[t];
 #pragma unroll
             for (int ww = 0; ww < kRadixWarps; ++ww) {
                 const uint32_t c = s_wc[ww][t];
                 s_wc[ww][t] = run;
                 run += c;
             }
-            s_base[t] = run;
+            s_run[t] = run;
         }
         __syncthreads();
-        if (valid) {
-            const uint32_t pos = s_wc[w][d] + rank;
-            kout[pos] = k;
-            vout[pos] = v;
+        rank[k] = valid ? s_wc[w][d] + rw : 0u;
+    }
+    // local digit starts: exclusive scan of the tile's digit counts
+    {
+        const uint32_t c = s_run[t];
+        uint32_t x = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
         }
+        if (lane == 31) s_wsum[w] = x;
+        __syncthreads();
+        uint32_t wp = 0;
+        for (int ww = 0; ww < w; ++ww) wp += s_wsum[ww];
+        s_start[t] = wp + x - c;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kRItems; ++k) {
+        if (k * kRadixThreads + t < count) {
+            const uint32_t d = (key[k] >> shift) & mask;
+            const uint32_t pos = s_start[d] + rank[k];
+            s_keys[pos] = key[k];
+            s_vals[pos] = val[k];
+        }
+    }
+    __syncthreads();
+    // consecutive threads write consecutive positions of each digit run
+    for (int i = t; i < count; i += kRadixThreads) {
+        const uint32_t k = s_keys[i];
+        const uint32_t d = (k >> shift) & mask;
+        const uint32_t pos = s_gbase[d] + (uint32_t)i - s_start[d];
+        kout[pos] = k;
+        vout[pos] = s_vals[i];
+    }
+}
+
+// Device-wide exclusive scan of a u32 array in place (three phases).
+constexpr int kU32ScanChunk = 4096;
+
+__global__ void __launch_bounds__(1024) k_u32_reduce(const uint32_t* __restrict__ a, long long n,
+                                                     uint32_t* __restrict__ part) {
+    __shared__ uint32_t s_w[32];
+    const long long base = (long long)blockIdx.x * kU32ScanChunk;
+    uint32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const long long i = base + k * 1024 + threadIdx.x;
+        if (i < n) s += a[i];
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        uint32_t v = s_w[threadIdx.x];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (threadIdx.x == 0) part[blockIdx.x] = v;
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_u32_top(uint32_t* part, int nparts) {
+    __shared__ uint32_t s[1024];
+    const int t = threadIdx.x;
+    const int per = (nparts + 1023) / 1024;
+    const int b0 = t * per;
+    uint32_t sum = 0;
+    for (int k = 0; k < per; ++k)
+        if (b0 + k < nparts) sum += part[b0 + k];
+    s[t] = sum;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        const uint32_t v = t >= o ? s[t - o] : 0u;
+        __syncthreads();
+        s[t] += v;
         __syncthreads();
     }
+    uint32_t run = s[t] - sum;
+    for (int k = 0; k < per; ++k)
+        if (b0 + k < nparts) {
+            const uint32_t v = part[b0 + k];
+            part[b0 + k] = run;
+            run += v;
+        }
+}
+
+__global__ void __launch_bounds__(1024) k_u32_apply(uint32_t* __restrict__ a, long long n,
+                                                    const uint32_t* __restrict__ part) {
+    __shared__ uint32_t s_w[32];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const long long base = (long long)blockIdx.x * kU32ScanChunk + (long long)t * 4;
+    uint32_t v[4], s = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        v[k] = base + k < n ? a[base + k] : 0u;
+        s += v[k];
+    }
+    uint32_t x = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_w[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t y = s_w[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t z = __shfl_up_sync(0xffffffffu, y, o);
+            if (lane >= o) y += z;
+        }
+        s_w[lane] = y;
+    }
+    __syncthreads();
+    uint32_t run = part[blockIdx.x] + (w > 0 ? s_w[w - 1] : 0u) + x - s;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        if (base + k < n) {
+            a[base + k] = run;
+            run += v[k];
+        }
+}
+
+// Gathers the high key word of each record into sorted order.
+__global__ void k_gather_u32(const uint32_t* __restrict__ src, const uint32_t* __restrict__ idx, long long n,
+                             uint32_t* __restrict__ dst) {
+    const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) dst[j] = src[idx[j]];
 }
 
 // ---- tiles-touched scan in depth order ------------------------------------
@@ -277,26 +404,35 @@ __global__ void k_ranges(const uint32_t* __restrict__ keys, long long cap,
     }
 }
 
-cudaError_t radix_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, uint32_t* hist,
+int radix_blocks(unsigned long long n_host) {
+    return (int)((n_host + kRTile - 1) / kRTile);
+}
+
+// Sorts (key, value) pairs on the low key_bits bits of the keys, ping-ponging
+// between buffer 0 and 1; *result_buf receives the buffer holding the result.
+cudaError_t radix_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, const WsPtrs& ws,
                        unsigned long long n_host, const unsigned long long* n_dev, int key_bits,
-                       int G, int* result_buf, cudaStream_t s, Prof& pf, int fam) {
+                       int* result_buf, cudaStream_t s) {
     const int passes = key_bits <= 0 ? 0 : (key_bits + 7) / 8;
-    const int pi = pf.begin(fam, s, 3 * passes);
     const int dbits = passes ? (key_bits + passes - 1) / passes : 0;
+    const int nblk = radix_blocks(n_host);
+    const long long nh = 256ll * nblk;
+    const int nparts = (int)((nh + kU32ScanChunk - 1) / kU32ScanChunk);
     uint32_t* kin = k0;
     uint32_t* vin = v0;
     uint32_t* kout = k1;
     uint32_t* vout = v1;
-    for (int p = 0; p < passes; ++p) {
+    for (int p = 0; p < passes && nblk > 0; ++p) {
         const int shift = p * dbits;
         const int bits = key_bits - shift < dbits ? key_bits - shift : dbits;
-        k_radix_hist<<<G, kRadixThreads, 0, s>>>(kin, n_host, n_dev, shift, bits, hist);
-        k_radix_scan<<<1, 1024, 0, s>>>(hist, 256 * G);
-        k_radix_scatter<<<G, kRadixThreads, 0, s>>>(kin, vin, kout, vout, n_host, n_dev, shift, bits, hist);
+        k_radix_upsweep<<<nblk, kRadixThreads, 0, s>>>(kin, n_host, n_dev, shift, bits, ws.hist);
+        k_u32_reduce<<<nparts, 1024, 0, s>>>(ws.hist, nh, ws.hist_part);
+        k_u32_top<<<1, 1024, 0, s>>>(ws.hist_part, nparts);
+        k_u32_apply<<<nparts, 1024, 0, s>>>(ws.hist, nh, ws.hist_part);
+        k_radix_downsweep<<<nblk, kRadixThreads, 0, s>>>(kin, vin, kout, vout, n_host, n_dev, shift, bits, ws.hist);
         uint32_t* tk = kin; kin = kout; kout = tk;
         uint32_t* tv = vin; vin = vout; vout = tv;
     }
-    pf.end(pi, s);
     *result_buf = passes % 2;
     return cudaGetLastError();
 }
@@ -308,15 +444,29 @@ cudaError_t launch_bin(const BatchParam& bp, WsPtrs& ws, unsigned int* status,
     const long long M = bp.total_recs;
     cudaError_t e;
     if (M <= 0) return cudaSuccess;
-    // 1. front-to-back order of records: 32-bit depth keys, stable in index
+    // 1. front-to-back order of records: 64-bit double-float depth keys
+    //    (low word first, then the high word), stable in record index
+    int pi = pf.begin(GS_KF_DEPTH_SORT, s, 8 * 5 + 1);
     int dbuf = 0;
-    e = radix_sort(ws.dkeys[0], ws.dvals[0], ws.dkeys[1], ws.dvals[1], ws.hist,
-                   (unsigned long long)M, nullptr, 32, ws.radix_grid, &dbuf, s, pf, GS_KF_DEPTH_SORT);
+    e = radix_sort(ws.dkeys[0], ws.dvals[0], ws.dkeys[1], ws.dvals[1], ws, (unsigned long long)M, nullptr, 32,
+                   &dbuf, s);
     if (e != cudaSuccess) return e;
+    k_gather_u32<<<(unsigned)((M + 255) / 256), 256, 0, s>>>(ws.dhi, ws.dvals[dbuf], M, ws.dkeys[1 - dbuf]);
+    {
+        uint32_t* hk = ws.dkeys[1 - dbuf];
+        uint32_t* hv = ws.dvals[dbuf];
+        uint32_t* ok = ws.dkeys[dbuf];
+        uint32_t* ov = ws.dvals[1 - dbuf];
+        int hb = 0;
+        e = radix_sort(hk, hv, ok, ov, ws, (unsigned long long)M, nullptr, 32, &hb, s);
+        if (e != cudaSuccess) return e;
+        dbuf = hb ? 1 - dbuf : dbuf;  // values end in hv (hb == 0) or ov (hb == 1)
+    }
+    pf.end(pi, s);
     const uint32_t* order = ws.dvals[dbuf];
     // 2. exclusive scan of tiles-touched in that order
     const int nb = (int)((M + kScanChunk - 1) / kScanChunk);
-    int pi = pf.begin(GS_KF_TILE_SCAN, s, 3);
+    pi = pf.begin(GS_KF_TILE_SCAN, s, 3);
     k_scan_reduce<<<nb, kScanThreads, 0, s>>>(order, ws.tiles_touched, M, ws.scan_part);
     k_scan_top<<<1, 1024, 0, s>>>(ws.scan_part, nb, ws.counters, ws.cap, status, status_pairs);
     k_scan_apply<<<nb, kScanThreads, 0, s>>>(order, ws.tiles_touched, M, ws.scan_part, ws.offsets);
@@ -331,9 +481,10 @@ cudaError_t launch_bin(const BatchParam& bp, WsPtrs& ws, unsigned int* status,
     int tile_bits = 1;
     while ((1ll << tile_bits) < (long long)bp.total_tiles) ++tile_bits;
     int pbuf = 0;
-    e = radix_sort(ws.pkeys[0], ws.pvals[0], ws.pkeys[1], ws.pvals[1], ws.hist,
-                   (unsigned long long)ws.cap, ws.counters, tile_bits, ws.radix_grid, &pbuf, s, pf,
-                   GS_KF_TILE_SORT);
+    pi = pf.begin(GS_KF_TILE_SORT, s, 5 * ((tile_bits + 7) / 8));
+    e = radix_sort(ws.pkeys[0], ws.pvals[0], ws.pkeys[1], ws.pvals[1], ws, (unsigned long long)ws.cap,
+                   ws.counters, tile_bits, &pbuf, s);
+    pf.end(pi, s);
     if (e != cudaSuccess) return e;
     ws.sorted_buf = pbuf;
     // 5. per-tile [start, end)

@@ -106,15 +106,18 @@ def test_projection_records_match_oracle(orc):
         vis = (o["valid"] == 1) & (o["opac"] > 1 / 255) & (touched[off:off + n] > 0)
         np.testing.assert_allclose(R[vis, 0], o["q"][vis, 0], rtol=2e-6, atol=2e-4)
         np.testing.assert_allclose(R[vis, 1], o["q"][vis, 1], rtol=2e-6, atol=2e-4)
-        A = R[vis, 2] / (-0.5 * LOG2E)
-        Bc = R[vis, 3] / (-LOG2E)
-        C = R[vis, 4] / (-0.5 * LOG2E)
+        # conic = (2 / log2 e) (v1 v1^T + v2 v2^T)
+        Rv = R[vis].astype(np.float64)
+        k = 2.0 / LOG2E
+        A = k * (Rv[:, 2] ** 2 + Rv[:, 4] ** 2)
+        Bc = k * (Rv[:, 2] * Rv[:, 3] + Rv[:, 4] * Rv[:, 5])
+        C = k * (Rv[:, 3] ** 2 + Rv[:, 5] ** 2)
         scale = np.abs(o["conic"][vis]).max(1)
-        for got, k in ((A, 0), (Bc, 1), (C, 2)):
-            assert np.max(np.abs(got - o["conic"][vis, k]) / scale) < 2e-4
-        np.testing.assert_allclose(2.0 ** R[vis, 5], o["opac"][vis], rtol=2e-6)
-        np.testing.assert_allclose(R[vis][:, [6, 7, 8]], o["colour"][vis], atol=2e-6)
-        np.testing.assert_allclose(R[vis, 9], o["depth"][vis], rtol=2e-6)
+        for got, kk in ((A, 0), (Bc, 1), (C, 2)):
+            assert np.max(np.abs(got - o["conic"][vis, kk]) / scale) < 2e-5
+        np.testing.assert_allclose(2.0 ** Rv[:, 6], o["opac"][vis], rtol=2e-6)
+        np.testing.assert_allclose(Rv[:, [7, 8, 9]], o["colour"][vis], atol=2e-6)
+        np.testing.assert_allclose(Rv[:, 10], o["depth"][vis], rtol=2e-6)
         # culled by the oracle -> no tiles on the GPU
         assert np.all(touched[off:off + n][o["valid"] == 0] == 0)
         off += n
@@ -166,11 +169,14 @@ def test_bins_are_sorted_and_complete():
         for ty in range(y0, y1):
             for tx in range(x0, x1):
                 expect[rect[i, 2] + ty * rect[i, 3] + tx].append(i)
-    depth_bits = rec[:, 9].view(np.uint32)
+    # each tile list is the set of records whose rectangle covers it, in the
+    # front-to-back order of the 64-bit depth keys (high words never decrease)
+    hi = ws_view(r, L.depth_hi, np.uint32, M).astype(np.int64)
     for t in range(T):
         got = sv[ranges[t, 0]:ranges[t, 1]].tolist()
-        want = sorted(expect[t], key=lambda i: (int(depth_bits[i]), i))
-        assert got == want, "tile %d" % t
+        assert sorted(got) == sorted(expect[t]), "tile %d holds the wrong records" % t
+        keys = hi[got]
+        assert np.all(keys[1:] >= keys[:-1]), "tile %d is not front to back" % t
 
 
 def l1_target(params, views, seed=5):
@@ -317,7 +323,9 @@ def test_autograd_function_matches_direct_calls():
     grads = win.grad_tensors()
     r2.backward(win.struct(), w.contiguous(), grads=grads)
     for t, g in zip(ts, grads):
-        assert torch.allclose(t.grad, g, rtol=1e-5, atol=1e-7)
+        # float atomics add in a different order on each run
+        err = (t.grad - g).norm() / g.norm().clamp_min(1e-30)
+        assert err < 1e-5
 
 
 def test_capacity_overflow_is_reported_and_recovered():
@@ -325,9 +333,9 @@ def test_capacity_overflow_is_reported_and_recovered():
     views = ragged_views(3000)
     win = GaussianWindow(p, 0)
     r = Renderer(views, 0, 16, capacity=100)
-    assert r.cap < 1000
+    cap0 = r.cap
     r.forward(win.struct())  # grows the workspace after GS_ERR_CAPACITY
-    assert r.cap >= r.last_pairs > 100
+    assert r.last_pairs > cap0 and r.cap >= r.last_pairs
     _, ref = gpu_forward(p, views)
     assert torch.equal(r.rgb, ref.rgb)
     # async path: a too-small workspace latches the status, reported later
@@ -335,6 +343,7 @@ def test_capacity_overflow_is_reported_and_recovered():
     r3._counted = True
     r3.forward(win.struct())
     rc, need = r3.ctx.sync_status()
+    assert r3.cap < r.last_pairs
     assert rc == B.GS_ERR_CAPACITY and need == r.last_pairs
     rc, _ = r3.ctx.sync_status()
     assert rc == B.GS_OK
@@ -386,3 +395,69 @@ def test_window_optimizer_step_reduces_loss():
     opt = WindowOptimizer(p, views, target, lr=1e-3)
     losses = [float(opt.step().item()) for _ in range(30)]
     assert losses[-1] < losses[0]
+
+
+def sampled_pixels(views, per_view, seed):
+    rng = np.random.default_rng(seed)
+    return [(rng.integers(0, v["W"], per_view), rng.integers(0, v["H"], per_view)) for v in views]
+
+
+def masked_dl(views, pix, seed):
+    """dL/drgb that is non-zero only at the sampled pixels (a loss that depends
+    on those pixels alone), packed for the GPU and per-pixel for the oracle."""
+    rng = np.random.default_rng(seed)
+    packed, per = [], []
+    for v, (px, py) in zip(views, pix):
+        w = rng.standard_normal((len(px), 3))
+        img = np.zeros((3, v["H"], v["W"]), np.float32)
+        np.add.at(img, (slice(None), py, px), w.T.astype(np.float32))
+        # duplicates accumulate on both sides
+        packed.append(img.reshape(-1))
+        per.append(w)
+    return torch.as_tensor(np.concatenate(packed)).cuda(), per
+
+
+def sampled_parity(orc, params, views, tile_size, per_view, seed, check_params=True):
+    win, r = gpu_forward(params, views, tile_size=tile_size)
+    pix = sampled_pixels(views, per_view, seed)
+    for v, img, T, (px, py) in zip(views, r.images(), B.unpack_images(r.T, views, 1), pix):
+        o = orc.render_pixels(params, v, px, py)
+        ok = ~o["border"]
+        got = img.cpu().numpy()[:, py, px].T
+        assert np.abs(got - o["rgb"])[ok].max() <= FWD_TOL
+        assert np.abs(T.cpu().numpy()[py, px] - o["T"])[ok].max() <= FWD_TOL
+    dl_gpu, dl_orc = masked_dl(views, pix, seed + 1)
+    grads = win.grad_tensors()
+    r.backward(win.struct(), dl_gpu, grads=grads if check_params else None, want_pose=True)
+    torch.cuda.synchronize()
+    g, pose, border = orc.backward(params, views, dl_orc, pixels=pix)
+    gp = r.dL_dpose.view(-1, 6).cpu().numpy().astype(np.float64)
+    if check_params:
+        compare_grads(win, g, border, pose=gp, orc_pose=pose)
+    else:
+        for vi in range(len(views)):
+            assert rel_l2(gp[vi], pose[vi]) <= GRAD_TOL
+    return r
+
+
+def test_full_size_window_sampled(orc):
+    """Headline size and launch configuration: 200k box-room Gaussians, 8
+    keyframes 640x512, 16x16 tiles; forward checked on sampled pixels,
+    gradients of a loss supported on those pixels checked in full."""
+    n = 200_000
+    p = scenes.box_room_scene(n, seed=0, sh_degree=1)
+    views = scenes.arc_views(8, 640, 512, 600.0, n_gaussians=n)
+    r = sampled_parity(orc, p, views, 16, 48, seed=21)
+    assert r.last_pairs > 1_000_000
+
+
+def test_odometry_view_pose_gradient_sampled(orc):
+    """Odometry size: 500k Gaussians, one 1280x1024 view at a perturbed pose;
+    pose-only backward on sampled pixels against the oracle."""
+    from paper_2501_08672_b300.render import apply_left
+    n = 500_000
+    p = scenes.box_room_scene(n, seed=2, sh_degree=1)
+    v = scenes.lookat_view((4.0 * math.cos(-1.7), 4.0 * math.sin(-1.7), 2.2), (0.0, 0.0, 0.6), 1280, 1024,
+                           1200.0, 0, n)
+    v = apply_left(v, np.array([0.02, -0.015, 0.01, 0.03, -0.02, 0.01]))
+    sampled_parity(orc, p, [v], 16, 64, seed=31, check_params=False)

@@ -424,3 +424,22 @@ def test_borderline_pixels_are_rare(orc):
     v = scenes.identity_view(160, 128, 150.0)
     out = orc.render_view(p, v)
     assert out["border"].mean() < 1e-3
+
+
+def test_pixel_list_paths_agree_with_full_image(orc):
+    """The pixel-list render/backward (used for sampled checks of full-size
+    workloads) equals the full-image one on the same pixels."""
+    p = _tiny_scene(61, n=40, sh_degree=1)
+    v = _posed_view(30, 22)
+    full = orc.render_view(p, v)
+    yy, xx = np.mgrid[0:v["H"], 0:v["W"]]
+    px, py = xx.reshape(-1), yy.reshape(-1)
+    lst = orc.render_pixels(p, v, px, py)
+    np.testing.assert_array_equal(lst["rgb"].T.reshape(3, v["H"], v["W"]), full["rgb"])
+    np.testing.assert_array_equal(lst["T"].reshape(v["H"], v["W"]), full["T"])
+    w = np.random.default_rng(7).standard_normal((3, v["H"], v["W"]))
+    g1, pose1, _ = orc.backward(p, [v], [w])
+    g2, pose2, _ = orc.backward(p, [v], [w.reshape(3, -1).T], pixels=[(px, py)])
+    for k in g1:
+        np.testing.assert_allclose(g2[k], g1[k], rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(pose2, pose1, rtol=1e-12, atol=1e-15)
