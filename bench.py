@@ -39,15 +39,18 @@ FOCAL = 600.0
 LR = 1e-3
 WORKLOAD = "box-room sliding window: 200k planar Gaussians (SH degree 1), 8 keyframes 640x512 on a 2 m arc"
 
-# Algorithmic FP32 work per visited fragment (FMA counted as 2 FLOP, the ex2 /
-# rcp of the special-function unit not counted): forward = offset (2), exponent
-# quadratic form (2 mul + 3 fma = 8), alpha clamp (1), 1-alpha and T update
-# (2), weight (1), colour accumulation (3 fma = 6) -> 20; backward = the same
-# exponent (10) and clamp (1), transmittance recovery (2), weight and colour
-# gradient (1 + 3), light-behind difference and alpha gradient (3 + 6),
-# light-behind update (3 fma = 6), opacity/exponent gradient (2), mean and
-# conic gradients (2 x 3 + 5) -> 45.
-FLOP_PER_FRAGMENT = {"raster_fwd": 20.0, "raster_bwd": 45.0}
+# Algorithmic FP32 work (FMA counted as 2 FLOP; the ex2 and divide of the
+# special-function unit are not counted).  Every visited fragment (pixel,
+# Gaussian) evaluates the exponent l - (d.v1)^2 - (d.v2)^2: one offset, two
+# projections (fma + mul) and two fma, plus its share of the per-column
+# offset = 10 FLOP.  A contributing fragment adds, in the forward, the alpha
+# clamp, 1 - alpha, the transmittance update, the weight and three colour fma
+# = 10 FLOP; in the backward, the transmittance recovery (2), weight and
+# colour gradient (1 + 6), light-behind differences and alpha gradient
+# (3 + 5 + 1), light-behind update (6), exponent gradient (2), mean gradient
+# (10), conic gradient (8) and opacity term (1) = 45 FLOP.
+FLOP_VISITED = 10.0
+FLOP_CONTRIB = {"raster_fwd": 10.0, "raster_bwd": 45.0}
 SM_COUNT = 148
 FP32_LANES = 128
 
@@ -278,14 +281,21 @@ def run_b300(args, world, rank, local):
     dom_launches, dom_ms = prof.get(dominant, (0, 0.0))
     avg_ms = dom_ms / max(dom_launches, 1)
     hbm, hbm_kind = peaks()
-    fragments = float(opt.r.n_contrib.double().sum().item())
-    if dominant in FLOP_PER_FRAGMENT:
+    # fragment counts of the last parameters (one extra forward, outside timing)
+    n_used = torch.empty_like(opt.r.n_contrib)
+    opt.r.forward(opt._g, count=False, n_used=n_used)
+    torch.cuda.synchronize()
+    visited = float(opt.r.n_contrib.double().sum().item())
+    contrib = float(n_used.double().sum().item())
+    if dominant in FLOP_CONTRIB:
         clk = 2032.0
         peak = SM_COUNT * FP32_LANES * 2 * clk * 1e6 / 1e12
-        achieved = fragments * FLOP_PER_FRAGMENT[dominant] / (avg_ms / 1e3) / 1e12
+        flop = FLOP_VISITED * visited + FLOP_CONTRIB[dominant] * contrib
+        achieved = flop / (avg_ms / 1e3) / 1e12
         roof = {"bound": "alu", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": None, "avg_launch_ms": avg_ms,
-                "fragments_per_launch": fragments,
+                "visited_fragments": visited, "contributing_fragments": contrib,
+                "flop_per_launch": flop,
                 "peak_basis": "FP32 FMA peak: 148 SMs x 128 lanes x 2 FLOP x 2032 MHz (maximum SM clock)"}
     else:
         roof = {"bound": "hbm", "kernel": dominant, "achieved": None, "peak": hbm, "unit": "GB/s",

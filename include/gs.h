@@ -222,9 +222,11 @@ GS_API int gs_bin(gs_ctx* ctx, const gs_view* views, int n_views, const gs_works
  * Outputs (device, packed over views): rgb [sum 3 H W] (view v planar
  * [3,H,W]), T_final [sum H W], n_contrib [sum H W] (1 + position in the
  * tile's list of the last contributing Gaussian, 0 if none; consumed by
- * gs_render_bwd).  Errors: GS_ERR_INVALID_ARG, GS_ERR_CUDA. */
+ * gs_render_bwd), n_used [sum H W] (number of contributing Gaussians; may be
+ * NULL).  Errors: GS_ERR_INVALID_ARG, GS_ERR_CUDA. */
 GS_API int gs_render_fwd(gs_ctx* ctx, const gs_view* views, int n_views, const gs_workspace* ws,
-                  float* rgb, float* T_final, uint32_t* n_contrib, gs_stream stream);
+                  float* rgb, float* T_final, uint32_t* n_contrib, uint32_t* n_used,
+                  gs_stream stream);
 
 /* a4: photometric loss (Eq. gaussian_optimization, L1 norm):
  * L = (1/V) sum_v mean_{3 H_v W_v} |rgb - target| written to loss_dev[0], and

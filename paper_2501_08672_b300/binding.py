@@ -74,7 +74,8 @@ class Workspace(ctypes.Structure):
 
 
 class WsLayout(ctypes.Structure):
-    _fields_ = [(n, ctypes.c_size_t) for n in ("records", "rects", "tiles_touched", "depth_keys", "depth_vals",
+    _fields_ = [(n, ctypes.c_size_t) for n in ("records", "rects", "tiles_touched", "depth_keys", "depth_hi",
+                                               "depth_vals",
                                                "pair_offsets", "pair_keys", "pair_vals", "sorted_vals",
                                                "tile_ranges", "grad2d", "counters", "total")] + [
         ("n_records", ctypes.c_int64), ("n_tiles", ctypes.c_int32), ("n_pixels", ctypes.c_int64)]
@@ -114,7 +115,7 @@ def lib():
         L.gs_workspace_layout.argtypes = [P, ctypes.POINTER(View), I, I64, ctypes.POINTER(WsLayout)]
         L.gs_project.argtypes = [P, ctypes.POINTER(Gaussians), ctypes.POINTER(View), I, ctypes.POINTER(Workspace), P]
         L.gs_bin.argtypes = [P, ctypes.POINTER(View), I, ctypes.POINTER(Workspace), ctypes.POINTER(ctypes.c_uint64), P]
-        L.gs_render_fwd.argtypes = [P, ctypes.POINTER(View), I, ctypes.POINTER(Workspace), P, P, P, P]
+        L.gs_render_fwd.argtypes = [P, ctypes.POINTER(View), I, ctypes.POINTER(Workspace), P, P, P, P, P]
         L.gs_l1_loss.argtypes = [P, ctypes.POINTER(View), I, ctypes.POINTER(Workspace), P, P, P, P, P]
         L.gs_render_bwd.argtypes = [P, ctypes.POINTER(Gaussians), ctypes.POINTER(View), I, ctypes.POINTER(Workspace),
                                     P, P, P, ctypes.POINTER(Grads), P, P]
@@ -261,9 +262,9 @@ class Context:
         self._ck(lib().gs_bin(self.h, views, len(views), ctypes.byref(ws), None, _stream(stream)))
         return None
 
-    def render_fwd(self, views, ws, rgb, T_final, n_contrib, stream=None):
+    def render_fwd(self, views, ws, rgb, T_final, n_contrib, n_used=None, stream=None):
         self._ck(lib().gs_render_fwd(self.h, views, len(views), ctypes.byref(ws), _ptr(rgb), _ptr(T_final),
-                                     _ptr(n_contrib), _stream(stream)))
+                                     _ptr(n_contrib), _ptr(n_used), _stream(stream)))
 
     def l1_loss(self, views, ws, rgb, target, dL_drgb, loss=None, stream=None):
         self._ck(lib().gs_l1_loss(self.h, views, len(views), ctypes.byref(ws), _ptr(rgb), _ptr(target),

@@ -471,7 +471,7 @@ int gs_bin(gs_ctx* ctx, const gs_view* views, int n_views, const gs_workspace* w
 }
 
 int gs_render_fwd(gs_ctx* ctx, const gs_view* views, int n_views, const gs_workspace* ws, float* rgb,
-                  float* T_final, uint32_t* n_contrib, gs_stream stream) {
+                  float* T_final, uint32_t* n_contrib, uint32_t* n_used, gs_stream stream) {
     if (!ctx) return GS_ERR_INVALID_ARG;
     if (!rgb || !T_final || !n_contrib) return fail(ctx, GS_ERR_INVALID_ARG, "an output pointer is NULL");
     Layout L;
@@ -481,7 +481,7 @@ int gs_render_fwd(gs_ctx* ctx, const gs_view* views, int n_views, const gs_works
     BatchParam bp;
     make_batch(ctx->cfg, views, n_views, bp);
     const WsPtrs wp = ws_ptrs(ws, L, bp.total_tiles);
-    cudaError_t e = launch_render_fwd(bp, make_rc(ctx->cfg), wp, rgb, T_final, n_contrib,
+    cudaError_t e = launch_render_fwd(bp, make_rc(ctx->cfg), wp, rgb, T_final, n_contrib, n_used,
                                       reinterpret_cast<cudaStream_t>(stream), ctx->prof);
     return e == cudaSuccess ? GS_OK : cuda_fail(ctx, e, "gs_render_fwd");
 }

@@ -141,8 +141,8 @@ cudaError_t launch_project(const BatchParam& bp, const GaussPtrs& g, const Rende
 cudaError_t launch_bin(const BatchParam& bp, WsPtrs& ws, unsigned int* status,
                        unsigned long long* status_pairs, cudaStream_t s, Prof& pf);
 cudaError_t launch_render_fwd(const BatchParam& bp, const RenderConst& rc, const WsPtrs& ws,
-                              float* rgb, float* T_final, uint32_t* n_contrib, cudaStream_t s,
-                              Prof& pf);
+                              float* rgb, float* T_final, uint32_t* n_contrib, uint32_t* n_used,
+                              cudaStream_t s, Prof& pf);
 cudaError_t launch_render_bwd(const BatchParam& bp, const RenderConst& rc, const WsPtrs& ws,
                               const float* T_final, const uint32_t* n_contrib,
                               const float* dL_drgb, cudaStream_t s, Prof& pf);

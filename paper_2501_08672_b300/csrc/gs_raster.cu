@@ -38,7 +38,8 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_render_fwd(const __grid_const
                                                               const uint32_t* __restrict__ svals,
                                                               float* __restrict__ rgb,
                                                               float* __restrict__ T_final,
-                                                              uint32_t* __restrict__ n_contrib) {
+                                                              uint32_t* __restrict__ n_contrib,
+                                                              uint32_t* __restrict__ n_used) {
     constexpr int NT = TS * TS / PPT;
     __shared__ float4 s_a[kBatch];
     __shared__ float4 s_b[kBatch];
@@ -52,7 +53,7 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_render_fwd(const __grid_const
     const int py0 = ty * TS + (t / TS) * PPT;
     const float fx = px + 0.5f;
     float fy[PPT], T[PPT], C0[PPT], C1[PPT], C2[PPT];
-    uint32_t last[PPT];
+    uint32_t last[PPT], used[PPT];
     bool done[PPT];
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
@@ -60,6 +61,7 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_render_fwd(const __grid_const
         T[k] = 1.f;
         C0[k] = C1[k] = C2[k] = 0.f;
         last[k] = 0;
+        used[k] = 0;
         done[k] = !(px < V.W && py0 + k < V.H);
     }
     const uint2 rg = ranges[tile];
@@ -110,6 +112,7 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_render_fwd(const __grid_const
                     C2[k] = fmaf(c.y, w, C2[k]);
                     T[k] = Tn;
                     last[k] = start - rg.x + j + 1;
+                    ++used[k];
                 }
             }
         }
@@ -125,6 +128,7 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_render_fwd(const __grid_const
             out[2 * hw + pl] = C2[k] + T[k] * rc.bg[2];
             T_final[V.pix_off + pl] = T[k];
             n_contrib[V.pix_off + pl] = last[k];
+            if (n_used) n_used[V.pix_off + pl] = used[k];
         }
     }
 }
@@ -330,20 +334,20 @@ __global__ void k_l1_finish(const float* __restrict__ partials, int n, float* __
 }  // namespace
 
 cudaError_t launch_render_fwd(const BatchParam& bp, const RenderConst& rc, const WsPtrs& ws,
-                              float* rgb, float* T_final, uint32_t* n_contrib, cudaStream_t s,
-                              Prof& pf) {
+                              float* rgb, float* T_final, uint32_t* n_contrib, uint32_t* n_used,
+                              cudaStream_t s, Prof& pf) {
     if (bp.total_tiles <= 0) return cudaSuccess;
     const uint32_t* svals = ws.pvals[ws.sorted_buf];
     const int pi = pf.begin(GS_KF_RASTER_FWD, s);
     switch (bp.tile_size) {
         case 8:
-            k_render_fwd<8, 2><<<bp.total_tiles, 32, 0, s>>>(bp, rc, ws.rec, ws.ranges, svals, rgb, T_final, n_contrib);
+            k_render_fwd<8, 2><<<bp.total_tiles, 32, 0, s>>>(bp, rc, ws.rec, ws.ranges, svals, rgb, T_final, n_contrib, n_used);
             break;
         case 16:
-            k_render_fwd<16, 4><<<bp.total_tiles, 64, 0, s>>>(bp, rc, ws.rec, ws.ranges, svals, rgb, T_final, n_contrib);
+            k_render_fwd<16, 4><<<bp.total_tiles, 64, 0, s>>>(bp, rc, ws.rec, ws.ranges, svals, rgb, T_final, n_contrib, n_used);
             break;
         case 32:
-            k_render_fwd<32, 4><<<bp.total_tiles, 256, 0, s>>>(bp, rc, ws.rec, ws.ranges, svals, rgb, T_final, n_contrib);
+            k_render_fwd<32, 4><<<bp.total_tiles, 256, 0, s>>>(bp, rc, ws.rec, ws.ranges, svals, rgb, T_final, n_contrib, n_used);
             break;
         default:
             return cudaErrorInvalidValue;

@@ -59,7 +59,7 @@ class Renderer:
     def layout(self):
         return self.ctx.layout(self.views, self.cap)
 
-    def forward(self, g, count=None):
+    def forward(self, g, count=None, n_used=None):
         """project + bin + composite into self.rgb / self.T / self.n_contrib.
         count: True synchronises to read the pair count and grows the workspace
         if needed (default: only on the first call)."""
@@ -80,7 +80,7 @@ class Renderer:
             self.last_pairs = n
         else:
             self.ctx.bin(self.views, self.ws_struct)
-        self.ctx.render_fwd(self.views, self.ws_struct, self.rgb, self.T, self.n_contrib)
+        self.ctx.render_fwd(self.views, self.ws_struct, self.rgb, self.T, self.n_contrib, n_used)
 
     def l1(self, target):
         self.ctx.l1_loss(self.views, self.ws_struct, self.rgb, target, self.dL_drgb, self.loss)

@@ -54,3 +54,30 @@ def test_host_only_calls_work_without_a_gpu(lib):
     lib.gs_last_error.restype = ctypes.c_char_p
     assert lib.gs_last_error(None) == b"context is NULL"
     assert lib.gs_project(None, None, None, 0, None, None) == B.GS_ERR_INVALID_ARG
+
+
+def header_struct_fields(name):
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    m = re.search(r"typedef struct %s \{(.*?)\} %s;" % (name, name), text, flags=re.S)
+    assert m, name
+    fields = []
+    for decl in m.group(1).split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        decl = re.sub(r"\[[^\]]*\]", "", decl)
+        for part in decl.split(","):
+            fields.append(re.findall(r"\w+", part)[-1])
+    return fields
+
+
+@pytest.mark.parametrize("cname,pyname", [("gs_config", "Config"), ("gs_view", "View"),
+                                          ("gs_gaussians", "Gaussians"), ("gs_grads", "Grads"),
+                                          ("gs_workspace", "Workspace"), ("gs_ws_layout", "WsLayout"),
+                                          ("gs_profile_entry", "ProfileEntry"),
+                                          ("gs_lowp_segment", "LowpSegment")])
+def test_binding_structs_match_header(cname, pyname):
+    """Every ctypes mirror lists the header struct's fields in the same order."""
+    from paper_2501_08672_b300 import binding
+    py = [f[0] for f in getattr(binding, pyname)._fields_]
+    assert py == header_struct_fields(cname)
