@@ -134,6 +134,7 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_downsweep(
         }
         __syncthreads();
         rank[k] = valid ? s_wc[w][d] + rw : 0u;
+        __syncthreads();  // every rank is read before the next round clears s_wc
     }
     // local digit starts: exclusive scan of the tile's digit counts
     {
@@ -166,8 +167,10 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_downsweep(
         const uint32_t k = s_keys[i];
         const uint32_t d = (k >> shift) & mask;
         const uint32_t pos = s_gbase[d] + (uint32_t)i - s_start[d];
-        kout[pos] = k;
-        vout[pos] = s_vals[i];
+        if (pos < n) {  // always true for a consistent histogram; guards the write
+            kout[pos] = k;
+            vout[pos] = s_vals[i];
+        }
     }
 }
 
@@ -394,11 +397,13 @@ __global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ order
 
 // Tile ranges over the sorted pair keys.
 __global__ void k_ranges(const uint32_t* __restrict__ keys, long long cap,
-                         const unsigned long long* __restrict__ n_dev, uint2* __restrict__ ranges) {
+                         const unsigned long long* __restrict__ n_dev, uint32_t n_tiles,
+                         uint2* __restrict__ ranges) {
     const unsigned long long n = clamp_n((unsigned long long)cap, n_dev);
     for (unsigned long long j = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; j < n;
          j += (unsigned long long)gridDim.x * blockDim.x) {
         const uint32_t k = keys[j];
+        if (k >= n_tiles) continue;  // tile ids come from k_emit and are < n_tiles
         if (j == 0 || keys[j - 1] != k) ranges[k].x = (uint32_t)j;
         if (j + 1 == n || keys[j + 1] != k) ranges[k].y = (uint32_t)(j + 1);
     }
@@ -491,7 +496,7 @@ cudaError_t launch_bin(const BatchParam& bp, WsPtrs& ws, unsigned int* status,
     pi = pf.begin(GS_KF_RANGES, s, 2);
     e = cudaMemsetAsync(ws.ranges, 0, sizeof(uint2) * (size_t)bp.total_tiles, s);
     if (e != cudaSuccess) return e;
-    k_ranges<<<1184, 256, 0, s>>>(ws.pkeys[pbuf], ws.cap, ws.counters, ws.ranges);
+    k_ranges<<<1184, 256, 0, s>>>(ws.pkeys[pbuf], ws.cap, ws.counters, (uint32_t)bp.total_tiles, ws.ranges);
     pf.end(pi, s);
     return cudaGetLastError();
 }
