@@ -276,6 +276,15 @@ GS_API int gs_adam_step(gs_ctx* ctx, float* param, const float* grad, float* m, 
                  float lr, float b1, float b2, float eps, int64_t step,
                  const gs_lowp_segment* segs, int n_segs, gs_stream stream);
 
+/* a8, graph-friendly form: as gs_adam_step, but the step count lives in
+ * device memory.  step_dev (device, int64) holds the number of steps already
+ * taken; the call increments it on the stream and uses the new value for the
+ * bias correction, so one captured launch sequence advances it on every
+ * replay.  Errors: GS_ERR_INVALID_ARG, GS_ERR_CUDA. */
+GS_API int gs_adam_step_dev(gs_ctx* ctx, float* param, const float* grad, float* m, float* v, int64_t n,
+                            float lr, float b1, float b2, float eps, int64_t* step_dev,
+                            const gs_lowp_segment* segs, int n_segs, gs_stream stream);
+
 /* Synchronises `stream`, returns and clears the latched device status
  * (GS_OK or GS_ERR_CAPACITY); pairs_needed (nullable, host) receives the
  * pair count of the last gs_bin on this context. */

@@ -32,7 +32,7 @@ _DTYPE = {torch.float32: GS_F32, torch.float16: GS_F16, torch.bfloat16: GS_BF16}
 EXPORTED = ["gs_config_default", "gs_version", "gs_context_create", "gs_context_destroy", "gs_last_error",
             "gs_get_config", "gs_workspace_query", "gs_workspace_layout", "gs_project", "gs_bin",
             "gs_render_fwd", "gs_l1_loss", "gs_render_bwd", "gs_pose_grad", "gs_adam_step", "gs_sync_status",
-            "gs_profile_enable", "gs_profile_collect", "gs_launch_count"]
+            "gs_profile_enable", "gs_profile_collect", "gs_launch_count", "gs_adam_step_dev"]
 
 KERNEL_FAMILIES = ["project", "depth_sort", "tile_scan", "emit", "tile_sort", "ranges", "raster_fwd", "l1",
                    "raster_bwd", "project_bwd", "adam"]
@@ -123,6 +123,8 @@ def lib():
                                    P, P, P, P, P]
         L.gs_adam_step.argtypes = [P, P, P, P, P, I64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                    ctypes.c_float, I64, ctypes.POINTER(LowpSegment), I, P]
+        L.gs_adam_step_dev.argtypes = [P, P, P, P, P, I64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                       ctypes.c_float, P, ctypes.POINTER(LowpSegment), I, P]
         L.gs_sync_status.argtypes = [P, P, ctypes.POINTER(ctypes.c_uint64)]
         L.gs_profile_enable.argtypes = [P, ctypes.c_uint32]
         L.gs_profile_collect.argtypes = [P, P, ctypes.POINTER(ProfileEntry), I, ctypes.POINTER(ctypes.c_int)]
@@ -309,6 +311,18 @@ class Context:
 
     def launch_count(self):
         return int(lib().gs_launch_count(self.h))
+
+    def adam_step_dev(self, param, grad, m, v, lr, b1, b2, eps, step_dev, segments=(), stream=None):
+        """Adam with the step counter in device memory (int64 tensor, incremented by the call)."""
+        segs = None
+        ns = len(segments)
+        if ns:
+            segs = (LowpSegment * ns)()
+            for k, (b, e, dst) in enumerate(segments):
+                segs[k].begin, segs[k].end, segs[k].dtype, segs[k].dst = int(b), int(e), _DTYPE[dst.dtype], dst.data_ptr()
+        _check_dev(step_dev, "step_dev", torch.int64, 1)
+        self._ck(lib().gs_adam_step_dev(self.h, _ptr(param), _ptr(grad), _ptr(m), _ptr(v), param.numel(), float(lr),
+                                        float(b1), float(b2), float(eps), _ptr(step_dev), segs, ns, _stream(stream)))
 
     def sync_status(self, stream=None):
         n = ctypes.c_uint64()

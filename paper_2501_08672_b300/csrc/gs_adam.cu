@@ -36,10 +36,25 @@ __device__ __forceinline__ float adam1(float& p, float g, float& m, float& v, fl
     return p;
 }
 
+// Step counter kept on the device (graph replays advance it): increments the
+// count and stores lr / (1 - b1^t) and 1 / sqrt(1 - b2^t) for the Adam launch.
+__global__ void k_adam_coef(long long* step, float lr, float b1, float b2, float2* coef) {
+    const long long t = ++(*step);
+    const double bc1 = 1.0 - pow((double)b1, (double)t);
+    const double bc2 = 1.0 - pow((double)b2, (double)t);
+    *coef = make_float2((float)(lr / bc1), (float)(1.0 / sqrt(bc2)));
+}
+
 __global__ void __launch_bounds__(256) k_adam4(float4* __restrict__ p, const float4* __restrict__ g,
                                                float4* __restrict__ m, float4* __restrict__ v,
                                                long long n4, float b1, float b2, float eps,
-                                               float step_size, float inv_sqrt_bc2, SegTable st) {
+                                               float step_size, float inv_sqrt_bc2, SegTable st,
+                                               const float2* __restrict__ coef) {
+    if (coef) {
+        const float2 c = *coef;
+        step_size = c.x;
+        inv_sqrt_bc2 = c.y;
+    }
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n4;
          i += (long long)gridDim.x * blockDim.x) {
         float4 pp = p[i], gg = g[i], mm = m[i], vv = v[i];
@@ -61,7 +76,13 @@ __global__ void __launch_bounds__(256) k_adam4(float4* __restrict__ p, const flo
 
 __global__ void k_adam_tail(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
                             float* __restrict__ v, long long start, long long n, float b1, float b2,
-                            float eps, float step_size, float inv_sqrt_bc2, SegTable st) {
+                            float eps, float step_size, float inv_sqrt_bc2, SegTable st,
+                            const float2* __restrict__ coef) {
+    if (coef) {
+        const float2 c = *coef;
+        step_size = c.x;
+        inv_sqrt_bc2 = c.y;
+    }
     for (long long i = start + (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         float pp = p[i], mm = m[i], vv = v[i];
@@ -77,7 +98,8 @@ __global__ void k_adam_tail(float* __restrict__ p, const float* __restrict__ g, 
 
 cudaError_t launch_adam(float* p, const float* g, float* m, float* v, long long n,
                         float b1, float b2, float eps, float step_size, float inv_sqrt_bc2,
-                        const gs_lowp_segment* segs, int n_segs, cudaStream_t s, Prof& pf) {
+                        const gs_lowp_segment* segs, int n_segs, cudaStream_t s, Prof& pf,
+                        long long* step_dev, float lr, float2* coef) {
     SegTable st{};
     st.n = n_segs;
     for (int k = 0; k < n_segs && k < 8; ++k) {
@@ -89,7 +111,9 @@ cudaError_t launch_adam(float* p, const float* g, float* m, float* v, long long 
     const bool aligned = ((reinterpret_cast<uintptr_t>(p) | reinterpret_cast<uintptr_t>(g) |
                            reinterpret_cast<uintptr_t>(m) | reinterpret_cast<uintptr_t>(v)) & 15) == 0;
     long long n4 = aligned ? n / 4 : 0;
-    const int pi = pf.begin(GS_KF_ADAM, s, (n4 > 0) + (4 * n4 < n));
+    const int pi = pf.begin(GS_KF_ADAM, s, (n4 > 0) + (4 * n4 < n) + (step_dev != nullptr));
+    if (step_dev) k_adam_coef<<<1, 1, 0, s>>>(step_dev, lr, b1, b2, coef);
+    const float2* cf = step_dev ? coef : nullptr;
     if (n4 > 0) {
         int dev = 0, sms = 148;
         cudaGetDevice(&dev);
@@ -99,13 +123,13 @@ cudaError_t launch_adam(float* p, const float* g, float* m, float* v, long long 
         if (blocks > cap) blocks = cap;
         k_adam4<<<(unsigned)blocks, 256, 0, s>>>(reinterpret_cast<float4*>(p), reinterpret_cast<const float4*>(g),
                                                  reinterpret_cast<float4*>(m), reinterpret_cast<float4*>(v), n4, b1,
-                                                 b2, eps, step_size, inv_sqrt_bc2, st);
+                                                 b2, eps, step_size, inv_sqrt_bc2, st, cf);
     }
     if (4 * n4 < n) {
         const long long rest = n - 4 * n4;
         const long long blocks = rest < 256 * 1184 ? (rest + 255) / 256 : 1184;
         k_adam_tail<<<(unsigned)blocks, 256, 0, s>>>(p, g, m, v, 4 * n4, n, b1, b2, eps, step_size,
-                                                     inv_sqrt_bc2, st);
+                                                     inv_sqrt_bc2, st, cf);
     }
     pf.end(pi, s);
     return cudaGetLastError();

@@ -19,6 +19,7 @@ struct gs_ctx {
     gsb::Prof prof;
     unsigned int* d_status;           // [0] latched status (negated gs_status), [2..3] pair count
     unsigned long long* d_pairs;      // points into d_status
+    float2* d_adam_coef;              // points into d_status (bytes 64..71)
     char err[512];
 };
 
@@ -372,13 +373,14 @@ int gs_context_create(gs_ctx** out, int device, const gs_config* cfg) {
         delete ctx;
         return GS_ERR_CUDA;
     }
-    if (cudaMalloc(&ctx->d_status, 64) != cudaSuccess) {
+    if (cudaMalloc(&ctx->d_status, 256) != cudaSuccess) {
         cudaGetLastError();
         delete ctx;
         return GS_ERR_OOM;
     }
     ctx->d_pairs = reinterpret_cast<unsigned long long*>(ctx->d_status + 2);
-    if (cudaMemset(ctx->d_status, 0, 64) != cudaSuccess) {
+    ctx->d_adam_coef = reinterpret_cast<float2*>(ctx->d_status + 16);
+    if (cudaMemset(ctx->d_status, 0, 256) != cudaSuccess) {
         cudaFree(ctx->d_status);
         delete ctx;
         return GS_ERR_CUDA;
@@ -542,12 +544,11 @@ int gs_pose_grad(gs_ctx* ctx, const gs_gaussians* g, const gs_view* views, int n
     return gs_render_bwd(ctx, g, views, n_views, ws, T_final, n_contrib, dL_drgb, nullptr, dL_dpose_dev, stream);
 }
 
-int gs_adam_step(gs_ctx* ctx, float* param, const float* grad, float* m, float* v, int64_t n, float lr, float b1,
-                 float b2, float eps, int64_t step, const gs_lowp_segment* segs, int n_segs, gs_stream stream) {
-    if (!ctx) return GS_ERR_INVALID_ARG;
+namespace {
+int check_adam(gs_ctx* ctx, float* param, const float* grad, float* m, float* v, int64_t n, float lr, float b1,
+               float b2, float eps, const gs_lowp_segment* segs, int n_segs) {
     if (!param || !grad || !m || !v) return fail(ctx, GS_ERR_INVALID_ARG, "an Adam buffer is NULL");
     if (n < 0) return fail(ctx, GS_ERR_INVALID_ARG, "n=%lld is negative", (long long)n);
-    if (step < 1) return fail(ctx, GS_ERR_INVALID_ARG, "step=%lld must be >= 1", (long long)step);
     if (!(lr >= 0.f) || !(b1 >= 0.f && b1 < 1.f) || !(b2 >= 0.f && b2 < 1.f) || !(eps > 0.f))
         return fail(ctx, GS_ERR_INVALID_ARG, "Adam hyper-parameters out of range");
     if (n_segs < 0 || n_segs > 8 || (n_segs > 0 && !segs))
@@ -557,6 +558,16 @@ int gs_adam_step(gs_ctx* ctx, float* param, const float* grad, float* m, float* 
             (segs[k].dtype != GS_F16 && segs[k].dtype != GS_BF16))
             return fail(ctx, GS_ERR_INVALID_ARG, "low-precision segment %d is invalid", k);
     }
+    return GS_OK;
+}
+}  // namespace
+
+int gs_adam_step(gs_ctx* ctx, float* param, const float* grad, float* m, float* v, int64_t n, float lr, float b1,
+                 float b2, float eps, int64_t step, const gs_lowp_segment* segs, int n_segs, gs_stream stream) {
+    if (!ctx) return GS_ERR_INVALID_ARG;
+    int rc = check_adam(ctx, param, grad, m, v, n, lr, b1, b2, eps, segs, n_segs);
+    if (rc) return rc;
+    if (step < 1) return fail(ctx, GS_ERR_INVALID_ARG, "step=%lld must be >= 1", (long long)step);
     if (n == 0) return GS_OK;
     DeviceGuard dg(ctx->device);
     const double bc1 = 1.0 - pow((double)b1, (double)step);
@@ -566,6 +577,21 @@ int gs_adam_step(gs_ctx* ctx, float* param, const float* grad, float* m, float* 
     cudaError_t e = launch_adam(param, grad, m, v, n, b1, b2, eps, step_size, inv_sqrt_bc2, segs, n_segs,
                                 reinterpret_cast<cudaStream_t>(stream), ctx->prof);
     return e == cudaSuccess ? GS_OK : cuda_fail(ctx, e, "gs_adam_step");
+}
+
+int gs_adam_step_dev(gs_ctx* ctx, float* param, const float* grad, float* m, float* v, int64_t n, float lr,
+                     float b1, float b2, float eps, int64_t* step_dev, const gs_lowp_segment* segs, int n_segs,
+                     gs_stream stream) {
+    if (!ctx) return GS_ERR_INVALID_ARG;
+    int rc = check_adam(ctx, param, grad, m, v, n, lr, b1, b2, eps, segs, n_segs);
+    if (rc) return rc;
+    if (!step_dev) return fail(ctx, GS_ERR_INVALID_ARG, "step_dev is NULL");
+    if (n == 0) return GS_OK;
+    DeviceGuard dg(ctx->device);
+    cudaError_t e = launch_adam(param, grad, m, v, n, b1, b2, eps, 0.f, 0.f, segs, n_segs,
+                                reinterpret_cast<cudaStream_t>(stream), ctx->prof,
+                                reinterpret_cast<long long*>(step_dev), lr, ctx->d_adam_coef);
+    return e == cudaSuccess ? GS_OK : cuda_fail(ctx, e, "gs_adam_step_dev");
 }
 
 int gs_sync_status(gs_ctx* ctx, gs_stream stream, uint64_t* pairs_needed) {

@@ -183,7 +183,13 @@ class WindowOptimizer:
         self._grads = self.win.grad_tensors()
         self._segs = self.win.segments()
 
+        self.graph = None
+        self.step_dev = None
+
     def step(self, count=None):
+        """One iteration through the C ABI (host-issued launches)."""
+        if self.graph is not None:
+            return self.replay()
         w, r = self.win, self.r
         r.forward(self._g, count=count)
         r.l1(self.targets)
@@ -192,6 +198,31 @@ class WindowOptimizer:
         r.ctx.adam_step(w.flat, w.gflat, w.m, w.v, self.lr, self.betas[0], self.betas[1], self.eps,
                         w.step_count, self._segs)
         return r.loss
+
+    def capture(self):
+        """Captures one iteration in a CUDA graph (the workspace must already
+        be sized, i.e. after one step).  Later `step()` calls replay it; the
+        Adam step count lives on the device, and a pair-capacity overflow is
+        latched and reported by `r.check_status()`."""
+        w, r = self.win, self.r
+        if not r._counted:
+            raise RuntimeError("run one step before capturing (sizes the pair workspace)")
+        self.step_dev = torch.tensor([w.step_count], dtype=torch.int64, device=w.device)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            r.forward(self._g, count=False)
+            r.l1(self.targets)
+            r.backward(self._g, r.dL_drgb, grads=self._grads)
+            r.ctx.adam_step_dev(w.flat, w.gflat, w.m, w.v, self.lr, self.betas[0], self.betas[1], self.eps,
+                                self.step_dev, self._segs)
+        self.graph = g
+        return g
+
+    def replay(self):
+        self.graph.replay()
+        self.win.step_count += 1
+        return self.r.loss
 
 
 class _Rasterize(torch.autograd.Function):
