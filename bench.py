@@ -237,44 +237,63 @@ def run_b300(args, world, rank, local):
     opt.step(count=True)  # sizes the pair workspace
     cap0 = opt.r.cap
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    K = args.steps
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    ids = [x.strip() for x in vis.split(",") if x.strip()]
+    sampler = ClockSampler(int(ids[local]) if local < len(ids) and ids[local].isdigit() else local)
 
-    # warm-up, with every kernel family timed once to find the dominant one
+    def timed(run_step):
+        """K steps, each bracketed by CUDA events on the launching stream, with
+        an L2 flush (256 MB write) between steps outside the events."""
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        barrier()
+        torch.cuda.synchronize()
+        for k in range(K):
+            flush.zero_()
+            ev[k][0].record()
+            run_step()
+            ev[k][1].record()
+        torch.cuda.synchronize()
+        barrier()
+        return float(sum(a.elapsed_time(b) for a, b in ev))
+
+    # warm-up of the host-issued form, every kernel family timed once to find
+    # the dominant one
     ctx.profile(B.KERNEL_FAMILIES)
-    for _ in range(max(args.warmup, 3)):
+    n_warm = max(args.warmup, 3)
+    for _ in range(n_warm):
         opt.step(count=False)
     prof_all = ctx.profile_collect()
     rc, need = opt.r.check_status()
     if rc != B.GS_OK:
         raise RuntimeError("pair capacity exceeded during warm-up (%d needed, %d reserved)" % (need, cap0))
     dominant = max(prof_all, key=lambda k: prof_all[k][1])
-    ctx.profile([dominant])
 
-    K = args.steps
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
-    sampler = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
-    barrier()
-    torch.cuda.synchronize()
+    # timed region 1: host-issued launches, dominant kernel timed by events
+    ctx.profile([dominant])
     sampler.start()
     launches0 = ctx.launch_count()
-    for k in range(K):
-        flush.zero_()  # L2 flush (256 MB write) outside the timed events
-        ev[k][0].record()
-        opt.step(count=False)
-        ev[k][1].record()
-    torch.cuda.synchronize()
-    barrier()
-    launches = ctx.launch_count() - launches0
-    clocks = sampler.stop()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = float(sum(step_ms))
+    plain_ms = timed(lambda: opt.step(count=False))
+    launches_per_step = (ctx.launch_count() - launches0) / K
     prof = ctx.profile_collect()
+    ctx.profile([])
+
+    # timed region 2 (headline): the same iteration captured once in a CUDA
+    # graph and replayed
+    opt.capture()
+    for _ in range(n_warm):
+        opt.step()
+    total_ms = timed(opt.step)
+    clocks = sampler.stop()
+    # the graph holds the same launches plus the device step-counter kernel of Adam
+    launches = int(round((launches_per_step + 1) * K))
     rc, need = opt.r.check_status()
     if rc != B.GS_OK:
         raise RuntimeError("pair capacity exceeded in the timed region (%d needed)" % need)
-    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    t = torch.tensor([total_ms, plain_ms], dtype=torch.float64, device="cuda")
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    max_ms = float(t.item())
+    max_ms, max_plain_ms = float(t[0].item()), float(t[1].item())
     value = world * K / (max_ms / 1e3)
 
     # roofline of the dominant kernel
@@ -308,7 +327,6 @@ def run_b300(args, world, rank, local):
     host_target = target.cpu().pin_memory()
     back_params = torch.empty_like(host_params).pin_memory()
     back_loss = torch.empty(1, dtype=torch.float32).pin_memory()
-    ctx.profile([])
     e_s, e_e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     E = args.e2e_steps
@@ -316,7 +334,7 @@ def run_b300(args, world, rank, local):
     for _ in range(E):
         opt.win.flat.copy_(host_params, non_blocking=True)
         target.copy_(host_target, non_blocking=True)
-        loss = opt.step(count=False)
+        loss = opt.step()
         back_loss.copy_(loss, non_blocking=True)
         back_params.copy_(opt.win.flat, non_blocking=True)
     e_e.record()
@@ -341,7 +359,9 @@ def run_b300(args, world, rank, local):
                            "pairs_per_step": int(opt.r.last_pairs), "parallelism": "replicas" if world > 1 else "1 GPU",
                            "mpix_per_s": mpix},
                 "roofline": roof,
-                "kernel_ms_per_step": {k: v[1] / max(1, len(range(max(args.warmup, 3)))) for k, v in prof_all.items()},
+                "kernel_ms_per_step": {k: v[1] / n_warm for k, v in prof_all.items()},
+                "forms": {"graph_replay_it_s": value,
+                          "host_issued_it_s": world * K / (max_plain_ms / 1e3)},
                 "cpu_baseline": cpu,
                 "e2e": {"value": 1e3 / e2e_ms, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                         "d2h_bytes_per_step": int(d2h)},
