@@ -285,6 +285,29 @@ GS_API int gs_adam_step_dev(gs_ctx* ctx, float* param, const float* grad, float*
                             float lr, float b1, float b2, float eps, int64_t* step_dev,
                             const gs_lowp_segment* segs, int n_segs, gs_stream stream);
 
+/* L1 loss that allocates nothing and needs no context or workspace.  The
+ * paper has no counterpart: this entry point exists for callers that cannot
+ * allocate device memory, such as a real-time loop that allocates nothing
+ * after start-up so that no allocation can stall or fail mid-run, or a host
+ * framework that owns every device allocation itself.
+ * It computes what gs_l1_loss computes (same arguments, without ctx and ws),
+ * on the current CUDA device.  Its per-block partial sums live in a fixed
+ * 1 MiB array inside the library's device memory (loaded on every GPU that
+ * uses the library and kept until the process exits), so
+ *   n_views * ceil(3 * max_v(W_v * H_v) / 1024) <= 262144
+ * is required, e.g. 64 views of 1280 x 1024; larger batches return
+ * GS_ERR_CAPACITY with a message in msg.  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress); make that first call
+ * before any stream capture on that device.  All calls on a device share the
+ * array: calls whose work overlaps on the GPU (for instance on two streams)
+ * race and must be ordered by the caller.  Each call rewrites every slot it
+ * reads, so nothing needs clearing between calls.
+ * msg: NULL or a host buffer of msg_len bytes that receives an error text.
+ * Errors: GS_ERR_INVALID_ARG, GS_ERR_CAPACITY, GS_ERR_CUDA. */
+GS_API int gs_l1_loss_noalloc(const gs_view* views, int n_views, const float* rgb, const float* target,
+                              float* dL_drgb, float* loss_dev, gs_stream stream, char* msg,
+                              size_t msg_len);
+
 /* Synchronises `stream`, returns and clears the latched device status
  * (GS_OK or GS_ERR_CAPACITY); pairs_needed (nullable, host) receives the
  * pair count of the last gs_bin on this context. */

@@ -32,7 +32,8 @@ _DTYPE = {torch.float32: GS_F32, torch.float16: GS_F16, torch.bfloat16: GS_BF16}
 EXPORTED = ["gs_config_default", "gs_version", "gs_context_create", "gs_context_destroy", "gs_last_error",
             "gs_get_config", "gs_workspace_query", "gs_workspace_layout", "gs_project", "gs_bin",
             "gs_render_fwd", "gs_l1_loss", "gs_render_bwd", "gs_pose_grad", "gs_adam_step", "gs_sync_status",
-            "gs_profile_enable", "gs_profile_collect", "gs_launch_count", "gs_adam_step_dev"]
+            "gs_profile_enable", "gs_profile_collect", "gs_launch_count", "gs_adam_step_dev",
+            "gs_l1_loss_noalloc"]
 
 KERNEL_FAMILIES = ["project", "depth_sort", "tile_scan", "emit", "tile_sort", "ranges", "raster_fwd", "l1",
                    "raster_bwd", "project_bwd", "adam"]
@@ -126,6 +127,7 @@ def lib():
         L.gs_adam_step_dev.argtypes = [P, P, P, P, P, I64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                        ctypes.c_float, P, ctypes.POINTER(LowpSegment), I, P]
         L.gs_sync_status.argtypes = [P, P, ctypes.POINTER(ctypes.c_uint64)]
+        L.gs_l1_loss_noalloc.argtypes = [ctypes.POINTER(View), I, P, P, P, P, P, ctypes.c_char_p, ctypes.c_size_t]
         L.gs_profile_enable.argtypes = [P, ctypes.c_uint32]
         L.gs_profile_collect.argtypes = [P, P, ctypes.POINTER(ProfileEntry), I, ctypes.POINTER(ctypes.c_int)]
         L.gs_launch_count.argtypes = [P]

@@ -88,6 +88,17 @@ int fail(gs_ctx* ctx, int code, const char* fmt, ...) {
     return code;
 }
 
+// Error text into a caller-supplied buffer (for entry points without a context).
+int fail_msg(char* msg, size_t len, int code, const char* fmt, ...) {
+    if (msg && len) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(msg, len, fmt, ap);
+        va_end(ap);
+    }
+    return code;
+}
+
 struct DeviceGuard {
     int prev = -1;
     bool ok = true;
@@ -501,6 +512,32 @@ int gs_l1_loss(gs_ctx* ctx, const gs_view* views, int n_views, const gs_workspac
     const WsPtrs wp = ws_ptrs(ws, L, bp.total_tiles);
     cudaError_t e = launch_l1(bp, wp, rgb, target, dL_drgb, loss_dev, reinterpret_cast<cudaStream_t>(stream), ctx->prof);
     return e == cudaSuccess ? GS_OK : cuda_fail(ctx, e, "gs_l1_loss");
+}
+
+int gs_l1_loss_noalloc(const gs_view* views, int n_views, const float* rgb, const float* target, float* dL_drgb,
+                       float* loss_dev, gs_stream stream, char* msg, size_t msg_len) {
+    if (msg && msg_len) msg[0] = 0;
+    if (!rgb || !target || !dL_drgb) return fail_msg(msg, msg_len, GS_ERR_INVALID_ARG, "an image pointer is NULL");
+    if (!views || n_views < 1 || n_views > GS_MAX_VIEWS)
+        return fail_msg(msg, msg_len, GS_ERR_INVALID_ARG, "n_views=%d outside [1, %d] or views is NULL", n_views,
+                        GS_MAX_VIEWS);
+    for (int v = 0; v < n_views; ++v)
+        if (views[v].width <= 0 || views[v].height <= 0 || views[v].width > 32768 || views[v].height > 32768)
+            return fail_msg(msg, msg_len, GS_ERR_INVALID_ARG, "view %d: size %dx%d outside [1, 32768]", v,
+                            views[v].width, views[v].height);
+    gs_config cfg;
+    gs_config_default(&cfg);
+    BatchParam bp;
+    make_batch(cfg, views, n_views, bp);
+    const long long need = l1_partials_needed(bp);
+    if (need > l1_scratch_capacity())
+        return fail_msg(msg, msg_len, GS_ERR_CAPACITY,
+                        "gs_l1_loss_noalloc: the batch needs %lld partial sums, the fixed scratch holds %lld", need,
+                        l1_scratch_capacity());
+    cudaError_t e = launch_l1_static(bp, rgb, target, dL_drgb, loss_dev, reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess)
+        return fail_msg(msg, msg_len, GS_ERR_CUDA, "gs_l1_loss_noalloc: %s", cudaGetErrorString(e));
+    return GS_OK;
 }
 
 int gs_render_bwd(gs_ctx* ctx, const gs_gaussians* g, const gs_view* views, int n_views, const gs_workspace* ws,

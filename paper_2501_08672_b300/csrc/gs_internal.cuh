@@ -151,6 +151,10 @@ cudaError_t launch_project_bwd(const BatchParam& bp, const GaussPtrs& g, const R
                                cudaStream_t s, Prof& pf);
 cudaError_t launch_l1(const BatchParam& bp, const WsPtrs& ws, const float* rgb,
                       const float* target, float* dL_drgb, float* loss, cudaStream_t s, Prof& pf);
+long long l1_partials_needed(const BatchParam& bp);
+long long l1_scratch_capacity();
+cudaError_t launch_l1_static(const BatchParam& bp, const float* rgb, const float* target, float* dL_drgb,
+                             float* loss, cudaStream_t s);
 cudaError_t launch_adam(float* p, const float* g, float* m, float* v, long long n,
                         float b1, float b2, float eps, float step_size, float inv_sqrt_bc2,
                         const gs_lowp_segment* segs, int n_segs, cudaStream_t s, Prof& pf,

@@ -18,6 +18,8 @@
 //
 // Unit of work: the visited fragment (pixel, Gaussian) pair.  These kernels
 // are bound by FP32/MUFU issue, not by HBM.
+#include <mutex>
+
 #include "gs_internal.cuh"
 
 namespace gsb {
@@ -398,6 +400,66 @@ cudaError_t launch_l1(const BatchParam& bp, const WsPtrs& ws, const float* rgb, 
     k_l1<<<grid, kL1Threads, 0, s>>>(bp, rgb, target, dL_drgb, ws.partials);
     if (loss) k_l1_finish<<<1, 1024, 0, s>>>(ws.partials, gx * bp.n_views, loss);
     pf.end(pi, s);
+    return cudaGetLastError();
+}
+
+// ---- L1 loss without any allocation --------------------------------------
+//
+// For callers that cannot allocate device memory: its block partial sums live
+// in a fixed array in the library's own device memory instead of a caller
+// workspace.  The array is loaded with the library on every GPU that uses it
+// and kept until the process exits.  Every call on a device shares it, so
+// calls whose launches overlap on that device race; each call writes every
+// slot it later reads, so nothing has to be cleared between calls.
+
+constexpr long long kL1ScratchFloats = 1ll << 18;  // 1 MiB of FP32 partial sums
+constexpr int kL1ScratchDevices = 64;
+
+static __device__ __align__(256) float g_l1_scratch[kL1ScratchFloats];
+
+namespace {
+std::mutex g_l1_scratch_mu;
+void* g_l1_scratch_ptr[kL1ScratchDevices] = {};
+}  // namespace
+
+long long l1_partials_needed(const BatchParam& bp) {
+    long long max_px = 0;
+    for (int v = 0; v < bp.n_views; ++v) {
+        const long long px = (long long)bp.v[v].W * bp.v[v].H;
+        if (px > max_px) max_px = px;
+    }
+    return (long long)l1_grid_x(max_px) * bp.n_views;
+}
+
+long long l1_scratch_capacity() { return kL1ScratchFloats; }
+
+cudaError_t launch_l1_static(const BatchParam& bp, const float* rgb, const float* target, float* dL_drgb,
+                             float* loss, cudaStream_t s) {
+    const long long need = l1_partials_needed(bp);
+    if (need > kL1ScratchFloats) return cudaErrorInvalidValue;  // the caller checks this first
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kL1ScratchDevices) return cudaErrorInvalidDevice;
+    void* ptr = nullptr;
+    {
+        // First use on this device (which is current): host code only knows a
+        // stand-in for the array, so look up its device address once.
+        std::lock_guard<std::mutex> lock(g_l1_scratch_mu);
+        if (!g_l1_scratch_ptr[dev]) {
+            e = cudaGetSymbolAddress(&g_l1_scratch_ptr[dev], g_l1_scratch);
+            if (e != cudaSuccess) {
+                g_l1_scratch_ptr[dev] = nullptr;
+                return e;
+            }
+        }
+        ptr = g_l1_scratch_ptr[dev];
+    }
+    float* partials = static_cast<float*>(ptr);
+    const int gx = (int)(need / bp.n_views);
+    dim3 grid(gx, bp.n_views);
+    k_l1<<<grid, kL1Threads, 0, s>>>(bp, rgb, target, dL_drgb, partials);
+    if (loss) k_l1_finish<<<1, 1024, 0, s>>>(partials, (int)need, loss);
     return cudaGetLastError();
 }
 
