@@ -31,6 +31,7 @@ namespace {
 // so a warp covers a compact block of rows.  Records are staged kBatch at a
 // time (each thread loads kBatch / threads of them).
 constexpr int kBatch = 256;
+constexpr int kGroup = 4;  // Gaussians per warp reduction in the backward
 
 template <int TS, int PPT>
 __global__ void __launch_bounds__(TS * TS / PPT) k_render_fwd(const __grid_constant__ BatchParam bp,
@@ -222,62 +223,102 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_render_bwd(const __grid_const
             }
         }
         __syncthreads();
-        for (int j = 0; j < cnt; ++j) {
-            const int rel = hi - 1 - j;
-            const float4 a = s_a[j];
-            const float4 b = s_b[j];
-            const float2 c = s_c[j];
-            const float dx = fx - a.x;
-            const float u1 = dx * a.z, u2 = dx * b.x;
-            float v[kGrad2D];
+        for (int j0 = 0; j0 < cnt; j0 += kGroup) {
+            // contributions of kGroup consecutive Gaussians, summed over this
+            // thread's pixels: v[g][e] (e indexes the 9 accumulators)
+            float v[kGroup][kGrad2D];
 #pragma unroll
-            for (int e = 0; e < kGrad2D; ++e) v[e] = 0.f;
+            for (int g = 0; g < kGroup; ++g)
+#pragma unroll
+                for (int e = 0; e < kGrad2D; ++e) v[g][e] = 0.f;
             bool any = false;
 #pragma unroll
-            for (int k = 0; k < PPT; ++k) {
-                if (rel >= nc[k]) continue;
-                const float dy = fy[k] - a.y;
-                const float t1 = fmaf(dy, a.w, u1);
-                const float t2 = fmaf(dy, b.y, u2);
-                const float p = fmaf(-t1, t1, fmaf(-t2, t2, b.z));
-                if (p < rc.log2_alpha_min) continue;
-                any = true;
-                const float araw = ex2_approx(p);
-                const float alpha = fminf(rc.alpha_max, araw);
-                T[k] = __fdividef(T[k], 1.f - alpha);
-                const float w = alpha * T[k];
-                v[6] = fmaf(w, g0[k], v[6]);
-                v[7] = fmaf(w, g1[k], v[7]);
-                v[8] = fmaf(w, g2[k], v[8]);
-                const float d0 = b.w - R0[k], d1 = c.x - R1[k], d2 = c.y - R2[k];
-                const float dalpha = T[k] * (g0[k] * d0 + g1[k] * d1 + g2[k] * d2);
-                R0[k] = fmaf(alpha, d0, R0[k]);
-                R1[k] = fmaf(alpha, d1, R1[k]);
-                R2[k] = fmaf(alpha, d2, R2[k]);
-                const float ga = araw < rc.alpha_max ? dalpha * araw : 0.f;
-                // dp/dq = 2 ((d.v1) v1 + (d.v2) v2)
-                const float gg = 2.f * ga;
-                v[0] = fmaf(gg, fmaf(t1, a.z, t2 * b.x), v[0]);
-                v[1] = fmaf(gg, fmaf(t1, a.w, t2 * b.y), v[1]);
-                const float gdx = ga * dx;
-                v[2] = fmaf(gdx, dx, v[2]);
-                v[3] = fmaf(gdx, dy, v[3]);
-                v[4] = fmaf(ga * dy, dy, v[4]);
-                v[5] += ga;
+            for (int g = 0; g < kGroup; ++g) {
+                const int j = j0 + g;
+                if (j >= cnt) break;
+                const int rel = hi - 1 - j;
+                const float4 a = s_a[j];
+                const float4 b = s_b[j];
+                const float2 c = s_c[j];
+                const float dx = fx - a.x;
+                const float u1 = dx * a.z, u2 = dx * b.x;
+#pragma unroll
+                for (int k = 0; k < PPT; ++k) {
+                    if (rel >= nc[k]) continue;
+                    const float dy = fy[k] - a.y;
+                    const float t1 = fmaf(dy, a.w, u1);
+                    const float t2 = fmaf(dy, b.y, u2);
+                    const float p = fmaf(-t1, t1, fmaf(-t2, t2, b.z));
+                    if (p < rc.log2_alpha_min) continue;
+                    any = true;
+                    const float araw = ex2_approx(p);
+                    const float alpha = fminf(rc.alpha_max, araw);
+                    T[k] = __fdividef(T[k], 1.f - alpha);
+                    const float w = alpha * T[k];
+                    v[g][6] = fmaf(w, g0[k], v[g][6]);
+                    v[g][7] = fmaf(w, g1[k], v[g][7]);
+                    v[g][8] = fmaf(w, g2[k], v[g][8]);
+                    const float d0 = b.w - R0[k], d1 = c.x - R1[k], d2 = c.y - R2[k];
+                    const float dalpha = T[k] * (g0[k] * d0 + g1[k] * d1 + g2[k] * d2);
+                    R0[k] = fmaf(alpha, d0, R0[k]);
+                    R1[k] = fmaf(alpha, d1, R1[k]);
+                    R2[k] = fmaf(alpha, d2, R2[k]);
+                    const float ga = araw < rc.alpha_max ? dalpha * araw : 0.f;
+                    // dp/dq = 2 ((d.v1) v1 + (d.v2) v2)
+                    const float gg = 2.f * ga;
+                    v[g][0] = fmaf(gg, fmaf(t1, a.z, t2 * b.x), v[g][0]);
+                    v[g][1] = fmaf(gg, fmaf(t1, a.w, t2 * b.y), v[g][1]);
+                    const float gdx = ga * dx;
+                    v[g][2] = fmaf(gdx, dx, v[g][2]);
+                    v[g][3] = fmaf(gdx, dy, v[g][3]);
+                    v[g][4] = fmaf(ga * dy, dy, v[g][4]);
+                    v[g][5] += ga;
+                }
             }
             if (__any_sync(0xffffffffu, any)) {
+                // Reduce-scatter over the warp: the 32 values v[g][e], e < 8,
+                // are halved at each butterfly level (a lane keeps the half
+                // selected by its lane bit and receives its partner's copy of
+                // it), leaving lane l with the warp total of value l, i.e.
+                // component l & 7 of Gaussian l >> 3.
+                float x[32];
 #pragma unroll
-                for (int e = 0; e < kGrad2D; ++e) {
-                    float x = v[e];
+                for (int g = 0; g < kGroup; ++g)
 #pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-                    v[e] = x;
+                    for (int e = 0; e < 8; ++e) x[g * 8 + e] = v[g][e];
+#pragma unroll
+                for (int o = 16, n = 32; o > 0; o >>= 1, n >>= 1) {
+                    const bool upper = (lane & o) != 0;
+#pragma unroll
+                    for (int i = 0; i < n / 2; ++i) {
+                        const float send = upper ? x[i] : x[i + n / 2];
+                        const float keep = upper ? x[i + n / 2] : x[i];
+                        x[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+                    }
                 }
-                if (lane == 0) {
-                    float* dst = grad2d + (size_t)s_r[j] * kGrad2D;
+                // component 8 of the 4 Gaussians: two halving levels leave
+                // lane l with Gaussian l >> 3, then a sum over its 8 lanes
+                float y[kGroup];
 #pragma unroll
-                    for (int e = 0; e < kGrad2D; ++e)
-                        if (v[e] != 0.f) atomicAdd(dst + e, v[e]);
+                for (int g = 0; g < kGroup; ++g) y[g] = v[g][8];
+#pragma unroll
+                for (int o = 16, n = kGroup; o >= 8; o >>= 1, n >>= 1) {
+                    const bool upper = (lane & o) != 0;
+#pragma unroll
+                    for (int i = 0; i < n / 2; ++i) {
+                        const float send = upper ? y[i] : y[i + n / 2];
+                        const float keep = upper ? y[i + n / 2] : y[i];
+                        y[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+                    }
+                }
+                float yb = y[0];
+#pragma unroll
+                for (int o = 4; o > 0; o >>= 1) yb += __shfl_xor_sync(0xffffffffu, yb, o);
+                const int gl = lane >> 3, el = lane & 7;
+                if (j0 + gl < cnt) {
+                    float* dst = grad2d + (size_t)s_r[j0 + gl] * kGrad2D;
+                    if (x[0] != 0.f) atomicAdd(dst + el, x[0]);
+                    if (el == 0 && yb != 0.f) atomicAdd(dst + 8, yb);
                 }
             }
         }
