@@ -248,6 +248,7 @@ WsPtrs ws_ptrs(const gs_workspace* ws, const Layout& L, int total_tiles) {
     p.cap = ws->max_pairs;
     p.scan_blocks = L.scan_blocks;
     p.sorted_buf = sorted_buffer(total_tiles);
+    p.log2_alpha_min = -INFINITY;
     return p;
 }
 
@@ -465,6 +466,7 @@ int gs_bin(gs_ctx* ctx, const gs_view* views, int n_views, const gs_workspace* w
     BatchParam bp;
     make_batch(ctx->cfg, views, n_views, bp);
     WsPtrs wp = ws_ptrs(ws, L, bp.total_tiles);
+    wp.log2_alpha_min = make_rc(ctx->cfg).log2_alpha_min;
     const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     cudaError_t e = launch_bin(bp, wp, ctx->d_status, ctx->d_pairs, s, ctx->prof);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "gs_bin");

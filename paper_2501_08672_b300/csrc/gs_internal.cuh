@@ -86,6 +86,7 @@ struct WsPtrs {
     float* partials;         // reduction scratch
     long long cap;
     int scan_blocks;
+    float log2_alpha_min;    // -inf in exact mode (every tile of the box is reached)
     int sorted_buf;          // which pvals buffer holds the sorted pairs
 };
 
@@ -110,6 +111,41 @@ __device__ __forceinline__ int find_view_by_tile(const BatchParam& bp, int tile)
         if (bp.v[mid].tile_off <= tile) lo = mid; else hi = mid - 1;
     }
     return lo;
+}
+
+// Whether a record's footprint {d : (d.v1)^2 + (d.v2)^2 <= L}, centred at q,
+// reaches the rectangle [x0, x1] x [y0, y1] (pixel centres of a tile): the
+// minimum of the convex quadratic A dx^2 + 2 B dx dy + C dy^2 over the
+// rectangle is 0 when q lies inside, else it lies on one of the four edges,
+// where it is a clamped 1D minimum.  The small relative margin only adds
+// tiles.  Written with explicitly rounded operations so that every caller
+// gets bit-identical answers (the pair count and the pair emission must agree).
+__device__ __forceinline__ bool footprint_hits_rect(float qx, float qy, float4 r0, float4 r1, float L, float x0,
+                                                    float x1, float y0, float y1) {
+    const float ax = __fadd_rn(x0, -qx), bx = __fadd_rn(x1, -qx);
+    const float ay = __fadd_rn(y0, -qy), by = __fadd_rn(y1, -qy);
+    if (ax <= 0.f && bx >= 0.f && ay <= 0.f && by >= 0.f) return true;
+    const float A = __fmaf_rn(r0.z, r0.z, __fmul_rn(r1.x, r1.x));
+    const float B = __fmaf_rn(r0.z, r0.w, __fmul_rn(r1.x, r1.y));
+    const float C = __fmaf_rn(r0.w, r0.w, __fmul_rn(r1.y, r1.y));
+    auto q2 = [&](float dx, float dy) {
+        return __fmaf_rn(__fmul_rn(A, dx), dx, __fmaf_rn(__fmul_rn(2.f, __fmul_rn(B, dx)), dy, __fmul_rn(__fmul_rn(C, dy), dy)));
+    };
+    float best = 3.0e38f;
+    // horizontal edges (dy fixed): minimiser dx = -B dy / A
+    const float ys[2] = {ay, by};
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const float dx = fminf(fmaxf(__fdiv_rn(__fmul_rn(-B, ys[k]), A), ax), bx);
+        best = fminf(best, q2(dx, ys[k]));
+    }
+    const float xs[2] = {ax, bx};
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const float dy = fminf(fmaxf(__fdiv_rn(__fmul_rn(-B, xs[k]), C), ay), by);
+        best = fminf(best, q2(xs[k], dy));
+    }
+    return best <= __fmaf_rn(L, 1.001f, 1e-3f);
 }
 
 // ---- host-side launch accounting and optional event timing ---------------

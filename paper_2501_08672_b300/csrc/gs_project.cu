@@ -226,18 +226,39 @@ __global__ void __launch_bounds__(256) k_project(const __grid_constant__ BatchPa
         const float s1 = sqrtf(0.5f * kLog2e / l1), s2 = sqrtf(0.5f * kLog2e / l2);
         r0 = make_float4(qx, qy, ex0 * s1, ex1 * s1);
         r1 = make_float4(-ex1 * s2, ex0 * s2, log2f(sigma), col[0]);
-        r2 = make_float4(col[1], col[2], P.pc[2], 0.f);
+        // half-extents of the footprint's bounding box, rounded up to FP16, for
+        // the raster kernels' per-warp culling (full image in exact mode)
+        float hx = 65504.f, hy = 65504.f;
+        if (rc.alpha_min > 0.f) {
+            const float r2v = 2.f * logf(sigma / rc.alpha_min) * 1.001f;
+            hx = fminf(sqrtf(r2v * P.a) + 0.5f, 65504.f);
+            hy = fminf(sqrtf(r2v * P.c) + 0.5f, 65504.f);
+        }
+        const __half2 ext = __halves2half2(__float2half_ru(hx), __float2half_ru(hy));
+        r2 = make_float4(col[1], col[2], P.pc[2], *reinterpret_cast<const float*>(&ext));
         if (lo_x <= hi_x && lo_y <= hi_y) {
             const int ts = bp.tile_size;
             const int tx0 = (int)lo_x / ts, tx1 = (int)hi_x / ts + 1;
             const int ty0 = (int)lo_y / ts, ty1 = (int)hi_y / ts + 1;
             rect.x = tx0 | (ty0 << 16);
             rect.y = tx1 | (ty1 << 16);
-            touched = (uint32_t)((tx1 - tx0) * (ty1 - ty0));
+            // count only the tiles the footprint reaches (the same test k_emit uses)
+            uint32_t hits = 0;
+            if (rc.alpha_min > 0.f) {
+                const float L = r1.z - rc.log2_alpha_min;
+                for (int ty = ty0; ty < ty1; ++ty)
+                    for (int tx = tx0; tx < tx1; ++tx)
+                        hits += footprint_hits_rect(r0.x, r0.y, r0, r1, L, tx * ts + 0.5f, tx * ts + ts - 0.5f,
+                                                    ty * ts + 0.5f, ty * ts + ts - 0.5f);
+            } else {
+                hits = (uint32_t)((tx1 - tx0) * (ty1 - ty0));
+            }
+            touched = hits;
             float zhi, zlo;
             depth_dot2(V, mu, zhi, zlo);
             key_hi = ordered_bits(zhi);
             key_lo = ordered_bits(zlo);
+            if (hits == 0) key_hi = key_lo = 0xFFFFFFFFu;
         }
     }
     ws.rec[3 * r + 0] = r0;

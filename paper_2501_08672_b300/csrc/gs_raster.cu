@@ -31,6 +31,28 @@ namespace {
 // so a warp covers a compact block of rows.  Records are staged kBatch at a
 // time (each thread loads kBatch / threads of them).
 constexpr int kBatch = 256;
+
+// Pixel-centre box of the pixels a warp owns.  A record whose footprint box
+// (centre q, half-extents packed as two FP16 values rounded up) misses it
+// has alpha < alpha_min at every pixel of the warp, so the warp skips it.
+struct WarpBox {
+    float cx, cy, hx, hy;
+    __device__ __forceinline__ bool reaches(float qx, float qy, float ext) const {
+        const __half2 e = *reinterpret_cast<const __half2*>(&ext);
+        return fabsf(qx - cx) <= __low2float(e) + hx && fabsf(qy - cy) <= __high2float(e) + hy;
+    }
+};
+
+__device__ __forceinline__ WarpBox warp_box(int px, int py0, int ppt) {
+    const int x0 = __reduce_min_sync(0xffffffffu, px), x1 = __reduce_max_sync(0xffffffffu, px);
+    const int y0 = __reduce_min_sync(0xffffffffu, py0), y1 = __reduce_max_sync(0xffffffffu, py0 + ppt - 1);
+    WarpBox b;
+    b.cx = 0.5f * (float)(x0 + x1 + 1);
+    b.cy = 0.5f * (float)(y0 + y1 + 1);
+    b.hx = 0.5f * (float)(x1 - x0);
+    b.hy = 0.5f * (float)(y1 - y0);
+    return b;
+}
 constexpr int kGroup = 4;  // Gaussians per warp reduction in the backward
 
 template <int TS, int PPT>
@@ -47,6 +69,7 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_render_fwd(const __grid_const
     __shared__ float4 s_a[kBatch];
     __shared__ float4 s_b[kBatch];
     __shared__ float2 s_c[kBatch];
+    __shared__ float s_e[kBatch];
     const int t = threadIdx.x;
     const int tile = blockIdx.x;
     const ViewParam& V = bp.v[find_view_by_tile(bp, tile)];
@@ -55,6 +78,7 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_render_fwd(const __grid_const
     const int px = tx * TS + (t % TS);
     const int py0 = ty * TS + (t / TS) * PPT;
     const float fx = px + 0.5f;
+    const WarpBox wb = warp_box(px, py0, PPT);
     float fy[PPT], T[PPT], C0[PPT], C1[PPT], C2[PPT];
     uint32_t last[PPT], used[PPT];
     bool done[PPT];
@@ -84,6 +108,7 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_render_fwd(const __grid_const
                 s_b[slot] = rec[3 * r + 1];
                 const float4 c = rec[3 * r + 2];
                 s_c[slot] = make_float2(c.x, c.y);
+                s_e[slot] = c.w;
             }
         }
         __syncthreads();
@@ -91,6 +116,7 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_render_fwd(const __grid_const
             const int cnt = min((uint32_t)kBatch, rg.y - start);
             for (int j = 0; j < cnt; ++j) {
                 const float4 a = s_a[j];
+                if (!wb.reaches(a.x, a.y, s_e[j])) continue;  // warp-uniform
                 const float4 b = s_b[j];
                 const float2 c = s_c[j];
                 const float dx = fx - a.x;
@@ -160,6 +186,7 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_render_bwd(const __grid_const
     __shared__ float4 s_a[kBatch];
     __shared__ float4 s_b[kBatch];
     __shared__ float2 s_c[kBatch];
+    __shared__ float s_e[kBatch];
     __shared__ uint32_t s_r[kBatch];
     __shared__ uint32_t s_maxnc;
     const int t = threadIdx.x;
@@ -171,6 +198,7 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_render_bwd(const __grid_const
     const int px = tx * TS + (t % TS);
     const int py0 = ty * TS + (t / TS) * PPT;
     const float fx = px + 0.5f;
+    const WarpBox wb = warp_box(px, py0, PPT);
     const uint2 rg = ranges[tile];
     const long long hw = (long long)V.W * V.H;
     const float* gimg = dL_drgb + 3 * V.pix_off;
@@ -220,6 +248,7 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_render_bwd(const __grid_const
                 s_b[slot] = rec[3 * r + 1];
                 const float4 c = rec[3 * r + 2];
                 s_c[slot] = make_float2(c.x, c.y);
+                s_e[slot] = c.w;
             }
         }
         __syncthreads();
@@ -238,6 +267,7 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_render_bwd(const __grid_const
                 if (j >= cnt) break;
                 const int rel = hi - 1 - j;
                 const float4 a = s_a[j];
+                if (!wb.reaches(a.x, a.y, s_e[j])) continue;  // warp-uniform
                 const float4 b = s_b[j];
                 const float2 c = s_c[j];
                 const float dx = fx - a.x;

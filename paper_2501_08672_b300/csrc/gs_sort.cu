@@ -368,13 +368,15 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const uint32_t* __r
 }
 
 // One thread per record in depth order writes its pairs (global tile id,
-// record index) at its scanned offset, row-major over its tile rectangle.
+// record index) at its scanned offset, row-major over the tiles of its
+// rectangle that its footprint reaches (the test k_project counted with).
 __global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ order,
                                               const uint32_t* __restrict__ touched,
                                               const int4* __restrict__ rects,
+                                              const float4* __restrict__ rec,
                                               const unsigned long long* __restrict__ offsets, long long M,
-                                              long long cap, uint32_t* __restrict__ pkeys,
-                                              uint32_t* __restrict__ pvals) {
+                                              long long cap, int ts, float log2_alpha_min,
+                                              uint32_t* __restrict__ pkeys, uint32_t* __restrict__ pvals) {
     const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= M) return;
     const uint32_t r = order[j];
@@ -383,16 +385,31 @@ __global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ order
     const int4 rc = rects[r];
     const int tx0 = rc.x & 0xFFFF, ty0 = (rc.x >> 16) & 0xFFFF;
     const int tx1 = rc.y & 0xFFFF, ty1 = (rc.y >> 16) & 0xFFFF;
-    unsigned long long o = offsets[j];
-    for (int ty = ty0; ty < ty1; ++ty) {
+    const float4 r0 = rec[3 * r], r1 = rec[3 * r + 1];
+    const bool test = log2_alpha_min > -3.0e38f;
+    const float L = r1.z - log2_alpha_min;
+    const unsigned long long o0 = offsets[j];
+    const unsigned long long oend = o0 + tt;
+    unsigned long long o = o0;
+    for (int ty = ty0; ty < ty1 && o < oend; ++ty) {
         const uint32_t row = (uint32_t)rc.z + (uint32_t)ty * (uint32_t)rc.w;
-        for (int tx = tx0; tx < tx1; ++tx, ++o) {
+        for (int tx = tx0; tx < tx1 && o < oend; ++tx) {
+            if (test && !footprint_hits_rect(r0.x, r0.y, r0, r1, L, tx * ts + 0.5f, tx * ts + ts - 0.5f,
+                                             ty * ts + 0.5f, ty * ts + ts - 0.5f))
+                continue;
             if (o < (unsigned long long)cap) {
                 pkeys[o] = row + (uint32_t)tx;
                 pvals[o] = r;
             }
+            ++o;
         }
     }
+    // never reached when both passes agree; keeps the pair list well formed
+    for (; o < oend; ++o)
+        if (o < (unsigned long long)cap) {
+            pkeys[o] = 0xFFFFFFFFu;
+            pvals[o] = r;
+        }
 }
 
 // Tile ranges over the sorted pair keys.
@@ -478,8 +495,9 @@ cudaError_t launch_bin(const BatchParam& bp, WsPtrs& ws, unsigned int* status,
     pf.end(pi, s);
     // 3. expand records into (tile, record) pairs
     pi = pf.begin(GS_KF_EMIT, s);
-    k_emit<<<(unsigned)((M + 255) / 256), 256, 0, s>>>(order, ws.tiles_touched, ws.rect, ws.offsets, M,
-                                                       ws.cap, ws.pkeys[0], ws.pvals[0]);
+    k_emit<<<(unsigned)((M + 255) / 256), 256, 0, s>>>(order, ws.tiles_touched, ws.rect, ws.rec, ws.offsets, M,
+                                                       ws.cap, bp.tile_size, ws.log2_alpha_min, ws.pkeys[0],
+                                                       ws.pvals[0]);
     pf.end(pi, s);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // 4. stable sort of pairs by global tile id
