@@ -149,12 +149,36 @@ def test_forward_is_tile_size_invariant():
         assert torch.equal(T, outs[0][1])
 
 
+def _footprint_min(rec_i, x0, x1, y0, y1):
+    """FP64 minimum of (d.v1)^2 + (d.v2)^2 over the pixel-centre rectangle
+    (d = x - q), from a record's stored axes."""
+    qx, qy = float(rec_i[0]), float(rec_i[1])
+    v1 = rec_i[2:4].astype(np.float64)
+    v2 = rec_i[4:6].astype(np.float64)
+    A = v1[0] ** 2 + v2[0] ** 2
+    B = v1[0] * v1[1] + v2[0] * v2[1]
+    C = v1[1] ** 2 + v2[1] ** 2
+    ax, bx, ay, by = x0 - qx, x1 - qx, y0 - qy, y1 - qy
+    if ax <= 0 <= bx and ay <= 0 <= by:
+        return 0.0
+    f = lambda dx, dy: A * dx * dx + 2 * B * dx * dy + C * dy * dy  # noqa: E731
+    best = np.inf
+    for dy in (ay, by):
+        best = min(best, f(min(max(-B * dy / A, ax), bx), dy))
+    for dx in (ax, bx):
+        best = min(best, f(dx, min(max(-B * dx / C, ay), by)))
+    return best
+
+
 def test_bins_are_sorted_and_complete():
-    """Each tile list holds exactly the records whose tile rectangle contains
-    the tile, ordered by (depth bits, record index)."""
+    """Each record is listed in every tile its alpha >= alpha_min footprint
+    clearly reaches and in no tile it clearly misses (the binning test is
+    exact up to a small margin), tile lists are front to back, and the pair
+    count of each record equals its tiles-touched count."""
     p = scenes.frustum_scene(2500, seed=4)
     views = ragged_views(2500)
-    _, r = gpu_forward(p, views, tile_size=16)
+    ts = 16
+    _, r = gpu_forward(p, views, tile_size=ts)
     L = r.layout()
     M, T = L.n_records, L.n_tiles
     rect = ws_view(r, L.rects, np.int32, 4 * M).reshape(M, 4)
@@ -164,19 +188,32 @@ def test_bins_are_sorted_and_complete():
     npairs = int(r.last_pairs)
     sv = ws_view(r, L.sorted_vals, np.uint32, npairs)
     assert int(touched.sum()) == npairs
-    expect = [[] for _ in range(T)]
+    listed = [set(sv[ranges[t, 0]:ranges[t, 1]].tolist()) for t in range(T)]
+    per_record = np.zeros(M, np.int64)
+    for t in range(T):
+        for i in listed[t]:
+            per_record[i] += 1
+    np.testing.assert_array_equal(per_record, touched.astype(np.int64))
+    log2_amin = math.log2(1.0 / 255.0)
+    checked = 0
     for i in np.nonzero(touched)[0]:
         x0, y0 = rect[i, 0] & 0xFFFF, rect[i, 0] >> 16
         x1, y1 = rect[i, 1] & 0xFFFF, rect[i, 1] >> 16
+        Lim = float(rec[i, 6]) - log2_amin
         for ty in range(y0, y1):
             for tx in range(x0, x1):
-                expect[rect[i, 2] + ty * rect[i, 3] + tx].append(i)
-    # each tile list is the set of records whose rectangle covers it, in the
-    # front-to-back order of the 64-bit depth keys (high words never decrease)
+                t = rect[i, 2] + ty * rect[i, 3] + tx
+                m = _footprint_min(rec[i], tx * ts + 0.5, tx * ts + ts - 0.5, ty * ts + 0.5, ty * ts + ts - 0.5)
+                if m <= Lim * (1 - 1e-4):
+                    assert i in listed[t], "record %d missing from tile %d" % (i, t)
+                    checked += 1
+                elif m > Lim * 1.01 + 0.01:
+                    assert i not in listed[t], "record %d listed in unreached tile %d" % (i, t)
+    assert checked > 1000
+    # front to back: the high words of the 64-bit depth keys never decrease
     hi = ws_view(r, L.depth_hi, np.uint32, M).astype(np.int64)
     for t in range(T):
         got = sv[ranges[t, 0]:ranges[t, 1]].tolist()
-        assert sorted(got) == sorted(expect[t]), "tile %d holds the wrong records" % t
         keys = hi[got]
         assert np.all(keys[1:] >= keys[:-1]), "tile %d is not front to back" % t
 
