@@ -64,7 +64,9 @@ def parse():
     ap.add_argument("--cpu-pixels", type=int, default=128, help="oracle pixels sampled per view")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=10)
-    ap.add_argument("--tile-size", type=int, default=16)
+    ap.add_argument("--tile-size", type=int, default=0, help="0: autotune tile size, pixels per thread, batch")
+    ap.add_argument("--ppt", type=int, default=0)
+    ap.add_argument("--batch", type=int, default=0)
     return ap.parse_args()
 
 
@@ -213,7 +215,7 @@ def run_b300(args, world, rank, local):
     import torch.distributed as dist
     from paper_2501_08672_b300 import binding as B
     from paper_2501_08672_b300 import scenes
-    from paper_2501_08672_b300.render import GaussianWindow, Renderer, WindowOptimizer
+    from paper_2501_08672_b300.render import GaussianWindow, Renderer, WindowOptimizer, autotune
 
     torch.cuda.set_device(local)
     if world > 1:
@@ -226,13 +228,20 @@ def run_b300(args, world, rank, local):
     params, views = workload(seed=rank)
     # target keyframes: render of a perturbed copy of the window
     q = scenes.perturbed_copy(params, seed=1000 + rank)
-    rt = Renderer(views, local, args.tile_size)
+    rt = Renderer(views, local, 16)
     wq = GaussianWindow(q, local)
     rt.forward(wq.struct())
     target = rt.rgb.clone()
     del rt, wq
 
-    opt = WindowOptimizer(params, views, target, lr=LR, device=local, tile_size=args.tile_size)
+    # launch shape: autotuned over the compiled variants unless given
+    tune_table = None
+    if args.tile_size:
+        shape = (args.tile_size, args.ppt, args.batch)
+    else:
+        shape, tune_table = autotune(params, views, target, steps=3, device=local)
+    opt = WindowOptimizer(params, views, target, lr=LR, device=local, tile_size=shape[0],
+                          pixels_per_thread=shape[1], batch=shape[2])
     ctx = opt.r.ctx
     opt.step(count=True)  # sizes the pair workspace
     cap0 = opt.r.cap
@@ -354,7 +363,10 @@ def run_b300(args, world, rank, local):
                 "warmup": args.warmup, "ms_per_step": max_ms / K, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "n_gaussians": N_GAUSS, "views": N_VIEWS,
-                           "image": [W_IMG, H_IMG], "tile_size": args.tile_size, "sh_degree": 1, "lr": LR,
+                           "image": [W_IMG, H_IMG], "tile_size": shape[0], "pixels_per_thread": shape[1],
+                           "batch": shape[2], "sh_degree": 1, "lr": LR,
+                           "autotune_ms": ({"%d/%d/%d" % k: round(v, 4) for k, v in tune_table.items()}
+                                           if tune_table else None),
                            "l2": "flushed between steps (256 MB write outside the timed events)",
                            "pairs_per_step": int(opt.r.last_pairs), "parallelism": "replicas" if world > 1 else "1 GPU",
                            "mpix_per_s": mpix},

@@ -99,6 +99,13 @@ typedef struct gs_config {
     float blur;        /* low-pass term added to the diagonal of Sigma2, px^2 [0.3] */
     float z_near;      /* Gaussians with camera depth <= z_near are culled, m [0.2] */
     float bg[3];       /* background colour [0, 0, 0] */
+    /* Launch shape of the compositing kernels (0 = default).  pixels_per_thread:
+     * 1, 2 for tile 8; 1, 2, 4, 8 for tile 16; 4, 8 for tile 32 [2, 4, 4];
+     * batch: records staged per shared-memory batch, 128 or 256, at least the
+     * threads per tile (tile^2 / pixels_per_thread) [256].  The result does not
+     * depend on them; gs_tune-style autotuning picks the fastest. */
+    int32_t pixels_per_thread;
+    int32_t batch;
 } gs_config;
 
 GS_API void gs_config_default(gs_config* cfg);

@@ -252,10 +252,14 @@ WsPtrs ws_ptrs(const gs_workspace* ws, const Layout& L, int total_tiles) {
     return p;
 }
 
+int default_ppt(int ts) { return ts == 8 ? 2 : 4; }
+
 void make_batch(const gs_config& cfg, const gs_view* views, int n_views, BatchParam& bp) {
     memset(&bp, 0, sizeof(bp));
     bp.n_views = n_views;
     bp.tile_size = cfg.tile_size;
+    bp.ppt = cfg.pixels_per_thread ? cfg.pixels_per_thread : default_ppt(cfg.tile_size);
+    bp.batch = cfg.batch ? cfg.batch : 256;
     long long rec = 0, pix = 0;
     int tiles = 0, maxc = 0;
     for (int v = 0; v < n_views; ++v) {
@@ -336,6 +340,12 @@ int check_config(const gs_config& c, char* msg, size_t n) {
         snprintf(msg, n, "tile_size=%d not in {8, 16, 32}", c.tile_size);
         return GS_ERR_INVALID_ARG;
     }
+    const int ppt = c.pixels_per_thread ? c.pixels_per_thread : default_ppt(c.tile_size);
+    const int batch = c.batch ? c.batch : 256;
+    if (!raster_variant_exists(c.tile_size, ppt, batch)) {
+        snprintf(msg, n, "no compositing kernel for tile %d, %d pixels per thread, batch %d", c.tile_size, ppt, batch);
+        return GS_ERR_INVALID_ARG;
+    }
     if (!(c.alpha_min >= 0.f) || !(c.alpha_max > c.alpha_min) || !(c.alpha_max <= 1.f) || !(c.T_min >= 0.f) ||
         !(c.T_min < 1.f) || !(c.blur >= 0.f) || !(c.z_near > 0.f)) {
         snprintf(msg, n, "config constants out of range");
@@ -362,6 +372,8 @@ void gs_config_default(gs_config* cfg) {
     cfg->blur = 0.3f;
     cfg->z_near = 0.2f;
     cfg->bg[0] = cfg->bg[1] = cfg->bg[2] = 0.f;
+    cfg->pixels_per_thread = 0;
+    cfg->batch = 0;
 }
 
 const char* gs_version(void) { return "gs_b300 0.1 (sm_103a)"; }

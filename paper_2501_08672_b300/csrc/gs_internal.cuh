@@ -38,6 +38,8 @@ struct BatchParam {
     long long total_px;
     int max_count;       // largest g_end - g_begin over views
     int tile_size;
+    int ppt;             // pixels per thread of the raster kernels
+    int batch;           // records staged per shared-memory batch
     ViewParam v[kMaxViews];
 };
 
@@ -120,32 +122,37 @@ __device__ __forceinline__ int find_view_by_tile(const BatchParam& bp, int tile)
 // where it is a clamped 1D minimum.  The small relative margin only adds
 // tiles.  Written with explicitly rounded operations so that every caller
 // gets bit-identical answers (the pair count and the pair emission must agree).
-__device__ __forceinline__ bool footprint_hits_rect(float qx, float qy, float4 r0, float4 r1, float L, float x0,
-                                                    float x1, float y0, float y1) {
-    const float ax = __fadd_rn(x0, -qx), bx = __fadd_rn(x1, -qx);
-    const float ay = __fadd_rn(y0, -qy), by = __fadd_rn(y1, -qy);
+struct Footprint {
+    float qx, qy, A, B, C, nBoA, nBoC, lim;  // nBoA = -B/A, nBoC = -B/C
+};
+
+__device__ __forceinline__ Footprint make_footprint(float4 r0, float4 r1, float L) {
+    Footprint f;
+    f.qx = r0.x;
+    f.qy = r0.y;
+    f.A = __fmaf_rn(r0.z, r0.z, __fmul_rn(r1.x, r1.x));
+    f.B = __fmaf_rn(r0.z, r0.w, __fmul_rn(r1.x, r1.y));
+    f.C = __fmaf_rn(r0.w, r0.w, __fmul_rn(r1.y, r1.y));
+    f.nBoA = __fdiv_rn(-f.B, f.A);
+    f.nBoC = __fdiv_rn(-f.B, f.C);
+    f.lim = __fmaf_rn(L, 1.001f, 1e-3f);
+    return f;
+}
+
+__device__ __forceinline__ bool footprint_hits_rect(const Footprint& f, float x0, float x1, float y0, float y1) {
+    const float ax = __fadd_rn(x0, -f.qx), bx = __fadd_rn(x1, -f.qx);
+    const float ay = __fadd_rn(y0, -f.qy), by = __fadd_rn(y1, -f.qy);
     if (ax <= 0.f && bx >= 0.f && ay <= 0.f && by >= 0.f) return true;
-    const float A = __fmaf_rn(r0.z, r0.z, __fmul_rn(r1.x, r1.x));
-    const float B = __fmaf_rn(r0.z, r0.w, __fmul_rn(r1.x, r1.y));
-    const float C = __fmaf_rn(r0.w, r0.w, __fmul_rn(r1.y, r1.y));
     auto q2 = [&](float dx, float dy) {
-        return __fmaf_rn(__fmul_rn(A, dx), dx, __fmaf_rn(__fmul_rn(2.f, __fmul_rn(B, dx)), dy, __fmul_rn(__fmul_rn(C, dy), dy)));
+        return __fmaf_rn(__fmul_rn(f.A, dx), dx,
+                         __fmaf_rn(__fmul_rn(2.f, __fmul_rn(f.B, dx)), dy, __fmul_rn(__fmul_rn(f.C, dy), dy)));
     };
-    float best = 3.0e38f;
-    // horizontal edges (dy fixed): minimiser dx = -B dy / A
-    const float ys[2] = {ay, by};
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        const float dx = fminf(fmaxf(__fdiv_rn(__fmul_rn(-B, ys[k]), A), ax), bx);
-        best = fminf(best, q2(dx, ys[k]));
-    }
-    const float xs[2] = {ax, bx};
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        const float dy = fminf(fmaxf(__fdiv_rn(__fmul_rn(-B, xs[k]), C), ay), by);
-        best = fminf(best, q2(xs[k], dy));
-    }
-    return best <= __fmaf_rn(L, 1.001f, 1e-3f);
+    // horizontal edges (dy fixed): minimiser dx = -B dy / A; vertical: dy = -B dx / C
+    float best = q2(fminf(fmaxf(__fmul_rn(f.nBoA, ay), ax), bx), ay);
+    best = fminf(best, q2(fminf(fmaxf(__fmul_rn(f.nBoA, by), ax), bx), by));
+    best = fminf(best, q2(ax, fminf(fmaxf(__fmul_rn(f.nBoC, ax), ay), by)));
+    best = fminf(best, q2(bx, fminf(fmaxf(__fmul_rn(f.nBoC, bx), ay), by)));
+    return best <= f.lim;
 }
 
 // ---- host-side launch accounting and optional event timing ---------------
@@ -176,6 +183,7 @@ cudaError_t launch_project(const BatchParam& bp, const GaussPtrs& g, const Rende
                            const WsPtrs& ws, cudaStream_t s, Prof& pf);
 cudaError_t launch_bin(const BatchParam& bp, WsPtrs& ws, unsigned int* status,
                        unsigned long long* status_pairs, cudaStream_t s, Prof& pf);
+bool raster_variant_exists(int ts, int ppt, int batch);
 cudaError_t launch_render_fwd(const BatchParam& bp, const RenderConst& rc, const WsPtrs& ws,
                               float* rgb, float* T_final, uint32_t* n_contrib, uint32_t* n_used,
                               cudaStream_t s, Prof& pf);

@@ -245,11 +245,11 @@ __global__ void __launch_bounds__(256) k_project(const __grid_constant__ BatchPa
             // count only the tiles the footprint reaches (the same test k_emit uses)
             uint32_t hits = 0;
             if (rc.alpha_min > 0.f) {
-                const float L = r1.z - rc.log2_alpha_min;
+                const Footprint fp = make_footprint(r0, r1, r1.z - rc.log2_alpha_min);
                 for (int ty = ty0; ty < ty1; ++ty)
                     for (int tx = tx0; tx < tx1; ++tx)
-                        hits += footprint_hits_rect(r0.x, r0.y, r0, r1, L, tx * ts + 0.5f, tx * ts + ts - 0.5f,
-                                                    ty * ts + 0.5f, ty * ts + ts - 0.5f);
+                        hits += footprint_hits_rect(fp, tx * ts + 0.5f, tx * ts + ts - 0.5f, ty * ts + 0.5f,
+                                                    ty * ts + ts - 0.5f);
             } else {
                 hits = (uint32_t)((tx1 - tx0) * (ty1 - ty0));
             }

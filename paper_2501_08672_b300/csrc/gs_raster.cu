@@ -28,9 +28,8 @@ namespace {
 
 // Thread layout: a TS x TS tile is covered by TS*TS/PPT threads; thread t
 // owns column t % TS and the PPT consecutive rows starting at (t / TS) * PPT,
-// so a warp covers a compact block of rows.  Records are staged kBatch at a
-// time (each thread loads kBatch / threads of them).
-constexpr int kBatch = 256;
+// so a warp covers a compact block of rows.  Records are staged BATCH at a
+// time (each thread loads BATCH / threads of them).
 
 // Pixel-centre box of the pixels a warp owns.  A record whose footprint box
 // (centre q, half-extents packed as two FP16 values rounded up) misses it
@@ -55,7 +54,7 @@ __device__ __forceinline__ WarpBox warp_box(int px, int py0, int ppt) {
 }
 constexpr int kGroup = 4;  // Gaussians per warp reduction in the backward
 
-template <int TS, int PPT>
+template <int TS, int PPT, int BATCH>
 __global__ void __launch_bounds__(TS * TS / PPT) k_render_fwd(const __grid_constant__ BatchParam bp,
                                                               RenderConst rc,
                                                               const float4* __restrict__ rec,
@@ -66,10 +65,10 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_render_fwd(const __grid_const
                                                               uint32_t* __restrict__ n_contrib,
                                                               uint32_t* __restrict__ n_used) {
     constexpr int NT = TS * TS / PPT;
-    __shared__ float4 s_a[kBatch];
-    __shared__ float4 s_b[kBatch];
-    __shared__ float2 s_c[kBatch];
-    __shared__ float s_e[kBatch];
+    __shared__ float4 s_a[BATCH];
+    __shared__ float4 s_b[BATCH];
+    __shared__ float2 s_c[BATCH];
+    __shared__ float s_e[BATCH];
     const int t = threadIdx.x;
     const int tile = blockIdx.x;
     const ViewParam& V = bp.v[find_view_by_tile(bp, tile)];
@@ -93,13 +92,13 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_render_fwd(const __grid_const
     }
     const uint2 rg = ranges[tile];
 
-    for (uint32_t start = rg.x; start < rg.y; start += kBatch) {
+    for (uint32_t start = rg.x; start < rg.y; start += BATCH) {
         bool all = true;
 #pragma unroll
         for (int k = 0; k < PPT; ++k) all = all && done[k];
         if (__syncthreads_count(all) == NT) break;
 #pragma unroll
-        for (int q = 0; q < kBatch / NT; ++q) {
+        for (int q = 0; q < BATCH / NT; ++q) {
             const int slot = q * NT + t;
             const uint32_t idx = start + slot;
             if (idx < rg.y) {
@@ -113,7 +112,7 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_render_fwd(const __grid_const
         }
         __syncthreads();
         if (!all) {
-            const int cnt = min((uint32_t)kBatch, rg.y - start);
+            const int cnt = min((uint32_t)BATCH, rg.y - start);
             for (int j = 0; j < cnt; ++j) {
                 const float4 a = s_a[j];
                 if (!wb.reaches(a.x, a.y, s_e[j])) continue;  // warp-uniform
@@ -172,7 +171,7 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_render_fwd(const __grid_const
 // warp reduces them, and lane 0 adds them with one atomic per component;
 // the factor ln 2 and the conversion to the natural conic happen in the
 // projection backward.
-template <int TS, int PPT>
+template <int TS, int PPT, int BATCH>
 __global__ void __launch_bounds__(TS * TS / PPT) k_render_bwd(const __grid_constant__ BatchParam bp,
                                                               RenderConst rc,
                                                               const float4* __restrict__ rec,
@@ -183,11 +182,11 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_render_bwd(const __grid_const
                                                               const float* __restrict__ dL_drgb,
                                                               float* __restrict__ grad2d) {
     constexpr int NT = TS * TS / PPT;
-    __shared__ float4 s_a[kBatch];
-    __shared__ float4 s_b[kBatch];
-    __shared__ float2 s_c[kBatch];
-    __shared__ float s_e[kBatch];
-    __shared__ uint32_t s_r[kBatch];
+    __shared__ float4 s_a[BATCH];
+    __shared__ float4 s_b[BATCH];
+    __shared__ float2 s_c[BATCH];
+    __shared__ float s_e[BATCH];
+    __shared__ uint32_t s_r[BATCH];
     __shared__ uint32_t s_maxnc;
     const int t = threadIdx.x;
     const int lane = t & 31;
@@ -234,12 +233,12 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_render_bwd(const __grid_const
     // the list.
     const int maxnc = min((int)s_maxnc, (int)(rg.y - rg.x));
 
-    for (int hi = maxnc; hi > 0; hi -= kBatch) {
-        const int lo = hi - kBatch > 0 ? hi - kBatch : 0;
+    for (int hi = maxnc; hi > 0; hi -= BATCH) {
+        const int lo = hi - BATCH > 0 ? hi - BATCH : 0;
         const int cnt = hi - lo;
         __syncthreads();
 #pragma unroll
-        for (int q = 0; q < kBatch / NT; ++q) {
+        for (int q = 0; q < BATCH / NT; ++q) {
             const int slot = q * NT + t;
             if (slot < cnt) {
                 const uint32_t r = svals[rg.x + hi - 1 - slot];
@@ -406,26 +405,37 @@ __global__ void k_l1_finish(const float* __restrict__ partials, int n, float* __
 
 }  // namespace
 
+// Compiled raster variants: (tile size, pixels per thread, staging depth).
+// Threads per CTA = TS * TS / PPT (a multiple of 32); BATCH is a multiple of it.
+#define GS_RASTER_VARIANTS(X) \
+    X(8, 1, 128) X(8, 1, 256) X(8, 2, 128) X(8, 2, 256) \
+    X(16, 1, 256) X(16, 2, 128) X(16, 2, 256) X(16, 4, 128) X(16, 4, 256) X(16, 8, 128) X(16, 8, 256) \
+    X(32, 4, 256) X(32, 8, 128) X(32, 8, 256)
+
+bool raster_variant_exists(int ts, int ppt, int batch) {
+#define GS_X(T, P, B) if (ts == T && ppt == P && batch == B) return true;
+    GS_RASTER_VARIANTS(GS_X)
+#undef GS_X
+    return false;
+}
+
 cudaError_t launch_render_fwd(const BatchParam& bp, const RenderConst& rc, const WsPtrs& ws,
                               float* rgb, float* T_final, uint32_t* n_contrib, uint32_t* n_used,
                               cudaStream_t s, Prof& pf) {
     if (bp.total_tiles <= 0) return cudaSuccess;
     const uint32_t* svals = ws.pvals[ws.sorted_buf];
     const int pi = pf.begin(GS_KF_RASTER_FWD, s);
-    switch (bp.tile_size) {
-        case 8:
-            k_render_fwd<8, 2><<<bp.total_tiles, 32, 0, s>>>(bp, rc, ws.rec, ws.ranges, svals, rgb, T_final, n_contrib, n_used);
-            break;
-        case 16:
-            k_render_fwd<16, 4><<<bp.total_tiles, 64, 0, s>>>(bp, rc, ws.rec, ws.ranges, svals, rgb, T_final, n_contrib, n_used);
-            break;
-        case 32:
-            k_render_fwd<32, 4><<<bp.total_tiles, 256, 0, s>>>(bp, rc, ws.rec, ws.ranges, svals, rgb, T_final, n_contrib, n_used);
-            break;
-        default:
-            return cudaErrorInvalidValue;
+    bool done = false;
+#define GS_X(T, P, B)                                                                                  \
+    if (!done && bp.tile_size == T && bp.ppt == P && bp.batch == B) {                                  \
+        k_render_fwd<T, P, B><<<bp.total_tiles, T * T / P, 0, s>>>(bp, rc, ws.rec, ws.ranges, svals, rgb, \
+                                                                    T_final, n_contrib, n_used);      \
+        done = true;                                                                                   \
     }
+    GS_RASTER_VARIANTS(GS_X)
+#undef GS_X
     pf.end(pi, s);
+    if (!done) return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 
@@ -437,20 +447,17 @@ cudaError_t launch_render_bwd(const BatchParam& bp, const RenderConst& rc, const
     if (e != cudaSuccess || bp.total_tiles <= 0) return e;
     const uint32_t* svals = ws.pvals[ws.sorted_buf];
     const int pi = pf.begin(GS_KF_RASTER_BWD, s);
-    switch (bp.tile_size) {
-        case 8:
-            k_render_bwd<8, 2><<<bp.total_tiles, 32, 0, s>>>(bp, rc, ws.rec, ws.ranges, svals, T_final, n_contrib, dL_drgb, ws.grad2d);
-            break;
-        case 16:
-            k_render_bwd<16, 4><<<bp.total_tiles, 64, 0, s>>>(bp, rc, ws.rec, ws.ranges, svals, T_final, n_contrib, dL_drgb, ws.grad2d);
-            break;
-        case 32:
-            k_render_bwd<32, 4><<<bp.total_tiles, 256, 0, s>>>(bp, rc, ws.rec, ws.ranges, svals, T_final, n_contrib, dL_drgb, ws.grad2d);
-            break;
-        default:
-            return cudaErrorInvalidValue;
+    bool done = false;
+#define GS_X(T, P, B)                                                                                      \
+    if (!done && bp.tile_size == T && bp.ppt == P && bp.batch == B) {                                      \
+        k_render_bwd<T, P, B><<<bp.total_tiles, T * T / P, 0, s>>>(bp, rc, ws.rec, ws.ranges, svals, T_final, \
+                                                                    n_contrib, dL_drgb, ws.grad2d);       \
+        done = true;                                                                                       \
     }
+    GS_RASTER_VARIANTS(GS_X)
+#undef GS_X
     pf.end(pi, s);
+    if (!done) return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 

@@ -387,15 +387,15 @@ __global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ order
     const int tx1 = rc.y & 0xFFFF, ty1 = (rc.y >> 16) & 0xFFFF;
     const float4 r0 = rec[3 * r], r1 = rec[3 * r + 1];
     const bool test = log2_alpha_min > -3.0e38f;
-    const float L = r1.z - log2_alpha_min;
+    const Footprint fp = make_footprint(r0, r1, r1.z - log2_alpha_min);
     const unsigned long long o0 = offsets[j];
     const unsigned long long oend = o0 + tt;
     unsigned long long o = o0;
     for (int ty = ty0; ty < ty1 && o < oend; ++ty) {
         const uint32_t row = (uint32_t)rc.z + (uint32_t)ty * (uint32_t)rc.w;
         for (int tx = tx0; tx < tx1 && o < oend; ++tx) {
-            if (test && !footprint_hits_rect(r0.x, r0.y, r0, r1, L, tx * ts + 0.5f, tx * ts + ts - 0.5f,
-                                             ty * ts + 0.5f, ty * ts + ts - 0.5f))
+            if (test && !footprint_hits_rect(fp, tx * ts + 0.5f, tx * ts + ts - 0.5f, ty * ts + 0.5f,
+                                             ty * ts + ts - 0.5f))
                 continue;
             if (o < (unsigned long long)cap) {
                 pkeys[o] = row + (uint32_t)tx;

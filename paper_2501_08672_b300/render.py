@@ -313,3 +313,41 @@ class PoseTracker:
         gpose = self.iterate(view, target).double().cpu().numpy()
         xi = np.concatenate([-self.eta_rot * gpose[:3], -self.eta_trans * gpose[3:]])
         return apply_left(view, xi), gpose
+
+
+# Compiled launch shapes of the compositing kernels: (tile size, pixels per
+# thread, records per staged batch).  Every one renders the same image.
+RASTER_VARIANTS = [(8, 1, 128), (8, 1, 256), (8, 2, 128), (8, 2, 256),
+                   (16, 1, 256), (16, 2, 128), (16, 2, 256), (16, 4, 128), (16, 4, 256), (16, 8, 128),
+                   (16, 8, 256), (32, 4, 256), (32, 8, 128), (32, 8, 256)]
+
+
+def autotune(params, views, targets, candidates=None, steps=3, device=0, storage=None, verbose=False):
+    """Picks the fastest (tile size, pixels per thread, batch) for this window
+    and batch of views by timing whole optimisation iterations (projection to
+    Adam, lr = 0 so the parameters do not move) with CUDA events on the
+    launching stream.  Returns (best, table) with table[(ts, ppt, batch)] =
+    ms per iteration."""
+    cands = candidates or RASTER_VARIANTS
+    table = {}
+    for ts, ppt, batch in cands:
+        opt = WindowOptimizer(params, views, targets, lr=0.0, device=device, tile_size=ts, storage=storage,
+                              pixels_per_thread=ppt, batch=batch)
+        opt.step(count=True)
+        opt.step(count=False)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        for _ in range(steps):
+            opt.step(count=False)
+        b.record()
+        torch.cuda.synchronize()
+        rc, _ = opt.r.check_status()
+        if rc != B.GS_OK:
+            continue
+        table[(ts, ppt, batch)] = a.elapsed_time(b) / steps
+        if verbose:
+            print("autotune tile %2d ppt %d batch %3d: %.3f ms" % (ts, ppt, batch, table[(ts, ppt, batch)]))
+        del opt
+    best = min(table, key=table.get)
+    return best, table

@@ -137,16 +137,48 @@ def test_forward_matches_oracle_ragged_multiview(orc, ts):
         compare_images(o, img.cpu().numpy(), T.cpu().numpy())
 
 
-def test_forward_is_tile_size_invariant():
+def test_forward_is_launch_shape_invariant():
+    """Every compiled (tile size, pixels per thread, batch) renders the same
+    image bit for bit: each pixel sees the same Gaussians in the same order."""
+    from paper_2501_08672_b300.render import RASTER_VARIANTS
     p = scenes.frustum_scene(4000, seed=3)
     views = ragged_views(4000)
     outs = []
-    for ts in (8, 16, 32):
-        _, r = gpu_forward(p, views, tile_size=ts)
+    for ts, ppt, batch in RASTER_VARIANTS:
+        _, r = gpu_forward(p, views, tile_size=ts, pixels_per_thread=ppt, batch=batch)
         outs.append((r.rgb.clone(), r.T.clone()))
     for rgb, T in outs[1:]:
         assert torch.equal(rgb, outs[0][0])
         assert torch.equal(T, outs[0][1])
+
+
+def test_backward_is_launch_shape_invariant():
+    from paper_2501_08672_b300.render import RASTER_VARIANTS
+    p = scenes.frustum_scene(3000, seed=13)
+    views = ragged_views(3000)
+    ref = None
+    for ts, ppt, batch in RASTER_VARIANTS:
+        win, r = gpu_forward(p, views, tile_size=ts, pixels_per_thread=ppt, batch=batch)
+        w = torch.linspace(-1, 1, r.rgb.numel(), device="cuda")
+        grads = win.grad_tensors()
+        r.backward(win.struct(), w, grads=grads, want_pose=True)
+        torch.cuda.synchronize()
+        g = torch.cat([win.gflat, r.dL_dpose])
+        if ref is None:
+            ref = g.clone()
+        else:
+            assert float((g - ref).norm() / ref.norm()) < 1e-5, (ts, ppt, batch)
+
+
+def test_autotuner_picks_a_compiled_variant():
+    from paper_2501_08672_b300.render import RASTER_VARIANTS, autotune
+    n = 20_000
+    p = scenes.box_room_scene(n, seed=18)
+    views = scenes.arc_views(2, 160, 128, 150.0, n_gaussians=n)
+    _, rt = gpu_forward(p, views)
+    best, table = autotune(p, views, rt.rgb.clone(), candidates=RASTER_VARIANTS[:4] + RASTER_VARIANTS[7:9], steps=1)
+    assert best in RASTER_VARIANTS and len(table) == 6
+    assert table[best] == min(table.values())
 
 
 def _footprint_min(rec_i, x0, x1, y0, y1):
