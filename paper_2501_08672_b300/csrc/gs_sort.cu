@@ -38,10 +38,10 @@ __device__ __forceinline__ unsigned long long clamp_n(unsigned long long n_host,
 //   upsweep:   per-tile digit histogram -> hist[digit * nblk + tile]
 //   scan:      device-wide exclusive scan of hist (digit-major), so the entry
 //              is the first output position of that digit from that tile
-//   downsweep: the tile ranks its keys stably (16 rounds of 256 keys; within
-//              a round, match.any ranks lanes of a warp and per-warp counts
-//              order the warps), stages them digit-sorted in shared memory,
-//              and writes each digit run to consecutive global positions.
+//   downsweep: the tile ranks its keys stably (each warp ranks a contiguous
+//              slice with private digit counters, a scan over warps and
+//              digits places the slices), stages them digit-sorted in shared
+//              memory, and writes each digit run to consecutive positions.
 // The key count may live in device memory (n_dev), so the grid is sized by
 // the capacity and tiles past the count do nothing.
 
@@ -67,14 +67,16 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_upsweep(const uint32_t*
     const unsigned long long n = clamp_n(n_host, n_dev);
     const unsigned long long base = (unsigned long long)blockIdx.x * kRTile;
     const uint32_t mask = (1u << bits) - 1u;
-    const uint32_t lt = lane_lt_mask();
-#pragma unroll 4
+    uint32_t kk[kRItems];
+#pragma unroll
     for (int k = 0; k < kRItems; ++k) {
         const unsigned long long i = base + (unsigned long long)k * kRadixThreads + t;
-        const bool valid = i < n;
-        const uint32_t d = valid ? ((keys[i] >> shift) & mask) : 0x100u;
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
-        if (valid && (peers & lt) == 0) atomicAdd(&wh[w][d], (uint32_t)__popc(peers));
+        kk[k] = i < n ? keys[i] : 0u;
+    }
+#pragma unroll
+    for (int k = 0; k < kRItems; ++k) {
+        const unsigned long long i = base + (unsigned long long)k * kRadixThreads + t;
+        if (i < n) atomicAdd(&wh[w][(kk[k] >> shift) & mask], 1u);
     }
     __syncthreads();
     uint32_t c = 0;
@@ -83,14 +85,22 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_upsweep(const uint32_t*
     hist[(size_t)t * gridDim.x + blockIdx.x] = c;
 }
 
+// Downsweep.  Warp w owns the contiguous slice [w * 512, (w + 1) * 512) of
+// the tile and ranks it in 16 rounds of 32 consecutive keys with counters
+// only it touches: match.any groups equal digits of a round, the group
+// leader reads the running count of its digit and adds the group size, and
+// the group's lanes take consecutive ranks after it.  A scan over the warps
+// per digit and over the digits then places every key stably within the
+// tile, the tile is staged digit-sorted in shared memory and written out in
+// runs of consecutive positions.
 __global__ void __launch_bounds__(kRadixThreads) k_radix_downsweep(
     const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
     uint32_t* __restrict__ vout, unsigned long long n_host, const unsigned long long* n_dev, int shift,
     int bits, const uint32_t* __restrict__ hist) {
+    constexpr int kSlice = kRTile / kRadixWarps;  // 512 keys per warp
     __shared__ uint32_t s_keys[kRTile];
     __shared__ uint32_t s_vals[kRTile];
     __shared__ uint32_t s_wc[kRadixWarps][256];
-    __shared__ uint32_t s_run[256];
     __shared__ uint32_t s_start[256];
     __shared__ uint32_t s_gbase[256];
     __shared__ uint32_t s_wsum[kRadixWarps];
@@ -101,45 +111,44 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_downsweep(
     const int count = (int)(n - base < (unsigned long long)kRTile ? n - base : (unsigned long long)kRTile);
     const uint32_t mask = (1u << bits) - 1u;
     const uint32_t lt = lane_lt_mask();
-    s_run[t] = 0u;
+#pragma unroll
+    for (int ww = 0; ww < kRadixWarps; ++ww) s_wc[ww][t] = 0u;
     s_gbase[t] = hist[(size_t)t * gridDim.x + blockIdx.x];
+    __syncthreads();
 
     uint32_t key[kRItems], val[kRItems], rank[kRItems];
 #pragma unroll
     for (int k = 0; k < kRItems; ++k) {
-        const int j = k * kRadixThreads + t;
+        const int j = w * kSlice + k * 32 + lane;
         key[k] = j < count ? kin[base + j] : 0u;
         val[k] = j < count ? vin[base + j] : 0u;
     }
 #pragma unroll
     for (int k = 0; k < kRItems; ++k) {
-#pragma unroll
-        for (int ww = 0; ww < kRadixWarps; ++ww) s_wc[ww][t] = 0u;
-        __syncthreads();
-        const bool valid = k * kRadixThreads + t < count;
+        const bool valid = w * kSlice + k * 32 + lane < count;
         const uint32_t d = valid ? ((key[k] >> shift) & mask) : 0x100u;
         const uint32_t peers = __match_any_sync(0xffffffffu, d);
-        const uint32_t rw = __popc(peers & lt);
-        if (valid && rw == 0) s_wc[w][d] = __popc(peers);
-        __syncthreads();
-        {
-            uint32_t run = s_run[t];
-#pragma unroll
-            for (int ww = 0; ww < kRadixWarps; ++ww) {
-                const uint32_t c = s_wc[ww][t];
-                s_wc[ww][t] = run;
-                run += c;
-            }
-            s_run[t] = run;
+        const int leader = __ffs(peers) - 1;
+        uint32_t before = 0;
+        if (valid && lane == leader) {
+            before = s_wc[w][d];
+            s_wc[w][d] = before + __popc(peers);
         }
-        __syncthreads();
-        rank[k] = valid ? s_wc[w][d] + rw : 0u;
-        __syncthreads();  // every rank is read before the next round clears s_wc
+        before = __shfl_sync(0xffffffffu, before, leader);
+        rank[k] = before + __popc(peers & lt);
+        __syncwarp();
     }
-    // local digit starts: exclusive scan of the tile's digit counts
+    __syncthreads();
+    // per digit t: offsets of the warps' runs, and the tile's digit count
+    uint32_t total = 0;
+#pragma unroll
+    for (int ww = 0; ww < kRadixWarps; ++ww) {
+        const uint32_t c = s_wc[ww][t];
+        s_wc[ww][t] = total;
+        total += c;
+    }
     {
-        const uint32_t c = s_run[t];
-        uint32_t x = c;
+        uint32_t x = total;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
@@ -149,14 +158,14 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_downsweep(
         __syncthreads();
         uint32_t wp = 0;
         for (int ww = 0; ww < w; ++ww) wp += s_wsum[ww];
-        s_start[t] = wp + x - c;
+        s_start[t] = wp + x - total;
     }
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < kRItems; ++k) {
-        if (k * kRadixThreads + t < count) {
+        if (w * kSlice + k * 32 + lane < count) {
             const uint32_t d = (key[k] >> shift) & mask;
-            const uint32_t pos = s_start[d] + rank[k];
+            const uint32_t pos = s_start[d] + s_wc[w][d] + rank[k];
             s_keys[pos] = key[k];
             s_vals[pos] = val[k];
         }
