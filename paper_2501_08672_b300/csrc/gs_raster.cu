@@ -182,14 +182,24 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_render_bwd(const __grid_const
                                                               const float* __restrict__ dL_drgb,
                                                               float* __restrict__ grad2d) {
     constexpr int NT = TS * TS / PPT;
+    constexpr int NW = NT / 32;
+    // With several warps per tile, each warp parks its warp-reduced values in
+    // its own slot and the tile adds them up before one global atomic per
+    // (record, component): global float atomics, not shuffles, bound this
+    // kernel.  Skipped when the slots would not fit a small shared budget.
+    constexpr bool kTileSum = NW > 1 && NW * BATCH * kGrad2D * 4 <= 20 * 1024;
+    constexpr int kAccW = kTileSum ? NW : 1;
+    constexpr int kAccB = kTileSum ? BATCH : 1;
     __shared__ float4 s_a[BATCH];
     __shared__ float4 s_b[BATCH];
     __shared__ float2 s_c[BATCH];
     __shared__ float s_e[BATCH];
     __shared__ uint32_t s_r[BATCH];
+    __shared__ float s_acc[kAccW][kGrad2D][kAccB];
     __shared__ uint32_t s_maxnc;
     const int t = threadIdx.x;
     const int lane = t & 31;
+    const int warp = t >> 5;
     const int tile = blockIdx.x;
     const ViewParam& V = bp.v[find_view_by_tile(bp, tile)];
     const int lt = tile - V.tile_off;
@@ -249,6 +259,9 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_render_bwd(const __grid_const
                 s_c[slot] = make_float2(c.x, c.y);
                 s_e[slot] = c.w;
             }
+        }
+        if (kTileSum) {
+            for (int i = t; i < kAccW * kGrad2D * kAccB; i += NT) (&s_acc[0][0][0])[i] = 0.f;
         }
         __syncthreads();
         for (int j0 = 0; j0 < cnt; j0 += kGroup) {
@@ -345,10 +358,25 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_render_bwd(const __grid_const
                 for (int o = 4; o > 0; o >>= 1) yb += __shfl_xor_sync(0xffffffffu, yb, o);
                 const int gl = lane >> 3, el = lane & 7;
                 if (j0 + gl < cnt) {
-                    float* dst = grad2d + (size_t)s_r[j0 + gl] * kGrad2D;
-                    if (x[0] != 0.f) atomicAdd(dst + el, x[0]);
-                    if (el == 0 && yb != 0.f) atomicAdd(dst + 8, yb);
+                    if (kTileSum) {
+                        s_acc[kTileSum ? warp : 0][el][kTileSum ? j0 + gl : 0] = x[0];
+                        if (el == 0) s_acc[kTileSum ? warp : 0][8][kTileSum ? j0 + gl : 0] = yb;
+                    } else {
+                        float* dst = grad2d + (size_t)s_r[j0 + gl] * kGrad2D;
+                        if (x[0] != 0.f) atomicAdd(dst + el, x[0]);
+                        if (el == 0 && yb != 0.f) atomicAdd(dst + 8, yb);
+                    }
                 }
+            }
+        }
+        if (kTileSum) {
+            __syncthreads();
+            for (int i = t; i < kGrad2D * cnt; i += NT) {
+                const int e = i / cnt, j = i - e * cnt;
+                float sum = 0.f;
+#pragma unroll
+                for (int ww = 0; ww < kAccW; ++ww) sum += s_acc[ww][e][kTileSum ? j : 0];
+                if (sum != 0.f) atomicAdd(grad2d + (size_t)s_r[j] * kGrad2D + e, sum);
             }
         }
     }
