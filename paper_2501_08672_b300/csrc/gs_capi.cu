@@ -126,7 +126,7 @@ int sorted_buffer(int total_tiles) {
 
 struct Layout {
     gs_ws_layout pub;
-    size_t scan_part, dkeys1, dvals1, pkeys1, pvals1, hist, hist_part, partials;
+    size_t scan_part, dkeys1, dvals1, pkeys1, pvals1, hist, hist_part, partials, okeys0, okeys1, ovals0, ovals1;
     int scan_blocks;
     long long max_g_end;
 };
@@ -169,7 +169,8 @@ int make_layout(gs_ctx* ctx, const gs_config& cfg, const gs_view* views, int n_v
     if (T >= 0x7FFFFFFFll) return fail(ctx, GS_ERR_INVALID_ARG, "too many tiles: %lld", T);
 
     const long long cap = max_pairs;
-    const long long big = M > cap ? M : cap;
+    long long big = M > cap ? M : cap;
+    if (T > big) big = T;
     const long long radix_tiles = (big + 4095) / 4096;      // tiles of the radix sort passes
     const long long hist_parts = (256 * radix_tiles + 4095) / 4096;
     L.scan_blocks = (int)((M + 4095) / 4096);
@@ -200,6 +201,10 @@ int make_layout(gs_ctx* ctx, const gs_config& cfg, const gs_view* views, int n_v
     L.hist = take(sizeof(uint32_t) * 256 * (size_t)(radix_tiles > 0 ? radix_tiles : 1));
     L.hist_part = take(sizeof(uint32_t) * (size_t)(hist_parts + 1));
     W.tile_ranges = take(sizeof(uint2) * (size_t)T);
+    L.okeys0 = take(sizeof(uint32_t) * (size_t)T);
+    L.okeys1 = take(sizeof(uint32_t) * (size_t)T);
+    L.ovals0 = take(sizeof(uint32_t) * (size_t)T);
+    L.ovals1 = take(sizeof(uint32_t) * (size_t)T);
     W.grad2d = take(sizeof(float) * kGrad2D * (size_t)M);
     W.counters = take(sizeof(unsigned long long) * 8);
     L.partials = take(sizeof(float) * (size_t)partials);
@@ -242,6 +247,10 @@ WsPtrs ws_ptrs(const gs_workspace* ws, const Layout& L, int total_tiles) {
     p.hist = reinterpret_cast<uint32_t*>(b + L.hist);
     p.hist_part = reinterpret_cast<uint32_t*>(b + L.hist_part);
     p.ranges = reinterpret_cast<uint2*>(b + L.pub.tile_ranges);
+    p.okeys[0] = reinterpret_cast<uint32_t*>(b + L.okeys0);
+    p.okeys[1] = reinterpret_cast<uint32_t*>(b + L.okeys1);
+    p.ovals[0] = reinterpret_cast<uint32_t*>(b + L.ovals0);
+    p.ovals[1] = reinterpret_cast<uint32_t*>(b + L.ovals1);
     p.grad2d = reinterpret_cast<float*>(b + L.pub.grad2d);
     p.counters = reinterpret_cast<unsigned long long*>(b + L.pub.counters);
     p.partials = reinterpret_cast<float*>(b + L.partials);

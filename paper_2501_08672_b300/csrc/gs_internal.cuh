@@ -83,6 +83,8 @@ struct WsPtrs {
     uint32_t* hist;          // [256 * radix tiles]
     uint32_t* hist_part;     // [radix scan blocks]
     uint2* ranges;           // [T]
+    uint32_t* okeys[2];      // [T] tile-order keys
+    uint32_t* ovals[2];      // [T] tiles, longest list first (buffer 1 after the sort)
     float* grad2d;           // [M][9]
     unsigned long long* counters; // [8]
     float* partials;         // reduction scratch

@@ -59,6 +59,7 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_render_fwd(const __grid_const
                                                               RenderConst rc,
                                                               const float4* __restrict__ rec,
                                                               const uint2* __restrict__ ranges,
+                                                              const uint32_t* __restrict__ tile_order,
                                                               const uint32_t* __restrict__ svals,
                                                               float* __restrict__ rgb,
                                                               float* __restrict__ T_final,
@@ -70,7 +71,7 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_render_fwd(const __grid_const
     __shared__ float2 s_c[BATCH];
     __shared__ float s_e[BATCH];
     const int t = threadIdx.x;
-    const int tile = blockIdx.x;
+    const int tile = (int)tile_order[blockIdx.x];  // longest lists first
     const ViewParam& V = bp.v[find_view_by_tile(bp, tile)];
     const int lt = tile - V.tile_off;
     const int ty = lt / V.tiles_x, tx = lt - ty * V.tiles_x;
@@ -176,6 +177,7 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_render_bwd(const __grid_const
                                                               RenderConst rc,
                                                               const float4* __restrict__ rec,
                                                               const uint2* __restrict__ ranges,
+                                                              const uint32_t* __restrict__ tile_order,
                                                               const uint32_t* __restrict__ svals,
                                                               const float* __restrict__ T_final,
                                                               const uint32_t* __restrict__ n_contrib,
@@ -200,7 +202,7 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_render_bwd(const __grid_const
     const int t = threadIdx.x;
     const int lane = t & 31;
     const int warp = t >> 5;
-    const int tile = blockIdx.x;
+    const int tile = (int)tile_order[blockIdx.x];  // longest lists first
     const ViewParam& V = bp.v[find_view_by_tile(bp, tile)];
     const int lt = tile - V.tile_off;
     const int ty = lt / V.tiles_x, tx = lt - ty * V.tiles_x;
@@ -456,7 +458,7 @@ cudaError_t launch_render_fwd(const BatchParam& bp, const RenderConst& rc, const
     bool done = false;
 #define GS_X(T, P, B)                                                                                  \
     if (!done && bp.tile_size == T && bp.ppt == P && bp.batch == B) {                                  \
-        k_render_fwd<T, P, B><<<bp.total_tiles, T * T / P, 0, s>>>(bp, rc, ws.rec, ws.ranges, svals, rgb, \
+        k_render_fwd<T, P, B><<<bp.total_tiles, T * T / P, 0, s>>>(bp, rc, ws.rec, ws.ranges, ws.ovals[1], svals, rgb, \
                                                                     T_final, n_contrib, n_used);      \
         done = true;                                                                                   \
     }
@@ -478,7 +480,7 @@ cudaError_t launch_render_bwd(const BatchParam& bp, const RenderConst& rc, const
     bool done = false;
 #define GS_X(T, P, B)                                                                                      \
     if (!done && bp.tile_size == T && bp.ppt == P && bp.batch == B) {                                      \
-        k_render_bwd<T, P, B><<<bp.total_tiles, T * T / P, 0, s>>>(bp, rc, ws.rec, ws.ranges, svals, T_final, \
+        k_render_bwd<T, P, B><<<bp.total_tiles, T * T / P, 0, s>>>(bp, rc, ws.rec, ws.ranges, ws.ovals[1], svals, T_final, \
                                                                     n_contrib, dL_drgb, ws.grad2d);       \
         done = true;                                                                                       \
     }

@@ -421,6 +421,26 @@ __global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ order
         }
 }
 
+// Longest-list-first tile order for the compositing launches: key = 255 -
+// (a log-scale code of the list length: 16 steps per octave), one stable
+// 8-bit radix pass, so CTAs of long lists are dispatched first and short ones
+// fill the tail.
+__global__ void k_tile_keys(const uint2* __restrict__ ranges, int n_tiles, uint32_t* __restrict__ keys,
+                            uint32_t* __restrict__ vals) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_tiles) return;
+    const uint2 rg = ranges[i];
+    const uint32_t len = rg.y - rg.x;
+    uint32_t code = 0;
+    if (len) {
+        const int e = 31 - __clz(len);
+        const uint32_t m = e >= 4 ? (len >> (e - 4)) & 15u : (len << (4 - e)) & 15u;
+        code = min(255u, (uint32_t)e * 16u + m);
+    }
+    keys[i] = 255u - code;
+    vals[i] = (uint32_t)i;
+}
+
 // Tile ranges over the sorted pair keys.
 __global__ void k_ranges(const uint32_t* __restrict__ keys, long long cap,
                          const unsigned long long* __restrict__ n_dev, uint32_t n_tiles,
@@ -524,7 +544,13 @@ cudaError_t launch_bin(const BatchParam& bp, WsPtrs& ws, unsigned int* status,
     e = cudaMemsetAsync(ws.ranges, 0, sizeof(uint2) * (size_t)bp.total_tiles, s);
     if (e != cudaSuccess) return e;
     k_ranges<<<1184, 256, 0, s>>>(ws.pkeys[pbuf], ws.cap, ws.counters, (uint32_t)bp.total_tiles, ws.ranges);
+    k_tile_keys<<<(bp.total_tiles + 255) / 256, 256, 0, s>>>(ws.ranges, bp.total_tiles, ws.okeys[0], ws.ovals[0]);
+    pf.count(6);
+    int obuf = 0;
+    e = radix_sort(ws.okeys[0], ws.ovals[0], ws.okeys[1], ws.ovals[1], ws, (unsigned long long)bp.total_tiles,
+                   nullptr, 8, &obuf, s);
     pf.end(pi, s);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
