@@ -124,6 +124,10 @@ __device__ __forceinline__ int find_view_by_tile(const BatchParam& bp, int tile)
 // where it is a clamped 1D minimum.  The small relative margin only adds
 // tiles.  Written with explicitly rounded operations so that every caller
 // gets bit-identical answers (the pair count and the pair emission must agree).
+// Footprints whose bounding rectangle spans more tiles than this are
+// counted and emitted by a whole warp (32 candidate tiles at a time).
+constexpr int kCoopTiles = 8;
+
 struct Footprint {
     float qx, qy, A, B, C, nBoA, nBoC, lim;  // nBoA = -B/A, nBoC = -B/C
 };

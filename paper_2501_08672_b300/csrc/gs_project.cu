@@ -172,11 +172,18 @@ __device__ __forceinline__ uint32_t ordered_bits(float x) {
 __global__ void __launch_bounds__(256) k_project(const __grid_constant__ BatchParam bp, GaussPtrs g,
                                                  RenderConst rc, WsPtrs ws) {
     const ViewParam& V = bp.v[blockIdx.y];
-    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long k0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long cnt = V.g_end - V.g_begin;
-    if (k >= cnt) return;
+    // Threads past the view's count stay alive (on a valid Gaussian) so the
+    // whole warp can share the tile counting of large footprints; they write
+    // nothing.
+    const bool live = k0 < cnt;
+    if (__all_sync(0xffffffffu, !live)) return;
+    const long long k = live ? k0 : 0;
     const long long i = V.g_begin + k;
     const long long r = V.rec_off + k;
+    bool coop = false;  // footprint counted by the whole warp below
+    int area = 0;
 
     float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0;
     int4 rect = make_int4(0, 0, V.tile_off, V.tiles_x);
@@ -244,7 +251,11 @@ __global__ void __launch_bounds__(256) k_project(const __grid_constant__ BatchPa
             rect.y = tx1 | (ty1 << 16);
             // count only the tiles the footprint reaches (the same test k_emit uses)
             uint32_t hits = 0;
-            if (rc.alpha_min > 0.f) {
+            area = (tx1 - tx0) * (ty1 - ty0);
+            coop = live && rc.alpha_min > 0.f && area > kCoopTiles;
+            if (coop) {
+                hits = 0;  // counted cooperatively below
+            } else if (rc.alpha_min > 0.f) {
                 const Footprint fp = make_footprint(r0, r1, r1.z - rc.log2_alpha_min);
                 for (int ty = ty0; ty < ty1; ++ty)
                     for (int tx = tx0; tx < tx1; ++tx)
@@ -258,9 +269,34 @@ __global__ void __launch_bounds__(256) k_project(const __grid_constant__ BatchPa
             depth_dot2(V, mu, zhi, zlo);
             key_hi = ordered_bits(zhi);
             key_lo = ordered_bits(zlo);
-            if (hits == 0) key_hi = key_lo = 0xFFFFFFFFu;
+            if (hits == 0 && !coop) key_hi = key_lo = 0xFFFFFFFFu;
         }
     }
+    // Large footprints: the warp tests their candidate tiles 32 at a time.
+    for (unsigned big = __ballot_sync(0xffffffffu, coop); big; big &= big - 1) {
+        const int src = __ffs(big) - 1;
+        const float4 b0 = make_float4(__shfl_sync(0xffffffffu, r0.x, src), __shfl_sync(0xffffffffu, r0.y, src),
+                                      __shfl_sync(0xffffffffu, r0.z, src), __shfl_sync(0xffffffffu, r0.w, src));
+        const float4 b1 = make_float4(__shfl_sync(0xffffffffu, r1.x, src), __shfl_sync(0xffffffffu, r1.y, src),
+                                      __shfl_sync(0xffffffffu, r1.z, src), __shfl_sync(0xffffffffu, r1.w, src));
+        const int rx = __shfl_sync(0xffffffffu, rect.x, src), ry = __shfl_sync(0xffffffffu, rect.y, src);
+        const int bx0 = rx & 0xFFFF, by0 = (rx >> 16) & 0xFFFF, bx1 = ry & 0xFFFF, by1 = (ry >> 16) & 0xFFFF;
+        const int bw = bx1 - bx0, barea = bw * (by1 - by0);
+        const Footprint fp = make_footprint(b0, b1, b1.z - rc.log2_alpha_min);
+        const int ts = bp.tile_size;
+        const int lane = threadIdx.x & 31;
+        uint32_t c = 0;
+        for (int q = lane; q < barea; q += 32) {
+            const int ty = by0 + q / bw, tx = bx0 + q % bw;
+            c += footprint_hits_rect(fp, tx * ts + 0.5f, tx * ts + ts - 0.5f, ty * ts + 0.5f, ty * ts + ts - 0.5f);
+        }
+        c = __reduce_add_sync(0xffffffffu, c);
+        if (lane == src) {
+            touched = c;
+            if (c == 0) key_hi = key_lo = 0xFFFFFFFFu;
+        }
+    }
+    if (!live) return;
     ws.rec[3 * r + 0] = r0;
     ws.rec[3 * r + 1] = r1;
     ws.rec[3 * r + 2] = r2;

@@ -379,6 +379,8 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const uint32_t* __r
 // One thread per record in depth order writes its pairs (global tile id,
 // record index) at its scanned offset, row-major over the tiles of its
 // rectangle that its footprint reaches (the test k_project counted with).
+// Rectangles of more than kCoopTiles tiles are emitted by the whole warp:
+// 32 candidate tiles at a time, hits compacted in row-major order by ballot.
 __global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ order,
                                               const uint32_t* __restrict__ touched,
                                               const int4* __restrict__ rects,
@@ -386,39 +388,79 @@ __global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ order
                                               const unsigned long long* __restrict__ offsets, long long M,
                                               long long cap, int ts, float log2_alpha_min,
                                               uint32_t* __restrict__ pkeys, uint32_t* __restrict__ pvals) {
-    const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= M) return;
+    const long long j0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = j0 < M;
+    if (__all_sync(0xffffffffu, !live)) return;
+    const long long j = live ? j0 : 0;
     const uint32_t r = order[j];
-    const uint32_t tt = touched[r];
-    if (tt == 0) return;
+    const uint32_t tt = live ? touched[r] : 0u;
     const int4 rc = rects[r];
     const int tx0 = rc.x & 0xFFFF, ty0 = (rc.x >> 16) & 0xFFFF;
     const int tx1 = rc.y & 0xFFFF, ty1 = (rc.y >> 16) & 0xFFFF;
-    const float4 r0 = rec[3 * r], r1 = rec[3 * r + 1];
     const bool test = log2_alpha_min > -3.0e38f;
-    const Footprint fp = make_footprint(r0, r1, r1.z - log2_alpha_min);
+    const int area = (tx1 - tx0) * (ty1 - ty0);
+    const bool coop = tt > 0 && test && area > kCoopTiles;
     const unsigned long long o0 = offsets[j];
     const unsigned long long oend = o0 + tt;
-    unsigned long long o = o0;
-    for (int ty = ty0; ty < ty1 && o < oend; ++ty) {
-        const uint32_t row = (uint32_t)rc.z + (uint32_t)ty * (uint32_t)rc.w;
-        for (int tx = tx0; tx < tx1 && o < oend; ++tx) {
-            if (test && !footprint_hits_rect(fp, tx * ts + 0.5f, tx * ts + ts - 0.5f, ty * ts + 0.5f,
-                                             ty * ts + ts - 0.5f))
-                continue;
-            if (o < (unsigned long long)cap) {
-                pkeys[o] = row + (uint32_t)tx;
+    const unsigned long long ucap = (unsigned long long)cap;
+    if (tt > 0 && !coop) {
+        const float4 r0 = rec[3 * r], r1 = rec[3 * r + 1];
+        const Footprint fp = make_footprint(r0, r1, r1.z - log2_alpha_min);
+        unsigned long long o = o0;
+        for (int ty = ty0; ty < ty1 && o < oend; ++ty) {
+            const uint32_t row = (uint32_t)rc.z + (uint32_t)ty * (uint32_t)rc.w;
+            for (int tx = tx0; tx < tx1 && o < oend; ++tx) {
+                if (test && !footprint_hits_rect(fp, tx * ts + 0.5f, tx * ts + ts - 0.5f, ty * ts + 0.5f,
+                                                 ty * ts + ts - 0.5f))
+                    continue;
+                if (o < ucap) {
+                    pkeys[o] = row + (uint32_t)tx;
+                    pvals[o] = r;
+                }
+                ++o;
+            }
+        }
+        // never reached when both passes agree; keeps the pair list well formed
+        for (; o < oend; ++o)
+            if (o < ucap) {
+                pkeys[o] = 0xFFFFFFFFu;
                 pvals[o] = r;
             }
-            ++o;
-        }
     }
-    // never reached when both passes agree; keeps the pair list well formed
-    for (; o < oend; ++o)
-        if (o < (unsigned long long)cap) {
-            pkeys[o] = 0xFFFFFFFFu;
-            pvals[o] = r;
+    const int lane = threadIdx.x & 31;
+    const uint32_t lt = (1u << lane) - 1u;
+    for (unsigned big = __ballot_sync(0xffffffffu, coop); big; big &= big - 1) {
+        const int src = __ffs(big) - 1;
+        const uint32_t br = __shfl_sync(0xffffffffu, r, src);
+        const int rx = __shfl_sync(0xffffffffu, rc.x, src), ry = __shfl_sync(0xffffffffu, rc.y, src);
+        const uint32_t bz = (uint32_t)__shfl_sync(0xffffffffu, rc.z, src);
+        const uint32_t bwid = (uint32_t)__shfl_sync(0xffffffffu, rc.w, src);
+        const unsigned long long bo0 = __shfl_sync(0xffffffffu, o0, src);
+        const unsigned long long boend = __shfl_sync(0xffffffffu, oend, src);
+        const int bx0 = rx & 0xFFFF, by0 = (rx >> 16) & 0xFFFF, bx1 = ry & 0xFFFF, by1 = (ry >> 16) & 0xFFFF;
+        const int bw = bx1 - bx0, barea = bw * (by1 - by0);
+        const float4 r0 = rec[3 * br], r1 = rec[3 * br + 1];
+        const Footprint fp = make_footprint(r0, r1, r1.z - log2_alpha_min);
+        unsigned long long o = bo0;
+        for (int base = 0; base < barea; base += 32) {
+            const int q = base + lane;
+            const int ty = by0 + q / bw, tx = bx0 + q % bw;
+            const bool hit = q < barea && footprint_hits_rect(fp, tx * ts + 0.5f, tx * ts + ts - 0.5f,
+                                                              ty * ts + 0.5f, ty * ts + ts - 0.5f);
+            const uint32_t m = __ballot_sync(0xffffffffu, hit);
+            const unsigned long long pos = o + __popc(m & lt);
+            if (hit && pos < boend && pos < ucap) {
+                pkeys[pos] = bz + (uint32_t)ty * bwid + (uint32_t)tx;
+                pvals[pos] = br;
+            }
+            o += __popc(m);
         }
+        for (unsigned long long q = o + lane; q < boend; q += 32)
+            if (q < ucap) {
+                pkeys[q] = 0xFFFFFFFFu;
+                pvals[q] = br;
+            }
+    }
 }
 
 // Longest-list-first tile order for the compositing launches: key = 255 -
