@@ -347,7 +347,10 @@ __global__ void __launch_bounds__(256) k_project_bwd(const __grid_constant__ Bat
         if (inview) {
             const float sigma = 1.f / (1.f + expf(-ologit));
             // record-space gradients -> natural parameters (see k_render_bwd):
-            const float gqx = kLn2 * acc[0], gqy = kLn2 * acc[1];
+            // acc[0..1] hold sum ga (d.v1), sum ga (d.v2); dp/dq = 2 ((d.v1) v1 + (d.v2) v2)
+            const float4 ra = ws.rec[3 * r], rb = ws.rec[3 * r + 1];
+            const float gqx = 2.f * kLn2 * fmaf(ra.z, acc[0], rb.x * acc[1]);
+            const float gqy = 2.f * kLn2 * fmaf(ra.w, acc[0], rb.y * acc[1]);
             const float gA = -0.5f * acc[2], gB = -acc[3], gC = -0.5f * acc[4];
             const float gsig = acc[5] / sigma;
             float col[3];

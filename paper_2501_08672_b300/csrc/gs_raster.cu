@@ -26,10 +26,24 @@ namespace gsb {
 
 namespace {
 
-// Thread layout: a TS x TS tile is covered by TS*TS/PPT threads; thread t
-// owns column t % TS and the PPT consecutive rows starting at (t / TS) * PPT,
-// so a warp covers a compact block of rows.  Records are staged BATCH at a
-// time (each thread loads BATCH / threads of them).
+// Thread layout: a TS x TS tile is covered by TS*TS/PPT threads.  A warp
+// covers RPW = 32/TS thread rows, i.e. a block of TS columns x RPW*PPT pixel
+// rows; lane l owns column l % TS and, for its k-th pixel, row
+// k*RPW + l/TS of the warp's block.  The k-th pixels of a warp thus form a
+// compact TS x RPW block, so a footprint edge crossing the warp's block
+// leaves few k with only a handful of active lanes.  Records are staged
+// BATCH at a time (each thread loads BATCH / threads of them).
+template <int TS, int PPT>
+struct PixelMap {
+    static_assert(TS <= 32 && 32 % TS == 0 && (TS * TS / PPT) % 32 == 0, "unsupported launch shape");
+    static constexpr int RPW = 32 / TS;
+    int px, py;  // column, row of pixel 0; pixel k is at row py + k * RPW
+    __device__ __forceinline__ PixelMap(int tx, int ty, int t) {
+        px = tx * TS + (t % TS);
+        py = ty * TS + (t >> 5) * RPW * PPT + (t & 31) / TS;
+    }
+    __device__ __forceinline__ int row(int k) const { return py + k * RPW; }
+};
 
 // Pixel-centre box of the pixels a warp owns.  A record whose footprint box
 // (centre q, half-extents packed as two FP16 values rounded up) misses it
@@ -42,9 +56,9 @@ struct WarpBox {
     }
 };
 
-__device__ __forceinline__ WarpBox warp_box(int px, int py0, int ppt) {
+__device__ __forceinline__ WarpBox warp_box(int px, int py_first, int py_last) {
     const int x0 = __reduce_min_sync(0xffffffffu, px), x1 = __reduce_max_sync(0xffffffffu, px);
-    const int y0 = __reduce_min_sync(0xffffffffu, py0), y1 = __reduce_max_sync(0xffffffffu, py0 + ppt - 1);
+    const int y0 = __reduce_min_sync(0xffffffffu, py_first), y1 = __reduce_max_sync(0xffffffffu, py_last);
     WarpBox b;
     b.cx = 0.5f * (float)(x0 + x1 + 1);
     b.cy = 0.5f * (float)(y0 + y1 + 1);
@@ -75,21 +89,21 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_render_fwd(const __grid_const
     const ViewParam& V = bp.v[find_view_by_tile(bp, tile)];
     const int lt = tile - V.tile_off;
     const int ty = lt / V.tiles_x, tx = lt - ty * V.tiles_x;
-    const int px = tx * TS + (t % TS);
-    const int py0 = ty * TS + (t / TS) * PPT;
+    const PixelMap<TS, PPT> pm(tx, ty, t);
+    const int px = pm.px;
     const float fx = px + 0.5f;
-    const WarpBox wb = warp_box(px, py0, PPT);
+    const WarpBox wb = warp_box(px, pm.row(0), pm.row(PPT - 1));
     float fy[PPT], T[PPT], C0[PPT], C1[PPT], C2[PPT];
     uint32_t last[PPT], used[PPT];
     bool done[PPT];
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
-        fy[k] = py0 + k + 0.5f;
+        fy[k] = pm.row(k) + 0.5f;
         T[k] = 1.f;
         C0[k] = C1[k] = C2[k] = 0.f;
         last[k] = 0;
         used[k] = 0;
-        done[k] = !(px < V.W && py0 + k < V.H);
+        done[k] = !(px < V.W && pm.row(k) < V.H);
     }
     const uint2 rg = ranges[tile];
 
@@ -150,8 +164,8 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_render_fwd(const __grid_const
     float* out = rgb + 3 * V.pix_off;
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
-        if (px < V.W && py0 + k < V.H) {
-            const long long pl = (long long)(py0 + k) * V.W + px;
+        if (px < V.W && pm.row(k) < V.H) {
+            const long long pl = (long long)pm.row(k) * V.W + px;
             out[pl] = C0[k] + T[k] * rc.bg[0];
             out[hw + pl] = C1[k] + T[k] * rc.bg[1];
             out[2 * hw + pl] = C2[k] + T[k] * rc.bg[2];
@@ -167,11 +181,15 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_render_fwd(const __grid_const
 // fragment j and R the light composited behind it (normalised by T),
 //   T_j = T_{j+1} / (1 - alpha_j),   dL/dc_j = alpha_j T_j g,
 //   dL/dalpha_j = T_j g . (c_j - R_j),  R_{j-1} = R_j + alpha_j (c_j - R_j),
-// with R = bg behind the last contributor.  A thread sums its PPT pixels'
-// contributions to the 9 per-record accumulators (see grad2d in gs.h), the
-// warp reduces them, and lane 0 adds them with one atomic per component;
-// the factor ln 2 and the conversion to the natural conic happen in the
-// projection backward.
+// with R = bg behind the last contributor.  With ga = dL/dalpha * 2^p where
+// alpha is not clamped (dL/dp up to the factor ln 2), the 9 per-record
+// accumulators are
+//   sum ga (d.v1), sum ga (d.v2), sum ga dx^2, sum ga dx dy, sum ga dy^2,
+//   sum ga, sum w g_r, sum w g_g, sum w g_b      (w = alpha T),
+// summed over the thread's PPT pixels, reduced over the warp and then the
+// tile, and added with one atomic per component; the factor ln 2, the
+// principal axes and the conversion to the natural conic are applied in
+// the projection backward.
 template <int TS, int PPT, int BATCH>
 __global__ void __launch_bounds__(TS * TS / PPT) k_render_bwd(const __grid_constant__ BatchParam bp,
                                                               RenderConst rc,
@@ -206,10 +224,10 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_render_bwd(const __grid_const
     const ViewParam& V = bp.v[find_view_by_tile(bp, tile)];
     const int lt = tile - V.tile_off;
     const int ty = lt / V.tiles_x, tx = lt - ty * V.tiles_x;
-    const int px = tx * TS + (t % TS);
-    const int py0 = ty * TS + (t / TS) * PPT;
+    const PixelMap<TS, PPT> pm(tx, ty, t);
+    const int px = pm.px;
     const float fx = px + 0.5f;
-    const WarpBox wb = warp_box(px, py0, PPT);
+    const WarpBox wb = warp_box(px, pm.row(0), pm.row(PPT - 1));
     const uint2 rg = ranges[tile];
     const long long hw = (long long)V.W * V.H;
     const float* gimg = dL_drgb + 3 * V.pix_off;
@@ -219,12 +237,12 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_render_bwd(const __grid_const
     uint32_t mine = 0;
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
-        fy[k] = py0 + k + 0.5f;
+        fy[k] = pm.row(k) + 0.5f;
         T[k] = 1.f;
         g0[k] = g1[k] = g2[k] = 0.f;
         nc[k] = 0;
-        if (px < V.W && py0 + k < V.H) {
-            const long long pl = (long long)(py0 + k) * V.W + px;
+        if (px < V.W && pm.row(k) < V.H) {
+            const long long pl = (long long)pm.row(k) * V.W + px;
             T[k] = T_final[V.pix_off + pl];
             nc[k] = (int)n_contrib[V.pix_off + pl];
             g0[k] = gimg[pl];
@@ -308,10 +326,10 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_render_bwd(const __grid_const
                     R1[k] = fmaf(alpha, d1, R1[k]);
                     R2[k] = fmaf(alpha, d2, R2[k]);
                     const float ga = araw < rc.alpha_max ? dalpha * araw : 0.f;
-                    // dp/dq = 2 ((d.v1) v1 + (d.v2) v2)
-                    const float gg = 2.f * ga;
-                    v[g][0] = fmaf(gg, fmaf(t1, a.z, t2 * b.x), v[g][0]);
-                    v[g][1] = fmaf(gg, fmaf(t1, a.w, t2 * b.y), v[g][1]);
+                    // dp/dq = 2 ((d.v1) v1 + (d.v2) v2) with v1, v2 fixed per
+                    // record: only ga (d.v1), ga (d.v2) are summed here
+                    v[g][0] = fmaf(ga, t1, v[g][0]);
+                    v[g][1] = fmaf(ga, t2, v[g][1]);
                     const float gdx = ga * dx;
                     v[g][2] = fmaf(gdx, dx, v[g][2]);
                     v[g][3] = fmaf(gdx, dy, v[g][3]);
