@@ -79,12 +79,23 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_render_fwd(const __grid_const
                                                               float* __restrict__ T_final,
                                                               uint32_t* __restrict__ n_contrib,
                                                               uint32_t* __restrict__ n_used) {
+    // Each warp walks the tile's list on its own: per step every lane fetches
+    // Q records, the records whose footprint box reaches the warp's pixels
+    // are compacted (in list order) into the warp's shared slots, and the
+    // warp composites only those.  No block barrier: a warp whose pixels
+    // are all saturated stops without waiting for the others.
     constexpr int NT = TS * TS / PPT;
-    __shared__ float4 s_a[BATCH];
-    __shared__ float4 s_b[BATCH];
-    __shared__ float2 s_c[BATCH];
-    __shared__ float s_e[BATCH];
+    constexpr int NW = NT / 32;
+    constexpr int Q = BATCH >= 256 ? 2 : 1;
+    constexpr int WB = 32 * Q;
+    __shared__ float4 s_a[NW][WB];
+    __shared__ float4 s_b[NW][WB];
+    __shared__ float2 s_c[NW][WB];
+    __shared__ uint32_t s_j[NW][WB];
     const int t = threadIdx.x;
+    const int lane = t & 31;
+    const int w = t >> 5;
+    const uint32_t lt_mask = (1u << lane) - 1u;
     const int tile = (int)tile_order[blockIdx.x];  // longest lists first
     const ViewParam& V = bp.v[find_view_by_tile(bp, tile)];
     const int lt = tile - V.tile_off;
@@ -107,32 +118,41 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_render_fwd(const __grid_const
     }
     const uint2 rg = ranges[tile];
 
-    for (uint32_t start = rg.x; start < rg.y; start += BATCH) {
+    for (uint32_t start = rg.x; start < rg.y; start += WB) {
         bool all = true;
 #pragma unroll
         for (int k = 0; k < PPT; ++k) all = all && done[k];
-        if (__syncthreads_count(all) == NT) break;
+        if (__all_sync(0xffffffffu, all)) break;
+        int n = 0;
 #pragma unroll
-        for (int q = 0; q < BATCH / NT; ++q) {
-            const int slot = q * NT + t;
-            const uint32_t idx = start + slot;
+        for (int q = 0; q < Q; ++q) {
+            const uint32_t idx = start + q * 32 + lane;
+            bool reach = false;
+            uint32_t r = 0;
+            float4 a = make_float4(0.f, 0.f, 0.f, 0.f), c = a;
             if (idx < rg.y) {
-                const uint32_t r = svals[idx];
-                s_a[slot] = rec[3 * r];
-                s_b[slot] = rec[3 * r + 1];
-                const float4 c = rec[3 * r + 2];
-                s_c[slot] = make_float2(c.x, c.y);
-                s_e[slot] = c.w;
+                r = svals[idx];
+                a = rec[3 * r];
+                c = rec[3 * r + 2];
+                reach = wb.reaches(a.x, a.y, c.w);
             }
+            const uint32_t m = __ballot_sync(0xffffffffu, reach);
+            if (reach) {
+                const int pos = n + __popc(m & lt_mask);
+                s_a[w][pos] = a;
+                s_b[w][pos] = rec[3 * r + 1];
+                s_c[w][pos] = make_float2(c.x, c.y);
+                s_j[w][pos] = idx - rg.x + 1;
+            }
+            n += __popc(m);
         }
-        __syncthreads();
+        __syncwarp();
         if (!all) {
-            const int cnt = min((uint32_t)BATCH, rg.y - start);
-            for (int j = 0; j < cnt; ++j) {
-                const float4 a = s_a[j];
-                if (!wb.reaches(a.x, a.y, s_e[j])) continue;  // warp-uniform
-                const float4 b = s_b[j];
-                const float2 c = s_c[j];
+            for (int j = 0; j < n; ++j) {
+                const float4 a = s_a[w][j];
+                const float4 b = s_b[w][j];
+                const float2 c = s_c[w][j];
+                const uint32_t pos1 = s_j[w][j];
                 const float dx = fx - a.x;
                 const float u1 = dx * a.z, u2 = dx * b.x;
 #pragma unroll
@@ -149,16 +169,17 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_render_fwd(const __grid_const
                         done[k] = true;
                         continue;
                     }
-                    const float w = alpha * T[k];
-                    C0[k] = fmaf(b.w, w, C0[k]);
-                    C1[k] = fmaf(c.x, w, C1[k]);
-                    C2[k] = fmaf(c.y, w, C2[k]);
+                    const float wgt = alpha * T[k];
+                    C0[k] = fmaf(b.w, wgt, C0[k]);
+                    C1[k] = fmaf(c.x, wgt, C1[k]);
+                    C2[k] = fmaf(c.y, wgt, C2[k]);
                     T[k] = Tn;
-                    last[k] = start - rg.x + j + 1;
+                    last[k] = pos1;
                     ++used[k];
                 }
             }
         }
+        __syncwarp();
     }
     const long long hw = (long long)V.W * V.H;
     float* out = rgb + 3 * V.pix_off;
@@ -216,10 +237,12 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_render_bwd(const __grid_const
     __shared__ float s_e[BATCH];
     __shared__ uint32_t s_r[BATCH];
     __shared__ float s_acc[kAccW][kGrad2D][kAccB];
+    __shared__ uint16_t s_list[NW][BATCH];
     __shared__ uint32_t s_maxnc;
     const int t = threadIdx.x;
     const int lane = t & 31;
     const int warp = t >> 5;
+    const uint32_t lt_mask = (1u << lane) - 1u;
     const int tile = (int)tile_order[blockIdx.x];  // longest lists first
     const ViewParam& V = bp.v[find_view_by_tile(bp, tile)];
     const int lt = tile - V.tile_off;
@@ -257,6 +280,7 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_render_bwd(const __grid_const
     if (t == 0) s_maxnc = 0;
     __syncthreads();
     if (mine) atomicMax(&s_maxnc, mine);
+    const int wmax = (int)__reduce_max_sync(0xffffffffu, mine);  // this warp's deepest contributor
     __syncthreads();
     // n_contrib never exceeds the tile's list length when it comes from the
     // forward pass over the same bins; clamp so other inputs cannot read past
@@ -284,9 +308,24 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_render_bwd(const __grid_const
             for (int i = t; i < kAccW * kGrad2D * kAccB; i += NT) (&s_acc[0][0][0])[i] = 0.f;
         }
         __syncthreads();
-        for (int j0 = 0; j0 < cnt; j0 += kGroup) {
-            // contributions of kGroup consecutive Gaussians, summed over this
-            // thread's pixels: v[g][e] (e indexes the 9 accumulators)
+        // this warp's list: the staged records (back to front) that lie above
+        // its deepest contributor and whose footprint box reaches its pixels
+        int n = 0;
+        for (int c0 = 0; c0 < cnt; c0 += 32) {
+            const int slot = c0 + lane;
+            bool reach = false;
+            if (slot < cnt && hi - 1 - slot < wmax) {
+                const float4 a = s_a[slot];
+                reach = wb.reaches(a.x, a.y, s_e[slot]);
+            }
+            const uint32_t m = __ballot_sync(0xffffffffu, reach);
+            if (reach) s_list[warp][n + __popc(m & lt_mask)] = (uint16_t)slot;
+            n += __popc(m);
+        }
+        __syncwarp();
+        for (int j0 = 0; j0 < n; j0 += kGroup) {
+            // contributions of kGroup consecutive listed Gaussians, summed over
+            // this thread's pixels: v[g][e] (e indexes the 9 accumulators)
             float v[kGroup][kGrad2D];
 #pragma unroll
             for (int g = 0; g < kGroup; ++g)
@@ -295,11 +334,10 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_render_bwd(const __grid_const
             bool any = false;
 #pragma unroll
             for (int g = 0; g < kGroup; ++g) {
-                const int j = j0 + g;
-                if (j >= cnt) break;
+                if (j0 + g >= n) break;
+                const int j = s_list[warp][j0 + g];
                 const int rel = hi - 1 - j;
                 const float4 a = s_a[j];
-                if (!wb.reaches(a.x, a.y, s_e[j])) continue;  // warp-uniform
                 const float4 b = s_b[j];
                 const float2 c = s_c[j];
                 const float dx = fx - a.x;
@@ -349,12 +387,12 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_render_bwd(const __grid_const
 #pragma unroll
                     for (int e = 0; e < 8; ++e) x[g * 8 + e] = v[g][e];
 #pragma unroll
-                for (int o = 16, n = 32; o > 0; o >>= 1, n >>= 1) {
+                for (int o = 16, len = 32; o > 0; o >>= 1, len >>= 1) {
                     const bool upper = (lane & o) != 0;
 #pragma unroll
-                    for (int i = 0; i < n / 2; ++i) {
-                        const float send = upper ? x[i] : x[i + n / 2];
-                        const float keep = upper ? x[i + n / 2] : x[i];
+                    for (int i = 0; i < len / 2; ++i) {
+                        const float send = upper ? x[i] : x[i + len / 2];
+                        const float keep = upper ? x[i + len / 2] : x[i];
                         x[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
                     }
                 }
@@ -364,12 +402,12 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_render_bwd(const __grid_const
 #pragma unroll
                 for (int g = 0; g < kGroup; ++g) y[g] = v[g][8];
 #pragma unroll
-                for (int o = 16, n = kGroup; o >= 8; o >>= 1, n >>= 1) {
+                for (int o = 16, len = kGroup; o >= 8; o >>= 1, len >>= 1) {
                     const bool upper = (lane & o) != 0;
 #pragma unroll
-                    for (int i = 0; i < n / 2; ++i) {
-                        const float send = upper ? y[i] : y[i + n / 2];
-                        const float keep = upper ? y[i + n / 2] : y[i];
+                    for (int i = 0; i < len / 2; ++i) {
+                        const float send = upper ? y[i] : y[i + len / 2];
+                        const float keep = upper ? y[i + len / 2] : y[i];
                         y[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
                     }
                 }
@@ -377,12 +415,13 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_render_bwd(const __grid_const
 #pragma unroll
                 for (int o = 4; o > 0; o >>= 1) yb += __shfl_xor_sync(0xffffffffu, yb, o);
                 const int gl = lane >> 3, el = lane & 7;
-                if (j0 + gl < cnt) {
+                if (j0 + gl < n) {
+                    const int j = s_list[warp][j0 + gl];
                     if (kTileSum) {
-                        s_acc[kTileSum ? warp : 0][el][kTileSum ? j0 + gl : 0] = x[0];
-                        if (el == 0) s_acc[kTileSum ? warp : 0][8][kTileSum ? j0 + gl : 0] = yb;
+                        s_acc[kTileSum ? warp : 0][el][kTileSum ? j : 0] = x[0];
+                        if (el == 0) s_acc[kTileSum ? warp : 0][8][kTileSum ? j : 0] = yb;
                     } else {
-                        float* dst = grad2d + (size_t)s_r[j0 + gl] * kGrad2D;
+                        float* dst = grad2d + (size_t)s_r[j] * kGrad2D;
                         if (x[0] != 0.f) atomicAdd(dst + el, x[0]);
                         if (el == 0 && yb != 0.f) atomicAdd(dst + 8, yb);
                     }
