@@ -1,10 +1,13 @@
 // Per-tile compositing (Eq. raster), its backward pass, and the L1
 // photometric loss (Eq. gaussian_optimization).
 //
-// One CTA per screen tile of TS x TS pixels, PPT pixels per thread.  The
-// tile's depth-sorted Gaussian list is staged through shared memory in
-// batches of 256 records (every thread reads all of them: broadcast reads,
-// no bank conflicts).
+// One CTA per screen tile of TS x TS pixels, PPT pixels per thread; the
+// CTAs are dispatched longest tile list first.  Each warp walks the tile's
+// depth-sorted list on its own: per step its lanes fetch 32 (or 64)
+// records, keep those whose footprint box reaches the warp's pixels
+// (ballot-compacted, in list order, into the warp's shared slots), and the
+// warp then composites only those (every lane reads every slot: broadcast
+// reads).  There is no block-wide barrier.
 //
 // The fragment test is done in the log2 domain: with the record holding the
 // scaled principal axes v1, v2 of the footprint (v_k = e_k sqrt(log2(e) /
@@ -12,7 +15,7 @@
 //   p = l - (d.v1)^2 - (d.v2)^2  =  log2(sigma G(x)),   d = x - q,
 // so alpha_raw = 2^p (one ex2) and alpha < alpha_min is p < log2(alpha_min).
 // Record layout (3 x float4): (qx, qy, v1x, v1y), (v2x, v2y, l, r), (g, b,
-// depth, 0).
+// depth, ext) with ext the footprint box's half-extents as two FP16.
 // Forward and backward evaluate p and alpha with the same operations in the
 // same order, so both passes make identical decisions.
 //
@@ -198,17 +201,18 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_render_fwd(const __grid_const
 }
 
 // Backward of the compositing.  Walks the tile's list back to front from
-// the largest n_contrib in the tile.  With T the transmittance behind
+// the largest n_contrib of each warp's pixels.  With T the transmittance behind
 // fragment j and R the light composited behind it (normalised by T),
 //   T_j = T_{j+1} / (1 - alpha_j),   dL/dc_j = alpha_j T_j g,
 //   dL/dalpha_j = T_j g . (c_j - R_j),  R_{j-1} = R_j + alpha_j (c_j - R_j),
-// with R = bg behind the last contributor.  With ga = dL/dalpha * 2^p where
+// with R = bg behind the last contributor; only the scalar g . R is carried
+// (g . R_{j-1} = g . R_j + alpha_j (g . c_j - g . R_j)).  With ga = dL/dalpha * 2^p where
 // alpha is not clamped (dL/dp up to the factor ln 2), the 9 per-record
 // accumulators are
 //   sum ga (d.v1), sum ga (d.v2), sum ga dx^2, sum ga dx dy, sum ga dy^2,
 //   sum ga, sum w g_r, sum w g_g, sum w g_b      (w = alpha T),
-// summed over the thread's PPT pixels, reduced over the warp and then the
-// tile, and added with one atomic per component; the factor ln 2, the
+// summed over the thread's PPT pixels, reduced over the warp, and added
+// with one atomic per (warp, record, component); the factor ln 2, the
 // principal axes and the conversion to the natural conic are applied in
 // the projection backward.
 template <int TS, int PPT, int BATCH>
@@ -222,23 +226,19 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_render_bwd(const __grid_const
                                                               const uint32_t* __restrict__ n_contrib,
                                                               const float* __restrict__ dL_drgb,
                                                               float* __restrict__ grad2d) {
+    // Each warp walks the list on its own, back to front from its deepest
+    // contributor, fetching Q records per lane per step and compacting the
+    // ones whose footprint box reaches its pixels (as in the forward).  No
+    // block barrier: the warps of a tile finish independently.
     constexpr int NT = TS * TS / PPT;
     constexpr int NW = NT / 32;
-    // With several warps per tile, each warp parks its warp-reduced values in
-    // its own slot and the tile adds them up before one global atomic per
-    // (record, component): global float atomics, not shuffles, bound this
-    // kernel.  Skipped when the slots would not fit a small shared budget.
-    constexpr bool kTileSum = NW > 1 && NW * BATCH * kGrad2D * 4 <= 20 * 1024;
-    constexpr int kAccW = kTileSum ? NW : 1;
-    constexpr int kAccB = kTileSum ? BATCH : 1;
-    __shared__ float4 s_a[BATCH];
-    __shared__ float4 s_b[BATCH];
-    __shared__ float2 s_c[BATCH];
-    __shared__ float s_e[BATCH];
-    __shared__ uint32_t s_r[BATCH];
-    __shared__ float s_acc[kAccW][kGrad2D][kAccB];
-    __shared__ uint16_t s_list[NW][BATCH];
-    __shared__ uint32_t s_maxnc;
+    constexpr int Q = BATCH >= 256 ? 2 : 1;
+    constexpr int WB = 32 * Q;
+    __shared__ float4 s_a[NW][WB];
+    __shared__ float4 s_b[NW][WB];
+    __shared__ float2 s_c[NW][WB];
+    __shared__ uint32_t s_r[NW][WB];
+    __shared__ int s_rel[NW][WB];
     const int t = threadIdx.x;
     const int lane = t & 31;
     const int warp = t >> 5;
@@ -255,7 +255,7 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_render_bwd(const __grid_const
     const long long hw = (long long)V.W * V.H;
     const float* gimg = dL_drgb + 3 * V.pix_off;
 
-    float fy[PPT], T[PPT], g0[PPT], g1[PPT], g2[PPT], R0[PPT], R1[PPT], R2[PPT];
+    float fy[PPT], T[PPT], g0[PPT], g1[PPT], g2[PPT], gR[PPT];
     int nc[PPT];
     uint32_t mine = 0;
 #pragma unroll
@@ -272,54 +272,34 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_render_bwd(const __grid_const
             g1[k] = gimg[hw + pl];
             g2[k] = gimg[2 * hw + pl];
         }
-        R0[k] = rc.bg[0];
-        R1[k] = rc.bg[1];
-        R2[k] = rc.bg[2];
+        gR[k] = g0[k] * rc.bg[0] + g1[k] * rc.bg[1] + g2[k] * rc.bg[2];
         mine = max(mine, (uint32_t)nc[k]);
     }
-    if (t == 0) s_maxnc = 0;
-    __syncthreads();
-    if (mine) atomicMax(&s_maxnc, mine);
-    const int wmax = (int)__reduce_max_sync(0xffffffffu, mine);  // this warp's deepest contributor
-    __syncthreads();
-    // n_contrib never exceeds the tile's list length when it comes from the
-    // forward pass over the same bins; clamp so other inputs cannot read past
-    // the list.
-    const int maxnc = min((int)s_maxnc, (int)(rg.y - rg.x));
+    const int wmax = min((int)__reduce_max_sync(0xffffffffu, mine), (int)(rg.y - rg.x));
 
-    for (int hi = maxnc; hi > 0; hi -= BATCH) {
-        const int lo = hi - BATCH > 0 ? hi - BATCH : 0;
-        const int cnt = hi - lo;
-        __syncthreads();
-#pragma unroll
-        for (int q = 0; q < BATCH / NT; ++q) {
-            const int slot = q * NT + t;
-            if (slot < cnt) {
-                const uint32_t r = svals[rg.x + hi - 1 - slot];
-                s_r[slot] = r;
-                s_a[slot] = rec[3 * r];
-                s_b[slot] = rec[3 * r + 1];
-                const float4 c = rec[3 * r + 2];
-                s_c[slot] = make_float2(c.x, c.y);
-                s_e[slot] = c.w;
-            }
-        }
-        if (kTileSum) {
-            for (int i = t; i < kAccW * kGrad2D * kAccB; i += NT) (&s_acc[0][0][0])[i] = 0.f;
-        }
-        __syncthreads();
-        // this warp's list: the staged records (back to front) that lie above
-        // its deepest contributor and whose footprint box reaches its pixels
+    for (int hi = wmax; hi > 0; hi -= WB) {
         int n = 0;
-        for (int c0 = 0; c0 < cnt; c0 += 32) {
-            const int slot = c0 + lane;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const int rel = hi - 1 - (q * 32 + lane);
             bool reach = false;
-            if (slot < cnt && hi - 1 - slot < wmax) {
-                const float4 a = s_a[slot];
-                reach = wb.reaches(a.x, a.y, s_e[slot]);
+            uint32_t r = 0;
+            float4 a = make_float4(0.f, 0.f, 0.f, 0.f), c = a;
+            if (rel >= 0) {
+                r = svals[rg.x + rel];
+                a = rec[3 * r];
+                c = rec[3 * r + 2];
+                reach = wb.reaches(a.x, a.y, c.w);
             }
             const uint32_t m = __ballot_sync(0xffffffffu, reach);
-            if (reach) s_list[warp][n + __popc(m & lt_mask)] = (uint16_t)slot;
+            if (reach) {
+                const int pos = n + __popc(m & lt_mask);
+                s_a[warp][pos] = a;
+                s_b[warp][pos] = rec[3 * r + 1];
+                s_c[warp][pos] = make_float2(c.x, c.y);
+                s_r[warp][pos] = r;
+                s_rel[warp][pos] = rel;
+            }
             n += __popc(m);
         }
         __syncwarp();
@@ -334,12 +314,12 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_render_bwd(const __grid_const
             bool any = false;
 #pragma unroll
             for (int g = 0; g < kGroup; ++g) {
-                if (j0 + g >= n) break;
-                const int j = s_list[warp][j0 + g];
-                const int rel = hi - 1 - j;
-                const float4 a = s_a[j];
-                const float4 b = s_b[j];
-                const float2 c = s_c[j];
+                const int j = j0 + g;
+                if (j >= n) break;
+                const int rel = s_rel[warp][j];
+                const float4 a = s_a[warp][j];
+                const float4 b = s_b[warp][j];
+                const float2 c = s_c[warp][j];
                 const float dx = fx - a.x;
                 const float u1 = dx * a.z, u2 = dx * b.x;
 #pragma unroll
@@ -358,11 +338,9 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_render_bwd(const __grid_const
                     v[g][6] = fmaf(w, g0[k], v[g][6]);
                     v[g][7] = fmaf(w, g1[k], v[g][7]);
                     v[g][8] = fmaf(w, g2[k], v[g][8]);
-                    const float d0 = b.w - R0[k], d1 = c.x - R1[k], d2 = c.y - R2[k];
-                    const float dalpha = T[k] * (g0[k] * d0 + g1[k] * d1 + g2[k] * d2);
-                    R0[k] = fmaf(alpha, d0, R0[k]);
-                    R1[k] = fmaf(alpha, d1, R1[k]);
-                    R2[k] = fmaf(alpha, d2, R2[k]);
+                    const float gd = fmaf(g0[k], b.w, fmaf(g1[k], c.x, g2[k] * c.y)) - gR[k];
+                    const float dalpha = T[k] * gd;
+                    gR[k] = fmaf(alpha, gd, gR[k]);
                     const float ga = araw < rc.alpha_max ? dalpha * araw : 0.f;
                     // dp/dq = 2 ((d.v1) v1 + (d.v2) v2) with v1, v2 fixed per
                     // record: only ga (d.v1), ga (d.v2) are summed here
@@ -416,28 +394,13 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_render_bwd(const __grid_const
                 for (int o = 4; o > 0; o >>= 1) yb += __shfl_xor_sync(0xffffffffu, yb, o);
                 const int gl = lane >> 3, el = lane & 7;
                 if (j0 + gl < n) {
-                    const int j = s_list[warp][j0 + gl];
-                    if (kTileSum) {
-                        s_acc[kTileSum ? warp : 0][el][kTileSum ? j : 0] = x[0];
-                        if (el == 0) s_acc[kTileSum ? warp : 0][8][kTileSum ? j : 0] = yb;
-                    } else {
-                        float* dst = grad2d + (size_t)s_r[j] * kGrad2D;
-                        if (x[0] != 0.f) atomicAdd(dst + el, x[0]);
-                        if (el == 0 && yb != 0.f) atomicAdd(dst + 8, yb);
-                    }
+                    float* dst = grad2d + (size_t)s_r[warp][j0 + gl] * kGrad2D;
+                    if (x[0] != 0.f) atomicAdd(dst + el, x[0]);
+                    if (el == 0 && yb != 0.f) atomicAdd(dst + 8, yb);
                 }
             }
         }
-        if (kTileSum) {
-            __syncthreads();
-            for (int i = t; i < kGrad2D * cnt; i += NT) {
-                const int e = i / cnt, j = i - e * cnt;
-                float sum = 0.f;
-#pragma unroll
-                for (int ww = 0; ww < kAccW; ++ww) sum += s_acc[ww][e][kTileSum ? j : 0];
-                if (sum != 0.f) atomicAdd(grad2d + (size_t)s_r[j] * kGrad2D + e, sum);
-            }
-        }
+        __syncwarp();
     }
 }
 
