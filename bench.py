@@ -49,10 +49,17 @@ WORKLOAD = "box-room sliding window: 200k planar Gaussians (SH degree 1), 8 keyf
 # colour gradient (1 + 6), light-behind differences and alpha gradient
 # (3 + 5 + 1), light-behind update (6), exponent gradient (2), mean gradient
 # (10), conic gradient (8) and opacity term (1) = 45 FLOP.
-FLOP_VISITED = 10.0
-FLOP_CONTRIB = {"raster_fwd": 10.0, "raster_bwd": 45.0}
-SM_COUNT = 148
+# Algorithmic FP32 operations per fragment (FMA = 2; compares, min/max and
+# selects not counted; ex2 and the divide count 1 each):
+#   every visited fragment:  d = x - q (2), t_k = d . v_k (2 x 3), p = l - t1^2 - t2^2 (4)   = 12
+#   forward, contributing:   ex2, 1 - alpha, T (1 - alpha), w = alpha T, C += w c (6)        = 10
+#   backward, contributing:  ex2, 1 - alpha, T / (1 - alpha), w, dL/dc += w g (6), g.c (5),
+#                            g.c - g.R, dL/dalpha, g.R update (2), ga, ga t1, ga t2 (4),
+#                            ga dx, ga dy, ga dx^2, ga dx dy, ga dy^2 (6), sum ga            = 34
+FLOP_VISITED = 12.0
+FLOP_CONTRIB = {"raster_fwd": 10.0, "raster_bwd": 34.0}
 FP32_LANES = 128
+MAX_SM_MHZ = 2032
 
 
 def parse():
@@ -309,6 +316,8 @@ def run_b300(args, world, rank, local):
     dom_launches, dom_ms = prof.get(dominant, (0, 0.0))
     avg_ms = dom_ms / max(dom_launches, 1)
     hbm, hbm_kind = peaks()
+    # measured ALU peaks of this device (FFMA and ex2 microbenchmarks, outside timing)
+    ffma_tflops, ex2_gops = ctx.calibrate_alu()
     # fragment counts of the last parameters (one extra forward, outside timing)
     n_used = torch.empty_like(opt.r.n_contrib)
     opt.r.forward(opt._g, count=False, n_used=n_used)
@@ -316,15 +325,20 @@ def run_b300(args, world, rank, local):
     visited = float(opt.r.n_contrib.double().sum().item())
     contrib = float(n_used.double().sum().item())
     if dominant in FLOP_CONTRIB:
-        clk = 2032.0
-        peak = SM_COUNT * FP32_LANES * 2 * clk * 1e6 / 1e12
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        nominal = sms * FP32_LANES * 2 * MAX_SM_MHZ * 1e6 / 1e12
+        peak = ffma_tflops
         flop = FLOP_VISITED * visited + FLOP_CONTRIB[dominant] * contrib
         achieved = flop / (avg_ms / 1e3) / 1e12
         roof = {"bound": "alu", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": None, "avg_launch_ms": avg_ms,
                 "visited_fragments": visited, "contributing_fragments": contrib,
                 "flop_per_launch": flop,
-                "peak_basis": "FP32 FMA peak: 148 SMs x 128 lanes x 2 FLOP x 2032 MHz (maximum SM clock)"}
+                "peak_basis": "measured: FP32 FMA microbenchmark (gs_calibrate_alu, best of 3)",
+                "peak_nominal": nominal,
+                "peak_nominal_basis": "%d SMs x 128 lanes x 2 FLOP x %d MHz (maximum SM clock)" % (sms, MAX_SM_MHZ),
+                "frac_of_nominal": achieved / nominal,
+                "ex2_measured_gops": ex2_gops}
     else:
         roof = {"bound": "hbm", "kernel": dominant, "achieved": None, "peak": hbm, "unit": "GB/s",
                 "frac": None, "traffic": None, "avg_launch_ms": avg_ms, "peak_kind": hbm_kind}

@@ -354,6 +354,14 @@ GS_API int gs_profile_collect(gs_ctx* ctx, gs_stream stream, gs_profile_entry* o
 /* Number of kernel launches (and memset nodes) this context has issued. */
 GS_API int64_t gs_launch_count(const gs_ctx* ctx);
 
+/* Measures, on the context's device, the throughput of the FP32 FMA pipe
+ * (FLOP/s, an FMA counting 2) and of the ex2 special-function unit (ex2/s)
+ * with two short microbenchmarks (a few ms each, best of 3), the measured
+ * ALU peaks that the compositing kernels' roofline is quoted against.  Not
+ * part of the rendering path; synchronises `stream`.
+ * Errors: GS_ERR_INVALID_ARG (NULL output), GS_ERR_CUDA. */
+GS_API int gs_calibrate_alu(gs_ctx* ctx, gs_stream stream, double* ffma_tflops, double* ex2_gops);
+
 /* Library version string. */
 GS_API const char* gs_version(void);
 

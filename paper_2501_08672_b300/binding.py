@@ -33,7 +33,7 @@ EXPORTED = ["gs_config_default", "gs_version", "gs_context_create", "gs_context_
             "gs_get_config", "gs_workspace_query", "gs_workspace_layout", "gs_project", "gs_bin",
             "gs_render_fwd", "gs_l1_loss", "gs_render_bwd", "gs_pose_grad", "gs_adam_step", "gs_sync_status",
             "gs_profile_enable", "gs_profile_collect", "gs_launch_count", "gs_adam_step_dev",
-            "gs_l1_loss_noalloc"]
+            "gs_l1_loss_noalloc", "gs_calibrate_alu"]
 
 KERNEL_FAMILIES = ["project", "depth_sort", "tile_scan", "emit", "tile_sort", "ranges", "raster_fwd", "l1",
                    "raster_bwd", "project_bwd", "adam"]
@@ -132,6 +132,7 @@ def lib():
         L.gs_profile_collect.argtypes = [P, P, ctypes.POINTER(ProfileEntry), I, ctypes.POINTER(ctypes.c_int)]
         L.gs_launch_count.argtypes = [P]
         L.gs_launch_count.restype = ctypes.c_int64
+        L.gs_calibrate_alu.argtypes = [P, P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
         _lib = L
     return _lib
 
@@ -325,6 +326,12 @@ class Context:
         _check_dev(step_dev, "step_dev", torch.int64, 1)
         self._ck(lib().gs_adam_step_dev(self.h, _ptr(param), _ptr(grad), _ptr(m), _ptr(v), param.numel(), float(lr),
                                         float(b1), float(b2), float(eps), _ptr(step_dev), segs, ns, _stream(stream)))
+
+    def calibrate_alu(self, stream=None):
+        """Measured FP32 FMA throughput (TFLOP/s) and ex2 throughput (G/s) of this device."""
+        f, x = ctypes.c_double(), ctypes.c_double()
+        self._ck(lib().gs_calibrate_alu(self.h, _stream(stream), ctypes.byref(f), ctypes.byref(x)))
+        return f.value, x.value
 
     def sync_status(self, stream=None):
         n = ctypes.c_uint64()

@@ -433,6 +433,19 @@ int gs_context_destroy(gs_ctx* ctx) {
     return GS_OK;
 }
 
+int gs_calibrate_alu(gs_ctx* ctx, gs_stream stream, double* ffma_tflops, double* ex2_gops) {
+    if (!ctx) return GS_ERR_INVALID_ARG;
+    if (!ffma_tflops || !ex2_gops) return fail(ctx, GS_ERR_INVALID_ARG, "output pointer is NULL");
+    DeviceGuard dg(ctx->device);
+    if (!dg.ok) return fail(ctx, GS_ERR_CUDA, "cudaSetDevice(%d) failed", ctx->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // the never-taken stores of the microbenchmarks point at a spare word of the status block
+    cudaError_t e = measure_alu(ctx->sm_count, reinterpret_cast<float*>(ctx->d_status + 48), s, ffma_tflops,
+                                ex2_gops);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "gs_calibrate_alu");
+    return GS_OK;
+}
+
 const char* gs_last_error(const gs_ctx* ctx) { return ctx ? ctx->err : "context is NULL"; }
 
 int gs_get_config(const gs_ctx* ctx, gs_config* cfg) {

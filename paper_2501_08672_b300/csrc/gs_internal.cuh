@@ -190,6 +190,7 @@ cudaError_t launch_project(const BatchParam& bp, const GaussPtrs& g, const Rende
 cudaError_t launch_bin(const BatchParam& bp, WsPtrs& ws, unsigned int* status,
                        unsigned long long* status_pairs, cudaStream_t s, Prof& pf);
 bool raster_variant_exists(int ts, int ppt, int batch);
+cudaError_t measure_alu(int sm_count, float* sink, cudaStream_t s, double* ffma_tflops, double* ex2_gops);
 cudaError_t launch_render_fwd(const BatchParam& bp, const RenderConst& rc, const WsPtrs& ws,
                               float* rgb, float* T_final, uint32_t* n_contrib, uint32_t* n_used,
                               cudaStream_t s, Prof& pf);

@@ -90,6 +90,20 @@ def test_library_exports_and_version():
     assert b"sm_103a" in lib.gs_version()
 
 
+def test_alu_calibration_is_plausible():
+    """The measured FFMA rate lies below the nominal peak of the device
+    (SMs x 128 FP32 lanes x 2 FLOP at no more than 2.2 GHz) and above a tenth
+    of it; the ex2 rate lies between one ex2 per 16 lanes at 1 GHz and one per
+    FP32 lane at 2.2 GHz."""
+    ctx = B.Context(0)
+    f, x = ctx.calibrate_alu()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    f_nom = sms * 128 * 2 * 2.2e9 / 1e12
+    print("FFMA %.1f TFLOP/s (nominal bound %.1f), ex2 %.0f G/s (%.1f per SM per ns)" % (f, f_nom, x, x / sms))
+    assert 0.1 * f_nom < f <= f_nom
+    assert sms * 8 * 1.0 < x <= sms * 128 * 2.2
+
+
 def test_projection_records_match_oracle(orc):
     p = scenes.frustum_scene(3000, seed=1)
     p["sh"] = np.concatenate([p["sh"], np.random.default_rng(0).normal(0, 0.2, (3000, 3, 3)).astype(np.float32)], 1)
