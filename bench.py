@@ -17,6 +17,7 @@ same workload (the method has no other reference implementation).
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -59,6 +60,12 @@ WORKLOAD = "box-room sliding window: 200k planar Gaussians (SH degree 1), 8 keyf
 FLOP_VISITED = 12.0
 FLOP_CONTRIB = {"raster_fwd": 10.0, "raster_bwd": 34.0}
 FP32_LANES = 128
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# compositing kernels from one ncu capture of this workload, valid only for the
+# kernel source they were taken on (sha256 prefix of gs_raster.cu) and the
+# launch shape; otherwise the roofline reports traffic null.
+TRAFFIC = {"raster_fwd": ("4e7e4c1a585e08e3", (16, 2, 256), 116.9e6),
+           "raster_bwd": ("4e7e4c1a585e08e3", (16, 2, 256), 236.4e6)}
 MAX_SM_MHZ = 2032
 
 
@@ -330,8 +337,16 @@ def run_b300(args, world, rank, local):
         peak = ffma_tflops
         flop = FLOP_VISITED * visited + FLOP_CONTRIB[dominant] * contrib
         achieved = flop / (avg_ms / 1e3) / 1e12
+        traffic = None
+        if dominant in TRAFFIC:
+            sha, tshape, tbytes = TRAFFIC[dominant]
+            with open(os.path.join(HERE, "paper_2501_08672_b300", "csrc", "gs_raster.cu"), "rb") as f:
+                cur = hashlib.sha256(f.read()).hexdigest()[:16]
+            if cur == sha and tuple(shape) == tshape:
+                traffic = tbytes
         roof = {"bound": "alu", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None, "avg_launch_ms": avg_ms,
+                "frac": achieved / peak, "traffic": traffic, "traffic_unit": "bytes per launch (ncu DRAM read + write)",
+                "avg_launch_ms": avg_ms,
                 "visited_fragments": visited, "contributing_fragments": contrib,
                 "flop_per_launch": flop,
                 "peak_basis": "measured: FP32 FMA microbenchmark (gs_calibrate_alu, best of 3)",
