@@ -17,6 +17,10 @@
  *     Eq. minimization:             photometric loss, minimised over the
  *                                   Gaussian parameters and over the pose
  *   - Appendix A, perturbation model: left perturbation of T_CW
+ *   - Sec. II-D, Eq. minimization: the per-pixel pose Jacobian of the
+ *                                   rendered image (measurement Jacobian of
+ *                                   the photometric update) and its normal
+ *                                   equations
  *   - Sec. II-B.2 ("Adam optimizer"): Kingma-Ba Adam with bias correction.
  *
  * Readings taken where the paper is silent (the same ones the CUDA path uses):
@@ -673,6 +677,199 @@ int orc_project_backward(long n, const double* means, const double* log_scales,
                 g_pose[3 + k] += gp[k] + (W[3 * k] * gd[0] + W[3 * k + 1] * gd[1] + W[3 * k + 2] * gd[2]);
         }
     }
+    return 0;
+}
+
+/* ---------- pose Jacobian of the rendered pixels (Sec. II-D) ---------- */
+
+/* Tangents of one Gaussian's projected quantities with respect to the
+ * left-perturbed camera pose xi = [dphi; dt], T_CW <- Exp(xi) T_CW (Appendix
+ * A, perturbation model), written forward from Eqs. q and spat:
+ *   dp_C/ddphi_k = e_k x p_C,   dp_C/ddt_k = e_k,
+ *   dW/ddphi_k = [e_k]x W,      campos = -W^T t moves by -W^T dt only,
+ *   q = pi(p_C):  dq = J dp_C,
+ *   T = J W:      dT = dJ W + J dW with dJ from J(p_C),
+ *   Sigma2 = T Sigma3 T^T + b I:  dSigma2 = dT Sigma3 T^T + T Sigma3 dT^T,
+ *   conic = Sigma2^-1:            dconic = -conic dSigma2 conic,
+ *   colour = max(0, SH(dir)), dir = (mu - campos) / |mu - campos|.
+ * Outputs (column k = d/dxi_k): dq[2][6], dconic[3][6] (A, B, C) and
+ * dcol[3][6]. */
+static void pose_tangents(const orc_proj* P, const double* cam, const double* sh, int sh_degree,
+                          double dq[2][6], double dconic[3][6], double dcol[3][6]) {
+    const double* W = cam;
+    double fx = cam[12], fy = cam[13];
+    double x = P->pc[0], y = P->pc[1], z = P->pc[2];
+    for (int k = 0; k < 6; ++k) {
+        /* dp_C and dW for xi = e_k */
+        double dp[3] = {0, 0, 0}, dW[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        if (k < 3) {
+            double e[3] = {0, 0, 0};
+            e[k] = 1.0;
+            dp[0] = e[1] * z - e[2] * y;
+            dp[1] = e[2] * x - e[0] * z;
+            dp[2] = e[0] * y - e[1] * x;
+            /* [e]x W: row r of [e]x is (e x .) applied to the columns of W */
+            for (int c = 0; c < 3; ++c) {
+                double w0 = W[c], w1 = W[3 + c], w2 = W[6 + c];
+                dW[c] = e[1] * w2 - e[2] * w1;
+                dW[3 + c] = e[2] * w0 - e[0] * w2;
+                dW[6 + c] = e[0] * w1 - e[1] * w0;
+            }
+        } else {
+            dp[k - 3] = 1.0;
+        }
+        /* q = (fx x / z + cx, fy y / z + cy) */
+        dq[0][k] = P->J[0] * dp[0] + P->J[1] * dp[1] + P->J[2] * dp[2];
+        dq[1][k] = P->J[3] * dp[0] + P->J[4] * dp[1] + P->J[5] * dp[2];
+        /* J = [[fx/z, 0, -fx x/z^2], [0, fy/z, -fy y/z^2]] */
+        double dJ[6];
+        dJ[0] = -fx * dp[2] / (z * z);
+        dJ[1] = 0.0;
+        dJ[2] = -fx * dp[0] / (z * z) + 2.0 * fx * x * dp[2] / (z * z * z);
+        dJ[3] = 0.0;
+        dJ[4] = -fy * dp[2] / (z * z);
+        dJ[5] = -fy * dp[1] / (z * z) + 2.0 * fy * y * dp[2] / (z * z * z);
+        double dT[6];
+        for (int r = 0; r < 2; ++r)
+            for (int c = 0; c < 3; ++c) {
+                double s = 0.0;
+                for (int m = 0; m < 3; ++m) s += dJ[3 * r + m] * W[3 * m + c] + P->J[3 * r + m] * dW[3 * m + c];
+                dT[3 * r + c] = s;
+            }
+        /* dSigma2 = dT S3 T^T + T S3 dT^T */
+        double dS[4];
+        for (int r = 0; r < 2; ++r)
+            for (int c = 0; c < 2; ++c) {
+                double s = 0.0;
+                for (int i = 0; i < 3; ++i)
+                    for (int j = 0; j < 3; ++j)
+                        s += dT[3 * r + i] * P->S3[3 * i + j] * P->T[3 * c + j] +
+                             P->T[3 * r + i] * P->S3[3 * i + j] * dT[3 * c + j];
+                dS[2 * r + c] = s;
+            }
+        double Q[4] = {P->conic[0], P->conic[1], P->conic[1], P->conic[2]};
+        double QdS[4], dQ[4];
+        for (int r = 0; r < 2; ++r)
+            for (int c = 0; c < 2; ++c) QdS[2 * r + c] = Q[2 * r] * dS[c] + Q[2 * r + 1] * dS[2 + c];
+        for (int r = 0; r < 2; ++r)
+            for (int c = 0; c < 2; ++c) dQ[2 * r + c] = -(QdS[2 * r] * Q[c] + QdS[2 * r + 1] * Q[2 + c]);
+        dconic[0][k] = dQ[0];
+        dconic[1][k] = 0.5 * (dQ[1] + dQ[2]);
+        dconic[2][k] = dQ[3];
+        /* colour: dvec = mu - campos, d campos/d dt_j = -W^T e_j = -(row j of W) */
+        double ddv[3] = {0, 0, 0};
+        if (k >= 3)
+            for (int i = 0; i < 3; ++i) ddv[i] = W[3 * (k - 3) + i];
+        double dd = P->dir[0] * ddv[0] + P->dir[1] * ddv[1] + P->dir[2] * ddv[2];
+        double ddir[3];
+        for (int i = 0; i < 3; ++i) ddir[i] = (ddv[i] - P->dir[i] * dd) / P->dlen;
+        for (int ch = 0; ch < 3; ++ch) {
+            double draw = 0.0;
+            if (sh_degree >= 1)
+                draw = sh_c1() * (-ddir[1] * sh[3 + ch] + ddir[2] * sh[6 + ch] - ddir[0] * sh[9 + ch]);
+            dcol[ch][k] = P->raw[ch] > 0.0 ? draw : 0.0;
+        }
+    }
+}
+
+/* Per-pixel pose Jacobian of the rendered colour, H[p][ch][k] = dI_ch(x_p) /
+ * dxi_k, by forward-mode differentiation of Eq. raster at the listed pixels
+ * of one view (the measurement Jacobian of the photometric update, Sec. II-D,
+ * Eq. minimization).  With T_j the transmittance in front of fragment j,
+ *   I = sum_j c_j alpha_j T_j + T_final bg,  T_{j+1} = T_j (1 - alpha_j),
+ *   dI = sum_j (dc_j alpha_j T_j + c_j dalpha_j T_j + c_j alpha_j dT_j)
+ *        + dT_final bg,  dT_{j+1} = dT_j (1 - alpha_j) - T_j dalpha_j,
+ *   alpha_j = sigma_j G_j (0 derivative where clamped), G = exp(power),
+ *   dpower = -1/2 (dA dx^2 + 2 dB dx dy + dC dy^2)
+ *            + (A dx + B dy) dq_x + (B dx + C dy) dq_y.
+ * The fragment list (which Gaussians contribute, in which order) is the one
+ * composite_pixel decides; culling is locally constant.  rgb [n_pix][3] and
+ * borderline [n_pix] as orc_render_pixels. */
+int orc_pose_jacobian_pixels(long n_pix, const int* pxs, const int* pys, long n, const double* means,
+                             const double* log_scales, const double* quats, const double* opacity,
+                             const double* sh, int sh_degree, const double* cam, const double* cfg,
+                             double* Hout, double* rgb, unsigned char* borderline, int n_threads) {
+    int K = (sh_degree + 1) * (sh_degree + 1);
+    const double* bg = cfg + 5;
+    double amax = cfg[1];
+    orc_proj* P = (orc_proj*)malloc(sizeof(orc_proj) * (n > 0 ? n : 1));
+    int* valid = (int*)malloc(sizeof(int) * (n > 0 ? n : 1));
+    double* q = (double*)malloc(sizeof(double) * 2 * (n > 0 ? n : 1));
+    double* conic = (double*)malloc(sizeof(double) * 3 * (n > 0 ? n : 1));
+    double* opac = (double*)malloc(sizeof(double) * (n > 0 ? n : 1));
+    double* depth = (double*)malloc(sizeof(double) * (n > 0 ? n : 1));
+    double* zerr = (double*)malloc(sizeof(double) * (n > 0 ? n : 1));
+    double* tq = (double*)malloc(sizeof(double) * 12 * (n > 0 ? n : 1));
+    double* tc = (double*)malloc(sizeof(double) * 18 * (n > 0 ? n : 1));
+    double* tcol = (double*)malloc(sizeof(double) * 18 * (n > 0 ? n : 1));
+    long* order = (long*)malloc(sizeof(long) * (n > 0 ? n : 1));
+    for (long i = 0; i < n; ++i) {
+        project_one(means + 3 * i, log_scales + 3 * i, quats + 4 * i, opacity[i], sh + 3 * K * i, sh_degree,
+                    cam, cfg, &P[i]);
+        valid[i] = P[i].valid;
+        q[2 * i] = P[i].q[0];
+        q[2 * i + 1] = P[i].q[1];
+        for (int k = 0; k < 3; ++k) conic[3 * i + k] = P[i].conic[k];
+        opac[i] = P[i].sigma;
+        depth[i] = P[i].pc[2];
+        zerr[i] = P[i].zerr;
+        if (P[i].valid) {
+            double dq[2][6], dcn[3][6], dcol[3][6];
+            pose_tangents(&P[i], cam, sh + 3 * K * i, sh_degree, dq, dcn, dcol);
+            memcpy(tq + 12 * i, dq, sizeof(dq));
+            memcpy(tc + 18 * i, dcn, sizeof(dcn));
+            memcpy(tcol + 18 * i, dcol, sizeof(dcol));
+        }
+    }
+    long m = depth_order(n, valid, depth, order);
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#pragma omp parallel
+#endif
+    {
+        orc_frag* frags = (orc_frag*)malloc(sizeof(orc_frag) * (m > 0 ? m : 1));
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 16)
+#endif
+        for (long p = 0; p < n_pix; ++p) {
+            double T;
+            int bd;
+            long nf = composite_pixel(pxs[p] + 0.5, pys[p] + 0.5, m, order, q, conic, opac, depth, zerr, cfg,
+                                      frags, &T, &bd, NULL);
+            double C[3] = {0, 0, 0}, dC[3][6], dT[6];
+            memset(dC, 0, sizeof(dC));
+            memset(dT, 0, sizeof(dT));
+            for (long f = 0; f < nf; ++f) {
+                long i = frags[f].i;
+                double dx = frags[f].dx, dy = frags[f].dy, a = frags[f].alpha, Tj = frags[f].Tin;
+                double A = conic[3 * i], B = conic[3 * i + 1], Cc = conic[3 * i + 2];
+                const double* dq = tq + 12 * i;     /* [2][6] */
+                const double* dcn = tc + 18 * i;    /* [3][6] */
+                const double* dcol = tcol + 18 * i; /* [3][6] */
+                double da[6];
+                for (int k = 0; k < 6; ++k) {
+                    double dpow = -0.5 * (dcn[k] * dx * dx + 2.0 * dcn[6 + k] * dx * dy + dcn[12 + k] * dy * dy) +
+                                  (A * dx + B * dy) * dq[k] + (B * dx + Cc * dy) * dq[6 + k];
+                    da[k] = frags[f].araw < amax ? a * dpow : 0.0;
+                }
+                for (int ch = 0; ch < 3; ++ch) {
+                    double c = P[i].colour[ch];
+                    C[ch] += c * a * Tj;
+                    for (int k = 0; k < 6; ++k)
+                        dC[ch][k] += dcol[6 * ch + k] * a * Tj + c * da[k] * Tj + c * a * dT[k];
+                }
+                for (int k = 0; k < 6; ++k) dT[k] = dT[k] * (1.0 - a) - Tj * da[k];
+            }
+            for (int ch = 0; ch < 3; ++ch) {
+                rgb[3 * p + ch] = C[ch] + T * bg[ch];
+                for (int k = 0; k < 6; ++k) Hout[18 * p + 6 * ch + k] = dC[ch][k] + dT[k] * bg[ch];
+            }
+            borderline[p] = (unsigned char)bd;
+        }
+        free(frags);
+    }
+    free(P); free(valid); free(q); free(conic); free(opac); free(depth); free(zerr);
+    free(tq); free(tc); free(tcol); free(order);
     return 0;
 }
 

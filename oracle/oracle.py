@@ -14,6 +14,10 @@ Functions, with the passage each restates:
                  (Appendix A, perturbation model)
   adam           Sec. II-B.2 ("Adam optimizer"), Kingma & Ba with bias
                  correction
+  pose_jacobian  Sec. II-D, Eq. minimization: per-pixel d(rendered colour) /
+                 d(left pose perturbation), forward mode
+  pose_normal    the Gauss-Newton normal equations of the photometric
+                 residual in the pose: sum H^T H, sum H^T (target - I)
 """
 from __future__ import annotations
 
@@ -62,6 +66,8 @@ def lib():
                                ctypes.c_double, ctypes.c_double, ctypes.c_long]
         L.orc_adam.restype = None
         L.orc_num_threads.restype = ctypes.c_int
+        L.orc_pose_jacobian_pixels.argtypes = ([ctypes.c_long, P, P, ctypes.c_long] + [P] * 5 + [ctypes.c_int] +
+                                               [P] * 5 + [ctypes.c_int])
         _lib = L
     return _lib
 
@@ -226,3 +232,38 @@ def adam(p, g, m, v, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8, step=1):
 
 def num_threads():
     return int(lib().orc_num_threads())
+
+
+def pose_jacobian(params, view, px, py, cfg=None, n_threads=0):
+    """Per-pixel pose Jacobian H [n, 3, 6] of the rendered colour at pixels
+    (px, py) of one view, with respect to xi = [dphi; dt], T_CW <- Exp(xi) T_CW
+    (forward mode through Eq. raster); also rgb [n, 3] and the borderline
+    mask [n]."""
+    b, e = _slice(params, view)
+    n = e - b
+    mu, ls, qt, op, sh = _params64(params, b, e)
+    px = np.ascontiguousarray(px, np.int32)
+    py = np.ascontiguousarray(py, np.int32)
+    k = px.size
+    H = np.zeros((k, 3, 6))
+    rgb = np.zeros((k, 3))
+    bd = np.zeros(k, np.uint8)
+    lib().orc_pose_jacobian_pixels(k, _p(px), _p(py), n, _p(mu), _p(ls), _p(qt), _p(op), _p(sh),
+                                   int(params["sh_degree"]), _p(cam_array(view)), _p(cfg_array(cfg)), _p(H),
+                                   _p(rgb), _p(bd), int(n_threads))
+    return H, rgb, bd.astype(bool)
+
+
+def pose_normal(params, view, target, cfg=None, n_threads=0):
+    """Normal equations of the photometric residual r = target - I over every
+    pixel of one view: A = sum_p sum_ch H H^T (6 x 6), b = sum H r (6),
+    rr = sum r^2, with H from pose_jacobian (target is [3, H, W]).  Also
+    returns the borderline mask [H, W]."""
+    W, Hh = int(view["W"]), int(view["H"])
+    vv, uu = np.mgrid[0:Hh, 0:W]
+    Hj, rgb, bd = pose_jacobian(params, view, uu.reshape(-1), vv.reshape(-1), cfg, n_threads)
+    r = np.asarray(target, np.float64).reshape(3, -1).T - rgb          # [n, 3]
+    A = np.einsum("pci,pcj->ij", Hj, Hj)
+    b = np.einsum("pci,pc->i", Hj, r)
+    return A, b, float((r * r).sum()), bd.reshape(Hh, W)
+

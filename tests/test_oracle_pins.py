@@ -443,3 +443,75 @@ def test_pixel_list_paths_agree_with_full_image(orc):
     for k in g1:
         np.testing.assert_allclose(g2[k], g1[k], rtol=1e-12, atol=1e-15)
     np.testing.assert_allclose(pose2, pose1, rtol=1e-12, atol=1e-15)
+
+
+# ---- pose Jacobian and normal equations (Sec. II-D, Eq. minimization) ----
+
+@pytest.mark.parametrize("sh_degree", [0, 1])
+def test_pose_jacobian_matches_central_differences(orc, sh_degree):
+    """Per-pixel dI/dxi by forward mode against central differences of the
+    rendered image through scipy's matrix exponential, T_CW <- Exp(xi) T_CW,
+    exact mode and a coloured background (so dT_final enters)."""
+    p = _tiny_scene(41 + sh_degree, n=6, sh_degree=sh_degree)
+    v = _posed_view(20, 16)
+    cfg = dict(orc.EXACT_CFG)
+    cfg["bg"] = (0.2, 0.5, 0.7)
+    vv, uu = np.mgrid[0:v["H"], 0:v["W"]]
+    Hj, rgb, _ = orc.pose_jacobian(p, v, uu.reshape(-1), vv.reshape(-1), cfg)
+    base = orc.render_view(p, v, cfg)["rgb"]
+    np.testing.assert_allclose(rgb.T.reshape(base.shape), base, atol=1e-13)
+    h = 1e-6
+    for k in range(6):
+        e = np.zeros(6); e[k] = h
+        num = (orc.render_view(p, _perturb(v, e), cfg)["rgb"] - orc.render_view(p, _perturb(v, -e), cfg)["rgb"]) / (2 * h)
+        ana = Hj[:, :, k].T.reshape(num.shape)
+        err = np.linalg.norm(ana - num) / max(np.linalg.norm(num), 1e-30)
+        assert err < 1e-6, (k, err)
+
+
+def test_pose_jacobian_agrees_with_reverse_mode(orc):
+    """Truncated mode (alpha_min, alpha_max clamp, T_min early stop active):
+    for any dL/dI, sum_p sum_ch dL/dI_ch(p) H_ch(p) equals the pose gradient of
+    the reverse-mode backward, an independent derivation."""
+    p = _tiny_scene(47, n=40, sh_degree=1)
+    p["opacity"][:20] += 6.0   # sigma > 0.99: the alpha_max clamp and the T_min stop act
+    v = _posed_view(24, 20)
+    cfg = dict(orc.DEFAULT_CFG)
+    cfg["bg"] = (0.1, 0.3, 0.2)
+    vv, uu = np.mgrid[0:v["H"], 0:v["W"]]
+    Hj, _, _ = orc.pose_jacobian(p, v, uu.reshape(-1), vv.reshape(-1), cfg)
+    rng = np.random.default_rng(5)
+    w = rng.standard_normal((3, v["H"], v["W"]))
+    _, pose, _ = orc.backward(p, [v], [w], cfg)
+    fwd = np.einsum("pck,pc->k", Hj, w.reshape(3, -1).T)
+    np.testing.assert_allclose(fwd, pose[0], rtol=1e-10, atol=1e-12 * np.abs(pose[0]).max())
+    out = orc.render_view(p, v, cfg)
+    assert out["n_contrib"].max() >= 3
+    assert (out["T"] < 1e-3).any()   # pixels that stopped at T_min
+
+
+def test_pose_normal_equations_brute_force(orc):
+    """A = sum H^T H and b = sum H^T (target - I) against an explicit loop over
+    pixels and channels; A is symmetric positive semi-definite and the
+    Gauss-Newton step A^-1 b reduces the residual of a pose perturbed by a
+    small known xi (first-order model)."""
+    p = _tiny_scene(53, n=12, sh_degree=1)
+    v = _posed_view(20, 16)
+    cfg = dict(orc.EXACT_CFG)
+    xi_true = np.array([0.002, -0.003, 0.001, 0.004, -0.002, 0.003])
+    target = orc.render_view(p, _perturb(v, xi_true), cfg)["rgb"]
+    A, b, rr, _ = orc.pose_normal(p, v, target, cfg)
+    vv, uu = np.mgrid[0:v["H"], 0:v["W"]]
+    Hj, rgb, _ = orc.pose_jacobian(p, v, uu.reshape(-1), vv.reshape(-1), cfg)
+    A2 = np.zeros((6, 6)); b2 = np.zeros(6); rr2 = 0.0
+    for q in range(Hj.shape[0]):
+        for ch in range(3):
+            r = target[ch].reshape(-1)[q] - rgb[q, ch]
+            A2 += np.outer(Hj[q, ch], Hj[q, ch]); b2 += Hj[q, ch] * r; rr2 += r * r
+    np.testing.assert_allclose(A, A2, rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(b, b2, rtol=1e-12, atol=1e-14)
+    assert abs(rr - rr2) <= 1e-12 * rr2
+    assert np.allclose(A, A.T) and np.linalg.eigvalsh(A).min() > -1e-9 * np.abs(A).max()
+    step = np.linalg.solve(A, b)
+    # the linearisation recovers the perturbation to first order
+    np.testing.assert_allclose(step, xi_true, rtol=0.05, atol=2e-4)
