@@ -333,7 +333,8 @@ typedef enum gs_kernel_family {
     GS_KF_RASTER_BWD = 8,  /* a5 compositing backward */
     GS_KF_PROJECT_BWD = 9, /* a6/a7 projection backward and pose reduction */
     GS_KF_ADAM = 10,       /* a8 Adam */
-    GS_KF_COUNT = 11
+    GS_KF_POSE_NORMAL = 11, /* pose tangents, forward-mode compositing, normal equations */
+    GS_KF_COUNT = 12
 } gs_kernel_family;
 
 typedef struct gs_profile_entry {
@@ -353,6 +354,36 @@ GS_API int gs_profile_collect(gs_ctx* ctx, gs_stream stream, gs_profile_entry* o
                               int* n_out);
 /* Number of kernel launches (and memset nodes) this context has issued. */
 GS_API int64_t gs_launch_count(const gs_ctx* ctx);
+
+/* ---- pose normal equations of the photometric residual (Sec. II-D) ----
+ *
+ * The visual update of the paper's iterated error-state Kalman filter
+ * (Sec. II-D, Eq. minimization; Appendix A) linearises the rendered image in
+ * the camera pose.  For each view this computes, over every pixel x and
+ * channel ch, with H_ch(x) = dI_ch(x)/dxi the 6-vector derivative of the
+ * rendered colour with respect to the left perturbation xi = [dphi; dt],
+ * T_CW <- Exp(xi) T_CW, and r_ch(x) = target_ch(x) - I_ch(x):
+ *   normal[v][0..20]  = upper triangle of A = sum H H^T, row-major
+ *                       ((0,0), (0,1), ..., (0,5), (1,1), ..., (5,5)),
+ *   normal[v][21..26] = b = sum H r,
+ *   normal[v][27]     = sum r^2,
+ * so that the Gauss-Newton step of the pose is xi = A^-1 b.  H is obtained
+ * by forward-mode differentiation of Eq. raster through Eqs. q and spat and
+ * the view direction of the SH colour; culling and the set of contributing
+ * fragments are locally constant, clamped alphas and colours contribute zero
+ * derivative.  The per-tile sums are FP32, the per-view sums FP64.
+ *
+ * Requires gs_project and gs_bin on the same views and workspace (as
+ * gs_render_fwd) and a tile size of 8 or 16 (GS_ERR_UNSUPPORTED otherwise).
+ * target: device FP32, packed like rgb of gs_render_fwd.  scratch: device
+ * FP32 of gs_pose_normal_scratch() floats, 16-byte aligned, caller-owned,
+ * overwritten.  normal: device FP64 [n_views][28].  H_pix: NULL, or device
+ * FP32 [total pixels][3][6] (packed over views like T_final) receiving H.
+ * Errors: GS_ERR_INVALID_ARG, GS_ERR_UNSUPPORTED, GS_ERR_CUDA. */
+GS_API int gs_pose_normal_scratch(gs_ctx* ctx, const gs_view* views, int n_views, size_t* floats);
+GS_API int gs_pose_normal(gs_ctx* ctx, const gs_gaussians* g, const gs_view* views, int n_views,
+                          const gs_workspace* ws, const float* target, float* scratch, double* normal,
+                          float* H_pix, gs_stream stream);
 
 /* Measures, on the context's device, the throughput of the FP32 FMA pipe
  * (FLOP/s, an FMA counting 2) and of the ex2 special-function unit (ex2/s)

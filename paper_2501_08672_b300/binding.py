@@ -33,10 +33,10 @@ EXPORTED = ["gs_config_default", "gs_version", "gs_context_create", "gs_context_
             "gs_get_config", "gs_workspace_query", "gs_workspace_layout", "gs_project", "gs_bin",
             "gs_render_fwd", "gs_l1_loss", "gs_render_bwd", "gs_pose_grad", "gs_adam_step", "gs_sync_status",
             "gs_profile_enable", "gs_profile_collect", "gs_launch_count", "gs_adam_step_dev",
-            "gs_l1_loss_noalloc", "gs_calibrate_alu"]
+            "gs_l1_loss_noalloc", "gs_calibrate_alu", "gs_pose_normal_scratch", "gs_pose_normal"]
 
 KERNEL_FAMILIES = ["project", "depth_sort", "tile_scan", "emit", "tile_sort", "ranges", "raster_fwd", "l1",
-                   "raster_bwd", "project_bwd", "adam"]
+                   "raster_bwd", "project_bwd", "adam", "pose_normal"]
 
 
 class GsError(RuntimeError):
@@ -133,6 +133,9 @@ def lib():
         L.gs_launch_count.argtypes = [P]
         L.gs_launch_count.restype = ctypes.c_int64
         L.gs_calibrate_alu.argtypes = [P, P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+        L.gs_pose_normal_scratch.argtypes = [P, ctypes.POINTER(View), I, ctypes.POINTER(ctypes.c_size_t)]
+        L.gs_pose_normal.argtypes = [P, ctypes.POINTER(Gaussians), ctypes.POINTER(View), I,
+                                     ctypes.POINTER(Workspace), P, P, P, P, P]
         _lib = L
     return _lib
 
@@ -288,6 +291,19 @@ class Context:
         self._ck(lib().gs_pose_grad(self.h, ctypes.byref(g), views, len(views), ctypes.byref(ws), _ptr(T_final),
                                     _ptr(n_contrib), _ptr(dL_drgb), _ptr(dL_dpose), _stream(stream)))
 
+    def pose_normal_scratch(self, views):
+        """FP32 scratch floats gs_pose_normal needs for this batch of views."""
+        n = ctypes.c_size_t()
+        self._ck(lib().gs_pose_normal_scratch(self.h, views, len(views), ctypes.byref(n)))
+        return int(n.value)
+
+    def pose_normal(self, g, views, ws, target, scratch, normal, H_pix=None, stream=None):
+        """Per-view Gauss-Newton normal equations of the photometric residual in
+        the pose: normal [n_views, 28] float64 (A upper triangle, b, r.r)."""
+        _check_dev(normal, "normal", torch.float64, 28 * len(views))
+        self._ck(lib().gs_pose_normal(self.h, ctypes.byref(g), views, len(views), ctypes.byref(ws), _ptr(target),
+                                      _ptr(scratch), _ptr(normal), _ptr(H_pix), _stream(stream)))
+
     def adam_step(self, param, grad, m, v, lr, b1, b2, eps, step, segments=(), stream=None):
         segs = None
         ns = len(segments)
@@ -356,3 +372,17 @@ def unpack_images(flat, views, channels=3):
 
 def suggest_capacity(n_pairs, headroom=1.25):
     return int(math.ceil(max(n_pairs, 1024) * headroom))
+
+
+def unpack_normal(normal):
+    """[n_views, 28] normal-equation rows -> list of (A 6x6, b 6, r.r) in float64 numpy."""
+    out = []
+    rows = normal.detach().double().cpu().numpy().reshape(-1, 28)
+    iu = np.triu_indices(6)
+    for r in rows:
+        A = np.zeros((6, 6))
+        A[iu] = r[:21]
+        A = A + np.triu(A, 1).T
+        out.append((A, r[21:27].copy(), float(r[27])))
+    return out
+

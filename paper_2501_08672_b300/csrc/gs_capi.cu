@@ -617,6 +617,44 @@ int gs_pose_grad(gs_ctx* ctx, const gs_gaussians* g, const gs_view* views, int n
     return gs_render_bwd(ctx, g, views, n_views, ws, T_final, n_contrib, dL_drgb, nullptr, dL_dpose_dev, stream);
 }
 
+int gs_pose_normal_scratch(gs_ctx* ctx, const gs_view* views, int n_views, size_t* floats) {
+    if (!ctx) return GS_ERR_INVALID_ARG;
+    if (!floats) return fail(ctx, GS_ERR_INVALID_ARG, "floats is NULL");
+    Layout L;
+    int rc = make_layout(ctx, ctx->cfg, views, n_views, 0, L);
+    if (rc) return rc;
+    *floats = (size_t)4 * kPoseTan4 * (size_t)L.pub.n_records + (size_t)kNormalVals * (size_t)L.pub.n_tiles;
+    return GS_OK;
+}
+
+int gs_pose_normal(gs_ctx* ctx, const gs_gaussians* g, const gs_view* views, int n_views, const gs_workspace* ws,
+                   const float* target, float* scratch, double* normal, float* H_pix, gs_stream stream) {
+    if (!ctx) return GS_ERR_INVALID_ARG;
+    if (!target || !scratch || !normal) return fail(ctx, GS_ERR_INVALID_ARG, "target, scratch or normal is NULL");
+    if (reinterpret_cast<uintptr_t>(scratch) % 16)
+        return fail(ctx, GS_ERR_INVALID_ARG, "scratch is not 16-byte aligned");
+    if (!pose_normal_supported(ctx->cfg.tile_size))
+        return fail(ctx, GS_ERR_UNSUPPORTED, "pose normal equations need a tile size of 8 or 16 (config has %d)",
+                    ctx->cfg.tile_size);
+    Layout L;
+    int rc = check_ws(ctx, views, n_views, ws, L);
+    if (rc) return rc;
+    GaussPtrs gp;
+    if ((rc = check_gaussians(ctx, g, views, n_views, gp))) return rc;
+    DeviceGuard dg(ctx->device);
+    BatchParam bp;
+    make_batch(ctx->cfg, views, n_views, bp);
+    const WsPtrs wp = ws_ptrs(ws, L, bp.total_tiles);
+    const RenderConst rcst = make_rc(ctx->cfg);
+    const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    float4* tangents = reinterpret_cast<float4*>(scratch);
+    float* partials = scratch + (size_t)4 * kPoseTan4 * (size_t)L.pub.n_records;
+    cudaError_t e = launch_pose_tangents(bp, gp, rcst, wp, tangents, s, ctx->prof);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "gs_pose_normal (tangents)");
+    e = launch_pose_normal(bp, rcst, wp, tangents, target, partials, normal, H_pix, s, ctx->prof);
+    return e == cudaSuccess ? GS_OK : cuda_fail(ctx, e, "gs_pose_normal (compositing)");
+}
+
 namespace {
 int check_adam(gs_ctx* ctx, float* param, const float* grad, float* m, float* v, int64_t n, float lr, float b1,
                float b2, float eps, const gs_lowp_segment* segs, int n_segs) {

@@ -13,6 +13,8 @@ namespace gsb {
 constexpr int kMaxViews = GS_MAX_VIEWS;
 constexpr int kRecFloats = 12;   // projected record: 3 x float4
 constexpr int kGrad2D = 9;       // per-record 2D gradient
+constexpr int kPoseTan4 = 12;     // per-record pose tangents: 12 x float4 (see k_pose_tangents)
+constexpr int kNormalVals = 28;   // per-view normal equations: 21 + 6 + 1
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kLn2 = 0.6931471805599453f;
 
@@ -191,6 +193,12 @@ cudaError_t launch_bin(const BatchParam& bp, WsPtrs& ws, unsigned int* status,
                        unsigned long long* status_pairs, cudaStream_t s, Prof& pf);
 bool raster_variant_exists(int ts, int ppt, int batch);
 cudaError_t measure_alu(int sm_count, float* sink, cudaStream_t s, double* ffma_tflops, double* ex2_gops);
+cudaError_t launch_pose_tangents(const BatchParam& bp, const GaussPtrs& g, const RenderConst& rc,
+                                 const WsPtrs& ws, float4* tangents, cudaStream_t s, Prof& pf);
+bool pose_normal_supported(int ts);
+cudaError_t launch_pose_normal(const BatchParam& bp, const RenderConst& rc, const WsPtrs& ws,
+                               const float4* tangents, const float* target, float* partials, double* normal,
+                               float* H_pix, cudaStream_t s, Prof& pf);
 cudaError_t launch_render_fwd(const BatchParam& bp, const RenderConst& rc, const WsPtrs& ws,
                               float* rgb, float* T_final, uint32_t* n_contrib, uint32_t* n_used,
                               cudaStream_t s, Prof& pf);

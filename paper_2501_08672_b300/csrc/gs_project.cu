@@ -499,6 +499,101 @@ __global__ void k_pose_finish(const float* partials, int nblocks, int n_views, f
     if (threadIdx.x == 0) dL_dpose[vi * 6 + k] = s;
 }
 
+// Pose tangents of one record (view, Gaussian): derivatives of its projected
+// mean q, of Sigma2 and of its colour with respect to the left perturbation
+// xi = [dphi; dt] of the camera, T_CW <- Exp(xi) T_CW (Appendix A), for the
+// forward-mode compositing of the pose normal equations.  With p_C the
+// camera-frame mean, J the projection Jacobian and Mc = R_CW R S:
+//   dp_C/ddphi_k = e_k x p_C,  dp_C/ddt_k = e_k,  dR_CW/ddphi_k = [e_k]x R_CW,
+//   dq = J dp_C,  U = J Mc:  dU = dJ Mc + J [e_k]x Mc,
+//   dSigma2 = dU U^T + U dU^T,
+//   dcolour = d SH(dir) with dir = (mu - campos)/|mu - campos| and
+//   dcampos/ddt_k = -(row k of R_CW)^T (0 where the colour is clamped).
+// Layout per record, k = 0..5: tan[12 r + 2k] = (dq_x, dq_y, dS_a, dS_b),
+// tan[12 r + 2k + 1] = (dS_c, dc_r, dc_g, dc_b), with Sigma2 = [[a, b], [b, c]].
+// Records with no listed tile are skipped (never read).
+__global__ void __launch_bounds__(256) k_pose_tangents(const __grid_constant__ BatchParam bp, GaussPtrs g,
+                                                       RenderConst rc, WsPtrs ws, float4* __restrict__ tan) {
+    const ViewParam& V = bp.v[blockIdx.y];
+    const long long k0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long cnt = V.g_end - V.g_begin;
+    if (k0 >= cnt) return;
+    const long long i = V.g_begin + k0;
+    const long long r = V.rec_off + k0;
+    if (ws.tiles_touched[r] == 0) return;
+    Proj P;
+    float mu[3], ologit;
+    load_gaussian(g, i, mu, P, ologit);
+    if (!project_view(V, rc, mu, P)) return;
+    float col[3];
+    view_colour(V, g, i, mu, P, col);
+    float Mc[9];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+            Mc[3 * a + b] = V.R[3 * a] * P.M[b] + V.R[3 * a + 1] * P.M[3 + b] + V.R[3 * a + 2] * P.M[6 + b];
+    const float x = P.pc[0], y = P.pc[1], z = P.pc[2];
+    const float iz = 1.f / z, iz2 = iz * iz, iz3 = iz2 * iz;
+    const float j00 = V.fx * iz, j02 = -V.fx * x * iz2;
+    const float j11 = V.fy * iz, j12 = -V.fy * y * iz2;
+    const int K = (g.sh_degree + 1) * (g.sh_degree + 1);
+    float kk[3][3];  // SH degree-1 coefficients k1, k2, k3 per channel
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch)
+#pragma unroll
+        for (int m = 0; m < 3; ++m)
+            kk[ch][m] = g.sh_degree >= 1 ? load_as_float(g.sh, g.sh_dtype, i * K * 3 + 3 * (m + 1) + ch) : 0.f;
+    float4* out = tan + (size_t)kPoseTan4 * r;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        float dp[3] = {0.f, 0.f, 0.f};
+        if (k == 0) { dp[1] = -z; dp[2] = y; }
+        if (k == 1) { dp[0] = z; dp[2] = -x; }
+        if (k == 2) { dp[0] = -y; dp[1] = x; }
+        if (k >= 3) dp[k - 3] = 1.f;
+        const float dj00 = -V.fx * dp[2] * iz2;
+        const float dj02 = -V.fx * dp[0] * iz2 + 2.f * V.fx * x * dp[2] * iz3;
+        const float dj11 = -V.fy * dp[2] * iz2;
+        const float dj12 = -V.fy * dp[1] * iz2 + 2.f * V.fy * y * dp[2] * iz3;
+        const float dqx = j00 * dp[0] + j02 * dp[2];
+        const float dqy = j11 * dp[1] + j12 * dp[2];
+        float dU0[3], dU1[3];
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const float m0 = Mc[b], m1 = Mc[3 + b], m2 = Mc[6 + b];
+            // [e_k]x Mc, column b
+            float X0 = 0.f, X1 = 0.f, X2 = 0.f;
+            if (k == 0) { X1 = -m2; X2 = m1; }
+            if (k == 1) { X0 = m2; X2 = -m0; }
+            if (k == 2) { X0 = -m1; X1 = m0; }
+            dU0[b] = dj00 * m0 + dj02 * m2 + j00 * X0 + j02 * X2;
+            dU1[b] = dj11 * m1 + dj12 * m2 + j11 * X1 + j12 * X2;
+        }
+        const float* U0 = P.U;
+        const float* U1 = P.U + 3;
+        const float dSa = 2.f * (dU0[0] * U0[0] + dU0[1] * U0[1] + dU0[2] * U0[2]);
+        const float dSb = dU0[0] * U1[0] + dU0[1] * U1[1] + dU0[2] * U1[2] + U0[0] * dU1[0] + U0[1] * dU1[1] +
+                          U0[2] * dU1[2];
+        const float dSc = 2.f * (dU1[0] * U1[0] + dU1[1] * U1[1] + dU1[2] * U1[2]);
+        float dc[3] = {0.f, 0.f, 0.f};
+        if (k >= 3 && g.sh_degree >= 1) {
+            const float dv0 = V.R[3 * (k - 3)], dv1 = V.R[3 * (k - 3) + 1], dv2 = V.R[3 * (k - 3) + 2];
+            const float dd = P.dir[0] * dv0 + P.dir[1] * dv1 + P.dir[2] * dv2;
+            const float dr0 = (dv0 - P.dir[0] * dd) * P.inv_len;
+            const float dr1 = (dv1 - P.dir[1] * dd) * P.inv_len;
+            const float dr2 = (dv2 - P.dir[2] * dd) * P.inv_len;
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) {
+                const float draw = kShC1 * (-dr1 * kk[ch][0] + dr2 * kk[ch][1] - dr0 * kk[ch][2]);
+                dc[ch] = P.raw[ch] > 0.f ? draw : 0.f;
+            }
+        }
+        out[2 * k] = make_float4(dqx, dqy, dSa, dSb);
+        out[2 * k + 1] = make_float4(dSc, dc[0], dc[1], dc[2]);
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_project(const BatchParam& bp, const GaussPtrs& g, const RenderConst& rc,
@@ -526,6 +621,16 @@ cudaError_t launch_project_bwd(const BatchParam& bp, const GaussPtrs& g, const R
     const int pi = pf.begin(GS_KF_PROJECT_BWD, s, dL_dpose ? 2 : 1);
     k_project_bwd<<<nblk, 256, 0, s>>>(bp, g, rc, ws, gr, grads != nullptr, dL_dpose != nullptr, pose_blocks);
     if (dL_dpose) k_pose_finish<<<bp.n_views * 6, 32, 0, s>>>(ws.partials, pose_blocks, bp.n_views, dL_dpose);
+    pf.end(pi, s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pose_tangents(const BatchParam& bp, const GaussPtrs& g, const RenderConst& rc,
+                                 const WsPtrs& ws, float4* tangents, cudaStream_t s, Prof& pf) {
+    if (bp.max_count <= 0) return cudaSuccess;
+    dim3 grid((unsigned)((bp.max_count + 255) / 256), (unsigned)bp.n_views);
+    const int pi = pf.begin(GS_KF_POSE_NORMAL, s);
+    k_pose_tangents<<<grid, 256, 0, s>>>(bp, g, rc, ws, tangents);
     pf.end(pi, s);
     return cudaGetLastError();
 }

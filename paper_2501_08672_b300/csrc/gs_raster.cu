@@ -453,6 +453,201 @@ __global__ void k_l1_finish(const float* __restrict__ partials, int n, float* __
     }
 }
 
+// ---- pose normal equations (Sec. II-D) -------------------------------------
+//
+// Forward-mode compositing: per pixel, the colour C, transmittance T and their
+// derivatives dC (3 x 6), dT (6) with respect to the pose perturbation xi, over
+// the same fragments and with the same decisions as k_render_fwd.  With
+// m = (d.v1) v1 + (d.v2) v2 = M d (M = log2(e)/2 Sigma2^-1), the exponent
+// p = l - d^T M d moves by
+//   dp = 2 m . dq + 2 ln2 m^T dSigma2 m
+// (d = x - q; dM = -M dSigma2 M / (log2(e)/2)), alpha = 2^p by
+// dalpha = alpha ln2 dp unless clamped, and
+//   dC += dc w + c (dalpha T + alpha dT),  dT <- dT (1 - alpha) - T dalpha.
+// Each pixel then adds H H^T, H r and r^2 (H_ch = dC_ch + bg_ch dT,
+// r = target - (C + T bg)) to its thread's 28 sums; the tile sums them over
+// its warps and writes one FP32 partial per tile.  Each warp walks the list
+// on its own, kPNBatch records per step, compacted by footprint box as in the
+// forward.
+constexpr int kPNBatch = 16;
+
+template <int TS>
+__global__ void __launch_bounds__(TS * TS) k_render_pose_normal(const __grid_constant__ BatchParam bp,
+                                                                RenderConst rc,
+                                                                const float4* __restrict__ rec,
+                                                                const uint2* __restrict__ ranges,
+                                                                const uint32_t* __restrict__ tile_order,
+                                                                const uint32_t* __restrict__ svals,
+                                                                const float4* __restrict__ tan,
+                                                                const float* __restrict__ target,
+                                                                float* __restrict__ partials,
+                                                                float* __restrict__ H_pix) {
+    constexpr int NT = TS * TS;
+    constexpr int NW = NT / 32;
+    __shared__ float4 s_a[NW][kPNBatch];
+    __shared__ float4 s_b[NW][kPNBatch];
+    __shared__ float2 s_c[NW][kPNBatch];
+    __shared__ float4 s_t[NW][kPNBatch][kPoseTan4];
+    __shared__ float s_red[NW][kNormalVals];
+    const int t = threadIdx.x;
+    const int lane = t & 31;
+    const int w = t >> 5;
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    const int tile = (int)tile_order[blockIdx.x];
+    const ViewParam& V = bp.v[find_view_by_tile(bp, tile)];
+    const int lt = tile - V.tile_off;
+    const int ty = lt / V.tiles_x, tx = lt - ty * V.tiles_x;
+    const PixelMap<TS, 1> pm(tx, ty, t);
+    const int px = pm.px, py = pm.row(0);
+    const float fx = px + 0.5f, fy = py + 0.5f;
+    const WarpBox wb = warp_box(px, py, py);
+    const bool inside = px < V.W && py < V.H;
+    bool done = !inside;
+    float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
+    float dT[6], dC[3][6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        dT[k] = 0.f;
+        dC[0][k] = dC[1][k] = dC[2][k] = 0.f;
+    }
+    const uint2 rg = ranges[tile];
+    for (uint32_t start = rg.x; start < rg.y; start += kPNBatch) {
+        if (__all_sync(0xffffffffu, done)) break;
+        const uint32_t idx = start + lane;
+        bool reach = false;
+        uint32_t r = 0;
+        float4 a = make_float4(0.f, 0.f, 0.f, 0.f), c = a;
+        if (lane < kPNBatch && idx < rg.y) {
+            r = svals[idx];
+            a = rec[3 * r];
+            c = rec[3 * r + 2];
+            reach = wb.reaches(a.x, a.y, c.w);
+        }
+        const uint32_t m = __ballot_sync(0xffffffffu, reach);
+        if (reach) {
+            const int pos = __popc(m & lt_mask);
+            s_a[w][pos] = a;
+            s_b[w][pos] = rec[3 * r + 1];
+            s_c[w][pos] = make_float2(c.x, c.y);
+#pragma unroll
+            for (int q = 0; q < kPoseTan4; ++q) s_t[w][pos][q] = tan[(size_t)kPoseTan4 * r + q];
+        }
+        const int n = __popc(m);
+        __syncwarp();
+        if (!done) {
+            for (int j = 0; j < n; ++j) {
+                const float4 ra = s_a[w][j];
+                const float4 rb = s_b[w][j];
+                const float2 rc2 = s_c[w][j];
+                const float dx = fx - ra.x;
+                const float dy = fy - ra.y;
+                const float t1 = fmaf(dy, ra.w, dx * ra.z);
+                const float t2 = fmaf(dy, rb.y, dx * rb.x);
+                const float p = fmaf(-t1, t1, fmaf(-t2, t2, rb.z));
+                if (p < rc.log2_alpha_min) continue;
+                const float araw = ex2_approx(p);
+                const float alpha = fminf(rc.alpha_max, araw);
+                const float Tn = T * (1.f - alpha);
+                if (Tn < rc.T_min) {
+                    done = true;
+                    break;
+                }
+                const float wgt = alpha * T;
+                const float mx = fmaf(t1, ra.z, t2 * rb.x);
+                const float my = fmaf(t1, ra.w, t2 * rb.y);
+                const float sc = araw < rc.alpha_max ? alpha * kLn2 : 0.f;
+                const float k2 = 2.f * kLn2;
+                const float mm0 = k2 * mx * mx, mm1 = 2.f * k2 * mx * my, mm2 = k2 * my * my;
+                const float m2x = 2.f * mx, m2y = 2.f * my;
+#pragma unroll
+                for (int k = 0; k < 6; ++k) {
+                    const float4 ta = s_t[w][j][2 * k];
+                    const float4 tb = s_t[w][j][2 * k + 1];
+                    const float dp = fmaf(m2x, ta.x, fmaf(m2y, ta.y, fmaf(mm0, ta.z, fmaf(mm1, ta.w, mm2 * tb.x))));
+                    const float da = sc * dp;
+                    const float dw = fmaf(da, T, alpha * dT[k]);
+                    dC[0][k] = fmaf(tb.y, wgt, fmaf(rb.w, dw, dC[0][k]));
+                    dC[1][k] = fmaf(tb.z, wgt, fmaf(rc2.x, dw, dC[1][k]));
+                    dC[2][k] = fmaf(tb.w, wgt, fmaf(rc2.y, dw, dC[2][k]));
+                    dT[k] = fmaf(dT[k], 1.f - alpha, -T * da);
+                }
+                C0 = fmaf(rb.w, wgt, C0);
+                C1 = fmaf(rc2.x, wgt, C1);
+                C2 = fmaf(rc2.y, wgt, C2);
+                T = Tn;
+            }
+        }
+        __syncwarp();
+    }
+    // this pixel's terms of the normal equations
+    float acc[kNormalVals];
+#pragma unroll
+    for (int e = 0; e < kNormalVals; ++e) acc[e] = 0.f;
+    if (inside) {
+        const long long hw = (long long)V.W * V.H;
+        const long long pl = (long long)py * V.W + px;
+        const float* tg = target + 3 * V.pix_off;
+        const float Cc[3] = {C0, C1, C2};
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            float Hc[6];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) Hc[k] = fmaf(rc.bg[ch], dT[k], dC[ch][k]);
+            const float res = tg[ch * hw + pl] - fmaf(T, rc.bg[ch], Cc[ch]);
+            int e = 0;
+#pragma unroll
+            for (int i = 0; i < 6; ++i)
+#pragma unroll
+                for (int k = i; k < 6; ++k) {
+                    acc[e] = fmaf(Hc[i], Hc[k], acc[e]);
+                    ++e;
+                }
+#pragma unroll
+            for (int k = 0; k < 6; ++k) acc[21 + k] = fmaf(Hc[k], res, acc[21 + k]);
+            acc[27] = fmaf(res, res, acc[27]);
+            if (H_pix) {
+                float* hp = H_pix + 18 * (V.pix_off + pl) + 6 * ch;
+#pragma unroll
+                for (int k = 0; k < 6; ++k) hp[k] = Hc[k];
+            }
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < kNormalVals; ++e) {
+        float v = acc[e];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) s_red[w][e] = v;
+    }
+    __syncthreads();
+    if (t < kNormalVals) {
+        float v = 0.f;
+#pragma unroll
+        for (int ww = 0; ww < NW; ++ww) v += s_red[ww][t];
+        partials[(size_t)tile * kNormalVals + t] = v;
+    }
+}
+
+// Per view: the FP64 sum of its tiles' partials.  grid.x is the view.
+__global__ void __launch_bounds__(256) k_pose_normal_finish(const __grid_constant__ BatchParam bp,
+                                                            const float* __restrict__ partials,
+                                                            double* __restrict__ normal) {
+    __shared__ double s_sum[8][32];
+    const ViewParam& V = bp.v[blockIdx.x];
+    const int e = threadIdx.x & 31, grp = threadIdx.x >> 5;
+    const int ntiles = V.tiles_x * ((V.H + bp.tile_size - 1) / bp.tile_size);
+    double acc = 0.0;
+    if (e < kNormalVals)
+        for (int tl = grp; tl < ntiles; tl += 8) acc += (double)partials[(size_t)(V.tile_off + tl) * kNormalVals + e];
+    s_sum[grp][e] = acc;
+    __syncthreads();
+    if (threadIdx.x < kNormalVals) {
+        double v = 0.0;
+        for (int g = 0; g < 8; ++g) v += s_sum[g][threadIdx.x];
+        normal[(size_t)blockIdx.x * kNormalVals + threadIdx.x] = v;
+    }
+}
+
 }  // namespace
 
 // Compiled raster variants: (tile size, pixels per thread, staging depth).
@@ -591,4 +786,26 @@ cudaError_t launch_l1_static(const BatchParam& bp, const float* rgb, const float
     return cudaGetLastError();
 }
 
+bool pose_normal_supported(int ts) { return ts == 8 || ts == 16; }
+
+cudaError_t launch_pose_normal(const BatchParam& bp, const RenderConst& rc, const WsPtrs& ws,
+                               const float4* tangents, const float* target, float* partials, double* normal,
+                               float* H_pix, cudaStream_t s, Prof& pf) {
+    if (bp.total_tiles <= 0) return cudaSuccess;
+    const uint32_t* svals = ws.pvals[ws.sorted_buf];
+    const int pi = pf.begin(GS_KF_POSE_NORMAL, s, 2);
+    if (bp.tile_size == 8)
+        k_render_pose_normal<8><<<bp.total_tiles, 64, 0, s>>>(bp, rc, ws.rec, ws.ranges, ws.ovals[1], svals,
+                                                               tangents, target, partials, H_pix);
+    else if (bp.tile_size == 16)
+        k_render_pose_normal<16><<<bp.total_tiles, 256, 0, s>>>(bp, rc, ws.rec, ws.ranges, ws.ovals[1], svals,
+                                                                 tangents, target, partials, H_pix);
+    else
+        return cudaErrorInvalidValue;
+    k_pose_normal_finish<<<bp.n_views, 256, 0, s>>>(bp, partials, normal);
+    pf.end(pi, s);
+    return cudaGetLastError();
+}
+
 }  // namespace gsb
+

@@ -92,6 +92,17 @@ class Renderer:
     def pose_grad(self, g, dL_drgb):
         self.ctx.pose_grad(g, self.views, self.ws_struct, self.T, self.n_contrib, dL_drgb, self.dL_dpose)
 
+    def pose_normal(self, g, target, H_pix=None):
+        """Per-view Gauss-Newton normal equations of target - render in the pose
+        (Sec. II-D) over the bins of the last forward: returns [n_views, 28]
+        float64 (see gs_pose_normal)."""
+        need = self.ctx.pose_normal_scratch(self.views)
+        if getattr(self, "_pn_scratch", None) is None or self._pn_scratch.numel() < need:
+            self._pn_scratch = torch.empty(need, device=self.device, dtype=torch.float32)
+            self.normal = torch.zeros(self.n_views, 28, device=self.device, dtype=torch.float64)
+        self.ctx.pose_normal(g, self.views, self.ws_struct, target, self._pn_scratch, self.normal, H_pix)
+        return self.normal
+
     def images(self, flat=None):
         return B.unpack_images(self.rgb if flat is None else flat, self.view_dicts, 3)
 
@@ -151,8 +162,12 @@ class GaussianWindow:
         return [self.lowp.get(k, self.group(k)) for k in self.GROUPS]
 
     def struct(self):
+        """The C-ABI view of the render tensors.  It keeps this window alive as
+        long as it is referenced, so its device pointers stay valid."""
         t = self.render_tensors()
-        return B.gaussians_struct(*t, self.sh_degree)
+        g = B.gaussians_struct(*t, self.sh_degree)
+        g._owner = self
+        return g
 
     def grad_tensors(self):
         return [self.grad(k) for k in self.GROUPS]
@@ -313,6 +328,17 @@ class PoseTracker:
         gpose = self.iterate(view, target).double().cpu().numpy()
         xi = np.concatenate([-self.eta_rot * gpose[:3], -self.eta_trans * gpose[3:]])
         return apply_left(view, xi), gpose
+
+    def gauss_newton(self, view, target, damping=1e-6):
+        """One Gauss-Newton pose update from the normal equations of the
+        photometric residual (the linearisation the IESKF's visual update
+        uses, Sec. II-D): xi = (A + damping tr(A)/6 I)^-1 b, T <- Exp(xi) T.
+        Returns the new view and (A, b, r.r)."""
+        self.r.set_views([view])
+        self.r.forward(self.g)
+        A, b, rr = B.unpack_normal(self.r.pose_normal(self.g, target))[0]
+        xi = np.linalg.solve(A + damping * np.trace(A) / 6.0 * np.eye(6), b)
+        return apply_left(view, xi), (A, b, rr)
 
 
 # Compiled launch shapes of the compositing kernels: (tile size, pixels per
