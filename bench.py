@@ -19,6 +19,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -62,10 +63,17 @@ FLOP_CONTRIB = {"raster_fwd": 10.0, "raster_bwd": 34.0}
 FP32_LANES = 128
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # compositing kernels from one ncu capture of this workload, valid only for the
-# kernel source they were taken on (sha256 prefix of gs_raster.cu) and the
-# launch shape; otherwise the roofline reports traffic null.
-TRAFFIC = {"raster_fwd": ("4e7e4c1a585e08e3", (16, 2, 256), 116.9e6),
-           "raster_bwd": ("4e7e4c1a585e08e3", (16, 2, 256), 236.4e6)}
+# kernel source they were taken on (sha256 prefix of gs_raster.cu up to the L1
+# kernels, which holds both compositing kernels) and the launch shape;
+# otherwise the roofline reports traffic null.
+TRAFFIC = {"raster_fwd": ("46f36c50060e94a0", (16, 2, 256), 116.9e6),
+           "raster_bwd": ("46f36c50060e94a0", (16, 2, 256), 236.4e6)}
+
+
+def raster_source_hash():
+    with open(os.path.join(HERE, "paper_2501_08672_b300", "csrc", "gs_raster.cu")) as f:
+        src = f.read()
+    return hashlib.sha256(src[:src.index("constexpr int kL1Threads")].encode()).hexdigest()[:16]
 MAX_SM_MHZ = 2032
 
 
@@ -75,6 +83,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
+    ap.add_argument("--workload", default="window", choices=["window", "odometry"],
+                    help="window: the headline window step; odometry: Gauss-Newton pose iterations")
     ap.add_argument("--cpu-pixels", type=int, default=128, help="oracle pixels sampled per view")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=10)
@@ -340,9 +350,7 @@ def run_b300(args, world, rank, local):
         traffic = None
         if dominant in TRAFFIC:
             sha, tshape, tbytes = TRAFFIC[dominant]
-            with open(os.path.join(HERE, "paper_2501_08672_b300", "csrc", "gs_raster.cu"), "rb") as f:
-                cur = hashlib.sha256(f.read()).hexdigest()[:16]
-            if cur == sha and tuple(shape) == tshape:
+            if raster_source_hash() == sha and tuple(shape) == tshape:
                 traffic = tbytes
         roof = {"bound": "alu", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic, "traffic_unit": "bytes per launch (ncu DRAM read + write)",
@@ -412,10 +420,148 @@ def run_b300(args, world, rank, local):
         dist.destroy_process_group()
 
 
+ODO_METRIC = ("odometry Gauss-Newton pose iterations/s at 500k Gaussians, 1280x1024 "
+              "(project + bin + pose normal equations); % of roofline")
+ODO_N, ODO_W, ODO_H, ODO_F, ODO_FRAMES, ODO_ITERS = 500_000, 1280, 1024, 1200.0, 24, 5
+# algorithmic FP32 operations of the pose normal equations (FMA = 2):
+#   per visited fragment 12 (the test, as above);
+#   per contributing fragment 10 (forward) + 16 (m = M d, its products, the alpha
+#   tangent scale) + 6 x 28 (dp, dalpha, dw, dC (3), dT per pose component) = 194;
+#   per pixel 36 (H = dC + bg dT) + 126 (H H^T, 21 entries x 3 channels) + 36 (H r) + 6 (r^2) = 204
+FLOP_PN_VISITED, FLOP_PN_CONTRIB, FLOP_PN_PIXEL = 12.0, 194.0, 204.0
+
+
+def run_odometry(args, world, rank, local):
+    """One Gauss-Newton pose iteration per step on the odometry workload:
+    500k fixed Gaussians, one 1280x1024 view, frames on an arc, each started
+    from a pose perturbed by 2 degrees and 5 cm, ODO_ITERS iterations per
+    frame; each iteration projects, bins, builds the normal equations of the
+    photometric residual on the GPU, reads the 28 sums back and solves the
+    6x6 system on the host."""
+    import torch
+    from paper_2501_08672_b300 import binding as B
+    from paper_2501_08672_b300 import scenes
+    from paper_2501_08672_b300.render import GaussianWindow, Renderer, apply_left
+
+    torch.cuda.set_device(local)
+    n = ODO_N
+    params = scenes.box_room_scene(n, seed=2 + rank, sh_degree=1)
+    true_v, start_v = scenes.odometry_frames(ODO_FRAMES, ODO_W, ODO_H, ODO_F, seed=rank)
+    for v in true_v + start_v:
+        v["g_begin"], v["g_end"] = 0, n
+    win = GaussianWindow(params, local)
+    g = win.struct()
+    r = Renderer([true_v[0]], local, 16)
+    targets = []
+    most = 0
+    for v in true_v:                      # input generation: the camera frames
+        r.set_views([v])
+        r.forward(g, count=True)
+        most = max(most, r.last_pairs)
+        targets.append(r.rgb.clone())
+    r.ensure_capacity(int(most * 1.5))
+    torch.cuda.synchronize()
+
+    def pose_err(a, b):
+        D = np.eye(4); D[:3, :3] = np.asarray(a["R"], np.float64); D[:3, 3] = a["t"]
+        E = np.eye(4); E[:3, :3] = np.asarray(b["R"], np.float64); E[:3, 3] = b["t"]
+        X = D @ np.linalg.inv(E)
+        return math.degrees(math.acos(max(-1.0, min(1.0, (np.trace(X[:3, :3]) - 1) / 2)))), float(np.linalg.norm(X[:3, 3]))
+
+    def iterate(view, target, ev=None):
+        r.set_views([view])
+        if ev is not None:
+            ev[0].record()
+        r.ctx.project(g, r.views, r.ws_struct)
+        r.ctx.bin(r.views, r.ws_struct)
+        normal = r.pose_normal(g, target)
+        if ev is not None:
+            ev[1].record()
+        A, b, rr = B.unpack_normal(normal)[0]          # synchronises: D2H of 28 doubles
+        xi = np.linalg.solve(A + 1e-6 * np.trace(A) / 6.0 * np.eye(6), b)
+        return apply_left(view, xi), rr
+
+    # warm-up
+    v = start_v[0]
+    for _ in range(max(args.warmup, 3)):
+        v, _ = iterate(v, targets[0])
+    K = args.steps
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    sampler = ClockSampler(local)
+    r.ctx.profile(B.KERNEL_FAMILIES)
+    sampler.start()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    finals = []
+    k = 0
+    frame = 0
+    while k < K:
+        fr = frame % ODO_FRAMES
+        v = start_v[fr]
+        for _ in range(ODO_ITERS):
+            if k >= K:
+                break
+            v, rr = iterate(v, targets[fr], evs[k])
+            k += 1
+        finals.append(pose_err(v, true_v[fr]))
+        frame += 1
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    clocks = sampler.stop()
+    prof = r.ctx.profile_collect()
+    rc, need = r.check_status()
+    if rc != B.GS_OK:
+        raise RuntimeError("pair capacity exceeded in the timed region (%d needed)" % need)
+    dev_ms = float(sum(a.elapsed_time(b) for a, b in evs))
+    value = K / (dev_ms / 1e3)
+    # roofline of the pose-normal kernels from fragment counts at the last pose
+    n_used = torch.empty_like(r.n_contrib)
+    r.set_views([v])
+    r.forward(g, count=False, n_used=n_used)
+    torch.cuda.synchronize()
+    visited = float(r.n_contrib.double().sum().item())
+    contrib = float(n_used.double().sum().item())
+    pn_launches, pn_ms = prof.get("pose_normal", (0, 0.0))
+    calls = K
+    flop = FLOP_PN_VISITED * visited + FLOP_PN_CONTRIB * contrib + FLOP_PN_PIXEL * ODO_W * ODO_H
+    ffma, ex2 = r.ctx.calibrate_alu()
+    achieved = flop / (pn_ms / calls / 1e3) / 1e12
+    roof = {"bound": "alu", "kernel": "pose_normal (tangents + forward-mode compositing + FP64 totals)",
+            "achieved": achieved, "peak": ffma, "unit": "TFLOP/s", "frac": achieved / ffma, "traffic": None,
+            "avg_call_ms": pn_ms / calls, "visited_fragments": visited, "contributing_fragments": contrib,
+            "flop_per_call": flop, "peak_basis": "measured: FP32 FMA microbenchmark (gs_calibrate_alu, best of 3)"}
+    rot = [a for a, _ in finals]
+    trn = [t for _, t in finals]
+    line = {"metric": ODO_METRIC, "value": value, "unit": "it/s", "n_gpus": world, "steps": K,
+            "warmup": max(args.warmup, 3), "ms_per_step": dev_ms / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "odometry: 500k fixed planar Gaussians (SH degree 1), one 1280x1024 view, "
+                                   "%d frames on an arc, start poses perturbed by 2 deg and 5 cm, %d Gauss-Newton "
+                                   "iterations per frame" % (ODO_FRAMES, ODO_ITERS),
+                       "n_gaussians": n, "image": [ODO_W, ODO_H], "tile_size": 16,
+                       "timed": "device time of project + bin + pose normal equations per iteration (CUDA events)",
+                       "l2": "inputs larger than L2 (500k x 48 B records, 1.3 Mpix images)"},
+            "roofline": roof,
+            "kernel_ms_per_step": {kk: vv[1] / K for kk, vv in prof.items()},
+            "e2e": {"value": K / wall, "unit": "it/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 28 * 8,
+                    "note": "wall clock per iteration including the D2H of the normal equations and the host solve; "
+                            "targets are resident"},
+            "convergence": {"frames": len(finals), "median_final_rot_deg": float(np.median(rot)),
+                            "median_final_trans_m": float(np.median(trn)),
+                            "max_final_rot_deg": float(np.max(rot))},
+            "gpu_launches": int(sum(vv[0] for vv in prof.values())), "clocks": clocks}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     world, rank, local = dist_env()
-    if args.impl == "reference":
+    if args.workload == "odometry":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the reference arm times the window workload"}))
+            return
+        run_odometry(args, world, rank, local)
+    elif args.impl == "reference":
         run_reference(args, world, rank)
     else:
         run_b300(args, world, rank, local)
