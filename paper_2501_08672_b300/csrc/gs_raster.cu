@@ -59,6 +59,14 @@ struct WarpBox {
     }
 };
 
+// The exact test behind the box test: does the record's alpha >= alpha_min
+// ellipse reach a pixel centre of the warp's block (the test the binning uses
+// for tiles, with the same margin)?  Only meaningful when alpha_min > 0.
+__device__ __forceinline__ bool ellipse_reaches(const WarpBox& wb, float4 r0, float4 r1, float log2_alpha_min) {
+    const Footprint fp = make_footprint(r0, r1, r1.z - log2_alpha_min);
+    return footprint_hits_rect(fp, wb.cx - wb.hx, wb.cx + wb.hx, wb.cy - wb.hy, wb.cy + wb.hy);
+}
+
 __device__ __forceinline__ WarpBox warp_box(int px, int py_first, int py_last) {
     const int x0 = __reduce_min_sync(0xffffffffu, px), x1 = __reduce_max_sync(0xffffffffu, px);
     const int y0 = __reduce_min_sync(0xffffffffu, py_first), y1 = __reduce_max_sync(0xffffffffu, py_last);
@@ -132,18 +140,19 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_render_fwd(const __grid_const
             const uint32_t idx = start + q * 32 + lane;
             bool reach = false;
             uint32_t r = 0;
-            float4 a = make_float4(0.f, 0.f, 0.f, 0.f), c = a;
+            float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a, c = a;
             if (idx < rg.y) {
                 r = svals[idx];
                 a = rec[3 * r];
                 c = rec[3 * r + 2];
                 reach = wb.reaches(a.x, a.y, c.w);
+                if (reach) b = rec[3 * r + 1];
             }
             const uint32_t m = __ballot_sync(0xffffffffu, reach);
             if (reach) {
                 const int pos = n + __popc(m & lt_mask);
                 s_a[w][pos] = a;
-                s_b[w][pos] = rec[3 * r + 1];
+                s_b[w][pos] = b;
                 s_c[w][pos] = make_float2(c.x, c.y);
                 s_j[w][pos] = idx - rg.x + 1;
             }
@@ -284,18 +293,24 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_render_bwd(const __grid_const
             const int rel = hi - 1 - (q * 32 + lane);
             bool reach = false;
             uint32_t r = 0;
-            float4 a = make_float4(0.f, 0.f, 0.f, 0.f), c = a;
+            float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a, c = a;
             if (rel >= 0) {
                 r = svals[rg.x + rel];
                 a = rec[3 * r];
                 c = rec[3 * r + 2];
                 reach = wb.reaches(a.x, a.y, c.w);
+                if (reach) {
+                    b = rec[3 * r + 1];
+                    // a warp smaller than the tile also drops records whose
+                    // ellipse misses its block (the bins only test the tile)
+                    if (NW > 1 && rc.alpha_min > 0.f) reach = ellipse_reaches(wb, a, b, rc.log2_alpha_min);
+                }
             }
             const uint32_t m = __ballot_sync(0xffffffffu, reach);
             if (reach) {
                 const int pos = n + __popc(m & lt_mask);
                 s_a[warp][pos] = a;
-                s_b[warp][pos] = rec[3 * r + 1];
+                s_b[warp][pos] = b;
                 s_c[warp][pos] = make_float2(c.x, c.y);
                 s_r[warp][pos] = r;
                 s_rel[warp][pos] = rel;
@@ -517,17 +532,19 @@ __global__ void __launch_bounds__(TS * TS) k_render_pose_normal(const __grid_con
         bool reach = false;
         uint32_t r = 0;
         float4 a = make_float4(0.f, 0.f, 0.f, 0.f), c = a;
+        float4 b = a;
         if (lane < kPNBatch && idx < rg.y) {
             r = svals[idx];
             a = rec[3 * r];
             c = rec[3 * r + 2];
             reach = wb.reaches(a.x, a.y, c.w);
+            if (reach) b = rec[3 * r + 1];
         }
         const uint32_t m = __ballot_sync(0xffffffffu, reach);
         if (reach) {
             const int pos = __popc(m & lt_mask);
             s_a[w][pos] = a;
-            s_b[w][pos] = rec[3 * r + 1];
+            s_b[w][pos] = b;
             s_c[w][pos] = make_float2(c.x, c.y);
 #pragma unroll
             for (int q = 0; q < kPoseTan4; ++q) s_t[w][pos][q] = tan[(size_t)kPoseTan4 * r + q];
