@@ -178,8 +178,8 @@ typedef struct gs_ws_layout {
     size_t records;       /* float[M][12]: qx, qy, v1x, v1y, v2x, v2y, log2(opacity), r, g, b, depth, 0 */
     size_t rects;         /* int32[M][4]: x0|y0<<16, x1|y1<<16, first tile id of the view, tiles_x */
     size_t tiles_touched; /* uint32[M] */
-    size_t depth_keys;    /* uint32[M] low words of the 64-bit depth keys (two buffers) */
-    size_t depth_hi;      /* uint32[M] high words of the 64-bit depth keys */
+    size_t depth_keys;    /* uint32[M] low words of the 64-bit depth keys, record order (two buffers) */
+    size_t depth_hi;      /* uint32[M] high words of the 64-bit depth keys (sorted in place by gs_bin) */
     size_t depth_vals;    /* uint32[M] record indices (two buffers) */
     size_t pair_offsets;  /* uint64[M] */
     size_t pair_keys;     /* uint32[max_pairs] x 2 */

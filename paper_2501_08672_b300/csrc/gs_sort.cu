@@ -4,10 +4,12 @@
 // A least-significant-digit radix sort of 64-bit keys (tile << 32 | depth
 // bits) first sorts on the depth digits, which are identical for every pair
 // a Gaussian emits.  So the depth digits are sorted once per record (M keys)
-// instead of once per pair (P keys): records are radix-sorted by depth bits
-// (stable in record index), expanded into pairs in that order, and the pairs
-// are stably radix-sorted by tile id only (ceil(log2 T) bits).  The result is
-// the order of the full 64-bit sort with ties broken by record index.
+// instead of once per pair (P keys): records are put in depth order (a
+// stable radix sort on the high word of their 64-bit double-float depth key,
+// then runs of equal high words ordered by the low word), expanded into pairs
+// in that order, and the pairs are stably radix-sorted by tile id only
+// (ceil(log2 T) bits).  The result is the order of the full sort on
+// (tile, 64-bit depth key) with ties broken by record index.
 //
 // Every kernel reads counts from device memory, so the whole binning step
 // needs no host synchronisation and can be captured in a CUDA graph; the
@@ -269,11 +271,115 @@ __global__ void __launch_bounds__(1024) k_u32_apply(uint32_t* __restrict__ a, lo
         }
 }
 
-// Gathers the high key word of each record into sorted order.
-__global__ void k_gather_u32(const uint32_t* __restrict__ src, const uint32_t* __restrict__ idx, long long n,
-                             uint32_t* __restrict__ dst) {
+// Exclusive scan of a u32 array in place by one block: thread t scans a
+// contiguous chunk, a block scan of the chunk totals gives its offset.  For
+// the digit-major histograms of tiny sorts (up to kU32SingleScanMax entries,
+// e.g. the tile-order pass), where the three-phase scan is three
+// latency-bound launches; beyond a few thousand entries one block is slower
+// than the three phases (measured: 80 us against 15 us at 100k entries).
+constexpr long long kU32SingleScanMax = 1ll << 14;
+
+__global__ void __launch_bounds__(1024) k_u32_scan_single(uint32_t* __restrict__ a, long long n) {
+    __shared__ uint32_t s_w[32];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const long long per = (n + 1023) / 1024;
+    const long long b0 = (long long)t * per;
+    const long long b1 = b0 + per < n ? b0 + per : n;
+    uint32_t sum = 0;
+    for (long long i = b0; i < b1; ++i) sum += a[i];
+    uint32_t x = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_w[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t y = s_w[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t z = __shfl_up_sync(0xffffffffu, y, o);
+            if (lane >= o) y += z;
+        }
+        s_w[lane] = y;
+    }
+    __syncthreads();
+    uint32_t run = (w > 0 ? s_w[w - 1] : 0u) + x - sum;
+    for (long long i = b0; i < b1; ++i) {
+        const uint32_t v = a[i];
+        a[i] = run;
+        run += v;
+    }
+}
+
+// Depth order, second step.  The records are sorted stably by the high word
+// of their 64-bit depth key, so records with equal high words sit in runs in
+// record order; each run is put in (low word, record) order here, which is
+// the order of the full 64-bit key with ties by record index.  One thread
+// per run: insertion sort for short runs (the common case: coplanar splats),
+// heapsort beyond kFixupInsertion (a long run only costs time).  Culled
+// records (high word 0xFFFFFFFF, never listed) are left alone.
+constexpr long long kFixupInsertion = 48;
+
+__device__ __forceinline__ unsigned long long depth_lo_key(const uint32_t* lo, uint32_t v) {
+    return ((unsigned long long)lo[v] << 32) | v;
+}
+
+__device__ void heap_sift(uint32_t* a, long long root, long long n, const uint32_t* lo) {
+    const uint32_t v = a[root];
+    const unsigned long long kv = depth_lo_key(lo, v);
+    long long i = root;
+    while (true) {
+        long long c = 2 * i + 1;
+        if (c >= n) break;
+        unsigned long long kc = depth_lo_key(lo, a[c]);
+        if (c + 1 < n) {
+            const unsigned long long kr = depth_lo_key(lo, a[c + 1]);
+            if (kr > kc) {
+                ++c;
+                kc = kr;
+            }
+        }
+        if (kc <= kv) break;
+        a[i] = a[c];
+        i = c;
+    }
+    a[i] = v;
+}
+
+__global__ void __launch_bounds__(256) k_depth_fixup(const uint32_t* __restrict__ hi, uint32_t* __restrict__ vals,
+                                                     const uint32_t* __restrict__ lo, long long M) {
     const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j < n) dst[j] = src[idx[j]];
+    if (j >= M) return;
+    const uint32_t h = hi[j];
+    if (h == 0xFFFFFFFFu) return;
+    if (j > 0 && hi[j - 1] == h) return;      // not the first of its run
+    if (j + 1 >= M || hi[j + 1] != h) return;  // a run of one
+    long long e = j + 2;
+    while (e < M && hi[e] == h) ++e;
+    uint32_t* a = vals + j;
+    const long long n = e - j;
+    if (n <= kFixupInsertion) {
+        for (long long i = 1; i < n; ++i) {
+            const uint32_t v = a[i];
+            const unsigned long long kv = depth_lo_key(lo, v);
+            long long k = i - 1;
+            while (k >= 0 && depth_lo_key(lo, a[k]) > kv) {
+                a[k + 1] = a[k];
+                --k;
+            }
+            a[k + 1] = v;
+        }
+        return;
+    }
+    for (long long r = n / 2 - 1; r >= 0; --r) heap_sift(a, r, n, lo);
+    for (long long end = n - 1; end > 0; --end) {
+        const uint32_t t = a[0];
+        a[0] = a[end];
+        a[end] = t;
+        heap_sift(a, 0, end, lo);
+    }
 }
 
 // ---- tiles-touched scan in depth order ------------------------------------
@@ -505,7 +611,7 @@ int radix_blocks(unsigned long long n_host) {
 // between buffer 0 and 1; *result_buf receives the buffer holding the result.
 cudaError_t radix_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, const WsPtrs& ws,
                        unsigned long long n_host, const unsigned long long* n_dev, int key_bits,
-                       int* result_buf, cudaStream_t s) {
+                       int* result_buf, cudaStream_t s, Prof& pf) {
     const int passes = key_bits <= 0 ? 0 : (key_bits + 7) / 8;
     const int dbits = passes ? (key_bits + passes - 1) / passes : 0;
     const int nblk = radix_blocks(n_host);
@@ -519,9 +625,15 @@ cudaError_t radix_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, c
         const int shift = p * dbits;
         const int bits = key_bits - shift < dbits ? key_bits - shift : dbits;
         k_radix_upsweep<<<nblk, kRadixThreads, 0, s>>>(kin, n_host, n_dev, shift, bits, ws.hist);
-        k_u32_reduce<<<nparts, 1024, 0, s>>>(ws.hist, nh, ws.hist_part);
-        k_u32_top<<<1, 1024, 0, s>>>(ws.hist_part, nparts);
-        k_u32_apply<<<nparts, 1024, 0, s>>>(ws.hist, nh, ws.hist_part);
+        if (nh <= kU32SingleScanMax) {
+            k_u32_scan_single<<<1, 1024, 0, s>>>(ws.hist, nh);
+            pf.count(3);
+        } else {
+            pf.count(5);
+            k_u32_reduce<<<nparts, 1024, 0, s>>>(ws.hist, nh, ws.hist_part);
+            k_u32_top<<<1, 1024, 0, s>>>(ws.hist_part, nparts);
+            k_u32_apply<<<nparts, 1024, 0, s>>>(ws.hist, nh, ws.hist_part);
+        }
         k_radix_downsweep<<<nblk, kRadixThreads, 0, s>>>(kin, vin, kout, vout, n_host, n_dev, shift, bits, ws.hist);
         uint32_t* tk = kin; kin = kout; kout = tk;
         uint32_t* tv = vin; vin = vout; vout = tv;
@@ -537,24 +649,16 @@ cudaError_t launch_bin(const BatchParam& bp, WsPtrs& ws, unsigned int* status,
     const long long M = bp.total_recs;
     cudaError_t e;
     if (M <= 0) return cudaSuccess;
-    // 1. front-to-back order of records: 64-bit double-float depth keys
-    //    (low word first, then the high word), stable in record index
-    int pi = pf.begin(GS_KF_DEPTH_SORT, s, 8 * 5 + 1);
+    // 1. front-to-back order of records by the 64-bit double-float depth key:
+    //    a stable radix sort on the high word (4 passes, in place in dhi /
+    //    dvals[0]), then the runs of equal high words by (low word, record)
+    int pi = pf.begin(GS_KF_DEPTH_SORT, s, 1);  // the fix-up; radix_sort counts its own launches
     int dbuf = 0;
-    e = radix_sort(ws.dkeys[0], ws.dvals[0], ws.dkeys[1], ws.dvals[1], ws, (unsigned long long)M, nullptr, 32,
-                   &dbuf, s);
+    e = radix_sort(ws.dhi, ws.dvals[0], ws.dkeys[1], ws.dvals[1], ws, (unsigned long long)M, nullptr, 32, &dbuf, s,
+                   pf);
     if (e != cudaSuccess) return e;
-    k_gather_u32<<<(unsigned)((M + 255) / 256), 256, 0, s>>>(ws.dhi, ws.dvals[dbuf], M, ws.dkeys[1 - dbuf]);
-    {
-        uint32_t* hk = ws.dkeys[1 - dbuf];
-        uint32_t* hv = ws.dvals[dbuf];
-        uint32_t* ok = ws.dkeys[dbuf];
-        uint32_t* ov = ws.dvals[1 - dbuf];
-        int hb = 0;
-        e = radix_sort(hk, hv, ok, ov, ws, (unsigned long long)M, nullptr, 32, &hb, s);
-        if (e != cudaSuccess) return e;
-        dbuf = hb ? 1 - dbuf : dbuf;  // values end in hv (hb == 0) or ov (hb == 1)
-    }
+    uint32_t* sorted_hi = dbuf ? ws.dkeys[1] : ws.dhi;
+    k_depth_fixup<<<(unsigned)((M + 255) / 256), 256, 0, s>>>(sorted_hi, ws.dvals[dbuf], ws.dkeys[0], M);
     pf.end(pi, s);
     const uint32_t* order = ws.dvals[dbuf];
     // 2. exclusive scan of tiles-touched in that order
@@ -575,22 +679,21 @@ cudaError_t launch_bin(const BatchParam& bp, WsPtrs& ws, unsigned int* status,
     int tile_bits = 1;
     while ((1ll << tile_bits) < (long long)bp.total_tiles) ++tile_bits;
     int pbuf = 0;
-    pi = pf.begin(GS_KF_TILE_SORT, s, 5 * ((tile_bits + 7) / 8));
+    pi = pf.begin(GS_KF_TILE_SORT, s, 0);
     e = radix_sort(ws.pkeys[0], ws.pvals[0], ws.pkeys[1], ws.pvals[1], ws, (unsigned long long)ws.cap,
-                   ws.counters, tile_bits, &pbuf, s);
+                   ws.counters, tile_bits, &pbuf, s, pf);
     pf.end(pi, s);
     if (e != cudaSuccess) return e;
     ws.sorted_buf = pbuf;
     // 5. per-tile [start, end)
-    pi = pf.begin(GS_KF_RANGES, s, 2);
+    pi = pf.begin(GS_KF_RANGES, s, 3);  // memset, ranges, keys
     e = cudaMemsetAsync(ws.ranges, 0, sizeof(uint2) * (size_t)bp.total_tiles, s);
     if (e != cudaSuccess) return e;
     k_ranges<<<1184, 256, 0, s>>>(ws.pkeys[pbuf], ws.cap, ws.counters, (uint32_t)bp.total_tiles, ws.ranges);
     k_tile_keys<<<(bp.total_tiles + 255) / 256, 256, 0, s>>>(ws.ranges, bp.total_tiles, ws.okeys[0], ws.ovals[0]);
-    pf.count(6);
     int obuf = 0;
     e = radix_sort(ws.okeys[0], ws.ovals[0], ws.okeys[1], ws.ovals[1], ws, (unsigned long long)bp.total_tiles,
-                   nullptr, 8, &obuf, s);
+                   nullptr, 8, &obuf, s, pf);
     pf.end(pi, s);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();

@@ -256,12 +256,65 @@ def test_bins_are_sorted_and_complete():
                 elif m > Lim * 1.01 + 0.01:
                     assert i not in listed[t], "record %d listed in unreached tile %d" % (i, t)
     assert checked > 1000
-    # front to back: the high words of the 64-bit depth keys never decrease
-    hi = ws_view(r, L.depth_hi, np.uint32, M).astype(np.int64)
+    # front to back: the records' depths never decrease along a tile list
+    # (up to the rounding of the FP32 depth against the double-float key)
+    depth = rec[:, 10].astype(np.float64)
     for t in range(T):
         got = sv[ranges[t, 0]:ranges[t, 1]].tolist()
-        keys = hi[got]
-        assert np.all(keys[1:] >= keys[:-1]), "tile %d is not front to back" % t
+        d = depth[got]
+        assert np.all(d[1:] >= d[:-1] - 1e-6 * np.abs(d[:-1])), "tile %d is not front to back" % t
+
+
+def _tie_scene(mu, rng):
+    n = mu.shape[0]
+    return dict(means=mu.astype(np.float32), log_scales=rng.normal(-3.0, 0.3, (n, 3)).astype(np.float32),
+                quats=rng.standard_normal((n, 4)).astype(np.float32),
+                opacity=rng.normal(0.0, 1.0, n).astype(np.float32),
+                sh=rng.uniform(-0.5, 1.0, (n, 1, 3)).astype(np.float32), sh_degree=0)
+
+
+def test_depth_ties_long_run():
+    """3000 Gaussians on the fronto-parallel plane z = 3 seen by the identity
+    camera: every depth key is exactly equal (one run of 3000 for the tie
+    fix-up, past its insertion-sort length), so every tile lists its records
+    in record order."""
+    rng = np.random.default_rng(41)
+    n = 3000
+    mu = np.stack([rng.uniform(-1.2, 1.2, n), rng.uniform(-0.9, 0.9, n), np.full(n, 3.0)], 1)
+    p = _tie_scene(mu, rng)
+    v = scenes.identity_view(160, 120, 120.0, 0, n)
+    _, r = gpu_forward(p, [v])
+    L = r.layout()
+    T = L.n_tiles
+    npairs = int(r.last_pairs)
+    sv = ws_view(r, L.sorted_vals, np.uint32, npairs).astype(np.int64)
+    ranges = ws_view(r, L.tile_ranges, np.uint32, 2 * T).reshape(T, 2)
+    longest = 0
+    for t in range(T):
+        got = sv[ranges[t, 0]:ranges[t, 1]]
+        longest = max(longest, got.size)
+        assert np.all(np.diff(got) > 0), "tile %d: equal depths not in record order" % t
+    assert longest > 100
+
+
+def test_depth_near_ties_below_fp32(orc):
+    """Pairs of Gaussians one FP32 step apart in x under a rotated camera:
+    their camera depths differ by far less than an FP32 step of the depth, so
+    the high words of their depth keys mostly tie and the low word (the
+    Dot2 residual) orders them (short runs of the tie fix-up)."""
+    rng = np.random.default_rng(43)
+    m = 2000
+    base = np.stack([rng.uniform(-1.0, 1.0, m), rng.uniform(-0.8, 0.8, m), rng.uniform(2.5, 3.5, m)],
+                    1).astype(np.float32)
+    twin = base.copy()
+    twin[:, 0] = np.nextafter(base[:, 0], np.float32(np.inf))
+    mu = np.concatenate([base, twin])
+    p = _tie_scene(mu, rng)
+    n = mu.shape[0]
+    v = scenes.lookat_view((0.3, -0.2, -0.1), (0.0, 0.0, 3.0), 160, 120, 120.0, 0, n, up=(0, -1, 0))
+    _, r = gpu_forward(p, [v])
+    out = orc.render_view(p, v)
+    compare_images(out, r.images()[0].cpu().numpy(), r.T.cpu().numpy().reshape(120, 160))
 
 
 def l1_target(params, views, seed=5):
