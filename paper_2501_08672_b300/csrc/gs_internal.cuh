@@ -75,6 +75,7 @@ struct WsPtrs {
     float4* rec;             // [M][3]
     int4* rect;              // [M]
     uint32_t* tiles_touched; // [M]
+    uint32_t* hitmask;       // [M] listed tiles of rectangles of <= 32 tiles, bit = row-major index
     uint32_t* dkeys[2];      // [M] low depth-key words, then scratch
     uint32_t* dvals[2];      // [M]
     uint32_t* dhi;           // [M] high depth-key words
@@ -127,8 +128,11 @@ __device__ __forceinline__ int find_view_by_tile(const BatchParam& bp, int tile)
 // tiles.  Written with explicitly rounded operations so that every caller
 // gets bit-identical answers (the pair count and the pair emission must agree).
 // Footprints whose bounding rectangle spans more tiles than this are
-// counted and emitted by a whole warp (32 candidate tiles at a time).
+// counted by a whole warp (32 candidate tiles at a time).  For rectangles of
+// up to kMaskTiles tiles the projection also stores which tiles it listed
+// (a row-major bit mask), so the emission does not test them again.
 constexpr int kCoopTiles = 8;
+constexpr int kMaskTiles = 32;
 
 struct Footprint {
     float qx, qy, A, B, C, nBoA, nBoC, lim;  // nBoA = -B/A, nBoC = -B/C

@@ -184,6 +184,8 @@ __global__ void __launch_bounds__(256) k_project(const __grid_constant__ BatchPa
     const long long r = V.rec_off + k;
     bool coop = false;  // footprint counted by the whole warp below
     int area = 0;
+    uint32_t mask = 0;  // listed tiles (row-major bits) when area <= kMaskTiles
+    Footprint fp{};
 
     float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0;
     int4 rect = make_int4(0, 0, V.tile_off, V.tiles_x);
@@ -253,16 +255,21 @@ __global__ void __launch_bounds__(256) k_project(const __grid_constant__ BatchPa
             uint32_t hits = 0;
             area = (tx1 - tx0) * (ty1 - ty0);
             coop = live && rc.alpha_min > 0.f && area > kCoopTiles;
+            if (rc.alpha_min > 0.f) fp = make_footprint(r0, r1, r1.z - rc.log2_alpha_min);
             if (coop) {
                 hits = 0;  // counted cooperatively below
             } else if (rc.alpha_min > 0.f) {
-                const Footprint fp = make_footprint(r0, r1, r1.z - rc.log2_alpha_min);
+                int bit = 0;
                 for (int ty = ty0; ty < ty1; ++ty)
-                    for (int tx = tx0; tx < tx1; ++tx)
-                        hits += footprint_hits_rect(fp, tx * ts + 0.5f, tx * ts + ts - 0.5f, ty * ts + 0.5f,
-                                                    ty * ts + ts - 0.5f);
+                    for (int tx = tx0; tx < tx1; ++tx, ++bit)
+                        if (footprint_hits_rect(fp, tx * ts + 0.5f, tx * ts + ts - 0.5f, ty * ts + 0.5f,
+                                                ty * ts + ts - 0.5f)) {
+                            ++hits;
+                            mask |= 1u << bit;
+                        }
             } else {
                 hits = (uint32_t)((tx1 - tx0) * (ty1 - ty0));
+                mask = area >= 32 ? 0xFFFFFFFFu : (1u << area) - 1u;
             }
             touched = hits;
             float zhi, zlo;
@@ -272,31 +279,42 @@ __global__ void __launch_bounds__(256) k_project(const __grid_constant__ BatchPa
             if (hits == 0 && !coop) key_hi = key_lo = 0xFFFFFFFFu;
         }
     }
-    // Large footprints: the warp tests their candidate tiles 32 at a time.
+    // Large footprints: the warp tests their candidate tiles 32 at a time,
+    // with the owner's footprint broadcast.
     for (unsigned big = __ballot_sync(0xffffffffu, coop); big; big &= big - 1) {
         const int src = __ffs(big) - 1;
-        const float4 b0 = make_float4(__shfl_sync(0xffffffffu, r0.x, src), __shfl_sync(0xffffffffu, r0.y, src),
-                                      __shfl_sync(0xffffffffu, r0.z, src), __shfl_sync(0xffffffffu, r0.w, src));
-        const float4 b1 = make_float4(__shfl_sync(0xffffffffu, r1.x, src), __shfl_sync(0xffffffffu, r1.y, src),
-                                      __shfl_sync(0xffffffffu, r1.z, src), __shfl_sync(0xffffffffu, r1.w, src));
+        Footprint bf;
+        bf.qx = __shfl_sync(0xffffffffu, fp.qx, src);
+        bf.qy = __shfl_sync(0xffffffffu, fp.qy, src);
+        bf.A = __shfl_sync(0xffffffffu, fp.A, src);
+        bf.B = __shfl_sync(0xffffffffu, fp.B, src);
+        bf.C = __shfl_sync(0xffffffffu, fp.C, src);
+        bf.nBoA = __shfl_sync(0xffffffffu, fp.nBoA, src);
+        bf.nBoC = __shfl_sync(0xffffffffu, fp.nBoC, src);
+        bf.lim = __shfl_sync(0xffffffffu, fp.lim, src);
         const int rx = __shfl_sync(0xffffffffu, rect.x, src), ry = __shfl_sync(0xffffffffu, rect.y, src);
         const int bx0 = rx & 0xFFFF, by0 = (rx >> 16) & 0xFFFF, bx1 = ry & 0xFFFF, by1 = (ry >> 16) & 0xFFFF;
         const int bw = bx1 - bx0, barea = bw * (by1 - by0);
-        const Footprint fp = make_footprint(b0, b1, b1.z - rc.log2_alpha_min);
         const int ts = bp.tile_size;
         const int lane = threadIdx.x & 31;
-        uint32_t c = 0;
-        for (int q = lane; q < barea; q += 32) {
+        uint32_t c = 0, bmask = 0;
+        for (int q0 = 0; q0 < barea; q0 += 32) {
+            const int q = q0 + lane;
             const int ty = by0 + q / bw, tx = bx0 + q % bw;
-            c += footprint_hits_rect(fp, tx * ts + 0.5f, tx * ts + ts - 0.5f, ty * ts + 0.5f, ty * ts + ts - 0.5f);
+            const bool hit = q < barea && footprint_hits_rect(bf, tx * ts + 0.5f, tx * ts + ts - 0.5f,
+                                                              ty * ts + 0.5f, ty * ts + ts - 0.5f);
+            const uint32_t m = __ballot_sync(0xffffffffu, hit);
+            c += __popc(m);
+            if (q0 == 0) bmask = m;
         }
-        c = __reduce_add_sync(0xffffffffu, c);
         if (lane == src) {
             touched = c;
+            mask = barea <= kMaskTiles ? bmask : 0u;
             if (c == 0) key_hi = key_lo = 0xFFFFFFFFu;
         }
     }
     if (!live) return;
+    ws.hitmask[r] = mask;
     ws.rec[3 * r + 0] = r0;
     ws.rec[3 * r + 1] = r1;
     ws.rec[3 * r + 2] = r2;

@@ -484,11 +484,14 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const uint32_t* __r
 
 // One thread per record in depth order writes its pairs (global tile id,
 // record index) at its scanned offset, row-major over the tiles of its
-// rectangle that its footprint reaches (the test k_project counted with).
-// Rectangles of more than kCoopTiles tiles are emitted by the whole warp:
-// 32 candidate tiles at a time, hits compacted in row-major order by ballot.
+// rectangle that its footprint reaches.  Rectangles of up to kMaskTiles
+// tiles come with the mask of listed tiles from the projection; larger ones
+// are tested again (the test k_project counted with) by the whole warp, 32
+// candidate tiles at a time with the owner's footprint broadcast, hits
+// compacted in row-major order by ballot.
 __global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ order,
                                               const uint32_t* __restrict__ touched,
+                                              const uint32_t* __restrict__ hitmask,
                                               const int4* __restrict__ rects,
                                               const float4* __restrict__ rec,
                                               const unsigned long long* __restrict__ offsets, long long M,
@@ -504,27 +507,24 @@ __global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ order
     const int tx0 = rc.x & 0xFFFF, ty0 = (rc.x >> 16) & 0xFFFF;
     const int tx1 = rc.y & 0xFFFF, ty1 = (rc.y >> 16) & 0xFFFF;
     const bool test = log2_alpha_min > -3.0e38f;
-    const int area = (tx1 - tx0) * (ty1 - ty0);
-    const bool coop = tt > 0 && test && area > kCoopTiles;
+    const int w = tx1 - tx0;
+    const int area = w * (ty1 - ty0);
+    const bool coop = tt > 0 && test && area > kMaskTiles;
     const unsigned long long o0 = offsets[j];
     const unsigned long long oend = o0 + tt;
     const unsigned long long ucap = (unsigned long long)cap;
-    if (tt > 0 && !coop) {
-        const float4 r0 = rec[3 * r], r1 = rec[3 * r + 1];
-        const Footprint fp = make_footprint(r0, r1, r1.z - log2_alpha_min);
+    if (tt > 0 && area <= kMaskTiles) {
+        uint32_t mk = hitmask[r];
         unsigned long long o = o0;
-        for (int ty = ty0; ty < ty1 && o < oend; ++ty) {
-            const uint32_t row = (uint32_t)rc.z + (uint32_t)ty * (uint32_t)rc.w;
-            for (int tx = tx0; tx < tx1 && o < oend; ++tx) {
-                if (test && !footprint_hits_rect(fp, tx * ts + 0.5f, tx * ts + ts - 0.5f, ty * ts + 0.5f,
-                                                 ty * ts + ts - 0.5f))
-                    continue;
-                if (o < ucap) {
-                    pkeys[o] = row + (uint32_t)tx;
-                    pvals[o] = r;
-                }
-                ++o;
+        while (mk && o < oend) {
+            const int bit = __ffs(mk) - 1;
+            mk &= mk - 1;
+            const int ty = ty0 + bit / w, tx = tx0 + bit % w;
+            if (o < ucap) {
+                pkeys[o] = (uint32_t)rc.z + (uint32_t)ty * (uint32_t)rc.w + (uint32_t)tx;
+                pvals[o] = r;
             }
+            ++o;
         }
         // never reached when both passes agree; keeps the pair list well formed
         for (; o < oend; ++o)
@@ -532,11 +532,31 @@ __global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ order
                 pkeys[o] = 0xFFFFFFFFu;
                 pvals[o] = r;
             }
+    } else if (tt > 0 && !coop) {
+        // exact mode (no test): every tile of a large rectangle
+        unsigned long long o = o0;
+        for (int ty = ty0; ty < ty1 && o < oend; ++ty)
+            for (int tx = tx0; tx < tx1 && o < oend; ++tx, ++o)
+                if (o < ucap) {
+                    pkeys[o] = (uint32_t)rc.z + (uint32_t)ty * (uint32_t)rc.w + (uint32_t)tx;
+                    pvals[o] = r;
+                }
     }
+    Footprint fp{};
+    if (coop) fp = make_footprint(rec[3 * r], rec[3 * r + 1], rec[3 * r + 1].z - log2_alpha_min);
     const int lane = threadIdx.x & 31;
     const uint32_t lt = (1u << lane) - 1u;
     for (unsigned big = __ballot_sync(0xffffffffu, coop); big; big &= big - 1) {
         const int src = __ffs(big) - 1;
+        Footprint bf;
+        bf.qx = __shfl_sync(0xffffffffu, fp.qx, src);
+        bf.qy = __shfl_sync(0xffffffffu, fp.qy, src);
+        bf.A = __shfl_sync(0xffffffffu, fp.A, src);
+        bf.B = __shfl_sync(0xffffffffu, fp.B, src);
+        bf.C = __shfl_sync(0xffffffffu, fp.C, src);
+        bf.nBoA = __shfl_sync(0xffffffffu, fp.nBoA, src);
+        bf.nBoC = __shfl_sync(0xffffffffu, fp.nBoC, src);
+        bf.lim = __shfl_sync(0xffffffffu, fp.lim, src);
         const uint32_t br = __shfl_sync(0xffffffffu, r, src);
         const int rx = __shfl_sync(0xffffffffu, rc.x, src), ry = __shfl_sync(0xffffffffu, rc.y, src);
         const uint32_t bz = (uint32_t)__shfl_sync(0xffffffffu, rc.z, src);
@@ -545,13 +565,11 @@ __global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ order
         const unsigned long long boend = __shfl_sync(0xffffffffu, oend, src);
         const int bx0 = rx & 0xFFFF, by0 = (rx >> 16) & 0xFFFF, bx1 = ry & 0xFFFF, by1 = (ry >> 16) & 0xFFFF;
         const int bw = bx1 - bx0, barea = bw * (by1 - by0);
-        const float4 r0 = rec[3 * br], r1 = rec[3 * br + 1];
-        const Footprint fp = make_footprint(r0, r1, r1.z - log2_alpha_min);
         unsigned long long o = bo0;
         for (int base = 0; base < barea; base += 32) {
             const int q = base + lane;
             const int ty = by0 + q / bw, tx = bx0 + q % bw;
-            const bool hit = q < barea && footprint_hits_rect(fp, tx * ts + 0.5f, tx * ts + ts - 0.5f,
+            const bool hit = q < barea && footprint_hits_rect(bf, tx * ts + 0.5f, tx * ts + ts - 0.5f,
                                                               ty * ts + 0.5f, ty * ts + ts - 0.5f);
             const uint32_t m = __ballot_sync(0xffffffffu, hit);
             const unsigned long long pos = o + __popc(m & lt);
@@ -670,7 +688,7 @@ cudaError_t launch_bin(const BatchParam& bp, WsPtrs& ws, unsigned int* status,
     pf.end(pi, s);
     // 3. expand records into (tile, record) pairs
     pi = pf.begin(GS_KF_EMIT, s);
-    k_emit<<<(unsigned)((M + 255) / 256), 256, 0, s>>>(order, ws.tiles_touched, ws.rect, ws.rec, ws.offsets, M,
+    k_emit<<<(unsigned)((M + 255) / 256), 256, 0, s>>>(order, ws.tiles_touched, ws.hitmask, ws.rect, ws.rec, ws.offsets, M,
                                                        ws.cap, bp.tile_size, ws.log2_alpha_min, ws.pkeys[0],
                                                        ws.pvals[0]);
     pf.end(pi, s);

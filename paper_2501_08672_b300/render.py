@@ -225,7 +225,9 @@ class WindowOptimizer:
         self.step_dev = torch.tensor([w.step_count], dtype=torch.int64, device=w.device)
         torch.cuda.synchronize()
         g = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(g):
+        # thread-local capture: CUDA calls other host threads make meanwhile
+        # (another library's, an allocator's) do not invalidate it
+        with torch.cuda.graph(g, capture_error_mode="thread_local"):
             r.forward(self._g, count=False)
             r.l1(self.targets)
             r.backward(self._g, r.dL_drgb, grads=self._grads)
