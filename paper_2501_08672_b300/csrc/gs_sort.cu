@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_upsweep(const uint32_t*
 // per digit and over the digits then places every key stably within the
 // tile, the tile is staged digit-sorted in shared memory and written out in
 // runs of consecutive positions.
-__global__ void __launch_bounds__(kRadixThreads) k_radix_downsweep(
+__global__ void __launch_bounds__(kRadixThreads, 3) k_radix_downsweep(
     const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
     uint32_t* __restrict__ vout, unsigned long long n_host, const unsigned long long* n_dev, int shift,
     int bits, const uint32_t* __restrict__ hist) {
