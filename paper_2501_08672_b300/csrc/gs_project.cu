@@ -212,9 +212,11 @@ __global__ void __launch_bounds__(256) k_project(const __grid_constant__ BatchPa
         // sqrt(r2 Sigma2_xx), sqrt(r2 Sigma2_yy).  The small margin only adds
         // pixels where alpha < alpha_min.
         float lo_x = 0.f, hi_x = (float)(V.W - 1), lo_y = 0.f, hi_y = (float)(V.H - 1);
+        float ex = 65504.f, ey = 65504.f;  // half-widths of the box (exact mode: unbounded)
         if (rc.alpha_min > 0.f) {
             const float r2 = 2.f * logf(sigma / rc.alpha_min) * 1.001f;
-            const float ex = sqrtf(r2 * P.a), ey = sqrtf(r2 * P.c);
+            ex = sqrtf(r2 * P.a);
+            ey = sqrtf(r2 * P.c);
             lo_x = fmaxf(ceilf(qx - ex - 0.5f), 0.f);
             hi_x = fminf(floorf(qx + ex - 0.5f), (float)(V.W - 1));
             lo_y = fmaxf(ceilf(qy - ey - 0.5f), 0.f);
@@ -237,12 +239,7 @@ __global__ void __launch_bounds__(256) k_project(const __grid_constant__ BatchPa
         r1 = make_float4(-ex1 * s2, ex0 * s2, log2f(sigma), col[0]);
         // half-extents of the footprint's bounding box, rounded up to FP16, for
         // the raster kernels' per-warp culling (full image in exact mode)
-        float hx = 65504.f, hy = 65504.f;
-        if (rc.alpha_min > 0.f) {
-            const float r2v = 2.f * logf(sigma / rc.alpha_min) * 1.001f;
-            hx = fminf(sqrtf(r2v * P.a) + 0.5f, 65504.f);
-            hy = fminf(sqrtf(r2v * P.c) + 0.5f, 65504.f);
-        }
+        const float hx = fminf(ex + 0.5f, 65504.f), hy = fminf(ey + 0.5f, 65504.f);
         const __half2 ext = __halves2half2(__float2half_ru(hx), __float2half_ru(hy));
         r2 = make_float4(col[1], col[2], P.pc[2], *reinterpret_cast<const float*>(&ext));
         if (lo_x <= hi_x && lo_y <= hi_y) {
