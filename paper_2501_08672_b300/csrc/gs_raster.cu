@@ -224,8 +224,15 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_render_fwd(const __grid_const
 // with one atomic per (warp, record, component); the factor ln 2, the
 // principal axes and the conversion to the natural conic are applied in
 // the projection backward.
+// Register budget of the backward: enough blocks for 24 resident warps per
+// SM (the kernel is issue-bound and its warps stall on short dependency
+// chains, so occupancy buys issue slots).
+// (From 4 pixels per thread on, the cap would spill: no target there.)
+template <int NT, int PPT>
+constexpr int bwd_min_blocks() { return PPT >= 4 ? 1 : (768 / NT > 32 ? 32 : 768 / NT); }
+
 template <int TS, int PPT, int BATCH>
-__global__ void __launch_bounds__(TS * TS / PPT) k_render_bwd(const __grid_constant__ BatchParam bp,
+__global__ void __launch_bounds__(TS * TS / PPT, bwd_min_blocks<TS * TS / PPT, PPT>()) k_render_bwd(const __grid_constant__ BatchParam bp,
                                                               RenderConst rc,
                                                               const float4* __restrict__ rec,
                                                               const uint2* __restrict__ ranges,
