@@ -115,9 +115,12 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_render_fwd(const __grid_const
     const int px = pm.px;
     const float fx = px + 0.5f;
     const WarpBox wb = warp_box(px, pm.row(0), pm.row(PPT - 1));
-    float fy[PPT], T[PPT], C0[PPT], C1[PPT], C2[PPT];
+    // thr[k]: the exponent a fragment must reach at pixel k; +inf once the
+    // pixel is saturated (or outside the image), so one compare both skips
+    // faint fragments and finished pixels
+    float fy[PPT], T[PPT], C0[PPT], C1[PPT], C2[PPT], thr[PPT];
     uint32_t last[PPT], used[PPT];
-    bool done[PPT];
+    const float kDone = __int_as_float(0x7f800000);
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
         fy[k] = pm.row(k) + 0.5f;
@@ -125,14 +128,14 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_render_fwd(const __grid_const
         C0[k] = C1[k] = C2[k] = 0.f;
         last[k] = 0;
         used[k] = 0;
-        done[k] = !(px < V.W && pm.row(k) < V.H);
+        thr[k] = (px < V.W && pm.row(k) < V.H) ? rc.log2_alpha_min : kDone;
     }
     const uint2 rg = ranges[tile];
 
     for (uint32_t start = rg.x; start < rg.y; start += WB) {
         bool all = true;
 #pragma unroll
-        for (int k = 0; k < PPT; ++k) all = all && done[k];
+        for (int k = 0; k < PPT; ++k) all = all && thr[k] == kDone;
         if (__all_sync(0xffffffffu, all)) break;
         int n = 0;
 #pragma unroll
@@ -169,16 +172,15 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_render_fwd(const __grid_const
                 const float u1 = dx * a.z, u2 = dx * b.x;
 #pragma unroll
                 for (int k = 0; k < PPT; ++k) {
-                    if (done[k]) continue;
                     const float dy = fy[k] - a.y;
                     const float t1 = fmaf(dy, a.w, u1);
                     const float t2 = fmaf(dy, b.y, u2);
                     const float p = fmaf(-t1, t1, fmaf(-t2, t2, b.z));
-                    if (p < rc.log2_alpha_min) continue;
+                    if (p < thr[k]) continue;  // faint fragment, or pixel finished
                     const float alpha = fminf(rc.alpha_max, ex2_approx(p));
                     const float Tn = T[k] * (1.f - alpha);
                     if (Tn < rc.T_min) {
-                        done[k] = true;
+                        thr[k] = kDone;
                         continue;
                     }
                     const float wgt = alpha * T[k];
