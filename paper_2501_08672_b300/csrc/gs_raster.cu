@@ -348,12 +348,12 @@ __global__ void __launch_bounds__(TS * TS / PPT, bwd_min_blocks<TS * TS / PPT, P
                 const float u1 = dx * a.z, u2 = dx * b.x;
 #pragma unroll
                 for (int k = 0; k < PPT; ++k) {
-                    if (rel >= nc[k]) continue;
                     const float dy = fy[k] - a.y;
                     const float t1 = fmaf(dy, a.w, u1);
                     const float t2 = fmaf(dy, b.y, u2);
                     const float p = fmaf(-t1, t1, fmaf(-t2, t2, b.z));
-                    if (p < rc.log2_alpha_min) continue;
+                    // behind the pixel's last contributor, or a faint fragment
+                    if (rel >= nc[k] || p < rc.log2_alpha_min) continue;
                     any = true;
                     const float araw = ex2_approx(p);
                     const float alpha = fminf(rc.alpha_max, araw);
