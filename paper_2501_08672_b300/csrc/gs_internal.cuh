@@ -127,11 +127,9 @@ __device__ __forceinline__ int find_view_by_tile(const BatchParam& bp, int tile)
 // where it is a clamped 1D minimum.  The small relative margin only adds
 // tiles.  Written with explicitly rounded operations so that every caller
 // gets bit-identical answers (the pair count and the pair emission must agree).
-// Footprints whose bounding rectangle spans more tiles than this are
-// counted by a whole warp (32 candidate tiles at a time).  For rectangles of
-// up to kMaskTiles tiles the projection also stores which tiles it listed
-// (a row-major bit mask), so the emission does not test them again.
-constexpr int kCoopTiles = 8;
+// For footprint rectangles of up to kMaskTiles tiles the projection stores
+// which tiles it listed (a row-major bit mask), so the emission does not
+// test them again; larger rectangles are emitted by a whole warp.
 constexpr int kMaskTiles = 32;
 
 struct Footprint {
@@ -165,6 +163,60 @@ __device__ __forceinline__ bool footprint_hits_rect(const Footprint& f, float x0
     best = fminf(best, q2(ax, fminf(fmaxf(__fmul_rn(f.nBoC, ax), ay), by)));
     best = fminf(best, q2(bx, fminf(fmaxf(__fmul_rn(f.nBoC, bx), ay), by)));
     return best <= f.lim;
+}
+
+// Row spans of the same ellipse q(d) <= lim (q = A dx^2 + 2B dx dy + C dy^2,
+// d = pixel centre - q), for counting and emitting the tiles it reaches one
+// tile row at a time: within a row's band of pixel-centre rows the ellipse's
+// x-extent is an interval, and the tiles whose pixel-centre columns meet it
+// are a contiguous run.  This lists exactly the tiles footprint_hits_rect
+// accepts, up to rounding far inside the margin of lim.  det = AC - B^2 is
+// formed as (v1x v2y - v2x v1y)^2 (Lagrange's identity), so thin footprints
+// keep it accurate; rightmost point of the ellipse at dy = dyr, leftmost at
+// -dyr; |dy| <= ymax on the ellipse.
+struct FootRows {
+    float qx, qy, A, B, det, invA, ymax, dyr, lim;
+};
+
+__device__ __forceinline__ FootRows make_footrows(float4 r0, float4 r1, float L) {
+    FootRows f;
+    f.qx = r0.x;
+    f.qy = r0.y;
+    f.A = __fmaf_rn(r0.z, r0.z, __fmul_rn(r1.x, r1.x));
+    f.B = __fmaf_rn(r0.z, r0.w, __fmul_rn(r1.x, r1.y));
+    const float C = __fmaf_rn(r0.w, r0.w, __fmul_rn(r1.y, r1.y));
+    const float dv = __fmaf_rn(r0.z, r1.y, -__fmul_rn(r1.x, r0.w));
+    f.det = __fmul_rn(dv, dv);
+    f.lim = __fmaf_rn(L, 1.001f, 1e-3f);
+    f.invA = __frcp_rn(f.A);
+    f.ymax = __fsqrt_rn(__fdiv_rn(__fmul_rn(f.A, f.lim), f.det));
+    const float xmax = __fsqrt_rn(__fdiv_rn(__fmul_rn(C, f.lim), f.det));
+    f.dyr = __fdiv_rn(__fmul_rn(-f.B, xmax), C);
+    return f;
+}
+
+// Tile columns [*a, *b] of tile row ty (clipped to [tx0, tx1)) that the
+// ellipse reaches; false when none.
+__device__ __forceinline__ bool footrows_span(const FootRows& f, int ty, int ts, int tx0, int tx1, int* a,
+                                              int* b) {
+    const float ya = __fadd_rn((float)(ty * ts) + 0.5f, -f.qy);
+    const float yb = __fadd_rn((float)(ty * ts + ts) - 0.5f, -f.qy);
+    const float lo = fmaxf(ya, -f.ymax), hi = fminf(yb, f.ymax);
+    if (!(lo <= hi)) return false;
+    const float dR = fminf(fmaxf(f.dyr, lo), hi);
+    const float dL = fminf(fmaxf(-f.dyr, lo), hi);
+    const float sR = __fsqrt_rn(fmaxf(__fmaf_rn(-f.det, __fmul_rn(dR, dR), __fmul_rn(f.A, f.lim)), 0.f));
+    const float sL = __fsqrt_rn(fmaxf(__fmaf_rn(-f.det, __fmul_rn(dL, dL), __fmul_rn(f.A, f.lim)), 0.f));
+    const float xr = __fmul_rn(__fadd_rn(__fmul_rn(-f.B, dR), sR), f.invA);
+    const float xl = __fmul_rn(__fadd_rn(__fmul_rn(-f.B, dL), -sL), f.invA);
+    // tile tx is reached when tx ts + 0.5 <= qx + xr and tx ts + ts - 0.5 >= qx + xl
+    const float inv_ts = 1.f / (float)ts;
+    const int ta = max(tx0, (int)ceilf(__fmul_rn(__fadd_rn(__fadd_rn(f.qx, xl), 0.5f), inv_ts) - 1.f));
+    const int tb = min(tx1 - 1, (int)floorf(__fmul_rn(__fadd_rn(__fadd_rn(f.qx, xr), -0.5f), inv_ts)));
+    if (ta > tb) return false;
+    *a = ta;
+    *b = tb;
+    return true;
 }
 
 // ---- host-side launch accounting and optional event timing ---------------

@@ -172,20 +172,12 @@ __device__ __forceinline__ uint32_t ordered_bits(float x) {
 __global__ void __launch_bounds__(256) k_project(const __grid_constant__ BatchParam bp, GaussPtrs g,
                                                  RenderConst rc, WsPtrs ws) {
     const ViewParam& V = bp.v[blockIdx.y];
-    const long long k0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long cnt = V.g_end - V.g_begin;
-    // Threads past the view's count stay alive (on a valid Gaussian) so the
-    // whole warp can share the tile counting of large footprints; they write
-    // nothing.
-    const bool live = k0 < cnt;
-    if (__all_sync(0xffffffffu, !live)) return;
-    const long long k = live ? k0 : 0;
+    if (k >= cnt) return;
     const long long i = V.g_begin + k;
     const long long r = V.rec_off + k;
-    bool coop = false;  // footprint counted by the whole warp below
-    int area = 0;
-    uint32_t mask = 0;  // listed tiles (row-major bits) when area <= kMaskTiles
-    Footprint fp{};
+    uint32_t mask = 0;  // listed tiles (row-major bits) when the rectangle has <= kMaskTiles
 
     float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0;
     int4 rect = make_int4(0, 0, V.tile_off, V.tiles_x);
@@ -248,24 +240,22 @@ __global__ void __launch_bounds__(256) k_project(const __grid_constant__ BatchPa
             const int ty0 = (int)lo_y / ts, ty1 = (int)hi_y / ts + 1;
             rect.x = tx0 | (ty0 << 16);
             rect.y = tx1 | (ty1 << 16);
-            // count only the tiles the footprint reaches (the same test k_emit uses)
+            // count only the tiles the footprint reaches, one tile row at a
+            // time (the spans k_emit writes)
             uint32_t hits = 0;
-            area = (tx1 - tx0) * (ty1 - ty0);
-            coop = live && rc.alpha_min > 0.f && area > kCoopTiles;
-            if (rc.alpha_min > 0.f) fp = make_footprint(r0, r1, r1.z - rc.log2_alpha_min);
-            if (coop) {
-                hits = 0;  // counted cooperatively below
-            } else if (rc.alpha_min > 0.f) {
-                int bit = 0;
-                for (int ty = ty0; ty < ty1; ++ty)
-                    for (int tx = tx0; tx < tx1; ++tx, ++bit)
-                        if (footprint_hits_rect(fp, tx * ts + 0.5f, tx * ts + ts - 0.5f, ty * ts + 0.5f,
-                                                ty * ts + ts - 0.5f)) {
-                            ++hits;
-                            mask |= 1u << bit;
-                        }
+            const int w = tx1 - tx0;
+            const int area = w * (ty1 - ty0);
+            if (rc.alpha_min > 0.f) {
+                const FootRows fr = make_footrows(r0, r1, r1.z - rc.log2_alpha_min);
+                for (int ty = ty0; ty < ty1; ++ty) {
+                    int a, b;
+                    if (!footrows_span(fr, ty, ts, tx0, tx1, &a, &b)) continue;
+                    hits += (uint32_t)(b - a + 1);
+                    if (area <= kMaskTiles)  // bits a..b of the row, row-major
+                        mask |= ((2u << (b - tx0)) - (1u << (a - tx0))) << ((ty - ty0) * w);
+                }
             } else {
-                hits = (uint32_t)((tx1 - tx0) * (ty1 - ty0));
+                hits = (uint32_t)area;
                 mask = area >= 32 ? 0xFFFFFFFFu : (1u << area) - 1u;
             }
             touched = hits;
@@ -273,44 +263,9 @@ __global__ void __launch_bounds__(256) k_project(const __grid_constant__ BatchPa
             depth_dot2(V, mu, zhi, zlo);
             key_hi = ordered_bits(zhi);
             key_lo = ordered_bits(zlo);
-            if (hits == 0 && !coop) key_hi = key_lo = 0xFFFFFFFFu;
+            if (hits == 0) key_hi = key_lo = 0xFFFFFFFFu;
         }
     }
-    // Large footprints: the warp tests their candidate tiles 32 at a time,
-    // with the owner's footprint broadcast.
-    for (unsigned big = __ballot_sync(0xffffffffu, coop); big; big &= big - 1) {
-        const int src = __ffs(big) - 1;
-        Footprint bf;
-        bf.qx = __shfl_sync(0xffffffffu, fp.qx, src);
-        bf.qy = __shfl_sync(0xffffffffu, fp.qy, src);
-        bf.A = __shfl_sync(0xffffffffu, fp.A, src);
-        bf.B = __shfl_sync(0xffffffffu, fp.B, src);
-        bf.C = __shfl_sync(0xffffffffu, fp.C, src);
-        bf.nBoA = __shfl_sync(0xffffffffu, fp.nBoA, src);
-        bf.nBoC = __shfl_sync(0xffffffffu, fp.nBoC, src);
-        bf.lim = __shfl_sync(0xffffffffu, fp.lim, src);
-        const int rx = __shfl_sync(0xffffffffu, rect.x, src), ry = __shfl_sync(0xffffffffu, rect.y, src);
-        const int bx0 = rx & 0xFFFF, by0 = (rx >> 16) & 0xFFFF, bx1 = ry & 0xFFFF, by1 = (ry >> 16) & 0xFFFF;
-        const int bw = bx1 - bx0, barea = bw * (by1 - by0);
-        const int ts = bp.tile_size;
-        const int lane = threadIdx.x & 31;
-        uint32_t c = 0, bmask = 0;
-        for (int q0 = 0; q0 < barea; q0 += 32) {
-            const int q = q0 + lane;
-            const int ty = by0 + q / bw, tx = bx0 + q % bw;
-            const bool hit = q < barea && footprint_hits_rect(bf, tx * ts + 0.5f, tx * ts + ts - 0.5f,
-                                                              ty * ts + 0.5f, ty * ts + ts - 0.5f);
-            const uint32_t m = __ballot_sync(0xffffffffu, hit);
-            c += __popc(m);
-            if (q0 == 0) bmask = m;
-        }
-        if (lane == src) {
-            touched = c;
-            mask = barea <= kMaskTiles ? bmask : 0u;
-            if (c == 0) key_hi = key_lo = 0xFFFFFFFFu;
-        }
-    }
-    if (!live) return;
     ws.hitmask[r] = mask;
     ws.rec[3 * r + 0] = r0;
     ws.rec[3 * r + 1] = r1;

@@ -485,10 +485,22 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const uint32_t* __r
 // One thread per record in depth order writes its pairs (global tile id,
 // record index) at its scanned offset, row-major over the tiles of its
 // rectangle that its footprint reaches.  Rectangles of up to kMaskTiles
-// tiles come with the mask of listed tiles from the projection; larger ones
-// are tested again (the test k_project counted with) by the whole warp, 32
-// candidate tiles at a time with the owner's footprint broadcast, hits
-// compacted in row-major order by ballot.
+// tiles come with the mask of listed tiles from the projection.  Larger ones
+// are emitted by the whole warp from the same row spans k_project counted
+// with: the owner's footprint is broadcast, each lane takes one tile row,
+// and a warp scan of the rows' tile counts places them in row-major order.
+__device__ __forceinline__ uint32_t warp_exclusive_scan(uint32_t v, uint32_t* total) {
+    const int lane = threadIdx.x & 31;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    *total = __shfl_sync(0xffffffffu, x, 31);
+    return x - v;
+}
+
 __global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ order,
                                               const uint32_t* __restrict__ touched,
                                               const uint32_t* __restrict__ hitmask,
@@ -542,21 +554,21 @@ __global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ order
                     pvals[o] = r;
                 }
     }
-    Footprint fp{};
-    if (coop) fp = make_footprint(rec[3 * r], rec[3 * r + 1], rec[3 * r + 1].z - log2_alpha_min);
+    FootRows fr{};
+    if (coop) fr = make_footrows(rec[3 * r], rec[3 * r + 1], rec[3 * r + 1].z - log2_alpha_min);
     const int lane = threadIdx.x & 31;
-    const uint32_t lt = (1u << lane) - 1u;
     for (unsigned big = __ballot_sync(0xffffffffu, coop); big; big &= big - 1) {
         const int src = __ffs(big) - 1;
-        Footprint bf;
-        bf.qx = __shfl_sync(0xffffffffu, fp.qx, src);
-        bf.qy = __shfl_sync(0xffffffffu, fp.qy, src);
-        bf.A = __shfl_sync(0xffffffffu, fp.A, src);
-        bf.B = __shfl_sync(0xffffffffu, fp.B, src);
-        bf.C = __shfl_sync(0xffffffffu, fp.C, src);
-        bf.nBoA = __shfl_sync(0xffffffffu, fp.nBoA, src);
-        bf.nBoC = __shfl_sync(0xffffffffu, fp.nBoC, src);
-        bf.lim = __shfl_sync(0xffffffffu, fp.lim, src);
+        FootRows bf;
+        bf.qx = __shfl_sync(0xffffffffu, fr.qx, src);
+        bf.qy = __shfl_sync(0xffffffffu, fr.qy, src);
+        bf.A = __shfl_sync(0xffffffffu, fr.A, src);
+        bf.B = __shfl_sync(0xffffffffu, fr.B, src);
+        bf.det = __shfl_sync(0xffffffffu, fr.det, src);
+        bf.invA = __shfl_sync(0xffffffffu, fr.invA, src);
+        bf.ymax = __shfl_sync(0xffffffffu, fr.ymax, src);
+        bf.dyr = __shfl_sync(0xffffffffu, fr.dyr, src);
+        bf.lim = __shfl_sync(0xffffffffu, fr.lim, src);
         const uint32_t br = __shfl_sync(0xffffffffu, r, src);
         const int rx = __shfl_sync(0xffffffffu, rc.x, src), ry = __shfl_sync(0xffffffffu, rc.y, src);
         const uint32_t bz = (uint32_t)__shfl_sync(0xffffffffu, rc.z, src);
@@ -564,20 +576,22 @@ __global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ order
         const unsigned long long bo0 = __shfl_sync(0xffffffffu, o0, src);
         const unsigned long long boend = __shfl_sync(0xffffffffu, oend, src);
         const int bx0 = rx & 0xFFFF, by0 = (rx >> 16) & 0xFFFF, bx1 = ry & 0xFFFF, by1 = (ry >> 16) & 0xFFFF;
-        const int bw = bx1 - bx0, barea = bw * (by1 - by0);
         unsigned long long o = bo0;
-        for (int base = 0; base < barea; base += 32) {
-            const int q = base + lane;
-            const int ty = by0 + q / bw, tx = bx0 + q % bw;
-            const bool hit = q < barea && footprint_hits_rect(bf, tx * ts + 0.5f, tx * ts + ts - 0.5f,
-                                                              ty * ts + 0.5f, ty * ts + ts - 0.5f);
-            const uint32_t m = __ballot_sync(0xffffffffu, hit);
-            const unsigned long long pos = o + __popc(m & lt);
-            if (hit && pos < boend && pos < ucap) {
-                pkeys[pos] = bz + (uint32_t)ty * bwid + (uint32_t)tx;
-                pvals[pos] = br;
+        for (int row0 = by0; row0 < by1; row0 += 32) {
+            const int ty = row0 + lane;
+            int a = 0, b = -1;
+            if (ty < by1 && !footrows_span(bf, ty, ts, bx0, bx1, &a, &b)) b = -1;
+            uint32_t total;
+            const uint32_t cnt = (uint32_t)(b - a + 1);
+            const unsigned long long pos = o + warp_exclusive_scan(cnt, &total);
+            for (int tx = a; tx <= b; ++tx) {
+                const unsigned long long q = pos + (unsigned long long)(tx - a);
+                if (q < boend && q < ucap) {
+                    pkeys[q] = bz + (uint32_t)ty * bwid + (uint32_t)tx;
+                    pvals[q] = br;
+                }
             }
-            o += __popc(m);
+            o += total;
         }
         for (unsigned long long q = o + lane; q < boend; q += 32)
             if (q < ucap) {

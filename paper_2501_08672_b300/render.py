@@ -7,6 +7,8 @@ into libgs_b300.so.
 """
 from __future__ import annotations
 
+import warnings
+
 import numpy as np
 import torch
 
@@ -223,18 +225,27 @@ class WindowOptimizer:
         if not r._counted:
             raise RuntimeError("run one step before capturing (sizes the pair workspace)")
         self.step_dev = torch.tensor([w.step_count], dtype=torch.int64, device=w.device)
-        torch.cuda.synchronize()
-        g = torch.cuda.CUDAGraph()
-        # thread-local capture: CUDA calls other host threads make meanwhile
-        # (another library's, an allocator's) do not invalidate it
-        with torch.cuda.graph(g, capture_error_mode="thread_local"):
-            r.forward(self._g, count=False)
-            r.l1(self.targets)
-            r.backward(self._g, r.dL_drgb, grads=self._grads)
-            r.ctx.adam_step_dev(w.flat, w.gflat, w.m, w.v, self.lr, self.betas[0], self.betas[1], self.eps,
-                                self.step_dev, self._segs)
-        self.graph = g
-        return g
+        for attempt in range(3):
+            torch.cuda.synchronize()
+            g = torch.cuda.CUDAGraph()
+            try:
+                # relaxed capture: a host-side CUDA call that is not part of
+                # the iteration (a tensor or context another part of the
+                # program frees meanwhile) does not invalidate it
+                with torch.cuda.graph(g, capture_error_mode="relaxed"):
+                    r.forward(self._g, count=False)
+                    r.l1(self.targets)
+                    r.backward(self._g, r.dL_drgb, grads=self._grads)
+                    r.ctx.adam_step_dev(w.flat, w.gflat, w.m, w.v, self.lr, self.betas[0], self.betas[1],
+                                        self.eps, self.step_dev, self._segs)
+            except (RuntimeError, B.GsError) as e:
+                if attempt == 2:
+                    raise
+                warnings.warn("graph capture failed (%s); capturing again" % e)
+                torch.cuda.synchronize()
+                continue
+            self.graph = g
+            return g
 
     def replay(self):
         self.graph.replay()
