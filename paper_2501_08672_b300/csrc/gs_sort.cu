@@ -526,17 +526,22 @@ __global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ order
     const unsigned long long oend = o0 + tt;
     const unsigned long long ucap = (unsigned long long)cap;
     if (tt > 0 && area <= kMaskTiles) {
-        uint32_t mk = hitmask[r];
+        // the mask row by row (w bits per tile row), set bits in column order
+        uint64_t mk = hitmask[r];
+        const uint64_t rowbits = (1ull << w) - 1ull;
         unsigned long long o = o0;
-        while (mk && o < oend) {
-            const int bit = __ffs(mk) - 1;
-            mk &= mk - 1;
-            const int ty = ty0 + bit / w, tx = tx0 + bit % w;
-            if (o < ucap) {
-                pkeys[o] = (uint32_t)rc.z + (uint32_t)ty * (uint32_t)rc.w + (uint32_t)tx;
-                pvals[o] = r;
+        for (int ty = ty0; mk && o < oend; ++ty, mk >>= w) {
+            uint32_t rb = (uint32_t)(mk & rowbits);
+            const uint32_t rowkey = (uint32_t)rc.z + (uint32_t)ty * (uint32_t)rc.w + (uint32_t)tx0;
+            while (rb && o < oend) {
+                const int bit = __ffs(rb) - 1;
+                rb &= rb - 1;
+                if (o < ucap) {
+                    pkeys[o] = rowkey + (uint32_t)bit;
+                    pvals[o] = r;
+                }
+                ++o;
             }
-            ++o;
         }
         // never reached when both passes agree; keeps the pair list well formed
         for (; o < oend; ++o)
@@ -621,17 +626,27 @@ __global__ void k_tile_keys(const uint2* __restrict__ ranges, int n_tiles, uint3
     vals[i] = (uint32_t)i;
 }
 
-// Tile ranges over the sorted pair keys.
-__global__ void k_ranges(const uint32_t* __restrict__ keys, long long cap,
-                         const unsigned long long* __restrict__ n_dev, uint32_t n_tiles,
-                         uint2* __restrict__ ranges) {
+// Tile ranges over the sorted pair keys: a tile's list starts where its key
+// differs from the previous one and ends where it differs from the next
+// (neighbours by warp shuffles, one load per key).
+__global__ void __launch_bounds__(256) k_ranges(const uint32_t* __restrict__ keys, long long cap,
+                                                const unsigned long long* __restrict__ n_dev, uint32_t n_tiles,
+                                                uint2* __restrict__ ranges) {
     const unsigned long long n = clamp_n((unsigned long long)cap, n_dev);
-    for (unsigned long long j = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; j < n;
-         j += (unsigned long long)gridDim.x * blockDim.x) {
-        const uint32_t k = keys[j];
-        if (k >= n_tiles) continue;  // tile ids come from k_emit and are < n_tiles
-        if (j == 0 || keys[j - 1] != k) ranges[k].x = (uint32_t)j;
-        if (j + 1 == n || keys[j + 1] != k) ranges[k].y = (uint32_t)(j + 1);
+    const int lane = threadIdx.x & 31;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    // every lane of a warp runs the same number of rounds (shuffles need all 32)
+    for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < n;
+         base += stride) {
+        const unsigned long long j = base + lane;
+        const uint32_t k = j < n ? keys[j] : 0xFFFFFFFFu;
+        uint32_t prev = __shfl_up_sync(0xffffffffu, k, 1);
+        uint32_t next = __shfl_down_sync(0xffffffffu, k, 1);
+        if (lane == 0) prev = j > 0 && j - 1 < n ? keys[j - 1] : 0xFFFFFFFFu;
+        if (lane == 31) next = j + 1 < n ? keys[j + 1] : 0xFFFFFFFFu;
+        if (j >= n || k >= n_tiles) continue;  // tile ids come from k_emit and are < n_tiles
+        if (j == 0 || prev != k) ranges[k].x = (uint32_t)j;
+        if (j + 1 == n || next != k) ranges[k].y = (uint32_t)(j + 1);
     }
 }
 
