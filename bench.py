@@ -41,16 +41,6 @@ FOCAL = 600.0
 LR = 1e-3
 WORKLOAD = "box-room sliding window: 200k planar Gaussians (SH degree 1), 8 keyframes 640x512 on a 2 m arc"
 
-# Algorithmic FP32 work (FMA counted as 2 FLOP; the ex2 and divide of the
-# special-function unit are not counted).  Every visited fragment (pixel,
-# Gaussian) evaluates the exponent l - (d.v1)^2 - (d.v2)^2: one offset, two
-# projections (fma + mul) and two fma, plus its share of the per-column
-# offset = 10 FLOP.  A contributing fragment adds, in the forward, the alpha
-# clamp, 1 - alpha, the transmittance update, the weight and three colour fma
-# = 10 FLOP; in the backward, the transmittance recovery (2), weight and
-# colour gradient (1 + 6), light-behind differences and alpha gradient
-# (3 + 5 + 1), light-behind update (6), exponent gradient (2), mean gradient
-# (10), conic gradient (8) and opacity term (1) = 45 FLOP.
 # Algorithmic FP32 operations per fragment (FMA = 2; compares, min/max and
 # selects not counted; ex2 and the divide count 1 each):
 #   every visited fragment:  d = x - q (2), t_k = d . v_k (2 x 3), p = l - t1^2 - t2^2 (4)   = 12
@@ -74,6 +64,8 @@ def raster_source_hash():
     with open(os.path.join(HERE, "paper_2501_08672_b300", "csrc", "gs_raster.cu")) as f:
         src = f.read()
     return hashlib.sha256(src[:src.index("constexpr int kL1Threads")].encode()).hexdigest()[:16]
+
+
 MAX_SM_MHZ = 2032
 
 
@@ -83,8 +75,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
-    ap.add_argument("--workload", default="window", choices=["window", "odometry"],
-                    help="window: the headline window step; odometry: Gauss-Newton pose iterations")
+    ap.add_argument("--workload", default="window", choices=["window", "plain", "uneven", "mixed", "odometry"],
+                    help="window: the headline window step; plain, uneven, mixed: the other window "
+                         "configurations; odometry: Gauss-Newton pose iterations")
     ap.add_argument("--cpu-pixels", type=int, default=128, help="oracle pixels sampled per view")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
@@ -101,11 +94,38 @@ def dist_env():
     return world, rank, local
 
 
-def workload(seed=0):
+def workload(seed=0, name="window"):
+    """(params, views, storage dtypes, metric, description) of a window
+    workload.  "window" is the headline; "plain", "uneven" and "mixed" are
+    the single-view, batched-uneven and mixed-precision windows of the
+    parity tests, timed the same way."""
+    import torch
     from paper_2501_08672_b300 import scenes
-    params = scenes.box_room_scene(N_GAUSS, seed=seed, sh_degree=1)
-    views = scenes.arc_views(N_VIEWS, W_IMG, H_IMG, FOCAL, n_gaussians=N_GAUSS)
-    return params, views
+    if name == "window":
+        params = scenes.box_room_scene(N_GAUSS, seed=seed, sh_degree=1)
+        views = scenes.arc_views(N_VIEWS, W_IMG, H_IMG, FOCAL, n_gaussians=N_GAUSS)
+        return params, views, None, METRIC, WORKLOAD
+    if name == "plain":
+        n = 10_000
+        params = scenes.frustum_scene(n, seed=seed)
+        views = [scenes.identity_view(320, 256, 300.0, 0, n)]
+        return (params, views, None, "fwd+bwd window-opt iters/s at 10k Gaussians x 1 view 320x256",
+                "plain single view: 10k random Gaussians (SH degree 0) in front of an identity camera, 320x256")
+    if name == "uneven":
+        params, views = scenes.uneven_batch(16, 2_000_000, seed=seed)
+        desc = ("batched uneven: 16 views of a 2M-Gaussian box room (SH degree 1), widths %s, "
+                "contiguous Gaussian ranges of %d to %d" % (sorted({int(v["W"]) for v in views}),
+                                                        min(v["g_end"] - v["g_begin"] for v in views),
+                                                        max(v["g_end"] - v["g_begin"] for v in views)))
+        return params, views, None, "fwd+bwd window-opt iters/s, 16 uneven views of a 2M-Gaussian window", desc
+    if name == "mixed":
+        params, views = scenes.mixed_precision_scene(2_000_000, seed=seed)
+        storage = dict(log_scales=torch.bfloat16, quats=torch.bfloat16, opacity=torch.float16, sh=torch.float16)
+        return (params, views, storage,
+                "fwd+bwd window-opt iters/s at 2M Gaussians x 10 views 1280x1024, FP16/BF16 storage",
+                "mixed precision: 2M-Gaussian box room (SH degree 1), 10 keyframes 1280x1024; colour/SH and "
+                "opacity stored FP16, log-scale and quaternion BF16, means FP32; FP32 arithmetic")
+    raise ValueError(name)
 
 
 def peaks():
@@ -213,7 +233,7 @@ def cpu_oracle_iteration(params, views, pixels_per_view, seed=1):
 def run_reference(args, world, rank):
     if rank != 0:
         return
-    params, views = workload()
+    params, views = workload()[:2]
     ppv = 4
     for _ in range(args.warmup):
         cpu_oracle_iteration(params, views[:1], ppv)
@@ -249,11 +269,13 @@ def run_b300(args, world, rank, local):
         if world > 1:
             dist.barrier()
 
-    params, views = workload(seed=rank)
+    params, views, storage, metric, wdesc = workload(seed=rank, name=args.workload)
+    n_gauss = int(params["means"].shape[0])
+    n_px = sum(int(v["W"]) * int(v["H"]) for v in views)
     # target keyframes: render of a perturbed copy of the window
     q = scenes.perturbed_copy(params, seed=1000 + rank)
     rt = Renderer(views, local, 16)
-    wq = GaussianWindow(q, local)
+    wq = GaussianWindow(q, local, storage)
     rt.forward(wq.struct())
     target = rt.rgb.clone()
     del rt, wq
@@ -263,9 +285,9 @@ def run_b300(args, world, rank, local):
     if args.tile_size:
         shape = (args.tile_size, args.ppt, args.batch)
     else:
-        shape, tune_table = autotune(params, views, target, steps=3, device=local)
+        shape, tune_table = autotune(params, views, target, steps=3, device=local, storage=storage)
     opt = WindowOptimizer(params, views, target, lr=LR, device=local, tile_size=shape[0],
-                          pixels_per_thread=shape[1], batch=shape[2])
+                          pixels_per_thread=shape[1], batch=shape[2], storage=storage)
     ctx = opt.r.ctx
     opt.step(count=True)  # sizes the pair workspace
     cap0 = opt.r.cap
@@ -350,7 +372,7 @@ def run_b300(args, world, rank, local):
         traffic = None
         if dominant in TRAFFIC:
             sha, tshape, tbytes = TRAFFIC[dominant]
-            if raster_source_hash() == sha and tuple(shape) == tshape:
+            if raster_source_hash() == sha and tuple(shape) == tshape and args.workload == "window":
                 traffic = tbytes
         roof = {"bound": "alu", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic, "traffic_unit": "bytes per launch (ncu DRAM read + write)",
@@ -428,18 +450,22 @@ def run_b300(args, world, rank, local):
     d2h = back_params.numel() * 4 + 4
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "window":
         sec, threads, desc = cpu_oracle_iteration(params, views, args.cpu_pixels)
         cpu = {"value": 1.0 / sec, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc}
 
     if rank == 0:
-        mpix = world * K * N_VIEWS * W_IMG * H_IMG / (max_ms / 1e3) / 1e6
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+        mpix = world * K * n_px / (max_ms / 1e3) / 1e6
+        line = {"metric": metric, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
                 "warmup": args.warmup, "ms_per_step": max_ms / K, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "n_gaussians": N_GAUSS, "views": N_VIEWS,
-                           "image": [W_IMG, H_IMG], "tile_size": shape[0], "pixels_per_thread": shape[1],
-                           "batch": shape[2], "sh_degree": 1, "lr": LR,
+                "config": {"workload": wdesc, "n_gaussians": n_gauss, "views": len(views),
+                           "image": ([int(views[0]["W"]), int(views[0]["H"])] if len({(v["W"], v["H"]) for v in views}) == 1
+                                     else [[int(v["W"]), int(v["H"])] for v in views]),
+                           "tile_size": shape[0], "pixels_per_thread": shape[1],
+                           "batch": shape[2], "sh_degree": int(params["sh_degree"]), "lr": LR,
+                           "storage": ({k: str(v).replace("torch.", "") for k, v in storage.items()} if storage
+                                       else "float32"),
                            "autotune_ms": ({"%d/%d/%d" % k: round(v, 4) for k, v in tune_table.items()}
                                            if tune_table else None),
                            "l2": "flushed between steps (256 MB write outside the timed events)",
@@ -594,10 +620,10 @@ def run_odometry(args, world, rank, local):
 def main():
     args = parse()
     world, rank, local = dist_env()
+    if args.workload != "window" and args.impl == "reference":
+        print(json.dumps({"impl": "reference", "unavailable": "the reference arm times the headline window workload"}))
+        return
     if args.workload == "odometry":
-        if args.impl == "reference":
-            print(json.dumps({"impl": "reference", "unavailable": "the reference arm times the window workload"}))
-            return
         run_odometry(args, world, rank, local)
     elif args.impl == "reference":
         run_reference(args, world, rank)
