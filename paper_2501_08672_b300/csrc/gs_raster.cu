@@ -30,20 +30,24 @@ namespace gsb {
 namespace {
 
 // Thread layout: a TS x TS tile is covered by TS*TS/PPT threads.  A warp
-// covers RPW = 32/TS thread rows, i.e. a block of TS columns x RPW*PPT pixel
-// rows; lane l owns column l % TS and, for its k-th pixel, row
-// k*RPW + l/TS of the warp's block.  The k-th pixels of a warp thus form a
-// compact TS x RPW block, so a footprint edge crossing the warp's block
-// leaves few k with only a handful of active lanes.  Records are staged
-// BATCH at a time (each thread loads BATCH / threads of them).
+// covers a block of WW columns x RPW*PPT pixel rows (RPW = 32/WW thread
+// rows); lane l owns column l % WW and, for its k-th pixel, row
+// k*RPW + l/WW of the warp's block.  The k-th pixels of a warp thus form a
+// compact WW x RPW block, so a footprint edge crossing the warp's block
+// leaves few k with only a handful of active lanes.  WW = TS, except for
+// 16 x 16 tiles at 2 pixels per thread, whose four warps take 8 x 8 blocks
+// (squarer blocks are reached by fewer records than 16 x 4 strips).
 template <int TS, int PPT>
 struct PixelMap {
     static_assert(TS <= 32 && 32 % TS == 0 && (TS * TS / PPT) % 32 == 0, "unsupported launch shape");
-    static constexpr int RPW = 32 / TS;
+    static constexpr int WW = (TS == 16 && PPT == 2) ? 8 : TS;
+    static constexpr int RPW = 32 / WW;
+    static constexpr int WCOLS = TS / WW;
     int px, py;  // column, row of pixel 0; pixel k is at row py + k * RPW
     __device__ __forceinline__ PixelMap(int tx, int ty, int t) {
-        px = tx * TS + (t % TS);
-        py = ty * TS + (t >> 5) * RPW * PPT + (t & 31) / TS;
+        const int w = t >> 5, l = t & 31;
+        px = tx * TS + (w % WCOLS) * WW + (l % WW);
+        py = ty * TS + (w / WCOLS) * RPW * PPT + l / WW;
     }
     __device__ __forceinline__ int row(int k) const { return py + k * RPW; }
 };
