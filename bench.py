@@ -87,6 +87,23 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(values, world, device="cuda"):
+    """Element-wise maximum of per-rank timings over all ranks (the job ends
+    when its slowest replica does); the identity for one rank."""
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
+def whole_job_rate(world, steps, max_ms):
+    """Units per second of the whole job: every rank ran `steps` units in at
+    most `max_ms` milliseconds (replicas: weak scaling)."""
+    return world * steps / (max_ms / 1e3)
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -345,11 +362,8 @@ def run_b300(args, world, rank, local):
     rc, need = opt.r.check_status()
     if rc != B.GS_OK:
         raise RuntimeError("pair capacity exceeded in the timed region (%d needed)" % need)
-    t = torch.tensor([total_ms, plain_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    max_ms, max_plain_ms = float(t[0].item()), float(t[1].item())
-    value = world * K / (max_ms / 1e3)
+    max_ms, max_plain_ms = max_over_ranks([total_ms, plain_ms], world)
+    value = whole_job_rate(world, K, max_ms)
 
     # roofline of the dominant kernel
     dom_launches, dom_ms = prof.get(dominant, (0, 0.0))
@@ -474,7 +488,7 @@ def run_b300(args, world, rank, local):
                 "roofline": roof,
                 "kernel_ms_per_step": {k: v[1] / n_warm for k, v in prof_all.items()},
                 "forms": {"graph_replay_it_s": value,
-                          "host_issued_it_s": world * K / (max_plain_ms / 1e3)},
+                          "host_issued_it_s": whole_job_rate(world, K, max_plain_ms)},
                 "cpu_baseline": cpu,
                 "e2e": {"value": 1e3 / e2e_ms, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                         "d2h_bytes_per_step": int(d2h)},
