@@ -354,6 +354,48 @@ class PoseTracker:
         return apply_left(view, xi), (A, b, rr)
 
 
+class IESKFPoseTracker:
+    """The visual update of the paper's IESKF for the IMU pose (Sec. II-D,
+    Appendix A): iterated updates of T_WI from the photometric normal
+    equations computed on the GPU (gs_pose_normal), mapped through the
+    camera-IMU Jacobian, against a prior (mean, covariance) on the host.
+    `view` gives the camera intrinsics and image size; T_CI is the fixed
+    camera-IMU extrinsic; sigma2 the photometric noise variance per channel."""
+
+    def __init__(self, params, view, R_CI, t_CI, device=0, tile_size=16, sigma2=1e-3, **cfg):
+        from . import ieskf
+        self.ieskf = ieskf
+        self.win = GaussianWindow(params, device)
+        self.r = Renderer([view], device, tile_size, **cfg)
+        self.g = self.win.struct()
+        self.view = dict(view)
+        self.R_CI, self.t_CI = np.asarray(R_CI, np.float64), np.asarray(t_CI, np.float64)
+        self.sigma2 = float(sigma2)
+
+    def camera_view(self, R_WI, p_WI):
+        R_CW, t_CW = self.ieskf.camera_pose(R_WI, p_WI, self.R_CI, self.t_CI)
+        v = dict(self.view)
+        v["R"], v["t"] = R_CW.astype(np.float32), t_CW.astype(np.float32)
+        return v
+
+    def update(self, R_prior, p_prior, P_prior, target, iters=5):
+        """Iterated update from the prior; returns (R_WI, p_WI, P_post, residuals r.r)."""
+        R, p = np.asarray(R_prior, np.float64), np.asarray(p_prior, np.float64)
+        P_post = np.asarray(P_prior, np.float64)
+        rrs = []
+        for _ in range(iters):
+            v = self.camera_view(R, p)
+            self.r.set_views([v])
+            self.r.forward(self.g)
+            A, b, rr = B.unpack_normal(self.r.pose_normal(self.g, target))[0]
+            rrs.append(rr)
+            J = self.ieskf.camera_from_imu_jacobian(self.R_CI, self.t_CI, np.asarray(v["R"], np.float64))
+            off = self.ieskf.boxminus(R, p, R_prior, p_prior)
+            dx, P_post = self.ieskf.ieskf_pose_update(A, b, J, self.sigma2, P_prior, offset=off)
+            R, p = self.ieskf.boxplus(R, p, dx)
+        return R, p, P_post, rrs
+
+
 # Compiled launch shapes of the compositing kernels: (tile size, pixels per
 # thread, records per staged batch).  Every one renders the same image.
 RASTER_VARIANTS = [(8, 1, 128), (8, 1, 256), (8, 2, 128), (8, 2, 256),
