@@ -334,7 +334,8 @@ typedef enum gs_kernel_family {
     GS_KF_PROJECT_BWD = 9, /* a6/a7 projection backward and pose reduction */
     GS_KF_ADAM = 10,       /* a8 Adam */
     GS_KF_POSE_NORMAL = 11, /* pose tangents, forward-mode compositing, normal equations */
-    GS_KF_COUNT = 12
+    GS_KF_WINDOW = 12,      /* sliding-window maintenance and SH0 initialisation */
+    GS_KF_COUNT = 13
 } gs_kernel_family;
 
 typedef struct gs_profile_entry {
@@ -384,6 +385,52 @@ GS_API int gs_pose_normal_scratch(gs_ctx* ctx, const gs_view* views, int n_views
 GS_API int gs_pose_normal(gs_ctx* ctx, const gs_gaussians* g, const gs_view* views, int n_views,
                           const gs_workspace* ws, const float* target, float* scratch, double* normal,
                           float* H_pix, gs_stream stream);
+
+/* ---- sliding-window maintenance on the device (Sec. II-C) ----
+ *
+ * The window's per-Gaussian data are columns: column c holds
+ * bytes_per_gaussian bytes for every Gaussian (a multiple of 4), Gaussian i
+ * at ptr + i * bytes_per_gaussian (device).  The FP32 parameter groups, the
+ * Adam moments and the FP16/BF16 render copies are all columns. */
+typedef struct gs_window_column {
+    void* ptr;
+    int32_t bytes_per_gaussian;
+} gs_window_column;
+
+/* Device scratch bytes gs_window_compact needs for a window of n rows. */
+GS_API size_t gs_window_scratch_bytes(int64_t n);
+
+/* Step 2 of the window maintenance (deletion and compaction, Sec. II-C):
+ * removes the rows whose keep[i] is 0 by swapping survivors from the rear
+ * into the holes.  With n_keep survivors, the k-th hole (a removed row below
+ * n_keep, ascending) receives the k-th surviving row at or above n_keep
+ * counted from the rear (descending); survivors below n_keep do not move, so
+ * afterwards the window is rows [0, n_keep).  keep: device uint8[n].
+ * n_keep_dev: device int64, receives n_keep.  moved_from: NULL or device
+ * int32[n]; for every row r < n_keep it receives the row whose data r now
+ * holds (r itself if unmoved); rows >= n_keep are left as they were.
+ * scratch: device, gs_window_scratch_bytes(n) bytes, caller-owned.  At most 32
+ * columns.  Errors: GS_ERR_INVALID_ARG, GS_ERR_CUDA. */
+GS_API int gs_window_compact(gs_ctx* ctx, const gs_window_column* cols, int n_cols, int64_t n, const uint8_t* keep,
+                             int64_t* n_keep_dev, int32_t* moved_from, void* scratch, gs_stream stream);
+
+/* Step 1 copy-back: gathers rows idx[0..m) (device int32, each in [0, n))
+ * of every src column into rows 0..m of the matching dst column (same
+ * bytes_per_gaussian), for the copy of leaving Gaussians to the global map.
+ * At most 32 columns.  Errors: GS_ERR_INVALID_ARG, GS_ERR_CUDA. */
+GS_API int gs_window_gather(gs_ctx* ctx, const gs_window_column* src, const gs_window_column* dst, int n_cols,
+                            int64_t n, const int32_t* idx, int64_t m, gs_stream stream);
+
+/* SH initialisation of new Gaussians (Sec. II-B.2): for Gaussians
+ * [begin, end) of g, the colour c is the bilinear interpolation of `image`
+ * (device FP32 [3, H, W] of `view`) at the projected mean, pixel (u, v)
+ * sampled at (u + 0.5, v + 0.5), and the FP32 SH coefficients sh_out
+ * ([n][(D+1)^2][3], D = g->sh_degree) get k0 = (c - 0.5) / C0 and 0 for the
+ * higher orders.  A Gaussian behind z_near or projecting outside the image
+ * gets c = 0.5 (k0 = 0).  g->means must be FP32.
+ * Errors: GS_ERR_INVALID_ARG, GS_ERR_NONFINITE, GS_ERR_CUDA. */
+GS_API int gs_sh_init_bilinear(gs_ctx* ctx, const gs_gaussians* g, const gs_view* view, const float* image,
+                               int64_t begin, int64_t end, float* sh_out, gs_stream stream);
 
 /* Measures, on the context's device, the throughput of the FP32 FMA pipe
  * (FLOP/s, an FMA counting 2) and of the ex2 special-function unit (ex2/s)

@@ -18,6 +18,10 @@ Functions, with the passage each restates:
                  d(left pose perturbation), forward mode
   pose_normal    the Gauss-Newton normal equations of the photometric
                  residual in the pose: sum H^T H, sum H^T (target - I)
+  window_compact Sec. II-C Step 2: deletion and compaction of the window by
+                 swapping survivors from the rear into the holes
+  sh0_bilinear   Sec. II-B.2: SH0 initialisation from the bilinear colour of
+                 the image at the projected mean
 """
 from __future__ import annotations
 
@@ -266,4 +270,61 @@ def pose_normal(params, view, target, cfg=None, n_threads=0):
     A = np.einsum("pci,pcj->ij", Hj, Hj)
     b = np.einsum("pci,pc->i", Hj, r)
     return A, b, float((r * r).sum()), bd.reshape(Hh, W)
+
+
+def window_compact(keep):
+    """Sec. II-C Step 2 (deletion and compaction).  Rows whose keep flag is
+    false are removed by swapping rows from the rear of the window into them:
+    walking the holes front to back, each takes the last surviving row that
+    has not moved yet, as long as that row lies behind the hole.  Returns
+    moved_from: for every row r < n_keep, the row whose data r holds."""
+    keep = np.asarray(keep).astype(bool)
+    n = keep.size
+    rows = list(range(n))
+    alive = keep.copy()
+    tail = n - 1
+    for h in range(n):
+        if alive[h]:
+            continue
+        while tail > h and not alive[tail]:
+            tail -= 1
+        if tail <= h:
+            break
+        rows[h], alive[h] = rows[tail], True
+        alive[tail] = False
+        tail -= 1
+    n_keep = int(keep.sum())
+    return np.array(rows[:n_keep], dtype=np.int64)
+
+
+def sh0_bilinear(means, view, image, sh_degree, z_near=0.2):
+    """Sec. II-B.2: SH coefficients of new Gaussians whose degree-0 colour is
+    the bilinear interpolation of image [3, H, W] at the projected mean (pixel
+    (u, v) at (u + 0.5, v + 0.5), weights the areas of the opposite
+    sub-rectangles, clamped at the border); c = 0.5 where the mean is behind
+    z_near or projects outside the image.  Returns [n, (D+1)^2, 3]."""
+    means = np.asarray(means, np.float64)
+    R = np.asarray(view["R"], np.float64)
+    t = np.asarray(view["t"], np.float64)
+    W, H = int(view["W"]), int(view["H"])
+    img = np.asarray(image, np.float64)
+    K = (sh_degree + 1) ** 2
+    out = np.zeros((means.shape[0], K, 3))
+    c0 = 0.5 / np.sqrt(np.pi)
+    for i, mu in enumerate(means):
+        pc = R @ mu + t
+        c = np.full(3, 0.5)
+        if pc[2] > z_near:
+            u = view["fx"] * pc[0] / pc[2] + view["cx"] - 0.5
+            v = view["fy"] * pc[1] / pc[2] + view["cy"] - 0.5
+            if -0.5 < u < W - 0.5 and -0.5 < v < H - 0.5:
+                u = min(max(u, 0.0), W - 1.0)
+                v = min(max(v, 0.0), H - 1.0)
+                u0, v0 = int(np.floor(u)), int(np.floor(v))
+                u1, v1 = min(u0 + 1, W - 1), min(v0 + 1, H - 1)
+                a, b = u - u0, v - v0
+                c = ((1 - a) * (1 - b) * img[:, v0, u0] + a * (1 - b) * img[:, v0, u1] +
+                     (1 - a) * b * img[:, v1, u0] + a * b * img[:, v1, u1])
+        out[i, 0, :] = (c - 0.5) / c0
+    return out
 

@@ -33,10 +33,15 @@ EXPORTED = ["gs_config_default", "gs_version", "gs_context_create", "gs_context_
             "gs_get_config", "gs_workspace_query", "gs_workspace_layout", "gs_project", "gs_bin",
             "gs_render_fwd", "gs_l1_loss", "gs_render_bwd", "gs_pose_grad", "gs_adam_step", "gs_sync_status",
             "gs_profile_enable", "gs_profile_collect", "gs_launch_count", "gs_adam_step_dev",
-            "gs_l1_loss_noalloc", "gs_calibrate_alu", "gs_pose_normal_scratch", "gs_pose_normal"]
+            "gs_l1_loss_noalloc", "gs_calibrate_alu", "gs_pose_normal_scratch", "gs_pose_normal",
+            "gs_window_scratch_bytes", "gs_window_compact", "gs_window_gather", "gs_sh_init_bilinear"]
 
 KERNEL_FAMILIES = ["project", "depth_sort", "tile_scan", "emit", "tile_sort", "ranges", "raster_fwd", "l1",
-                   "raster_bwd", "project_bwd", "adam", "pose_normal"]
+                   "raster_bwd", "project_bwd", "adam", "pose_normal", "window"]
+
+
+class WindowColumn(ctypes.Structure):
+    _fields_ = [("ptr", ctypes.c_void_p), ("bytes_per_gaussian", ctypes.c_int32)]
 
 
 class GsError(RuntimeError):
@@ -134,6 +139,12 @@ def lib():
         L.gs_launch_count.restype = ctypes.c_int64
         L.gs_calibrate_alu.argtypes = [P, P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
         L.gs_pose_normal_scratch.argtypes = [P, ctypes.POINTER(View), I, ctypes.POINTER(ctypes.c_size_t)]
+        L.gs_window_scratch_bytes.argtypes = [I64]
+        L.gs_window_scratch_bytes.restype = ctypes.c_size_t
+        L.gs_window_compact.argtypes = [P, ctypes.POINTER(WindowColumn), I, I64, P, P, P, P, P]
+        L.gs_window_gather.argtypes = [P, ctypes.POINTER(WindowColumn), ctypes.POINTER(WindowColumn), I, I64, P,
+                                       I64, P]
+        L.gs_sh_init_bilinear.argtypes = [P, ctypes.POINTER(Gaussians), ctypes.POINTER(View), P, I64, I64, P, P]
         L.gs_pose_normal.argtypes = [P, ctypes.POINTER(Gaussians), ctypes.POINTER(View), I,
                                      ctypes.POINTER(Workspace), P, P, P, P, P]
         _lib = L
@@ -303,6 +314,46 @@ class Context:
         _check_dev(normal, "normal", torch.float64, 28 * len(views))
         self._ck(lib().gs_pose_normal(self.h, ctypes.byref(g), views, len(views), ctypes.byref(ws), _ptr(target),
                                       _ptr(scratch), _ptr(normal), _ptr(H_pix), _stream(stream)))
+
+    @staticmethod
+    def _columns(tensors):
+        """WindowColumn array for [n, ...] tensors (row i = Gaussian i)."""
+        cols = (WindowColumn * len(tensors))()
+        for k, t in enumerate(tensors):
+            _check_dev(t, "window column")
+            rows = t.shape[0]
+            cols[k].ptr = t.data_ptr()
+            cols[k].bytes_per_gaussian = t.numel() * t.element_size() // max(rows, 1)
+        return cols
+
+    def window_compact(self, tensors, keep, n_keep, moved_from=None, scratch=None, stream=None):
+        """Deletion and compaction of the window rows (keep: uint8 [n]); n_keep:
+        int64 tensor [1] receiving the survivors; moved_from: None or int32 [n]."""
+        n = int(keep.numel())
+        if scratch is None:
+            scratch = torch.empty(int(lib().gs_window_scratch_bytes(n)), dtype=torch.uint8, device=keep.device)
+        _check_dev(keep, "keep", torch.uint8, n)
+        _check_dev(n_keep, "n_keep", torch.int64, 1)
+        if moved_from is not None:
+            _check_dev(moved_from, "moved_from", torch.int32, n)
+        cols = self._columns(tensors)
+        self._ck(lib().gs_window_compact(self.h, cols, len(tensors), n, _ptr(keep), _ptr(n_keep), _ptr(moved_from),
+                                         _ptr(scratch), _stream(stream)))
+
+    def window_gather(self, src, dst, idx, stream=None):
+        """Rows idx (int32 device) of every src tensor into rows 0.. of dst."""
+        _check_dev(idx, "idx", torch.int32)
+        n = int(src[0].shape[0])
+        self._ck(lib().gs_window_gather(self.h, self._columns(src), self._columns(dst), len(src), n, _ptr(idx),
+                                        int(idx.numel()), _stream(stream)))
+
+    def sh_init_bilinear(self, g, view, image, begin, end, sh_out, stream=None):
+        """k0 of Gaussians [begin, end) from the bilinear colour of image [3, H, W] (FP32 device)."""
+        _check_dev(image, "image", torch.float32)
+        _check_dev(sh_out, "sh_out", torch.float32)
+        v = make_views([view])
+        self._ck(lib().gs_sh_init_bilinear(self.h, ctypes.byref(g), v, _ptr(image), int(begin), int(end),
+                                           _ptr(sh_out), _stream(stream)))
 
     def adam_step(self, param, grad, m, v, lr, b1, b2, eps, step, segments=(), stream=None):
         segs = None

@@ -619,6 +619,89 @@ int gs_pose_grad(gs_ctx* ctx, const gs_gaussians* g, const gs_view* views, int n
     return gs_render_bwd(ctx, g, views, n_views, ws, T_final, n_contrib, dL_drgb, nullptr, dL_dpose_dev, stream);
 }
 
+namespace {
+int check_columns(gs_ctx* ctx, const gs_window_column* cols, int n_cols, const char* what) {
+    if (!cols) return fail(ctx, GS_ERR_INVALID_ARG, "%s columns are NULL", what);
+    if (n_cols < 1 || n_cols > window_max_columns())
+        return fail(ctx, GS_ERR_INVALID_ARG, "n_cols=%d outside [1, %d]", n_cols, window_max_columns());
+    for (int c = 0; c < n_cols; ++c) {
+        if (!cols[c].ptr) return fail(ctx, GS_ERR_INVALID_ARG, "%s column %d is NULL", what, c);
+        if (cols[c].bytes_per_gaussian <= 0 || cols[c].bytes_per_gaussian % 4)
+            return fail(ctx, GS_ERR_INVALID_ARG, "%s column %d: bytes_per_gaussian=%d is not a positive multiple of 4",
+                        what, c, cols[c].bytes_per_gaussian);
+        if (reinterpret_cast<uintptr_t>(cols[c].ptr) % 4)
+            return fail(ctx, GS_ERR_INVALID_ARG, "%s column %d is not 4-byte aligned", what, c);
+    }
+    return GS_OK;
+}
+}  // namespace
+
+size_t gs_window_scratch_bytes(int64_t n) { return window_scratch_bytes(n < 0 ? 0 : (long long)n); }
+
+int gs_window_compact(gs_ctx* ctx, const gs_window_column* cols, int n_cols, int64_t n, const uint8_t* keep,
+                      int64_t* n_keep_dev, int32_t* moved_from, void* scratch, gs_stream stream) {
+    if (!ctx) return GS_ERR_INVALID_ARG;
+    int rc = check_columns(ctx, cols, n_cols, "window");
+    if (rc) return rc;
+    if (n < 0 || n > 0x7FFFFFFFll) return fail(ctx, GS_ERR_INVALID_ARG, "n=%lld outside [0, 2^31)", (long long)n);
+    if (!keep || !n_keep_dev || !scratch) return fail(ctx, GS_ERR_INVALID_ARG, "keep, n_keep or scratch is NULL");
+    if (reinterpret_cast<uintptr_t>(scratch) % 256)
+        return fail(ctx, GS_ERR_INVALID_ARG, "scratch is not 256-byte aligned");
+    DeviceGuard dg(ctx->device);
+    const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (n == 0) {
+        const cudaError_t e = cudaMemsetAsync(n_keep_dev, 0, sizeof(int64_t), s);
+        return e == cudaSuccess ? GS_OK : cuda_fail(ctx, e, "gs_window_compact");
+    }
+    const cudaError_t e = launch_window_compact(cols, n_cols, (long long)n, keep, reinterpret_cast<long long*>(n_keep_dev),
+                                                moved_from, scratch, s, ctx->prof);
+    return e == cudaSuccess ? GS_OK : cuda_fail(ctx, e, "gs_window_compact");
+}
+
+int gs_window_gather(gs_ctx* ctx, const gs_window_column* src, const gs_window_column* dst, int n_cols, int64_t n,
+                     const int32_t* idx, int64_t m, gs_stream stream) {
+    if (!ctx) return GS_ERR_INVALID_ARG;
+    int rc = check_columns(ctx, src, n_cols, "source");
+    if (rc) return rc;
+    if ((rc = check_columns(ctx, dst, n_cols, "destination"))) return rc;
+    for (int c = 0; c < n_cols; ++c)
+        if (src[c].bytes_per_gaussian != dst[c].bytes_per_gaussian)
+            return fail(ctx, GS_ERR_INVALID_ARG, "column %d: source and destination widths differ", c);
+    if (n < 0 || m < 0 || (m > 0 && !idx)) return fail(ctx, GS_ERR_INVALID_ARG, "bad n, m or idx");
+    DeviceGuard dg(ctx->device);
+    const cudaError_t e = launch_window_gather(src, dst, n_cols, idx, (long long)m, (long long)n,
+                                               reinterpret_cast<cudaStream_t>(stream), ctx->prof);
+    return e == cudaSuccess ? GS_OK : cuda_fail(ctx, e, "gs_window_gather");
+}
+
+int gs_sh_init_bilinear(gs_ctx* ctx, const gs_gaussians* g, const gs_view* view, const float* image, int64_t begin,
+                        int64_t end, float* sh_out, gs_stream stream) {
+    if (!ctx) return GS_ERR_INVALID_ARG;
+    if (!g || !g->means || !view || !image || !sh_out)
+        return fail(ctx, GS_ERR_INVALID_ARG, "gaussians, means, view, image or sh_out is NULL");
+    if (g->sh_degree < 0 || g->sh_degree > 1) return fail(ctx, GS_ERR_INVALID_ARG, "sh_degree=%d", g->sh_degree);
+    if (begin < 0 || end < begin || end > g->n)
+        return fail(ctx, GS_ERR_INVALID_ARG, "range [%lld, %lld) outside [0, %lld]", (long long)begin,
+                    (long long)end, (long long)g->n);
+    if (view->width <= 0 || view->height <= 0)
+        return fail(ctx, GS_ERR_INVALID_ARG, "view size %dx%d", view->width, view->height);
+    for (int k = 0; k < 9; ++k)
+        if (!isfinite(view->R_cw[k])) return fail(ctx, GS_ERR_NONFINITE, "R_cw not finite");
+    for (int k = 0; k < 3; ++k)
+        if (!isfinite(view->t_cw[k])) return fail(ctx, GS_ERR_NONFINITE, "t_cw not finite");
+    if (!(view->fx > 0.f) || !(view->fy > 0.f) || !isfinite(view->cx) || !isfinite(view->cy))
+        return fail(ctx, GS_ERR_INVALID_ARG, "bad intrinsics");
+    DeviceGuard dg(ctx->device);
+    gs_view v1 = *view;
+    v1.g_begin = 0;
+    v1.g_end = g->n > 0 ? g->n : 1;
+    BatchParam bp;
+    make_batch(ctx->cfg, &v1, 1, bp);
+    const cudaError_t e = launch_sh_init(bp.v[0], g->means, image, (long long)begin, (long long)end, g->sh_degree,
+                                         ctx->cfg.z_near, sh_out, reinterpret_cast<cudaStream_t>(stream), ctx->prof);
+    return e == cudaSuccess ? GS_OK : cuda_fail(ctx, e, "gs_sh_init_bilinear");
+}
+
 int gs_pose_normal_scratch(gs_ctx* ctx, const gs_view* views, int n_views, size_t* floats) {
     if (!ctx) return GS_ERR_INVALID_ARG;
     if (!floats) return fail(ctx, GS_ERR_INVALID_ARG, "floats is NULL");

@@ -118,18 +118,24 @@ class Renderer:
 class GaussianWindow:
     """The window's parameters as one flat FP32 master vector (Adam runs over
     it in one launch) with per-group views, gradients, Adam moments and
-    optional FP16/BF16 render copies of the non-mean groups."""
+    optional FP16/BF16 render copies of the non-mean groups.
+
+    Rows [0, n) are the active window; `capacity` rows are allocated so that
+    new Gaussians can be appended in place (Sec. II-C, Step 4).  `maintain`
+    removes leaving Gaussians by the swap-with-tail compaction of Step 2 on
+    the device and returns their parameters for the global map (Step 1)."""
 
     GROUPS = ("means", "log_scales", "quats", "opacity", "sh")
 
-    def __init__(self, params, device=0, storage=None):
+    def __init__(self, params, device=0, storage=None, capacity=None):
         self.device = torch.device("cuda", device)
         self.sh_degree = int(params["sh_degree"])
         self.K = (self.sh_degree + 1) ** 2
         self.n = int(params["means"].shape[0])
-        n, K = self.n, self.K
-        self.sizes = dict(means=3 * n, log_scales=3 * n, quats=4 * n, opacity=n, sh=3 * K * n)
-        self.shapes = dict(means=(n, 3), log_scales=(n, 3), quats=(n, 4), opacity=(n,), sh=(n, K, 3))
+        self.capacity = max(int(capacity or 0), self.n)
+        cap, K = self.capacity, self.K
+        self.widths = dict(means=(3,), log_scales=(3,), quats=(4,), opacity=(), sh=(K, 3))
+        self.sizes = {k: cap * int(np.prod(w)) for k, w in self.widths.items()}
         self.offsets = {}
         off = 0
         for k in self.GROUPS:
@@ -144,24 +150,33 @@ class GaussianWindow:
         self.v = torch.zeros(self.total, device=dev, dtype=torch.float32)
         self.step_count = 0
         for k in self.GROUPS:
-            self.group(k).copy_(torch.as_tensor(np.ascontiguousarray(params[k], np.float32)).view(self.shapes[k]))
+            self.group(k).copy_(torch.as_tensor(np.ascontiguousarray(params[k], np.float32)).view(self.shape(k)))
         self.storage = dict(storage or {})
         self.lowp = {}
         for k, dt in self.storage.items():
             if k == "means":
                 raise ValueError("means are always FP32")
-            self.lowp[k] = self.group(k).to(dt).contiguous()
+            self.lowp[k] = self.column(k).to(dt).contiguous()
+        self._ctx = None
 
-    def group(self, k, flat=None):
+    def shape(self, k, rows=None):
+        return (self.n if rows is None else rows,) + self.widths[k]
+
+    def column(self, k, flat=None):
+        """All `capacity` rows of group k in `flat` (default: the parameters)."""
         f = self.flat if flat is None else flat
         o = self.offsets[k]
-        return f[o:o + self.sizes[k]].view(self.shapes[k])
+        return f[o:o + self.sizes[k]].view(self.shape(k, self.capacity))
+
+    def group(self, k, flat=None):
+        """The active rows [0, n) of group k."""
+        return self.column(k, flat)[:self.n]
 
     def grad(self, k):
         return self.group(k, self.gflat)
 
     def render_tensors(self):
-        return [self.lowp.get(k, self.group(k)) for k in self.GROUPS]
+        return [self.lowp[k][:self.n] if k in self.lowp else self.group(k) for k in self.GROUPS]
 
     def struct(self):
         """The C-ABI view of the render tensors.  It keeps this window alive as
@@ -180,10 +195,77 @@ class GaussianWindow:
     def numpy(self, use_render_copy=False):
         out = {}
         for k in self.GROUPS:
-            t = self.lowp[k] if (use_render_copy and k in self.lowp) else self.group(k)
+            t = self.lowp[k][:self.n] if (use_render_copy and k in self.lowp) else self.group(k)
             out[k] = t.float().cpu().numpy()
         out["sh_degree"] = self.sh_degree
         return out
+
+    # ---- sliding-window maintenance (Sec. II-C) ----
+
+    def ctx(self):
+        if self._ctx is None:
+            self._ctx = B.Context(self.device.index or 0)
+        return self._ctx
+
+    def _columns(self, rows):
+        cols = []
+        for k in self.GROUPS:
+            for f in (self.flat, self.gflat, self.m, self.v):
+                cols.append(self.column(k, f)[:rows].reshape(rows, -1))
+            if k in self.lowp:
+                cols.append(self.lowp[k][:rows].reshape(rows, -1))
+        return cols
+
+    def maintain(self, keep):
+        """Steps 1 and 2: `keep` (bool or uint8 [n], device or host) marks the
+        Gaussians that stay.  The leaving ones are gathered and returned as a
+        host parameter dict (for the global map); the window is compacted on
+        the device by swapping rear survivors into the holes.  Returns
+        (leaving params, moved_from [n_keep] int64 host: the old row of every
+        new row)."""
+        n = self.n
+        keep = torch.as_tensor(keep, device=self.device).to(torch.uint8).contiguous()
+        if keep.numel() != n:
+            raise ValueError("keep has %d entries for %d Gaussians" % (keep.numel(), n))
+        ctx = self.ctx()
+        idx = torch.nonzero(keep == 0).view(-1).to(torch.int32)
+        m = int(idx.numel())
+        src = [self.group(k).reshape(n, -1) for k in self.GROUPS]
+        dst = [torch.empty((max(m, 1),) + tuple(s.shape[1:]), dtype=torch.float32, device=self.device) for s in src]
+        if m:
+            ctx.window_gather(src, dst, idx)
+        leaving = {k: d[:m].reshape((m,) + self.widths[k]).cpu().numpy() for k, d in zip(self.GROUPS, dst)}
+        leaving["sh_degree"] = self.sh_degree
+        n_keep = torch.zeros(1, dtype=torch.int64, device=self.device)
+        moved = torch.empty(max(n, 1), dtype=torch.int32, device=self.device)
+        ctx.window_compact(self._columns(n), keep, n_keep, moved[:n] if n else None)
+        self.n = int(n_keep.item())
+        return leaving, moved[:self.n].to(torch.int64).cpu().numpy()
+
+    def append(self, params, image=None, view=None, stream=None):
+        """Step 4: appends the Gaussians of `params` (host arrays) at rows
+        [n, n + m) (parameters copied host to device, Adam moments and
+        gradients zeroed); with `image` ([3, H, W] device FP32) and `view`
+        their SH start from the bilinear image colour (Sec. II-B.2).  The
+        copies are issued on `stream` (default: the current stream)."""
+        m = int(params["means"].shape[0])
+        if self.n + m > self.capacity:
+            raise ValueError("window capacity %d exceeded (%d + %d)" % (self.capacity, self.n, m))
+        a, b = self.n, self.n + m
+        s = stream or torch.cuda.current_stream(self.device)
+        with torch.cuda.stream(s):
+            for k in self.GROUPS:
+                host = torch.as_tensor(np.ascontiguousarray(params[k], np.float32)).view(self.shape(k, m))
+                self.column(k)[a:b].copy_(host.pin_memory(), non_blocking=True)
+                for f in (self.gflat, self.m, self.v):
+                    self.column(k, f)[a:b].zero_()
+            self.n = b
+            if image is not None:
+                g = self.struct()
+                self.ctx().sh_init_bilinear(g, view, image, a, b, self.column("sh"), stream=s)
+            for k in self.lowp:
+                self.lowp[k][a:b].copy_(self.column(k)[a:b])
+        return a, b
 
 
 class WindowOptimizer:

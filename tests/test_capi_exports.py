@@ -75,7 +75,8 @@ def header_struct_fields(name):
                                           ("gs_gaussians", "Gaussians"), ("gs_grads", "Grads"),
                                           ("gs_workspace", "Workspace"), ("gs_ws_layout", "WsLayout"),
                                           ("gs_profile_entry", "ProfileEntry"),
-                                          ("gs_lowp_segment", "LowpSegment")])
+                                          ("gs_lowp_segment", "LowpSegment"),
+                                          ("gs_window_column", "WindowColumn")])
 def test_binding_structs_match_header(cname, pyname):
     """Every ctypes mirror lists the header struct's fields in the same order."""
     from paper_2501_08672_b300 import binding

@@ -515,3 +515,64 @@ def test_pose_normal_equations_brute_force(orc):
     step = np.linalg.solve(A, b)
     # the linearisation recovers the perturbation to first order
     np.testing.assert_allclose(step, xi_true, rtol=0.05, atol=2e-4)
+
+
+# ---- sliding-window maintenance (Sec. II-C) and SH0 initialisation (Sec. II-B.2) ----
+
+def test_window_compact_worked_example(orc):
+    """Rows 0..7, rows 1, 4 and 6 leave: n_keep = 5; the holes 1 and 4 take the
+    rear survivors 7 and 5; survivors 0, 2, 3 stay."""
+    keep = np.array([1, 0, 1, 1, 0, 1, 0, 1], bool)
+    np.testing.assert_array_equal(orc.window_compact(keep), [0, 7, 2, 3, 5])
+
+
+def test_window_compact_invariants(orc):
+    """Random masks: the window keeps exactly the survivors, survivors below
+    n_keep never move, every mover comes from at or behind n_keep, and the
+    k-th hole takes the k-th survivor from the rear (the closed form)."""
+    rng = np.random.default_rng(9)
+    for n in (1, 2, 7, 64, 1000):
+        for p in (0.0, 0.1, 0.5, 0.9, 1.0):
+            keep = rng.uniform(size=n) >= p
+            mf = orc.window_compact(keep)
+            nk = int(keep.sum())
+            assert mf.size == nk
+            assert sorted(mf.tolist()) == np.nonzero(keep)[0].tolist()
+            for r in range(nk):
+                if keep[r]:
+                    assert mf[r] == r
+                else:
+                    assert mf[r] >= nk
+            holes = [r for r in range(nk) if not keep[r]]
+            movers = [r for r in range(nk, n) if keep[r]][::-1]
+            assert [int(mf[h]) for h in holes] == movers
+
+
+def test_sh0_bilinear_pins(orc):
+    """At a pixel centre the colour is that pixel's; a linear image is
+    reproduced exactly (bilinear interpolation is exact on it); inside the
+    image it matches scipy's order-1 map_coordinates; outside, grey."""
+    from scipy import ndimage
+    rng = np.random.default_rng(10)
+    W, H = 9, 7
+    view = dict(R=np.eye(3), t=np.zeros(3), fx=10.0, fy=10.0, cx=4.5, cy=3.5, W=W, H=H)
+    img = rng.uniform(0.1, 0.9, (3, H, W))
+    z = 2.0
+    c0 = 0.5 / np.sqrt(np.pi)
+    # pixel centre (u, v) = (3, 2): q = (3.5, 2.5)
+    mu = np.array([[(3.5 - 4.5) * z / 10.0, (2.5 - 3.5) * z / 10.0, z]])
+    sh = orc.sh0_bilinear(mu, view, img, 1)
+    np.testing.assert_allclose(sh[0, 0] * c0 + 0.5, img[:, 2, 3], atol=1e-12)
+    assert np.all(sh[0, 1:] == 0)
+    uu, vv = np.meshgrid(np.arange(W), np.arange(H))
+    lin = np.stack([0.2 + 0.03 * uu - 0.02 * vv, 0.5 + 0.01 * vv, 0.3 - 0.01 * uu])
+    pts = rng.uniform([0.3, 0.3], [W - 1.3, H - 1.3], (50, 2))   # continuous pixel coordinates
+    mus = np.stack([(pts[:, 0] + 0.5 - 4.5) * z / 10.0, (pts[:, 1] + 0.5 - 3.5) * z / 10.0, np.full(50, z)], 1)
+    got = orc.sh0_bilinear(mus, view, lin, 0)[:, 0] * c0 + 0.5
+    exact = np.stack([0.2 + 0.03 * pts[:, 0] - 0.02 * pts[:, 1], 0.5 + 0.01 * pts[:, 1], 0.3 - 0.01 * pts[:, 0]], 1)
+    np.testing.assert_allclose(got, exact, atol=1e-12)
+    got = orc.sh0_bilinear(mus, view, img, 0)[:, 0] * c0 + 0.5
+    ref = np.stack([ndimage.map_coordinates(img[ch], [pts[:, 1], pts[:, 0]], order=1) for ch in range(3)], 1)
+    np.testing.assert_allclose(got, ref, atol=1e-12)
+    far = np.array([[10.0, 0.0, z], [0.0, 0.0, -1.0]])
+    np.testing.assert_array_equal(orc.sh0_bilinear(far, view, img, 0)[:, 0], 0.0)
