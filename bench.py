@@ -75,7 +75,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
-    ap.add_argument("--workload", default="window", choices=["window", "plain", "uneven", "mixed", "odometry"],
+    ap.add_argument("--workload", default="window",
+                    choices=["window", "plain", "uneven", "mixed", "odometry", "maintenance"],
                     help="window: the headline window step; plain, uneven, mixed: the other window "
                          "configurations; odometry: Gauss-Newton pose iterations")
     ap.add_argument("--cpu-pixels", type=int, default=128, help="oracle pixels sampled per view")
@@ -631,6 +632,134 @@ def run_odometry(args, world, rank, local):
     print(json.dumps(line), flush=True)
 
 
+MAINT_SIZES = (100_000, 500_000, 1_000_000, 2_000_000, 5_000_000)
+
+
+def run_maintenance(args, world, rank, local):
+    """Sliding-window maintenance on the device (Sec. II-C) against the window
+    size N: per step 10 % of the window leaves (gathered for the global map,
+    Step 1, and compacted, Step 2) and as many new Gaussians enter (host to
+    device from pinned memory, gradients and moments cleared, SH0 from a
+    640x512 image, Step 4).  Each part is captured in a CUDA graph and timed
+    by replay (device time, no host launch overhead): `value` is the whole
+    step, the roofline covers the kernels alone (HBM bound; the host-to-device
+    copy is bound by the host link and reported beside it).  Algorithmic bytes
+    of the kernels: every compaction mover copies its parameters and both Adam
+    moments (3 x 92 B read + written; gradients are dead between iterations,
+    every backward overwrites them), every leaving row is gathered (92 B read
+    + written), every new row gets 2 x 92 B cleared, its mean read and its SH
+    written by the initialisation (12 + 48 B), and the keep flags are read
+    (1 B per row).  `e2e`: the same step through
+    GaussianWindow.maintain / append, which also copy the leaving Gaussians
+    and the row map to the host."""
+    import torch
+    from paper_2501_08672_b300 import binding as B
+    from paper_2501_08672_b300 import scenes
+    from paper_2501_08672_b300.render import GaussianWindow
+
+    torch.cuda.set_device(local)
+    hbm, hbm_kind = peaks()
+    rows = []
+    v = scenes.lookat_view((4.0, -1.0, 2.2), (0.0, 0.0, 0.6), 640, 512, 600.0, 0, 1)
+    image = torch.rand(3, 512, 640, device="cuda")
+    K = max(args.steps // 5, 5)
+
+    def replay_ms(fn):
+        fn()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, capture_error_mode="relaxed"):
+            fn()
+        for _ in range(3):
+            g.replay()
+        ts = []
+        for _ in range(K):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record()
+            g.replay()
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return float(np.median(ts))
+
+    for N in MAINT_SIZES:
+        params = scenes.box_room_scene(N, seed=rank, sh_degree=1)
+        turn = N // 10
+        extra = scenes.box_room_scene(turn, seed=rank + 1, sh_degree=1)
+        pinned = {k: torch.as_tensor(np.ascontiguousarray(extra[k], np.float32)).pin_memory()
+                  for k in GaussianWindow.GROUPS}
+        win = GaussianWindow(params, local, capacity=N + turn)
+        ctx = win.ctx()
+        rng = np.random.default_rng(rank)
+        keep = torch.as_tensor((rng.uniform(size=N) >= 0.1).astype(np.uint8)).cuda()
+        leave_idx = torch.nonzero(keep == 0).view(-1).to(torch.int32)
+        n_leave = int(leave_idx.numel())
+        n_keep_t = torch.zeros(1, dtype=torch.int64, device="cuda")
+        moved = torch.empty(N, dtype=torch.int32, device="cuda")
+        scratch = torch.empty(int(B.lib().gs_window_scratch_bytes(N)), dtype=torch.uint8, device="cuda")
+        src = [win.group(k).reshape(N, -1) for k in GaussianWindow.GROUPS]
+        dst = [torch.empty((n_leave,) + tuple(t.shape[1:]), device="cuda") for t in src]
+        cols = win._columns(N)
+        zcols = [win.column(k, f) for k in GaussianWindow.GROUPS for f in (win.m, win.v)]
+        nk = N - n_leave
+
+        def kernels():
+            ctx.window_gather(src, dst, leave_idx)
+            ctx.window_compact(cols, keep, n_keep_t, moved, scratch)
+            ctx.window_clear(zcols, nk, nk + turn)
+            win.n = nk + turn
+            ctx.sh_init_bilinear(win.struct(), dict(v, g_begin=0, g_end=win.n), image, nk, nk + turn,
+                                 win.column("sh"))
+            win.n = N
+
+        def h2d():
+            for k in GaussianWindow.GROUPS:
+                win.column(k)[nk:nk + turn].view(turn, -1).copy_(pinned[k].view(turn, -1), non_blocking=True)
+
+        def step():
+            kernels()
+            h2d()
+
+        ms_k = replay_ms(kernels)
+        ms_h = replay_ms(h2d)
+        ms = replay_ms(step)
+        movers = int((moved[:nk].cpu().numpy() != np.arange(nk)).sum())
+        # end to end through the window API (host syncs and read-backs included)
+        e2e = []
+        for k in range(3):
+            win2 = GaussianWindow(params, local, capacity=N + turn)
+            keep_h = rng.uniform(size=N) >= 0.1
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            win2.maintain(keep_h)
+            win2.append(extra, image=image, view=dict(v, g_begin=0, g_end=win2.n + turn))
+            torch.cuda.synchronize()
+            e2e.append((time.perf_counter() - t0) * 1e3)
+            del win2
+        algo = movers * 3 * 92 * 2 + n_leave * 92 * 2 + turn * (2 * 92 + 12 + 48) + N
+        rows.append({"n": N, "step_ms": ms, "kernels_ms": ms_k, "h2d_ms": ms_h, "e2e_ms": float(np.median(e2e)),
+                     "movers": movers, "leaving": n_leave, "appended": turn, "kernel_bytes": algo,
+                     "kernels_gbs": algo / (ms_k / 1e3) / 1e9, "h2d_gbs": turn * 92 / (ms_h / 1e3) / 1e9})
+        print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+        del win, cols, src, dst, zcols
+    big = rows[-1]
+    line = {"metric": "window maintenance step (10 pct leave: gather + compact; 10 pct enter: copy in, clear, "
+                      "SH0 init), device ms at N=%d" % big["n"],
+            "value": big["step_ms"], "unit": "ms", "n_gpus": world, "steps": K, "warmup": 3,
+            "ms_per_step": big["step_ms"], "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "sliding-window maintenance of a box-room window of N Gaussians (SH degree 1)",
+                       "sizes": list(MAINT_SIZES), "per_size": rows,
+                       "l2": "window larger than L2 from N=1M (368 B per Gaussian with gradient and moments)"},
+            "roofline": {"bound": "hbm", "achieved": big["kernels_gbs"], "peak": hbm, "unit": "GB/s",
+                         "frac": big["kernels_gbs"] / hbm, "traffic": None, "peak_kind": hbm_kind,
+                         "kernel": "maintenance kernels (gather, compaction, clear, SH0 init) as one graph"},
+            "e2e": {"value": big["e2e_ms"], "unit": "ms", "h2d_bytes_per_step": big["appended"] * 92,
+                    "d2h_bytes_per_step": big["leaving"] * 92 + 8}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     world, rank, local = dist_env()
@@ -639,6 +768,8 @@ def main():
         return
     if args.workload == "odometry":
         run_odometry(args, world, rank, local)
+    elif args.workload == "maintenance":
+        run_maintenance(args, world, rank, local)
     elif args.impl == "reference":
         run_reference(args, world, rank)
     else:

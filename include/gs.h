@@ -389,9 +389,11 @@ GS_API int gs_pose_normal(gs_ctx* ctx, const gs_gaussians* g, const gs_view* vie
 /* ---- sliding-window maintenance on the device (Sec. II-C) ----
  *
  * The window's per-Gaussian data are columns: column c holds
- * bytes_per_gaussian bytes for every Gaussian (a multiple of 4), Gaussian i
- * at ptr + i * bytes_per_gaussian (device).  The FP32 parameter groups, the
- * Adam moments and the FP16/BF16 render copies are all columns. */
+ * bytes_per_gaussian bytes for every Gaussian (a multiple of 4, at most
+ * GS_WINDOW_MAX_COLUMN_BYTES), Gaussian i at ptr + i * bytes_per_gaussian
+ * (device, 4-byte aligned).  The FP32 parameter groups, the Adam moments and
+ * the FP16/BF16 render copies are all columns. */
+#define GS_WINDOW_MAX_COLUMN_BYTES 16384
 typedef struct gs_window_column {
     void* ptr;
     int32_t bytes_per_gaussian;
@@ -420,6 +422,13 @@ GS_API int gs_window_compact(gs_ctx* ctx, const gs_window_column* cols, int n_co
  * At most 32 columns.  Errors: GS_ERR_INVALID_ARG, GS_ERR_CUDA. */
 GS_API int gs_window_gather(gs_ctx* ctx, const gs_window_column* src, const gs_window_column* dst, int n_cols,
                             int64_t n, const int32_t* idx, int64_t m, gs_stream stream);
+
+/* Step 4 insertion: sets rows [begin, end) of every column to zero (the
+ * gradients and Adam moments of Gaussians entering the window).  The columns
+ * must hold at least `end` rows.  At most 32 columns.
+ * Errors: GS_ERR_INVALID_ARG, GS_ERR_CUDA. */
+GS_API int gs_window_clear(gs_ctx* ctx, const gs_window_column* cols, int n_cols, int64_t begin, int64_t end,
+                           gs_stream stream);
 
 /* SH initialisation of new Gaussians (Sec. II-B.2): for Gaussians
  * [begin, end) of g, the colour c is the bilinear interpolation of `image`

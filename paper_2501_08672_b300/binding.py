@@ -34,7 +34,8 @@ EXPORTED = ["gs_config_default", "gs_version", "gs_context_create", "gs_context_
             "gs_render_fwd", "gs_l1_loss", "gs_render_bwd", "gs_pose_grad", "gs_adam_step", "gs_sync_status",
             "gs_profile_enable", "gs_profile_collect", "gs_launch_count", "gs_adam_step_dev",
             "gs_l1_loss_noalloc", "gs_calibrate_alu", "gs_pose_normal_scratch", "gs_pose_normal",
-            "gs_window_scratch_bytes", "gs_window_compact", "gs_window_gather", "gs_sh_init_bilinear"]
+            "gs_window_scratch_bytes", "gs_window_compact", "gs_window_gather", "gs_window_clear",
+            "gs_sh_init_bilinear"]
 
 KERNEL_FAMILIES = ["project", "depth_sort", "tile_scan", "emit", "tile_sort", "ranges", "raster_fwd", "l1",
                    "raster_bwd", "project_bwd", "adam", "pose_normal", "window"]
@@ -144,6 +145,7 @@ def lib():
         L.gs_window_compact.argtypes = [P, ctypes.POINTER(WindowColumn), I, I64, P, P, P, P, P]
         L.gs_window_gather.argtypes = [P, ctypes.POINTER(WindowColumn), ctypes.POINTER(WindowColumn), I, I64, P,
                                        I64, P]
+        L.gs_window_clear.argtypes = [P, ctypes.POINTER(WindowColumn), I, I64, I64, P]
         L.gs_sh_init_bilinear.argtypes = [P, ctypes.POINTER(Gaussians), ctypes.POINTER(View), P, I64, I64, P, P]
         L.gs_pose_normal.argtypes = [P, ctypes.POINTER(Gaussians), ctypes.POINTER(View), I,
                                      ctypes.POINTER(Workspace), P, P, P, P, P]
@@ -346,6 +348,11 @@ class Context:
         n = int(src[0].shape[0])
         self._ck(lib().gs_window_gather(self.h, self._columns(src), self._columns(dst), len(src), n, _ptr(idx),
                                         int(idx.numel()), _stream(stream)))
+
+    def window_clear(self, tensors, begin, end, stream=None):
+        """Rows [begin, end) of every tensor set to zero."""
+        self._ck(lib().gs_window_clear(self.h, self._columns(tensors), len(tensors), int(begin), int(end),
+                                       _stream(stream)))
 
     def sh_init_bilinear(self, g, view, image, begin, end, sh_out, stream=None):
         """k0 of Gaussians [begin, end) from the bilinear colour of image [3, H, W] (FP32 device)."""

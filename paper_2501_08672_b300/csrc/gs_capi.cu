@@ -626,9 +626,11 @@ int check_columns(gs_ctx* ctx, const gs_window_column* cols, int n_cols, const c
         return fail(ctx, GS_ERR_INVALID_ARG, "n_cols=%d outside [1, %d]", n_cols, window_max_columns());
     for (int c = 0; c < n_cols; ++c) {
         if (!cols[c].ptr) return fail(ctx, GS_ERR_INVALID_ARG, "%s column %d is NULL", what, c);
-        if (cols[c].bytes_per_gaussian <= 0 || cols[c].bytes_per_gaussian % 4)
-            return fail(ctx, GS_ERR_INVALID_ARG, "%s column %d: bytes_per_gaussian=%d is not a positive multiple of 4",
-                        what, c, cols[c].bytes_per_gaussian);
+        if (cols[c].bytes_per_gaussian <= 0 || cols[c].bytes_per_gaussian % 4 ||
+            cols[c].bytes_per_gaussian > GS_WINDOW_MAX_COLUMN_BYTES)
+            return fail(ctx, GS_ERR_INVALID_ARG,
+                        "%s column %d: bytes_per_gaussian=%d is not a positive multiple of 4 up to %d", what, c,
+                        cols[c].bytes_per_gaussian, GS_WINDOW_MAX_COLUMN_BYTES);
         if (reinterpret_cast<uintptr_t>(cols[c].ptr) % 4)
             return fail(ctx, GS_ERR_INVALID_ARG, "%s column %d is not 4-byte aligned", what, c);
     }
@@ -654,7 +656,7 @@ int gs_window_compact(gs_ctx* ctx, const gs_window_column* cols, int n_cols, int
         return e == cudaSuccess ? GS_OK : cuda_fail(ctx, e, "gs_window_compact");
     }
     const cudaError_t e = launch_window_compact(cols, n_cols, (long long)n, keep, reinterpret_cast<long long*>(n_keep_dev),
-                                                moved_from, scratch, s, ctx->prof);
+                                                moved_from, scratch, ctx->sm_count, s, ctx->prof);
     return e == cudaSuccess ? GS_OK : cuda_fail(ctx, e, "gs_window_compact");
 }
 
@@ -669,9 +671,22 @@ int gs_window_gather(gs_ctx* ctx, const gs_window_column* src, const gs_window_c
             return fail(ctx, GS_ERR_INVALID_ARG, "column %d: source and destination widths differ", c);
     if (n < 0 || m < 0 || (m > 0 && !idx)) return fail(ctx, GS_ERR_INVALID_ARG, "bad n, m or idx");
     DeviceGuard dg(ctx->device);
-    const cudaError_t e = launch_window_gather(src, dst, n_cols, idx, (long long)m, (long long)n,
+    const cudaError_t e = launch_window_gather(src, dst, n_cols, idx, (long long)m, (long long)n, ctx->sm_count,
                                                reinterpret_cast<cudaStream_t>(stream), ctx->prof);
     return e == cudaSuccess ? GS_OK : cuda_fail(ctx, e, "gs_window_gather");
+}
+
+int gs_window_clear(gs_ctx* ctx, const gs_window_column* cols, int n_cols, int64_t begin, int64_t end,
+                    gs_stream stream) {
+    if (!ctx) return GS_ERR_INVALID_ARG;
+    int rc = check_columns(ctx, cols, n_cols, "window");
+    if (rc) return rc;
+    if (begin < 0 || end < begin || end > 0x7FFFFFFFll)
+        return fail(ctx, GS_ERR_INVALID_ARG, "rows [%lld, %lld) outside [0, 2^31)", (long long)begin, (long long)end);
+    DeviceGuard dg(ctx->device);
+    const cudaError_t e = launch_window_clear(cols, n_cols, (long long)begin, (long long)end, ctx->sm_count,
+                                              reinterpret_cast<cudaStream_t>(stream), ctx->prof);
+    return e == cudaSuccess ? GS_OK : cuda_fail(ctx, e, "gs_window_clear");
 }
 
 int gs_sh_init_bilinear(gs_ctx* ctx, const gs_gaussians* g, const gs_view* view, const float* image, int64_t begin,

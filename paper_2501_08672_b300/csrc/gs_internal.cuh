@@ -252,10 +252,13 @@ cudaError_t measure_alu(int sm_count, float* sink, cudaStream_t s, double* ffma_
 int window_max_columns();
 size_t window_scratch_bytes(long long n);
 cudaError_t launch_window_compact(const gs_window_column* cols, int n_cols, long long n, const uint8_t* keep,
-                                  long long* n_keep_dev, int32_t* moved_from, void* scratch, cudaStream_t s,
-                                  Prof& pf);
+                                  long long* n_keep_dev, int32_t* moved_from, void* scratch, int sm_count,
+                                  cudaStream_t s, Prof& pf);
 cudaError_t launch_window_gather(const gs_window_column* src, const gs_window_column* dst, int n_cols,
-                                 const int32_t* idx, long long m, long long n, cudaStream_t s, Prof& pf);
+                                 const int32_t* idx, long long m, long long n, int sm_count, cudaStream_t s,
+                                 Prof& pf);
+cudaError_t launch_window_clear(const gs_window_column* cols, int n_cols, long long begin, long long end,
+                                int sm_count, cudaStream_t s, Prof& pf);
 cudaError_t launch_sh_init(const ViewParam& V, const float* means, const float* image, long long begin,
                            long long end, int sh_degree, float z_near, float* sh, cudaStream_t s, Prof& pf);
 cudaError_t launch_pose_tangents(const BatchParam& bp, const GaussPtrs& g, const RenderConst& rc,

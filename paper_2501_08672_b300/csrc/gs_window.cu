@@ -5,11 +5,13 @@
 // (deleted row below n_keep, ascending) receives the k-th survivor at or
 // above n_keep counted from the rear (descending), so survivors below n_keep
 // never move and the window stays contiguous in [0, n_keep).  Holes and
-// movers are counted together: both exclusive prefix counts are packed in
-// one 64-bit word (holes low, movers high) and scanned in three phases
-// (block totals, one-block scan of the totals, block-local scan), all counts
-// in device memory.  Every mover's source row is at or above n_keep and
-// every destination below it, so the row copies do not overlap.
+// movers both follow from one survivor prefix S(i) (survivors before row i):
+// a hole i < n_keep has rank i - S(i), a mover i >= n_keep rank
+// S(i) - S(n_keep).  S is scanned in three phases (block totals, one-block
+// scan of the totals that also yields n_keep and S(n_keep), block-local
+// scan), all counts in device memory.  Every mover's source row is at or
+// above n_keep and every destination below it, so the row copies do not
+// overlap.
 //
 // SH0 initialisation: the colour of a new Gaussian is the bilinear
 // interpolation of the camera image at its projected mean (pixel (u, v)
@@ -34,61 +36,56 @@ struct ColTable {
 constexpr int kWinItems = 4;
 constexpr int kWinChunk = kWinThreads * kWinItems;
 
-__device__ __forceinline__ unsigned long long block_exclusive_scan_u64(unsigned long long v,
-                                                                       unsigned long long* total) {
-    __shared__ unsigned long long s_w[32];
+// Exclusive scan of one value per thread over the block; *total receives the block sum.
+__device__ __forceinline__ unsigned block_exclusive_scan(unsigned v, unsigned* total) {
+    __shared__ unsigned s_w[32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    unsigned long long x = v;
+    unsigned x = v;
     for (int o = 1; o < 32; o <<= 1) {
-        const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+        const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
         if (lane >= o) x += y;
     }
     if (lane == 31) s_w[w] = x;
     __syncthreads();
     if (w == 0) {
         const int nw = blockDim.x >> 5;
-        unsigned long long y = lane < nw ? s_w[lane] : 0ull;
+        unsigned y = lane < nw ? s_w[lane] : 0u;
         for (int o = 1; o < 32; o <<= 1) {
-            const unsigned long long z = __shfl_up_sync(0xffffffffu, y, o);
+            const unsigned z = __shfl_up_sync(0xffffffffu, y, o);
             if (lane >= o) y += z;
         }
         s_w[lane] = y;
     }
     __syncthreads();
     *total = s_w[(blockDim.x >> 5) - 1];
-    const unsigned long long wprefix = w > 0 ? s_w[w - 1] : 0ull;
+    const unsigned wprefix = w > 0 ? s_w[w - 1] : 0u;
     __syncthreads();
     return wprefix + x - v;
 }
 
-// Per-row flags: survivors (phase "keep"), or hole | mover << 32 once n_keep is known.
-__device__ __forceinline__ unsigned long long row_flags(const uint8_t* keep, long long i, long long n,
-                                                        const long long* n_keep) {
-    if (i >= n) return 0ull;
-    const bool k = keep[i] != 0;
-    if (!n_keep) return k ? 1ull : 0ull;
-    const long long nk = *n_keep;
-    if (!k && i < nk) return 1ull;               // hole
-    if (k && i >= nk) return 1ull << 32;         // mover
-    return 0ull;
+__device__ __forceinline__ unsigned keep_count(const uint8_t* keep, long long base, long long end) {
+    unsigned s = 0;
+#pragma unroll
+    for (int k = 0; k < kWinItems; ++k)
+        if (base + k < end) s += keep[base + k] != 0;
+    return s;
 }
 
+// Survivors per block of kWinChunk rows.
 __global__ void __launch_bounds__(kWinThreads) k_win_reduce(const uint8_t* __restrict__ keep, long long n,
-                                                            const long long* n_keep,
-                                                            unsigned long long* __restrict__ part) {
+                                                            unsigned* __restrict__ part) {
     const long long base = (long long)blockIdx.x * kWinChunk + (long long)threadIdx.x * kWinItems;
-    unsigned long long s = 0;
-#pragma unroll
-    for (int k = 0; k < kWinItems; ++k) s += row_flags(keep, base + k, n, n_keep);
-    unsigned long long total;
-    block_exclusive_scan_u64(s, &total);
+    unsigned total;
+    block_exclusive_scan(keep_count(keep, base, n), &total);
     if (threadIdx.x == 0) part[blockIdx.x] = total;
 }
 
-// Exclusive scan of the block totals by one block; with keep_total set, the
-// grand total (the survivors) is written there.
-__global__ void __launch_bounds__(1024) k_win_top(unsigned long long* part, int nparts, long long* keep_total,
-                                                  unsigned long long* grand) {
+// One block: exclusive scan of the block survivor counts (part becomes the
+// survivor prefix S at each block start), n_keep = the grand total, and
+// S(n_keep), the survivors below n_keep, counted in the block holding row
+// n_keep; movers = holes = n_keep - S(n_keep).
+__global__ void __launch_bounds__(1024) k_win_top(const uint8_t* __restrict__ keep, long long n, unsigned* part,
+                                                  int nparts, long long* n_keep_out, long long* counts) {
     __shared__ unsigned long long s[1024];
     const int t = threadIdx.x;
     const int per = (nparts + 1023) / 1024;
@@ -107,79 +104,154 @@ __global__ void __launch_bounds__(1024) k_win_top(unsigned long long* part, int 
     unsigned long long run = s[t] - sum;
     for (int k = 0; k < per; ++k)
         if (b0 + k < nparts) {
-            const unsigned long long v = part[b0 + k];
-            part[b0 + k] = run;
+            const unsigned v = part[b0 + k];
+            part[b0 + k] = (unsigned)run;
             run += v;
         }
-    if (t == 1023) {
-        if (keep_total) *keep_total = (long long)s[1023];
-        if (grand) *grand = s[1023];
+    const long long nk = (long long)s[1023];
+    __syncthreads();  // part[] rewritten before the read below
+    const long long blk = nk / kWinChunk;
+    unsigned below = 0;
+    if (blk < nparts) below = keep_count(keep, blk * kWinChunk + (long long)t * kWinItems, nk);
+    unsigned tot;
+    block_exclusive_scan(below, &tot);
+    if (t == 0) {
+        const long long snk = (blk < nparts ? (long long)part[blk] : nk) + (blk < nparts ? (long long)tot : 0ll);
+        *n_keep_out = nk;
+        counts[0] = snk;       // survivors below n_keep
+        counts[1] = nk - snk;  // holes = movers
     }
 }
 
-// Ranks: holes_list[hole rank] = row, movers_asc[mover rank] = row, and
-// moved_from[r] = r for the survivors below n_keep.
+// Ranks from the survivor prefix S(i) (survivors before row i): a hole i <
+// n_keep has rank i - S(i) among the holes, a mover i >= n_keep has rank
+// S(i) - S(n_keep) among the movers (ascending); moved_from[r] = r for the
+// survivors below n_keep.
 __global__ void __launch_bounds__(kWinThreads) k_win_rank(const uint8_t* __restrict__ keep, long long n,
                                                           const long long* __restrict__ n_keep,
-                                                          const unsigned long long* __restrict__ part,
+                                                          const unsigned* __restrict__ part,
+                                                          const long long* __restrict__ counts,
                                                           int32_t* __restrict__ holes_list,
                                                           int32_t* __restrict__ movers_asc,
                                                           int32_t* __restrict__ moved_from) {
     const long long base = (long long)blockIdx.x * kWinChunk + (long long)threadIdx.x * kWinItems;
-    unsigned long long f[kWinItems];
-    unsigned long long s = 0;
+    bool f[kWinItems];
+    unsigned c = 0;
 #pragma unroll
     for (int k = 0; k < kWinItems; ++k) {
-        f[k] = row_flags(keep, base + k, n, n_keep);
-        s += f[k];
+        f[k] = base + k < n && keep[base + k] != 0;
+        c += f[k];
     }
-    unsigned long long total;
-    unsigned long long run = part[blockIdx.x] + block_exclusive_scan_u64(s, &total);
-    const long long nk = *n_keep;
+    unsigned total;
+    long long S = (long long)part[blockIdx.x] + block_exclusive_scan(c, &total);
+    const long long nk = *n_keep, snk = counts[0];
 #pragma unroll
     for (int k = 0; k < kWinItems; ++k) {
         const long long i = base + k;
         if (i >= n) break;
-        if (f[k] & 0xFFFFFFFFull) holes_list[run & 0xFFFFFFFFull] = (int32_t)i;
-        if (f[k] >> 32) movers_asc[run >> 32] = (int32_t)i;
-        if (moved_from && i < nk && keep[i]) moved_from[i] = (int32_t)i;
-        run += f[k];
+        if (i < nk) {
+            if (!f[k]) holes_list[i - S] = (int32_t)i;
+            else if (moved_from) moved_from[i] = (int32_t)i;
+        } else if (f[k]) {
+            movers_asc[S - snk] = (int32_t)i;
+        }
+        S += f[k];
     }
 }
 
-// One thread per mover (ascending rank q): its row moves into the hole of
-// rank n_movers - 1 - q.
-__global__ void __launch_bounds__(256) k_win_move(const ColTable cols, long long n,
-                                                  const unsigned long long* __restrict__ grand,
-                                                  const int32_t* __restrict__ holes_list,
-                                                  const int32_t* __restrict__ movers_asc,
-                                                  int32_t* __restrict__ moved_from) {
-    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long n_movers = (long long)(*grand >> 32);
-    if (q >= n_movers || q >= n) return;
-    const int32_t src = movers_asc[q];
-    const int32_t dst = holes_list[n_movers - 1 - q];
-    for (int c = 0; c < cols.n; ++c) {
-        const int words = cols.words[c];
-        const uint32_t* from = cols.ptr[c] + (size_t)src * words;
-        uint32_t* to = cols.ptr[c] + (size_t)dst * words;
-        for (int k = 0; k < words; ++k) to[k] = from[k];
+// Row copies by warps.  A warp holds up to 32 entries (lane e: source row
+// s_row, destination row d_row, d_row < 0 = no entry) and copies every column
+// of those rows word-parallel: word w of a column's chunk is word w % words of
+// entry w / words, so neighbouring lanes touch neighbouring words of a row and
+// the rows of neighbouring entries; four words per lane are in flight.
+constexpr int kCopyThreads = 256;
+constexpr int kCopyUnroll = 4;
+constexpr int kCopyBlocksPerSM = 5;
+
+__device__ __forceinline__ void warp_copy_rows(const ColTable& from, const ColTable& to, int32_t s_row,
+                                               int32_t d_row) {
+    const int lane = threadIdx.x & 31;
+    for (int c = 0; c < from.n; ++c) {
+        const int words = from.words[c];
+        // (w + 0.5) / words is at least 1 / (2 words) from an integer and below
+        // 32, so the FP32 quotient truncates to w / words exactly.
+        const float inv = 1.f / (float)words;
+        const int total = 32 * words;
+        const uint32_t* __restrict__ f = from.ptr[c];
+        uint32_t* __restrict__ t = to.ptr[c];
+        for (int w0 = 0; w0 < total; w0 += 32 * kCopyUnroll) {
+            uint32_t val[kCopyUnroll];
+            long long dpos[kCopyUnroll];
+#pragma unroll
+            for (int u = 0; u < kCopyUnroll; ++u) {
+                const int w = w0 + u * 32 + lane;
+                const int e = min(__float2int_rz(((float)w + 0.5f) * inv), 31);
+                const int k = w - e * words;
+                const int32_t sr = __shfl_sync(0xffffffffu, s_row, e);
+                const int32_t dr = __shfl_sync(0xffffffffu, d_row, e);
+                const bool ok = w < total && dr >= 0;
+                dpos[u] = ok ? (long long)dr * words + k : -1ll;
+                val[u] = ok ? f[(long long)sr * words + k] : 0u;
+            }
+#pragma unroll
+            for (int u = 0; u < kCopyUnroll; ++u)
+                if (dpos[u] >= 0) t[dpos[u]] = val[u];
+        }
     }
-    if (moved_from) moved_from[dst] = src;
+}
+
+// Mover of ascending rank q moves into the hole of rank n_movers - 1 - q; a
+// warp takes 32 consecutive ranks (grid-stride over the rank chunks).
+__global__ void __launch_bounds__(kCopyThreads, kCopyBlocksPerSM) k_win_move(const ColTable cols, long long n,
+                                                           const long long* __restrict__ counts,
+                                                           const int32_t* __restrict__ holes_list,
+                                                           const int32_t* __restrict__ movers_asc,
+                                                           int32_t* __restrict__ moved_from) {
+    const long long n_movers = min(counts[1], n);
+    const int lane = threadIdx.x & 31;
+    const long long warp = ((long long)blockIdx.x * kCopyThreads + threadIdx.x) >> 5;
+    const long long n_warps = (long long)gridDim.x * (kCopyThreads / 32);
+    for (long long q0 = warp * 32; q0 < n_movers; q0 += n_warps * 32) {
+        const long long q = q0 + lane;
+        int32_t src = 0, dst = -1;
+        if (q < n_movers) {
+            src = movers_asc[q];
+            dst = holes_list[n_movers - 1 - q];
+            if (moved_from) moved_from[dst] = src;
+        }
+        warp_copy_rows(cols, cols, src, dst);
+    }
 }
 
 // Rows idx[0..m) of each source column, gathered contiguously into dst.
-__global__ void __launch_bounds__(256) k_win_gather(const ColTable src, const ColTable dst,
-                                                    const int32_t* __restrict__ idx, long long m, long long n) {
-    const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= m) return;
-    const int32_t r = idx[j];
-    if (r < 0 || r >= n) return;  // validated on the host for host-known indices; guards the read
-    for (int c = 0; c < src.n; ++c) {
-        const int words = src.words[c];
-        const uint32_t* from = src.ptr[c] + (size_t)r * words;
-        uint32_t* to = dst.ptr[c] + (size_t)j * words;
-        for (int k = 0; k < words; ++k) to[k] = from[k];
+__global__ void __launch_bounds__(kCopyThreads, kCopyBlocksPerSM) k_win_gather(const ColTable src, const ColTable dst,
+                                                             const int32_t* __restrict__ idx, long long m,
+                                                             long long n) {
+    const int lane = threadIdx.x & 31;
+    const long long warp = ((long long)blockIdx.x * kCopyThreads + threadIdx.x) >> 5;
+    const long long n_warps = (long long)gridDim.x * (kCopyThreads / 32);
+    for (long long j0 = warp * 32; j0 < m; j0 += n_warps * 32) {
+        const long long j = j0 + lane;
+        int32_t r = 0, d = -1;
+        if (j < m) {
+            r = idx[j];
+            // validated on the host for host-known indices; guards the read
+            if (r >= 0 && r < n) d = (int32_t)j;
+            else r = 0;
+        }
+        warp_copy_rows(src, dst, r, d);
+    }
+}
+
+// Rows [a, b) of every column set to zero (contiguous words per column).
+__global__ void __launch_bounds__(kCopyThreads) k_win_clear(const ColTable cols, long long a, long long b) {
+    const long long t0 = (long long)blockIdx.x * kCopyThreads + threadIdx.x;
+    const long long stride = (long long)gridDim.x * kCopyThreads;
+    for (int c = 0; c < cols.n; ++c) {
+        const int words = cols.words[c];
+        uint32_t* p = cols.ptr[c] + a * words;
+        const long long cnt = (b - a) * words;
+        for (long long i = t0; i < cnt; i += stride) p[i] = 0u;
     }
 }
 
@@ -234,42 +306,64 @@ int window_max_columns() { return kMaxCols; }
 size_t window_scratch_bytes(long long n) {
     const long long nblk = (n + kWinChunk - 1) / kWinChunk;
     auto al = [](size_t b) { return (b + 255) / 256 * 256; };
-    return al(sizeof(unsigned long long) * (size_t)(2 * nblk + 2)) + al(sizeof(int32_t) * (size_t)(n > 0 ? n : 1)) * 2;
+    return al(sizeof(long long) * 2) + al(sizeof(unsigned) * (size_t)(nblk > 0 ? nblk : 1)) +
+           al(sizeof(int32_t) * (size_t)(n > 0 ? n : 1)) * 2;
+}
+
+// Grid of the row-copy kernels: one chunk of 32 rows per warp, at most the
+// blocks one SM holds at once (up to 51 registers a thread) times the SMs,
+// grid-stride beyond that.
+unsigned copy_grid(long long rows, int sm_count) {
+    const long long chunks = (rows + 31) / 32;
+    const long long blocks = (chunks + kCopyThreads / 32 - 1) / (kCopyThreads / 32);
+    const long long cap = (long long)(sm_count > 0 ? sm_count : 148) * kCopyBlocksPerSM;
+    return (unsigned)(blocks < 1 ? 1 : (blocks < cap ? blocks : cap));
 }
 
 cudaError_t launch_window_compact(const gs_window_column* cols_host, int n_cols, long long n, const uint8_t* keep,
-                                  long long* n_keep_dev, int32_t* moved_from, void* scratch, cudaStream_t s,
-                                  Prof& pf) {
+                                  long long* n_keep_dev, int32_t* moved_from, void* scratch, int sm_count,
+                                  cudaStream_t s, Prof& pf) {
     const long long nblk = (n + kWinChunk - 1) / kWinChunk;
     auto al = [](size_t b) { return (b + 255) / 256 * 256; };
     char* p = static_cast<char*>(scratch);
-    unsigned long long* part = reinterpret_cast<unsigned long long*>(p);
-    unsigned long long* grand = part + nblk;
-    p += al(sizeof(unsigned long long) * (size_t)(2 * nblk + 2));
+    long long* counts = reinterpret_cast<long long*>(p);
+    p += al(sizeof(long long) * 2);
+    unsigned* part = reinterpret_cast<unsigned*>(p);
+    p += al(sizeof(unsigned) * (size_t)(nblk > 0 ? nblk : 1));
     int32_t* holes_list = reinterpret_cast<int32_t*>(p);
     p += al(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
     int32_t* movers_asc = reinterpret_cast<int32_t*>(p);
     const ColTable cols = col_table(cols_host, n_cols);
-    const int pi = pf.begin(GS_KF_WINDOW, s, 6);
-    // survivors -> n_keep
-    k_win_reduce<<<(unsigned)nblk, kWinThreads, 0, s>>>(keep, n, nullptr, part);
-    k_win_top<<<1, 1024, 0, s>>>(part, (int)nblk, n_keep_dev, nullptr);
-    // holes and movers
-    k_win_reduce<<<(unsigned)nblk, kWinThreads, 0, s>>>(keep, n, n_keep_dev, part);
-    k_win_top<<<1, 1024, 0, s>>>(part, (int)nblk, nullptr, grand);
-    k_win_rank<<<(unsigned)nblk, kWinThreads, 0, s>>>(keep, n, n_keep_dev, part, holes_list, movers_asc,
+    const int pi = pf.begin(GS_KF_WINDOW, s, 4);
+    k_win_reduce<<<(unsigned)nblk, kWinThreads, 0, s>>>(keep, n, part);
+    k_win_top<<<1, 1024, 0, s>>>(keep, n, part, (int)nblk, n_keep_dev, counts);
+    k_win_rank<<<(unsigned)nblk, kWinThreads, 0, s>>>(keep, n, n_keep_dev, part, counts, holes_list, movers_asc,
                                                        moved_from);
-    k_win_move<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(cols, n, grand, holes_list, movers_asc, moved_from);
+    k_win_move<<<copy_grid(n / 2, sm_count), kCopyThreads, 0, s>>>(cols, n, counts, holes_list, movers_asc,
+                                                                  moved_from);
     pf.end(pi, s);
     return cudaGetLastError();
 }
 
 cudaError_t launch_window_gather(const gs_window_column* src_host, const gs_window_column* dst_host, int n_cols,
-                                 const int32_t* idx, long long m, long long n, cudaStream_t s, Prof& pf) {
+                                 const int32_t* idx, long long m, long long n, int sm_count, cudaStream_t s,
+                                 Prof& pf) {
     const int pi = pf.begin(GS_KF_WINDOW, s);
     if (m > 0)
-        k_win_gather<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(col_table(src_host, n_cols),
-                                                                  col_table(dst_host, n_cols), idx, m, n);
+        k_win_gather<<<copy_grid(m, sm_count), kCopyThreads, 0, s>>>(col_table(src_host, n_cols),
+                                                                      col_table(dst_host, n_cols), idx, m, n);
+    pf.end(pi, s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_window_clear(const gs_window_column* cols_host, int n_cols, long long begin, long long end,
+                                int sm_count, cudaStream_t s, Prof& pf) {
+    if (end <= begin) return cudaSuccess;
+    const int pi = pf.begin(GS_KF_WINDOW, s);
+    const ColTable cols = col_table(cols_host, n_cols);
+    long long words = 0;
+    for (int c = 0; c < n_cols; ++c) words += cols.words[c];
+    k_win_clear<<<copy_grid((end - begin) * words / 32, sm_count), kCopyThreads, 0, s>>>(cols, begin, end);
     pf.end(pi, s);
     return cudaGetLastError();
 }

@@ -208,9 +208,12 @@ class GaussianWindow:
         return self._ctx
 
     def _columns(self, rows):
+        """The per-Gaussian state that maintenance carries: parameters, Adam
+        moments and render copies.  The gradients are not carried: every
+        backward overwrites all of them."""
         cols = []
         for k in self.GROUPS:
-            for f in (self.flat, self.gflat, self.m, self.v):
+            for f in (self.flat, self.m, self.v):
                 cols.append(self.column(k, f)[:rows].reshape(rows, -1))
             if k in self.lowp:
                 cols.append(self.lowp[k][:rows].reshape(rows, -1))
@@ -244,8 +247,7 @@ class GaussianWindow:
 
     def append(self, params, image=None, view=None, stream=None):
         """Step 4: appends the Gaussians of `params` (host arrays) at rows
-        [n, n + m) (parameters copied host to device, Adam moments and
-        gradients zeroed); with `image` ([3, H, W] device FP32) and `view`
+        [n, n + m) (parameters copied host to device, Adam moments zeroed); with `image` ([3, H, W] device FP32) and `view`
         their SH start from the bilinear image colour (Sec. II-B.2).  The
         copies are issued on `stream` (default: the current stream)."""
         m = int(params["means"].shape[0])
@@ -257,8 +259,7 @@ class GaussianWindow:
             for k in self.GROUPS:
                 host = torch.as_tensor(np.ascontiguousarray(params[k], np.float32)).view(self.shape(k, m))
                 self.column(k)[a:b].copy_(host.pin_memory(), non_blocking=True)
-                for f in (self.gflat, self.m, self.v):
-                    self.column(k, f)[a:b].zero_()
+            self.ctx().window_clear([self.column(k, f) for k in self.GROUPS for f in (self.m, self.v)], a, b, stream=s)
             self.n = b
             if image is not None:
                 g = self.struct()

@@ -43,6 +43,57 @@ def test_window_compact_matches_oracle(orc, n, p_leave):
         np.testing.assert_array_equal(c[:nk].cpu().numpy(), h[ref])
 
 
+def test_window_compact_many_movers(orc):
+    """More movers than one pass of the copy grid holds (grid-stride path),
+    with a 48-word column (SH degree 3) and a 1-word column."""
+    rng = np.random.default_rng(11)
+    n = 1_300_001
+    keep = rng.uniform(size=n) >= 0.5
+    cols_h = [rng.standard_normal((n, 48)).astype(np.float32), rng.integers(0, 1 << 30, (n, 1)).astype(np.int32)]
+    cols = [torch.as_tensor(c).cuda() for c in cols_h]
+    n_keep = torch.zeros(1, dtype=torch.int64, device="cuda")
+    moved = torch.full((n,), -7, dtype=torch.int32, device="cuda")
+    B.Context(0).window_compact(cols, torch.as_tensor(keep.astype(np.uint8)).cuda(), n_keep, moved)
+    ref = orc.window_compact(keep)
+    nk = int(n_keep.item())
+    assert nk == ref.size
+    np.testing.assert_array_equal(moved[:nk].cpu().numpy(), ref)
+    for c, h in zip(cols, cols_h):
+        np.testing.assert_array_equal(c[:nk].cpu().numpy(), h[ref])
+
+
+@pytest.mark.parametrize("m", [1, 31, 33, 500_000])
+def test_window_gather_sizes(m):
+    rng = np.random.default_rng(m)
+    n = 1_000_003
+    src = [torch.as_tensor(rng.standard_normal((n, w)).astype(np.float32)).cuda() for w in (1, 3, 48)]
+    src.append(torch.as_tensor(rng.standard_normal((n, 6)).astype(np.float16)).cuda())
+    dst = [torch.full((m,) + tuple(s.shape[1:]), 7, dtype=s.dtype, device="cuda") for s in src]
+    idx = rng.integers(0, n, m).astype(np.int32)
+    B.Context(0).window_gather(src, dst, torch.as_tensor(idx).cuda())
+    for s, d in zip(src, dst):
+        np.testing.assert_array_equal(d.cpu().numpy(), s.cpu().numpy()[idx])
+
+
+def test_window_clear_rows():
+    rng = np.random.default_rng(5)
+    n, a, b = 70_001, 12_345, 69_999
+    host = [rng.standard_normal((n, w)).astype(np.float32) for w in (1, 3, 4, 12)]
+    cols = [torch.as_tensor(h).cuda() for h in host]
+    ctx = B.Context(0)
+    ctx.window_clear(cols, a, b)
+    ctx.window_clear(cols, 5, 5)
+    for c, h in zip(cols, host):
+        got = c.cpu().numpy()
+        assert np.all(got[a:b] == 0)
+        np.testing.assert_array_equal(got[:a], h[:a])
+        np.testing.assert_array_equal(got[b:], h[b:])
+    with pytest.raises(B.GsError):
+        ctx.window_clear(cols, 10, 5)
+    with pytest.raises(B.GsError):
+        ctx.window_clear([torch.zeros((4, 4097), device="cuda")], 0, 1)
+
+
 def test_window_gather_is_exact():
     rng = np.random.default_rng(3)
     n, m = 5000, 777
