@@ -41,8 +41,10 @@
  *   R(q) the rotation of the normalised quaternion (w, x, y, z);
  *   Sigma2 = J R_CW Sigma3 R_CW^T J^T + blur I with J the Jacobian of the
  *   pinhole map; opacity sigmoid(o); colour from real spherical harmonics of
- *   degree 0 or 1 along the unit direction from the camera centre to the
- *   mean: c = max(0, C0 k0 + C1 (-d_y k1 + d_z k2 - d_x k3) + 0.5).
+ *   degree D <= 3 along the unit direction d from the camera centre to the
+ *   mean: c = max(0, sum_k Y_k(d) k_k + 0.5), Y_k (k = l^2 + l + m,
+ *   m = -l..l) the real harmonics with the Condon-Shortley phase; degree 1
+ *   reads c = max(0, C0 k0 + C1 (-d_y k1 + d_z k2 - d_x k3) + 0.5).
  * - Compositing (Eq. raster): per pixel, front to back over the Gaussians
  *   ordered by (depth, index): alpha = min(alpha_max, sigma G(x)); skip if
  *   alpha < alpha_min; stop before the Gaussian that would take the
@@ -149,7 +151,7 @@ typedef struct gs_gaussians {
     const void* sh;         /* [N,K,3], K = (sh_degree+1)^2, coefficient-major */
     int32_t scale_dtype, rot_dtype, opacity_dtype, sh_dtype; /* gs_dtype */
     int64_t n;
-    int32_t sh_degree; /* 0 or 1 */
+    int32_t sh_degree; /* 0 to 3 */
 } gs_gaussians;
 
 /* Gradients (device memory, FP32, same shapes as gs_gaussians).  Every entry

@@ -31,9 +31,10 @@
  *   - a low-pass blur b is added to the diagonal of Sigma2;
  *   - pixel (u, v) is sampled at (u + 0.5, v + 0.5);
  *   - depth ties are ordered by Gaussian index;
- *   - colour = max(0, C0 k0 + C1 (-d_y k1 + d_z k2 - d_x k3) + 0.5) with d the
- *     unit view direction from the camera centre, C0, C1 the real spherical
- *     harmonic normalisations of degree 0 and 1;
+ *   - colour = max(0, sum_k Y_k(d) k_k + 0.5) with d the unit view direction
+ *     from the camera centre and Y_k, k = l^2 + l + m, the real spherical
+ *     harmonics of degree l <= 3 with the Condon-Shortley phase, ordered
+ *     m = -l..l (degree 1: Y = C1 (-d_y, d_z, -d_x));
  *   - opacity sigma = sigmoid(logit); scale = exp(log-scale);
  *   - clamps contribute zero derivative; culling is locally constant.
  * With alpha_min = 0, alpha_max = 1, T_min = 0 ("exact mode") the compositing
@@ -60,10 +61,80 @@
  * of their bounds may be ordered either way. */
 #define U32 (1.0 / 16777216.0)
 
-/* Real spherical-harmonic normalisations: Y_00 = 1 / (2 sqrt(pi)),
- * |Y_1m| prefactor = sqrt(3) / (2 sqrt(pi)). */
-static double sh_c0(void) { return 0.5 / sqrt(ORC_PI); }
-static double sh_c1(void) { return 0.5 * sqrt(3.0) / sqrt(ORC_PI); }
+/* Real spherical harmonics up to degree 3 at the direction d (a unit
+ * vector), with the Condon-Shortley phase (-1)^m, index k = l^2 + l + m,
+ * written as homogeneous polynomials of degree l in (x, y, z) = d (on the
+ * unit sphere r^2 = 1 completes the textbook forms, e.g. 5 z^2 - 3 r^2), and
+ * their partial derivatives dY[k][j] = dY_k / dd_j of those polynomials.
+ * Normalisations, from N_lm = sqrt((2l+1)/(4 pi) (l-|m|)!/(l+|m|)!) times the
+ * associated Legendre factor (x sqrt 2 for m != 0):
+ *   l = 0: 1/2 sqrt(1/pi);  l = 1: 1/2 sqrt(3/pi);
+ *   l = 2: 1/2 sqrt(15/pi) (xy, yz, xz), 1/4 sqrt(5/pi) (2z^2 - x^2 - y^2),
+ *          1/4 sqrt(15/pi) (x^2 - y^2);
+ *   l = 3: 1/4 sqrt(35/(2 pi)) (y (3x^2 - y^2), x (x^2 - 3y^2)),
+ *          1/2 sqrt(105/pi) (xyz), 1/4 sqrt(21/(2 pi)) (y, x times
+ *          4z^2 - x^2 - y^2), 1/4 sqrt(7/pi) (z (2z^2 - 3x^2 - 3y^2)),
+ *          1/4 sqrt(105/pi) (z (x^2 - y^2)). */
+static void sh_basis(const double* d, int degree, double* Y, double dY[16][3]) {
+    double x = d[0], y = d[1], z = d[2];
+    for (int k = 0; k < 16; ++k) {
+        Y[k] = 0.0;
+        dY[k][0] = dY[k][1] = dY[k][2] = 0.0;
+    }
+    Y[0] = 0.5 * sqrt(1.0 / ORC_PI);
+    if (degree < 1) return;
+    double c1 = 0.5 * sqrt(3.0 / ORC_PI);
+    Y[1] = -c1 * y; dY[1][1] = -c1;
+    Y[2] = c1 * z;  dY[2][2] = c1;
+    Y[3] = -c1 * x; dY[3][0] = -c1;
+    if (degree < 2) return;
+    double a = 0.5 * sqrt(15.0 / ORC_PI), b = 0.25 * sqrt(5.0 / ORC_PI), c = 0.25 * sqrt(15.0 / ORC_PI);
+    Y[4] = a * x * y;
+    dY[4][0] = a * y; dY[4][1] = a * x;
+    Y[5] = -a * y * z;
+    dY[5][1] = -a * z; dY[5][2] = -a * y;
+    Y[6] = b * (2.0 * z * z - x * x - y * y);
+    dY[6][0] = -2.0 * b * x; dY[6][1] = -2.0 * b * y; dY[6][2] = 4.0 * b * z;
+    Y[7] = -a * x * z;
+    dY[7][0] = -a * z; dY[7][2] = -a * x;
+    Y[8] = c * (x * x - y * y);
+    dY[8][0] = 2.0 * c * x; dY[8][1] = -2.0 * c * y;
+    if (degree < 3) return;
+    double e = 0.25 * sqrt(35.0 / (2.0 * ORC_PI)), f = 0.5 * sqrt(105.0 / ORC_PI);
+    double g = 0.25 * sqrt(21.0 / (2.0 * ORC_PI)), h = 0.25 * sqrt(7.0 / ORC_PI);
+    double j = 0.25 * sqrt(105.0 / ORC_PI);
+    Y[9] = -e * y * (3.0 * x * x - y * y);
+    dY[9][0] = -6.0 * e * x * y; dY[9][1] = -e * (3.0 * x * x - 3.0 * y * y);
+    Y[10] = f * x * y * z;
+    dY[10][0] = f * y * z; dY[10][1] = f * x * z; dY[10][2] = f * x * y;
+    Y[11] = -g * y * (4.0 * z * z - x * x - y * y);
+    dY[11][0] = 2.0 * g * x * y; dY[11][1] = -g * (4.0 * z * z - x * x - 3.0 * y * y);
+    dY[11][2] = -8.0 * g * y * z;
+    Y[12] = h * z * (2.0 * z * z - 3.0 * x * x - 3.0 * y * y);
+    dY[12][0] = -6.0 * h * x * z; dY[12][1] = -6.0 * h * y * z;
+    dY[12][2] = h * (6.0 * z * z - 3.0 * x * x - 3.0 * y * y);
+    Y[13] = -g * x * (4.0 * z * z - x * x - y * y);
+    dY[13][0] = -g * (4.0 * z * z - 3.0 * x * x - y * y); dY[13][1] = 2.0 * g * x * y;
+    dY[13][2] = -8.0 * g * x * z;
+    Y[14] = j * z * (x * x - y * y);
+    dY[14][0] = 2.0 * j * x * z; dY[14][1] = -2.0 * j * y * z; dY[14][2] = j * (x * x - y * y);
+    Y[15] = -e * x * (x * x - 3.0 * y * y);
+    dY[15][0] = -e * (3.0 * x * x - 3.0 * y * y); dY[15][1] = 6.0 * e * x * y;
+}
+
+/* The basis above for n directions (tests): Y [n][16], dY [n][16][3]. */
+int orc_sh_basis(long n, const double* dirs, int degree, double* Y, double* dY) {
+    if (degree < 0 || degree > 3) return -1;
+    for (long i = 0; i < n; ++i) {
+        double y[16], dy[16][3];
+        sh_basis(dirs + 3 * i, degree, y, dy);
+        for (int k = 0; k < 16; ++k) {
+            Y[16 * i + k] = y[k];
+            for (int c = 0; c < 3; ++c) dY[48 * i + 3 * k + c] = dy[k][c];
+        }
+    }
+    return 0;
+}
 
 /* Rotation of the unit quaternion (w, x, y, z): the textbook formula. */
 static void quat_to_R(const double* qh, double* R) {
@@ -163,16 +234,18 @@ static void project_one(const double* mu, const double* ls, const double* quat, 
 
     P->sigma = 1.0 / (1.0 + exp(-ologit));
 
-    /* Colour from SH of degree 0 or 1 along the view direction. */
+    /* Colour from SH of degree <= 3 along the view direction. */
     double campos[3];
     for (int i = 0; i < 3; ++i) campos[i] = -(W[i] * t[0] + W[3 + i] * t[1] + W[6 + i] * t[2]);
     for (int i = 0; i < 3; ++i) P->dvec[i] = mu[i] - campos[i];
     P->dlen = sqrt(P->dvec[0] * P->dvec[0] + P->dvec[1] * P->dvec[1] + P->dvec[2] * P->dvec[2]);
     for (int i = 0; i < 3; ++i) P->dir[i] = P->dvec[i] / P->dlen;
+    double Y[16], dY[16][3];
+    int K = (sh_degree + 1) * (sh_degree + 1);
+    sh_basis(P->dir, sh_degree, Y, dY);
     for (int ch = 0; ch < 3; ++ch) {
-        double v = sh_c0() * sh[ch] + 0.5;
-        if (sh_degree >= 1)
-            v += sh_c1() * (-P->dir[1] * sh[3 + ch] + P->dir[2] * sh[6 + ch] - P->dir[0] * sh[9 + ch]);
+        double v = 0.5;
+        for (int k = 0; k < K; ++k) v += Y[k] * sh[3 * k + ch];
         P->raw[ch] = v;
         P->colour[ch] = v > 0.0 ? v : 0.0;
     }
@@ -553,18 +626,16 @@ int orc_project_backward(long n, const double* means, const double* log_scales,
             graw[ch] = P.raw[ch] > 0.0 ? g_colour[3 * i + ch] : 0.0;
             if (fabs(P.raw[ch]) <= REL_BORDER) g_border_colour[i] = 1;
         }
-        for (int ch = 0; ch < 3; ++ch) g_sh[3 * K * i + ch] += sh_c0() * graw[ch];
+        double Y[16], dY[16][3];
+        sh_basis(P.dir, sh_degree, Y, dY);
+        for (int k = 0; k < K; ++k)
+            for (int ch = 0; ch < 3; ++ch) g_sh[3 * K * i + 3 * k + ch] += Y[k] * graw[ch];
         double gd[3] = {0, 0, 0};
         if (sh_degree >= 1) {
             double gdir[3] = {0, 0, 0};
-            for (int ch = 0; ch < 3; ++ch) {
-                g_sh[3 * K * i + 3 + ch] += -sh_c1() * P.dir[1] * graw[ch];
-                g_sh[3 * K * i + 6 + ch] += sh_c1() * P.dir[2] * graw[ch];
-                g_sh[3 * K * i + 9 + ch] += -sh_c1() * P.dir[0] * graw[ch];
-                gdir[0] += -sh_c1() * shi[9 + ch] * graw[ch];
-                gdir[1] += -sh_c1() * shi[3 + ch] * graw[ch];
-                gdir[2] += sh_c1() * shi[6 + ch] * graw[ch];
-            }
+            for (int k = 1; k < K; ++k)
+                for (int ch = 0; ch < 3; ++ch)
+                    for (int c = 0; c < 3; ++c) gdir[c] += dY[k][c] * shi[3 * k + ch] * graw[ch];
             /* dir = d / |d|: g_d = (g_dir - dir (dir . g_dir)) / |d|. */
             double dotv = P.dir[0] * gdir[0] + P.dir[1] * gdir[1] + P.dir[2] * gdir[2];
             for (int k = 0; k < 3; ++k) gd[k] = (gdir[k] - P.dir[k] * dotv) / P.dlen;
@@ -763,10 +834,13 @@ static void pose_tangents(const orc_proj* P, const double* cam, const double* sh
         double dd = P->dir[0] * ddv[0] + P->dir[1] * ddv[1] + P->dir[2] * ddv[2];
         double ddir[3];
         for (int i = 0; i < 3; ++i) ddir[i] = (ddv[i] - P->dir[i] * dd) / P->dlen;
+        double Y[16], dY[16][3];
+        int K = (sh_degree + 1) * (sh_degree + 1);
+        sh_basis(P->dir, sh_degree, Y, dY);
         for (int ch = 0; ch < 3; ++ch) {
             double draw = 0.0;
-            if (sh_degree >= 1)
-                draw = sh_c1() * (-ddir[1] * sh[3 + ch] + ddir[2] * sh[6 + ch] - ddir[0] * sh[9 + ch]);
+            for (int m = 1; m < K; ++m)
+                draw += (dY[m][0] * ddir[0] + dY[m][1] * ddir[1] + dY[m][2] * ddir[2]) * sh[3 * m + ch];
             dcol[ch][k] = P->raw[ch] > 0.0 ? draw : 0.0;
         }
     }

@@ -72,6 +72,7 @@ def lib():
         L.orc_num_threads.restype = ctypes.c_int
         L.orc_pose_jacobian_pixels.argtypes = ([ctypes.c_long, P, P, ctypes.c_long] + [P] * 5 + [ctypes.c_int] +
                                                [P] * 5 + [ctypes.c_int])
+        L.orc_sh_basis.argtypes = [ctypes.c_long, P, ctypes.c_int, P, P]
         _lib = L
     return _lib
 
@@ -270,6 +271,20 @@ def pose_normal(params, view, target, cfg=None, n_threads=0):
     A = np.einsum("pci,pcj->ij", Hj, Hj)
     b = np.einsum("pci,pc->i", Hj, r)
     return A, b, float((r * r).sum()), bd.reshape(Hh, W)
+
+
+def sh_basis(dirs, degree):
+    """Real spherical harmonics (Condon-Shortley phase, k = l^2 + l + m) of
+    degree <= 3 at unit directions dirs [n, 3], and their partial derivatives
+    as homogeneous polynomials: (Y [n, 16], dY [n, 16, 3]); entries above the
+    degree are 0."""
+    d = _f64(dirs).reshape(-1, 3)
+    n = d.shape[0]
+    Y = np.zeros((n, 16))
+    dY = np.zeros((n, 16, 3))
+    if lib().orc_sh_basis(n, _p(d), int(degree), _p(Y), _p(dY)) != 0:
+        raise ValueError("degree %d outside [0, 3]" % degree)
+    return Y, dY
 
 
 def window_compact(keep):

@@ -319,8 +319,8 @@ int check_gaussians(gs_ctx* ctx, const gs_gaussians* g, const gs_view* views, in
     if (!g->means || !g->log_scales || !g->quats || !g->opacity || !g->sh)
         return fail(ctx, GS_ERR_INVALID_ARG, "a Gaussian attribute pointer is NULL");
     if (g->n <= 0) return fail(ctx, GS_ERR_INVALID_ARG, "n=%lld must be positive", (long long)g->n);
-    if (g->sh_degree < 0 || g->sh_degree > 1)
-        return fail(ctx, GS_ERR_INVALID_ARG, "sh_degree=%d not in {0, 1}", g->sh_degree);
+    if (g->sh_degree < 0 || g->sh_degree > 3)
+        return fail(ctx, GS_ERR_INVALID_ARG, "sh_degree=%d not in [0, 3]", g->sh_degree);
     const int dts[4] = {g->scale_dtype, g->rot_dtype, g->opacity_dtype, g->sh_dtype};
     for (int k = 0; k < 4; ++k)
         if (dts[k] < GS_F32 || dts[k] > GS_BF16) return fail(ctx, GS_ERR_INVALID_ARG, "bad dtype %d", dts[k]);
@@ -694,7 +694,8 @@ int gs_sh_init_bilinear(gs_ctx* ctx, const gs_gaussians* g, const gs_view* view,
     if (!ctx) return GS_ERR_INVALID_ARG;
     if (!g || !g->means || !view || !image || !sh_out)
         return fail(ctx, GS_ERR_INVALID_ARG, "gaussians, means, view, image or sh_out is NULL");
-    if (g->sh_degree < 0 || g->sh_degree > 1) return fail(ctx, GS_ERR_INVALID_ARG, "sh_degree=%d", g->sh_degree);
+    if (g->sh_degree < 0 || g->sh_degree > 3)
+        return fail(ctx, GS_ERR_INVALID_ARG, "sh_degree=%d not in [0, 3]", g->sh_degree);
     if (begin < 0 || end < begin || end > g->n)
         return fail(ctx, GS_ERR_INVALID_ARG, "range [%lld, %lld) outside [0, %lld]", (long long)begin,
                     (long long)end, (long long)g->n);

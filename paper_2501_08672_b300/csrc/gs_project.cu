@@ -20,8 +20,78 @@ namespace gsb {
 
 namespace {
 
-constexpr float kShC0 = 0.28209479177387814f;  // 1 / (2 sqrt(pi))
-constexpr float kShC1 = 0.48860251190291992f;  // sqrt(3) / (2 sqrt(pi))
+// Real spherical harmonics of degree D <= 3 with the Condon-Shortley phase,
+// index k = l^2 + l + m (m = -l..l), as homogeneous polynomials of the unit
+// view direction (x, y, z).  The normalisation of (l, m) is
+// sqrt((2l+1)/(4 pi) (l-|m|)!/(l+|m|)!), times sqrt(2) for m != 0, folded with
+// the Legendre factor of each polynomial:
+constexpr float kShC0 = 0.28209479177387814f;  // 1/2 sqrt(1/pi)
+constexpr float kShC1 = 0.48860251190291990f;  // 1/2 sqrt(3/pi): y, z, x
+constexpr float kShA2 = 1.0925484305920792f;   // 1/2 sqrt(15/pi): xy, yz, xz
+constexpr float kShB2 = 0.31539156525252005f;  // 1/4 sqrt(5/pi): 2z^2 - x^2 - y^2
+constexpr float kShC2 = 0.54627421529603960f;  // 1/4 sqrt(15/pi): x^2 - y^2
+constexpr float kShE3 = 0.59004358992664350f;  // 1/4 sqrt(35/(2 pi)): y (3x^2 - y^2), x (x^2 - 3y^2)
+constexpr float kShF3 = 2.8906114426405540f;   // 1/2 sqrt(105/pi): xyz
+constexpr float kShG3 = 0.45704579946446580f;  // 1/4 sqrt(21/(2 pi)): y, x times (4z^2 - x^2 - y^2)
+constexpr float kShH3 = 0.37317633259011540f;  // 1/4 sqrt(7/pi): z (2z^2 - 3x^2 - 3y^2)
+constexpr float kShJ3 = 1.4453057213202770f;   // 1/4 sqrt(105/pi): z (x^2 - y^2)
+
+template <int D>
+__device__ __forceinline__ void sh_basis(const float* d, float* Y) {
+    const float x = d[0], y = d[1], z = d[2];
+    Y[0] = kShC0;
+    if (D >= 1) {
+        Y[1] = -kShC1 * y;
+        Y[2] = kShC1 * z;
+        Y[3] = -kShC1 * x;
+    }
+    if (D >= 2) {
+        const float xx = x * x, yy = y * y, zz = z * z;
+        Y[4] = kShA2 * x * y;
+        Y[5] = -kShA2 * y * z;
+        Y[6] = kShB2 * (2.f * zz - xx - yy);
+        Y[7] = -kShA2 * x * z;
+        Y[8] = kShC2 * (xx - yy);
+        if (D >= 3) {
+            Y[9] = -kShE3 * y * (3.f * xx - yy);
+            Y[10] = kShF3 * x * y * z;
+            Y[11] = -kShG3 * y * (4.f * zz - xx - yy);
+            Y[12] = kShH3 * z * (2.f * zz - 3.f * xx - 3.f * yy);
+            Y[13] = -kShG3 * x * (4.f * zz - xx - yy);
+            Y[14] = kShJ3 * z * (xx - yy);
+            Y[15] = -kShE3 * x * (xx - 3.f * yy);
+        }
+    }
+}
+
+// Derivative of every basis polynomial along v: T[k] = grad Y_k(d) . v.
+template <int D>
+__device__ __forceinline__ void sh_basis_along(const float* d, const float* v, float* T) {
+    const float x = d[0], y = d[1], z = d[2], vx = v[0], vy = v[1], vz = v[2];
+    T[0] = 0.f;
+    if (D >= 1) {
+        T[1] = -kShC1 * vy;
+        T[2] = kShC1 * vz;
+        T[3] = -kShC1 * vx;
+    }
+    if (D >= 2) {
+        T[4] = kShA2 * (vx * y + x * vy);
+        T[5] = -kShA2 * (vy * z + y * vz);
+        T[6] = 2.f * kShB2 * (2.f * z * vz - x * vx - y * vy);
+        T[7] = -kShA2 * (vx * z + x * vz);
+        T[8] = 2.f * kShC2 * (x * vx - y * vy);
+        if (D >= 3) {
+            const float xx = x * x, yy = y * y, zz = z * z;
+            T[9] = -kShE3 * (6.f * x * y * vx + 3.f * (xx - yy) * vy);
+            T[10] = kShF3 * (y * z * vx + x * z * vy + x * y * vz);
+            T[11] = -kShG3 * (-2.f * x * y * vx + (4.f * zz - xx - 3.f * yy) * vy + 8.f * y * z * vz);
+            T[12] = kShH3 * (-6.f * x * z * vx - 6.f * y * z * vy + (6.f * zz - 3.f * xx - 3.f * yy) * vz);
+            T[13] = -kShG3 * ((4.f * zz - 3.f * xx - yy) * vx - 2.f * x * y * vy + 8.f * x * z * vz);
+            T[14] = kShJ3 * (2.f * x * z * vx - 2.f * y * z * vy + (xx - yy) * vz);
+            T[15] = -kShE3 * (3.f * (xx - yy) * vx - 6.f * x * y * vy);
+        }
+    }
+}
 
 struct Proj {
     float qh[4];     // unit quaternion
@@ -113,21 +183,21 @@ __device__ __forceinline__ bool project_view(const ViewParam& V, const RenderCon
     return true;
 }
 
+template <int D>
 __device__ __forceinline__ void view_colour(const ViewParam& V, const GaussPtrs& g, long long i,
                                             const float* mu, Proj& P, float* col) {
+    constexpr int K = (D + 1) * (D + 1);
     float d[3] = {mu[0] - V.campos[0], mu[1] - V.campos[1], mu[2] - V.campos[2]};
     P.inv_len = 1.f / sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
     for (int k = 0; k < 3; ++k) P.dir[k] = d[k] * P.inv_len;
-    const int K = (g.sh_degree + 1) * (g.sh_degree + 1);
+    float Y[K];
+    sh_basis<D>(P.dir, Y);
     const long long base = i * K * 3;
+#pragma unroll
     for (int ch = 0; ch < 3; ++ch) {
-        float v = kShC0 * load_as_float(g.sh, g.sh_dtype, base + ch) + 0.5f;
-        if (g.sh_degree >= 1) {
-            const float k1 = load_as_float(g.sh, g.sh_dtype, base + 3 + ch);
-            const float k2 = load_as_float(g.sh, g.sh_dtype, base + 6 + ch);
-            const float k3 = load_as_float(g.sh, g.sh_dtype, base + 9 + ch);
-            v += kShC1 * (-P.dir[1] * k1 + P.dir[2] * k2 - P.dir[0] * k3);
-        }
+        float v = 0.5f;
+#pragma unroll
+        for (int k = 0; k < K; ++k) v = fmaf(Y[k], load_as_float(g.sh, g.sh_dtype, base + 3 * k + ch), v);
         P.raw[ch] = v;
         col[ch] = fmaxf(v, 0.f);
     }
@@ -169,6 +239,7 @@ __device__ __forceinline__ uint32_t ordered_bits(float x) {
     return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
 }
 
+template <int D>
 __global__ void __launch_bounds__(256) k_project(const __grid_constant__ BatchParam bp, GaussPtrs g,
                                                  RenderConst rc, WsPtrs ws) {
     const ViewParam& V = bp.v[blockIdx.y];
@@ -198,7 +269,7 @@ __global__ void __launch_bounds__(256) k_project(const __grid_constant__ BatchPa
         const float qx = V.fx * P.pc[0] * iz + V.cx;
         const float qy = V.fy * P.pc[1] * iz + V.cy;
         float col[3];
-        view_colour(V, g, i, mu, P, col);
+        view_colour<D>(V, g, i, mu, P, col);
         // Pixel box containing every pixel centre where sigma G >= alpha_min:
         // the ellipse d^T Sigma2^-1 d <= 2 ln(sigma / alpha_min) has half-widths
         // sqrt(r2 Sigma2_xx), sqrt(r2 Sigma2_yy).  The small margin only adds
@@ -280,13 +351,14 @@ __global__ void __launch_bounds__(256) k_project(const __grid_constant__ BatchPa
 // ---------------------------------------------------------------------------
 // Backward
 
+template <int D>
 __global__ void __launch_bounds__(256) k_project_bwd(const __grid_constant__ BatchParam bp,
                                                      GaussPtrs g, RenderConst rc, WsPtrs ws,
                                                      GradPtrs gr, int want_params, int want_pose,
                                                      int pose_blocks) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const bool live = i < g.n;
-    const int K = (g.sh_degree + 1) * (g.sh_degree + 1);
+    constexpr int K = (D + 1) * (D + 1);
 
     Proj P;
     float mu[3] = {0.f, 0.f, 0.f}, ologit = 0.f;
@@ -295,7 +367,8 @@ __global__ void __launch_bounds__(256) k_project_bwd(const __grid_constant__ Bat
     float gmu[3] = {0.f, 0.f, 0.f};
     float gM[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // dL/d(R S)
     float gop = 0.f;
-    float gsh[16 * 3];
+    float gsh[K * 3];
+#pragma unroll
     for (int e = 0; e < K * 3; ++e) gsh[e] = 0.f;
 
     __shared__ float s_red[8][6];
@@ -324,26 +397,43 @@ __global__ void __launch_bounds__(256) k_project_bwd(const __grid_constant__ Bat
             const float gA = -0.5f * acc[2], gB = -acc[3], gC = -0.5f * acc[4];
             const float gsig = acc[5] / sigma;
             float col[3];
-            view_colour(V, g, i, mu, P, col);
-            // colour -> SH (+ view direction)
+            view_colour<D>(V, g, i, mu, P, col);
+            // colour -> SH (+ view direction): dL/dk_k = Y_k graw, and the
+            // direction gradient sum_k w_k grad Y_k with w_k = sum_ch k_k,ch graw_ch
             float gd[3] = {0.f, 0.f, 0.f};
             {
-                float gdir[3] = {0.f, 0.f, 0.f};
-                const long long base = i * K * 3;
-                for (int ch = 0; ch < 3; ++ch) {
-                    const float graw = P.raw[ch] > 0.f ? acc[6 + ch] : 0.f;
-                    gsh[ch] += kShC0 * graw;
-                    if (g.sh_degree >= 1) {
-                        gsh[3 + ch] += -kShC1 * P.dir[1] * graw;
-                        gsh[6 + ch] += kShC1 * P.dir[2] * graw;
-                        gsh[9 + ch] += -kShC1 * P.dir[0] * graw;
-                        gdir[0] += -kShC1 * load_as_float(g.sh, g.sh_dtype, base + 9 + ch) * graw;
-                        gdir[1] += -kShC1 * load_as_float(g.sh, g.sh_dtype, base + 3 + ch) * graw;
-                        gdir[2] += kShC1 * load_as_float(g.sh, g.sh_dtype, base + 6 + ch) * graw;
+                float graw[3];
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch) graw[ch] = P.raw[ch] > 0.f ? acc[6 + ch] : 0.f;
+                float Y[K];
+                sh_basis<D>(P.dir, Y);
+#pragma unroll
+                for (int k = 0; k < K; ++k)
+#pragma unroll
+                    for (int ch = 0; ch < 3; ++ch) gsh[3 * k + ch] = fmaf(Y[k], graw[ch], gsh[3 * k + ch]);
+                if (D >= 1) {
+                    const long long base = i * K * 3;
+                    float w[K];
+#pragma unroll
+                    for (int k = 0; k < K; ++k) {
+                        w[k] = 0.f;
+#pragma unroll
+                        for (int ch = 0; ch < 3; ++ch)
+                            w[k] = fmaf(load_as_float(g.sh, g.sh_dtype, base + 3 * k + ch), graw[ch], w[k]);
                     }
-                }
-                if (g.sh_degree >= 1) {
+                    float gdir[3];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        const float e[3] = {c == 0 ? 1.f : 0.f, c == 1 ? 1.f : 0.f, c == 2 ? 1.f : 0.f};
+                        float T[K];
+                        sh_basis_along<D>(P.dir, e, T);
+                        gdir[c] = 0.f;
+#pragma unroll
+                        for (int k = 1; k < K; ++k) gdir[c] = fmaf(w[k], T[k], gdir[c]);
+                    }
+                    // dir = d / |d|: dL/dd = (gdir - dir (dir . gdir)) / |d|
                     const float dd = P.dir[0] * gdir[0] + P.dir[1] * gdir[1] + P.dir[2] * gdir[2];
+#pragma unroll
                     for (int k = 0; k < 3; ++k) {
                         gd[k] = (gdir[k] - P.dir[k] * dd) * P.inv_len;
                         gmu[k] += gd[k];
@@ -455,6 +545,7 @@ __global__ void __launch_bounds__(256) k_project_bwd(const __grid_constant__ Bat
     for (int k = 0; k < 4; ++k) gr.quats[4 * i + k] = (gq[k] - P.qh[k] * dq) * P.inv_qn;
     for (int k = 0; k < 3; ++k) gr.means[3 * i + k] = gmu[k];
     gr.opacity[i] = gop;
+#pragma unroll
     for (int e = 0; e < K * 3; ++e) gr.sh[i * K * 3 + e] = gsh[e];
 }
 
@@ -482,6 +573,7 @@ __global__ void k_pose_finish(const float* partials, int nblocks, int n_views, f
 // Layout per record, k = 0..5: tan[12 r + 2k] = (dq_x, dq_y, dS_a, dS_b),
 // tan[12 r + 2k + 1] = (dS_c, dc_r, dc_g, dc_b), with Sigma2 = [[a, b], [b, c]].
 // Records with no listed tile are skipped (never read).
+template <int D>
 __global__ void __launch_bounds__(256) k_pose_tangents(const __grid_constant__ BatchParam bp, GaussPtrs g,
                                                        RenderConst rc, WsPtrs ws, float4* __restrict__ tan) {
     const ViewParam& V = bp.v[blockIdx.y];
@@ -496,7 +588,7 @@ __global__ void __launch_bounds__(256) k_pose_tangents(const __grid_constant__ B
     load_gaussian(g, i, mu, P, ologit);
     if (!project_view(V, rc, mu, P)) return;
     float col[3];
-    view_colour(V, g, i, mu, P, col);
+    view_colour<D>(V, g, i, mu, P, col);
     float Mc[9];
 #pragma unroll
     for (int a = 0; a < 3; ++a)
@@ -507,13 +599,7 @@ __global__ void __launch_bounds__(256) k_pose_tangents(const __grid_constant__ B
     const float iz = 1.f / z, iz2 = iz * iz, iz3 = iz2 * iz;
     const float j00 = V.fx * iz, j02 = -V.fx * x * iz2;
     const float j11 = V.fy * iz, j12 = -V.fy * y * iz2;
-    const int K = (g.sh_degree + 1) * (g.sh_degree + 1);
-    float kk[3][3];  // SH degree-1 coefficients k1, k2, k3 per channel
-#pragma unroll
-    for (int ch = 0; ch < 3; ++ch)
-#pragma unroll
-        for (int m = 0; m < 3; ++m)
-            kk[ch][m] = g.sh_degree >= 1 ? load_as_float(g.sh, g.sh_dtype, i * K * 3 + 3 * (m + 1) + ch) : 0.f;
+    constexpr int K = (D + 1) * (D + 1);
     float4* out = tan + (size_t)kPoseTan4 * r;
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
@@ -547,15 +633,20 @@ __global__ void __launch_bounds__(256) k_pose_tangents(const __grid_constant__ B
                           U0[2] * dU1[2];
         const float dSc = 2.f * (dU1[0] * U1[0] + dU1[1] * U1[1] + dU1[2] * U1[2]);
         float dc[3] = {0.f, 0.f, 0.f};
-        if (k >= 3 && g.sh_degree >= 1) {
+        if (k >= 3 && D >= 1) {
+            // a camera translation moves the centre: d(dir) = (W^T e - dir (dir . W^T e)) / |d|
             const float dv0 = V.R[3 * (k - 3)], dv1 = V.R[3 * (k - 3) + 1], dv2 = V.R[3 * (k - 3) + 2];
             const float dd = P.dir[0] * dv0 + P.dir[1] * dv1 + P.dir[2] * dv2;
-            const float dr0 = (dv0 - P.dir[0] * dd) * P.inv_len;
-            const float dr1 = (dv1 - P.dir[1] * dd) * P.inv_len;
-            const float dr2 = (dv2 - P.dir[2] * dd) * P.inv_len;
+            const float ddir[3] = {(dv0 - P.dir[0] * dd) * P.inv_len, (dv1 - P.dir[1] * dd) * P.inv_len,
+                                   (dv2 - P.dir[2] * dd) * P.inv_len};
+            float T[K];
+            sh_basis_along<D>(P.dir, ddir, T);
 #pragma unroll
             for (int ch = 0; ch < 3; ++ch) {
-                const float draw = kShC1 * (-dr1 * kk[ch][0] + dr2 * kk[ch][1] - dr0 * kk[ch][2]);
+                float draw = 0.f;
+#pragma unroll
+                for (int m = 1; m < K; ++m)
+                    draw = fmaf(T[m], load_as_float(g.sh, g.sh_dtype, i * K * 3 + 3 * m + ch), draw);
                 dc[ch] = P.raw[ch] > 0.f ? draw : 0.f;
             }
         }
@@ -571,7 +662,12 @@ cudaError_t launch_project(const BatchParam& bp, const GaussPtrs& g, const Rende
     if (bp.max_count <= 0) return cudaSuccess;
     dim3 grid((unsigned)((bp.max_count + 255) / 256), (unsigned)bp.n_views);
     const int pi = pf.begin(GS_KF_PROJECT, s);
-    k_project<<<grid, 256, 0, s>>>(bp, g, rc, ws);
+    switch (g.sh_degree) {
+        case 0: k_project<0><<<grid, 256, 0, s>>>(bp, g, rc, ws); break;
+        case 1: k_project<1><<<grid, 256, 0, s>>>(bp, g, rc, ws); break;
+        case 2: k_project<2><<<grid, 256, 0, s>>>(bp, g, rc, ws); break;
+        default: k_project<3><<<grid, 256, 0, s>>>(bp, g, rc, ws); break;
+    }
     pf.end(pi, s);
     return cudaGetLastError();
 }
@@ -589,7 +685,13 @@ cudaError_t launch_project_bwd(const BatchParam& bp, const GaussPtrs& g, const R
     const int pose_blocks = (int)((max_g_end + 255) / 256);
     GradPtrs gr = grads ? *grads : GradPtrs{nullptr, nullptr, nullptr, nullptr, nullptr};
     const int pi = pf.begin(GS_KF_PROJECT_BWD, s, dL_dpose ? 2 : 1);
-    k_project_bwd<<<nblk, 256, 0, s>>>(bp, g, rc, ws, gr, grads != nullptr, dL_dpose != nullptr, pose_blocks);
+    const int wp = grads != nullptr, wq = dL_dpose != nullptr;
+    switch (g.sh_degree) {
+        case 0: k_project_bwd<0><<<nblk, 256, 0, s>>>(bp, g, rc, ws, gr, wp, wq, pose_blocks); break;
+        case 1: k_project_bwd<1><<<nblk, 256, 0, s>>>(bp, g, rc, ws, gr, wp, wq, pose_blocks); break;
+        case 2: k_project_bwd<2><<<nblk, 256, 0, s>>>(bp, g, rc, ws, gr, wp, wq, pose_blocks); break;
+        default: k_project_bwd<3><<<nblk, 256, 0, s>>>(bp, g, rc, ws, gr, wp, wq, pose_blocks); break;
+    }
     if (dL_dpose) k_pose_finish<<<bp.n_views * 6, 32, 0, s>>>(ws.partials, pose_blocks, bp.n_views, dL_dpose);
     pf.end(pi, s);
     return cudaGetLastError();
@@ -600,7 +702,12 @@ cudaError_t launch_pose_tangents(const BatchParam& bp, const GaussPtrs& g, const
     if (bp.max_count <= 0) return cudaSuccess;
     dim3 grid((unsigned)((bp.max_count + 255) / 256), (unsigned)bp.n_views);
     const int pi = pf.begin(GS_KF_POSE_NORMAL, s);
-    k_pose_tangents<<<grid, 256, 0, s>>>(bp, g, rc, ws, tangents);
+    switch (g.sh_degree) {
+        case 0: k_pose_tangents<0><<<grid, 256, 0, s>>>(bp, g, rc, ws, tangents); break;
+        case 1: k_pose_tangents<1><<<grid, 256, 0, s>>>(bp, g, rc, ws, tangents); break;
+        case 2: k_pose_tangents<2><<<grid, 256, 0, s>>>(bp, g, rc, ws, tangents); break;
+        default: k_pose_tangents<3><<<grid, 256, 0, s>>>(bp, g, rc, ws, tangents); break;
+    }
     pf.end(pi, s);
     return cudaGetLastError();
 }

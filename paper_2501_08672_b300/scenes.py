@@ -144,7 +144,8 @@ def box_room_scene(n=200_000, seed=0, sh_degree=1, scale=1.0, slice_log_scale=ma
     points uniform by area, offset along the normal by N(0, 2 cm), rotation
     from the surface normal, tangential log-scales ~ N(-3, 0.5), normal-axis
     scale 1 mm (the slice axis), degree-0 colour from a procedural texture,
-    degree-1 coefficients ~ N(0, 0.1), opacity logit ~ N(0, 1)."""
+    coefficients of degree 1 to sh_degree (<= 3) ~ N(0, 0.1), opacity logit
+    ~ N(0, 1)."""
     rng = _rng(seed)
     rects = _box_room_surfaces(scale)
     areas = np.array([np.linalg.norm(np.cross(u, v)) for _, u, v, _ in rects])

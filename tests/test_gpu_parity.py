@@ -392,6 +392,29 @@ def test_box_room_window_degree1(orc):
     compare_grads(win, g, border, pose=r.dL_dpose.view(-1, 6).cpu().numpy().astype(np.float64), orc_pose=pose)
 
 
+@pytest.mark.parametrize("sh_degree", [2, 3])
+def test_box_room_window_higher_sh(orc, sh_degree):
+    """The same window at SH degree 2 and 3 (higher coefficients ~ N(0, 0.1)):
+    forward images, Gaussian gradients including every SH coefficient, and
+    the pose gradient (the colour moves with the camera centre)."""
+    n = 20_000
+    p = scenes.box_room_scene(n, seed=17 + sh_degree, sh_degree=sh_degree)
+    views = scenes.arc_views(3, 192, 160, 180.0, n_gaussians=n)
+    win, r = gpu_forward(p, views)
+    tg = l1_target(p, views)
+    for v, img, T in zip(views, r.images(), B.unpack_images(r.T, views, 1)):
+        compare_images(orc.render_view(p, v), img.cpu().numpy(), T.cpu().numpy())
+    gpu_loss_backward(win, r, tg)
+    L, g, pose, border, _ = oracle_l1_backward(orc, p, views, tg, r)
+    compare_grads(win, g, border, pose=r.dL_dpose.view(-1, 6).cpu().numpy().astype(np.float64), orc_pose=pose)
+    # the highest-degree block on its own (not drowned by k0 in the group norm)
+    ok = ~border
+    K = (sh_degree + 1) ** 2
+    lo = sh_degree * sh_degree
+    a = win.grad("sh").detach().cpu().numpy().astype(np.float64)[ok][:, lo:K]
+    assert rel_l2(a.reshape(-1), g["sh"][ok][:, lo:K].reshape(-1)) <= GRAD_TOL
+
+
 def test_uneven_gaussian_ranges(orc):
     """Each view renders its own contiguous range of the window."""
     n = 6000

@@ -51,7 +51,7 @@ def gpu_pose_normal(p, views, target, tile_size, **cfg):
     return r, normal, H.view(-1, 3, 6).double().cpu().numpy()
 
 
-@pytest.mark.parametrize("ts,sh_degree", [(16, 0), (8, 1), (16, 1)])
+@pytest.mark.parametrize("ts,sh_degree", [(16, 0), (8, 1), (16, 1), (16, 2), (16, 3)])
 def test_pose_normal_full_images_match_oracle(orc, ts, sh_degree):
     """Two ragged views of a 20k-Gaussian room, every pixel: per-pixel H
     against the oracle, and the per-view normal equations."""

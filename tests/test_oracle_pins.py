@@ -159,6 +159,73 @@ def test_degree_one_colour_is_real_sh(orc):
         np.testing.assert_allclose(pr["raw_colour"][0], expect, rtol=1e-12, atol=1e-13)
 
 
+def _real_sh_from_scipy(d, lmax=3):
+    """Real harmonics with the Condon-Shortley phase, k = l^2 + l + m, from
+    scipy's complex Y_l^m (which carry the phase): sqrt(2) Im Y_l^|m| for
+    m < 0, Y_l^0, sqrt(2) Re Y_l^m for m > 0."""
+    theta = math.acos(max(-1.0, min(1.0, d[2])))
+    phi = math.atan2(d[1], d[0])
+    out = []
+    for l in range(lmax + 1):
+        for m in range(-l, l + 1):
+            y = scipy.special.sph_harm_y(l, abs(m), theta, phi)
+            out.append(math.sqrt(2) * y.imag if m < 0 else (y.real if m == 0 else math.sqrt(2) * y.real))
+    return np.array(out)
+
+
+def test_sh_basis_is_scipy_real_sh(orc):
+    """Degrees 0-3: the oracle's basis equals the real harmonics built from
+    scipy's complex ones (the degree-1 reading extended), and the basis of a
+    lower degree is its prefix."""
+    rng = np.random.default_rng(8)
+    d = rng.standard_normal((40, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    Y, _ = orc.sh_basis(d, 3)
+    for i in range(len(d)):
+        np.testing.assert_allclose(Y[i], _real_sh_from_scipy(d[i]), rtol=1e-12, atol=1e-14)
+    for deg in range(3):
+        Yd, _ = orc.sh_basis(d, deg)
+        K = (deg + 1) ** 2
+        np.testing.assert_array_equal(Yd[:, :K], Y[:, :K])
+        assert np.all(Yd[:, K:] == 0)
+
+
+@pytest.mark.parametrize("l", [1, 2, 3])
+def test_sh_addition_theorem(orc, l):
+    """sum_m Y_lm(a) Y_lm(b) = (2l+1)/(4 pi) P_l(a.b) (textbook Legendre
+    polynomials): any wrong constant, sign mix-up inside a product or missing
+    term of degree l breaks it."""
+    P = {1: lambda t: t, 2: lambda t: 1.5 * t * t - 0.5, 3: lambda t: 2.5 * t ** 3 - 1.5 * t}[l]
+    rng = np.random.default_rng(9 + l)
+    a = rng.standard_normal((50, 3))
+    b = rng.standard_normal((50, 3))
+    a /= np.linalg.norm(a, axis=1, keepdims=True)
+    b /= np.linalg.norm(b, axis=1, keepdims=True)
+    Ya, _ = orc.sh_basis(a, 3)
+    Yb, _ = orc.sh_basis(b, 3)
+    blk = slice(l * l, (l + 1) ** 2)
+    lhs = (Ya[:, blk] * Yb[:, blk]).sum(1)
+    rhs = (2 * l + 1) / (4 * math.pi) * P((a * b).sum(1))
+    np.testing.assert_allclose(lhs, rhs, rtol=1e-12, atol=1e-14)
+
+
+def test_sh_basis_derivatives_match_differences(orc):
+    """dY: the partial derivatives of the homogeneous polynomials, against
+    central differences off the sphere (the polynomials are evaluated as
+    written, without renormalising the direction)."""
+    rng = np.random.default_rng(10)
+    d = rng.standard_normal((20, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    _, dY = orc.sh_basis(d, 3)
+    h = 1e-6
+    for c in range(3):
+        e = np.zeros(3)
+        e[c] = h
+        Yp, _ = orc.sh_basis(d + e, 3)
+        Ym, _ = orc.sh_basis(d - e, 3)
+        np.testing.assert_allclose((Yp - Ym) / (2 * h), dY[:, :, c], rtol=1e-6, atol=1e-8)
+
+
 # ---------------------------------------------------------------- compositing
 
 def test_single_isotropic_gaussian_closed_form(orc):
@@ -281,7 +348,7 @@ def _loss(orc, p, views, w, cfg):
     return sum(float(np.sum(o["rgb"] * wi)) for o, wi in zip(outs, w))
 
 
-@pytest.mark.parametrize("sh_degree", [0, 1])
+@pytest.mark.parametrize("sh_degree", [0, 1, 2, 3])
 def test_gaussian_gradients_match_central_differences(orc, sh_degree):
     """Exact mode, smooth loss L = sum w * I: analytic backward vs central
     differences for every parameter of every Gaussian, two views."""
@@ -447,7 +514,7 @@ def test_pixel_list_paths_agree_with_full_image(orc):
 
 # ---- pose Jacobian and normal equations (Sec. II-D, Eq. minimization) ----
 
-@pytest.mark.parametrize("sh_degree", [0, 1])
+@pytest.mark.parametrize("sh_degree", [0, 1, 2, 3])
 def test_pose_jacobian_matches_central_differences(orc, sh_degree):
     """Per-pixel dI/dxi by forward mode against central differences of the
     rendered image through scipy's matrix exponential, T_CW <- Exp(xi) T_CW,
