@@ -22,6 +22,13 @@ Functions, with the passage each restates:
                  swapping survivors from the rear into the holes
   sh0_bilinear   Sec. II-B.2: SH0 initialisation from the bilinear colour of
                  the image at the projected mean
+  sh_basis       the real spherical harmonics of degree <= 3 the colour uses
+  ssim_map,      the photometric loss with a structural term, (1 - lambda) L1
+  dssim_loss_grad  + lambda (1 - SSIM), SSIM of Wang et al. (2004) with an
+                 11 x 11 Gaussian window (sigma 1.5), zero padding,
+                 C1 = 0.01^2, C2 = 0.03^2 (the paper names only the L1 norm
+                 of Eq. gaussian_optimization; this is the common 3D-GS
+                 variant)
 """
 from __future__ import annotations
 
@@ -173,6 +180,84 @@ def l1_loss_grad(rgbs, targets):
         d = np.asarray(r, np.float64) - np.asarray(t, np.float64)
         L += np.abs(d).mean() / V
         grads.append(np.sign(d) / (d.size * V))
+    return L, grads
+
+
+SSIM_C1 = 0.01 ** 2
+SSIM_C2 = 0.03 ** 2
+
+
+def ssim_window(size=11, sigma=1.5):
+    """Normalised 1D Gaussian taps g[k] ~ exp(-(k - size//2)^2 / (2 sigma^2));
+    the 2D window is the outer product g g^T."""
+    k = np.arange(size) - size // 2
+    g = np.exp(-(k * k) / (2.0 * sigma * sigma))
+    return g / g.sum()
+
+
+def _window_mean(img, g):
+    """Windowed mean of a [H, W] plane: sum_{a,b} g[a] g[b] img[y + a - r,
+    x + b - r] over the pixels inside the image (zero padding), the window
+    centred on each pixel.  scipy's correlate serves as the step."""
+    import scipy.ndimage
+    return scipy.ndimage.correlate(img, np.outer(g, g), mode="constant", cval=0.0)
+
+
+def ssim_map(x, y, size=11, sigma=1.5):
+    """Per-pixel SSIM of [C, H, W] images x (rendered) and y (target):
+    ((2 mu_x mu_y + C1)(2 s_xy + C2)) / ((mu_x^2 + mu_y^2 + C1)(s_x^2 + s_y^2 + C2))
+    with mu, s^2, s_xy the windowed means, variances E[x^2] - mu^2 and
+    covariance E[xy] - mu_x mu_y, per channel."""
+    g = ssim_window(size, sigma)
+    x = np.asarray(x, np.float64)
+    y = np.asarray(y, np.float64)
+    out = np.empty_like(x)
+    for c in range(x.shape[0]):
+        mx, my = _window_mean(x[c], g), _window_mean(y[c], g)
+        sxx = _window_mean(x[c] * x[c], g) - mx * mx
+        syy = _window_mean(y[c] * y[c], g) - my * my
+        sxy = _window_mean(x[c] * y[c], g) - mx * my
+        out[c] = ((2 * mx * my + SSIM_C1) * (2 * sxy + SSIM_C2)) / \
+                 ((mx * mx + my * my + SSIM_C1) * (sxx + syy + SSIM_C2))
+    return out
+
+
+def dssim_loss_grad(rgbs, targets, lam=0.2, size=11, sigma=1.5):
+    """L = (1/V) sum_v [(1 - lam) mean |x - y| + lam (1 - mean SSIM(x, y))] over
+    views v with x the rendered image [3, H, W] and y the target; returns L
+    and dL/dx per view.  The SSIM term's gradient: with s the SSIM map and
+    the window means mu_x = G * x, E_xx = G * x^2, E_xy = G * (x y),
+    ds(q)/dx(p) = G(q - p) [ds/dmu_x + 2 x(p) ds/dE_xx + y(p) ds/dE_xy](q),
+    and the window G is symmetric, so the sum over q is again a windowed mean
+    of the three partial-derivative maps."""
+    g = ssim_window(size, sigma)
+    V = len(rgbs)
+    L = 0.0
+    grads = []
+    for xr, yr in zip(rgbs, targets):
+        x = np.asarray(xr, np.float64)
+        y = np.asarray(yr, np.float64)
+        n = x.size
+        d = x - y
+        grad = (1.0 - lam) * np.sign(d) / (n * V)
+        smean = 0.0
+        for c in range(x.shape[0]):
+            mx, my = _window_mean(x[c], g), _window_mean(y[c], g)
+            exx, eyy, exy = _window_mean(x[c] * x[c], g), _window_mean(y[c] * y[c], g), _window_mean(x[c] * y[c], g)
+            a1 = 2 * mx * my + SSIM_C1
+            a2 = 2 * (exy - mx * my) + SSIM_C2
+            b1 = mx * mx + my * my + SSIM_C1
+            b2 = (exx - mx * mx) + (eyy - my * my) + SSIM_C2
+            s = a1 * a2 / (b1 * b2)
+            smean += s.sum()
+            # partial derivatives of s with respect to mu_x, E_xx, E_xy
+            d_mx = (2 * my * a2 - 2 * my * a1) / (b1 * b2) - s * (2 * mx / b1 - 2 * mx / b2)
+            d_exx = -s / b2
+            d_exy = 2 * a1 / (b1 * b2)
+            ds_dx = _window_mean(d_mx, g) + 2 * x[c] * _window_mean(d_exx, g) + y[c] * _window_mean(d_exy, g)
+            grad[c] -= lam * ds_dx / (n * V)
+        L += ((1.0 - lam) * np.abs(d).mean() + lam * (1.0 - smean / n)) / V
+        grads.append(grad)
     return L, grads
 
 

@@ -643,3 +643,101 @@ def test_sh0_bilinear_pins(orc):
     np.testing.assert_allclose(got, ref, atol=1e-12)
     far = np.array([[10.0, 0.0, z], [0.0, 0.0, -1.0]])
     np.testing.assert_array_equal(orc.sh0_bilinear(far, view, img, 0)[:, 0], 0.0)
+
+
+# ---------------------------------------------------------------- D-SSIM term
+
+def _ssim_brute(x, y, size=11, sigma=1.5, C1=1e-4, C2=9e-4):
+    """SSIM map by explicit loops: at each pixel the Gaussian-weighted means,
+    variances and covariance over the window's pixels inside the image (the
+    outside counts as zeros, its weight still in the normalisation)."""
+    r = size // 2
+    k = np.arange(size) - r
+    g = np.exp(-k * k / (2 * sigma * sigma))
+    w = np.outer(g, g) / np.outer(g, g).sum()
+    C, H, W = x.shape
+    out = np.zeros((C, H, W))
+    for c in range(C):
+        for i in range(H):
+            for j in range(W):
+                m = {"x": 0.0, "y": 0.0, "xx": 0.0, "yy": 0.0, "xy": 0.0}
+                for a in range(size):
+                    for b in range(size):
+                        ii, jj = i + a - r, j + b - r
+                        if 0 <= ii < H and 0 <= jj < W:
+                            u, v = x[c, ii, jj], y[c, ii, jj]
+                            m["x"] += w[a, b] * u
+                            m["y"] += w[a, b] * v
+                            m["xx"] += w[a, b] * u * u
+                            m["yy"] += w[a, b] * v * v
+                            m["xy"] += w[a, b] * u * v
+                sx = m["xx"] - m["x"] ** 2
+                sy = m["yy"] - m["y"] ** 2
+                sxy = m["xy"] - m["x"] * m["y"]
+                out[c, i, j] = ((2 * m["x"] * m["y"] + C1) * (2 * sxy + C2)) / \
+                               ((m["x"] ** 2 + m["y"] ** 2 + C1) * (sx + sy + C2))
+    return out
+
+
+def test_ssim_map_brute_force(orc):
+    rng = np.random.default_rng(12)
+    x = rng.uniform(0, 1, (2, 9, 13))
+    y = np.clip(x + rng.normal(0, 0.2, x.shape), 0, 1)
+    np.testing.assert_allclose(orc.ssim_map(x, y), _ssim_brute(x, y), rtol=1e-12, atol=1e-13)
+
+
+def test_ssim_window_taps(orc):
+    g = orc.ssim_window()
+    assert g.size == 11 and abs(g.sum() - 1.0) < 1e-15
+    np.testing.assert_allclose(g, g[::-1], rtol=0, atol=0)
+    k = np.arange(10) - 5
+    np.testing.assert_allclose(g[1:] / g[:-1], np.exp(-(2 * k + 1) / (2 * 1.5 ** 2)), rtol=1e-13)
+
+
+def test_ssim_constant_images_interior_closed_form(orc):
+    """Constant planes a and b: away from the border (window inside the
+    image) the variances vanish and s = (2ab + C1) / (a^2 + b^2 + C1)."""
+    a, b = 0.7, 0.25
+    x = np.full((1, 24, 24), a)
+    y = np.full((1, 24, 24), b)
+    s = orc.ssim_map(x, y)
+    np.testing.assert_allclose(s[0, 5:19, 5:19], (2 * a * b + 1e-4) / (a * a + b * b + 1e-4), rtol=1e-12)
+
+
+def test_dssim_identical_images_is_stationary(orc):
+    """x = y: every s(q) is at its maximum 1, so the SSIM term and its gradient
+    vanish (and sign(0) = 0 for the L1 part)."""
+    rng = np.random.default_rng(13)
+    x = rng.uniform(0, 1, (3, 16, 12))
+    L, g = orc.dssim_loss_grad([x], [x], lam=1.0)
+    assert abs(L) < 1e-14
+    assert np.abs(g[0]).max() < 1e-12
+
+
+def test_dssim_lambda_zero_is_l1(orc):
+    rng = np.random.default_rng(14)
+    xs = [rng.uniform(0, 1, (3, 10, 14)), rng.uniform(0, 1, (3, 7, 9))]
+    ys = [rng.uniform(0, 1, x.shape) for x in xs]
+    L, g = orc.dssim_loss_grad(xs, ys, lam=0.0)
+    L1, g1 = orc.l1_loss_grad(xs, ys)
+    assert abs(L - L1) < 1e-15
+    for a, b in zip(g, g1):
+        np.testing.assert_array_equal(a, b)
+
+
+def test_dssim_gradient_matches_differences(orc):
+    """Central differences of the loss at interior, edge and corner pixels of
+    two views of different sizes."""
+    rng = np.random.default_rng(15)
+    xs = [rng.uniform(0.05, 0.95, (3, 14, 19)), rng.uniform(0.05, 0.95, (3, 11, 8))]
+    ys = [np.clip(x + rng.normal(0, 0.15, x.shape), 0, 1) for x in xs]
+    lam = 0.2
+    _, g = orc.dssim_loss_grad(xs, ys, lam)
+    h = 1e-6
+    for v, idx in [(0, (0, 0, 0)), (0, (1, 7, 9)), (0, (2, 13, 18)), (1, (0, 0, 4)), (1, (2, 10, 7)), (1, (1, 5, 5))]:
+        xp = [x.copy() for x in xs]
+        xm = [x.copy() for x in xs]
+        xp[v][idx] += h
+        xm[v][idx] -= h
+        fd = (orc.dssim_loss_grad(xp, ys, lam)[0] - orc.dssim_loss_grad(xm, ys, lam)[0]) / (2 * h)
+        assert abs(fd - g[v][idx]) <= 1e-6 * abs(g[v][idx]) + 1e-11, (v, idx, fd, g[v][idx])
