@@ -85,6 +85,8 @@ def parse():
     ap.add_argument("--tile-size", type=int, default=0, help="0: autotune tile size, pixels per thread, batch")
     ap.add_argument("--ppt", type=int, default=0)
     ap.add_argument("--batch", type=int, default=0)
+    ap.add_argument("--ssim-lambda", type=float, default=0.0,
+                    help="weight of the D-SSIM term in the photometric loss (0: the L1 loss of the paper)")
     return ap.parse_args()
 
 
@@ -305,6 +307,7 @@ def run_b300(args, world, rank, local):
     else:
         shape, tune_table = autotune(params, views, target, steps=3, device=local, storage=storage)
     opt = WindowOptimizer(params, views, target, lr=LR, device=local, tile_size=shape[0],
+                          ssim_lambda=args.ssim_lambda,
                           pixels_per_thread=shape[1], batch=shape[2], storage=storage)
     ctx = opt.r.ctx
     opt.step(count=True)  # sizes the pair workspace
@@ -465,7 +468,8 @@ def run_b300(args, world, rank, local):
     d2h = back_params.numel() * 4 + 4
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "window":
+    if (rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "window"
+            and args.ssim_lambda == 0):
         sec, threads, desc = cpu_oracle_iteration(params, views, args.cpu_pixels)
         cpu = {"value": 1.0 / sec, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc}
 
@@ -479,6 +483,8 @@ def run_b300(args, world, rank, local):
                                      else [[int(v["W"]), int(v["H"])] for v in views]),
                            "tile_size": shape[0], "pixels_per_thread": shape[1],
                            "batch": shape[2], "sh_degree": int(params["sh_degree"]), "lr": LR,
+                           "loss": ("L1" if args.ssim_lambda == 0 else
+                                    "(1 - %g) L1 + %g (1 - SSIM), 11x11 window" % (args.ssim_lambda, args.ssim_lambda)),
                            "storage": ({k: str(v).replace("torch.", "") for k, v in storage.items()} if storage
                                        else "float32"),
                            "autotune_ms": ({"%d/%d/%d" % k: round(v, 4) for k, v in tune_table.items()}

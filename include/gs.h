@@ -237,6 +237,26 @@ GS_API int gs_render_fwd(gs_ctx* ctx, const gs_view* views, int n_views, const g
                   float* rgb, float* T_final, uint32_t* n_contrib, uint32_t* n_used,
                   gs_stream stream);
 
+/* Device floats of scratch gs_dssim_loss needs for these views: 9 per pixel
+ * (three SSIM derivative maps per channel) plus one per 32 x 16 tile of each
+ * channel; 0 if the views are invalid. */
+GS_API size_t gs_dssim_scratch_floats(const gs_view* views, int n_views);
+
+/* Photometric loss with a structural term (the paper's Eq.
+ * gaussian_optimization uses the L1 norm; this is the D-SSIM variant common
+ * in 3D-GS training):
+ *   L = (1/V) sum_v [(1 - lambda) mean_{3 H_v W_v} |x - y| + lambda (1 - mean SSIM(x, y))]
+ * with x = rgb, y = target (both packed over views like gs_render_fwd's
+ * output), SSIM per channel with an 11 x 11 Gaussian window (sigma 1.5), zero
+ * padding, C1 = 0.01^2, C2 = 0.03^2:
+ *   SSIM = (2 mu_x mu_y + C1)(2 s_xy + C2) / ((mu_x^2 + mu_y^2 + C1)(s_x^2 + s_y^2 + C2)).
+ * Writes L to loss_dev[0] (may be NULL) and dL/drgb to dL_drgb.  lambda in
+ * [0, 1]; lambda = 0 is gs_l1_loss.  scratch: device, caller-owned,
+ * gs_dssim_scratch_floats(views, n_views) floats, 16-byte aligned.
+ * Errors: GS_ERR_INVALID_ARG, GS_ERR_CUDA. */
+GS_API int gs_dssim_loss(gs_ctx* ctx, const gs_view* views, int n_views, const float* rgb, const float* target,
+                         float lambda, float* scratch, float* dL_drgb, float* loss_dev, gs_stream stream);
+
 /* a4: photometric loss (Eq. gaussian_optimization, L1 norm):
  * L = (1/V) sum_v mean_{3 H_v W_v} |rgb - target| written to loss_dev[0], and
  * dL/drgb = sign(rgb - target) / (3 H_v W_v V) written to dL_drgb (sign(0) = 0).
@@ -337,7 +357,8 @@ typedef enum gs_kernel_family {
     GS_KF_ADAM = 10,       /* a8 Adam */
     GS_KF_POSE_NORMAL = 11, /* pose tangents, forward-mode compositing, normal equations */
     GS_KF_WINDOW = 12,      /* sliding-window maintenance and SH0 initialisation */
-    GS_KF_COUNT = 13
+    GS_KF_SSIM = 13,        /* photometric loss with the D-SSIM term */
+    GS_KF_COUNT = 14
 } gs_kernel_family;
 
 typedef struct gs_profile_entry {

@@ -35,10 +35,10 @@ EXPORTED = ["gs_config_default", "gs_version", "gs_context_create", "gs_context_
             "gs_profile_enable", "gs_profile_collect", "gs_launch_count", "gs_adam_step_dev",
             "gs_l1_loss_noalloc", "gs_calibrate_alu", "gs_pose_normal_scratch", "gs_pose_normal",
             "gs_window_scratch_bytes", "gs_window_compact", "gs_window_gather", "gs_window_clear",
-            "gs_sh_init_bilinear"]
+            "gs_sh_init_bilinear", "gs_dssim_scratch_floats", "gs_dssim_loss"]
 
 KERNEL_FAMILIES = ["project", "depth_sort", "tile_scan", "emit", "tile_sort", "ranges", "raster_fwd", "l1",
-                   "raster_bwd", "project_bwd", "adam", "pose_normal", "window"]
+                   "raster_bwd", "project_bwd", "adam", "pose_normal", "window", "ssim"]
 
 
 class WindowColumn(ctypes.Structure):
@@ -133,6 +133,9 @@ def lib():
         L.gs_adam_step_dev.argtypes = [P, P, P, P, P, I64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                        ctypes.c_float, P, ctypes.POINTER(LowpSegment), I, P]
         L.gs_sync_status.argtypes = [P, P, ctypes.POINTER(ctypes.c_uint64)]
+        L.gs_dssim_scratch_floats.argtypes = [ctypes.POINTER(View), I]
+        L.gs_dssim_scratch_floats.restype = ctypes.c_size_t
+        L.gs_dssim_loss.argtypes = [P, ctypes.POINTER(View), I, P, P, ctypes.c_float, P, P, P, P]
         L.gs_l1_loss_noalloc.argtypes = [ctypes.POINTER(View), I, P, P, P, P, P, ctypes.c_char_p, ctypes.c_size_t]
         L.gs_profile_enable.argtypes = [P, ctypes.c_uint32]
         L.gs_profile_collect.argtypes = [P, P, ctypes.POINTER(ProfileEntry), I, ctypes.POINTER(ctypes.c_int)]
@@ -290,6 +293,13 @@ class Context:
     def l1_loss(self, views, ws, rgb, target, dL_drgb, loss=None, stream=None):
         self._ck(lib().gs_l1_loss(self.h, views, len(views), ctypes.byref(ws), _ptr(rgb), _ptr(target),
                                   _ptr(dL_drgb), _ptr(loss), _stream(stream)))
+
+    def dssim_loss(self, views, rgb, target, lam, scratch, dL_drgb, loss=None, stream=None):
+        """(1 - lam) L1 + lam (1 - SSIM) and its gradient; scratch: FP32 device
+        tensor of dssim_scratch_floats(views) elements."""
+        _check_dev(scratch, "scratch", torch.float32, int(lib().gs_dssim_scratch_floats(views, len(views))))
+        self._ck(lib().gs_dssim_loss(self.h, views, len(views), _ptr(rgb), _ptr(target), float(lam), _ptr(scratch),
+                                     _ptr(dL_drgb), _ptr(loss), _stream(stream)))
 
     def render_bwd(self, g, views, ws, T_final, n_contrib, dL_drgb, grads=None, dL_dpose=None, stream=None):
         gr = None

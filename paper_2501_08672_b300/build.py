@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libgs_b300.so")
 SOURCES = ["gs_capi.cu", "gs_project.cu", "gs_sort.cu", "gs_raster.cu", "gs_adam.cu", "gs_calib.cu",
-           "gs_window.cu"]
+           "gs_window.cu", "gs_ssim.cu"]
 HEADERS = ["gs_internal.cuh", os.path.join("..", "..", "include", "gs.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")

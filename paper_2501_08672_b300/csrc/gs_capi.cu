@@ -578,6 +578,54 @@ int gs_l1_loss_noalloc(const gs_view* views, int n_views, const float* rgb, cons
     return GS_OK;
 }
 
+namespace {
+bool image_views_ok(const gs_view* views, int n_views) {
+    if (!views || n_views < 1 || n_views > GS_MAX_VIEWS) return false;
+    for (int v = 0; v < n_views; ++v)
+        if (views[v].width <= 0 || views[v].height <= 0 || views[v].width > 32768 || views[v].height > 32768)
+            return false;
+    return true;
+}
+}  // namespace
+
+size_t gs_dssim_scratch_floats(const gs_view* views, int n_views) {
+    if (!image_views_ok(views, n_views)) return 0;
+    gs_config cfg;
+    gs_config_default(&cfg);
+    BatchParam bp;
+    make_batch(cfg, views, n_views, bp);
+    return ssim_scratch_floats(bp);
+}
+
+int gs_dssim_loss(gs_ctx* ctx, const gs_view* views, int n_views, const float* rgb, const float* target,
+                  float lambda, float* scratch, float* dL_drgb, float* loss_dev, gs_stream stream) {
+    if (!ctx) return GS_ERR_INVALID_ARG;
+    if (!rgb || !target || !dL_drgb || !scratch)
+        return fail(ctx, GS_ERR_INVALID_ARG, "an image or scratch pointer is NULL");
+    if (!image_views_ok(views, n_views))
+        return fail(ctx, GS_ERR_INVALID_ARG, "views NULL, n_views=%d outside [1, %d] or a size outside [1, 32768]",
+                    n_views, GS_MAX_VIEWS);
+    if (!(lambda >= 0.f && lambda <= 1.f)) return fail(ctx, GS_ERR_INVALID_ARG, "lambda=%g outside [0, 1]", lambda);
+    if (reinterpret_cast<uintptr_t>(scratch) % 16) return fail(ctx, GS_ERR_INVALID_ARG, "scratch is not 16-byte aligned");
+    DeviceGuard dg(ctx->device);
+    BatchParam bp;
+    make_batch(ctx->cfg, views, n_views, bp);
+    SsimParam sp;
+    double g[2 * kSsimRadius + 1], sum = 0.0;
+    for (int k = 0; k <= 2 * kSsimRadius; ++k) {
+        const double d = (double)(k - kSsimRadius);
+        g[k] = exp(-d * d / (2.0 * 1.5 * 1.5));
+        sum += g[k];
+    }
+    for (int k = 0; k <= 2 * kSsimRadius; ++k) sp.g[k] = (float)(g[k] / sum);
+    sp.C1 = 0.01f * 0.01f;
+    sp.C2 = 0.03f * 0.03f;
+    sp.lambda = lambda;
+    const cudaError_t e = launch_ssim(bp, sp, rgb, target, scratch, dL_drgb, loss_dev,
+                                      reinterpret_cast<cudaStream_t>(stream), ctx->prof);
+    return e == cudaSuccess ? GS_OK : cuda_fail(ctx, e, "gs_dssim_loss");
+}
+
 int gs_render_bwd(gs_ctx* ctx, const gs_gaussians* g, const gs_view* views, int n_views, const gs_workspace* ws,
                   const float* T_final, const uint32_t* n_contrib, const float* dL_drgb, const gs_grads* grads,
                   float* dL_dpose_dev, gs_stream stream) {

@@ -13,6 +13,7 @@ namespace gsb {
 constexpr int kMaxViews = GS_MAX_VIEWS;
 constexpr int kRecFloats = 12;   // projected record: 3 x float4
 constexpr int kGrad2D = 9;       // per-record 2D gradient
+constexpr int kSsimRadius = 5;    // 11-tap SSIM window
 constexpr int kPoseTan4 = 12;     // per-record pose tangents: 12 x float4 (see k_pose_tangents)
 constexpr int kNormalVals = 28;   // per-view normal equations: 21 + 6 + 1
 constexpr float kLog2e = 1.4426950408889634f;
@@ -43,6 +44,13 @@ struct BatchParam {
     int ppt;             // pixels per thread of the raster kernels
     int batch;           // records staged per shared-memory batch
     ViewParam v[kMaxViews];
+};
+
+// SSIM window taps (normalised Gaussian, sigma 1.5), constants and the
+// weight of the structural term.
+struct SsimParam {
+    float g[2 * kSsimRadius + 1];
+    float C1, C2, lambda;
 };
 
 struct RenderConst {
@@ -249,6 +257,9 @@ cudaError_t launch_bin(const BatchParam& bp, WsPtrs& ws, unsigned int* status,
                        unsigned long long* status_pairs, cudaStream_t s, Prof& pf);
 bool raster_variant_exists(int ts, int ppt, int batch);
 cudaError_t measure_alu(int sm_count, float* sink, cudaStream_t s, double* ffma_tflops, double* ex2_gops);
+size_t ssim_scratch_floats(const BatchParam& bp);
+cudaError_t launch_ssim(const BatchParam& bp, const SsimParam& sp, const float* rgb, const float* target,
+                        float* scratch, float* dL_drgb, float* loss, cudaStream_t s, Prof& pf);
 int window_max_columns();
 size_t window_scratch_bytes(long long n);
 cudaError_t launch_window_compact(const gs_window_column* cols, int n_cols, long long n, const uint8_t* keep,

@@ -87,6 +87,20 @@ class Renderer:
     def l1(self, target):
         self.ctx.l1_loss(self.views, self.ws_struct, self.rgb, target, self.dL_drgb, self.loss)
 
+    def dssim(self, target, lam=0.2):
+        """(1 - lam) L1 + lam (1 - SSIM) of the last forward against target,
+        into self.loss and self.dL_drgb."""
+        n = int(B.lib().gs_dssim_scratch_floats(self.views, len(self.views)))
+        if getattr(self, "_ssim_scratch", None) is None or self._ssim_scratch.numel() != n:
+            self._ssim_scratch = torch.empty(n, dtype=torch.float32, device=self.rgb.device)
+        self.ctx.dssim_loss(self.views, self.rgb, target, lam, self._ssim_scratch, self.dL_drgb, self.loss)
+
+    def loss_and_grad(self, target, ssim_lambda=0.0):
+        if ssim_lambda > 0.0:
+            self.dssim(target, ssim_lambda)
+        else:
+            self.l1(target)
+
     def backward(self, g, dL_drgb, grads=None, want_pose=False):
         self.ctx.render_bwd(g, self.views, self.ws_struct, self.T, self.n_contrib, dL_drgb, grads,
                             self.dL_dpose if want_pose else None)
@@ -271,13 +285,15 @@ class GaussianWindow:
 
 class WindowOptimizer:
     """One sliding-window optimisation iteration (Sec. II-B.2): render every
-    keyframe, L1 photometric loss, backward to the Gaussians, Adam."""
+    keyframe, photometric loss (L1; with ssim_lambda > 0 the D-SSIM variant
+    (1 - lambda) L1 + lambda (1 - SSIM)), backward to the Gaussians, Adam."""
 
     def __init__(self, params, views, targets, lr=1e-3, betas=(0.9, 0.999), eps=1e-8, device=0,
-                 tile_size=16, storage=None, **cfg):
+                 tile_size=16, storage=None, ssim_lambda=0.0, **cfg):
         self.win = GaussianWindow(params, device, storage)
         self.r = Renderer(views, device, tile_size, **cfg)
         self.targets = targets
+        self.ssim_lambda = float(ssim_lambda)
         self.lr, self.betas, self.eps = lr, betas, eps
         self._g = self.win.struct()
         self._grads = self.win.grad_tensors()
@@ -292,7 +308,7 @@ class WindowOptimizer:
             return self.replay()
         w, r = self.win, self.r
         r.forward(self._g, count=count)
-        r.l1(self.targets)
+        r.loss_and_grad(self.targets, self.ssim_lambda)
         r.backward(self._g, r.dL_drgb, grads=self._grads)
         w.step_count += 1
         r.ctx.adam_step(w.flat, w.gflat, w.m, w.v, self.lr, self.betas[0], self.betas[1], self.eps,
@@ -317,7 +333,7 @@ class WindowOptimizer:
                 # program frees meanwhile) does not invalidate it
                 with torch.cuda.graph(g, capture_error_mode="relaxed"):
                     r.forward(self._g, count=False)
-                    r.l1(self.targets)
+                    r.loss_and_grad(self.targets, self.ssim_lambda)
                     r.backward(self._g, r.dL_drgb, grads=self._grads)
                     r.ctx.adam_step_dev(w.flat, w.gflat, w.m, w.v, self.lr, self.betas[0], self.betas[1],
                                         self.eps, self.step_dev, self._segs)
