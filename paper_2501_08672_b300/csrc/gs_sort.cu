@@ -525,31 +525,59 @@ __global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ order
     const unsigned long long o0 = offsets[j];
     const unsigned long long oend = o0 + tt;
     const unsigned long long ucap = (unsigned long long)cap;
-    if (tt > 0 && area <= kMaskTiles) {
-        // the mask row by row (w bits per tile row), set bits in column order
-        uint64_t mk = hitmask[r];
-        const uint64_t rowbits = (1ull << w) - 1ull;
-        unsigned long long o = o0;
-        for (int ty = ty0; mk && o < oend; ++ty, mk >>= w) {
-            uint32_t rb = (uint32_t)(mk & rowbits);
-            const uint32_t rowkey = (uint32_t)rc.z + (uint32_t)ty * (uint32_t)rc.w + (uint32_t)tx0;
-            while (rb && o < oend) {
-                const int bit = __ffs(rb) - 1;
-                rb &= rb - 1;
-                if (o < ucap) {
-                    pkeys[o] = rowkey + (uint32_t)bit;
-                    pvals[o] = r;
+    const int lane = threadIdx.x & 31;
+    {
+        // Records of the mask path (rectangles of <= 32 tiles) are written by
+        // the warp together: the warp's records are consecutive in depth
+        // order, so their pairs fill one contiguous range, and lane l writes
+        // positions l, l + 32, ... of it.  The owner of a position is the
+        // last record whose first position is at or below it (binary search
+        // over the lanes' offsets), the tile its mask's j-th set bit, bits
+        // in row-major order of the rectangle.
+        const bool mp = tt > 0 && area <= kMaskTiles;
+        const unsigned long long wbase = __shfl_sync(0xffffffffu, o0, 0);  // lane 0 is live
+        const uint32_t rel = live ? (uint32_t)(o0 - wbase) : 0xFFFFFFFFu;
+        const uint32_t wtotal = __reduce_max_sync(0xffffffffu, live ? rel + tt : 0u);
+        const uint32_t mask = mp ? hitmask[r] : 0u;
+        const uint32_t key0 = (uint32_t)rc.z + (uint32_t)ty0 * (uint32_t)rc.w + (uint32_t)tx0;
+        // floor(b / w) = (b * ceil(2048 / w)) >> 11 for b < 32, w <= 32
+        const uint32_t info = mp ? ((uint32_t)w | ((2048u + (uint32_t)w - 1u) / (uint32_t)w) << 8 | 0x80000000u) : 0u;
+        for (uint32_t p0 = 0; p0 < wtotal; p0 += 32) {
+            const uint32_t pr = p0 + (uint32_t)lane;
+            int e = 0;
+#pragma unroll
+            for (int st = 16; st >= 1; st >>= 1) {
+                const uint32_t oc = __shfl_sync(0xffffffffu, rel, e + st);
+                if (oc <= pr) e += st;
+            }
+            const uint32_t ie = __shfl_sync(0xffffffffu, info, e);
+            const uint32_t me = __shfl_sync(0xffffffffu, mask, e);
+            const uint32_t ke = __shfl_sync(0xffffffffu, key0, e);
+            const uint32_t se = (uint32_t)__shfl_sync(0xffffffffu, rc.w, e);
+            const uint32_t re = __shfl_sync(0xffffffffu, r, e);
+            const uint32_t be = __shfl_sync(0xffffffffu, rel, e);
+            const unsigned long long q = wbase + pr;
+            if (pr < wtotal && (ie >> 31) && q < ucap) {
+                // the (pr - be)-th set bit of the mask (0 based), by halving
+                uint32_t jj = pr - be, m = me, bit = 0;
+#pragma unroll
+                for (int h = 16; h >= 1; h >>= 1) {
+                    const uint32_t c = __popc(m & ((1u << h) - 1u));
+                    if (jj >= c) {
+                        jj -= c;
+                        bit += (uint32_t)h;
+                        m >>= h;
+                    }
                 }
-                ++o;
+                const bool found = (m & 1u) && jj == 0;  // else the mask holds fewer bits than counted
+                const uint32_t we = ie & 0xFFu, mul = (ie >> 8) & 0xFFFu;
+                const uint32_t row = (bit * mul) >> 11;
+                pkeys[q] = found ? ke + row * se + (bit - row * we) : 0xFFFFFFFFu;
+                pvals[q] = re;
             }
         }
-        // never reached when both passes agree; keeps the pair list well formed
-        for (; o < oend; ++o)
-            if (o < ucap) {
-                pkeys[o] = 0xFFFFFFFFu;
-                pvals[o] = r;
-            }
-    } else if (tt > 0 && !coop) {
+    }
+    if (tt > 0 && !coop && area > kMaskTiles) {
         // exact mode (no test): every tile of a large rectangle
         unsigned long long o = o0;
         for (int ty = ty0; ty < ty1 && o < oend; ++ty)
@@ -561,7 +589,6 @@ __global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ order
     }
     FootRows fr{};
     if (coop) fr = make_footrows(rec[3 * r], rec[3 * r + 1], rec[3 * r + 1].z - log2_alpha_min);
-    const int lane = threadIdx.x & 31;
     for (unsigned big = __ballot_sync(0xffffffffu, coop); big; big &= big - 1) {
         const int src = __ffs(big) - 1;
         FootRows bf;
