@@ -654,26 +654,48 @@ __global__ void k_tile_keys(const uint2* __restrict__ ranges, int n_tiles, uint3
 }
 
 // Tile ranges over the sorted pair keys: a tile's list starts where its key
-// differs from the previous one and ends where it differs from the next
-// (neighbours by warp shuffles, one load per key).
+// differs from the previous one and ends where it differs from the next.
+// Each thread takes 4 consecutive keys in one 16-byte load (the key buffer is
+// 256-byte aligned); the neighbours across threads come by warp shuffles.
 __global__ void __launch_bounds__(256) k_ranges(const uint32_t* __restrict__ keys, long long cap,
                                                 const unsigned long long* __restrict__ n_dev, uint32_t n_tiles,
                                                 uint2* __restrict__ ranges) {
     const unsigned long long n = clamp_n((unsigned long long)cap, n_dev);
+    const unsigned long long n4 = (n + 3) / 4;
+    const uint4* __restrict__ k4 = reinterpret_cast<const uint4*>(keys);
     const int lane = threadIdx.x & 31;
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
     // every lane of a warp runs the same number of rounds (shuffles need all 32)
-    for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < n;
+    for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < n4;
          base += stride) {
-        const unsigned long long j = base + lane;
-        const uint32_t k = j < n ? keys[j] : 0xFFFFFFFFu;
-        uint32_t prev = __shfl_up_sync(0xffffffffu, k, 1);
-        uint32_t next = __shfl_down_sync(0xffffffffu, k, 1);
-        if (lane == 0) prev = j > 0 && j - 1 < n ? keys[j - 1] : 0xFFFFFFFFu;
-        if (lane == 31) next = j + 1 < n ? keys[j + 1] : 0xFFFFFFFFu;
-        if (j >= n || k >= n_tiles) continue;  // tile ids come from k_emit and are < n_tiles
-        if (j == 0 || prev != k) ranges[k].x = (uint32_t)j;
-        if (j + 1 == n || next != k) ranges[k].y = (uint32_t)(j + 1);
+        const unsigned long long g = base + lane;
+        const unsigned long long j0 = 4 * g;
+        uint32_t v[4] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
+        if (j0 + 3 < n) {
+            const uint4 q = k4[g];
+            v[0] = q.x;
+            v[1] = q.y;
+            v[2] = q.z;
+            v[3] = q.w;
+        } else {
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if (j0 + i < n) v[i] = keys[j0 + i];
+        }
+        uint32_t prev = __shfl_up_sync(0xffffffffu, v[3], 1);
+        uint32_t next = __shfl_down_sync(0xffffffffu, v[0], 1);
+        if (lane == 0) prev = j0 > 0 && j0 - 1 < n ? keys[j0 - 1] : 0xFFFFFFFFu;
+        if (lane == 31) next = j0 + 4 < n ? keys[j0 + 4] : 0xFFFFFFFFu;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const unsigned long long j = j0 + i;
+            const uint32_t k = v[i];
+            if (j >= n || k >= n_tiles) continue;  // tile ids come from k_emit and are < n_tiles
+            const uint32_t p = i > 0 ? v[i - 1] : prev;
+            const uint32_t x = i < 3 ? v[i + 1] : next;
+            if (j == 0 || p != k) ranges[k].x = (uint32_t)j;
+            if (j + 1 == n || x != k) ranges[k].y = (uint32_t)(j + 1);
+        }
     }
 }
 
