@@ -85,6 +85,8 @@ def parse():
     ap.add_argument("--tile-size", type=int, default=0, help="0: autotune tile size, pixels per thread, batch")
     ap.add_argument("--ppt", type=int, default=0)
     ap.add_argument("--batch", type=int, default=0)
+    ap.add_argument("--maint-n", default="",
+                    help="maintenance workload: comma-separated window sizes (default: the full sweep)")
     ap.add_argument("--ssim-lambda", type=float, default=0.0,
                     help="weight of the D-SSIM term in the photometric loss (0: the L1 loss of the paper)")
     return ap.parse_args()
@@ -689,7 +691,8 @@ def run_maintenance(args, world, rank, local):
             ts.append(a.elapsed_time(b))
         return float(np.median(ts))
 
-    for N in MAINT_SIZES:
+    sizes = [int(x) for x in args.maint_n.split(",") if x.strip()] or list(MAINT_SIZES)
+    for N in sizes:
         params = scenes.box_room_scene(N, seed=rank, sh_degree=1)
         turn = N // 10
         extra = scenes.box_room_scene(turn, seed=rank + 1, sh_degree=1)
@@ -704,15 +707,18 @@ def run_maintenance(args, world, rank, local):
         n_keep_t = torch.zeros(1, dtype=torch.int64, device="cuda")
         moved = torch.empty(N, dtype=torch.int32, device="cuda")
         scratch = torch.empty(int(B.lib().gs_window_scratch_bytes(N)), dtype=torch.uint8, device="cuda")
-        src = [win.group(k).reshape(N, -1) for k in GaussianWindow.GROUPS]
-        dst = [torch.empty((n_leave,) + tuple(t.shape[1:]), device="cuda") for t in src]
         cols = win._columns(N)
+        # the parameter column of each group receives the leaving rows (room for N rows)
+        leave = [None] * len(cols)
+        c = 0
+        for k in GaussianWindow.GROUPS:
+            leave[c] = torch.empty((N,) + tuple(win.widths[k]), device="cuda").reshape(N, -1)
+            c += 3 + (1 if k in win.lowp else 0)
         zcols = [win.column(k, f) for k in GaussianWindow.GROUPS for f in (win.m, win.v)]
         nk = N - n_leave
 
         def kernels():
-            ctx.window_gather(src, dst, leave_idx)
-            ctx.window_compact(cols, keep, n_keep_t, moved, scratch)
+            ctx.window_remove(cols, leave, keep, n_keep_t, moved, scratch=scratch)
             ctx.window_clear(zcols, nk, nk + turn)
             win.n = nk + turn
             ctx.sh_init_bilinear(win.struct(), dict(v, g_begin=0, g_end=win.n), image, nk, nk + turn,
@@ -731,24 +737,29 @@ def run_maintenance(args, world, rank, local):
         ms_h = replay_ms(h2d)
         ms = replay_ms(step)
         movers = int((moved[:nk].cpu().numpy() != np.arange(nk)).sum())
-        # end to end through the window API (host syncs and read-backs included)
+        # end to end through the window API (host syncs and read-backs
+        # included); the entering Gaussians come from a pinned host map
+        pinned_params = dict(pinned, sh_degree=1)
+        # steady state: one window, each step maintain (10 % leave) then append
+        # (10 % enter); the first step (allocations) is not counted
+        win2 = GaussianWindow(params, local, capacity=N + 2 * turn)
         e2e = []
-        for k in range(3):
-            win2 = GaussianWindow(params, local, capacity=N + turn)
-            keep_h = rng.uniform(size=N) >= 0.1
+        for k in range(6):
+            keep_h = rng.uniform(size=win2.n) >= 0.1
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             win2.maintain(keep_h)
-            win2.append(extra, image=image, view=dict(v, g_begin=0, g_end=win2.n + turn))
+            win2.append(pinned_params, image=image, view=dict(v, g_begin=0, g_end=win2.n + turn))
             torch.cuda.synchronize()
-            e2e.append((time.perf_counter() - t0) * 1e3)
-            del win2
+            if k > 0:
+                e2e.append((time.perf_counter() - t0) * 1e3)
+        del win2
         algo = movers * 3 * 92 * 2 + n_leave * 92 * 2 + turn * (2 * 92 + 12 + 48) + N
         rows.append({"n": N, "step_ms": ms, "kernels_ms": ms_k, "h2d_ms": ms_h, "e2e_ms": float(np.median(e2e)),
                      "movers": movers, "leaving": n_leave, "appended": turn, "kernel_bytes": algo,
                      "kernels_gbs": algo / (ms_k / 1e3) / 1e9, "h2d_gbs": turn * 92 / (ms_h / 1e3) / 1e9})
         print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
-        del win, cols, src, dst, zcols
+        del win, cols, leave, zcols
     big = rows[-1]
     line = {"metric": "window maintenance step (10 pct leave: gather + compact; 10 pct enter: copy in, clear, "
                       "SH0 init), device ms at N=%d" % big["n"],
@@ -756,7 +767,7 @@ def run_maintenance(args, world, rank, local):
             "ms_per_step": big["step_ms"], "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "sliding-window maintenance of a box-room window of N Gaussians (SH degree 1)",
-                       "sizes": list(MAINT_SIZES), "per_size": rows,
+                       "sizes": sizes, "per_size": rows,
                        "l2": "window larger than L2 from N=1M (368 B per Gaussian with gradient and moments)"},
             "roofline": {"bound": "hbm", "achieved": big["kernels_gbs"], "peak": hbm, "unit": "GB/s",
                          "frac": big["kernels_gbs"] / hbm, "traffic": None, "peak_kind": hbm_kind,

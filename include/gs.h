@@ -439,6 +439,21 @@ GS_API size_t gs_window_scratch_bytes(int64_t n);
 GS_API int gs_window_compact(gs_ctx* ctx, const gs_window_column* cols, int n_cols, int64_t n, const uint8_t* keep,
                              int64_t* n_keep_dev, int32_t* moved_from, void* scratch, gs_stream stream);
 
+/* Steps 1 and 2 in one stream-ordered call, without host synchronisation:
+ * the rows whose keep[i] is 0 are (1) gathered in ascending row order into
+ * rows 0, 1, ... of leave_dst (the copy of leaving Gaussians to the global
+ * map; a NULL column pointer skips that column, leave_dst NULL skips the
+ * gather) and (2) removed by the compaction of gs_window_compact.  The
+ * number of leaving rows is n - n_keep (n_keep_dev receives n_keep); every
+ * leave_dst column must have room for n rows.  leaving_rows: NULL or device
+ * int32[n]; its first n - n_keep entries receive the leaving rows ascending.
+ * moved_from and scratch as gs_window_compact.  leave_dst columns have the
+ * bytes_per_gaussian of the matching window column.
+ * Errors: GS_ERR_INVALID_ARG, GS_ERR_CUDA. */
+GS_API int gs_window_remove(gs_ctx* ctx, const gs_window_column* cols, const gs_window_column* leave_dst, int n_cols,
+                            int64_t n, const uint8_t* keep, int64_t* n_keep_dev, int32_t* moved_from,
+                            int32_t* leaving_rows, void* scratch, gs_stream stream);
+
 /* Step 1 copy-back: gathers rows idx[0..m) (device int32, each in [0, n))
  * of every src column into rows 0..m of the matching dst column (same
  * bytes_per_gaussian), for the copy of leaving Gaussians to the global map.

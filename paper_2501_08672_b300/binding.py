@@ -34,7 +34,7 @@ EXPORTED = ["gs_config_default", "gs_version", "gs_context_create", "gs_context_
             "gs_render_fwd", "gs_l1_loss", "gs_render_bwd", "gs_pose_grad", "gs_adam_step", "gs_sync_status",
             "gs_profile_enable", "gs_profile_collect", "gs_launch_count", "gs_adam_step_dev",
             "gs_l1_loss_noalloc", "gs_calibrate_alu", "gs_pose_normal_scratch", "gs_pose_normal",
-            "gs_window_scratch_bytes", "gs_window_compact", "gs_window_gather", "gs_window_clear",
+            "gs_window_scratch_bytes", "gs_window_compact", "gs_window_remove", "gs_window_gather", "gs_window_clear",
             "gs_sh_init_bilinear", "gs_dssim_scratch_floats", "gs_dssim_loss"]
 
 KERNEL_FAMILIES = ["project", "depth_sort", "tile_scan", "emit", "tile_sort", "ranges", "raster_fwd", "l1",
@@ -146,6 +146,8 @@ def lib():
         L.gs_window_scratch_bytes.argtypes = [I64]
         L.gs_window_scratch_bytes.restype = ctypes.c_size_t
         L.gs_window_compact.argtypes = [P, ctypes.POINTER(WindowColumn), I, I64, P, P, P, P, P]
+        L.gs_window_remove.argtypes = [P, ctypes.POINTER(WindowColumn), ctypes.POINTER(WindowColumn), I, I64, P, P, P,
+                                       P, P, P]
         L.gs_window_gather.argtypes = [P, ctypes.POINTER(WindowColumn), ctypes.POINTER(WindowColumn), I, I64, P,
                                        I64, P]
         L.gs_window_clear.argtypes = [P, ctypes.POINTER(WindowColumn), I, I64, I64, P]
@@ -351,6 +353,35 @@ class Context:
         cols = self._columns(tensors)
         self._ck(lib().gs_window_compact(self.h, cols, len(tensors), n, _ptr(keep), _ptr(n_keep), _ptr(moved_from),
                                          _ptr(scratch), _stream(stream)))
+
+    def window_remove(self, tensors, leave_dst, keep, n_keep, moved_from=None, leaving_rows=None, scratch=None,
+                      stream=None):
+        """Gather of the rows with keep == 0 into leave_dst (a list matching
+        tensors, None entries skipped; each with room for n rows) and the
+        compaction, in one stream-ordered call."""
+        n = int(keep.numel())
+        if scratch is None:
+            scratch = torch.empty(int(lib().gs_window_scratch_bytes(n)), dtype=torch.uint8, device=keep.device)
+        _check_dev(keep, "keep", torch.uint8, n)
+        _check_dev(n_keep, "n_keep", torch.int64, 1)
+        for name, t in (("moved_from", moved_from), ("leaving_rows", leaving_rows)):
+            if t is not None:
+                _check_dev(t, name, torch.int32, n)
+        cols = self._columns(tensors)
+        dst = None
+        if leave_dst is not None:
+            if len(leave_dst) != len(tensors):
+                raise ValueError("leave_dst has %d entries for %d columns" % (len(leave_dst), len(tensors)))
+            dst = (WindowColumn * len(tensors))()
+            for k, (t, d) in enumerate(zip(tensors, leave_dst)):
+                dst[k].bytes_per_gaussian = cols[k].bytes_per_gaussian
+                if d is not None:
+                    _check_dev(d, "leave_dst column")
+                    if d.shape[0] < n or d.numel() * d.element_size() // max(d.shape[0], 1) != cols[k].bytes_per_gaussian:
+                        raise ValueError("leave_dst column %d must hold %d rows of the column's width" % (k, n))
+                    dst[k].ptr = d.data_ptr()
+        self._ck(lib().gs_window_remove(self.h, cols, dst, len(tensors), n, _ptr(keep), _ptr(n_keep),
+                                        _ptr(moved_from), _ptr(leaving_rows), _ptr(scratch), _stream(stream)))
 
     def window_gather(self, src, dst, idx, stream=None):
         """Rows idx (int32 device) of every src tensor into rows 0.. of dst."""

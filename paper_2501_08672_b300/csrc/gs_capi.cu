@@ -688,11 +688,22 @@ int check_columns(gs_ctx* ctx, const gs_window_column* cols, int n_cols, const c
 
 size_t gs_window_scratch_bytes(int64_t n) { return window_scratch_bytes(n < 0 ? 0 : (long long)n); }
 
-int gs_window_compact(gs_ctx* ctx, const gs_window_column* cols, int n_cols, int64_t n, const uint8_t* keep,
-                      int64_t* n_keep_dev, int32_t* moved_from, void* scratch, gs_stream stream) {
+namespace {
+int window_remove_impl(gs_ctx* ctx, const gs_window_column* cols, const gs_window_column* leave_dst, int n_cols,
+                       int64_t n, const uint8_t* keep, int64_t* n_keep_dev, int32_t* moved_from,
+                       int32_t* leaving_rows, void* scratch, gs_stream stream, const char* what) {
     if (!ctx) return GS_ERR_INVALID_ARG;
     int rc = check_columns(ctx, cols, n_cols, "window");
     if (rc) return rc;
+    if (leave_dst) {
+        for (int c = 0; c < n_cols; ++c) {
+            if (!leave_dst[c].ptr) continue;  // column not gathered
+            if (leave_dst[c].bytes_per_gaussian != cols[c].bytes_per_gaussian)
+                return fail(ctx, GS_ERR_INVALID_ARG, "column %d: leave_dst width differs from the window's", c);
+            if (reinterpret_cast<uintptr_t>(leave_dst[c].ptr) % 4)
+                return fail(ctx, GS_ERR_INVALID_ARG, "leave_dst column %d is not 4-byte aligned", c);
+        }
+    }
     if (n < 0 || n > 0x7FFFFFFFll) return fail(ctx, GS_ERR_INVALID_ARG, "n=%lld outside [0, 2^31)", (long long)n);
     if (!keep || !n_keep_dev || !scratch) return fail(ctx, GS_ERR_INVALID_ARG, "keep, n_keep or scratch is NULL");
     if (reinterpret_cast<uintptr_t>(scratch) % 256)
@@ -701,11 +712,26 @@ int gs_window_compact(gs_ctx* ctx, const gs_window_column* cols, int n_cols, int
     const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     if (n == 0) {
         const cudaError_t e = cudaMemsetAsync(n_keep_dev, 0, sizeof(int64_t), s);
-        return e == cudaSuccess ? GS_OK : cuda_fail(ctx, e, "gs_window_compact");
+        return e == cudaSuccess ? GS_OK : cuda_fail(ctx, e, what);
     }
-    const cudaError_t e = launch_window_compact(cols, n_cols, (long long)n, keep, reinterpret_cast<long long*>(n_keep_dev),
-                                                moved_from, scratch, ctx->sm_count, s, ctx->prof);
-    return e == cudaSuccess ? GS_OK : cuda_fail(ctx, e, "gs_window_compact");
+    const cudaError_t e = launch_window_compact(cols, leave_dst, n_cols, (long long)n, keep,
+                                                reinterpret_cast<long long*>(n_keep_dev), moved_from, leaving_rows,
+                                                scratch, ctx->sm_count, s, ctx->prof);
+    return e == cudaSuccess ? GS_OK : cuda_fail(ctx, e, what);
+}
+}  // namespace
+
+int gs_window_compact(gs_ctx* ctx, const gs_window_column* cols, int n_cols, int64_t n, const uint8_t* keep,
+                      int64_t* n_keep_dev, int32_t* moved_from, void* scratch, gs_stream stream) {
+    return window_remove_impl(ctx, cols, nullptr, n_cols, n, keep, n_keep_dev, moved_from, nullptr, scratch, stream,
+                              "gs_window_compact");
+}
+
+int gs_window_remove(gs_ctx* ctx, const gs_window_column* cols, const gs_window_column* leave_dst, int n_cols,
+                     int64_t n, const uint8_t* keep, int64_t* n_keep_dev, int32_t* moved_from, int32_t* leaving_rows,
+                     void* scratch, gs_stream stream) {
+    return window_remove_impl(ctx, cols, leave_dst, n_cols, n, keep, n_keep_dev, moved_from, leaving_rows, scratch,
+                              stream, "gs_window_remove");
 }
 
 int gs_window_gather(gs_ctx* ctx, const gs_window_column* src, const gs_window_column* dst, int n_cols, int64_t n,

@@ -262,9 +262,9 @@ cudaError_t launch_ssim(const BatchParam& bp, const SsimParam& sp, const float* 
                         float* scratch, float* dL_drgb, float* loss, cudaStream_t s, Prof& pf);
 int window_max_columns();
 size_t window_scratch_bytes(long long n);
-cudaError_t launch_window_compact(const gs_window_column* cols, int n_cols, long long n, const uint8_t* keep,
-                                  long long* n_keep_dev, int32_t* moved_from, void* scratch, int sm_count,
-                                  cudaStream_t s, Prof& pf);
+cudaError_t launch_window_compact(const gs_window_column* cols, const gs_window_column* leave_dst, int n_cols,
+                                  long long n, const uint8_t* keep, long long* n_keep_dev, int32_t* moved_from,
+                                  int32_t* leaving_rows, void* scratch, int sm_count, cudaStream_t s, Prof& pf);
 cudaError_t launch_window_gather(const gs_window_column* src, const gs_window_column* dst, int n_cols,
                                  const int32_t* idx, long long m, long long n, int sm_count, cudaStream_t s,
                                  Prof& pf);

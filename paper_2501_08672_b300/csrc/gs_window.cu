@@ -123,17 +123,20 @@ __global__ void __launch_bounds__(1024) k_win_top(const uint8_t* __restrict__ ke
     }
 }
 
-// Ranks from the survivor prefix S(i) (survivors before row i): a hole i <
-// n_keep has rank i - S(i) among the holes, a mover i >= n_keep has rank
-// S(i) - S(n_keep) among the movers (ascending); moved_from[r] = r for the
-// survivors below n_keep.
+// Ranks from the survivor prefix S(i) (survivors before row i): a removed
+// row i has rank i - S(i) among all removed rows (ascending), so the first
+// n_movers entries of that list are the holes below n_keep; a mover
+// i >= n_keep has rank S(i) - S(n_keep) among the movers (ascending);
+// moved_from[r] = r for the survivors below n_keep.  leaving_rows (optional)
+// receives the removed rows' list too.
 __global__ void __launch_bounds__(kWinThreads) k_win_rank(const uint8_t* __restrict__ keep, long long n,
                                                           const long long* __restrict__ n_keep,
                                                           const unsigned* __restrict__ part,
                                                           const long long* __restrict__ counts,
                                                           int32_t* __restrict__ holes_list,
                                                           int32_t* __restrict__ movers_asc,
-                                                          int32_t* __restrict__ moved_from) {
+                                                          int32_t* __restrict__ moved_from,
+                                                          int32_t* __restrict__ leaving_rows) {
     const long long base = (long long)blockIdx.x * kWinChunk + (long long)threadIdx.x * kWinItems;
     bool f[kWinItems];
     unsigned c = 0;
@@ -149,10 +152,12 @@ __global__ void __launch_bounds__(kWinThreads) k_win_rank(const uint8_t* __restr
     for (int k = 0; k < kWinItems; ++k) {
         const long long i = base + k;
         if (i >= n) break;
-        if (i < nk) {
-            if (!f[k]) holes_list[i - S] = (int32_t)i;
-            else if (moved_from) moved_from[i] = (int32_t)i;
-        } else if (f[k]) {
+        if (!f[k]) {
+            holes_list[i - S] = (int32_t)i;
+            if (leaving_rows) leaving_rows[i - S] = (int32_t)i;
+        } else if (i < nk) {
+            if (moved_from) moved_from[i] = (int32_t)i;
+        } else {
             movers_asc[S - snk] = (int32_t)i;
         }
         S += f[k];
@@ -163,10 +168,10 @@ __global__ void __launch_bounds__(kWinThreads) k_win_rank(const uint8_t* __restr
 // s_row, destination row d_row, d_row < 0 = no entry) and copies every column
 // of those rows word-parallel: word w of a column's chunk is word w % words of
 // entry w / words, so neighbouring lanes touch neighbouring words of a row and
-// the rows of neighbouring entries; four words per lane are in flight.
+// the rows of neighbouring entries; eight words per lane are in flight.
 constexpr int kCopyThreads = 256;
-constexpr int kCopyUnroll = 4;
-constexpr int kCopyBlocksPerSM = 5;
+constexpr int kCopyUnroll = 8;
+constexpr int kCopyBlocksPerSM = 4;
 
 __device__ __forceinline__ void warp_copy_rows(const ColTable& from, const ColTable& to, int32_t s_row,
                                                int32_t d_row) {
@@ -179,6 +184,7 @@ __device__ __forceinline__ void warp_copy_rows(const ColTable& from, const ColTa
         const int total = 32 * words;
         const uint32_t* __restrict__ f = from.ptr[c];
         uint32_t* __restrict__ t = to.ptr[c];
+        if (!t) continue;  // a column the caller does not want (warp-uniform)
         for (int w0 = 0; w0 < total; w0 += 32 * kCopyUnroll) {
             uint32_t val[kCopyUnroll];
             long long dpos[kCopyUnroll];
@@ -223,10 +229,13 @@ __global__ void __launch_bounds__(kCopyThreads, kCopyBlocksPerSM) k_win_move(con
     }
 }
 
-// Rows idx[0..m) of each source column, gathered contiguously into dst.
+// Rows idx[0..m) of each source column, gathered contiguously into dst
+// (columns whose destination is NULL are skipped).  With n_keep set, m is
+// n - *n_keep (the rows removed by the compaction), read on the device.
 __global__ void __launch_bounds__(kCopyThreads, kCopyBlocksPerSM) k_win_gather(const ColTable src, const ColTable dst,
                                                              const int32_t* __restrict__ idx, long long m,
-                                                             long long n) {
+                                                             long long n, const long long* __restrict__ n_keep) {
+    if (n_keep) m = min(max(n - *n_keep, 0ll), m);
     const int lane = threadIdx.x & 31;
     const long long warp = ((long long)blockIdx.x * kCopyThreads + threadIdx.x) >> 5;
     const long long n_warps = (long long)gridDim.x * (kCopyThreads / 32);
@@ -255,12 +264,22 @@ __global__ void __launch_bounds__(kCopyThreads) k_win_clear(const ColTable cols,
     }
 }
 
+// One thread per new Gaussian for the colour; the warp's 32 rows of SH
+// coefficients are one contiguous range, written by the whole warp in
+// coalesced stores (lane l takes positions l, l + 32, ...; the k0 values
+// come from their rows' lanes by shuffles).
+template <int D>
 __global__ void __launch_bounds__(256) k_sh_init(const ViewParam V, const float* __restrict__ means,
                                                  const float* __restrict__ image, long long begin, long long end,
-                                                 int K, float z_near, float* __restrict__ sh) {
-    const long long i = begin + (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= end) return;
-    const float mx = means[3 * i], my = means[3 * i + 1], mz = means[3 * i + 2];
+                                                 float z_near, float* __restrict__ sh) {
+    constexpr int K3 = 3 * (D + 1) * (D + 1);  // floats per row
+    const long long i0 = begin + (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u);
+    if (i0 >= end) return;  // warp-uniform
+    const int lane = threadIdx.x & 31;
+    const long long i = i0 + lane;
+    const bool live = i < end;
+    const long long ii = live ? i : i0;
+    const float mx = means[3 * ii], my = means[3 * ii + 1], mz = means[3 * ii + 2];
     const float x = V.R[0] * mx + V.R[1] * my + V.R[2] * mz + V.t[0];
     const float y = V.R[3] * mx + V.R[4] * my + V.R[5] * mz + V.t[1];
     const float z = V.R[6] * mx + V.R[7] * my + V.R[8] * mz + V.t[2];
@@ -284,9 +303,18 @@ __global__ void __launch_bounds__(256) k_sh_init(const ViewParam V, const float*
         }
     }
     constexpr float kInvShC0 = 3.5449077018110318f;  // 2 sqrt(pi) = 1 / C0
-    float* o = sh + (size_t)i * K * 3;
-    for (int ch = 0; ch < 3; ++ch) o[ch] = (c[ch] - 0.5f) * kInvShC0;
-    for (int e = 3; e < K * 3; ++e) o[e] = 0.f;
+    const float k0[3] = {(c[0] - 0.5f) * kInvShC0, (c[1] - 0.5f) * kInvShC0, (c[2] - 0.5f) * kInvShC0};
+    const long long rows = end - i0 < 32 ? end - i0 : 32;
+    float* o = sh + (size_t)i0 * K3;
+#pragma unroll
+    for (int e0 = 0; e0 < 32 * K3; e0 += 32) {
+        const int e = e0 + lane;
+        const int row = e / K3, ch = e - row * K3;
+        const float v0 = __shfl_sync(0xffffffffu, k0[0], row);
+        const float v1 = __shfl_sync(0xffffffffu, k0[1], row);
+        const float v2 = __shfl_sync(0xffffffffu, k0[2], row);
+        if (row < rows) o[e] = ch == 0 ? v0 : ch == 1 ? v1 : ch == 2 ? v2 : 0.f;
+    }
 }
 
 ColTable col_table(const gs_window_column* cols, int n_cols) {
@@ -311,7 +339,7 @@ size_t window_scratch_bytes(long long n) {
 }
 
 // Grid of the row-copy kernels: one chunk of 32 rows per warp, at most the
-// blocks one SM holds at once (up to 51 registers a thread) times the SMs,
+// blocks one SM holds at once (up to 64 registers a thread) times the SMs,
 // grid-stride beyond that.
 unsigned copy_grid(long long rows, int sm_count) {
     const long long chunks = (rows + 31) / 32;
@@ -320,9 +348,9 @@ unsigned copy_grid(long long rows, int sm_count) {
     return (unsigned)(blocks < 1 ? 1 : (blocks < cap ? blocks : cap));
 }
 
-cudaError_t launch_window_compact(const gs_window_column* cols_host, int n_cols, long long n, const uint8_t* keep,
-                                  long long* n_keep_dev, int32_t* moved_from, void* scratch, int sm_count,
-                                  cudaStream_t s, Prof& pf) {
+cudaError_t launch_window_compact(const gs_window_column* cols_host, const gs_window_column* leave_dst, int n_cols,
+                                  long long n, const uint8_t* keep, long long* n_keep_dev, int32_t* moved_from,
+                                  int32_t* leaving_rows, void* scratch, int sm_count, cudaStream_t s, Prof& pf) {
     const long long nblk = (n + kWinChunk - 1) / kWinChunk;
     auto al = [](size_t b) { return (b + 255) / 256 * 256; };
     char* p = static_cast<char*>(scratch);
@@ -334,11 +362,14 @@ cudaError_t launch_window_compact(const gs_window_column* cols_host, int n_cols,
     p += al(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
     int32_t* movers_asc = reinterpret_cast<int32_t*>(p);
     const ColTable cols = col_table(cols_host, n_cols);
-    const int pi = pf.begin(GS_KF_WINDOW, s, 4);
+    const int pi = pf.begin(GS_KF_WINDOW, s, leave_dst ? 5 : 4);
     k_win_reduce<<<(unsigned)nblk, kWinThreads, 0, s>>>(keep, n, part);
     k_win_top<<<1, 1024, 0, s>>>(keep, n, part, (int)nblk, n_keep_dev, counts);
     k_win_rank<<<(unsigned)nblk, kWinThreads, 0, s>>>(keep, n, n_keep_dev, part, counts, holes_list, movers_asc,
-                                                       moved_from);
+                                                       moved_from, leaving_rows);
+    if (leave_dst)  // Step 1 before the moves overwrite the holes
+        k_win_gather<<<copy_grid(n, sm_count), kCopyThreads, 0, s>>>(cols, col_table(leave_dst, n_cols), holes_list,
+                                                                      n, n, n_keep_dev);
     k_win_move<<<copy_grid(n / 2, sm_count), kCopyThreads, 0, s>>>(cols, n, counts, holes_list, movers_asc,
                                                                   moved_from);
     pf.end(pi, s);
@@ -351,7 +382,7 @@ cudaError_t launch_window_gather(const gs_window_column* src_host, const gs_wind
     const int pi = pf.begin(GS_KF_WINDOW, s);
     if (m > 0)
         k_win_gather<<<copy_grid(m, sm_count), kCopyThreads, 0, s>>>(col_table(src_host, n_cols),
-                                                                      col_table(dst_host, n_cols), idx, m, n);
+                                                                      col_table(dst_host, n_cols), idx, m, n, nullptr);
     pf.end(pi, s);
     return cudaGetLastError();
 }
@@ -373,7 +404,13 @@ cudaError_t launch_sh_init(const ViewParam& V, const float* means, const float* 
     if (end <= begin) return cudaSuccess;
     const int pi = pf.begin(GS_KF_WINDOW, s);
     const int K = (sh_degree + 1) * (sh_degree + 1);
-    k_sh_init<<<(unsigned)((end - begin + 255) / 256), 256, 0, s>>>(V, means, image, begin, end, K, z_near, sh);
+    const unsigned grid = (unsigned)((end - begin + 255) / 256);
+    switch (K) {
+        case 1: k_sh_init<0><<<grid, 256, 0, s>>>(V, means, image, begin, end, z_near, sh); break;
+        case 4: k_sh_init<1><<<grid, 256, 0, s>>>(V, means, image, begin, end, z_near, sh); break;
+        case 9: k_sh_init<2><<<grid, 256, 0, s>>>(V, means, image, begin, end, z_near, sh); break;
+        default: k_sh_init<3><<<grid, 256, 0, s>>>(V, means, image, begin, end, z_near, sh); break;
+    }
     pf.end(pi, s);
     return cudaGetLastError();
 }

@@ -235,33 +235,40 @@ class GaussianWindow:
 
     def maintain(self, keep):
         """Steps 1 and 2: `keep` (bool or uint8 [n], device or host) marks the
-        Gaussians that stay.  The leaving ones are gathered and returned as a
-        host parameter dict (for the global map); the window is compacted on
-        the device by swapping rear survivors into the holes.  Returns
-        (leaving params, moved_from [n_keep] int64 host: the old row of every
-        new row)."""
+        Gaussians that stay.  One stream-ordered library call gathers the
+        leaving Gaussians' parameters (ascending row order) into a device
+        staging area and compacts the window by swapping rear survivors into
+        the holes; the host then reads the survivor count and copies the
+        leaving parameters and the row map back.  Returns (leaving params as
+        a host dict, moved_from [n_keep] int64 host: the old row of every new
+        row)."""
         n = self.n
         keep = torch.as_tensor(keep, device=self.device).to(torch.uint8).contiguous()
         if keep.numel() != n:
             raise ValueError("keep has %d entries for %d Gaussians" % (keep.numel(), n))
-        ctx = self.ctx()
-        idx = torch.nonzero(keep == 0).view(-1).to(torch.int32)
-        m = int(idx.numel())
-        src = [self.group(k).reshape(n, -1) for k in self.GROUPS]
-        dst = [torch.empty((max(m, 1),) + tuple(s.shape[1:]), dtype=torch.float32, device=self.device) for s in src]
-        if m:
-            ctx.window_gather(src, dst, idx)
-        leaving = {k: d[:m].reshape((m,) + self.widths[k]).cpu().numpy() for k, d in zip(self.GROUPS, dst)}
-        leaving["sh_degree"] = self.sh_degree
+        if getattr(self, "_leave", None) is None:
+            self._leave = {k: torch.empty((self.capacity,) + self.widths[k], dtype=torch.float32, device=self.device)
+                           for k in self.GROUPS}
+        cols = self._columns(n)
+        leave = [None] * len(cols)
+        c = 0
+        for k in self.GROUPS:
+            leave[c] = self._leave[k][:n].reshape(n, -1)  # the parameter column of group k
+            c += 3 + (1 if k in self.lowp else 0)
         n_keep = torch.zeros(1, dtype=torch.int64, device=self.device)
         moved = torch.empty(max(n, 1), dtype=torch.int32, device=self.device)
-        ctx.window_compact(self._columns(n), keep, n_keep, moved[:n] if n else None)
-        self.n = int(n_keep.item())
-        return leaving, moved[:self.n].to(torch.int64).cpu().numpy()
+        self.ctx().window_remove(cols, leave, keep, n_keep, moved[:n] if n else None)
+        nk = int(n_keep.item())
+        m = n - nk
+        leaving = {k: self._leave[k][:m].cpu().numpy() for k in self.GROUPS}
+        leaving["sh_degree"] = self.sh_degree
+        self.n = nk
+        return leaving, moved[:nk].to(torch.int64).cpu().numpy()
 
     def append(self, params, image=None, view=None, stream=None):
-        """Step 4: appends the Gaussians of `params` (host arrays) at rows
-        [n, n + m) (parameters copied host to device, Adam moments zeroed); with `image` ([3, H, W] device FP32) and `view`
+        """Step 4: appends the Gaussians of `params` (host arrays, or pinned
+        FP32 host tensors, which are copied without staging) at rows [n, n + m)
+        (parameters copied host to device, Adam moments zeroed); with `image` ([3, H, W] device FP32) and `view`
         their SH start from the bilinear image colour (Sec. II-B.2).  The
         copies are issued on `stream` (default: the current stream)."""
         m = int(params["means"].shape[0])
@@ -271,8 +278,12 @@ class GaussianWindow:
         s = stream or torch.cuda.current_stream(self.device)
         with torch.cuda.stream(s):
             for k in self.GROUPS:
-                host = torch.as_tensor(np.ascontiguousarray(params[k], np.float32)).view(self.shape(k, m))
-                self.column(k)[a:b].copy_(host.pin_memory(), non_blocking=True)
+                src = params[k]
+                if isinstance(src, torch.Tensor) and src.is_pinned() and src.dtype == torch.float32:
+                    host = src.reshape(self.shape(k, m))  # already pinned (e.g. a pinned host map): no staging copy
+                else:
+                    host = torch.as_tensor(np.ascontiguousarray(src, np.float32)).view(self.shape(k, m)).pin_memory()
+                self.column(k)[a:b].copy_(host, non_blocking=True)
             self.ctx().window_clear([self.column(k, f) for k in self.GROUPS for f in (self.m, self.v)], a, b, stream=s)
             self.n = b
             if image is not None:

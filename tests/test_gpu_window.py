@@ -62,6 +62,34 @@ def test_window_compact_many_movers(orc):
         np.testing.assert_array_equal(c[:nk].cpu().numpy(), h[ref])
 
 
+@pytest.mark.parametrize("n,p_leave", [(1, 1.0), (4097, 0.3), (300_001, 0.1), (300_001, 0.9)])
+def test_window_remove_gathers_then_compacts(orc, n, p_leave):
+    """One call: the leaving rows (ascending) gathered for the columns that ask
+    for it, the leaving row list, and the compaction as gs_window_compact."""
+    rng = np.random.default_rng(n + int(10 * p_leave))
+    keep = rng.uniform(size=n) >= p_leave
+    cols_h = [rng.standard_normal((n, 3)).astype(np.float32), rng.standard_normal((n, 12)).astype(np.float32),
+              rng.integers(0, 1 << 30, (n, 1)).astype(np.int32)]
+    cols = [torch.as_tensor(c).cuda() for c in cols_h]
+    leave = [torch.full((n, 3), -1.0, device="cuda"), None, torch.full((n, 1), -1, dtype=torch.int32, device="cuda")]
+    n_keep = torch.zeros(1, dtype=torch.int64, device="cuda")
+    moved = torch.full((n,), -7, dtype=torch.int32, device="cuda")
+    rows = torch.full((n,), -7, dtype=torch.int32, device="cuda")
+    B.Context(0).window_remove(cols, leave, torch.as_tensor(keep.astype(np.uint8)).cuda(), n_keep, moved, rows)
+    torch.cuda.synchronize()
+    ref = orc.window_compact(keep)
+    nk = int(n_keep.item())
+    gone = np.nonzero(~keep)[0]
+    assert nk == ref.size and n - nk == gone.size
+    np.testing.assert_array_equal(moved[:nk].cpu().numpy(), ref)
+    np.testing.assert_array_equal(rows[:gone.size].cpu().numpy(), gone)
+    for c, h in zip(cols, cols_h):
+        np.testing.assert_array_equal(c[:nk].cpu().numpy(), h[ref])
+    np.testing.assert_array_equal(leave[0][:gone.size].cpu().numpy(), cols_h[0][gone])
+    np.testing.assert_array_equal(leave[2][:gone.size].cpu().numpy(), cols_h[2][gone])
+    assert np.all(leave[0][gone.size:].cpu().numpy() == -1.0)
+
+
 @pytest.mark.parametrize("m", [1, 31, 33, 500_000])
 def test_window_gather_sizes(m):
     rng = np.random.default_rng(m)
