@@ -52,7 +52,8 @@ def ws_view(r, offset, dtype, count):
 def compare_images(orc_out, gpu_img, gpu_T, tol=FWD_TOL):
     ok = ~orc_out["border"]
     frac = 1.0 - ok.mean()
-    assert frac < 1e-3, "borderline pixel share %.2e" % frac
+    # a share bound: small images may hold a pixel or two whatever their size
+    assert frac < 1e-3 or (~ok).sum() <= 2, "borderline pixel share %.2e" % frac
     err = np.abs(gpu_img - orc_out["rgb"])[:, ok].max()
     errT = np.abs(gpu_T - orc_out["T"])[ok].max()
     assert err <= tol, "image max abs err %.3e" % err
@@ -666,3 +667,83 @@ def test_graph_replay_matches_plain_steps():
     err = (a.win.flat - b.win.flat).norm() / a.win.flat.norm()
     assert err < 1e-5
     assert abs(float(a.r.loss.item()) - float(b.r.loss.item())) < 1e-5
+
+
+# ---------------------------------------------------------------- limits and degenerate inputs
+
+def test_max_views_forward_backward(orc):
+    """GS_MAX_VIEWS (64) small views around a scene, each on its own part of
+    the window, forward and backward against the oracle."""
+    n = 3000
+    p = scenes.frustum_scene(n, seed=40)
+    views = []
+    for k in range(64):
+        ang = 0.02 * (k - 32)
+        b, e = (k * 37) % 2000, (k * 37) % 2000 + 1000
+        v = scenes.lookat_view((2.0 * math.sin(ang), 0.1 * (k % 5), -1.0), (0.0, 0.0, 5.0),
+                               24 + (k % 7) * 3, 16 + (k % 5) * 4, 30.0, b, e, up=(0, -1, 0))
+        views.append(v)
+    win, r = gpu_forward(p, views)
+    for v, img, T in zip(views, r.images(), B.unpack_images(r.T, views, 1)):
+        compare_images(orc.render_view(p, v), img.cpu().numpy(), T.cpu().numpy())
+    tg = l1_target(p, views)
+    gpu_loss_backward(win, r, tg)
+    L, g, pose, border, _ = oracle_l1_backward(orc, p, views, tg, r)
+    compare_grads(win, g, border, pose=r.dL_dpose.view(-1, 6).cpu().numpy().astype(np.float64), orc_pose=pose)
+
+
+def test_view_with_every_gaussian_culled(orc):
+    """A camera looking away from the whole window: no pairs, the background
+    everywhere, T = 1, and zero gradients (the other view still works)."""
+    n = 2000
+    p = scenes.frustum_scene(n, seed=41)
+    away = scenes.lookat_view((0.0, 0.0, 0.0), (0.0, 0.0, -5.0), 48, 40, 40.0, 0, n, up=(0, -1, 0))
+    seen = scenes.identity_view(48, 40, 40.0, 0, n)
+    cfg = dict(bg=(0.2, 0.4, 0.6))
+    win, r = gpu_forward(p, [away, seen], **cfg)
+    img = r.images()[0].cpu().numpy()
+    T = B.unpack_images(r.T, [away, seen], 1)[0].cpu().numpy()
+    np.testing.assert_array_equal(T, np.ones_like(T))
+    for c, b in enumerate(cfg["bg"]):
+        np.testing.assert_allclose(img[c], np.float32(b), rtol=0, atol=0)
+    o = orc.render_view(p, seen, dict(orc.DEFAULT_CFG, **cfg))
+    compare_images(o, r.images()[1].cpu().numpy(), B.unpack_images(r.T, [away, seen], 1)[1].cpu().numpy())
+    # only the culled view in the loss: every Gaussian gradient is zero
+    win2, r2 = gpu_forward(p, [away], **cfg)
+    tg = [np.zeros((3, 40, 48))]
+    gpu_loss_backward(win2, r2, tg)
+    for k in GaussianWindow.GROUPS:
+        assert float(win2.grad(k).abs().max()) == 0.0
+    assert float(r2.dL_dpose.abs().max()) == 0.0
+
+
+@pytest.mark.parametrize("W,H", [(1, 1), (1, 17), (17, 1), (33, 2)])
+def test_degenerate_image_sizes(orc, W, H):
+    n = 1500
+    p = scenes.frustum_scene(n, seed=42)
+    views = [scenes.identity_view(W, H, 0.5 * max(W, H) + 2.0, 0, n)]
+    win, r = gpu_forward(p, views)
+    compare_images(orc.render_view(p, views[0]), r.images()[0].cpu().numpy(),
+                   B.unpack_images(r.T, views, 1)[0].cpu().numpy())
+    tg = l1_target(p, views)
+    gpu_loss_backward(win, r, tg)
+    L, g, pose, border, _ = oracle_l1_backward(orc, p, views, tg, r)
+    compare_grads(win, g, border, pose=r.dL_dpose.view(-1, 6).cpu().numpy().astype(np.float64), orc_pose=pose)
+
+
+def test_huge_splats_cover_the_image(orc):
+    """A few Gaussians whose footprints span the whole image (hundreds of
+    tiles: the warp-cooperative emission path) over many small ones."""
+    n = 4000
+    p = scenes.frustum_scene(n, seed=43)
+    p["log_scales"][:6] = np.log(np.array([[1.5, 1.2, 0.4]] * 6, np.float32))
+    p["means"][:6, 2] = np.linspace(3.0, 7.0, 6)
+    p["opacity"][:6] = -1.5
+    views = [scenes.identity_view(256, 192, 200.0, 0, n)]
+    win, r = gpu_forward(p, views)
+    compare_images(orc.render_view(p, views[0]), r.images()[0].cpu().numpy(),
+                   B.unpack_images(r.T, views, 1)[0].cpu().numpy())
+    tg = l1_target(p, views)
+    gpu_loss_backward(win, r, tg)
+    L, g, pose, border, _ = oracle_l1_backward(orc, p, views, tg, r)
+    compare_grads(win, g, border, pose=r.dL_dpose.view(-1, 6).cpu().numpy().astype(np.float64), orc_pose=pose)
