@@ -314,6 +314,25 @@ GS_API int gs_adam_step_dev(gs_ctx* ctx, float* param, const float* grad, float*
                             float lr, float b1, float b2, float eps, int64_t* step_dev,
                             const gs_lowp_segment* segs, int n_segs, gs_stream stream);
 
+/* An element range [begin, end) of a flat parameter vector. */
+typedef struct gs_range {
+    int64_t begin, end;
+} gs_range;
+
+/* a8 over the active rows only: the Adam step of gs_adam_step applied to the
+ * elements of up to 8 disjoint ranges of the n-element buffers (begin a
+ * multiple of 4, end <= n; the buffers 16-byte aligned), e.g. rows [0, n_g)
+ * of each parameter group of a window with spare capacity, so that rows
+ * outside the ranges (Gaussians being appended on another stream) are never
+ * read or written.  With step_dev non-NULL the step count lives on the
+ * device as in gs_adam_step_dev (step is ignored); else step >= 1 is used.
+ * Low-precision segments as in gs_adam_step (written for elements inside
+ * the ranges).  Errors: GS_ERR_INVALID_ARG, GS_ERR_CUDA. */
+GS_API int gs_adam_step_ranges(gs_ctx* ctx, float* param, const float* grad, float* m, float* v, int64_t n,
+                               const gs_range* ranges, int n_ranges, float lr, float b1, float b2, float eps,
+                               int64_t step, int64_t* step_dev, const gs_lowp_segment* segs, int n_segs,
+                               gs_stream stream);
+
 /* L1 loss that allocates nothing and needs no context or workspace.  The
  * paper has no counterpart: this entry point exists for callers that cannot
  * allocate device memory, such as a real-time loop that allocates nothing

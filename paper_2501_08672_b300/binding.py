@@ -35,7 +35,7 @@ EXPORTED = ["gs_config_default", "gs_version", "gs_context_create", "gs_context_
             "gs_profile_enable", "gs_profile_collect", "gs_launch_count", "gs_adam_step_dev",
             "gs_l1_loss_noalloc", "gs_calibrate_alu", "gs_pose_normal_scratch", "gs_pose_normal",
             "gs_window_scratch_bytes", "gs_window_compact", "gs_window_remove", "gs_window_gather", "gs_window_clear",
-            "gs_sh_init_bilinear", "gs_dssim_scratch_floats", "gs_dssim_loss"]
+            "gs_sh_init_bilinear", "gs_dssim_scratch_floats", "gs_dssim_loss", "gs_adam_step_ranges"]
 
 KERNEL_FAMILIES = ["project", "depth_sort", "tile_scan", "emit", "tile_sort", "ranges", "raster_fwd", "l1",
                    "raster_bwd", "project_bwd", "adam", "pose_normal", "window", "ssim"]
@@ -92,6 +92,10 @@ class ProfileEntry(ctypes.Structure):
     _fields_ = [("family", ctypes.c_int32), ("launches", ctypes.c_int32), ("total_ms", ctypes.c_double)]
 
 
+class Range(ctypes.Structure):
+    _fields_ = [("begin", ctypes.c_int64), ("end", ctypes.c_int64)]
+
+
 class LowpSegment(ctypes.Structure):
     _fields_ = [("begin", ctypes.c_int64), ("end", ctypes.c_int64), ("dtype", ctypes.c_int32),
                 ("dst", ctypes.c_void_p)]
@@ -132,6 +136,9 @@ def lib():
                                    ctypes.c_float, I64, ctypes.POINTER(LowpSegment), I, P]
         L.gs_adam_step_dev.argtypes = [P, P, P, P, P, I64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                        ctypes.c_float, P, ctypes.POINTER(LowpSegment), I, P]
+        L.gs_adam_step_ranges.argtypes = [P, P, P, P, P, I64, ctypes.POINTER(Range), I, ctypes.c_float,
+                                          ctypes.c_float, ctypes.c_float, ctypes.c_float, I64, P,
+                                          ctypes.POINTER(LowpSegment), I, P]
         L.gs_sync_status.argtypes = [P, P, ctypes.POINTER(ctypes.c_uint64)]
         L.gs_dssim_scratch_floats.argtypes = [ctypes.POINTER(View), I]
         L.gs_dssim_scratch_floats.restype = ctypes.c_size_t
@@ -441,6 +448,26 @@ class Context:
         _check_dev(step_dev, "step_dev", torch.int64, 1)
         self._ck(lib().gs_adam_step_dev(self.h, _ptr(param), _ptr(grad), _ptr(m), _ptr(v), param.numel(), float(lr),
                                         float(b1), float(b2), float(eps), _ptr(step_dev), segs, ns, _stream(stream)))
+
+    def adam_step_ranges(self, param, grad, m, v, ranges, lr, b1, b2, eps, step=0, step_dev=None, segments=(),
+                         stream=None):
+        """Adam over the element ranges [(begin, end), ...] of the flat buffers
+        only; the step count from step_dev (device int64, incremented) when
+        given, else the host step."""
+        rg = (Range * len(ranges))()
+        for k, (b, e) in enumerate(ranges):
+            rg[k].begin, rg[k].end = int(b), int(e)
+        segs = None
+        ns = len(segments)
+        if ns:
+            segs = (LowpSegment * ns)()
+            for k, (b, e, dst) in enumerate(segments):
+                segs[k].begin, segs[k].end, segs[k].dtype, segs[k].dst = int(b), int(e), _DTYPE[dst.dtype], dst.data_ptr()
+        if step_dev is not None:
+            _check_dev(step_dev, "step_dev", torch.int64, 1)
+        self._ck(lib().gs_adam_step_ranges(self.h, _ptr(param), _ptr(grad), _ptr(m), _ptr(v), param.numel(), rg,
+                                           len(ranges), float(lr), float(b1), float(b2), float(eps), int(step),
+                                           _ptr(step_dev), segs, ns, _stream(stream)))
 
     def calibrate_alu(self, stream=None):
         """Measured FP32 FMA throughput (TFLOP/s) and ex2 throughput (G/s) of this device."""

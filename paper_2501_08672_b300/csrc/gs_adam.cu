@@ -94,7 +94,101 @@ __global__ void k_adam_tail(float* __restrict__ p, const float* __restrict__ g, 
     }
 }
 
+// Adam over the union of up to 8 element ranges (the active rows of each
+// parameter group): float4 work over the ranges' aligned parts concatenated
+// (range r covers virtual float4 indices [pre4[r], pre4[r + 1])), and the
+// ranges' last 0-3 elements by the first threads.
+struct RangeTable {
+    long long begin4[8];    // first float4 of the range (its begin / 4)
+    long long pre4[9];      // prefix of the ranges' float4 counts
+    long long tail0[8];     // first element of the range's scalar tail
+    int tail_len[8];        // 0..3
+    int n;
+};
+
+__global__ void __launch_bounds__(256) k_adam_ranges(float* __restrict__ p, const float* __restrict__ g,
+                                                     float* __restrict__ m, float* __restrict__ v, RangeTable rt,
+                                                     float b1, float b2, float eps, float step_size,
+                                                     float inv_sqrt_bc2, SegTable st,
+                                                     const float2* __restrict__ coef) {
+    if (coef) {
+        const float2 c = *coef;
+        step_size = c.x;
+        inv_sqrt_bc2 = c.y;
+    }
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long n4 = rt.pre4[rt.n];
+    int r = 0;
+    for (long long i = tid; i < n4; i += stride) {
+        while (i >= rt.pre4[r + 1]) ++r;  // i only grows, so r does too
+        const long long q = rt.begin4[r] + (i - rt.pre4[r]);
+        float4 pp = reinterpret_cast<float4*>(p)[q], gg = reinterpret_cast<const float4*>(g)[q];
+        float4 mm = reinterpret_cast<float4*>(m)[q], vv = reinterpret_cast<float4*>(v)[q];
+        adam1(pp.x, gg.x, mm.x, vv.x, b1, b2, eps, step_size, inv_sqrt_bc2);
+        adam1(pp.y, gg.y, mm.y, vv.y, b1, b2, eps, step_size, inv_sqrt_bc2);
+        adam1(pp.z, gg.z, mm.z, vv.z, b1, b2, eps, step_size, inv_sqrt_bc2);
+        adam1(pp.w, gg.w, mm.w, vv.w, b1, b2, eps, step_size, inv_sqrt_bc2);
+        reinterpret_cast<float4*>(p)[q] = pp;
+        reinterpret_cast<float4*>(m)[q] = mm;
+        reinterpret_cast<float4*>(v)[q] = vv;
+        if (st.n) {
+            store_lowp(st, 4 * q + 0, pp.x);
+            store_lowp(st, 4 * q + 1, pp.y);
+            store_lowp(st, 4 * q + 2, pp.z);
+            store_lowp(st, 4 * q + 3, pp.w);
+        }
+    }
+    if (tid < 4 * rt.n) {  // range tid / 4, tail element tid % 4
+        const int rr = (int)(tid / 4), e = (int)(tid % 4);
+        if (e < rt.tail_len[rr]) {
+            const long long i = rt.tail0[rr] + e;
+            float pp = p[i], mm = m[i], vv = v[i];
+            adam1(pp, g[i], mm, vv, b1, b2, eps, step_size, inv_sqrt_bc2);
+            p[i] = pp;
+            m[i] = mm;
+            v[i] = vv;
+            if (st.n) store_lowp(st, i, pp);
+        }
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_adam_ranges(float* p, const float* g, float* m, float* v, const gs_range* ranges, int n_ranges,
+                               float b1, float b2, float eps, float step_size, float inv_sqrt_bc2,
+                               const gs_lowp_segment* segs, int n_segs, cudaStream_t s, Prof& pf,
+                               long long* step_dev, float lr, float2* coef, int sm_count) {
+    SegTable st{};
+    st.n = n_segs;
+    for (int k = 0; k < n_segs && k < 8; ++k) {
+        st.begin[k] = segs[k].begin;
+        st.end[k] = segs[k].end;
+        st.dst[k] = segs[k].dst;
+        st.dtype[k] = segs[k].dtype;
+    }
+    RangeTable rt{};
+    rt.n = n_ranges;
+    rt.pre4[0] = 0;
+    for (int k = 0; k < n_ranges; ++k) {
+        const long long len = ranges[k].end - ranges[k].begin;
+        rt.begin4[k] = ranges[k].begin / 4;
+        rt.pre4[k + 1] = rt.pre4[k] + len / 4;
+        rt.tail0[k] = ranges[k].begin + 4 * (len / 4);
+        rt.tail_len[k] = (int)(len % 4);
+    }
+    const int pi = pf.begin(GS_KF_ADAM, s, 1 + (step_dev != nullptr));
+    if (step_dev) k_adam_coef<<<1, 1, 0, s>>>(step_dev, lr, b1, b2, coef);
+    const long long n4 = rt.pre4[n_ranges];
+    long long blocks = (n4 + 255) / 256;
+    const long long cap = (long long)(sm_count > 0 ? sm_count : 148) * 8;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;  // the tails need one block
+    k_adam_ranges<<<(unsigned)blocks, 256, 0, s>>>(p, g, m, v, rt, b1, b2, eps, step_size, inv_sqrt_bc2, st,
+                                                   step_dev ? coef : nullptr);
+    pf.end(pi, s);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_adam(float* p, const float* g, float* m, float* v, long long n,
                         float b1, float b2, float eps, float step_size, float inv_sqrt_bc2,

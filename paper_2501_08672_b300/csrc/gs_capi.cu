@@ -880,6 +880,38 @@ int gs_adam_step_dev(gs_ctx* ctx, float* param, const float* grad, float* m, flo
     return e == cudaSuccess ? GS_OK : cuda_fail(ctx, e, "gs_adam_step_dev");
 }
 
+int gs_adam_step_ranges(gs_ctx* ctx, float* param, const float* grad, float* m, float* v, int64_t n,
+                        const gs_range* ranges, int n_ranges, float lr, float b1, float b2, float eps, int64_t step,
+                        int64_t* step_dev, const gs_lowp_segment* segs, int n_segs, gs_stream stream) {
+    if (!ctx) return GS_ERR_INVALID_ARG;
+    int rc = check_adam(ctx, param, grad, m, v, n, lr, b1, b2, eps, segs, n_segs);
+    if (rc) return rc;
+    if (!step_dev && step < 1) return fail(ctx, GS_ERR_INVALID_ARG, "step=%lld must be >= 1", (long long)step);
+    if (!ranges || n_ranges < 1 || n_ranges > 8)
+        return fail(ctx, GS_ERR_INVALID_ARG, "n_ranges=%d outside [1, 8] or ranges is NULL", n_ranges);
+    if (((reinterpret_cast<uintptr_t>(param) | reinterpret_cast<uintptr_t>(grad) | reinterpret_cast<uintptr_t>(m) |
+          reinterpret_cast<uintptr_t>(v)) & 15) != 0)
+        return fail(ctx, GS_ERR_INVALID_ARG, "Adam buffers must be 16-byte aligned");
+    for (int k = 0; k < n_ranges; ++k) {
+        if (ranges[k].begin < 0 || ranges[k].end < ranges[k].begin || ranges[k].end > n || ranges[k].begin % 4)
+            return fail(ctx, GS_ERR_INVALID_ARG, "range %d [%lld, %lld) invalid (begin a multiple of 4, end <= n)", k,
+                        (long long)ranges[k].begin, (long long)ranges[k].end);
+        for (int j = 0; j < k; ++j)
+            if (ranges[k].begin < ranges[j].end && ranges[j].begin < ranges[k].end)
+                return fail(ctx, GS_ERR_INVALID_ARG, "ranges %d and %d overlap", j, k);
+    }
+    DeviceGuard dg(ctx->device);
+    float step_size = 0.f, inv_sqrt_bc2 = 0.f;
+    if (!step_dev) {
+        step_size = (float)(lr / (1.0 - pow((double)b1, (double)step)));
+        inv_sqrt_bc2 = (float)(1.0 / sqrt(1.0 - pow((double)b2, (double)step)));
+    }
+    cudaError_t e = launch_adam_ranges(param, grad, m, v, ranges, n_ranges, b1, b2, eps, step_size, inv_sqrt_bc2,
+                                       segs, n_segs, reinterpret_cast<cudaStream_t>(stream), ctx->prof,
+                                       reinterpret_cast<long long*>(step_dev), lr, ctx->d_adam_coef, ctx->sm_count);
+    return e == cudaSuccess ? GS_OK : cuda_fail(ctx, e, "gs_adam_step_ranges");
+}
+
 int gs_sync_status(gs_ctx* ctx, gs_stream stream, uint64_t* pairs_needed) {
     if (!ctx) return GS_ERR_INVALID_ARG;
     DeviceGuard dg(ctx->device);

@@ -293,6 +293,10 @@ long long l1_partials_needed(const BatchParam& bp);
 long long l1_scratch_capacity();
 cudaError_t launch_l1_static(const BatchParam& bp, const float* rgb, const float* target, float* dL_drgb,
                              float* loss, cudaStream_t s);
+cudaError_t launch_adam_ranges(float* p, const float* g, float* m, float* v, const gs_range* ranges, int n_ranges,
+                               float b1, float b2, float eps, float step_size, float inv_sqrt_bc2,
+                               const gs_lowp_segment* segs, int n_segs, cudaStream_t s, Prof& pf,
+                               long long* step_dev, float lr, float2* coef, int sm_count);
 cudaError_t launch_adam(float* p, const float* g, float* m, float* v, long long n,
                         float b1, float b2, float eps, float step_size, float inv_sqrt_bc2,
                         const gs_lowp_segment* segs, int n_segs, cudaStream_t s, Prof& pf,

@@ -206,6 +206,10 @@ class GaussianWindow:
     def segments(self):
         return [(self.offsets[k], self.offsets[k] + self.sizes[k], self.lowp[k]) for k in self.lowp]
 
+    def active_ranges(self):
+        """Element ranges of the flat buffers that hold rows [0, n) of each group."""
+        return [(self.offsets[k], self.offsets[k] + self.n * int(np.prod(self.widths[k]))) for k in self.GROUPS]
+
     def numpy(self, use_render_copy=False):
         out = {}
         for k in self.GROUPS:
@@ -300,8 +304,8 @@ class WindowOptimizer:
     (1 - lambda) L1 + lambda (1 - SSIM)), backward to the Gaussians, Adam."""
 
     def __init__(self, params, views, targets, lr=1e-3, betas=(0.9, 0.999), eps=1e-8, device=0,
-                 tile_size=16, storage=None, ssim_lambda=0.0, **cfg):
-        self.win = GaussianWindow(params, device, storage)
+                 tile_size=16, storage=None, ssim_lambda=0.0, capacity=None, **cfg):
+        self.win = GaussianWindow(params, device, storage, capacity)
         self.r = Renderer(views, device, tile_size, **cfg)
         self.targets = targets
         self.ssim_lambda = float(ssim_lambda)
@@ -322,8 +326,12 @@ class WindowOptimizer:
         r.loss_and_grad(self.targets, self.ssim_lambda)
         r.backward(self._g, r.dL_drgb, grads=self._grads)
         w.step_count += 1
-        r.ctx.adam_step(w.flat, w.gflat, w.m, w.v, self.lr, self.betas[0], self.betas[1], self.eps,
-                        w.step_count, self._segs)
+        if w.capacity > w.n:  # spare rows (appends may be in flight there): Adam on the active rows only
+            r.ctx.adam_step_ranges(w.flat, w.gflat, w.m, w.v, w.active_ranges(), self.lr, self.betas[0],
+                                   self.betas[1], self.eps, step=w.step_count, segments=self._segs)
+        else:
+            r.ctx.adam_step(w.flat, w.gflat, w.m, w.v, self.lr, self.betas[0], self.betas[1], self.eps,
+                            w.step_count, self._segs)
         return r.loss
 
     def capture(self):
@@ -346,8 +354,13 @@ class WindowOptimizer:
                     r.forward(self._g, count=False)
                     r.loss_and_grad(self.targets, self.ssim_lambda)
                     r.backward(self._g, r.dL_drgb, grads=self._grads)
-                    r.ctx.adam_step_dev(w.flat, w.gflat, w.m, w.v, self.lr, self.betas[0], self.betas[1],
-                                        self.eps, self.step_dev, self._segs)
+                    if w.capacity > w.n:
+                        r.ctx.adam_step_ranges(w.flat, w.gflat, w.m, w.v, w.active_ranges(), self.lr,
+                                               self.betas[0], self.betas[1], self.eps, step_dev=self.step_dev,
+                                               segments=self._segs)
+                    else:
+                        r.ctx.adam_step_dev(w.flat, w.gflat, w.m, w.v, self.lr, self.betas[0], self.betas[1],
+                                            self.eps, self.step_dev, self._segs)
             except (RuntimeError, B.GsError) as e:
                 if attempt == 2:
                     raise
