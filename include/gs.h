@@ -80,7 +80,7 @@ typedef enum gs_status {
     GS_ERR_CUDA = -2,        /* a CUDA runtime call or launch failed */
     GS_ERR_OOM = -3,         /* context status block could not be allocated */
     GS_ERR_CAPACITY = -4,    /* more (Gaussian, tile) pairs than the workspace holds */
-    GS_ERR_TIMEOUT = -5,     /* reserved: a bounded device wait expired */
+    GS_ERR_TIMEOUT = -5,     /* a bounded device wait expired (latched, see gs_sync_status) */
     GS_ERR_NONFINITE = -6,   /* a camera or intrinsic value is not finite */
     GS_ERR_UNSUPPORTED = -7  /* option not built into this library */
 } gs_status;
@@ -357,7 +357,8 @@ GS_API int gs_l1_loss_noalloc(const gs_view* views, int n_views, const float* rg
                               size_t msg_len);
 
 /* Synchronises `stream`, returns and clears the latched device status
- * (GS_OK or GS_ERR_CAPACITY); pairs_needed (nullable, host) receives the
+ * (GS_OK, GS_ERR_CAPACITY, or GS_ERR_TIMEOUT when a bounded wait of the
+ * binning's single-pass scan expired and its result is unusable); pairs_needed (nullable, host) receives the
  * pair count of the last gs_bin on this context. */
 GS_API int gs_sync_status(gs_ctx* ctx, gs_stream stream, uint64_t* pairs_needed);
 

@@ -200,7 +200,7 @@ int make_layout(gs_ctx* ctx, const gs_config& cfg, const gs_view* views, int n_v
     W.pair_vals = take(sizeof(uint32_t) * (size_t)cap);
     L.pvals1 = take(sizeof(uint32_t) * (size_t)cap);
     L.hist = take(sizeof(uint32_t) * 256 * (size_t)(radix_tiles > 0 ? radix_tiles : 1));
-    L.hist_part = take(sizeof(uint32_t) * (size_t)(hist_parts + 1));
+    L.hist_part = take(sizeof(unsigned long long) * (size_t)(hist_parts + 2));  // look-back flags + ticket
     W.tile_ranges = take(sizeof(uint2) * (size_t)T);
     L.okeys0 = take(sizeof(uint32_t) * (size_t)T);
     L.okeys1 = take(sizeof(uint32_t) * (size_t)T);

@@ -92,7 +92,7 @@ struct WsPtrs {
     uint32_t* pkeys[2];      // [cap]
     uint32_t* pvals[2];      // [cap]
     uint32_t* hist;          // [256 * radix tiles]
-    uint32_t* hist_part;     // [radix scan blocks]
+    uint32_t* hist_part;     // look-back scan: [radix scan chunks + 1] 64-bit flags, then the ticket
     uint2* ranges;           // [T]
     uint32_t* okeys[2];      // [T] tile-order keys
     uint32_t* ovals[2];      // [T] tiles, longest list first (buffer 1 after the sort)

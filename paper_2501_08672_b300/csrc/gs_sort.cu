@@ -56,13 +56,18 @@ __device__ __forceinline__ uint32_t lane_lt_mask() {
     return m;
 }
 
+// Also zeroes `nzero` 64-bit words at `zero` (block 0): the look-back flags
+// and ticket of the scan that follows, without a separate memset.
 __global__ void __launch_bounds__(kRadixThreads) k_radix_upsweep(const uint32_t* __restrict__ keys,
                                                                  unsigned long long n_host,
                                                                  const unsigned long long* n_dev,
                                                                  int shift, int bits,
-                                                                 uint32_t* __restrict__ hist) {
+                                                                 uint32_t* __restrict__ hist,
+                                                                 unsigned long long* __restrict__ zero, int nzero) {
     __shared__ uint32_t wh[kRadixWarps][256];
     const int t = threadIdx.x, w = t >> 5;
+    if (blockIdx.x == 0)
+        for (int i = t; i < nzero; i += kRadixThreads) zero[i] = 0ull;
 #pragma unroll
     for (int k = 0; k < kRadixWarps; ++k) wh[k][t] = 0u;
     __syncthreads();
@@ -263,6 +268,101 @@ __global__ void __launch_bounds__(1024) k_u32_apply(uint32_t* __restrict__ a, lo
     }
     __syncthreads();
     uint32_t run = part[blockIdx.x] + (w > 0 ? s_w[w - 1] : 0u) + x - s;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        if (base + k < n) {
+            a[base + k] = run;
+            run += v[k];
+        }
+}
+
+// Device-wide exclusive scan of a u32 array in place in one pass (decoupled
+// look-back): each block takes the next 4096-entry chunk from a ticket (so
+// every chunk before it belongs to a block that has started), publishes the
+// chunk's sum, and one warp walks back over the flags of the 32 chunks before
+// it at a time, adding sums until it meets a published inclusive prefix.
+// A flag word packs the status (bits 62-63: 0 not ready, 1 chunk sum, 2
+// inclusive prefix) with the 32-bit value; the words and the ticket are
+// zeroed before each scan.  Waits are bounded: after kLookbackPolls polls
+// without progress the block latches GS_ERR_TIMEOUT in the status word and
+// finishes with the sums it has (the result is then unusable, and the host
+// learns it from gs_sync_status).
+constexpr int kLookbackPolls = 1 << 20;
+
+__global__ void __launch_bounds__(1024) k_u32_scan_lookback(uint32_t* __restrict__ a, long long n,
+                                                            unsigned long long* flags, unsigned int* ticket,
+                                                            unsigned int* status) {
+    __shared__ uint32_t s_w[32];
+    __shared__ unsigned int s_chunk;
+    __shared__ uint32_t s_prefix;
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    if (t == 0) s_chunk = atomicAdd(ticket, 1u);
+    __syncthreads();
+    const long long chunk = s_chunk;
+    const long long base = chunk * kU32ScanChunk + (long long)t * 4;
+    uint32_t v[4], s = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        v[k] = base + k < n ? a[base + k] : 0u;
+        s += v[k];
+    }
+    uint32_t x = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_w[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t y = s_w[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t z = __shfl_up_sync(0xffffffffu, y, o);
+            if (lane >= o) y += z;
+        }
+        s_w[lane] = y;
+        const uint32_t agg = __shfl_sync(0xffffffffu, y, 31);
+        volatile unsigned long long* vf = flags;
+        if (chunk == 0) {
+            if (lane == 0) {
+                vf[0] = (2ull << 62) | agg;
+                s_prefix = 0;
+            }
+        } else {
+            if (lane == 0) vf[chunk] = (1ull << 62) | agg;
+            uint32_t excl = 0;
+            long long j = chunk - 1;  // the window is chunks j - 31 .. j
+            for (;;) {
+                const long long idx = j - lane;
+                unsigned long long f = 2ull << 62;  // before chunk 0: a prefix of 0
+                if (idx >= 0) f = vf[idx];
+                int polls = 0;
+                while (__any_sync(0xffffffffu, (f >> 62) == 0)) {
+                    if (++polls > kLookbackPolls) {
+                        if (lane == 0) atomicCAS(status, 0u, (unsigned int)(-GS_ERR_TIMEOUT));
+                        f = (2ull << 62) | (f & 0xFFFFFFFFull);  // give up: treat as a prefix
+                        break;
+                    }
+                    if ((f >> 62) == 0) f = vf[idx];
+                }
+                const uint32_t pre = __ballot_sync(0xffffffffu, (f >> 62) == 2);
+                const int stop = pre ? __ffs(pre) - 1 : 31;  // nearest chunk holding a prefix
+                uint32_t val = lane <= stop ? (uint32_t)(f & 0xFFFFFFFFull) : 0u;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) val += __shfl_xor_sync(0xffffffffu, val, o);
+                excl += val;
+                if (pre) break;
+                j -= 32;
+            }
+            if (lane == 0) {
+                vf[chunk] = (2ull << 62) | (uint32_t)(excl + agg);
+                s_prefix = excl;
+            }
+        }
+    }
+    __syncthreads();
+    uint32_t run = s_prefix + (w > 0 ? s_w[w - 1] : 0u) + x - s;
 #pragma unroll
     for (int k = 0; k < 4; ++k)
         if (base + k < n) {
@@ -707,7 +807,7 @@ int radix_blocks(unsigned long long n_host) {
 // between buffer 0 and 1; *result_buf receives the buffer holding the result.
 cudaError_t radix_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, const WsPtrs& ws,
                        unsigned long long n_host, const unsigned long long* n_dev, int key_bits,
-                       int* result_buf, cudaStream_t s, Prof& pf) {
+                       int* result_buf, unsigned int* status, cudaStream_t s, Prof& pf) {
     const int passes = key_bits <= 0 ? 0 : (key_bits + 7) / 8;
     const int dbits = passes ? (key_bits + passes - 1) / passes : 0;
     const int nblk = radix_blocks(n_host);
@@ -720,15 +820,18 @@ cudaError_t radix_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, c
     for (int p = 0; p < passes && nblk > 0; ++p) {
         const int shift = p * dbits;
         const int bits = key_bits - shift < dbits ? key_bits - shift : dbits;
-        k_radix_upsweep<<<nblk, kRadixThreads, 0, s>>>(kin, n_host, n_dev, shift, bits, ws.hist);
-        if (nh <= kU32SingleScanMax) {
+        // flags of the nparts chunks, then the ticket, zeroed by the upsweep for the look-back scan
+        unsigned long long* flags = reinterpret_cast<unsigned long long*>(ws.hist_part);
+        const bool single = nh <= kU32SingleScanMax;
+        k_radix_upsweep<<<nblk, kRadixThreads, 0, s>>>(kin, n_host, n_dev, shift, bits, ws.hist, flags,
+                                                       single ? 0 : nparts + 1);
+        if (single) {
             k_u32_scan_single<<<1, 1024, 0, s>>>(ws.hist, nh);
             pf.count(3);
         } else {
-            pf.count(5);
-            k_u32_reduce<<<nparts, 1024, 0, s>>>(ws.hist, nh, ws.hist_part);
-            k_u32_top<<<1, 1024, 0, s>>>(ws.hist_part, nparts);
-            k_u32_apply<<<nparts, 1024, 0, s>>>(ws.hist, nh, ws.hist_part);
+            pf.count(3);
+            k_u32_scan_lookback<<<nparts, 1024, 0, s>>>(ws.hist, nh, flags,
+                                                        reinterpret_cast<unsigned int*>(flags + nparts), status);
         }
         k_radix_downsweep<<<nblk, kRadixThreads, 0, s>>>(kin, vin, kout, vout, n_host, n_dev, shift, bits, ws.hist);
         uint32_t* tk = kin; kin = kout; kout = tk;
@@ -750,8 +853,8 @@ cudaError_t launch_bin(const BatchParam& bp, WsPtrs& ws, unsigned int* status,
     //    dvals[0]), then the runs of equal high words by (low word, record)
     int pi = pf.begin(GS_KF_DEPTH_SORT, s, 1);  // the fix-up; radix_sort counts its own launches
     int dbuf = 0;
-    e = radix_sort(ws.dhi, ws.dvals[0], ws.dkeys[1], ws.dvals[1], ws, (unsigned long long)M, nullptr, 32, &dbuf, s,
-                   pf);
+    e = radix_sort(ws.dhi, ws.dvals[0], ws.dkeys[1], ws.dvals[1], ws, (unsigned long long)M, nullptr, 32, &dbuf,
+                   status, s, pf);
     if (e != cudaSuccess) return e;
     uint32_t* sorted_hi = dbuf ? ws.dkeys[1] : ws.dhi;
     k_depth_fixup<<<(unsigned)((M + 255) / 256), 256, 0, s>>>(sorted_hi, ws.dvals[dbuf], ws.dkeys[0], M);
@@ -777,7 +880,7 @@ cudaError_t launch_bin(const BatchParam& bp, WsPtrs& ws, unsigned int* status,
     int pbuf = 0;
     pi = pf.begin(GS_KF_TILE_SORT, s, 0);
     e = radix_sort(ws.pkeys[0], ws.pvals[0], ws.pkeys[1], ws.pvals[1], ws, (unsigned long long)ws.cap,
-                   ws.counters, tile_bits, &pbuf, s, pf);
+                   ws.counters, tile_bits, &pbuf, status, s, pf);
     pf.end(pi, s);
     if (e != cudaSuccess) return e;
     ws.sorted_buf = pbuf;
@@ -789,7 +892,7 @@ cudaError_t launch_bin(const BatchParam& bp, WsPtrs& ws, unsigned int* status,
     k_tile_keys<<<(bp.total_tiles + 255) / 256, 256, 0, s>>>(ws.ranges, bp.total_tiles, ws.okeys[0], ws.ovals[0]);
     int obuf = 0;
     e = radix_sort(ws.okeys[0], ws.ovals[0], ws.okeys[1], ws.ovals[1], ws, (unsigned long long)bp.total_tiles,
-                   nullptr, 8, &obuf, s, pf);
+                   nullptr, 8, &obuf, status, s, pf);
     pf.end(pi, s);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
