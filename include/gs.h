@@ -362,6 +362,17 @@ GS_API int gs_l1_loss_noalloc(const gs_view* views, int n_views, const float* rg
  * pair count of the last gs_bin on this context. */
 GS_API int gs_sync_status(gs_ctx* ctx, gs_stream stream, uint64_t* pairs_needed);
 
+/* Failure-detection self-test.  Runs the binning's single-pass scan on two
+ * chunks of `scratch` (device, gs_selftest_wait_scratch_bytes() bytes,
+ * 256-byte aligned, caller-owned) with its ticket started past the first
+ * chunk, so the one block waits for a flag that nothing sets; its bounded
+ * wait expires (about a second at most) and the device latches
+ * GS_ERR_TIMEOUT, which the next gs_sync_status returns and clears.  Nothing
+ * faults and the context stays usable.  Errors: GS_ERR_INVALID_ARG,
+ * GS_ERR_CUDA. */
+GS_API size_t gs_selftest_wait_scratch_bytes(void);
+GS_API int gs_selftest_bounded_wait(gs_ctx* ctx, void* scratch, gs_stream stream);
+
 /* Kernel families, for profiling (bit i of a mask selects family i). */
 typedef enum gs_kernel_family {
     GS_KF_PROJECT = 0,     /* a1 projection */

@@ -35,7 +35,8 @@ EXPORTED = ["gs_config_default", "gs_version", "gs_context_create", "gs_context_
             "gs_profile_enable", "gs_profile_collect", "gs_launch_count", "gs_adam_step_dev",
             "gs_l1_loss_noalloc", "gs_calibrate_alu", "gs_pose_normal_scratch", "gs_pose_normal",
             "gs_window_scratch_bytes", "gs_window_compact", "gs_window_remove", "gs_window_gather", "gs_window_clear",
-            "gs_sh_init_bilinear", "gs_dssim_scratch_floats", "gs_dssim_loss", "gs_adam_step_ranges"]
+            "gs_sh_init_bilinear", "gs_dssim_scratch_floats", "gs_dssim_loss", "gs_adam_step_ranges",
+            "gs_selftest_wait_scratch_bytes", "gs_selftest_bounded_wait"]
 
 KERNEL_FAMILIES = ["project", "depth_sort", "tile_scan", "emit", "tile_sort", "ranges", "raster_fwd", "l1",
                    "raster_bwd", "project_bwd", "adam", "pose_normal", "window", "ssim"]
@@ -140,6 +141,9 @@ def lib():
                                           ctypes.c_float, ctypes.c_float, ctypes.c_float, I64, P,
                                           ctypes.POINTER(LowpSegment), I, P]
         L.gs_sync_status.argtypes = [P, P, ctypes.POINTER(ctypes.c_uint64)]
+        L.gs_selftest_wait_scratch_bytes.argtypes = []
+        L.gs_selftest_wait_scratch_bytes.restype = ctypes.c_size_t
+        L.gs_selftest_bounded_wait.argtypes = [P, P, P]
         L.gs_dssim_scratch_floats.argtypes = [ctypes.POINTER(View), I]
         L.gs_dssim_scratch_floats.restype = ctypes.c_size_t
         L.gs_dssim_loss.argtypes = [P, ctypes.POINTER(View), I, P, P, ctypes.c_float, P, P, P, P]
@@ -468,6 +472,13 @@ class Context:
         self._ck(lib().gs_adam_step_ranges(self.h, _ptr(param), _ptr(grad), _ptr(m), _ptr(v), param.numel(), rg,
                                            len(ranges), float(lr), float(b1), float(b2), float(eps), int(step),
                                            _ptr(step_dev), segs, ns, _stream(stream)))
+
+    def selftest_bounded_wait(self, stream=None):
+        """Makes the binning scan's bounded wait expire (see gs.h); the next
+        sync_status returns GS_ERR_TIMEOUT."""
+        scratch = torch.empty(int(lib().gs_selftest_wait_scratch_bytes()), dtype=torch.uint8, device="cuda")
+        self._ck(lib().gs_selftest_bounded_wait(self.h, _ptr(scratch), _stream(stream)))
+        return scratch  # kept alive by the caller until the stream has run
 
     def calibrate_alu(self, stream=None):
         """Measured FP32 FMA throughput (TFLOP/s) and ex2 throughput (G/s) of this device."""

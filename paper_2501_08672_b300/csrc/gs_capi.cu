@@ -912,6 +912,17 @@ int gs_adam_step_ranges(gs_ctx* ctx, float* param, const float* grad, float* m, 
     return e == cudaSuccess ? GS_OK : cuda_fail(ctx, e, "gs_adam_step_ranges");
 }
 
+size_t gs_selftest_wait_scratch_bytes(void) { return selftest_wait_scratch_bytes(); }
+
+int gs_selftest_bounded_wait(gs_ctx* ctx, void* scratch, gs_stream stream) {
+    if (!ctx) return GS_ERR_INVALID_ARG;
+    if (!scratch || reinterpret_cast<uintptr_t>(scratch) % 256)
+        return fail(ctx, GS_ERR_INVALID_ARG, "scratch is NULL or not 256-byte aligned");
+    DeviceGuard dg(ctx->device);
+    const cudaError_t e = launch_selftest_wait(scratch, ctx->d_status, reinterpret_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? GS_OK : cuda_fail(ctx, e, "gs_selftest_bounded_wait");
+}
+
 int gs_sync_status(gs_ctx* ctx, gs_stream stream, uint64_t* pairs_needed) {
     if (!ctx) return GS_ERR_INVALID_ARG;
     DeviceGuard dg(ctx->device);

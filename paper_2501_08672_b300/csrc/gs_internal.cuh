@@ -257,6 +257,8 @@ cudaError_t launch_bin(const BatchParam& bp, WsPtrs& ws, unsigned int* status,
                        unsigned long long* status_pairs, cudaStream_t s, Prof& pf);
 bool raster_variant_exists(int ts, int ppt, int batch);
 cudaError_t measure_alu(int sm_count, float* sink, cudaStream_t s, double* ffma_tflops, double* ex2_gops);
+size_t selftest_wait_scratch_bytes();
+cudaError_t launch_selftest_wait(void* scratch, unsigned int* status, cudaStream_t s);
 size_t ssim_scratch_floats(const BatchParam& bp);
 cudaError_t launch_ssim(const BatchParam& bp, const SsimParam& sp, const float* rgb, const float* target,
                         float* scratch, float* dL_drgb, float* loss, cudaStream_t s, Prof& pf);

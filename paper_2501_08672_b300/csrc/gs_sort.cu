@@ -799,6 +799,28 @@ __global__ void __launch_bounds__(256) k_ranges(const uint32_t* __restrict__ key
     }
 }
 
+__global__ void k_set_u32(unsigned int* p, unsigned int v) { *p = v; }
+
+}  // namespace
+
+size_t selftest_wait_scratch_bytes() { return sizeof(uint32_t) * 2 * kU32ScanChunk + 4 * sizeof(unsigned long long); }
+
+// The scan's bounded wait made to expire: two chunks whose ticket starts at 1,
+// so the one block takes chunk 1 and waits for chunk 0's flag, which nothing
+// sets; after its poll limit it latches GS_ERR_TIMEOUT and finishes.
+cudaError_t launch_selftest_wait(void* scratch, unsigned int* status, cudaStream_t s) {
+    uint32_t* a = static_cast<uint32_t*>(scratch);
+    unsigned long long* flags = reinterpret_cast<unsigned long long*>(a + 2 * kU32ScanChunk);
+    cudaError_t e = cudaMemsetAsync(scratch, 0, selftest_wait_scratch_bytes(), s);
+    if (e != cudaSuccess) return e;
+    k_set_u32<<<1, 1, 0, s>>>(reinterpret_cast<unsigned int*>(flags + 2), 1u);
+    k_u32_scan_lookback<<<1, 1024, 0, s>>>(a, 2 * kU32ScanChunk, flags, reinterpret_cast<unsigned int*>(flags + 2),
+                                          status);
+    return cudaGetLastError();
+}
+
+namespace {
+
 int radix_blocks(unsigned long long n_host) {
     return (int)((n_host + kRTile - 1) / kRTile);
 }

@@ -511,6 +511,30 @@ def test_capacity_overflow_is_reported_and_recovered():
     assert rc == B.GS_OK
 
 
+def test_bounded_wait_expires_and_is_reported(orc):
+    """Failure detection without a fault: the binning scan's wait on a flag
+    that nothing sets runs out, the device latches GS_ERR_TIMEOUT, the host
+    reads it once, and the context renders correctly afterwards."""
+    import time
+    p = scenes.frustum_scene(1200, seed=14)
+    views = [scenes.identity_view(96, 64, 80.0, 0, 1200)]
+    win = GaussianWindow(p, 0)
+    r = Renderer(views, 0, 16)
+    t0 = time.perf_counter()
+    keep = r.ctx.selftest_bounded_wait()
+    rc, _ = r.ctx.sync_status()
+    elapsed = time.perf_counter() - t0
+    del keep
+    assert rc == B.GS_ERR_TIMEOUT
+    assert elapsed < 5.0
+    rc, _ = r.ctx.sync_status()
+    assert rc == B.GS_OK
+    r.forward(win.struct())
+    torch.cuda.synchronize()
+    compare_images(orc.render_view(p, views[0]), r.images()[0].cpu().numpy(),
+                   B.unpack_images(r.T, views, 1)[0].cpu().numpy())
+
+
 def test_invalid_arguments_are_rejected():
     ctx = B.Context(0)
     v = B.make_views([scenes.identity_view(64, 48, 50.0, 0, 10)])
