@@ -39,6 +39,8 @@ __device__ __forceinline__ float adam1(float& p, float g, float& m, float& v, fl
 // Step counter kept on the device (graph replays advance it): increments the
 // count and stores lr / (1 - b1^t) and 1 / sqrt(1 - b2^t) for the Adam launch.
 __global__ void k_adam_coef(long long* step, float lr, float b1, float b2, float2* coef) {
+    pdl_wait();
+    pdl_trigger();
     const long long t = ++(*step);
     const double bc1 = 1.0 - pow((double)b1, (double)t);
     const double bc2 = 1.0 - pow((double)b2, (double)t);
@@ -50,6 +52,8 @@ __global__ void __launch_bounds__(256) k_adam4(float4* __restrict__ p, const flo
                                                long long n4, float b1, float b2, float eps,
                                                float step_size, float inv_sqrt_bc2, SegTable st,
                                                const float2* __restrict__ coef) {
+    pdl_wait();
+    pdl_trigger();
     if (coef) {
         const float2 c = *coef;
         step_size = c.x;
@@ -78,6 +82,8 @@ __global__ void k_adam_tail(float* __restrict__ p, const float* __restrict__ g, 
                             float* __restrict__ v, long long start, long long n, float b1, float b2,
                             float eps, float step_size, float inv_sqrt_bc2, SegTable st,
                             const float2* __restrict__ coef) {
+    pdl_wait();
+    pdl_trigger();
     if (coef) {
         const float2 c = *coef;
         step_size = c.x;
@@ -111,6 +117,8 @@ __global__ void __launch_bounds__(256) k_adam_ranges(float* __restrict__ p, cons
                                                      float b1, float b2, float eps, float step_size,
                                                      float inv_sqrt_bc2, SegTable st,
                                                      const float2* __restrict__ coef) {
+    pdl_wait();
+    pdl_trigger();
     if (coef) {
         const float2 c = *coef;
         step_size = c.x;
@@ -178,13 +186,13 @@ cudaError_t launch_adam_ranges(float* p, const float* g, float* m, float* v, con
         rt.tail_len[k] = (int)(len % 4);
     }
     const int pi = pf.begin(GS_KF_ADAM, s, 1 + (step_dev != nullptr));
-    if (step_dev) k_adam_coef<<<1, 1, 0, s>>>(step_dev, lr, b1, b2, coef);
+    if (step_dev) pdl_launch(k_adam_coef, 1, 1, 0, s, step_dev, lr, b1, b2, coef);
     const long long n4 = rt.pre4[n_ranges];
     long long blocks = (n4 + 255) / 256;
     const long long cap = (long long)(sm_count > 0 ? sm_count : 148) * 8;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;  // the tails need one block
-    k_adam_ranges<<<(unsigned)blocks, 256, 0, s>>>(p, g, m, v, rt, b1, b2, eps, step_size, inv_sqrt_bc2, st,
+    pdl_launch(k_adam_ranges, (unsigned)blocks, 256, 0, s, p, g, m, v, rt, b1, b2, eps, step_size, inv_sqrt_bc2, st,
                                                    step_dev ? coef : nullptr);
     pf.end(pi, s);
     return cudaGetLastError();
@@ -206,7 +214,7 @@ cudaError_t launch_adam(float* p, const float* g, float* m, float* v, long long 
                            reinterpret_cast<uintptr_t>(m) | reinterpret_cast<uintptr_t>(v)) & 15) == 0;
     long long n4 = aligned ? n / 4 : 0;
     const int pi = pf.begin(GS_KF_ADAM, s, (n4 > 0) + (4 * n4 < n) + (step_dev != nullptr));
-    if (step_dev) k_adam_coef<<<1, 1, 0, s>>>(step_dev, lr, b1, b2, coef);
+    if (step_dev) pdl_launch(k_adam_coef, 1, 1, 0, s, step_dev, lr, b1, b2, coef);
     const float2* cf = step_dev ? coef : nullptr;
     if (n4 > 0) {
         int dev = 0, sms = 148;
@@ -215,14 +223,14 @@ cudaError_t launch_adam(float* p, const float* g, float* m, float* v, long long 
         long long blocks = (n4 + 255) / 256;
         const long long cap = (long long)sms * 8;
         if (blocks > cap) blocks = cap;
-        k_adam4<<<(unsigned)blocks, 256, 0, s>>>(reinterpret_cast<float4*>(p), reinterpret_cast<const float4*>(g),
+        pdl_launch(k_adam4, (unsigned)blocks, 256, 0, s, reinterpret_cast<float4*>(p), reinterpret_cast<const float4*>(g),
                                                  reinterpret_cast<float4*>(m), reinterpret_cast<float4*>(v), n4, b1,
                                                  b2, eps, step_size, inv_sqrt_bc2, st, cf);
     }
     if (4 * n4 < n) {
         const long long rest = n - 4 * n4;
         const long long blocks = rest < 256 * 1184 ? (rest + 255) / 256 : 1184;
-        k_adam_tail<<<(unsigned)blocks, 256, 0, s>>>(p, g, m, v, 4 * n4, n, b1, b2, eps, step_size,
+        pdl_launch(k_adam_tail, (unsigned)blocks, 256, 0, s, p, g, m, v, 4 * n4, n, b1, b2, eps, step_size,
                                                      inv_sqrt_bc2, st, cf);
     }
     pf.end(pi, s);

@@ -8,6 +8,8 @@
 
 #include "../../include/gs.h"
 
+#include <utility>
+
 namespace gsb {
 
 constexpr int kMaxViews = GS_MAX_VIEWS;
@@ -225,6 +227,34 @@ __device__ __forceinline__ bool footrows_span(const FootRows& f, int ty, int ts,
     *a = ta;
     *b = tb;
     return true;
+}
+
+// ---- programmatic dependent launch ----------------------------------------
+//
+// Every kernel of the library starts with pdl_wait() and pdl_trigger() and is
+// launched by pdl_launch with programmatic stream serialization, so in a
+// stream (and in a captured graph) the next kernel is launched while this
+// one drains and its blocks wait in pdl_wait() until this grid has completed
+// and its memory is visible.  The wait comes first, before any early return:
+// a kernel's completion then implies the completion of everything before it
+// in the stream.  Without a programmatic dependency both are no-ops.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline void pdl_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args&&... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);  // errors surface via cudaGetLastError
 }
 
 // ---- host-side launch accounting and optional event timing ---------------

@@ -242,6 +242,8 @@ __device__ __forceinline__ uint32_t ordered_bits(float x) {
 template <int D>
 __global__ void __launch_bounds__(256) k_project(const __grid_constant__ BatchParam bp, GaussPtrs g,
                                                  RenderConst rc, WsPtrs ws) {
+    pdl_wait();
+    pdl_trigger();
     const ViewParam& V = bp.v[blockIdx.y];
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long cnt = V.g_end - V.g_begin;
@@ -356,6 +358,8 @@ __global__ void __launch_bounds__(256) k_project_bwd(const __grid_constant__ Bat
                                                      GaussPtrs g, RenderConst rc, WsPtrs ws,
                                                      GradPtrs gr, int want_params, int want_pose,
                                                      int pose_blocks) {
+    pdl_wait();
+    pdl_trigger();
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const bool live = i < g.n;
     constexpr int K = (D + 1) * (D + 1);
@@ -550,6 +554,8 @@ __global__ void __launch_bounds__(256) k_project_bwd(const __grid_constant__ Bat
 }
 
 __global__ void k_pose_finish(const float* partials, int nblocks, int n_views, float* dL_dpose) {
+    pdl_wait();
+    pdl_trigger();
     // one warp per (view, component): fixed-order sum for determinism
     const int item = blockIdx.x;
     if (item >= n_views * 6) return;
@@ -576,6 +582,8 @@ __global__ void k_pose_finish(const float* partials, int nblocks, int n_views, f
 template <int D>
 __global__ void __launch_bounds__(256) k_pose_tangents(const __grid_constant__ BatchParam bp, GaussPtrs g,
                                                        RenderConst rc, WsPtrs ws, float4* __restrict__ tan) {
+    pdl_wait();
+    pdl_trigger();
     const ViewParam& V = bp.v[blockIdx.y];
     const long long k0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long cnt = V.g_end - V.g_begin;
@@ -663,10 +671,10 @@ cudaError_t launch_project(const BatchParam& bp, const GaussPtrs& g, const Rende
     dim3 grid((unsigned)((bp.max_count + 255) / 256), (unsigned)bp.n_views);
     const int pi = pf.begin(GS_KF_PROJECT, s);
     switch (g.sh_degree) {
-        case 0: k_project<0><<<grid, 256, 0, s>>>(bp, g, rc, ws); break;
-        case 1: k_project<1><<<grid, 256, 0, s>>>(bp, g, rc, ws); break;
-        case 2: k_project<2><<<grid, 256, 0, s>>>(bp, g, rc, ws); break;
-        default: k_project<3><<<grid, 256, 0, s>>>(bp, g, rc, ws); break;
+        case 0: pdl_launch(k_project<0>, grid, 256, 0, s, bp, g, rc, ws); break;
+        case 1: pdl_launch(k_project<1>, grid, 256, 0, s, bp, g, rc, ws); break;
+        case 2: pdl_launch(k_project<2>, grid, 256, 0, s, bp, g, rc, ws); break;
+        default: pdl_launch(k_project<3>, grid, 256, 0, s, bp, g, rc, ws); break;
     }
     pf.end(pi, s);
     return cudaGetLastError();
@@ -687,12 +695,12 @@ cudaError_t launch_project_bwd(const BatchParam& bp, const GaussPtrs& g, const R
     const int pi = pf.begin(GS_KF_PROJECT_BWD, s, dL_dpose ? 2 : 1);
     const int wp = grads != nullptr, wq = dL_dpose != nullptr;
     switch (g.sh_degree) {
-        case 0: k_project_bwd<0><<<nblk, 256, 0, s>>>(bp, g, rc, ws, gr, wp, wq, pose_blocks); break;
-        case 1: k_project_bwd<1><<<nblk, 256, 0, s>>>(bp, g, rc, ws, gr, wp, wq, pose_blocks); break;
-        case 2: k_project_bwd<2><<<nblk, 256, 0, s>>>(bp, g, rc, ws, gr, wp, wq, pose_blocks); break;
-        default: k_project_bwd<3><<<nblk, 256, 0, s>>>(bp, g, rc, ws, gr, wp, wq, pose_blocks); break;
+        case 0: pdl_launch(k_project_bwd<0>, nblk, 256, 0, s, bp, g, rc, ws, gr, wp, wq, pose_blocks); break;
+        case 1: pdl_launch(k_project_bwd<1>, nblk, 256, 0, s, bp, g, rc, ws, gr, wp, wq, pose_blocks); break;
+        case 2: pdl_launch(k_project_bwd<2>, nblk, 256, 0, s, bp, g, rc, ws, gr, wp, wq, pose_blocks); break;
+        default: pdl_launch(k_project_bwd<3>, nblk, 256, 0, s, bp, g, rc, ws, gr, wp, wq, pose_blocks); break;
     }
-    if (dL_dpose) k_pose_finish<<<bp.n_views * 6, 32, 0, s>>>(ws.partials, pose_blocks, bp.n_views, dL_dpose);
+    if (dL_dpose) pdl_launch(k_pose_finish, bp.n_views * 6, 32, 0, s, ws.partials, pose_blocks, bp.n_views, dL_dpose);
     pf.end(pi, s);
     return cudaGetLastError();
 }
@@ -703,10 +711,10 @@ cudaError_t launch_pose_tangents(const BatchParam& bp, const GaussPtrs& g, const
     dim3 grid((unsigned)((bp.max_count + 255) / 256), (unsigned)bp.n_views);
     const int pi = pf.begin(GS_KF_POSE_NORMAL, s);
     switch (g.sh_degree) {
-        case 0: k_pose_tangents<0><<<grid, 256, 0, s>>>(bp, g, rc, ws, tangents); break;
-        case 1: k_pose_tangents<1><<<grid, 256, 0, s>>>(bp, g, rc, ws, tangents); break;
-        case 2: k_pose_tangents<2><<<grid, 256, 0, s>>>(bp, g, rc, ws, tangents); break;
-        default: k_pose_tangents<3><<<grid, 256, 0, s>>>(bp, g, rc, ws, tangents); break;
+        case 0: pdl_launch(k_pose_tangents<0>, grid, 256, 0, s, bp, g, rc, ws, tangents); break;
+        case 1: pdl_launch(k_pose_tangents<1>, grid, 256, 0, s, bp, g, rc, ws, tangents); break;
+        case 2: pdl_launch(k_pose_tangents<2>, grid, 256, 0, s, bp, g, rc, ws, tangents); break;
+        default: pdl_launch(k_pose_tangents<3>, grid, 256, 0, s, bp, g, rc, ws, tangents); break;
     }
     pf.end(pi, s);
     return cudaGetLastError();

@@ -94,6 +94,8 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_render_fwd(const __grid_const
                                                               float* __restrict__ T_final,
                                                               uint32_t* __restrict__ n_contrib,
                                                               uint32_t* __restrict__ n_used) {
+    pdl_wait();
+    pdl_trigger();
     // Each warp walks the tile's list on its own: per step every lane fetches
     // Q records, the records whose footprint box reaches the warp's pixels
     // are compacted (in list order) into the warp's shared slots, and the
@@ -248,6 +250,8 @@ __global__ void __launch_bounds__(TS * TS / PPT, bwd_min_blocks<TS * TS / PPT, P
                                                               const uint32_t* __restrict__ n_contrib,
                                                               const float* __restrict__ dL_drgb,
                                                               float* __restrict__ grad2d) {
+    pdl_wait();
+    pdl_trigger();
     // Each warp walks the list on its own, back to front from its deepest
     // contributor, fetching Q records per lane per step and compacting the
     // ones whose footprint box reaches its pixels (as in the forward).  No
@@ -441,6 +445,8 @@ __global__ void __launch_bounds__(kL1Threads) k_l1(const __grid_constant__ Batch
                                                    const float* __restrict__ target,
                                                    float* __restrict__ dL_drgb,
                                                    float* __restrict__ partials) {
+    pdl_wait();
+    pdl_trigger();
     const ViewParam& V = bp.v[blockIdx.y];
     const long long n = 3ll * V.W * V.H;
     const float scale = 1.f / ((float)n * (float)bp.n_views);
@@ -468,6 +474,8 @@ __global__ void __launch_bounds__(kL1Threads) k_l1(const __grid_constant__ Batch
 }
 
 __global__ void k_l1_finish(const float* __restrict__ partials, int n, float* __restrict__ loss) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ float sw[32];
     float s = 0.f;
     for (int i = threadIdx.x; i < n; i += blockDim.x) s += partials[i];
@@ -510,6 +518,8 @@ __global__ void __launch_bounds__(TS * TS) k_render_pose_normal(const __grid_con
                                                                 const float* __restrict__ target,
                                                                 float* __restrict__ partials,
                                                                 float* __restrict__ H_pix) {
+    pdl_wait();
+    pdl_trigger();
     constexpr int NT = TS * TS;
     constexpr int NW = NT / 32;
     __shared__ float4 s_a[NW][kPNBatch];
@@ -662,6 +672,8 @@ __global__ void __launch_bounds__(TS * TS) k_render_pose_normal(const __grid_con
 __global__ void __launch_bounds__(256) k_pose_normal_finish(const __grid_constant__ BatchParam bp,
                                                             const float* __restrict__ partials,
                                                             double* __restrict__ normal) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ double s_sum[8][32];
     const ViewParam& V = bp.v[blockIdx.x];
     const int e = threadIdx.x & 31, grp = threadIdx.x >> 5;
@@ -703,7 +715,7 @@ cudaError_t launch_render_fwd(const BatchParam& bp, const RenderConst& rc, const
     bool done = false;
 #define GS_X(T, P, B)                                                                                  \
     if (!done && bp.tile_size == T && bp.ppt == P && bp.batch == B) {                                  \
-        k_render_fwd<T, P, B><<<bp.total_tiles, T * T / P, 0, s>>>(bp, rc, ws.rec, ws.ranges, ws.ovals[1], svals, rgb, \
+        pdl_launch(k_render_fwd<T, P, B>, bp.total_tiles, T * T / P, 0, s, bp, rc, ws.rec, ws.ranges, ws.ovals[1], svals, rgb, \
                                                                     T_final, n_contrib, n_used);      \
         done = true;                                                                                   \
     }
@@ -725,7 +737,7 @@ cudaError_t launch_render_bwd(const BatchParam& bp, const RenderConst& rc, const
     bool done = false;
 #define GS_X(T, P, B)                                                                                      \
     if (!done && bp.tile_size == T && bp.ppt == P && bp.batch == B) {                                      \
-        k_render_bwd<T, P, B><<<bp.total_tiles, T * T / P, 0, s>>>(bp, rc, ws.rec, ws.ranges, ws.ovals[1], svals, T_final, \
+        pdl_launch(k_render_bwd<T, P, B>, bp.total_tiles, T * T / P, 0, s, bp, rc, ws.rec, ws.ranges, ws.ovals[1], svals, T_final, \
                                                                     n_contrib, dL_drgb, ws.grad2d);       \
         done = true;                                                                                       \
     }
@@ -750,8 +762,8 @@ cudaError_t launch_l1(const BatchParam& bp, const WsPtrs& ws, const float* rgb, 
     const int gx = l1_grid_x(max_px);
     dim3 grid(gx, bp.n_views);
     const int pi = pf.begin(GS_KF_L1, s, loss ? 2 : 1);
-    k_l1<<<grid, kL1Threads, 0, s>>>(bp, rgb, target, dL_drgb, ws.partials);
-    if (loss) k_l1_finish<<<1, 1024, 0, s>>>(ws.partials, gx * bp.n_views, loss);
+    pdl_launch(k_l1, grid, kL1Threads, 0, s, bp, rgb, target, dL_drgb, ws.partials);
+    if (loss) pdl_launch(k_l1_finish, 1, 1024, 0, s, ws.partials, gx * bp.n_views, loss);
     pf.end(pi, s);
     return cudaGetLastError();
 }
@@ -811,8 +823,8 @@ cudaError_t launch_l1_static(const BatchParam& bp, const float* rgb, const float
     float* partials = static_cast<float*>(ptr);
     const int gx = (int)(need / bp.n_views);
     dim3 grid(gx, bp.n_views);
-    k_l1<<<grid, kL1Threads, 0, s>>>(bp, rgb, target, dL_drgb, partials);
-    if (loss) k_l1_finish<<<1, 1024, 0, s>>>(partials, (int)need, loss);
+    pdl_launch(k_l1, grid, kL1Threads, 0, s, bp, rgb, target, dL_drgb, partials);
+    if (loss) pdl_launch(k_l1_finish, 1, 1024, 0, s, partials, (int)need, loss);
     return cudaGetLastError();
 }
 
@@ -825,14 +837,14 @@ cudaError_t launch_pose_normal(const BatchParam& bp, const RenderConst& rc, cons
     const uint32_t* svals = ws.pvals[ws.sorted_buf];
     const int pi = pf.begin(GS_KF_POSE_NORMAL, s, 2);
     if (bp.tile_size == 8)
-        k_render_pose_normal<8><<<bp.total_tiles, 64, 0, s>>>(bp, rc, ws.rec, ws.ranges, ws.ovals[1], svals,
+        pdl_launch(k_render_pose_normal<8>, bp.total_tiles, 64, 0, s, bp, rc, ws.rec, ws.ranges, ws.ovals[1], svals,
                                                                tangents, target, partials, H_pix);
     else if (bp.tile_size == 16)
-        k_render_pose_normal<16><<<bp.total_tiles, 256, 0, s>>>(bp, rc, ws.rec, ws.ranges, ws.ovals[1], svals,
+        pdl_launch(k_render_pose_normal<16>, bp.total_tiles, 256, 0, s, bp, rc, ws.rec, ws.ranges, ws.ovals[1], svals,
                                                                  tangents, target, partials, H_pix);
     else
         return cudaErrorInvalidValue;
-    k_pose_normal_finish<<<bp.n_views, 256, 0, s>>>(bp, partials, normal);
+    pdl_launch(k_pose_normal_finish, bp.n_views, 256, 0, s, bp, partials, normal);
     pf.end(pi, s);
     return cudaGetLastError();
 }

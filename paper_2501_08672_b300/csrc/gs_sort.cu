@@ -64,6 +64,8 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_upsweep(const uint32_t*
                                                                  int shift, int bits,
                                                                  uint32_t* __restrict__ hist,
                                                                  unsigned long long* __restrict__ zero, int nzero) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ uint32_t wh[kRadixWarps][256];
     const int t = threadIdx.x, w = t >> 5;
     if (blockIdx.x == 0)
@@ -104,6 +106,8 @@ __global__ void __launch_bounds__(kRadixThreads, 3) k_radix_downsweep(
     const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
     uint32_t* __restrict__ vout, unsigned long long n_host, const unsigned long long* n_dev, int shift,
     int bits, const uint32_t* __restrict__ hist) {
+    pdl_wait();
+    pdl_trigger();
     constexpr int kSlice = kRTile / kRadixWarps;  // 512 keys per warp
     __shared__ uint32_t s_keys[kRTile];
     __shared__ uint32_t s_vals[kRTile];
@@ -195,6 +199,8 @@ constexpr int kU32ScanChunk = 4096;
 
 __global__ void __launch_bounds__(1024) k_u32_reduce(const uint32_t* __restrict__ a, long long n,
                                                      uint32_t* __restrict__ part) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ uint32_t s_w[32];
     const long long base = (long long)blockIdx.x * kU32ScanChunk;
     uint32_t s = 0;
@@ -214,6 +220,8 @@ __global__ void __launch_bounds__(1024) k_u32_reduce(const uint32_t* __restrict_
 }
 
 __global__ void __launch_bounds__(1024) k_u32_top(uint32_t* part, int nparts) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ uint32_t s[1024];
     const int t = threadIdx.x;
     const int per = (nparts + 1023) / 1024;
@@ -240,6 +248,8 @@ __global__ void __launch_bounds__(1024) k_u32_top(uint32_t* part, int nparts) {
 
 __global__ void __launch_bounds__(1024) k_u32_apply(uint32_t* __restrict__ a, long long n,
                                                     const uint32_t* __restrict__ part) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ uint32_t s_w[32];
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
     const long long base = (long long)blockIdx.x * kU32ScanChunk + (long long)t * 4;
@@ -292,6 +302,8 @@ constexpr int kLookbackPolls = 1 << 20;
 __global__ void __launch_bounds__(1024) k_u32_scan_lookback(uint32_t* __restrict__ a, long long n,
                                                             unsigned long long* flags, unsigned int* ticket,
                                                             unsigned int* status) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ uint32_t s_w[32];
     __shared__ unsigned int s_chunk;
     __shared__ uint32_t s_prefix;
@@ -380,6 +392,8 @@ __global__ void __launch_bounds__(1024) k_u32_scan_lookback(uint32_t* __restrict
 constexpr long long kU32SingleScanMax = 1ll << 14;
 
 __global__ void __launch_bounds__(1024) k_u32_scan_single(uint32_t* __restrict__ a, long long n) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ uint32_t s_w[32];
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
     const long long per = (n + 1023) / 1024;
@@ -450,6 +464,8 @@ __device__ void heap_sift(uint32_t* a, long long root, long long n, const uint32
 
 __global__ void __launch_bounds__(256) k_depth_fixup(const uint32_t* __restrict__ hi, uint32_t* __restrict__ vals,
                                                      const uint32_t* __restrict__ lo, long long M) {
+    pdl_wait();
+    pdl_trigger();
     const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= M) return;
     const uint32_t h = hi[j];
@@ -514,6 +530,8 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* __
                                                               const uint32_t* __restrict__ touched,
                                                               long long M,
                                                               unsigned long long* __restrict__ part) {
+    pdl_wait();
+    pdl_trigger();
     const long long base = (long long)blockIdx.x * kScanChunk + threadIdx.x * kScanItems;
     uint32_t s = 0;
 #pragma unroll
@@ -528,6 +546,8 @@ __global__ void __launch_bounds__(1024) k_scan_top(unsigned long long* part, int
                                                    unsigned long long* counters, long long cap,
                                                    unsigned int* status,
                                                    unsigned long long* status_pairs) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ unsigned long long s[1024];
     const int t = threadIdx.x;
     const int per = (nparts + 1023) / 1024;
@@ -563,6 +583,8 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const uint32_t* __r
                                                              long long M,
                                                              const unsigned long long* __restrict__ part,
                                                              unsigned long long* __restrict__ offsets) {
+    pdl_wait();
+    pdl_trigger();
     const long long base = (long long)blockIdx.x * kScanChunk + threadIdx.x * kScanItems;
     uint32_t v[kScanItems];
     uint32_t s = 0;
@@ -609,6 +631,8 @@ __global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ order
                                               const unsigned long long* __restrict__ offsets, long long M,
                                               long long cap, int ts, float log2_alpha_min,
                                               uint32_t* __restrict__ pkeys, uint32_t* __restrict__ pvals) {
+    pdl_wait();
+    pdl_trigger();
     const long long j0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const bool live = j0 < M;
     if (__all_sync(0xffffffffu, !live)) return;
@@ -739,6 +763,8 @@ __global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ order
 // fill the tail.
 __global__ void k_tile_keys(const uint2* __restrict__ ranges, int n_tiles, uint32_t* __restrict__ keys,
                             uint32_t* __restrict__ vals) {
+    pdl_wait();
+    pdl_trigger();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_tiles) return;
     const uint2 rg = ranges[i];
@@ -760,6 +786,8 @@ __global__ void k_tile_keys(const uint2* __restrict__ ranges, int n_tiles, uint3
 __global__ void __launch_bounds__(256) k_ranges(const uint32_t* __restrict__ keys, long long cap,
                                                 const unsigned long long* __restrict__ n_dev, uint32_t n_tiles,
                                                 uint2* __restrict__ ranges) {
+    pdl_wait();
+    pdl_trigger();
     const unsigned long long n = clamp_n((unsigned long long)cap, n_dev);
     const unsigned long long n4 = (n + 3) / 4;
     const uint4* __restrict__ k4 = reinterpret_cast<const uint4*>(keys);
@@ -799,7 +827,9 @@ __global__ void __launch_bounds__(256) k_ranges(const uint32_t* __restrict__ key
     }
 }
 
-__global__ void k_set_u32(unsigned int* p, unsigned int v) { *p = v; }
+__global__ void k_set_u32(unsigned int* p, unsigned int v) {
+    pdl_wait();
+    pdl_trigger(); *p = v; }
 
 }  // namespace
 
@@ -813,8 +843,8 @@ cudaError_t launch_selftest_wait(void* scratch, unsigned int* status, cudaStream
     unsigned long long* flags = reinterpret_cast<unsigned long long*>(a + 2 * kU32ScanChunk);
     cudaError_t e = cudaMemsetAsync(scratch, 0, selftest_wait_scratch_bytes(), s);
     if (e != cudaSuccess) return e;
-    k_set_u32<<<1, 1, 0, s>>>(reinterpret_cast<unsigned int*>(flags + 2), 1u);
-    k_u32_scan_lookback<<<1, 1024, 0, s>>>(a, 2 * kU32ScanChunk, flags, reinterpret_cast<unsigned int*>(flags + 2),
+    pdl_launch(k_set_u32, 1, 1, 0, s, reinterpret_cast<unsigned int*>(flags + 2), 1u);
+    pdl_launch(k_u32_scan_lookback, 1, 1024, 0, s, a, 2 * kU32ScanChunk, flags, reinterpret_cast<unsigned int*>(flags + 2),
                                           status);
     return cudaGetLastError();
 }
@@ -845,17 +875,17 @@ cudaError_t radix_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, c
         // flags of the nparts chunks, then the ticket, zeroed by the upsweep for the look-back scan
         unsigned long long* flags = reinterpret_cast<unsigned long long*>(ws.hist_part);
         const bool single = nh <= kU32SingleScanMax;
-        k_radix_upsweep<<<nblk, kRadixThreads, 0, s>>>(kin, n_host, n_dev, shift, bits, ws.hist, flags,
+        pdl_launch(k_radix_upsweep, nblk, kRadixThreads, 0, s, kin, n_host, n_dev, shift, bits, ws.hist, flags,
                                                        single ? 0 : nparts + 1);
         if (single) {
-            k_u32_scan_single<<<1, 1024, 0, s>>>(ws.hist, nh);
+            pdl_launch(k_u32_scan_single, 1, 1024, 0, s, ws.hist, nh);
             pf.count(3);
         } else {
             pf.count(3);
-            k_u32_scan_lookback<<<nparts, 1024, 0, s>>>(ws.hist, nh, flags,
+            pdl_launch(k_u32_scan_lookback, nparts, 1024, 0, s, ws.hist, nh, flags,
                                                         reinterpret_cast<unsigned int*>(flags + nparts), status);
         }
-        k_radix_downsweep<<<nblk, kRadixThreads, 0, s>>>(kin, vin, kout, vout, n_host, n_dev, shift, bits, ws.hist);
+        pdl_launch(k_radix_downsweep, nblk, kRadixThreads, 0, s, kin, vin, kout, vout, n_host, n_dev, shift, bits, ws.hist);
         uint32_t* tk = kin; kin = kout; kout = tk;
         uint32_t* tv = vin; vin = vout; vout = tv;
     }
@@ -879,19 +909,19 @@ cudaError_t launch_bin(const BatchParam& bp, WsPtrs& ws, unsigned int* status,
                    status, s, pf);
     if (e != cudaSuccess) return e;
     uint32_t* sorted_hi = dbuf ? ws.dkeys[1] : ws.dhi;
-    k_depth_fixup<<<(unsigned)((M + 255) / 256), 256, 0, s>>>(sorted_hi, ws.dvals[dbuf], ws.dkeys[0], M);
+    pdl_launch(k_depth_fixup, (unsigned)((M + 255) / 256), 256, 0, s, sorted_hi, ws.dvals[dbuf], ws.dkeys[0], M);
     pf.end(pi, s);
     const uint32_t* order = ws.dvals[dbuf];
     // 2. exclusive scan of tiles-touched in that order
     const int nb = (int)((M + kScanChunk - 1) / kScanChunk);
     pi = pf.begin(GS_KF_TILE_SCAN, s, 3);
-    k_scan_reduce<<<nb, kScanThreads, 0, s>>>(order, ws.tiles_touched, M, ws.scan_part);
-    k_scan_top<<<1, 1024, 0, s>>>(ws.scan_part, nb, ws.counters, ws.cap, status, status_pairs);
-    k_scan_apply<<<nb, kScanThreads, 0, s>>>(order, ws.tiles_touched, M, ws.scan_part, ws.offsets);
+    pdl_launch(k_scan_reduce, nb, kScanThreads, 0, s, order, ws.tiles_touched, M, ws.scan_part);
+    pdl_launch(k_scan_top, 1, 1024, 0, s, ws.scan_part, nb, ws.counters, ws.cap, status, status_pairs);
+    pdl_launch(k_scan_apply, nb, kScanThreads, 0, s, order, ws.tiles_touched, M, ws.scan_part, ws.offsets);
     pf.end(pi, s);
     // 3. expand records into (tile, record) pairs
     pi = pf.begin(GS_KF_EMIT, s);
-    k_emit<<<(unsigned)((M + 255) / 256), 256, 0, s>>>(order, ws.tiles_touched, ws.hitmask, ws.rect, ws.rec, ws.offsets, M,
+    pdl_launch(k_emit, (unsigned)((M + 255) / 256), 256, 0, s, order, ws.tiles_touched, ws.hitmask, ws.rect, ws.rec, ws.offsets, M,
                                                        ws.cap, bp.tile_size, ws.log2_alpha_min, ws.pkeys[0],
                                                        ws.pvals[0]);
     pf.end(pi, s);
@@ -910,8 +940,8 @@ cudaError_t launch_bin(const BatchParam& bp, WsPtrs& ws, unsigned int* status,
     pi = pf.begin(GS_KF_RANGES, s, 3);  // memset, ranges, keys
     e = cudaMemsetAsync(ws.ranges, 0, sizeof(uint2) * (size_t)bp.total_tiles, s);
     if (e != cudaSuccess) return e;
-    k_ranges<<<1184, 256, 0, s>>>(ws.pkeys[pbuf], ws.cap, ws.counters, (uint32_t)bp.total_tiles, ws.ranges);
-    k_tile_keys<<<(bp.total_tiles + 255) / 256, 256, 0, s>>>(ws.ranges, bp.total_tiles, ws.okeys[0], ws.ovals[0]);
+    pdl_launch(k_ranges, 1184, 256, 0, s, ws.pkeys[pbuf], ws.cap, ws.counters, (uint32_t)bp.total_tiles, ws.ranges);
+    pdl_launch(k_tile_keys, (bp.total_tiles + 255) / 256, 256, 0, s, ws.ranges, bp.total_tiles, ws.okeys[0], ws.ovals[0]);
     int obuf = 0;
     e = radix_sort(ws.okeys[0], ws.ovals[0], ws.okeys[1], ws.ovals[1], ws, (unsigned long long)bp.total_tiles,
                    nullptr, 8, &obuf, status, s, pf);

@@ -118,6 +118,8 @@ __global__ void __launch_bounds__(kSsimThreads) k_ssim_fwd(const __grid_constant
                                                            const float* __restrict__ target,
                                                            float* __restrict__ dmaps, long long plane_stride,
                                                            float* __restrict__ partials) {
+    pdl_wait();
+    pdl_trigger();
     const int view = blockIdx.z / 3, ch = blockIdx.z - 3 * view;
     const ViewParam& V = bp.v[view];
     const int W = V.W, H = V.H;
@@ -186,6 +188,8 @@ __global__ void __launch_bounds__(kSsimThreads) k_ssim_bwd(const __grid_constant
                                                            const float* __restrict__ target,
                                                            const float* __restrict__ dmaps, long long plane_stride,
                                                            float* __restrict__ dL_drgb) {
+    pdl_wait();
+    pdl_trigger();
     const int view = blockIdx.z / 3, ch = blockIdx.z - 3 * view;
     const ViewParam& V = bp.v[view];
     const int W = V.W, H = V.H;
@@ -224,6 +228,8 @@ __global__ void __launch_bounds__(kSsimThreads) k_ssim_bwd(const __grid_constant
 
 __global__ void k_ssim_finish(const float* __restrict__ partials, long long n, float lambda,
                               float* __restrict__ loss) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ float sw[32];
     float s = 0.f;
     for (long long i = threadIdx.x; i < n; i += blockDim.x) s += partials[i];
@@ -260,9 +266,9 @@ cudaError_t launch_ssim(const BatchParam& bp, const SsimParam& sp, const float* 
     const long long plane = 3 * bp.total_px;
     float* partials = scratch + (size_t)3 * (size_t)plane;
     const int pi = pf.begin(GS_KF_SSIM, s, loss ? 3 : 2);
-    k_ssim_fwd<<<grid, kSsimThreads, 0, s>>>(bp, sp, rgb, target, dmaps, plane, partials);
-    k_ssim_bwd<<<grid, kSsimThreads, 0, s>>>(bp, sp, rgb, target, dmaps, plane, dL_drgb);
-    if (loss) k_ssim_finish<<<1, 1024, 0, s>>>(partials, (long long)grid.x * grid.y * grid.z, sp.lambda, loss);
+    pdl_launch(k_ssim_fwd, grid, kSsimThreads, 0, s, bp, sp, rgb, target, dmaps, plane, partials);
+    pdl_launch(k_ssim_bwd, grid, kSsimThreads, 0, s, bp, sp, rgb, target, dmaps, plane, dL_drgb);
+    if (loss) pdl_launch(k_ssim_finish, 1, 1024, 0, s, partials, (long long)grid.x * grid.y * grid.z, sp.lambda, loss);
     pf.end(pi, s);
     return cudaGetLastError();
 }

@@ -74,6 +74,8 @@ __device__ __forceinline__ unsigned keep_count(const uint8_t* keep, long long ba
 // Survivors per block of kWinChunk rows.
 __global__ void __launch_bounds__(kWinThreads) k_win_reduce(const uint8_t* __restrict__ keep, long long n,
                                                             unsigned* __restrict__ part) {
+    pdl_wait();
+    pdl_trigger();
     const long long base = (long long)blockIdx.x * kWinChunk + (long long)threadIdx.x * kWinItems;
     unsigned total;
     block_exclusive_scan(keep_count(keep, base, n), &total);
@@ -86,6 +88,8 @@ __global__ void __launch_bounds__(kWinThreads) k_win_reduce(const uint8_t* __res
 // n_keep; movers = holes = n_keep - S(n_keep).
 __global__ void __launch_bounds__(1024) k_win_top(const uint8_t* __restrict__ keep, long long n, unsigned* part,
                                                   int nparts, long long* n_keep_out, long long* counts) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ unsigned long long s[1024];
     const int t = threadIdx.x;
     const int per = (nparts + 1023) / 1024;
@@ -137,6 +141,8 @@ __global__ void __launch_bounds__(kWinThreads) k_win_rank(const uint8_t* __restr
                                                           int32_t* __restrict__ movers_asc,
                                                           int32_t* __restrict__ moved_from,
                                                           int32_t* __restrict__ leaving_rows) {
+    pdl_wait();
+    pdl_trigger();
     const long long base = (long long)blockIdx.x * kWinChunk + (long long)threadIdx.x * kWinItems;
     bool f[kWinItems];
     unsigned c = 0;
@@ -213,6 +219,8 @@ __global__ void __launch_bounds__(kCopyThreads, kCopyBlocksPerSM) k_win_move(con
                                                            const int32_t* __restrict__ holes_list,
                                                            const int32_t* __restrict__ movers_asc,
                                                            int32_t* __restrict__ moved_from) {
+    pdl_wait();
+    pdl_trigger();
     const long long n_movers = min(counts[1], n);
     const int lane = threadIdx.x & 31;
     const long long warp = ((long long)blockIdx.x * kCopyThreads + threadIdx.x) >> 5;
@@ -235,6 +243,8 @@ __global__ void __launch_bounds__(kCopyThreads, kCopyBlocksPerSM) k_win_move(con
 __global__ void __launch_bounds__(kCopyThreads, kCopyBlocksPerSM) k_win_gather(const ColTable src, const ColTable dst,
                                                              const int32_t* __restrict__ idx, long long m,
                                                              long long n, const long long* __restrict__ n_keep) {
+    pdl_wait();
+    pdl_trigger();
     if (n_keep) m = min(max(n - *n_keep, 0ll), m);
     const int lane = threadIdx.x & 31;
     const long long warp = ((long long)blockIdx.x * kCopyThreads + threadIdx.x) >> 5;
@@ -254,6 +264,8 @@ __global__ void __launch_bounds__(kCopyThreads, kCopyBlocksPerSM) k_win_gather(c
 
 // Rows [a, b) of every column set to zero (contiguous words per column).
 __global__ void __launch_bounds__(kCopyThreads) k_win_clear(const ColTable cols, long long a, long long b) {
+    pdl_wait();
+    pdl_trigger();
     const long long t0 = (long long)blockIdx.x * kCopyThreads + threadIdx.x;
     const long long stride = (long long)gridDim.x * kCopyThreads;
     for (int c = 0; c < cols.n; ++c) {
@@ -272,6 +284,8 @@ template <int D>
 __global__ void __launch_bounds__(256) k_sh_init(const ViewParam V, const float* __restrict__ means,
                                                  const float* __restrict__ image, long long begin, long long end,
                                                  float z_near, float* __restrict__ sh) {
+    pdl_wait();
+    pdl_trigger();
     constexpr int K3 = 3 * (D + 1) * (D + 1);  // floats per row
     const long long i0 = begin + (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u);
     if (i0 >= end) return;  // warp-uniform
@@ -363,14 +377,14 @@ cudaError_t launch_window_compact(const gs_window_column* cols_host, const gs_wi
     int32_t* movers_asc = reinterpret_cast<int32_t*>(p);
     const ColTable cols = col_table(cols_host, n_cols);
     const int pi = pf.begin(GS_KF_WINDOW, s, leave_dst ? 5 : 4);
-    k_win_reduce<<<(unsigned)nblk, kWinThreads, 0, s>>>(keep, n, part);
-    k_win_top<<<1, 1024, 0, s>>>(keep, n, part, (int)nblk, n_keep_dev, counts);
-    k_win_rank<<<(unsigned)nblk, kWinThreads, 0, s>>>(keep, n, n_keep_dev, part, counts, holes_list, movers_asc,
+    pdl_launch(k_win_reduce, (unsigned)nblk, kWinThreads, 0, s, keep, n, part);
+    pdl_launch(k_win_top, 1, 1024, 0, s, keep, n, part, (int)nblk, n_keep_dev, counts);
+    pdl_launch(k_win_rank, (unsigned)nblk, kWinThreads, 0, s, keep, n, n_keep_dev, part, counts, holes_list, movers_asc,
                                                        moved_from, leaving_rows);
     if (leave_dst)  // Step 1 before the moves overwrite the holes
-        k_win_gather<<<copy_grid(n, sm_count), kCopyThreads, 0, s>>>(cols, col_table(leave_dst, n_cols), holes_list,
+        pdl_launch(k_win_gather, copy_grid(n, sm_count), kCopyThreads, 0, s, cols, col_table(leave_dst, n_cols), holes_list,
                                                                       n, n, n_keep_dev);
-    k_win_move<<<copy_grid(n / 2, sm_count), kCopyThreads, 0, s>>>(cols, n, counts, holes_list, movers_asc,
+    pdl_launch(k_win_move, copy_grid(n / 2, sm_count), kCopyThreads, 0, s, cols, n, counts, holes_list, movers_asc,
                                                                   moved_from);
     pf.end(pi, s);
     return cudaGetLastError();
@@ -381,7 +395,7 @@ cudaError_t launch_window_gather(const gs_window_column* src_host, const gs_wind
                                  Prof& pf) {
     const int pi = pf.begin(GS_KF_WINDOW, s);
     if (m > 0)
-        k_win_gather<<<copy_grid(m, sm_count), kCopyThreads, 0, s>>>(col_table(src_host, n_cols),
+        pdl_launch(k_win_gather, copy_grid(m, sm_count), kCopyThreads, 0, s, col_table(src_host, n_cols),
                                                                       col_table(dst_host, n_cols), idx, m, n, nullptr);
     pf.end(pi, s);
     return cudaGetLastError();
@@ -394,7 +408,7 @@ cudaError_t launch_window_clear(const gs_window_column* cols_host, int n_cols, l
     const ColTable cols = col_table(cols_host, n_cols);
     long long words = 0;
     for (int c = 0; c < n_cols; ++c) words += cols.words[c];
-    k_win_clear<<<copy_grid((end - begin) * words / 32, sm_count), kCopyThreads, 0, s>>>(cols, begin, end);
+    pdl_launch(k_win_clear, copy_grid((end - begin) * words / 32, sm_count), kCopyThreads, 0, s, cols, begin, end);
     pf.end(pi, s);
     return cudaGetLastError();
 }
@@ -406,10 +420,10 @@ cudaError_t launch_sh_init(const ViewParam& V, const float* means, const float* 
     const int K = (sh_degree + 1) * (sh_degree + 1);
     const unsigned grid = (unsigned)((end - begin + 255) / 256);
     switch (K) {
-        case 1: k_sh_init<0><<<grid, 256, 0, s>>>(V, means, image, begin, end, z_near, sh); break;
-        case 4: k_sh_init<1><<<grid, 256, 0, s>>>(V, means, image, begin, end, z_near, sh); break;
-        case 9: k_sh_init<2><<<grid, 256, 0, s>>>(V, means, image, begin, end, z_near, sh); break;
-        default: k_sh_init<3><<<grid, 256, 0, s>>>(V, means, image, begin, end, z_near, sh); break;
+        case 1: pdl_launch(k_sh_init<0>, grid, 256, 0, s, V, means, image, begin, end, z_near, sh); break;
+        case 4: pdl_launch(k_sh_init<1>, grid, 256, 0, s, V, means, image, begin, end, z_near, sh); break;
+        case 9: pdl_launch(k_sh_init<2>, grid, 256, 0, s, V, means, image, begin, end, z_near, sh); break;
+        default: pdl_launch(k_sh_init<3>, grid, 256, 0, s, V, means, image, begin, end, z_near, sh); break;
     }
     pf.end(pi, s);
     return cudaGetLastError();
