@@ -72,8 +72,8 @@ MAX_SM_MHZ = 2032
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
     ap.add_argument("--workload", default="window",
                     choices=["window", "plain", "uneven", "mixed", "odometry", "maintenance"],
@@ -211,10 +211,10 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_oracle_iteration(params, views, pixels_per_view, seed=1):
+def cpu_oracle_iteration(params, views, pixels_per_view, seed=1, n_threads=0):
     """Times the FP64 oracle on a pixel sample of one window iteration and
-    scales the per-pixel parts to the full images.  Returns (seconds per
-    iteration estimate, threads, description)."""
+    scales the per-pixel parts to the full images (n_threads 0: all host
+    cores).  Returns (seconds per iteration estimate, threads, description)."""
     from oracle import oracle as O
     rng = np.random.default_rng(seed)
     t_fixed = 0.0
@@ -227,12 +227,12 @@ def cpu_oracle_iteration(params, views, pixels_per_view, seed=1):
         t0 = time.perf_counter()
         pr = O.project(params, v)
         t1 = time.perf_counter()
-        O.render_pixels(params, v, px, py, proj=pr)
+        O.render_pixels(params, v, px, py, proj=pr, n_threads=n_threads)
         t2 = time.perf_counter()
         dl = [rng.standard_normal((pixels_per_view, 3)) * 1e-6]
-        O.backward(params, [v], dl, pixels=[(px, py)])
+        O.backward(params, [v], dl, pixels=[(px, py)], n_threads=n_threads)
         t3 = time.perf_counter()
-        O.backward(params, [v], [np.zeros((0, 3))], pixels=[(px[:0], py[:0])])
+        O.backward(params, [v], [np.zeros((0, 3))], pixels=[(px[:0], py[:0])], n_threads=n_threads)
         t4 = time.perf_counter()
         scale = (W * H) / float(pixels_per_view)
         t_fixed += (t1 - t0) + (t4 - t3)
@@ -249,7 +249,7 @@ def cpu_oracle_iteration(params, views, pixels_per_view, seed=1):
     desc = ("oracle FP64 on %d random pixels per view (%d of %d), projection and projection backward over all "
             "Gaussians, Adam over all %d parameters; per-pixel time scaled to the full images"
             % (pixels_per_view, n_pix_total, sum(int(v["W"]) * int(v["H"]) for v in views), n))
-    return t_fixed + t_pix + t_adam, O.num_threads(), desc
+    return t_fixed + t_pix + t_adam, (1 if n_threads == 1 else O.num_threads()), desc
 
 
 def run_reference(args, world, rank):
@@ -474,6 +474,9 @@ def run_b300(args, world, rank, local):
             and args.ssim_lambda == 0):
         sec, threads, desc = cpu_oracle_iteration(params, views, args.cpu_pixels)
         cpu = {"value": 1.0 / sec, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc}
+        # the same oracle on one host thread (a smaller pixel sample)
+        sec1, _, desc1 = cpu_oracle_iteration(params, views, max(args.cpu_pixels // 8, 4), seed=2, n_threads=1)
+        cpu["single_thread"] = {"value": 1.0 / sec1, "unit": UNIT, "cores": 1, "sample": desc1}
 
     if rank == 0:
         mpix = world * K * n_px / (max_ms / 1e3) / 1e6
