@@ -194,97 +194,7 @@ __global__ void __launch_bounds__(kRadixThreads, 3) k_radix_downsweep(
     }
 }
 
-// Device-wide exclusive scan of a u32 array in place (three phases).
 constexpr int kU32ScanChunk = 4096;
-
-__global__ void __launch_bounds__(1024) k_u32_reduce(const uint32_t* __restrict__ a, long long n,
-                                                     uint32_t* __restrict__ part) {
-    pdl_wait();
-    pdl_trigger();
-    __shared__ uint32_t s_w[32];
-    const long long base = (long long)blockIdx.x * kU32ScanChunk;
-    uint32_t s = 0;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const long long i = base + k * 1024 + threadIdx.x;
-        if (i < n) s += a[i];
-    }
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = s;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        uint32_t v = s_w[threadIdx.x];
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (threadIdx.x == 0) part[blockIdx.x] = v;
-    }
-}
-
-__global__ void __launch_bounds__(1024) k_u32_top(uint32_t* part, int nparts) {
-    pdl_wait();
-    pdl_trigger();
-    __shared__ uint32_t s[1024];
-    const int t = threadIdx.x;
-    const int per = (nparts + 1023) / 1024;
-    const int b0 = t * per;
-    uint32_t sum = 0;
-    for (int k = 0; k < per; ++k)
-        if (b0 + k < nparts) sum += part[b0 + k];
-    s[t] = sum;
-    __syncthreads();
-    for (int o = 1; o < 1024; o <<= 1) {
-        const uint32_t v = t >= o ? s[t - o] : 0u;
-        __syncthreads();
-        s[t] += v;
-        __syncthreads();
-    }
-    uint32_t run = s[t] - sum;
-    for (int k = 0; k < per; ++k)
-        if (b0 + k < nparts) {
-            const uint32_t v = part[b0 + k];
-            part[b0 + k] = run;
-            run += v;
-        }
-}
-
-__global__ void __launch_bounds__(1024) k_u32_apply(uint32_t* __restrict__ a, long long n,
-                                                    const uint32_t* __restrict__ part) {
-    pdl_wait();
-    pdl_trigger();
-    __shared__ uint32_t s_w[32];
-    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-    const long long base = (long long)blockIdx.x * kU32ScanChunk + (long long)t * 4;
-    uint32_t v[4], s = 0;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        v[k] = base + k < n ? a[base + k] : 0u;
-        s += v[k];
-    }
-    uint32_t x = s;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) s_w[w] = x;
-    __syncthreads();
-    if (w == 0) {
-        uint32_t y = s_w[lane];
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t z = __shfl_up_sync(0xffffffffu, y, o);
-            if (lane >= o) y += z;
-        }
-        s_w[lane] = y;
-    }
-    __syncthreads();
-    uint32_t run = part[blockIdx.x] + (w > 0 ? s_w[w - 1] : 0u) + x - s;
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-        if (base + k < n) {
-            a[base + k] = run;
-            run += v[k];
-        }
-}
 
 // Device-wide exclusive scan of a u32 array in place in one pass (decoupled
 // look-back): each block takes the next 4096-entry chunk from a ticket (so
@@ -386,9 +296,9 @@ __global__ void __launch_bounds__(1024) k_u32_scan_lookback(uint32_t* __restrict
 // Exclusive scan of a u32 array in place by one block: thread t scans a
 // contiguous chunk, a block scan of the chunk totals gives its offset.  For
 // the digit-major histograms of tiny sorts (up to kU32SingleScanMax entries,
-// e.g. the tile-order pass), where the three-phase scan is three
-// latency-bound launches; beyond a few thousand entries one block is slower
-// than the three phases (measured: 80 us against 15 us at 100k entries).
+// e.g. the tile-order pass); beyond a few thousand entries one block is
+// slower than a device-wide scan (measured: 80 us against 15 us at 100k
+// entries).
 constexpr long long kU32SingleScanMax = 1ll << 14;
 
 __global__ void __launch_bounds__(1024) k_u32_scan_single(uint32_t* __restrict__ a, long long n) {
@@ -462,10 +372,15 @@ __device__ void heap_sift(uint32_t* a, long long root, long long n, const uint32
     a[i] = v;
 }
 
+// Block 0 also zeroes `nzero` 64-bit words at `zero`: the look-back flags and
+// ticket of the offsets scan that follows.
 __global__ void __launch_bounds__(256) k_depth_fixup(const uint32_t* __restrict__ hi, uint32_t* __restrict__ vals,
-                                                     const uint32_t* __restrict__ lo, long long M) {
+                                                     const uint32_t* __restrict__ lo, long long M,
+                                                     unsigned long long* __restrict__ zero, int nzero) {
     pdl_wait();
     pdl_trigger();
+    if (blockIdx.x == 0)
+        for (int i = threadIdx.x; i < nzero; i += blockDim.x) zero[i] = 0ull;
     const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= M) return;
     const uint32_t h = hi[j];
@@ -526,76 +441,82 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t& t
     return wprefix + x - v;
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* __restrict__ order,
-                                                              const uint32_t* __restrict__ touched,
-                                                              long long M,
-                                                              unsigned long long* __restrict__ part) {
+// Pair offsets in one pass: the exclusive scan of tiles-touched over the
+// records in depth order, by decoupled look-back over 4096-record chunks taken
+// from a ticket (as k_u32_scan_lookback; flag words pack a 2-bit status with a
+// 62-bit value).  The block of the last chunk knows the grand total: it
+// stores the pair count and latches GS_ERR_CAPACITY when it exceeds cap.
+__global__ void __launch_bounds__(kScanThreads) k_scan_offsets(const uint32_t* __restrict__ order,
+                                                               const uint32_t* __restrict__ touched, long long M,
+                                                               unsigned long long* flags, int nchunks,
+                                                               unsigned long long* __restrict__ offsets,
+                                                               unsigned long long* __restrict__ counters, long long cap,
+                                                               unsigned int* status,
+                                                               unsigned long long* status_pairs) {
     pdl_wait();
     pdl_trigger();
-    const long long base = (long long)blockIdx.x * kScanChunk + threadIdx.x * kScanItems;
-    uint32_t s = 0;
-#pragma unroll
-    for (int k = 0; k < kScanItems; ++k)
-        if (base + k < M) s += touched[order[base + k]];
-    uint32_t total;
-    block_exclusive_scan(s, total);
-    if (threadIdx.x == 0) part[blockIdx.x] = total;
-}
-
-__global__ void __launch_bounds__(1024) k_scan_top(unsigned long long* part, int nparts,
-                                                   unsigned long long* counters, long long cap,
-                                                   unsigned int* status,
-                                                   unsigned long long* status_pairs) {
-    pdl_wait();
-    pdl_trigger();
-    __shared__ unsigned long long s[1024];
-    const int t = threadIdx.x;
-    const int per = (nparts + 1023) / 1024;
-    const int b0 = t * per;
-    unsigned long long sum = 0;
-    for (int k = 0; k < per; ++k)
-        if (b0 + k < nparts) sum += part[b0 + k];
-    s[t] = sum;
+    __shared__ unsigned int s_chunk;
+    __shared__ unsigned long long s_prefix;
+    const int t = threadIdx.x, lane = t & 31;
+    if (t == 0) s_chunk = atomicAdd(reinterpret_cast<unsigned int*>(flags + nchunks), 1u);
     __syncthreads();
-    for (int o = 1; o < 1024; o <<= 1) {
-        unsigned long long v = t >= o ? s[t - o] : 0ull;
-        __syncthreads();
-        s[t] += v;
-        __syncthreads();
-    }
-    unsigned long long run = s[t] - sum;
-    for (int k = 0; k < per; ++k)
-        if (b0 + k < nparts) {
-            const unsigned long long v = part[b0 + k];
-            part[b0 + k] = run;
-            run += v;
-        }
-    if (t == 1023) {
-        const unsigned long long total = s[1023];
-        counters[0] = total;
-        if (status_pairs) *status_pairs = total;
-        if (total > (unsigned long long)cap && status) atomicCAS(status, 0u, (unsigned int)(-GS_ERR_CAPACITY));
-    }
-}
-
-__global__ void __launch_bounds__(kScanThreads) k_scan_apply(const uint32_t* __restrict__ order,
-                                                             const uint32_t* __restrict__ touched,
-                                                             long long M,
-                                                             const unsigned long long* __restrict__ part,
-                                                             unsigned long long* __restrict__ offsets) {
-    pdl_wait();
-    pdl_trigger();
-    const long long base = (long long)blockIdx.x * kScanChunk + threadIdx.x * kScanItems;
+    const long long chunk = s_chunk;
+    const long long base = chunk * kScanChunk + (long long)t * kScanItems;
     uint32_t v[kScanItems];
-    uint32_t s = 0;
+    uint32_t sum = 0;
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
         v[k] = base + k < M ? touched[order[base + k]] : 0u;
-        s += v[k];
+        sum += v[k];
     }
-    uint32_t total;
-    const uint32_t ex = block_exclusive_scan(s, total);
-    unsigned long long run = part[blockIdx.x] + ex;
+    uint32_t agg32;
+    const uint32_t ex = block_exclusive_scan(sum, agg32);
+    if (t < 32) {
+        const unsigned long long agg = agg32;
+        constexpr unsigned long long kVal = (1ull << 62) - 1ull;
+        volatile unsigned long long* vf = flags;
+        unsigned long long excl = 0;
+        if (chunk == 0) {
+            if (lane == 0) vf[0] = (2ull << 62) | agg;
+        } else {
+            if (lane == 0) vf[chunk] = (1ull << 62) | agg;
+            long long j = chunk - 1;
+            for (;;) {
+                const long long idx = j - lane;
+                unsigned long long f = 2ull << 62;  // before chunk 0: a prefix of 0
+                if (idx >= 0) f = vf[idx];
+                int polls = 0;
+                while (__any_sync(0xffffffffu, (f >> 62) == 0)) {
+                    if (++polls > kLookbackPolls) {
+                        if (lane == 0) atomicCAS(status, 0u, (unsigned int)(-GS_ERR_TIMEOUT));
+                        f = (2ull << 62) | (f & kVal);
+                        break;
+                    }
+                    if ((f >> 62) == 0) f = vf[idx];
+                }
+                const uint32_t pre = __ballot_sync(0xffffffffu, (f >> 62) == 2);
+                const int stop = pre ? __ffs(pre) - 1 : 31;
+                unsigned long long val = lane <= stop ? (f & kVal) : 0ull;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) val += __shfl_xor_sync(0xffffffffu, val, o);
+                excl += val;
+                if (pre) break;
+                j -= 32;
+            }
+            if (lane == 0) vf[chunk] = (2ull << 62) | ((excl + agg) & kVal);
+        }
+        if (lane == 0) {
+            s_prefix = excl;
+            if (chunk == nchunks - 1) {
+                const unsigned long long total = excl + agg;
+                counters[0] = total;
+                if (status_pairs) *status_pairs = total;
+                if (total > (unsigned long long)cap && status) atomicCAS(status, 0u, (unsigned int)(-GS_ERR_CAPACITY));
+            }
+        }
+    }
+    __syncthreads();
+    unsigned long long run = s_prefix + ex;
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k)
         if (base + k < M) {
@@ -909,15 +830,15 @@ cudaError_t launch_bin(const BatchParam& bp, WsPtrs& ws, unsigned int* status,
                    status, s, pf);
     if (e != cudaSuccess) return e;
     uint32_t* sorted_hi = dbuf ? ws.dkeys[1] : ws.dhi;
-    pdl_launch(k_depth_fixup, (unsigned)((M + 255) / 256), 256, 0, s, sorted_hi, ws.dvals[dbuf], ws.dkeys[0], M);
+    const int nb = (int)((M + kScanChunk - 1) / kScanChunk);
+    pdl_launch(k_depth_fixup, (unsigned)((M + 255) / 256), 256, 0, s, sorted_hi, ws.dvals[dbuf], ws.dkeys[0], M,
+               ws.scan_part, nb + 1);
     pf.end(pi, s);
     const uint32_t* order = ws.dvals[dbuf];
-    // 2. exclusive scan of tiles-touched in that order
-    const int nb = (int)((M + kScanChunk - 1) / kScanChunk);
-    pi = pf.begin(GS_KF_TILE_SCAN, s, 3);
-    pdl_launch(k_scan_reduce, nb, kScanThreads, 0, s, order, ws.tiles_touched, M, ws.scan_part);
-    pdl_launch(k_scan_top, 1, 1024, 0, s, ws.scan_part, nb, ws.counters, ws.cap, status, status_pairs);
-    pdl_launch(k_scan_apply, nb, kScanThreads, 0, s, order, ws.tiles_touched, M, ws.scan_part, ws.offsets);
+    // 2. exclusive scan of tiles-touched in that order (single pass; flags zeroed by the fix-up)
+    pi = pf.begin(GS_KF_TILE_SCAN, s, 1);
+    pdl_launch(k_scan_offsets, nb, kScanThreads, 0, s, order, ws.tiles_touched, M, ws.scan_part, nb, ws.offsets,
+               ws.counters, ws.cap, status, status_pairs);
     pf.end(pi, s);
     // 3. expand records into (tile, record) pairs
     pi = pf.begin(GS_KF_EMIT, s);
