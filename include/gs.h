@@ -8,6 +8,7 @@
  * (photometric pose update, Sec. II-D and Appendix A).  One iteration is
  *
  *   gs_project -> gs_bin -> gs_render_fwd -> gs_l1_loss -> gs_render_bwd
+ *   (or gs_render_fwd_l1 for the middle two in one pass)
  *   -> gs_adam_step
  *
  * and the odometry form replaces the last two by gs_pose_grad.
@@ -236,6 +237,22 @@ GS_API int gs_bin(gs_ctx* ctx, const gs_view* views, int n_views, const gs_works
 GS_API int gs_render_fwd(gs_ctx* ctx, const gs_view* views, int n_views, const gs_workspace* ws,
                   float* rgb, float* T_final, uint32_t* n_contrib, uint32_t* n_used,
                   gs_stream stream);
+
+/* a3 + a4 in one pass: the compositing of gs_render_fwd with the L1 loss of
+ * gs_l1_loss folded into it (Eq. gaussian_optimization): each pixel's
+ * gradient needs only its own colour and target, so the compositing kernel
+ * writes dL_drgb as it finishes a pixel, and one partial sum per tile that a
+ * second launch adds up into loss_dev[0].  Same values as gs_render_fwd
+ * followed by gs_l1_loss: rgb, T_final, n_contrib, n_used and dL_drgb bit for
+ * bit; the loss up to the order of the FP32 sum.
+ * target: device FP32, packed like rgb.  rgb: may be NULL (the image is then
+ * not written; the loss and gradient are).  n_used, loss_dev: may be NULL.
+ * The per-tile partials live in the workspace.
+ * Errors: GS_ERR_INVALID_ARG (target, T_final, n_contrib or dL_drgb NULL),
+ * GS_ERR_CUDA. */
+GS_API int gs_render_fwd_l1(gs_ctx* ctx, const gs_view* views, int n_views, const gs_workspace* ws,
+                            const float* target, float* rgb, float* T_final, uint32_t* n_contrib,
+                            uint32_t* n_used, float* dL_drgb, float* loss_dev, gs_stream stream);
 
 /* Device floats of scratch gs_dssim_loss needs for these views: 9 per pixel
  * (three SSIM derivative maps per channel) plus one per 32 x 16 tile of each

@@ -36,7 +36,7 @@ EXPORTED = ["gs_config_default", "gs_version", "gs_context_create", "gs_context_
             "gs_l1_loss_noalloc", "gs_calibrate_alu", "gs_pose_normal_scratch", "gs_pose_normal",
             "gs_window_scratch_bytes", "gs_window_compact", "gs_window_remove", "gs_window_gather", "gs_window_clear",
             "gs_sh_init_bilinear", "gs_dssim_scratch_floats", "gs_dssim_loss", "gs_adam_step_ranges",
-            "gs_selftest_wait_scratch_bytes", "gs_selftest_bounded_wait"]
+            "gs_selftest_wait_scratch_bytes", "gs_selftest_bounded_wait", "gs_render_fwd_l1"]
 
 KERNEL_FAMILIES = ["project", "depth_sort", "tile_scan", "emit", "tile_sort", "ranges", "raster_fwd", "l1",
                    "raster_bwd", "project_bwd", "adam", "pose_normal", "window", "ssim"]
@@ -129,6 +129,8 @@ def lib():
         L.gs_bin.argtypes = [P, ctypes.POINTER(View), I, ctypes.POINTER(Workspace), ctypes.POINTER(ctypes.c_uint64), P]
         L.gs_render_fwd.argtypes = [P, ctypes.POINTER(View), I, ctypes.POINTER(Workspace), P, P, P, P, P]
         L.gs_l1_loss.argtypes = [P, ctypes.POINTER(View), I, ctypes.POINTER(Workspace), P, P, P, P, P]
+        L.gs_render_fwd_l1.argtypes = [P, ctypes.POINTER(View), I, ctypes.POINTER(Workspace), P, P, P, P, P, P, P,
+                                       P]
         L.gs_render_bwd.argtypes = [P, ctypes.POINTER(Gaussians), ctypes.POINTER(View), I, ctypes.POINTER(Workspace),
                                     P, P, P, ctypes.POINTER(Grads), P, P]
         L.gs_pose_grad.argtypes = [P, ctypes.POINTER(Gaussians), ctypes.POINTER(View), I, ctypes.POINTER(Workspace),
@@ -302,6 +304,13 @@ class Context:
     def render_fwd(self, views, ws, rgb, T_final, n_contrib, n_used=None, stream=None):
         self._ck(lib().gs_render_fwd(self.h, views, len(views), ctypes.byref(ws), _ptr(rgb), _ptr(T_final),
                                      _ptr(n_contrib), _ptr(n_used), _stream(stream)))
+
+    def render_fwd_l1(self, views, ws, target, rgb, T_final, n_contrib, dL_drgb, loss=None, n_used=None,
+                      stream=None):
+        """Compositing with the L1 loss folded in (rgb may be None: image not written)."""
+        self._ck(lib().gs_render_fwd_l1(self.h, views, len(views), ctypes.byref(ws), _ptr(target), _ptr(rgb),
+                                        _ptr(T_final), _ptr(n_contrib), _ptr(n_used), _ptr(dL_drgb), _ptr(loss),
+                                        _stream(stream)))
 
     def l1_loss(self, views, ws, rgb, target, dL_drgb, loss=None, stream=None):
         self._ck(lib().gs_l1_loss(self.h, views, len(views), ctypes.byref(ws), _ptr(rgb), _ptr(target),

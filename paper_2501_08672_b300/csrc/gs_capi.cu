@@ -179,6 +179,7 @@ int make_layout(gs_ctx* ctx, const gs_config& cfg, const gs_view* views, int n_v
     long long partials = (long long)n_views * pose_blocks * 6;
     const long long l1 = (long long)n_views * l1_blocks_x(max_px);
     if (l1 > partials) partials = l1;
+    if (T > partials) partials = T;  // the L1 loss folded into the forward: one partial per tile
 
     size_t off = 0;
     auto take = [&](size_t bytes) { const size_t o = off; off = align_up(off + bytes); return o; };
@@ -532,9 +533,27 @@ int gs_render_fwd(gs_ctx* ctx, const gs_view* views, int n_views, const gs_works
     BatchParam bp;
     make_batch(ctx->cfg, views, n_views, bp);
     const WsPtrs wp = ws_ptrs(ws, L, bp.total_tiles);
-    cudaError_t e = launch_render_fwd(bp, make_rc(ctx->cfg), wp, rgb, T_final, n_contrib, n_used,
-                                      reinterpret_cast<cudaStream_t>(stream), ctx->prof);
+    cudaError_t e = launch_render_fwd(bp, make_rc(ctx->cfg), wp, rgb, T_final, n_contrib, n_used, nullptr, nullptr,
+                                      nullptr, reinterpret_cast<cudaStream_t>(stream), ctx->prof);
     return e == cudaSuccess ? GS_OK : cuda_fail(ctx, e, "gs_render_fwd");
+}
+
+int gs_render_fwd_l1(gs_ctx* ctx, const gs_view* views, int n_views, const gs_workspace* ws, const float* target,
+                     float* rgb, float* T_final, uint32_t* n_contrib, uint32_t* n_used, float* dL_drgb,
+                     float* loss_dev, gs_stream stream) {
+    if (!ctx) return GS_ERR_INVALID_ARG;
+    if (!target || !T_final || !n_contrib || !dL_drgb)
+        return fail(ctx, GS_ERR_INVALID_ARG, "target, T_final, n_contrib or dL_drgb is NULL");
+    Layout L;
+    int rc = check_ws(ctx, views, n_views, ws, L);
+    if (rc) return rc;
+    DeviceGuard dg(ctx->device);
+    BatchParam bp;
+    make_batch(ctx->cfg, views, n_views, bp);
+    const WsPtrs wp = ws_ptrs(ws, L, bp.total_tiles);
+    cudaError_t e = launch_render_fwd(bp, make_rc(ctx->cfg), wp, rgb, T_final, n_contrib, n_used, target, dL_drgb,
+                                      loss_dev, reinterpret_cast<cudaStream_t>(stream), ctx->prof);
+    return e == cudaSuccess ? GS_OK : cuda_fail(ctx, e, "gs_render_fwd_l1");
 }
 
 int gs_l1_loss(gs_ctx* ctx, const gs_view* views, int n_views, const gs_workspace* ws, const float* rgb,

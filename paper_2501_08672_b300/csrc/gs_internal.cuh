@@ -310,9 +310,11 @@ bool pose_normal_supported(int ts);
 cudaError_t launch_pose_normal(const BatchParam& bp, const RenderConst& rc, const WsPtrs& ws,
                                const float4* tangents, const float* target, float* partials, double* normal,
                                float* H_pix, cudaStream_t s, Prof& pf);
+// target non-null: also the L1 loss (dL_drgb, and loss when non-null) from
+// per-tile partials in ws.partials (one per tile); rgb may then be null.
 cudaError_t launch_render_fwd(const BatchParam& bp, const RenderConst& rc, const WsPtrs& ws,
                               float* rgb, float* T_final, uint32_t* n_contrib, uint32_t* n_used,
-                              cudaStream_t s, Prof& pf);
+                              const float* target, float* dL_drgb, float* loss, cudaStream_t s, Prof& pf);
 cudaError_t launch_render_bwd(const BatchParam& bp, const RenderConst& rc, const WsPtrs& ws,
                               const float* T_final, const uint32_t* n_contrib,
                               const float* dL_drgb, cudaStream_t s, Prof& pf);

@@ -93,7 +93,10 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_render_fwd(const __grid_const
                                                               float* __restrict__ rgb,
                                                               float* __restrict__ T_final,
                                                               uint32_t* __restrict__ n_contrib,
-                                                              uint32_t* __restrict__ n_used) {
+                                                              uint32_t* __restrict__ n_used,
+                                                              const float* __restrict__ target,
+                                                              float* __restrict__ dL_drgb,
+                                                              float* __restrict__ partials) {
     pdl_wait();
     pdl_trigger();
     // Each warp walks the tile's list on its own: per step every lane fetches
@@ -202,17 +205,50 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_render_fwd(const __grid_const
         __syncwarp();
     }
     const long long hw = (long long)V.W * V.H;
-    float* out = rgb + 3 * V.pix_off;
+    // With a target the L1 loss is folded in here (Eq. gaussian_optimization):
+    // a pixel's gradient sign(C - target) / (3 H W V) needs only its own
+    // colour, and the tile's sum of |C - target| goes to partials[tile].
+    const float scale = 1.f / ((float)(3 * hw) * (float)bp.n_views);
+    float lsum = 0.f;
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
         if (px < V.W && pm.row(k) < V.H) {
             const long long pl = (long long)pm.row(k) * V.W + px;
-            out[pl] = C0[k] + T[k] * rc.bg[0];
-            out[hw + pl] = C1[k] + T[k] * rc.bg[1];
-            out[2 * hw + pl] = C2[k] + T[k] * rc.bg[2];
+            const float o0 = C0[k] + T[k] * rc.bg[0];
+            const float o1 = C1[k] + T[k] * rc.bg[1];
+            const float o2 = C2[k] + T[k] * rc.bg[2];
+            if (rgb) {
+                float* out = rgb + 3 * V.pix_off;
+                out[pl] = o0;
+                out[hw + pl] = o1;
+                out[2 * hw + pl] = o2;
+            }
             T_final[V.pix_off + pl] = T[k];
             n_contrib[V.pix_off + pl] = last[k];
             if (n_used) n_used[V.pix_off + pl] = used[k];
+            if (target) {
+                const float* y = target + 3 * V.pix_off;
+                float* g = dL_drgb + 3 * V.pix_off;
+                const float d0 = o0 - y[pl], d1 = o1 - y[hw + pl], d2 = o2 - y[2 * hw + pl];
+                lsum += fabsf(d0) + fabsf(d1) + fabsf(d2);
+                g[pl] = d0 > 0.f ? scale : (d0 < 0.f ? -scale : 0.f);
+                g[hw + pl] = d1 > 0.f ? scale : (d1 < 0.f ? -scale : 0.f);
+                g[2 * hw + pl] = d2 > 0.f ? scale : (d2 < 0.f ? -scale : 0.f);
+            }
+        }
+    }
+    if (target) {
+        // per-tile partial, summed in a fixed order (indexed by tile, not by
+        // launch order, so the loss does not depend on the dispatch order)
+        for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+        __shared__ float s_l[NW];
+        if (lane == 0) s_l[w] = lsum;
+        __syncthreads();
+        if (t == 0) {
+            float tsum = 0.f;
+#pragma unroll
+            for (int i = 0; i < NW; ++i) tsum += s_l[i];
+            partials[tile] = tsum * scale;
         }
     }
 }
@@ -708,21 +744,32 @@ bool raster_variant_exists(int ts, int ppt, int batch) {
 
 cudaError_t launch_render_fwd(const BatchParam& bp, const RenderConst& rc, const WsPtrs& ws,
                               float* rgb, float* T_final, uint32_t* n_contrib, uint32_t* n_used,
-                              cudaStream_t s, Prof& pf) {
-    if (bp.total_tiles <= 0) return cudaSuccess;
+                              const float* target, float* dL_drgb, float* loss, cudaStream_t s, Prof& pf) {
+    if (bp.total_tiles <= 0) {
+        // no pixels: the loss is 0 (the caller's views are all non-empty, so
+        // this is unreachable through the C ABI; kept for safety)
+        if (target && loss) return cudaMemsetAsync(loss, 0, sizeof(float), s);
+        return cudaSuccess;
+    }
     const uint32_t* svals = ws.pvals[ws.sorted_buf];
+    float* partials = target ? ws.partials : nullptr;
     const int pi = pf.begin(GS_KF_RASTER_FWD, s);
     bool done = false;
 #define GS_X(T, P, B)                                                                                  \
     if (!done && bp.tile_size == T && bp.ppt == P && bp.batch == B) {                                  \
         pdl_launch(k_render_fwd<T, P, B>, bp.total_tiles, T * T / P, 0, s, bp, rc, ws.rec, ws.ranges, ws.ovals[1], svals, rgb, \
-                                                                    T_final, n_contrib, n_used);      \
+                   T_final, n_contrib, n_used, target, dL_drgb, partials);                             \
         done = true;                                                                                   \
     }
     GS_RASTER_VARIANTS(GS_X)
 #undef GS_X
     pf.end(pi, s);
     if (!done) return cudaErrorInvalidValue;
+    if (target && loss) {
+        const int pl = pf.begin(GS_KF_L1, s);
+        pdl_launch(k_l1_finish, 1, 1024, 0, s, partials, bp.total_tiles, loss);
+        pf.end(pl, s);
+    }
     return cudaGetLastError();
 }
 

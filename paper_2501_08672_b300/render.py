@@ -61,10 +61,11 @@ class Renderer:
     def layout(self):
         return self.ctx.layout(self.views, self.cap)
 
-    def forward(self, g, count=None, n_used=None):
+    def forward(self, g, count=None, n_used=None, target=None):
         """project + bin + composite into self.rgb / self.T / self.n_contrib.
         count: True synchronises to read the pair count and grows the workspace
-        if needed (default: only on the first call)."""
+        if needed (default: only on the first call).  target: also the L1 loss
+        against it, folded into the compositing (self.loss, self.dL_drgb)."""
         if count is None:
             count = not self._counted
         self.ctx.project(g, self.views, self.ws_struct)
@@ -82,7 +83,21 @@ class Renderer:
             self.last_pairs = n
         else:
             self.ctx.bin(self.views, self.ws_struct)
-        self.ctx.render_fwd(self.views, self.ws_struct, self.rgb, self.T, self.n_contrib, n_used)
+        if target is None:
+            self.ctx.render_fwd(self.views, self.ws_struct, self.rgb, self.T, self.n_contrib, n_used)
+        else:
+            self.ctx.render_fwd_l1(self.views, self.ws_struct, target, self.rgb, self.T, self.n_contrib,
+                                   self.dL_drgb, self.loss, n_used)
+
+    def forward_loss(self, g, target, ssim_lambda=0.0, count=None):
+        """forward + photometric loss and its gradient into self.loss and
+        self.dL_drgb: L1 in the same pass as the compositing, or the D-SSIM
+        variant after it when ssim_lambda > 0."""
+        if ssim_lambda > 0.0:
+            self.forward(g, count=count)
+            self.dssim(target, ssim_lambda)
+        else:
+            self.forward(g, count=count, target=target)
 
     def l1(self, target):
         self.ctx.l1_loss(self.views, self.ws_struct, self.rgb, target, self.dL_drgb, self.loss)
@@ -322,8 +337,7 @@ class WindowOptimizer:
         if self.graph is not None:
             return self.replay()
         w, r = self.win, self.r
-        r.forward(self._g, count=count)
-        r.loss_and_grad(self.targets, self.ssim_lambda)
+        r.forward_loss(self._g, self.targets, self.ssim_lambda, count=count)
         r.backward(self._g, r.dL_drgb, grads=self._grads)
         w.step_count += 1
         if w.capacity > w.n:  # spare rows (appends may be in flight there): Adam on the active rows only
@@ -351,8 +365,7 @@ class WindowOptimizer:
                 # the iteration (a tensor or context another part of the
                 # program frees meanwhile) does not invalidate it
                 with torch.cuda.graph(g, capture_error_mode="relaxed"):
-                    r.forward(self._g, count=False)
-                    r.loss_and_grad(self.targets, self.ssim_lambda)
+                    r.forward_loss(self._g, self.targets, self.ssim_lambda, count=False)
                     r.backward(self._g, r.dL_drgb, grads=self._grads)
                     if w.capacity > w.n:
                         r.ctx.adam_step_ranges(w.flat, w.gflat, w.m, w.v, w.active_ranges(), self.lr,
@@ -455,8 +468,7 @@ class PoseTracker:
 
     def iterate(self, view, target):
         self.r.set_views([view])
-        self.r.forward(self.g)
-        self.r.l1(target)
+        self.r.forward(self.g, target=target)
         self.r.pose_grad(self.g, self.r.dL_drgb)
         return self.r.dL_dpose
 

@@ -363,6 +363,70 @@ def test_backward_matches_oracle_multiview(orc):
     compare_grads(win, g, border, pose=r.dL_dpose.view(-1, 6).cpu().numpy().astype(np.float64), orc_pose=pose)
 
 
+FUSED_CASES = [("ragged", None), ("degenerate", (1, 1)), ("degenerate", (17, 1)), ("degenerate", (33, 2))]
+
+
+@pytest.mark.parametrize("case,size", FUSED_CASES)
+def test_fused_l1_matches_separate_passes(case, size):
+    """The compositing with the L1 loss folded in writes the image, T,
+    n_contrib and dL/drgb of the two separate passes bit for bit, in every
+    compiled launch shape; the loss differs only by the order of its FP32
+    sum.  Without an image pointer nothing but the image changes."""
+    from paper_2501_08672_b300.render import RASTER_VARIANTS
+    n = 3000
+    p = scenes.frustum_scene(n, seed=13)
+    if case == "ragged":
+        views = ragged_views(n)
+    else:
+        W, H = size
+        views = [scenes.identity_view(W, H, 0.5 * max(W, H) + 2.0, 0, n)]
+    tg = torch.cat([torch.as_tensor(t, dtype=torch.float32).reshape(-1) for t in l1_target(p, views)]).cuda()
+    win = GaussianWindow(p, 0)
+    for ts, ppt, batch in RASTER_VARIANTS:
+        r = Renderer(views, 0, ts, pixels_per_thread=ppt, batch=batch)
+        r.forward(win.struct())
+        r.l1(tg)
+        torch.cuda.synchronize()
+        ref = (r.rgb.clone(), r.T.clone(), r.n_contrib.clone(), r.dL_drgb.clone(), float(r.loss.item()))
+        for t in (r.rgb, r.T, r.dL_drgb, r.loss):
+            t.fill_(7.0)
+        r.n_contrib.fill_(7)
+        r.forward(win.struct(), target=tg)
+        torch.cuda.synchronize()
+        assert torch.equal(r.rgb, ref[0])
+        assert torch.equal(r.T, ref[1])
+        assert torch.equal(r.n_contrib, ref[2])
+        assert torch.equal(r.dL_drgb, ref[3])
+        assert abs(float(r.loss.item()) - ref[4]) <= 1e-6 * max(ref[4], 1e-3)
+        # no image pointer: the image buffer is left alone
+        r.rgb.fill_(-3.0)
+        r.dL_drgb.zero_()
+        r.loss.zero_()
+        r.ctx.render_fwd_l1(r.views, r.ws_struct, tg, None, r.T, r.n_contrib, r.dL_drgb, r.loss)
+        torch.cuda.synchronize()
+        assert bool((r.rgb == -3.0).all())
+        assert torch.equal(r.dL_drgb, ref[3])
+        assert abs(float(r.loss.item()) - ref[4]) <= 1e-6 * max(ref[4], 1e-3)
+
+
+def test_fused_l1_loss_matches_oracle(orc):
+    """Loss and gradients of the fused pass against the FP64 oracle
+    (Eq. gaussian_optimization with the L1 norm), over ragged views."""
+    p = scenes.frustum_scene(1500, seed=6)
+    views = ragged_views(1500)
+    tg = l1_target(p, views)
+    win = GaussianWindow(p, 0)
+    r = Renderer(views, 0, 16)
+    tgt = torch.cat([torch.as_tensor(t, dtype=torch.float32).reshape(-1) for t in tg]).cuda()
+    r.forward(win.struct(), target=tgt)
+    grads = win.grad_tensors()
+    r.backward(win.struct(), r.dL_drgb, grads=grads, want_pose=True)
+    torch.cuda.synchronize()
+    L, g, pose, border, _ = oracle_l1_backward(orc, p, views, tg, r)
+    assert abs(float(r.loss.item()) - L) < 1e-5
+    compare_grads(win, g, border, pose=r.dL_dpose.view(-1, 6).cpu().numpy().astype(np.float64), orc_pose=pose)
+
+
 def test_plain_single_view_fp32_10k(orc):
     """Configuration: 10k Gaussians in a 4x4x(2..8) m box, 320x256, fx=fy=300,
     16x16 tiles, SH degree 0, target = render of a perturbed copy, L1."""
