@@ -56,8 +56,8 @@ FP32_LANES = 128
 # kernel source they were taken on (sha256 prefix of gs_raster.cu up to the L1
 # kernels, which holds both compositing kernels) and the launch shape;
 # otherwise the roofline reports traffic null.
-TRAFFIC = {"raster_fwd": ("ef23c7ef071d47ac", (16, 2, 128), 182.0e6),
-           "raster_bwd": ("17c1fdd455f304a4", (16, 2, 128), 235.3e6)}
+TRAFFIC = {"raster_fwd": ("ef23c7ef071d47ac", (16, 2, 128), 181.7e6),
+           "raster_bwd": ("ef23c7ef071d47ac", (16, 2, 128), 234.7e6)}
 
 
 def raster_source_hash():
