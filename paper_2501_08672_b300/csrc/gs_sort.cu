@@ -655,16 +655,29 @@ __global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ order
         const int bx0 = rx & 0xFFFF, by0 = (rx >> 16) & 0xFFFF, bx1 = ry & 0xFFFF, by1 = (ry >> 16) & 0xFFFF;
         unsigned long long o = bo0;
         for (int row0 = by0; row0 < by1; row0 += 32) {
+            // lane l finds the span of tile row row0 + l; the rows' runs then
+            // fill [o, o + total) and the warp writes that range together
+            // (lane l positions l, l + 32, ...), each position's row found
+            // by a binary search over the lanes' run starts as in the mask path
             const int ty = row0 + lane;
             int a = 0, b = -1;
             if (ty < by1 && !footrows_span(bf, ty, ts, bx0, bx1, &a, &b)) b = -1;
             uint32_t total;
             const uint32_t cnt = (uint32_t)(b - a + 1);
-            const unsigned long long pos = o + warp_exclusive_scan(cnt, &total);
-            for (int tx = a; tx <= b; ++tx) {
-                const unsigned long long q = pos + (unsigned long long)(tx - a);
-                if (q < boend && q < ucap) {
-                    pkeys[q] = bz + (uint32_t)ty * bwid + (uint32_t)tx;
+            const uint32_t start = warp_exclusive_scan(cnt, &total);
+            for (uint32_t p0 = 0; p0 < total; p0 += 32) {
+                const uint32_t pr = p0 + (uint32_t)lane;
+                int e = 0;
+#pragma unroll
+                for (int st = 16; st >= 1; st >>= 1) {
+                    const uint32_t sc = __shfl_sync(0xffffffffu, start, e + st);
+                    if (sc <= pr) e += st;
+                }
+                const int ae = __shfl_sync(0xffffffffu, a, e);
+                const uint32_t se = __shfl_sync(0xffffffffu, start, e);
+                const unsigned long long q = o + pr;
+                if (pr < total && q < boend && q < ucap) {
+                    pkeys[q] = bz + (uint32_t)(row0 + e) * bwid + (uint32_t)ae + (pr - se);
                     pvals[q] = br;
                 }
             }
