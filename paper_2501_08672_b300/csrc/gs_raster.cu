@@ -110,8 +110,7 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_render_fwd(const __grid_const
     constexpr int WB = 32 * Q;
     __shared__ float4 s_a[NW][WB];
     __shared__ float4 s_b[NW][WB];
-    __shared__ float2 s_c[NW][WB];
-    __shared__ uint32_t s_j[NW][WB];
+    __shared__ float4 s_c[NW][WB];  // colour 1, 2; list position + 1 (bits)
     const int t = threadIdx.x;
     const int lane = t & 31;
     const int w = t >> 5;
@@ -165,8 +164,7 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_render_fwd(const __grid_const
                 const int pos = n + __popc(m & lt_mask);
                 s_a[w][pos] = a;
                 s_b[w][pos] = b;
-                s_c[w][pos] = make_float2(c.x, c.y);
-                s_j[w][pos] = idx - rg.x + 1;
+                s_c[w][pos] = make_float4(c.x, c.y, __uint_as_float(idx - rg.x + 1), 0.f);
             }
             n += __popc(m);
         }
@@ -175,8 +173,8 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_render_fwd(const __grid_const
             for (int j = 0; j < n; ++j) {
                 const float4 a = s_a[w][j];
                 const float4 b = s_b[w][j];
-                const float2 c = s_c[w][j];
-                const uint32_t pos1 = s_j[w][j];
+                const float4 c = s_c[w][j];
+                const uint32_t pos1 = __float_as_uint(c.z);
                 const float dx = fx - a.x;
                 const float u1 = dx * a.z, u2 = dx * b.x;
 #pragma unroll
@@ -298,9 +296,7 @@ __global__ void __launch_bounds__(TS * TS / PPT, bwd_min_blocks<TS * TS / PPT, P
     constexpr int WB = 32 * Q;
     __shared__ float4 s_a[NW][WB];
     __shared__ float4 s_b[NW][WB];
-    __shared__ float2 s_c[NW][WB];
-    __shared__ uint32_t s_r[NW][WB];
-    __shared__ int s_rel[NW][WB];
+    __shared__ float4 s_c[NW][WB];  // colour 1, 2; position in the list (bits); record (bits)
     const int t = threadIdx.x;
     const int lane = t & 31;
     const int warp = t >> 5;
@@ -364,9 +360,7 @@ __global__ void __launch_bounds__(TS * TS / PPT, bwd_min_blocks<TS * TS / PPT, P
                 const int pos = n + __popc(m & lt_mask);
                 s_a[warp][pos] = a;
                 s_b[warp][pos] = b;
-                s_c[warp][pos] = make_float2(c.x, c.y);
-                s_r[warp][pos] = r;
-                s_rel[warp][pos] = rel;
+                s_c[warp][pos] = make_float4(c.x, c.y, __int_as_float(rel), __uint_as_float(r));
             }
             n += __popc(m);
         }
@@ -384,10 +378,11 @@ __global__ void __launch_bounds__(TS * TS / PPT, bwd_min_blocks<TS * TS / PPT, P
             for (int g = 0; g < kGroup; ++g) {
                 const int j = j0 + g;
                 if (j >= n) break;
-                const int rel = s_rel[warp][j];
+
                 const float4 a = s_a[warp][j];
                 const float4 b = s_b[warp][j];
-                const float2 c = s_c[warp][j];
+                const float4 c = s_c[warp][j];
+                const int rel = __float_as_int(c.z);
                 const float dx = fx - a.x;
                 const float u1 = dx * a.z, u2 = dx * b.x;
 #pragma unroll
@@ -462,7 +457,7 @@ __global__ void __launch_bounds__(TS * TS / PPT, bwd_min_blocks<TS * TS / PPT, P
                 for (int o = 4; o > 0; o >>= 1) yb += __shfl_xor_sync(0xffffffffu, yb, o);
                 const int gl = lane >> 3, el = lane & 7;
                 if (j0 + gl < n) {
-                    float* dst = grad2d + (size_t)s_r[warp][j0 + gl] * kGrad2D;
+                    float* dst = grad2d + (size_t)__float_as_uint(s_c[warp][j0 + gl].w) * kGrad2D;
                     if (x[0] != 0.f) atomicAdd(dst + el, x[0]);
                     if (el == 0 && yb != 0.f) atomicAdd(dst + 8, yb);
                 }
