@@ -354,7 +354,7 @@ __global__ void __launch_bounds__(256) k_project(const __grid_constant__ BatchPa
 // Backward
 
 template <int D>
-__global__ void __launch_bounds__(256) k_project_bwd(const __grid_constant__ BatchParam bp,
+__global__ void __launch_bounds__(256, 3) k_project_bwd(const __grid_constant__ BatchParam bp,
                                                      GaussPtrs g, RenderConst rc, WsPtrs ws,
                                                      GradPtrs gr, int want_params, int want_pose,
                                                      int pose_blocks) {

@@ -137,8 +137,18 @@ __global__ void __launch_bounds__(kRadixThreads, 3) k_radix_downsweep(
 #pragma unroll
     for (int k = 0; k < kRItems; ++k) {
         const bool valid = w * kSlice + k * 32 + lane < count;
-        const uint32_t d = valid ? ((key[k] >> shift) & mask) : 0x100u;
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t d = (key[k] >> shift) & mask;
+        // lanes holding the same digit: one ballot per digit bit (an invalid
+        // lane is its own group)
+        const uint32_t vm = __ballot_sync(0xffffffffu, valid);
+        uint32_t peers = vm;
+#pragma unroll
+        for (int bit = 0; bit < 8; ++bit) {
+            const bool set = (d >> bit) & 1u;
+            const uint32_t bm = __ballot_sync(0xffffffffu, set);
+            peers &= set ? bm : ~bm;
+        }
+        if (!valid) peers = 1u << lane;
         const int leader = __ffs(peers) - 1;
         uint32_t before = 0;
         if (valid && lane == leader) {
