@@ -737,36 +737,48 @@ __global__ void __launch_bounds__(256) k_ranges(const uint32_t* __restrict__ key
     const uint4* __restrict__ k4 = reinterpret_cast<const uint4*>(keys);
     const int lane = threadIdx.x & 31;
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-    // every lane of a warp runs the same number of rounds (shuffles need all 32)
-    for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < n4;
-         base += stride) {
-        const unsigned long long g = base + lane;
-        const unsigned long long j0 = 4 * g;
-        uint32_t v[4] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
-        if (j0 + 3 < n) {
-            const uint4 q = k4[g];
-            v[0] = q.x;
-            v[1] = q.y;
-            v[2] = q.z;
-            v[3] = q.w;
-        } else {
+    // every lane of a warp runs the same number of rounds (shuffles need all 32);
+    // each round takes two chunks of 32 x 4 keys, both loaded first
+    for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x * 2 + (threadIdx.x & ~31u) * 2; base < n4;
+         base += stride * 2) {
+        uint32_t v[2][4];
+        uint32_t pv[2], nx[2];
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
-                if (j0 + i < n) v[i] = keys[j0 + i];
+        for (int c = 0; c < 2; ++c) {
+            const unsigned long long g = base + 32 * c + lane;
+            const unsigned long long j0 = 4 * g;
+            v[c][0] = v[c][1] = v[c][2] = v[c][3] = 0xFFFFFFFFu;
+            if (j0 + 3 < n) {
+                const uint4 q = k4[g];
+                v[c][0] = q.x; v[c][1] = q.y; v[c][2] = q.z; v[c][3] = q.w;
+            } else {
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    if (j0 + i < n) v[c][i] = keys[j0 + i];
+            }
+            pv[c] = 0xFFFFFFFFu;
+            nx[c] = 0xFFFFFFFFu;
+            if (lane == 0 && j0 > 0 && j0 - 1 < n) pv[c] = keys[j0 - 1];
+            if (lane == 31 && j0 + 4 < n) nx[c] = keys[j0 + 4];
         }
-        uint32_t prev = __shfl_up_sync(0xffffffffu, v[3], 1);
-        uint32_t next = __shfl_down_sync(0xffffffffu, v[0], 1);
-        if (lane == 0) prev = j0 > 0 && j0 - 1 < n ? keys[j0 - 1] : 0xFFFFFFFFu;
-        if (lane == 31) next = j0 + 4 < n ? keys[j0 + 4] : 0xFFFFFFFFu;
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const unsigned long long j = j0 + i;
-            const uint32_t k = v[i];
-            if (j >= n || k >= n_tiles) continue;  // tile ids come from k_emit and are < n_tiles
-            const uint32_t p = i > 0 ? v[i - 1] : prev;
-            const uint32_t x = i < 3 ? v[i + 1] : next;
-            if (j == 0 || p != k) ranges[k].x = (uint32_t)j;
-            if (j + 1 == n || x != k) ranges[k].y = (uint32_t)(j + 1);
+        for (int c = 0; c < 2; ++c) {
+            const unsigned long long g = base + 32 * c + lane;
+            const unsigned long long j0 = 4 * g;
+            uint32_t prev = __shfl_up_sync(0xffffffffu, v[c][3], 1);
+            uint32_t next = __shfl_down_sync(0xffffffffu, v[c][0], 1);
+            if (lane == 0) prev = pv[c];
+            if (lane == 31) next = nx[c];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const unsigned long long j = j0 + i;
+                const uint32_t k = v[c][i];
+                if (j >= n || k >= n_tiles) continue;
+                const uint32_t p = i > 0 ? v[c][i - 1] : prev;
+                const uint32_t x = i < 3 ? v[c][i + 1] : next;
+                if (j == 0 || p != k) ranges[k].x = (uint32_t)j;
+                if (j + 1 == n || x != k) ranges[k].y = (uint32_t)(j + 1);
+            }
         }
     }
 }
