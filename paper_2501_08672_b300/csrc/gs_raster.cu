@@ -709,23 +709,36 @@ __global__ void __launch_bounds__(TS * TS) k_render_pose_normal(const __grid_con
 }
 
 // Per view: the FP64 sum of its tiles' partials.  grid.x is the view.
-__global__ void __launch_bounds__(256) k_pose_normal_finish(const __grid_constant__ BatchParam bp,
-                                                            const float* __restrict__ partials,
-                                                            double* __restrict__ normal) {
+constexpr int kPNFinishGroups = 32;  // warps per view in the final sum
+
+__global__ void __launch_bounds__(32 * kPNFinishGroups) k_pose_normal_finish(const __grid_constant__ BatchParam bp,
+                                                                          const float* __restrict__ partials,
+                                                                          double* __restrict__ normal) {
     pdl_wait();
     pdl_trigger();
-    __shared__ double s_sum[8][32];
+    __shared__ double s_sum[kPNFinishGroups][32];
     const ViewParam& V = bp.v[blockIdx.x];
     const int e = threadIdx.x & 31, grp = threadIdx.x >> 5;
     const int ntiles = V.tiles_x * ((V.H + bp.tile_size - 1) / bp.tile_size);
+    const float* src = partials + (size_t)V.tile_off * kNormalVals + e;
     double acc = 0.0;
-    if (e < kNormalVals)
-        for (int tl = grp; tl < ntiles; tl += 8) acc += (double)partials[(size_t)(V.tile_off + tl) * kNormalVals + e];
+    if (e < kNormalVals) {
+        // warp grp sums tiles grp, grp + G, ...; eight loads in flight per lane
+        int tl = grp;
+        for (; tl + 7 * kPNFinishGroups < ntiles; tl += 8 * kPNFinishGroups) {
+            float v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = src[(size_t)(tl + u * kPNFinishGroups) * kNormalVals];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) acc += (double)v[u];
+        }
+        for (; tl < ntiles; tl += kPNFinishGroups) acc += (double)src[(size_t)tl * kNormalVals];
+    }
     s_sum[grp][e] = acc;
     __syncthreads();
     if (threadIdx.x < kNormalVals) {
         double v = 0.0;
-        for (int g = 0; g < 8; ++g) v += s_sum[g][threadIdx.x];
+        for (int g = 0; g < kPNFinishGroups; ++g) v += s_sum[g][threadIdx.x];
         normal[(size_t)blockIdx.x * kNormalVals + threadIdx.x] = v;
     }
 }
@@ -895,7 +908,7 @@ cudaError_t launch_pose_normal(const BatchParam& bp, const RenderConst& rc, cons
                                                                  tangents, target, partials, H_pix);
     else
         return cudaErrorInvalidValue;
-    pdl_launch(k_pose_normal_finish, bp.n_views, 256, 0, s, bp, partials, normal);
+    pdl_launch(k_pose_normal_finish, bp.n_views, 32 * kPNFinishGroups, 0, s, bp, partials, normal);
     pf.end(pi, s);
     return cudaGetLastError();
 }

@@ -474,11 +474,18 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_offsets(const uint32_t* _
     const long long base = chunk * kScanChunk + (long long)t * kScanItems;
     uint32_t v[kScanItems];
     uint32_t sum = 0;
+    if (base + kScanItems <= M) {  // 16-byte aligned: base is a multiple of 4
+        const uint4 o4 = *reinterpret_cast<const uint4*>(order + base);
+        v[0] = touched[o4.x];
+        v[1] = touched[o4.y];
+        v[2] = touched[o4.z];
+        v[3] = touched[o4.w];
+    } else {
 #pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-        v[k] = base + k < M ? touched[order[base + k]] : 0u;
-        sum += v[k];
+        for (int k = 0; k < kScanItems; ++k) v[k] = base + k < M ? touched[order[base + k]] : 0u;
     }
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) sum += v[k];
     uint32_t agg32;
     const uint32_t ex = block_exclusive_scan(sum, agg32);
     if (t < 32) {
@@ -527,12 +534,19 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_offsets(const uint32_t* _
     }
     __syncthreads();
     unsigned long long run = s_prefix + ex;
+    if (base + kScanItems <= M) {
+        ulonglong2* o2 = reinterpret_cast<ulonglong2*>(offsets + base);
+        const unsigned long long r1 = run + v[0], r2 = r1 + v[1], r3 = r2 + v[2];
+        o2[0] = make_ulonglong2(run, r1);
+        o2[1] = make_ulonglong2(r2, r3);
+    } else {
 #pragma unroll
-    for (int k = 0; k < kScanItems; ++k)
-        if (base + k < M) {
-            offsets[base + k] = run;
-            run += v[k];
-        }
+        for (int k = 0; k < kScanItems; ++k)
+            if (base + k < M) {
+                offsets[base + k] = run;
+                run += v[k];
+            }
+    }
 }
 
 // One thread per record in depth order writes its pairs (global tile id,

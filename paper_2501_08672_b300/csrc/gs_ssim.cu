@@ -232,7 +232,16 @@ __global__ void k_ssim_finish(const float* __restrict__ partials, long long n, f
     pdl_trigger();
     __shared__ float sw[32];
     float s = 0.f;
-    for (long long i = threadIdx.x; i < n; i += blockDim.x) s += partials[i];
+    const long long nb = blockDim.x;
+    long long i = threadIdx.x;
+    for (; i + 7 * nb < n; i += 8 * nb) {  // eight loads in flight per thread
+        float v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = partials[i + u * nb];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) s += v[u];
+    }
+    for (; i < n; i += nb) s += partials[i];
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = s;
     __syncthreads();
