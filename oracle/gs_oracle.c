@@ -53,6 +53,24 @@
 
 #define ORC_PI 3.14159265358979323846
 
+/* Host threads of the parallel loops: n_threads > 0 for one call, otherwise
+ * the process-wide count set by orc_set_num_threads (all processors by
+ * default).  Threads only split independent pixels or Gaussians; every sum
+ * over threads is taken in thread order. */
+static int orc_default_threads = 0;
+
+static int orc_threads(int n_threads) {
+    if (n_threads > 0) return n_threads;
+    if (orc_default_threads > 0) return orc_default_threads;
+#ifdef _OPENMP
+    return omp_get_num_procs();
+#else
+    return 1;
+#endif
+}
+
+void orc_set_num_threads(int n) { orc_default_threads = n > 0 ? n : 0; }
+
 /* Unit roundoff of binary32.  Depth order is decided on the camera depth
  * R_CW[2] . p_W + t_CW[2] of binary32 inputs evaluated as a compensated dot
  * product in binary32 arithmetic ("Dot2", Ogita, Rump and Oishi 2005), whose
@@ -260,6 +278,12 @@ int orc_project(long n, const double* means, const double* log_scales, const dou
                 double* conic, double* opac, double* colour, double* raw_colour,
                 double* depth_err) {
     int K = (sh_degree + 1) * (sh_degree + 1);
+    int nthr = orc_threads(0);
+    (void)nthr;
+    /* Gaussians are independent. */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) num_threads(nthr)
+#endif
     for (long i = 0; i < n; ++i) {
         orc_proj P;
         project_one(means + 3 * i, log_scales + 3 * i, quats + 4 * i, opacity[i], sh + 3 * K * i,
@@ -362,9 +386,10 @@ int orc_render(int W, int H, long n, const int* valid, const double* q, const do
     long* order = (long*)malloc(sizeof(long) * (n > 0 ? n : 1));
     long m = depth_order(n, valid, depth, order);
     const double* bg = cfg + 5;
+    int nthr = orc_threads(n_threads);
+    (void)nthr;
 #ifdef _OPENMP
-    if (n_threads > 0) omp_set_num_threads(n_threads);
-#pragma omp parallel
+#pragma omp parallel num_threads(nthr)
 #endif
     {
         orc_frag* frags = (orc_frag*)malloc(sizeof(orc_frag) * (m > 0 ? m : 1));
@@ -407,14 +432,15 @@ int orc_render_pixels(long n_pix, const int* px, const int* py, long n, const in
     long* order = (long*)malloc(sizeof(long) * (n > 0 ? n : 1));
     long m = depth_order(n, valid, depth, order);
     const double* bg = cfg + 5;
+    int nthr = orc_threads(n_threads);
+    (void)nthr;
 #ifdef _OPENMP
-    if (n_threads > 0) omp_set_num_threads(n_threads);
-#pragma omp parallel
+#pragma omp parallel num_threads(nthr)
 #endif
     {
         orc_frag* frags = (orc_frag*)malloc(sizeof(orc_frag) * (m > 0 ? m : 1));
 #ifdef _OPENMP
-#pragma omp for schedule(dynamic, 16)
+#pragma omp for schedule(dynamic, 1)
 #endif
         for (long k = 0; k < n_pix; ++k) {
             double T;
@@ -438,34 +464,46 @@ int orc_render_pixels(long n_pix, const int* px, const int* py, long n, const in
     return 0;
 }
 
+/* One Gaussian's share of one pixel's gradient: dq_x, dq_y, dA, dB, dC,
+ * dsigma, dc_r, dc_g, dc_b. */
+typedef struct { long i; double a[9]; } orc_contrib;
+
+/* A pixel's contributions and the Gaussians it flags as borderline. */
+typedef struct { long n, nb; orc_contrib* c; long* b; } orc_pixel_out;
+
 /* Backward of Eq. raster at one pixel centre (px, py) with dL/dI = g[3]:
- * accumulates into a[9 i + k] (dq_x, dq_y, dA, dB, dC, dsigma, dc_r, dc_g,
- * dc_b) and flags ba[i] for Gaussians active at a borderline pixel.
+ * fills out->c with one record per contributing Gaussian and out->b with the
+ * Gaussians active at the pixel when it is borderline.
  * Written from the chain rule on Eq. raster: with T_k the transmittance in
  * front of fragment k and S_k the light composited behind it (including the
  * background through T_final),
  *   dI/dc_k = alpha_k T_k,  dI/dalpha_k = c_k T_k - S_k / (1 - alpha_k),
  * alpha_k = sigma_k G_k (unless clamped), G = exp(power),
- * power = -1/2 (A dx^2 + 2 B dx dy + C dy^2), dx = px - q_x. */
+ * power = -1/2 (A dx^2 + 2 B dx dy + C dy^2), dx = px - q_x.
+ * A pixel with dL/dI = 0 contributes nothing to any gradient, so it is
+ * skipped and flags nothing: its threshold decisions cannot change a
+ * gradient. */
 static void backward_pixel(double px, double py, const double* g, long m, const long* order,
                            const double* q, const double* conic, const double* opac,
                            const double* colour, const double* depth, const double* depth_err,
-                           const double* cfg,
-                           orc_frag* frags, double* S, double* a, unsigned char* ba) {
+                           const double* cfg, orc_frag* frags, double* S, orc_pixel_out* out) {
     const double* bg = cfg + 5;
     double amax = cfg[1], amin = cfg[0];
     double T;
     int bd;
     long ncons;
+    out->n = 0; out->nb = 0; out->c = NULL; out->b = NULL;
+    if (g[0] == 0.0 && g[1] == 0.0 && g[2] == 0.0) return;
     long nf = composite_pixel(px, py, m, order, q, conic, opac, depth, depth_err, cfg, frags, &T, &bd, &ncons);
     if (bd) {
         /* Every Gaussian that could be active here is unreliable. */
+        out->b = (long*)malloc(sizeof(long) * (ncons > 0 ? ncons : 1));
         for (long k = 0; k < ncons && k < m; ++k) {
             long i = order[k];
             double dx = px - q[2 * i], dy = py - q[2 * i + 1];
             double pw = -0.5 * (conic[3 * i] * dx * dx + 2.0 * conic[3 * i + 1] * dx * dy +
                                 conic[3 * i + 2] * dy * dy);
-            if (opac[i] * exp(pw) >= amin * (1.0 - REL_BORDER)) ba[i] = 1;
+            if (opac[i] * exp(pw) >= amin * (1.0 - REL_BORDER)) out->b[out->nb++] = i;
         }
     }
     /* S_k = sum_{j>k} c_j alpha_j T_j + T_final bg, from the back. */
@@ -475,12 +513,16 @@ static void backward_pixel(double px, double py, const double* g, long m, const 
         long i = frags[f].i;
         for (int ch = 0; ch < 3; ++ch) run[ch] += colour[3 * i + ch] * frags[f].alpha * frags[f].Tin;
     }
+    out->c = (orc_contrib*)calloc(nf > 0 ? nf : 1, sizeof(orc_contrib));
+    out->n = nf;
     for (long f = 0; f < nf; ++f) {
         long i = frags[f].i;
+        double* a = out->c[f].a;
+        out->c[f].i = i;
         double al = frags[f].alpha, Tk = frags[f].Tin;
         double dLda = 0.0;
         for (int ch = 0; ch < 3; ++ch) {
-            a[9 * i + 6 + ch] += al * Tk * g[ch];
+            a[6 + ch] = al * Tk * g[ch];
             dLda += g[ch] * (colour[3 * i + ch] * Tk - S[3 * f + ch] / (1.0 - al));
         }
         if (frags[f].araw < amax) {
@@ -488,12 +530,12 @@ static void backward_pixel(double px, double py, const double* g, long m, const 
             double dx = frags[f].dx, dy = frags[f].dy;
             double A = conic[3 * i], B = conic[3 * i + 1], C = conic[3 * i + 2];
             double dLdpow = dLda * sg * G;
-            a[9 * i + 5] += dLda * G;
-            a[9 * i + 0] += dLdpow * (A * dx + B * dy);
-            a[9 * i + 1] += dLdpow * (B * dx + C * dy);
-            a[9 * i + 2] += dLdpow * (-0.5 * dx * dx);
-            a[9 * i + 3] += dLdpow * (-dx * dy);
-            a[9 * i + 4] += dLdpow * (-0.5 * dy * dy);
+            a[5] = dLda * G;
+            a[0] = dLdpow * (A * dx + B * dy);
+            a[1] = dLdpow * (B * dx + C * dy);
+            a[2] = dLdpow * (-0.5 * dx * dx);
+            a[3] = dLdpow * (-dx * dy);
+            a[4] = dLdpow * (-0.5 * dy * dy);
         }
     }
 }
@@ -507,7 +549,9 @@ static void backward_pixel(double px, double py, const double* g, long m, const 
  *                  -1/2 (A dx^2 + 2 B dx dy + C dy^2)
  *   g_opac [n]     dL/dsigma
  *   g_colour [n,3] dL/dc
- *   g_border [n]   set to 1 for Gaussians active at a borderline pixel. */
+ *   g_border [n]   set to 1 for Gaussians active at a borderline pixel.
+ * Pixels are processed in parallel; their contributions are then added in
+ * pixel order, so the result does not depend on the thread count. */
 static int render_backward_impl(int W, int H, long n_pix, const int* pxs, const int* pys, long n,
                                 const int* valid, const double* q, const double* conic,
                                 const double* opac, const double* colour, const double* depth,
@@ -517,29 +561,18 @@ static int render_backward_impl(int W, int H, long n_pix, const int* pxs, const 
                                 unsigned char* g_border, int n_threads) {
     long* order = (long*)malloc(sizeof(long) * (n > 0 ? n : 1));
     long m = depth_order(n, valid, depth, order);
-    int nt = 1;
-#ifdef _OPENMP
-    if (n_threads > 0) omp_set_num_threads(n_threads);
-    nt = omp_get_max_threads();
-#endif
+    int nthr = orc_threads(n_threads);
+    (void)nthr;
     long total = pxs ? n_pix : (long)W * H;
-    /* Per-thread accumulators, summed at the end. */
-    double* acc = (double*)calloc((size_t)nt * (n > 0 ? n : 1) * 9, sizeof(double));
-    unsigned char* bacc = (unsigned char*)calloc((size_t)nt * (n > 0 ? n : 1), 1);
+    orc_pixel_out* outs = (orc_pixel_out*)calloc(total > 0 ? total : 1, sizeof(orc_pixel_out));
 #ifdef _OPENMP
-#pragma omp parallel
+#pragma omp parallel num_threads(nthr)
 #endif
     {
-        int tid = 0;
-#ifdef _OPENMP
-        tid = omp_get_thread_num();
-#endif
-        double* a = acc + (size_t)tid * n * 9;
-        unsigned char* ba = bacc + (size_t)tid * n;
         orc_frag* frags = (orc_frag*)malloc(sizeof(orc_frag) * (m > 0 ? m : 1));
         double* S = (double*)malloc(sizeof(double) * 3 * (m > 0 ? m : 1));
 #ifdef _OPENMP
-#pragma omp for schedule(dynamic, 64)
+#pragma omp for schedule(dynamic, 1)
 #endif
         for (long k = 0; k < total; ++k) {
             double px, py, g[3];
@@ -551,24 +584,25 @@ static int render_backward_impl(int W, int H, long n_pix, const int* pxs, const 
                 for (int ch = 0; ch < 3; ++ch) g[ch] = dL_drgb[(long)ch * W * H + k];
             }
             backward_pixel(px, py, g, m, order, q, conic, opac, colour, depth, depth_err, cfg, frags, S,
-                           a, ba);
+                           &outs[k]);
         }
         free(S);
         free(frags);
     }
-    for (int tt = 0; tt < nt; ++tt) {
-        const double* a = acc + (size_t)tt * n * 9;
-        const unsigned char* ba = bacc + (size_t)tt * n;
-        for (long i = 0; i < n; ++i) {
-            g_q[2 * i] += a[9 * i]; g_q[2 * i + 1] += a[9 * i + 1];
-            for (int k = 0; k < 3; ++k) g_conic[3 * i + k] += a[9 * i + 2 + k];
-            g_opac[i] += a[9 * i + 5];
-            for (int k = 0; k < 3; ++k) g_colour[3 * i + k] += a[9 * i + 6 + k];
-            if (ba[i]) g_border[i] = 1;
+    for (long k = 0; k < total; ++k) {
+        for (long f = 0; f < outs[k].n; ++f) {
+            long i = outs[k].c[f].i;
+            const double* a = outs[k].c[f].a;
+            g_q[2 * i] += a[0]; g_q[2 * i + 1] += a[1];
+            for (int c = 0; c < 3; ++c) g_conic[3 * i + c] += a[2 + c];
+            g_opac[i] += a[5];
+            for (int c = 0; c < 3; ++c) g_colour[3 * i + c] += a[6 + c];
         }
+        for (long f = 0; f < outs[k].nb; ++f) g_border[outs[k].b[f]] = 1;
+        free(outs[k].c);
+        free(outs[k].b);
     }
-    free(acc);
-    free(bacc);
+    free(outs);
     free(order);
     return 0;
 }
@@ -612,6 +646,14 @@ int orc_project_backward(long n, const double* means, const double* log_scales,
     int K = (sh_degree + 1) * (sh_degree + 1);
     const double* W = cam;
     double fx = cam[12], fy = cam[13];
+    /* Gaussians are independent except for the pose gradient: each writes its
+     * own pose term, and the terms are added in Gaussian order afterwards. */
+    double* pose_i = g_pose ? (double*)calloc((size_t)(n > 0 ? n : 1) * 6, sizeof(double)) : NULL;
+    int nthr = orc_threads(0);
+    (void)nthr;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 256) num_threads(nthr)
+#endif
     for (long i = 0; i < n; ++i) {
         orc_proj P;
         const double* shi = sh + 3 * K * i;
@@ -733,20 +775,26 @@ int orc_project_backward(long n, const double* means, const double* log_scales,
 
         /* Pose, left perturbation: p_C <- p_C + dphi x p_C + dt, W <- W + [dphi]x W,
          * campos <- campos - W^T dt. */
-        if (g_pose) {
+        if (pose_i) {
             double gW_Wt[9];
+            double* gpi = pose_i + 6 * i;
             for (int a = 0; a < 3; ++a)
                 for (int b = 0; b < 3; ++b) {
                     double s = 0.0;
                     for (int k = 0; k < 3; ++k) s += gW[3 * a + k] * W[3 * b + k];
                     gW_Wt[3 * a + b] = s;
                 }
-            g_pose[0] += (P.pc[1] * gp[2] - P.pc[2] * gp[1]) + (gW_Wt[7] - gW_Wt[5]);
-            g_pose[1] += (P.pc[2] * gp[0] - P.pc[0] * gp[2]) + (gW_Wt[2] - gW_Wt[6]);
-            g_pose[2] += (P.pc[0] * gp[1] - P.pc[1] * gp[0]) + (gW_Wt[3] - gW_Wt[1]);
+            gpi[0] = (P.pc[1] * gp[2] - P.pc[2] * gp[1]) + (gW_Wt[7] - gW_Wt[5]);
+            gpi[1] = (P.pc[2] * gp[0] - P.pc[0] * gp[2]) + (gW_Wt[2] - gW_Wt[6]);
+            gpi[2] = (P.pc[0] * gp[1] - P.pc[1] * gp[0]) + (gW_Wt[3] - gW_Wt[1]);
             for (int k = 0; k < 3; ++k)
-                g_pose[3 + k] += gp[k] + (W[3 * k] * gd[0] + W[3 * k + 1] * gd[1] + W[3 * k + 2] * gd[2]);
+                gpi[3 + k] = gp[k] + (W[3 * k] * gd[0] + W[3 * k + 1] * gd[1] + W[3 * k + 2] * gd[2]);
         }
+    }
+    if (pose_i) {
+        for (long i = 0; i < n; ++i)
+            for (int k = 0; k < 6; ++k) g_pose[k] += pose_i[6 * i + k];
+        free(pose_i);
     }
     return 0;
 }
@@ -896,14 +944,15 @@ int orc_pose_jacobian_pixels(long n_pix, const int* pxs, const int* pys, long n,
         }
     }
     long m = depth_order(n, valid, depth, order);
+    int nthr = orc_threads(n_threads);
+    (void)nthr;
 #ifdef _OPENMP
-    if (n_threads > 0) omp_set_num_threads(n_threads);
-#pragma omp parallel
+#pragma omp parallel num_threads(nthr)
 #endif
     {
         orc_frag* frags = (orc_frag*)malloc(sizeof(orc_frag) * (m > 0 ? m : 1));
 #ifdef _OPENMP
-#pragma omp for schedule(dynamic, 16)
+#pragma omp for schedule(dynamic, 1)
 #endif
         for (long p = 0; p < n_pix; ++p) {
             double T;
@@ -964,10 +1013,4 @@ void orc_adam(long n, double* p, const double* g, double* m, double* v, double l
     }
 }
 
-int orc_num_threads(void) {
-#ifdef _OPENMP
-    return omp_get_max_threads();
-#else
-    return 1;
-#endif
-}
+int orc_num_threads(void) { return orc_threads(0); }

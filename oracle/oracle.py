@@ -77,6 +77,8 @@ def lib():
                                ctypes.c_double, ctypes.c_double, ctypes.c_long]
         L.orc_adam.restype = None
         L.orc_num_threads.restype = ctypes.c_int
+        L.orc_set_num_threads.argtypes = [ctypes.c_int]
+        L.orc_set_num_threads.restype = None
         L.orc_pose_jacobian_pixels.argtypes = ([ctypes.c_long, P, P, ctypes.c_long] + [P] * 5 + [ctypes.c_int] +
                                                [P] * 5 + [ctypes.c_int])
         L.orc_sh_basis.argtypes = [ctypes.c_long, P, ctypes.c_int, P, P]
@@ -134,7 +136,8 @@ def project(params, view, cfg=None):
 
 def render_view(params, view, cfg=None, n_threads=0, proj=None):
     """Eq. raster for one view: returns rgb [3,H,W], T_final [H,W], contributor
-    count [H,W] and the borderline-pixel mask [H,W]."""
+    count [H,W], the borderline-pixel mask [H,W] and the opacities sigma of
+    the Gaussians in front of the camera."""
     W, H = int(view["W"]), int(view["H"])
     pr = proj if proj is not None else project(params, view, cfg)
     n = pr["valid"].shape[0]
@@ -145,7 +148,7 @@ def render_view(params, view, cfg=None, n_threads=0, proj=None):
     lib().orc_render(W, H, n, _p(pr["valid"]), _p(pr["q"]), _p(pr["conic"]), _p(pr["opac"]),
                      _p(pr["colour"]), _p(pr["depth"]), _p(pr["depth_err"]), _p(cfg_array(cfg)), _p(rgb), _p(T), _p(nc),
                      _p(bd), int(n_threads))
-    return dict(rgb=rgb, T=T, n_contrib=nc, border=bd.astype(bool))
+    return dict(rgb=rgb, T=T, n_contrib=nc, border=bd.astype(bool), sigma=pr["opac"][pr["valid"] == 1])
 
 
 def render_pixels(params, view, px, py, cfg=None, n_threads=0, proj=None):
@@ -163,7 +166,7 @@ def render_pixels(params, view, px, py, cfg=None, n_threads=0, proj=None):
     lib().orc_render_pixels(k, _p(px), _p(py), n, _p(pr["valid"]), _p(pr["q"]), _p(pr["conic"]),
                             _p(pr["opac"]), _p(pr["colour"]), _p(pr["depth"]), _p(pr["depth_err"]), _p(cfg_array(cfg)), _p(rgb),
                             _p(T), _p(nc), _p(bd), int(n_threads))
-    return dict(rgb=rgb, T=T, n_contrib=nc, border=bd.astype(bool))
+    return dict(rgb=rgb, T=T, n_contrib=nc, border=bd.astype(bool), sigma=pr["opac"][pr["valid"] == 1])
 
 
 def render(params, views, cfg=None, n_threads=0):
@@ -321,7 +324,14 @@ def adam(p, g, m, v, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8, step=1):
 
 
 def num_threads():
+    """Host threads the parallel loops use when a call passes n_threads=0."""
     return int(lib().orc_num_threads())
+
+
+def set_threads(n):
+    """Sets the host thread count of calls that pass n_threads=0 (n <= 0:
+    every processor).  Results do not depend on it."""
+    lib().orc_set_num_threads(int(n))
 
 
 def pose_jacobian(params, view, px, py, cfg=None, n_threads=0):

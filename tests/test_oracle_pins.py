@@ -512,6 +512,72 @@ def test_pixel_list_paths_agree_with_full_image(orc):
     np.testing.assert_allclose(pose2, pose1, rtol=1e-12, atol=1e-15)
 
 
+def test_backward_does_not_depend_on_thread_count(orc):
+    """The pixel loop runs in parallel, but each pixel's contributions are
+    added in pixel order and the projection backward's pose terms in
+    Gaussian order, so the FP64 result is the same bit for bit on any number
+    of host threads."""
+    p = scenes.frustum_scene(800, seed=5)
+    p["sh"] = np.concatenate([p["sh"], np.random.default_rng(1).normal(0, 0.2, (800, 3, 3)).astype(np.float32)], 1)
+    p["sh_degree"] = 1
+    v = scenes.lookat_view((0.3, -0.2, -0.5), (0.0, 0.0, 5.0), 64, 48, 60.0, 0, 800, up=(0, -1, 0))
+    w = np.random.default_rng(2).standard_normal((3, 48, 64))
+    outs = []
+    for nt in (1, 3, 8):
+        orc.set_threads(nt)
+        try:
+            outs.append(orc.backward(p, [v], [w], n_threads=nt))
+        finally:
+            orc.set_threads(0)
+    for g, pose, border in outs[1:]:
+        for k in g:
+            np.testing.assert_array_equal(g[k], outs[0][0][k])
+        np.testing.assert_array_equal(pose, outs[0][1])
+        np.testing.assert_array_equal(border, outs[0][2])
+
+
+def test_zero_gradient_pixels_contribute_and_flag_nothing(orc):
+    """A pixel whose dL/dI is zero adds nothing to any gradient, so the
+    backward over a pixel list with such pixels equals the backward over the
+    list without them, borderline flags included."""
+    p = scenes.frustum_scene(1500, seed=8)
+    v = scenes.identity_view(96, 80, 90.0, 0, 1500)
+    rng = np.random.default_rng(3)
+    px, py = rng.integers(0, 96, 400), rng.integers(0, 80, 400)
+    w = rng.standard_normal((400, 3))
+    zero = rng.random(400) < 0.4
+    w[zero] = 0.0
+    ga, pa, ba = orc.backward(p, [v], [w], pixels=[(px, py)])
+    keep = ~zero
+    gb, pb, bb = orc.backward(p, [v], [w[keep]], pixels=[(px[keep], py[keep])])
+    for k in ga:
+        np.testing.assert_array_equal(ga[k], gb[k])
+    np.testing.assert_array_equal(pa, pb)
+    np.testing.assert_array_equal(ba, bb)
+    # all zero: nothing at all
+    g0, p0, b0 = orc.backward(p, [v], [np.zeros((400, 3))], pixels=[(px, py)])
+    assert not b0.any() and not p0.any() and all(not g0[k].any() for k in g0)
+
+
+def test_borderline_share_follows_contributor_count(orc):
+    """The share of borderline pixels stays within twice the expectation
+    2 REL (n_contrib m + 1) that the parity tests bound it by (over a
+    footprint ln(alpha) is uniform between ln(alpha_min) and ln(sigma), so a
+    covering Gaussian lands within REL of alpha_min with probability
+    2 REL / ln(sigma / alpha_min); m is the mean of that reciprocal), on a
+    dense box-room view where pixels hold tens of contributors."""
+    n = 20_000
+    p = scenes.box_room_scene(n, seed=7)
+    v = scenes.arc_views(1, 192, 160, 180.0, n_gaussians=n)[0]
+    out = orc.render_view(p, v)
+    nbar = float(out["n_contrib"].mean())
+    assert nbar > 10
+    share = float(out["border"].mean())
+    s = out["sigma"][out["sigma"] > 1.0 / 255.0]
+    m = float(np.mean(1.0 / np.maximum(np.log(s * 255.0), 1.0)))
+    assert share <= 2.0 * 2.0 * 1e-5 * (nbar * m + 1.0)
+
+
 # ---- pose Jacobian and normal equations (Sec. II-D, Eq. minimization) ----
 
 @pytest.mark.parametrize("sh_degree", [0, 1, 2, 3])
