@@ -79,7 +79,8 @@ def parse():
                     choices=["window", "plain", "uneven", "mixed", "odometry", "maintenance"],
                     help="window: the headline window step; plain, uneven, mixed: the other window "
                          "configurations; odometry: Gauss-Newton pose iterations")
-    ap.add_argument("--cpu-pixels", type=int, default=128, help="oracle pixels sampled per view")
+    ap.add_argument("--cpu-pixels", type=int, default=0,
+                    help="oracle pixels sampled per view (0: 64 per host core)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=100,
                     help="steps of the end-to-end timing (including its pipeline fill and drain)")
@@ -212,52 +213,69 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
 def cpu_oracle_iteration(params, views, pixels_per_view, seed=1, n_threads=0):
     """Times the FP64 oracle on a pixel sample of one window iteration and
-    scales the per-pixel parts to the full images (n_threads 0: all host
-    cores).  Returns (seconds per iteration estimate, threads, description)."""
+    scales the per-pixel parts to the full images.  n_threads 0: every host
+    core, for the pixel loops and the projection passes alike (each pixel,
+    each Gaussian is independent in the oracle).  Returns (seconds per
+    iteration estimate, threads used, description)."""
     from oracle import oracle as O
+    threads = n_threads if n_threads > 0 else host_cores()
+    O.set_threads(threads)
     rng = np.random.default_rng(seed)
     t_fixed = 0.0
     t_pix = 0.0
     n_pix_total = 0
-    for v in views:
-        W, H = int(v["W"]), int(v["H"])
-        px = rng.integers(0, W, pixels_per_view)
-        py = rng.integers(0, H, pixels_per_view)
+    try:
+        for v in views:
+            W, H = int(v["W"]), int(v["H"])
+            px = rng.integers(0, W, pixels_per_view)
+            py = rng.integers(0, H, pixels_per_view)
+            t0 = time.perf_counter()
+            pr = O.project(params, v)
+            t1 = time.perf_counter()
+            O.render_pixels(params, v, px, py, proj=pr, n_threads=threads)
+            t2 = time.perf_counter()
+            dl = [rng.standard_normal((pixels_per_view, 3)) * 1e-6]
+            O.backward(params, [v], dl, pixels=[(px, py)], n_threads=threads)
+            t3 = time.perf_counter()
+            O.backward(params, [v], [np.zeros((0, 3))], pixels=[(px[:0], py[:0])], n_threads=threads)
+            t4 = time.perf_counter()
+            scale = (W * H) / float(pixels_per_view)
+            t_fixed += (t1 - t0) + (t4 - t3)
+            t_pix += ((t2 - t1) + max(0.0, (t3 - t2) - (t4 - t3))) * scale
+            n_pix_total += pixels_per_view
+        n = sum(int(params[k].size) for k in ("means", "log_scales", "quats", "opacity", "sh"))
+        p = rng.standard_normal(n)
+        g = rng.standard_normal(n)
+        m = np.zeros(n)
+        vv = np.zeros(n)
         t0 = time.perf_counter()
-        pr = O.project(params, v)
-        t1 = time.perf_counter()
-        O.render_pixels(params, v, px, py, proj=pr, n_threads=n_threads)
-        t2 = time.perf_counter()
-        dl = [rng.standard_normal((pixels_per_view, 3)) * 1e-6]
-        O.backward(params, [v], dl, pixels=[(px, py)], n_threads=n_threads)
-        t3 = time.perf_counter()
-        O.backward(params, [v], [np.zeros((0, 3))], pixels=[(px[:0], py[:0])], n_threads=n_threads)
-        t4 = time.perf_counter()
-        scale = (W * H) / float(pixels_per_view)
-        t_fixed += (t1 - t0) + (t4 - t3)
-        t_pix += ((t2 - t1) + max(0.0, (t3 - t2) - (t4 - t3))) * scale
-        n_pix_total += pixels_per_view
-    n = sum(int(params[k].size) for k in ("means", "log_scales", "quats", "opacity", "sh"))
-    p = rng.standard_normal(n)
-    g = rng.standard_normal(n)
-    m = np.zeros(n)
-    vv = np.zeros(n)
-    t0 = time.perf_counter()
-    O.adam(p, g, m, vv, LR, 0.9, 0.999, 1e-8, 1)
-    t_adam = time.perf_counter() - t0
-    desc = ("oracle FP64 on %d random pixels per view (%d of %d), projection and projection backward over all "
-            "Gaussians, Adam over all %d parameters; per-pixel time scaled to the full images"
-            % (pixels_per_view, n_pix_total, sum(int(v["W"]) * int(v["H"]) for v in views), n))
-    return t_fixed + t_pix + t_adam, (1 if n_threads == 1 else O.num_threads()), desc
+        O.adam(p, g, m, vv, LR, 0.9, 0.999, 1e-8, 1)
+        t_adam = time.perf_counter() - t0
+    finally:
+        O.set_threads(0)
+    desc = ("oracle FP64 on %d host threads: %d random pixels per view (%d of %d) rendered and back-propagated, "
+            "projection and projection backward over all Gaussians, Adam over all %d parameters (one thread); "
+            "per-pixel time scaled to the full images"
+            % (threads, pixels_per_view, n_pix_total, sum(int(v["W"]) * int(v["H"]) for v in views), n))
+    return t_fixed + t_pix + t_adam, threads, desc
 
 
 def run_reference(args, world, rank):
     if rank != 0:
         return
     params, views = workload()[:2]
-    ppv = 4
+    # a bounded sample per step: 16 pixels per view per host core (about a
+    # second per step on 16 cores)
+    ppv = 16 * host_cores()
     for _ in range(args.warmup):
         cpu_oracle_iteration(params, views[:1], ppv)
     times = []
@@ -466,11 +484,13 @@ def run_b300(args, world, rank, local):
     cpu = None
     if (rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "window"
             and args.ssim_lambda == 0):
-        sec, threads, desc = cpu_oracle_iteration(params, views, args.cpu_pixels)
+        ppv = args.cpu_pixels or 64 * host_cores()
+        sec, threads, desc = cpu_oracle_iteration(params, views, ppv)
         cpu = {"value": 1.0 / sec, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc}
         # the same oracle on one host thread (a smaller pixel sample)
-        sec1, _, desc1 = cpu_oracle_iteration(params, views, max(args.cpu_pixels // 8, 4), seed=2, n_threads=1)
+        sec1, _, desc1 = cpu_oracle_iteration(params, views, max(ppv // 16, 8), seed=2, n_threads=1)
         cpu["single_thread"] = {"value": 1.0 / sec1, "unit": UNIT, "cores": 1, "sample": desc1}
+        cpu["speedup_over_one_thread"] = sec1 / sec
 
     if rank == 0:
         mpix = world * K * n_px / (max_ms / 1e3) / 1e6

@@ -363,10 +363,15 @@ GS_API int gs_adam_step_ranges(gs_ctx* ctx, float* param, const float* grad, flo
  * is required, e.g. 64 views of 1280 x 1024; larger batches return
  * GS_ERR_CAPACITY with a message in msg.  The first call on a device looks up
  * the array's device address (cudaGetSymbolAddress); make that first call
- * before any stream capture on that device.  All calls on a device share the
- * array: calls whose work overlaps on the GPU (for instance on two streams)
- * race and must be ordered by the caller.  Each call rewrites every slot it
- * reads, so nothing needs clearing between calls.
+ * before any stream capture on that device.  The address belongs to the CUDA
+ * context it was looked up in: the first call in a new context on the device
+ * (after cudaDeviceReset, for instance) looks it up again, and that call too
+ * must come before any stream capture (a captured one returns
+ * GS_ERR_INVALID_ARG).  `stream` must belong to the current device
+ * (GS_ERR_INVALID_ARG otherwise).  All calls on a device share the array:
+ * calls whose work overlaps on the GPU (for instance on two streams) race and
+ * must be ordered by the caller.  Each call rewrites every slot it reads, so
+ * nothing needs clearing between calls.
  * msg: NULL or a host buffer of msg_len bytes that receives an error text.
  * Errors: GS_ERR_INVALID_ARG, GS_ERR_CAPACITY, GS_ERR_CUDA. */
 GS_API int gs_l1_loss_noalloc(const gs_view* views, int n_views, const float* rgb, const float* target,

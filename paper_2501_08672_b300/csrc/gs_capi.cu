@@ -591,7 +591,20 @@ int gs_l1_loss_noalloc(const gs_view* views, int n_views, const float* rgb, cons
         return fail_msg(msg, msg_len, GS_ERR_CAPACITY,
                         "gs_l1_loss_noalloc: the batch needs %lld partial sums, the fixed scratch holds %lld", need,
                         l1_scratch_capacity());
-    cudaError_t e = launch_l1_static(bp, rgb, target, dL_drgb, loss_dev, reinterpret_cast<cudaStream_t>(stream));
+    const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    int cur = -1, sdev = -1;
+    cudaError_t e = cudaGetDevice(&cur);
+    if (e == cudaSuccess) e = cudaStreamGetDevice(s, &sdev);
+    if (e != cudaSuccess)
+        return fail_msg(msg, msg_len, GS_ERR_CUDA, "gs_l1_loss_noalloc: %s", cudaGetErrorString(e));
+    if (sdev != cur)
+        return fail_msg(msg, msg_len, GS_ERR_INVALID_ARG,
+                        "gs_l1_loss_noalloc: the stream belongs to device %d, the current device is %d", sdev, cur);
+    e = launch_l1_static(bp, rgb, target, dL_drgb, loss_dev, s);
+    if (e == cudaErrorStreamCaptureUnsupported)
+        return fail_msg(msg, msg_len, GS_ERR_INVALID_ARG,
+                        "gs_l1_loss_noalloc: the first call in a CUDA context looks up the scratch address and "
+                        "must not be captured");
     if (e != cudaSuccess)
         return fail_msg(msg, msg_len, GS_ERR_CUDA, "gs_l1_loss_noalloc: %s", cudaGetErrorString(e));
     return GS_OK;

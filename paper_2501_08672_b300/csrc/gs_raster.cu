@@ -23,6 +23,8 @@
 // are bound by FP32/MUFU issue, not by HBM.
 #include <mutex>
 
+#include <cuda.h>
+
 #include "gs_internal.cuh"
 
 namespace gsb {
@@ -847,8 +849,44 @@ constexpr int kL1ScratchDevices = 64;
 static __device__ __align__(256) float g_l1_scratch[kL1ScratchFloats];
 
 namespace {
+// Device address of g_l1_scratch per device, with the unique id of the CUDA
+// context it was looked up in.  Host code only knows a stand-in for the
+// array; its device address belongs to the context that loaded the module,
+// so a new context on the device (after cudaDeviceReset, for instance) needs
+// a new lookup.
+struct L1ScratchAddr {
+    unsigned long long ctx_id;
+    void* ptr;
+};
 std::mutex g_l1_scratch_mu;
-void* g_l1_scratch_ptr[kL1ScratchDevices] = {};
+L1ScratchAddr g_l1_scratch_addr[kL1ScratchDevices] = {};
+
+typedef CUresult (*PfnCtxGetCurrent)(CUcontext*);
+typedef CUresult (*PfnCtxGetId)(CUcontext, unsigned long long*);
+PfnCtxGetCurrent g_ctx_get_current = nullptr;
+PfnCtxGetId g_ctx_get_id = nullptr;
+bool g_ctx_entry_points_tried = false;
+
+// Unique id of the current CUDA context (false when no context is current or
+// the driver lacks the entry points).  Called with g_l1_scratch_mu held.
+bool current_context_id(unsigned long long* id) {
+    if (!g_ctx_entry_points_tried) {
+        g_ctx_entry_points_tried = true;
+        cudaDriverEntryPointQueryResult q1, q2;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", reinterpret_cast<void**>(&g_ctx_get_current),
+                                             12000, cudaEnableDefault, &q1) != cudaSuccess ||
+            q1 != cudaDriverEntryPointSuccess)
+            g_ctx_get_current = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", reinterpret_cast<void**>(&g_ctx_get_id), 12000,
+                                             cudaEnableDefault, &q2) != cudaSuccess ||
+            q2 != cudaDriverEntryPointSuccess)
+            g_ctx_get_id = nullptr;
+    }
+    if (!g_ctx_get_current || !g_ctx_get_id) return false;
+    CUcontext c = nullptr;
+    if (g_ctx_get_current(&c) != CUDA_SUCCESS || !c) return false;
+    return g_ctx_get_id(c, id) == CUDA_SUCCESS;
+}
 }  // namespace
 
 long long l1_partials_needed(const BatchParam& bp) {
@@ -872,17 +910,32 @@ cudaError_t launch_l1_static(const BatchParam& bp, const float* rgb, const float
     if (dev < 0 || dev >= kL1ScratchDevices) return cudaErrorInvalidDevice;
     void* ptr = nullptr;
     {
-        // First use on this device (which is current): host code only knows a
-        // stand-in for the array, so look up its device address once.
+        // The first call in each context on this device (which is current)
+        // looks up the array's device address; later calls in the same
+        // context reuse it.
         std::lock_guard<std::mutex> lock(g_l1_scratch_mu);
-        if (!g_l1_scratch_ptr[dev]) {
-            e = cudaGetSymbolAddress(&g_l1_scratch_ptr[dev], g_l1_scratch);
-            if (e != cudaSuccess) {
-                g_l1_scratch_ptr[dev] = nullptr;
-                return e;
+        L1ScratchAddr& a = g_l1_scratch_addr[dev];
+        unsigned long long id = 0;
+        const bool have_id = current_context_id(&id);
+        if (a.ptr && have_id && a.ctx_id == id) {
+            ptr = a.ptr;
+        } else {
+            cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+            e = cudaStreamIsCapturing(s, &cs);
+            if (e != cudaSuccess) return e;
+            if (cs != cudaStreamCaptureStatusNone) {
+                // no lookup while capturing: without a context id to compare,
+                // the address of the last lookup is the best there is
+                if (!have_id && a.ptr) ptr = a.ptr;
+                else return cudaErrorStreamCaptureUnsupported;
+            } else {
+                e = cudaGetSymbolAddress(&ptr, g_l1_scratch);
+                if (e != cudaSuccess) return e;
+                unsigned long long id2 = 0;
+                a.ptr = ptr;
+                a.ctx_id = current_context_id(&id2) ? id2 : 0;
             }
         }
-        ptr = g_l1_scratch_ptr[dev];
     }
     float* partials = static_cast<float*>(ptr);
     const int gx = (int)(need / bp.n_views);

@@ -32,6 +32,9 @@ class Renderer:
         self.n_contrib = torch.empty(self.npx, device=dev, dtype=torch.int32)
         self.dL_drgb = torch.empty(3 * self.npx, device=dev, dtype=torch.float32)
         self.loss = torch.zeros(1, device=dev, dtype=torch.float32)
+        # forwards run so far: the autograd wrapper checks that the bins its
+        # backward recomputes alpha from still belong to its own forward
+        self.forward_count = 0
         self.dL_dpose = torch.zeros(self.n_views * 6, device=dev, dtype=torch.float32)
         self.cap = 0
         self.ws = None
@@ -68,6 +71,7 @@ class Renderer:
         against it, folded into the compositing (self.loss, self.dL_drgb)."""
         if count is None:
             count = not self._counted
+        self.forward_count += 1
         self.ctx.project(g, self.views, self.ws_struct)
         if count:
             while True:
@@ -395,6 +399,7 @@ class _Rasterize(torch.autograd.Function):
         g = B.gaussians_struct(means, log_scales, quats, opacity, sh, sh_degree)
         renderer.forward(g)
         ctx.renderer = renderer
+        ctx.forward_count = renderer.forward_count
         ctx.sh_degree = sh_degree
         ctx.save_for_backward(means, log_scales, quats, opacity, sh)
         rgb = renderer.rgb.clone()
@@ -406,6 +411,10 @@ class _Rasterize(torch.autograd.Function):
     def backward(ctx, dL_drgb, _dT):
         means, log_scales, quats, opacity, sh = ctx.saved_tensors
         r = ctx.renderer
+        if r.forward_count != ctx.forward_count:
+            raise RuntimeError("rasterize: the renderer ran another forward after this one; its bins, T and "
+                               "n_contrib (from which backward recomputes alpha) belong to that forward now. "
+                               "Use one Renderer per rasterize call that is differentiated.")
         g = B.gaussians_struct(means, log_scales, quats, opacity, sh, ctx.sh_degree)
         grads = [torch.empty(t.shape, device=t.device, dtype=torch.float32) for t in
                  (means, log_scales, quats, opacity, sh)]

@@ -19,6 +19,8 @@ from paper_2501_08672_b300 import binding as B  # noqa: E402
 from paper_2501_08672_b300 import scenes  # noqa: E402
 from paper_2501_08672_b300.render import GaussianWindow, PoseTracker, Renderer, apply_left  # noqa: E402
 
+import parity_log  # noqa: E402
+
 TOL = 1e-3
 
 
@@ -74,6 +76,7 @@ def test_pose_normal_full_images_match_oracle(orc, ts, sh_degree):
         Hv = Hg[off:off + W * Hh]
         tv = tgt[v].detach().double().cpu().numpy().reshape(3, -1).T
         ok = ~bd
+        parity_log.record("pixels", bd.mean(), 1e-3, int(bd.sum()), bd.size)
         assert bd.mean() < 1e-3, bd.mean()
         e = rel(Hv[ok], Ho[ok])
         print("view %d: H rel err %.2e, border %.1e" % (v, e, bd.mean()))
@@ -112,6 +115,7 @@ def test_pose_normal_odometry_sampled(orc):
     px, py = pick % 1280, pick // 1280
     Ho, _, bd = orc.pose_jacobian(p, v, px, py)
     ok = ~bd
+    parity_log.record("pixels", bd.mean(), 4.0 / 64, int(bd.sum()), bd.size)
     e = rel(Hg[pick][ok], Ho[ok])
     print("sampled H rel err %.2e over %d pixels" % (e, ok.sum()))
     assert ok.sum() >= 60 and e < TOL

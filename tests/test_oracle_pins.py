@@ -561,11 +561,13 @@ def test_zero_gradient_pixels_contribute_and_flag_nothing(orc):
 
 def test_borderline_share_follows_contributor_count(orc):
     """The share of borderline pixels stays within twice the expectation
-    2 REL (n_contrib m + 1) that the parity tests bound it by (over a
-    footprint ln(alpha) is uniform between ln(alpha_min) and ln(sigma), so a
-    covering Gaussian lands within REL of alpha_min with probability
-    2 REL / ln(sigma / alpha_min); m is the mean of that reciprocal), on a
-    dense box-room view where pixels hold tens of contributors."""
+    2 REL (n (m + 1 / |ln T_min|) + 1) that the parity tests bound it by:
+    over a footprint ln(alpha) is uniform between ln(alpha_min) and
+    ln(sigma), so a covering Gaussian lands within REL of alpha_min with
+    probability 2 REL / ln(sigma / alpha_min) (m is the mean of that
+    reciprocal), and the step of ln T that crosses ln T_min lands within REL
+    of it with probability 2 REL n / |ln T_min|; on a dense box-room view
+    where pixels hold tens of contributors."""
     n = 20_000
     p = scenes.box_room_scene(n, seed=7)
     v = scenes.arc_views(1, 192, 160, 180.0, n_gaussians=n)[0]
@@ -575,7 +577,7 @@ def test_borderline_share_follows_contributor_count(orc):
     share = float(out["border"].mean())
     s = out["sigma"][out["sigma"] > 1.0 / 255.0]
     m = float(np.mean(1.0 / np.maximum(np.log(s * 255.0), 1.0)))
-    assert share <= 2.0 * 2.0 * 1e-5 * (nbar * m + 1.0)
+    assert share <= 2.0 * 2.0 * 1e-5 * (nbar * (m + 1.0 / math.log(1e4)) + 1.0)
 
 
 # ---- pose Jacobian and normal equations (Sec. II-D, Eq. minimization) ----

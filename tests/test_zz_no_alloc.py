@@ -62,11 +62,37 @@ def test_noalloc_l1_matches_workspace_l1_on_two_calls():
         assert rc == B.GS_OK, msg
         assert float((dl - dl_ref).abs().max()) <= TOL
         assert abs(float(loss.item()) - float(loss_ref.item())) <= TOL
-        # and against the definition, in FP64 on the host
+        # and against the definition, in FP64 on the host: the mean absolute
+        # residual per view averaged over views, and its gradient
+        # sign(rgb - target) / (3 H W V)
         d = (rgb - target).double().cpu().numpy()
         sizes = [3 * v["W"] * v["H"] for v in views]
-        expect = sum(np.abs(c).mean() for c in np.split(d, np.cumsum(sizes)[:-1])) / len(views)
+        parts = np.split(d, np.cumsum(sizes)[:-1])
+        expect = sum(np.abs(c).mean() for c in parts) / len(views)
         assert abs(float(loss.item()) - expect) <= TOL
+        grad = np.concatenate([np.sign(c) / (c.size * len(views)) for c in parts])
+        np.testing.assert_allclose(dl.double().cpu().numpy(), grad, rtol=1e-6, atol=0)
+
+
+def test_noalloc_l1_without_loss_pointer_writes_the_gradient_only():
+    """With loss = NULL only the gradient is written (one launch), equal to
+    that of gs_l1_loss."""
+    views = _views()
+    vc = B.make_views(views)
+    npx = sum(v["W"] * v["H"] for v in views)
+    ctx = B.Context(0)
+    cap = 1024
+    ws = torch.empty(ctx.workspace_bytes(vc, cap), dtype=torch.uint8, device="cuda")
+    gen = torch.Generator(device="cuda").manual_seed(9)
+    rgb = torch.rand(3 * npx, device="cuda", generator=gen)
+    target = torch.rand(3 * npx, device="cuda", generator=gen)
+    dl_ref = torch.empty_like(rgb)
+    ctx.l1_loss(vc, B.Context.ws_struct(ws, cap), rgb, target, dl_ref, None)
+    dl = torch.full_like(rgb, float("nan"))
+    rc, msg = _noalloc(vc, len(views), rgb, target, dl, None)
+    torch.cuda.synchronize()
+    assert rc == B.GS_OK, msg
+    assert float((dl - dl_ref).abs().max()) <= TOL
 
 
 def test_noalloc_l1_rejects_batches_beyond_its_fixed_scratch():
