@@ -89,6 +89,10 @@ def parse():
     ap.add_argument("--batch", type=int, default=0)
     ap.add_argument("--maint-n", default="",
                     help="maintenance workload: comma-separated window sizes (default: the full sweep)")
+    ap.add_argument("--compare-forms", dest="compare_forms", action="store_true", default=None,
+                    help="also time the workload with FP32 storage and in the plain per-view form "
+                         "(default for --workload mixed)")
+    ap.add_argument("--no-compare-forms", dest="compare_forms", action="store_false")
     ap.add_argument("--ssim-lambda", type=float, default=0.0,
                     help="weight of the D-SSIM term in the photometric loss (0: the L1 loss of the paper)")
     return ap.parse_args()
@@ -295,6 +299,55 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def kernel_rooflines(kms, n_gauss, n_records, n_pairs, n_tiles, n_params, param_bytes, lowp_elems, visited,
+                     contrib, ffma_tflops, hbm_gbs):
+    """Achieved fraction of its roofline for every kernel family of one
+    iteration, from its CUDA-event time per iteration (kms, ms) and its
+    algorithmic work: FP32 FLOP per the fragment model for the compositing
+    kernels (bound by FP32 issue), bytes for the others (bound by HBM).
+    Algorithmic bytes (the minimum a kernel must move, not its traffic):
+      project      per record: the Gaussian's parameters (param_bytes) read,
+                   the 48 B record, 16 B rectangle, 4 B tile count and 12 B
+                   depth key and index written
+      depth_sort   per record: the 12 B (64-bit key, index) read and written
+                   once (one pass; more passes count as overhead)
+      tile_scan    per record: tile count and sorted index read, 8 B offset
+                   written
+      emit         per pair: 8 B (tile key, record index) written
+      tile_sort    per pair: 8 B read and 8 B written once
+      ranges       per pair: 4 B key read; per tile 8 B range written
+      project_bwd  per record 36 B of 2D gradients read; per Gaussian its
+                   parameters read and 4 B per parameter written
+      adam         per parameter 28 B (p, g, m, v read; p, m, v written),
+                   plus the low-precision copy written"""
+    work = {
+        "project": ("hbm", n_records * (param_bytes + 80.0)),
+        "depth_sort": ("hbm", n_records * 24.0),
+        "tile_scan": ("hbm", n_records * 16.0),
+        "emit": ("hbm", n_pairs * 8.0),
+        "tile_sort": ("hbm", n_pairs * 16.0),
+        "ranges": ("hbm", n_pairs * 4.0 + n_tiles * 8.0),
+        "raster_fwd": ("alu", FLOP_VISITED * visited + FLOP_CONTRIB["raster_fwd"] * contrib),
+        "raster_bwd": ("alu", FLOP_VISITED * visited + FLOP_CONTRIB["raster_bwd"] * contrib),
+        "project_bwd": ("hbm", n_records * 36.0 + n_gauss * param_bytes + n_params * 4.0),
+        "adam": ("hbm", n_params * 28.0 + lowp_elems * 2.0),
+    }
+    out = {}
+    for k, (bound, amount) in work.items():
+        ms = kms.get(k)
+        if not ms:
+            continue
+        if bound == "alu":
+            ach = amount / (ms / 1e3) / 1e12
+            out[k] = {"bound": "alu", "ms": ms, "achieved": ach, "peak": ffma_tflops, "unit": "TFLOP/s",
+                      "frac": ach / ffma_tflops, "work": amount}
+        else:
+            ach = amount / (ms / 1e3) / 1e9
+            out[k] = {"bound": "hbm", "ms": ms, "achieved": ach, "peak": hbm_gbs, "unit": "GB/s",
+                      "frac": ach / hbm_gbs, "work": amount}
+    return out
+
+
 def run_b300(args, world, rank, local):
     import torch
     import torch.distributed as dist
@@ -426,6 +479,18 @@ def run_b300(args, world, rank, local):
     else:
         roof = {"bound": "hbm", "kernel": dominant, "achieved": None, "peak": hbm, "unit": "GB/s",
                 "frac": None, "traffic": None, "avg_launch_ms": avg_ms, "peak_kind": hbm_kind}
+    # every kernel family against its own roofline
+    L = opt.r.layout()
+    K_sh = (int(params["sh_degree"]) + 1) ** 2
+    st = storage or {}
+    esz = lambda k: (2 if k in st else 4)  # noqa: E731
+    param_bytes = 12 + 3 * esz("log_scales") + 4 * esz("quats") + esz("opacity") + 3 * K_sh * esz("sh")
+    n_params = n_gauss * (11 + 3 * K_sh)
+    lowp_elems = sum(n_gauss * w for k, w in (("log_scales", 3), ("quats", 4), ("opacity", 1), ("sh", 3 * K_sh))
+                     if k in st)
+    kms = {k: v[1] / n_warm for k, v in prof_all.items()}
+    by_kernel = kernel_rooflines(kms, n_gauss, int(L.n_records), int(opt.r.last_pairs), int(L.n_tiles), n_params,
+                                 param_bytes, lowp_elems, visited, contrib, ffma_tflops, hbm)
 
     # end to end through the public API with host buffers: per step the step's
     # input, the keyframe images (targets), goes host->device from pinned
@@ -481,6 +546,36 @@ def run_b300(args, world, rank, local):
     h2d = host_target.numel() * 4
     d2h = 4
 
+    # the same workload in other forms, each graph-replayed and timed like the
+    # headline: FP32 storage batched, and the plain per-view FP32 form (one
+    # launch sequence per view, gradients accumulated, one Adam step)
+    other_forms = {}
+    if args.compare_forms or (args.compare_forms is None and args.workload == "mixed"):
+        from paper_2501_08672_b300.render import PerViewOptimizer
+
+        def form_rate(o):
+            o.step(count=True)
+            for _ in range(n_warm):
+                o.step(count=False)
+            o.capture()
+            for _ in range(n_warm):
+                o.step()
+            ms = timed(o.step)
+            st = o.check_status() if hasattr(o, "check_status") else o.r.check_status()
+            if st[0] != B.GS_OK:
+                raise RuntimeError("pair capacity exceeded in a compared form")
+            return whole_job_rate(world, K, max_over_ranks([ms], world)[0])
+
+        kw = dict(lr=LR, device=local, tile_size=shape[0], pixels_per_thread=shape[1], batch=shape[2])
+        if storage:
+            o = WindowOptimizer(params, views, target, **kw)
+            other_forms["batched_fp32_storage_it_s"] = form_rate(o)
+            del o
+        o = PerViewOptimizer(params, views, target, **kw)
+        other_forms["per_view_fp32_storage_it_s"] = form_rate(o)
+        del o
+        torch.cuda.empty_cache()
+
     cpu = None
     if (rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "window"
             and args.ssim_lambda == 0):
@@ -513,8 +608,9 @@ def run_b300(args, world, rank, local):
                            "mpix_per_s": mpix},
                 "roofline": roof,
                 "kernel_ms_per_step": {k: v[1] / n_warm for k, v in prof_all.items()},
-                "forms": {"graph_replay_it_s": value,
-                          "host_issued_it_s": whole_job_rate(world, K, max_plain_ms)},
+                "roofline_by_kernel": by_kernel,
+                "forms": dict({"graph_replay_it_s": value,
+                               "host_issued_it_s": whole_job_rate(world, K, max_plain_ms)}, **other_forms),
                 "cpu_baseline": cpu,
                 "e2e": {"value": 1e3 / e2e_ms, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                         "d2h_bytes_per_step": int(d2h)},

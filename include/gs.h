@@ -296,6 +296,20 @@ GS_API int gs_render_bwd(gs_ctx* ctx, const gs_gaussians* g, const gs_view* view
                   const float* dL_drgb, const gs_grads* grads, float* dL_dpose_dev,
                   gs_stream stream);
 
+/* gs_render_bwd, with the parameter gradients added to what grads already
+ * holds instead of overwriting it (every entry of every group, zero for
+ * Gaussians no view of this call sees), so that the views of one window
+ * iteration can be back-propagated in several calls (more views than
+ * GS_MAX_VIEWS, or one view per launch sequence) and their gradients summed
+ * before one Adam step.  The gradients of the first call's Gaussians must be
+ * cleared (or written by gs_render_bwd) first.  dL_dpose_dev, when non-NULL,
+ * is written per view as in gs_render_bwd.  grads is required.
+ * Errors: GS_ERR_INVALID_ARG, GS_ERR_CUDA. */
+GS_API int gs_render_bwd_accumulate(gs_ctx* ctx, const gs_gaussians* g, const gs_view* views, int n_views,
+                                    const gs_workspace* ws, const float* T_final, const uint32_t* n_contrib,
+                                    const float* dL_drgb, const gs_grads* grads, float* dL_dpose_dev,
+                                    gs_stream stream);
+
 /* a7: photometric pose gradient only (Sec. II-D, Eq. minimization; the
  * derivative chain of Eqs. grad_meani_rcw to grad_covi_tcw restricted to the
  * camera pose): gs_render_bwd with grads = NULL.  dL_dpose_dev is required. */

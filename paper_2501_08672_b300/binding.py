@@ -36,7 +36,8 @@ EXPORTED = ["gs_config_default", "gs_version", "gs_context_create", "gs_context_
             "gs_l1_loss_noalloc", "gs_calibrate_alu", "gs_pose_normal_scratch", "gs_pose_normal",
             "gs_window_scratch_bytes", "gs_window_compact", "gs_window_remove", "gs_window_gather", "gs_window_clear",
             "gs_sh_init_bilinear", "gs_dssim_scratch_floats", "gs_dssim_loss", "gs_adam_step_ranges",
-            "gs_selftest_wait_scratch_bytes", "gs_selftest_bounded_wait", "gs_render_fwd_l1"]
+            "gs_selftest_wait_scratch_bytes", "gs_selftest_bounded_wait", "gs_render_fwd_l1",
+            "gs_render_bwd_accumulate"]
 
 KERNEL_FAMILIES = ["project", "depth_sort", "tile_scan", "emit", "tile_sort", "ranges", "raster_fwd", "l1",
                    "raster_bwd", "project_bwd", "adam", "pose_normal", "window", "ssim"]
@@ -133,6 +134,7 @@ def lib():
                                        P]
         L.gs_render_bwd.argtypes = [P, ctypes.POINTER(Gaussians), ctypes.POINTER(View), I, ctypes.POINTER(Workspace),
                                     P, P, P, ctypes.POINTER(Grads), P, P]
+        L.gs_render_bwd_accumulate.argtypes = L.gs_render_bwd.argtypes
         L.gs_pose_grad.argtypes = [P, ctypes.POINTER(Gaussians), ctypes.POINTER(View), I, ctypes.POINTER(Workspace),
                                    P, P, P, P, P]
         L.gs_adam_step.argtypes = [P, P, P, P, P, I64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
@@ -323,14 +325,16 @@ class Context:
         self._ck(lib().gs_dssim_loss(self.h, views, len(views), _ptr(rgb), _ptr(target), float(lam), _ptr(scratch),
                                      _ptr(dL_drgb), _ptr(loss), _stream(stream)))
 
-    def render_bwd(self, g, views, ws, T_final, n_contrib, dL_drgb, grads=None, dL_dpose=None, stream=None):
+    def render_bwd(self, g, views, ws, T_final, n_contrib, dL_drgb, grads=None, dL_dpose=None, stream=None,
+                   accumulate=False):
         gr = None
         if grads is not None:
             gr = Grads()
             gr.means, gr.log_scales, gr.quats, gr.opacity, gr.sh = [t.data_ptr() for t in grads]
-        self._ck(lib().gs_render_bwd(self.h, ctypes.byref(g), views, len(views), ctypes.byref(ws), _ptr(T_final),
-                                     _ptr(n_contrib), _ptr(dL_drgb), ctypes.byref(gr) if gr is not None else None,
-                                     _ptr(dL_dpose), _stream(stream)))
+        fn = lib().gs_render_bwd_accumulate if accumulate else lib().gs_render_bwd
+        self._ck(fn(self.h, ctypes.byref(g), views, len(views), ctypes.byref(ws), _ptr(T_final),
+                    _ptr(n_contrib), _ptr(dL_drgb), ctypes.byref(gr) if gr is not None else None,
+                    _ptr(dL_dpose), _stream(stream)))
 
     def pose_grad(self, g, views, ws, T_final, n_contrib, dL_drgb, dL_dpose, stream=None):
         self._ck(lib().gs_pose_grad(self.h, ctypes.byref(g), views, len(views), ctypes.byref(ws), _ptr(T_final),

@@ -658,9 +658,10 @@ int gs_dssim_loss(gs_ctx* ctx, const gs_view* views, int n_views, const float* r
     return e == cudaSuccess ? GS_OK : cuda_fail(ctx, e, "gs_dssim_loss");
 }
 
-int gs_render_bwd(gs_ctx* ctx, const gs_gaussians* g, const gs_view* views, int n_views, const gs_workspace* ws,
-                  const float* T_final, const uint32_t* n_contrib, const float* dL_drgb, const gs_grads* grads,
-                  float* dL_dpose_dev, gs_stream stream) {
+namespace {
+int render_bwd_impl(gs_ctx* ctx, const gs_gaussians* g, const gs_view* views, int n_views, const gs_workspace* ws,
+                    const float* T_final, const uint32_t* n_contrib, const float* dL_drgb, const gs_grads* grads,
+                    float* dL_dpose_dev, gs_stream stream, bool accumulate) {
     if (!ctx) return GS_ERR_INVALID_ARG;
     if (!T_final || !n_contrib || !dL_drgb) return fail(ctx, GS_ERR_INVALID_ARG, "an image pointer is NULL");
     if (!grads && !dL_dpose_dev) return fail(ctx, GS_ERR_INVALID_ARG, "grads and dL_dpose are both NULL");
@@ -687,8 +688,25 @@ int gs_render_bwd(gs_ctx* ctx, const gs_gaussians* g, const gs_view* views, int 
         gr.opacity = grads->opacity;
         gr.sh = grads->sh;
     }
-    e = launch_project_bwd(bp, gp, rcst, wp, grads ? &gr : nullptr, dL_dpose_dev, s, ctx->prof);
+    e = launch_project_bwd(bp, gp, rcst, wp, grads ? &gr : nullptr, dL_dpose_dev, s, ctx->prof, accumulate);
     return e == cudaSuccess ? GS_OK : cuda_fail(ctx, e, "gs_render_bwd (projection)");
+}
+}  // namespace
+
+int gs_render_bwd(gs_ctx* ctx, const gs_gaussians* g, const gs_view* views, int n_views, const gs_workspace* ws,
+                  const float* T_final, const uint32_t* n_contrib, const float* dL_drgb, const gs_grads* grads,
+                  float* dL_dpose_dev, gs_stream stream) {
+    return render_bwd_impl(ctx, g, views, n_views, ws, T_final, n_contrib, dL_drgb, grads, dL_dpose_dev, stream,
+                           false);
+}
+
+int gs_render_bwd_accumulate(gs_ctx* ctx, const gs_gaussians* g, const gs_view* views, int n_views,
+                             const gs_workspace* ws, const float* T_final, const uint32_t* n_contrib,
+                             const float* dL_drgb, const gs_grads* grads, float* dL_dpose_dev, gs_stream stream) {
+    if (!ctx) return GS_ERR_INVALID_ARG;
+    if (!grads) return fail(ctx, GS_ERR_INVALID_ARG, "grads is NULL");
+    return render_bwd_impl(ctx, g, views, n_views, ws, T_final, n_contrib, dL_drgb, grads, dL_dpose_dev, stream,
+                           true);
 }
 
 int gs_pose_grad(gs_ctx* ctx, const gs_gaussians* g, const gs_view* views, int n_views, const gs_workspace* ws,
@@ -696,7 +714,8 @@ int gs_pose_grad(gs_ctx* ctx, const gs_gaussians* g, const gs_view* views, int n
                  gs_stream stream) {
     if (!ctx) return GS_ERR_INVALID_ARG;
     if (!dL_dpose_dev) return fail(ctx, GS_ERR_INVALID_ARG, "dL_dpose is NULL");
-    return gs_render_bwd(ctx, g, views, n_views, ws, T_final, n_contrib, dL_drgb, nullptr, dL_dpose_dev, stream);
+    return render_bwd_impl(ctx, g, views, n_views, ws, T_final, n_contrib, dL_drgb, nullptr, dL_dpose_dev, stream,
+                           false);
 }
 
 namespace {

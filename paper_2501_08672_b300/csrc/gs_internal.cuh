@@ -329,7 +329,7 @@ cudaError_t launch_render_bwd(const BatchParam& bp, const RenderConst& rc, const
                               const float* dL_drgb, cudaStream_t s, Prof& pf);
 cudaError_t launch_project_bwd(const BatchParam& bp, const GaussPtrs& g, const RenderConst& rc,
                                const WsPtrs& ws, const GradPtrs* grads, float* dL_dpose,
-                               cudaStream_t s, Prof& pf);
+                               cudaStream_t s, Prof& pf, bool accumulate = false);
 cudaError_t launch_l1(const BatchParam& bp, const WsPtrs& ws, const float* rgb,
                       const float* target, float* dL_drgb, float* loss, cudaStream_t s, Prof& pf);
 long long l1_partials_needed(const BatchParam& bp);

@@ -531,11 +531,15 @@ __global__ void __launch_bounds__(256, 3) k_project_bwd(const __grid_constant__ 
     }
 
     if (!live || !want_params) return;
+    // want_params 2: add to the gradients already there (several batches of
+    // views summed before one optimiser step)
+    const bool acc = want_params == 2;
+    auto put = [acc](float* dst, float v) { *dst = acc ? *dst + v : v; };
     float gR[9];
     for (int a = 0; a < 3; ++a)
         for (int b = 0; b < 3; ++b) gR[3 * a + b] = gM[3 * a + b] * P.s[b];
     for (int b = 0; b < 3; ++b)
-        gr.log_scales[3 * i + b] = (gM[b] * P.R[b] + gM[3 + b] * P.R[3 + b] + gM[6 + b] * P.R[6 + b]) * P.s[b];
+        put(gr.log_scales + 3 * i + b, (gM[b] * P.R[b] + gM[3 + b] * P.R[3 + b] + gM[6 + b] * P.R[6 + b]) * P.s[b]);
     const float w = P.qh[0], x = P.qh[1], y = P.qh[2], z = P.qh[3];
     float gq[4];
     gq[0] = 2.f * (-z * gR[1] + y * gR[2] + z * gR[3] - x * gR[5] - y * gR[6] + x * gR[7]);
@@ -546,11 +550,11 @@ __global__ void __launch_bounds__(256, 3) k_project_bwd(const __grid_constant__ 
     gq[3] = 2.f * (-2.f * z * gR[0] - w * gR[1] + x * gR[2] + w * gR[3] - 2.f * z * gR[4] + y * gR[5] +
                    x * gR[6] + y * gR[7]);
     const float dq = gq[0] * P.qh[0] + gq[1] * P.qh[1] + gq[2] * P.qh[2] + gq[3] * P.qh[3];
-    for (int k = 0; k < 4; ++k) gr.quats[4 * i + k] = (gq[k] - P.qh[k] * dq) * P.inv_qn;
-    for (int k = 0; k < 3; ++k) gr.means[3 * i + k] = gmu[k];
-    gr.opacity[i] = gop;
+    for (int k = 0; k < 4; ++k) put(gr.quats + 4 * i + k, (gq[k] - P.qh[k] * dq) * P.inv_qn);
+    for (int k = 0; k < 3; ++k) put(gr.means + 3 * i + k, gmu[k]);
+    put(gr.opacity + i, gop);
 #pragma unroll
-    for (int e = 0; e < K * 3; ++e) gr.sh[i * K * 3 + e] = gsh[e];
+    for (int e = 0; e < K * 3; ++e) put(gr.sh + i * K * 3 + e, gsh[e]);
 }
 
 __global__ void k_pose_finish(const float* partials, int nblocks, int n_views, float* dL_dpose) {
@@ -682,7 +686,7 @@ cudaError_t launch_project(const BatchParam& bp, const GaussPtrs& g, const Rende
 
 cudaError_t launch_project_bwd(const BatchParam& bp, const GaussPtrs& g, const RenderConst& rc,
                                const WsPtrs& ws, const GradPtrs* grads, float* dL_dpose,
-                               cudaStream_t s, Prof& pf) {
+                               cudaStream_t s, Prof& pf, bool accumulate) {
     if (g.n <= 0) return cudaSuccess;
     const int nblk = (int)((g.n + 255) / 256);
     long long max_g_end = 0;
@@ -693,7 +697,7 @@ cudaError_t launch_project_bwd(const BatchParam& bp, const GaussPtrs& g, const R
     const int pose_blocks = (int)((max_g_end + 255) / 256);
     GradPtrs gr = grads ? *grads : GradPtrs{nullptr, nullptr, nullptr, nullptr, nullptr};
     const int pi = pf.begin(GS_KF_PROJECT_BWD, s, dL_dpose ? 2 : 1);
-    const int wp = grads != nullptr, wq = dL_dpose != nullptr;
+    const int wp = grads == nullptr ? 0 : (accumulate ? 2 : 1), wq = dL_dpose != nullptr;
     switch (g.sh_degree) {
         case 0: pdl_launch(k_project_bwd<0>, nblk, 256, 0, s, bp, g, rc, ws, gr, wp, wq, pose_blocks); break;
         case 1: pdl_launch(k_project_bwd<1>, nblk, 256, 0, s, bp, g, rc, ws, gr, wp, wq, pose_blocks); break;

@@ -120,9 +120,11 @@ class Renderer:
         else:
             self.l1(target)
 
-    def backward(self, g, dL_drgb, grads=None, want_pose=False):
+    def backward(self, g, dL_drgb, grads=None, want_pose=False, accumulate=False):
+        """Gradients of the last forward's views.  accumulate: add to `grads`
+        instead of overwriting them (views back-propagated in several calls)."""
         self.ctx.render_bwd(g, self.views, self.ws_struct, self.T, self.n_contrib, dL_drgb, grads,
-                            self.dL_dpose if want_pose else None)
+                            self.dL_dpose if want_pose else None, accumulate=accumulate)
 
     def pose_grad(self, g, dL_drgb):
         self.ctx.pose_grad(g, self.views, self.ws_struct, self.T, self.n_contrib, dL_drgb, self.dL_dpose)
@@ -391,6 +393,98 @@ class WindowOptimizer:
         self.graph.replay()
         self.win.step_count += 1
         return self.r.loss
+
+
+class PerViewOptimizer:
+    """The window iteration of WindowOptimizer in the plain per-view form, the
+    baseline the batched form is measured against: every view is projected,
+    binned, composited and back-propagated by its own sequence of launches
+    (one Renderer per view, writing into its view's slice of the packed
+    images), the L1 loss is taken over all views in one call (the batched
+    form's normalisation), the per-view backward passes add their parameter
+    gradients up (gs_render_bwd_accumulate) and one Adam step follows.  Its
+    result equals the batched form's up to the order of float atomics."""
+
+    def __init__(self, params, views, targets, lr=1e-3, betas=(0.9, 0.999), eps=1e-8, device=0,
+                 tile_size=16, storage=None, **cfg):
+        self.win = GaussianWindow(params, device, storage)
+        self.targets = targets
+        self.lr, self.betas, self.eps = lr, betas, eps
+        # packed images of all views and the loss over them
+        self.all = Renderer(views, device, tile_size, capacity=1024, **cfg)
+        self.rs = []
+        off = 0
+        for v in views:
+            r = Renderer([v], device, tile_size, **cfg)
+            n = int(v["W"]) * int(v["H"])
+            r.rgb = self.all.rgb[3 * off:3 * (off + n)]
+            r.T = self.all.T[off:off + n]
+            r.n_contrib = self.all.n_contrib[off:off + n]
+            r.dL_drgb = self.all.dL_drgb[3 * off:3 * (off + n)]
+            self.rs.append(r)
+            off += n
+        self._g = self.win.struct()
+        self._grads = self.win.grad_tensors()
+        self._segs = self.win.segments()
+        self.graph = None
+        self.step_dev = None
+
+    @property
+    def r(self):
+        return self.all
+
+    def _iteration(self, count, step_dev=None):
+        w = self.win
+        for r in self.rs:
+            r.forward(self._g, count=count)
+        self.all.l1(self.targets)
+        for i, r in enumerate(self.rs):
+            r.backward(self._g, r.dL_drgb, grads=self._grads, accumulate=i > 0)
+        ctx = self.all.ctx
+        if step_dev is None:
+            ctx.adam_step(w.flat, w.gflat, w.m, w.v, self.lr, self.betas[0], self.betas[1], self.eps,
+                          w.step_count, self._segs)
+        else:
+            ctx.adam_step_dev(w.flat, w.gflat, w.m, w.v, self.lr, self.betas[0], self.betas[1], self.eps,
+                              step_dev, self._segs)
+
+    def step(self, count=None):
+        if self.graph is not None:
+            self.graph.replay()
+            self.win.step_count += 1
+            return self.all.loss
+        self.win.step_count += 1
+        self._iteration(count)
+        return self.all.loss
+
+    def pairs(self):
+        return sum(int(r.last_pairs) for r in self.rs)
+
+    def check_status(self):
+        out = [r.check_status() for r in self.rs]
+        bad = [o for o in out if o[0] != B.GS_OK]
+        return bad[0] if bad else (B.GS_OK, self.pairs())
+
+    def capture(self):
+        """Captures one iteration in a CUDA graph (after one step, which sizes
+        every view's pair workspace)."""
+        if not all(r._counted for r in self.rs):
+            raise RuntimeError("run one step before capturing (sizes the pair workspaces)")
+        self.step_dev = torch.tensor([self.win.step_count], dtype=torch.int64, device=self.win.device)
+        for attempt in range(3):
+            torch.cuda.synchronize()
+            g = torch.cuda.CUDAGraph()
+            try:
+                with torch.cuda.graph(g, capture_error_mode="relaxed"):
+                    self._iteration(False, self.step_dev)
+            except (RuntimeError, B.GsError) as e:
+                if attempt == 2:
+                    raise
+                warnings.warn("graph capture failed (%s); capturing again" % e)
+                torch.cuda.synchronize()
+                continue
+            self.graph = g
+            return g
 
 
 class _Rasterize(torch.autograd.Function):

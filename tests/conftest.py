@@ -18,6 +18,11 @@ def pytest_configure(config):
 
 def pytest_terminal_summary(terminalreporter, exitstatus, config):
     import parity_log
+    reports = parity_log.report_lines()
+    if reports:
+        terminalreporter.write_sep("-", "error reports")
+        for ln in reports:
+            terminalreporter.write_line(ln)
     lines = parity_log.summary_lines()
     if lines:
         terminalreporter.write_sep("-", "parity exclusions (oracle-flagged borderline pixels / Gaussians)")

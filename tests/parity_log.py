@@ -11,11 +11,25 @@ within 1e-5 of the clamp at 0.
 import os
 
 RECORDS = []
+REPORTS = []
 
 
 def record(kind, share, bound, count, total):
     test = os.environ.get("PYTEST_CURRENT_TEST", "?").split(" ")[0]
     RECORDS.append((test, kind, float(share), float(bound), int(count), int(total)))
+
+
+def report(title, lines):
+    """A table of measured errors to print with the summary."""
+    REPORTS.append((title, list(lines)))
+
+
+def report_lines():
+    out = []
+    for title, lines in REPORTS:
+        out.append(title)
+        out.extend("  " + ln for ln in lines)
+    return out
 
 
 def summary_lines():
