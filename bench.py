@@ -93,6 +93,8 @@ def parse():
                     help="also time the workload with FP32 storage and in the plain per-view form "
                          "(default for --workload mixed)")
     ap.add_argument("--no-compare-forms", dest="compare_forms", action="store_false")
+    ap.add_argument("--deterministic", action="store_true",
+                    help="bit-reproducible backward (fixed-order sums instead of float atomics)")
     ap.add_argument("--ssim-lambda", type=float, default=0.0,
                     help="weight of the D-SSIM term in the photometric loss (0: the L1 loss of the paper)")
     return ap.parse_args()
@@ -382,7 +384,8 @@ def run_b300(args, world, rank, local):
         shape, tune_table = autotune(params, views, target, steps=3, device=local, storage=storage)
     opt = WindowOptimizer(params, views, target, lr=LR, device=local, tile_size=shape[0],
                           ssim_lambda=args.ssim_lambda,
-                          pixels_per_thread=shape[1], batch=shape[2], storage=storage)
+                          pixels_per_thread=shape[1], batch=shape[2], storage=storage,
+                          deterministic=int(args.deterministic))
     ctx = opt.r.ctx
     opt.step(count=True)  # sizes the pair workspace
     cap0 = opt.r.cap
@@ -605,6 +608,7 @@ def run_b300(args, world, rank, local):
                                            if tune_table else None),
                            "l2": "flushed between steps (256 MB write outside the timed events)",
                            "pairs_per_step": int(opt.r.last_pairs), "parallelism": "replicas" if world > 1 else "1 GPU",
+                           "deterministic": bool(args.deterministic),
                            "mpix_per_s": mpix},
                 "roofline": roof,
                 "kernel_ms_per_step": {k: v[1] / n_warm for k, v in prof_all.items()},

@@ -109,6 +109,15 @@ typedef struct gs_config {
      * depend on them; gs_tune-style autotuning picks the fastest. */
     int32_t pixels_per_thread;
     int32_t batch;
+    /* 1: gs_render_bwd sums every gradient in a fixed order, so the same
+     * inputs give the same gradients bit for bit on every run [0].  Each
+     * tile's warps add their per-record totals in shared memory in warp
+     * order, one 9-float partial per (tile, record) pair is written at the
+     * pair's place in the tile lists, and each record's partials are added in
+     * the order of its tiles; the default adds the totals with float atomics,
+     * whose order varies.  Costs 44 bytes of workspace per pair of capacity
+     * (gs_workspace_query includes them) and some speed. */
+    int32_t deterministic;
 } gs_config;
 
 GS_API void gs_config_default(gs_config* cfg);

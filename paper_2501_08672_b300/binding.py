@@ -56,7 +56,8 @@ class GsError(RuntimeError):
 class Config(ctypes.Structure):
     _fields_ = [("tile_size", ctypes.c_int32), ("alpha_min", ctypes.c_float), ("alpha_max", ctypes.c_float),
                 ("T_min", ctypes.c_float), ("blur", ctypes.c_float), ("z_near", ctypes.c_float),
-                ("bg", ctypes.c_float * 3), ("pixels_per_thread", ctypes.c_int32), ("batch", ctypes.c_int32)]
+                ("bg", ctypes.c_float * 3), ("pixels_per_thread", ctypes.c_int32), ("batch", ctypes.c_int32),
+                ("deterministic", ctypes.c_int32)]
 
 
 class View(ctypes.Structure):

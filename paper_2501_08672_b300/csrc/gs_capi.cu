@@ -127,6 +127,7 @@ int sorted_buffer(int total_tiles) {
 struct Layout {
     gs_ws_layout pub;
     size_t scan_part, dkeys1, dvals1, pkeys1, pvals1, hist, hist_part, partials, okeys0, okeys1, ovals0, ovals1, hitmask;
+    size_t pair_rec, pair_inv, pair_grad;  // deterministic backward (0 when off)
     int scan_blocks;
     long long max_g_end;
 };
@@ -210,6 +211,12 @@ int make_layout(gs_ctx* ctx, const gs_config& cfg, const gs_view* views, int n_v
     W.grad2d = take(sizeof(float) * kGrad2D * (size_t)M);
     W.counters = take(sizeof(unsigned long long) * 8);
     L.partials = take(sizeof(float) * (size_t)partials);
+    L.pair_rec = L.pair_inv = L.pair_grad = 0;
+    if (cfg.deterministic) {
+        L.pair_rec = take(sizeof(uint32_t) * (size_t)cap);
+        L.pair_inv = take(sizeof(uint32_t) * (size_t)cap);
+        L.pair_grad = take(sizeof(float) * kGrad2D * (size_t)cap);
+    }
     W.total = off;
     W.sorted_vals = sorted_buffer((int)T) ? L.pvals1 : W.pair_vals;
     W.n_records = M;
@@ -257,6 +264,9 @@ WsPtrs ws_ptrs(const gs_workspace* ws, const Layout& L, int total_tiles) {
     p.grad2d = reinterpret_cast<float*>(b + L.pub.grad2d);
     p.counters = reinterpret_cast<unsigned long long*>(b + L.pub.counters);
     p.partials = reinterpret_cast<float*>(b + L.partials);
+    p.pair_rec = L.pair_rec ? reinterpret_cast<uint32_t*>(b + L.pair_rec) : nullptr;
+    p.pair_inv = L.pair_inv ? reinterpret_cast<uint32_t*>(b + L.pair_inv) : nullptr;
+    p.pair_grad = L.pair_grad ? reinterpret_cast<float*>(b + L.pair_grad) : nullptr;
     p.cap = ws->max_pairs;
     p.scan_blocks = L.scan_blocks;
     p.sorted_buf = sorted_buffer(total_tiles);
@@ -368,6 +378,10 @@ int check_config(const gs_config& c, char* msg, size_t n) {
             snprintf(msg, n, "background not finite");
             return GS_ERR_INVALID_ARG;
         }
+    if (c.deterministic != 0 && c.deterministic != 1) {
+        snprintf(msg, n, "deterministic=%d not in {0, 1}", c.deterministic);
+        return GS_ERR_INVALID_ARG;
+    }
     return GS_OK;
 }
 
@@ -386,6 +400,7 @@ void gs_config_default(gs_config* cfg) {
     cfg->bg[0] = cfg->bg[1] = cfg->bg[2] = 0.f;
     cfg->pixels_per_thread = 0;
     cfg->batch = 0;
+    cfg->deterministic = 0;
 }
 
 const char* gs_version(void) { return "gs_b300 0.1 (sm_103a)"; }

@@ -101,6 +101,10 @@ struct WsPtrs {
     float* grad2d;           // [M][9]
     unsigned long long* counters; // [8]
     float* partials;         // reduction scratch
+    // deterministic backward only (nullptr otherwise):
+    uint32_t* pair_rec;      // [cap] record of each pair at its emission index
+    uint32_t* pair_inv;      // [cap] emission index -> place in the tile lists (~0: listed in no tile)
+    float* pair_grad;        // [cap][9] per-(tile, record) 2D gradient partials, at the place in the tile lists
     long long cap;
     int scan_blocks;
     float log2_alpha_min;    // -inf in exact mode (every tile of the box is reached)

@@ -275,7 +275,12 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_render_fwd(const __grid_const
 template <int NT, int PPT>
 constexpr int bwd_min_blocks() { return PPT >= 4 ? 1 : (768 / NT > 32 ? 32 : 768 / NT); }
 
-template <int TS, int PPT, int BATCH>
+// DET: the deterministic form.  All warps of the tile walk the list in
+// lockstep batches from the tile's deepest contributor; each warp leaves its
+// per-record totals in shared memory, the block adds them in warp order and
+// writes one 9-float partial per listed record at its place in the tile
+// list (pair_grad), zeros where no pixel of the tile contributes; no atomics.
+template <int TS, int PPT, int BATCH, bool DET>
 __global__ void __launch_bounds__(TS * TS / PPT, bwd_min_blocks<TS * TS / PPT, PPT>()) k_render_bwd(const __grid_constant__ BatchParam bp,
                                                               RenderConst rc,
                                                               const float4* __restrict__ rec,
@@ -285,7 +290,8 @@ __global__ void __launch_bounds__(TS * TS / PPT, bwd_min_blocks<TS * TS / PPT, P
                                                               const float* __restrict__ T_final,
                                                               const uint32_t* __restrict__ n_contrib,
                                                               const float* __restrict__ dL_drgb,
-                                                              float* __restrict__ grad2d) {
+                                                              float* __restrict__ grad2d,
+                                                              float* __restrict__ pair_grad) {
     pdl_wait();
     pdl_trigger();
     // Each warp walks the list on its own, back to front from its deepest
@@ -336,11 +342,29 @@ __global__ void __launch_bounds__(TS * TS / PPT, bwd_min_blocks<TS * TS / PPT, P
         mine = max(mine, (uint32_t)nc[k]);
     }
     const int wmax = min((int)__reduce_max_sync(0xffffffffu, mine), (int)(rg.y - rg.x));
+    // deterministic form: per-warp totals of the batch's records, and the
+    // tile's deepest contributor
+    __shared__ float s_acc[DET ? NW : 1][DET ? WB : 1][kGrad2D];
+    __shared__ int s_wmax[DET ? NW : 1];
+    int walk = wmax;
+    if constexpr (DET) {
+        if (lane == 0) s_wmax[warp] = wmax;
+        __syncthreads();
+        walk = 0;
+#pragma unroll
+        for (int i = 0; i < NW; ++i) walk = max(walk, s_wmax[i]);
+    }
 
-    for (int hi = wmax; hi > 0; hi -= WB) {
+    for (int hi = walk; hi > 0; hi -= WB) {
         int n = 0;
+        if constexpr (DET) {
+            for (int i = lane; i < WB * kGrad2D; i += 32) (&s_acc[warp][0][0])[i] = 0.f;
+        }
+        // a warp whose pixels all stop before this batch stages nothing
+        const bool act = !DET || hi - WB < wmax;
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
+            if (!act) break;
             const int rel = hi - 1 - (q * 32 + lane);
             bool reach = false;
             uint32_t r = 0;
@@ -459,14 +483,73 @@ __global__ void __launch_bounds__(TS * TS / PPT, bwd_min_blocks<TS * TS / PPT, P
                 for (int o = 4; o > 0; o >>= 1) yb += __shfl_xor_sync(0xffffffffu, yb, o);
                 const int gl = lane >> 3, el = lane & 7;
                 if (j0 + gl < n) {
-                    float* dst = grad2d + (size_t)__float_as_uint(s_c[warp][j0 + gl].w) * kGrad2D;
-                    if (x[0] != 0.f) atomicAdd(dst + el, x[0]);
-                    if (el == 0 && yb != 0.f) atomicAdd(dst + 8, yb);
+                    if constexpr (DET) {
+                        float* slot = s_acc[warp][hi - 1 - __float_as_int(s_c[warp][j0 + gl].z)];
+                        slot[el] = x[0];
+                        if (el == 0) slot[8] = yb;
+                    } else {
+                        float* dst = grad2d + (size_t)__float_as_uint(s_c[warp][j0 + gl].w) * kGrad2D;
+                        if (x[0] != 0.f) atomicAdd(dst + el, x[0]);
+                        if (el == 0 && yb != 0.f) atomicAdd(dst + 8, yb);
+                    }
                 }
             }
         }
         __syncwarp();
+        if constexpr (DET) {
+            // the tile's partial of each record of the batch: warp totals
+            // added in warp order
+            __syncthreads();
+            for (int i = t; i < WB * kGrad2D; i += NT) {
+                const int slot = i / kGrad2D, c = i - slot * kGrad2D;
+                const int rel = hi - 1 - slot;
+                if (rel < 0) continue;
+                float v = 0.f;
+#pragma unroll
+                for (int w2 = 0; w2 < NW; ++w2) v += s_acc[w2][slot][c];
+                pair_grad[(size_t)(rg.x + (uint32_t)rel) * kGrad2D + c] = v;
+            }
+            __syncthreads();
+        }
     }
+    if constexpr (DET) {
+        // records beyond every pixel's last contributor
+        const size_t end = (size_t)rg.y * kGrad2D;
+        for (size_t i = (size_t)(rg.x + (uint32_t)walk) * kGrad2D + t; i < end; i += NT) pair_grad[i] = 0.f;
+    }
+}
+
+// Deterministic backward: a record's 2D gradient is the sum of its pairs'
+// partials in the order of its tiles.  Its pairs are contiguous in emission
+// order (records in depth order, k-th record at offsets[k]), and pair_inv
+// gives each one's place in the tile lists.  Every record is written.
+__global__ void __launch_bounds__(256) k_pair_grad_reduce(const uint32_t* __restrict__ order,
+                                                          const unsigned long long* __restrict__ offsets,
+                                                          const uint32_t* __restrict__ touched,
+                                                          const uint32_t* __restrict__ pair_inv,
+                                                          const float* __restrict__ pair_grad, long long M,
+                                                          long long cap, const unsigned long long* __restrict__ n_dev,
+                                                          float* __restrict__ grad2d) {
+    pdl_wait();
+    pdl_trigger();
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= M) return;
+    const uint32_t r = order[k];
+    unsigned long long n = n_dev[0];
+    if (n > (unsigned long long)cap) n = (unsigned long long)cap;
+    const unsigned long long e0 = offsets[k], e1 = e0 + touched[r];
+    float acc[kGrad2D];
+#pragma unroll
+    for (int c = 0; c < kGrad2D; ++c) acc[c] = 0.f;
+    for (unsigned long long e = e0; e < e1 && e < n; ++e) {
+        const uint32_t p = pair_inv[e];
+        if (p == 0xFFFFFFFFu) continue;
+        const float* src = pair_grad + (size_t)p * kGrad2D;
+#pragma unroll
+        for (int c = 0; c < kGrad2D; ++c) acc[c] += src[c];
+    }
+#pragma unroll
+    for (int c = 0; c < kGrad2D; ++c) grad2d[(size_t)r * kGrad2D + c] = acc[c];
 }
 
 constexpr int kL1Threads = 256;
@@ -795,20 +878,37 @@ cudaError_t launch_render_fwd(const BatchParam& bp, const RenderConst& rc, const
 cudaError_t launch_render_bwd(const BatchParam& bp, const RenderConst& rc, const WsPtrs& ws,
                               const float* T_final, const uint32_t* n_contrib,
                               const float* dL_drgb, cudaStream_t s, Prof& pf) {
-    pf.count(1);
-    cudaError_t e = cudaMemsetAsync(ws.grad2d, 0, sizeof(float) * kGrad2D * (size_t)bp.total_recs, s);
+    // deterministic form: per-pair partials, then a fixed-order sum per record
+    // (which writes every record, so no clearing)
+    const bool det = ws.pair_grad != nullptr;
+    cudaError_t e = cudaSuccess;
+    if (!det) {
+        pf.count(1);
+        e = cudaMemsetAsync(ws.grad2d, 0, sizeof(float) * kGrad2D * (size_t)bp.total_recs, s);
+    }
     if (e != cudaSuccess || bp.total_tiles <= 0) return e;
     const uint32_t* svals = ws.pvals[ws.sorted_buf];
-    const int pi = pf.begin(GS_KF_RASTER_BWD, s);
+    const int pi = pf.begin(GS_KF_RASTER_BWD, s, det ? 2 : 1);
     bool done = false;
 #define GS_X(T, P, B)                                                                                      \
     if (!done && bp.tile_size == T && bp.ppt == P && bp.batch == B) {                                      \
-        pdl_launch(k_render_bwd<T, P, B>, bp.total_tiles, T * T / P, 0, s, bp, rc, ws.rec, ws.ranges, ws.ovals[1], svals, T_final, \
-                                                                    n_contrib, dL_drgb, ws.grad2d);       \
+        if (det)                                                                                           \
+            pdl_launch(k_render_bwd<T, P, B, true>, bp.total_tiles, T * T / P, 0, s, bp, rc, ws.rec, ws.ranges, \
+                       ws.ovals[1], svals, T_final, n_contrib, dL_drgb, ws.grad2d, ws.pair_grad);         \
+        else                                                                                               \
+            pdl_launch(k_render_bwd<T, P, B, false>, bp.total_tiles, T * T / P, 0, s, bp, rc, ws.rec, ws.ranges, \
+                       ws.ovals[1], svals, T_final, n_contrib, dL_drgb, ws.grad2d, ws.pair_grad);         \
         done = true;                                                                                       \
     }
     GS_RASTER_VARIANTS(GS_X)
 #undef GS_X
+    if (done && det) {
+        // the binning's depth order: its 4-pass radix sort of the 32-bit high
+        // words ends in buffer 0, which the tie fix-up reorders in place
+        const long long M = bp.total_recs;
+        pdl_launch(k_pair_grad_reduce, (unsigned)((M + 255) / 256), 256, 0, s, ws.dvals[0], ws.offsets,
+                   ws.tiles_touched, ws.pair_inv, ws.pair_grad, M, ws.cap, ws.counters, ws.grad2d);
+    }
     pf.end(pi, s);
     if (!done) return cudaErrorInvalidValue;
     return cudaGetLastError();

@@ -575,9 +575,21 @@ __global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ order
                                               const float4* __restrict__ rec,
                                               const unsigned long long* __restrict__ offsets, long long M,
                                               long long cap, int ts, float log2_alpha_min,
-                                              uint32_t* __restrict__ pkeys, uint32_t* __restrict__ pvals) {
+                                              uint32_t* __restrict__ pkeys, uint32_t* __restrict__ pvals,
+                                              uint32_t* __restrict__ pair_rec) {
     pdl_wait();
     pdl_trigger();
+    // The pair's value: its record, or, for the deterministic backward
+    // (pair_rec non-NULL), its own emission index, the record going to
+    // pair_rec, so that the tile sort also yields every pair's emission index.
+    auto put_val = [pvals, pair_rec](unsigned long long q, uint32_t rr) {
+        if (pair_rec) {
+            pvals[q] = (uint32_t)q;
+            pair_rec[q] = rr;
+        } else {
+            pvals[q] = rr;
+        }
+    };
     const long long j0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const bool live = j0 < M;
     if (__all_sync(0xffffffffu, !live)) return;
@@ -642,7 +654,7 @@ __global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ order
                 const uint32_t we = ie & 0xFFu, mul = (ie >> 8) & 0xFFFu;
                 const uint32_t row = (bit * mul) >> 11;
                 pkeys[q] = found ? ke + row * se + (bit - row * we) : 0xFFFFFFFFu;
-                pvals[q] = re;
+                put_val(q, re);
             }
         }
     }
@@ -653,7 +665,7 @@ __global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ order
             for (int tx = tx0; tx < tx1 && o < oend; ++tx, ++o)
                 if (o < ucap) {
                     pkeys[o] = (uint32_t)rc.z + (uint32_t)ty * (uint32_t)rc.w + (uint32_t)tx;
-                    pvals[o] = r;
+                    put_val(o, r);
                 }
     }
     FootRows fr{};
@@ -702,7 +714,7 @@ __global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ order
                 const unsigned long long q = o + pr;
                 if (pr < total && q < boend && q < ucap) {
                     pkeys[q] = bz + (uint32_t)(row0 + e) * bwid + (uint32_t)ae + (pr - se);
-                    pvals[q] = br;
+                    put_val(q, br);
                 }
             }
             o += total;
@@ -710,7 +722,7 @@ __global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ order
         for (unsigned long long q = o + lane; q < boend; q += 32)
             if (q < ucap) {
                 pkeys[q] = 0xFFFFFFFFu;
-                pvals[q] = br;
+                put_val(q, br);
             }
     }
 }
@@ -794,6 +806,28 @@ __global__ void __launch_bounds__(256) k_ranges(const uint32_t* __restrict__ key
                 if (j + 1 == n || x != k) ranges[k].y = (uint32_t)(j + 1);
             }
         }
+    }
+}
+
+// Deterministic backward: after the tile sort the pair values are emission
+// indices.  Each place p of the tile lists gets its pair's record back, and
+// pair_inv records where each emission index went (~0 for a pair listed in
+// no tile), so that a record's partials can later be found in the order of
+// its tiles (its pairs are contiguous in emission order).
+__global__ void __launch_bounds__(256) k_pair_places(const uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                                                     const uint32_t* __restrict__ pair_rec,
+                                                     uint32_t* __restrict__ pair_inv, long long cap,
+                                                     const unsigned long long* __restrict__ n_dev,
+                                                     uint32_t n_tiles) {
+    pdl_wait();
+    pdl_trigger();
+    const unsigned long long n = clamp_n((unsigned long long)cap, n_dev);
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long p = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
+        const uint32_t e = vals[p];
+        if (e >= n) continue;  // cannot happen: every emitted value is an index below n
+        vals[p] = pair_rec[e];
+        pair_inv[e] = keys[p] < n_tiles ? (uint32_t)p : 0xFFFFFFFFu;
     }
 }
 
@@ -893,7 +927,7 @@ cudaError_t launch_bin(const BatchParam& bp, WsPtrs& ws, unsigned int* status,
     pi = pf.begin(GS_KF_EMIT, s);
     pdl_launch(k_emit, (unsigned)((M + 255) / 256), 256, 0, s, order, ws.tiles_touched, ws.hitmask, ws.rect, ws.rec, ws.offsets, M,
                                                        ws.cap, bp.tile_size, ws.log2_alpha_min, ws.pkeys[0],
-                                                       ws.pvals[0]);
+                                                       ws.pvals[0], ws.pair_rec);
     pf.end(pi, s);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // 4. stable sort of pairs by global tile id
@@ -903,6 +937,11 @@ cudaError_t launch_bin(const BatchParam& bp, WsPtrs& ws, unsigned int* status,
     pi = pf.begin(GS_KF_TILE_SORT, s, 0);
     e = radix_sort(ws.pkeys[0], ws.pvals[0], ws.pkeys[1], ws.pvals[1], ws, (unsigned long long)ws.cap,
                    ws.counters, tile_bits, &pbuf, status, s, pf);
+    if (e == cudaSuccess && ws.pair_rec) {
+        pf.count(1);
+        pdl_launch(k_pair_places, 1184, 256, 0, s, ws.pkeys[pbuf], ws.pvals[pbuf], ws.pair_rec, ws.pair_inv, ws.cap,
+                   ws.counters, (uint32_t)bp.total_tiles);
+    }
     pf.end(pi, s);
     if (e != cudaSuccess) return e;
     ws.sorted_buf = pbuf;
