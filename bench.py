@@ -93,6 +93,7 @@ def parse():
                     help="also time the workload with FP32 storage and in the plain per-view form "
                          "(default for --workload mixed)")
     ap.add_argument("--no-compare-forms", dest="compare_forms", action="store_false")
+    ap.add_argument("--odo-frames", type=int, default=0, help="odometry workload: frames (0: 200)")
     ap.add_argument("--deterministic", action="store_true",
                     help="bit-reproducible backward (fixed-order sums instead of float atomics)")
     ap.add_argument("--ssim-lambda", type=float, default=0.0,
@@ -624,9 +625,13 @@ def run_b300(args, world, rank, local):
         dist.destroy_process_group()
 
 
-ODO_METRIC = ("odometry Gauss-Newton pose iterations/s at 500k Gaussians, 1280x1024 "
-              "(project + bin + pose normal equations); % of roofline")
-ODO_N, ODO_W, ODO_H, ODO_F, ODO_FRAMES, ODO_ITERS = 500_000, 1280, 1024, 1200.0, 24, 5
+ODO_METRIC = ("odometry photometric pose iterations/s at 500k Gaussians, one 1280x1024 view "
+              "(forward + L1 + pose-only backward), 200 frames x 5 iterations; % of roofline")
+ODO_N, ODO_W, ODO_H, ODO_F, ODO_FRAMES, ODO_ITERS = 500_000, 1280, 1024, 1200.0, 200, 5
+# host step of the pose-gradient form, T <- Exp(-eta g) T, per unit of dL/dxi
+# (rotation, translation); the paper feeds the gradient to its IESKF, the
+# step rule does not change the GPU work
+ODO_ETA = (2e-2, 2e-2)
 # algorithmic FP32 operations of the pose normal equations (FMA = 2):
 #   per visited fragment 12 (the test, as above);
 #   per contributing fragment 10 (forward) + 16 (m = M d, its products, the alpha
@@ -636,12 +641,17 @@ FLOP_PN_VISITED, FLOP_PN_CONTRIB, FLOP_PN_PIXEL = 12.0, 194.0, 204.0
 
 
 def run_odometry(args, world, rank, local):
-    """One Gauss-Newton pose iteration per step on the odometry workload:
-    500k fixed Gaussians, one 1280x1024 view, frames on an arc, each started
-    from a pose perturbed by 2 degrees and 5 cm, ODO_ITERS iterations per
-    frame; each iteration projects, bins, builds the normal equations of the
-    photometric residual on the GPU, reads the 28 sums back and solves the
-    6x6 system on the host."""
+    """Configuration 5, the photometric pose update: 500k fixed Gaussians,
+    one 1280x1024 view, 200 frames on an arc, each started from a pose
+    perturbed by 2 degrees and 5 cm, 5 iterations per frame.  Two forms run
+    over all frames, each timed per iteration by CUDA events (device time)
+    and by the host clock (end to end, with the read-back and host step):
+      pose gradient (the headline value): project, bin, composite with the
+        L1 loss folded in, pose-only backward (gs_pose_grad), read back the 6
+        floats, host step T <- Exp(-eta g) T;
+      normal equations: project, bin, per-pixel pose Jacobian normal
+        equations (gs_pose_normal), read back the 28 sums, host Gauss-Newton
+        solve (the linearisation the paper's IESKF update uses)."""
     import torch
     from paper_2501_08672_b300 import binding as B
     from paper_2501_08672_b300 import scenes
@@ -649,8 +659,9 @@ def run_odometry(args, world, rank, local):
 
     torch.cuda.set_device(local)
     n = ODO_N
+    n_frames = args.odo_frames or ODO_FRAMES
     params = scenes.box_room_scene(n, seed=2 + rank, sh_degree=1)
-    true_v, start_v = scenes.odometry_frames(ODO_FRAMES, ODO_W, ODO_H, ODO_F, seed=rank)
+    true_v, start_v = scenes.odometry_frames(n_frames, ODO_W, ODO_H, ODO_F, seed=rank)
     for v in true_v + start_v:
         v["g_begin"], v["g_end"] = 0, n
     win = GaussianWindow(params, local)
@@ -672,7 +683,19 @@ def run_odometry(args, world, rank, local):
         X = D @ np.linalg.inv(E)
         return math.degrees(math.acos(max(-1.0, min(1.0, (np.trace(X[:3, :3]) - 1) / 2)))), float(np.linalg.norm(X[:3, 3]))
 
-    def iterate(view, target, ev=None):
+    def iterate_grad(view, target, ev=None):
+        r.set_views([view])
+        if ev is not None:
+            ev[0].record()
+        r.forward(g, count=False, target=target)
+        r.pose_grad(g, r.dL_drgb)
+        if ev is not None:
+            ev[1].record()
+        gp = r.dL_dpose.double().cpu().numpy()        # synchronises: D2H of 6 floats
+        xi = np.concatenate([-ODO_ETA[0] * gp[:3], -ODO_ETA[1] * gp[3:]])
+        return apply_left(view, xi)
+
+    def iterate_normal(view, target, ev=None):
         r.set_views([view])
         if ev is not None:
             ev[0].record()
@@ -683,79 +706,108 @@ def run_odometry(args, world, rank, local):
             ev[1].record()
         A, b, rr = B.unpack_normal(normal)[0]          # synchronises: D2H of 28 doubles
         xi = np.linalg.solve(A + 1e-6 * np.trace(A) / 6.0 * np.eye(6), b)
-        return apply_left(view, xi), rr
+        return apply_left(view, xi)
 
-    # warm-up
-    v = start_v[0]
-    for _ in range(max(args.warmup, 3)):
-        v, _ = iterate(v, targets[0])
-    K = args.steps
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    def run_path(iterate, families):
+        v = start_v[0]
+        for _ in range(max(args.warmup, 3)):
+            v = iterate(v, targets[0])
+        K = n_frames * ODO_ITERS
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        r.ctx.profile(families)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        finals, start_err = [], []
+        k = 0
+        for fr in range(n_frames):
+            v = start_v[fr]
+            start_err.append(pose_err(v, true_v[fr]))
+            for _ in range(ODO_ITERS):
+                v = iterate(v, targets[fr], evs[k])
+                k += 1
+            finals.append(pose_err(v, true_v[fr]))
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        prof = r.ctx.profile_collect()
+        r.ctx.profile([])
+        rc, need = r.check_status()
+        if rc != B.GS_OK:
+            raise RuntimeError("pair capacity exceeded in the timed region (%d needed)" % need)
+        dev_ms = float(sum(a.elapsed_time(b) for a, b in evs))
+        rot = [a for a, _ in finals]
+        trn = [t for _, t in finals]
+        conv = {"frames": len(finals), "median_start_rot_deg": float(np.median([a for a, _ in start_err])),
+                "median_start_trans_m": float(np.median([t for _, t in start_err])),
+                "median_final_rot_deg": float(np.median(rot)), "median_final_trans_m": float(np.median(trn)),
+                "max_final_rot_deg": float(np.max(rot)), "max_final_trans_m": float(np.max(trn))}
+        return K, dev_ms, wall, prof, conv, v
+
     sampler = ClockSampler(local)
-    r.ctx.profile(B.KERNEL_FAMILIES)
     sampler.start()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    finals = []
-    k = 0
-    frame = 0
-    while k < K:
-        fr = frame % ODO_FRAMES
-        v = start_v[fr]
-        for _ in range(ODO_ITERS):
-            if k >= K:
-                break
-            v, rr = iterate(v, targets[fr], evs[k])
-            k += 1
-        finals.append(pose_err(v, true_v[fr]))
-        frame += 1
-    torch.cuda.synchronize()
-    wall = time.perf_counter() - t0
+    K, dev_ms, wall, prof, conv, v_last = run_path(iterate_grad, B.KERNEL_FAMILIES)
+    Kn, dev_ms_n, wall_n, prof_n, conv_n, v_last_n = run_path(iterate_normal, B.KERNEL_FAMILIES)
     clocks = sampler.stop()
-    prof = r.ctx.profile_collect()
-    rc, need = r.check_status()
-    if rc != B.GS_OK:
-        raise RuntimeError("pair capacity exceeded in the timed region (%d needed)" % need)
-    dev_ms = float(sum(a.elapsed_time(b) for a, b in evs))
     value = K / (dev_ms / 1e3)
-    # roofline of the pose-normal kernels from fragment counts at the last pose
-    n_used = torch.empty_like(r.n_contrib)
-    r.set_views([v])
-    r.forward(g, count=False, n_used=n_used)
-    torch.cuda.synchronize()
-    visited = float(r.n_contrib.double().sum().item())
-    contrib = float(n_used.double().sum().item())
-    pn_launches, pn_ms = prof.get("pose_normal", (0, 0.0))
-    calls = K
-    flop = FLOP_PN_VISITED * visited + FLOP_PN_CONTRIB * contrib + FLOP_PN_PIXEL * ODO_W * ODO_H
     ffma, ex2 = r.ctx.calibrate_alu()
-    achieved = flop / (pn_ms / calls / 1e3) / 1e12
-    roof = {"bound": "alu", "kernel": "pose_normal (tangents + forward-mode compositing + FP64 totals)",
-            "achieved": achieved, "peak": ffma, "unit": "TFLOP/s", "frac": achieved / ffma, "traffic": None,
-            "avg_call_ms": pn_ms / calls, "visited_fragments": visited, "contributing_fragments": contrib,
-            "flop_per_call": flop, "peak_basis": "measured: FP32 FMA microbenchmark (gs_calibrate_alu, best of 3)"}
-    rot = [a for a, _ in finals]
-    trn = [t for _, t in finals]
+
+    def fragments(view):
+        n_used = torch.empty_like(r.n_contrib)
+        r.set_views([view])
+        r.forward(g, count=False, n_used=n_used)
+        torch.cuda.synchronize()
+        return float(r.n_contrib.double().sum().item()), float(n_used.double().sum().item())
+
+    # roofline of the dominant kernel of the pose-gradient form (the
+    # compositing backward) and of the normal-equation kernels, from
+    # fragment counts at each form's last pose
+    visited, contrib = fragments(v_last)
+    dom = max(prof, key=lambda kk: prof[kk][1])
+    d_l, d_ms = prof[dom]
+    if dom in FLOP_CONTRIB:
+        flop = FLOP_VISITED * visited + FLOP_CONTRIB[dom] * contrib
+        ach = flop / (d_ms / max(d_l, 1) / 1e3) / 1e12
+        roof = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": ffma, "unit": "TFLOP/s", "frac": ach / ffma,
+                "traffic": None, "avg_launch_ms": d_ms / max(d_l, 1), "visited_fragments": visited,
+                "contributing_fragments": contrib, "flop_per_launch": flop,
+                "peak_basis": "measured: FP32 FMA microbenchmark (gs_calibrate_alu, best of 3)"}
+    else:
+        roof = {"bound": "hbm", "kernel": dom, "achieved": None, "peak": peaks()[0], "unit": "GB/s", "frac": None,
+                "traffic": None}
+    visited_n, contrib_n = fragments(v_last_n)
+    pn_launches, pn_ms = prof_n.get("pose_normal", (0, 0.0))
+    flop_n = FLOP_PN_VISITED * visited_n + FLOP_PN_CONTRIB * contrib_n + FLOP_PN_PIXEL * ODO_W * ODO_H
+    ach_n = flop_n / (pn_ms / Kn / 1e3) / 1e12
     line = {"metric": ODO_METRIC, "value": value, "unit": "it/s", "n_gpus": world, "steps": K,
             "warmup": max(args.warmup, 3), "ms_per_step": dev_ms / K, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "odometry: 500k fixed planar Gaussians (SH degree 1), one 1280x1024 view, "
-                                   "%d frames on an arc, start poses perturbed by 2 deg and 5 cm, %d Gauss-Newton "
-                                   "iterations per frame" % (ODO_FRAMES, ODO_ITERS),
-                       "n_gaussians": n, "image": [ODO_W, ODO_H], "tile_size": 16,
-                       "timed": "device time of project + bin + pose normal equations per iteration (CUDA events)",
+                                   "%d frames on an arc, start poses perturbed by 2 deg and 5 cm, %d iterations "
+                                   "per frame" % (n_frames, ODO_ITERS),
+                       "n_gaussians": n, "image": [ODO_W, ODO_H], "tile_size": 16, "frames": n_frames,
+                       "iterations_per_frame": ODO_ITERS,
+                       "timed": "device time per iteration (CUDA events): project + bin + composite with the L1 "
+                                "loss + pose-only backward",
+                       "host_step": "T <- Exp(-eta g) T, eta = %g (rotation), %g (translation)" % ODO_ETA,
                        "l2": "inputs larger than L2 (500k x 48 B records, 1.3 Mpix images)"},
+            "frames_per_s": value / ODO_ITERS,
             "roofline": roof,
             "kernel_ms_per_step": {kk: vv[1] / K for kk, vv in prof.items()},
-            "e2e": {"value": K / wall, "unit": "it/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 28 * 8,
-                    "note": "wall clock per iteration including the D2H of the normal equations and the host solve; "
-                            "targets are resident"},
-            "convergence": {"frames": len(finals), "median_final_rot_deg": float(np.median(rot)),
-                            "median_final_trans_m": float(np.median(trn)),
-                            "max_final_rot_deg": float(np.max(rot))},
+            "e2e": {"value": K / wall, "unit": "it/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 6 * 4,
+                    "note": "host clock per iteration including the read-back of the pose gradient and the host "
+                            "step; the frames are resident"},
+            "convergence": conv,
+            "forms": {"normal_equations": {
+                "value": Kn / (dev_ms_n / 1e3), "unit": "it/s", "frames_per_s": Kn / (dev_ms_n / 1e3) / ODO_ITERS,
+                "ms_per_step": dev_ms_n / Kn,
+                "timed": "device time per iteration: project + bin + pose normal equations (tangents, "
+                         "forward-mode compositing, FP64 totals)",
+                "e2e_it_s": Kn / wall_n, "e2e_note": "with the read-back of 28 doubles and the host 6x6 solve",
+                "kernel_ms_per_step": {kk: vv[1] / Kn for kk, vv in prof_n.items()},
+                "roofline": {"bound": "alu", "kernel": "pose_normal", "achieved": ach_n, "peak": ffma,
+                             "unit": "TFLOP/s", "frac": ach_n / ffma, "flop_per_call": flop_n},
+                "convergence": conv_n}},
             "gpu_launches": int(sum(vv[0] for vv in prof.values())), "clocks": clocks}
     print(json.dumps(line), flush=True)
-
 
 MAINT_SIZES = (100_000, 500_000, 1_000_000, 2_000_000, 5_000_000)
 
