@@ -38,20 +38,28 @@ namespace {
 // compact WW x RPW block, so a footprint edge crossing the warp's block
 // leaves few k with only a handful of active lanes.  WW = TS, except for
 // 16 x 16 tiles at 2 pixels per thread, whose four warps take 8 x 8 blocks
-// (squarer blocks are reached by fewer records than 16 x 4 strips).
+// (squarer blocks are reached by fewer records than 16 x 4 strips), and at
+// 4 pixels per thread (QUAD), whose two warps take 16 x 8 blocks, the k-th
+// pixels of a warp being the k-th 8 x 4 quadrant of its block: the same
+// 8 x 4 groups of pixels per body as at 2 pixels per thread, with half as
+// many warps staging and reducing each record.
 template <int TS, int PPT>
 struct PixelMap {
     static_assert(TS <= 32 && 32 % TS == 0 && (TS * TS / PPT) % 32 == 0, "unsupported launch shape");
-    static constexpr int WW = (TS == 16 && PPT == 2) ? 8 : TS;
+    static constexpr bool QUAD = TS == 16 && PPT == 4;
+    static constexpr int WW = (TS == 16 && (PPT == 2 || QUAD)) ? 8 : TS;
     static constexpr int RPW = 32 / WW;
-    static constexpr int WCOLS = TS / WW;
-    int px, py;  // column, row of pixel 0; pixel k is at row py + k * RPW
+    static constexpr int WCOLS = QUAD ? 1 : TS / WW;
+    int px, py;  // column, row of pixel 0
     __device__ __forceinline__ PixelMap(int tx, int ty, int t) {
         const int w = t >> 5, l = t & 31;
         px = tx * TS + (w % WCOLS) * WW + (l % WW);
-        py = ty * TS + (w / WCOLS) * RPW * PPT + l / WW;
+        py = ty * TS + (w / WCOLS) * RPW * (QUAD ? 2 : PPT) + l / WW;
     }
-    __device__ __forceinline__ int row(int k) const { return py + k * RPW; }
+    __device__ __forceinline__ int row(int k) const { return py + (QUAD ? (k >> 1) : k) * RPW; }
+    __device__ __forceinline__ int col(int k) const { return QUAD ? px + (k & 1) * 8 : px; }
+    // distinct columns of a thread's pixels; pixel k is in column k % NCOL
+    static constexpr int NCOL = QUAD ? 2 : 1;
 };
 
 // Pixel-centre box of the pixels a warp owns.  A record whose footprint box
@@ -73,8 +81,8 @@ __device__ __forceinline__ bool ellipse_reaches(const WarpBox& wb, float4 r0, fl
     return footprint_hits_rect(fp, wb.cx - wb.hx, wb.cx + wb.hx, wb.cy - wb.hy, wb.cy + wb.hy);
 }
 
-__device__ __forceinline__ WarpBox warp_box(int px, int py_first, int py_last) {
-    const int x0 = __reduce_min_sync(0xffffffffu, px), x1 = __reduce_max_sync(0xffffffffu, px);
+__device__ __forceinline__ WarpBox warp_box(int px_first, int px_last, int py_first, int py_last) {
+    const int x0 = __reduce_min_sync(0xffffffffu, px_first), x1 = __reduce_max_sync(0xffffffffu, px_last);
     const int y0 = __reduce_min_sync(0xffffffffu, py_first), y1 = __reduce_max_sync(0xffffffffu, py_last);
     WarpBox b;
     b.cx = 0.5f * (float)(x0 + x1 + 1);
@@ -85,8 +93,14 @@ __device__ __forceinline__ WarpBox warp_box(int px, int py_first, int py_last) {
 }
 constexpr int kGroup = 4;  // Gaussians per warp reduction in the backward
 
+// Register budget of the forward: the compiler's choice (0 = no minimum of
+// resident blocks; capping the 16 x 16 tile at 4 pixels per thread to 64
+// registers for 32 warps spilled and was slower).
+template <int NT, int PPT>
+constexpr int fwd_min_blocks() { return 0; }
+
 template <int TS, int PPT, int BATCH>
-__global__ void __launch_bounds__(TS * TS / PPT) k_render_fwd(const __grid_constant__ BatchParam bp,
+__global__ void __launch_bounds__(TS * TS / PPT, fwd_min_blocks<TS * TS / PPT, PPT>()) k_render_fwd(const __grid_constant__ BatchParam bp,
                                                               RenderConst rc,
                                                               const float4* __restrict__ rec,
                                                               const uint2* __restrict__ ranges,
@@ -122,13 +136,14 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_render_fwd(const __grid_const
     const int lt = tile - V.tile_off;
     const int ty = lt / V.tiles_x, tx = lt - ty * V.tiles_x;
     const PixelMap<TS, PPT> pm(tx, ty, t);
-    const int px = pm.px;
-    const float fx = px + 0.5f;
-    const WarpBox wb = warp_box(px, pm.row(0), pm.row(PPT - 1));
+    const WarpBox wb = warp_box(pm.col(0), pm.col(PPT - 1), pm.row(0), pm.row(PPT - 1));
     // thr[k]: the exponent a fragment must reach at pixel k; +inf once the
     // pixel is saturated (or outside the image), so one compare both skips
     // faint fragments and finished pixels
-    float fy[PPT], T[PPT], C0[PPT], C1[PPT], C2[PPT], thr[PPT];
+    constexpr int NCOL = PixelMap<TS, PPT>::NCOL;
+    float fx[NCOL], fy[PPT], T[PPT], C0[PPT], C1[PPT], C2[PPT], thr[PPT];
+#pragma unroll
+    for (int c = 0; c < NCOL; ++c) fx[c] = pm.col(c) + 0.5f;
     uint32_t last[PPT], used[PPT];
     const float kDone = __int_as_float(0x7f800000);
 #pragma unroll
@@ -138,7 +153,7 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_render_fwd(const __grid_const
         C0[k] = C1[k] = C2[k] = 0.f;
         last[k] = 0;
         used[k] = 0;
-        thr[k] = (px < V.W && pm.row(k) < V.H) ? rc.log2_alpha_min : kDone;
+        thr[k] = (pm.col(k) < V.W && pm.row(k) < V.H) ? rc.log2_alpha_min : kDone;
     }
     const uint2 rg = ranges[tile];
 
@@ -177,10 +192,16 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_render_fwd(const __grid_const
                 const float4 b = s_b[w][j];
                 const float4 c = s_c[w][j];
                 const uint32_t pos1 = __float_as_uint(c.z);
-                const float dx = fx - a.x;
-                const float u1 = dx * a.z, u2 = dx * b.x;
+                float dxc[NCOL], u1c[NCOL], u2c[NCOL];
+#pragma unroll
+                for (int c = 0; c < NCOL; ++c) {
+                    dxc[c] = fx[c] - a.x;
+                    u1c[c] = dxc[c] * a.z;
+                    u2c[c] = dxc[c] * b.x;
+                }
 #pragma unroll
                 for (int k = 0; k < PPT; ++k) {
+                    const float dx = dxc[k % NCOL], u1 = u1c[k % NCOL], u2 = u2c[k % NCOL];
                     const float dy = fy[k] - a.y;
                     const float t1 = fmaf(dy, a.w, u1);
                     const float t2 = fmaf(dy, b.y, u2);
@@ -212,8 +233,8 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_render_fwd(const __grid_const
     float lsum = 0.f;
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
-        if (px < V.W && pm.row(k) < V.H) {
-            const long long pl = (long long)pm.row(k) * V.W + px;
+        if (pm.col(k) < V.W && pm.row(k) < V.H) {
+            const long long pl = (long long)pm.row(k) * V.W + pm.col(k);
             const float o0 = C0[k] + T[k] * rc.bg[0];
             const float o1 = C1[k] + T[k] * rc.bg[1];
             const float o2 = C2[k] + T[k] * rc.bg[2];
@@ -271,9 +292,14 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_render_fwd(const __grid_const
 // Register budget of the backward: enough blocks for 24 resident warps per
 // SM (the kernel is issue-bound and its warps stall on short dependency
 // chains, so occupancy buys issue slots).
-// (From 4 pixels per thread on, the cap would spill: no target there.)
+// (From 4 pixels per thread on, the cap would spill: no target there, except
+// the 16 x 16 tile's two 16 x 8 warp blocks (QUAD), held to 96 registers
+// for 20 resident warps: 1.127 ms against 1.162 at 116 registers and 1.135
+// at 80 with spills, at the headline workload.)
 template <int NT, int PPT>
-constexpr int bwd_min_blocks() { return PPT >= 4 ? 1 : (768 / NT > 32 ? 32 : 768 / NT); }
+constexpr int bwd_min_blocks() {
+    return (NT == 64 && PPT == 4) ? 10 : (PPT >= 4 ? 1 : (768 / NT > 32 ? 32 : 768 / NT));
+}
 
 // DET: the deterministic form.  All warps of the tile walk the list in
 // lockstep batches from the tile's deepest contributor; each warp leaves its
@@ -314,14 +340,15 @@ __global__ void __launch_bounds__(TS * TS / PPT, bwd_min_blocks<TS * TS / PPT, P
     const int lt = tile - V.tile_off;
     const int ty = lt / V.tiles_x, tx = lt - ty * V.tiles_x;
     const PixelMap<TS, PPT> pm(tx, ty, t);
-    const int px = pm.px;
-    const float fx = px + 0.5f;
-    const WarpBox wb = warp_box(px, pm.row(0), pm.row(PPT - 1));
+    const WarpBox wb = warp_box(pm.col(0), pm.col(PPT - 1), pm.row(0), pm.row(PPT - 1));
     const uint2 rg = ranges[tile];
     const long long hw = (long long)V.W * V.H;
     const float* gimg = dL_drgb + 3 * V.pix_off;
 
-    float fy[PPT], T[PPT], g0[PPT], g1[PPT], g2[PPT], gR[PPT];
+    constexpr int NCOL = PixelMap<TS, PPT>::NCOL;
+    float fx[NCOL], fy[PPT], T[PPT], g0[PPT], g1[PPT], g2[PPT], gR[PPT];
+#pragma unroll
+    for (int c = 0; c < NCOL; ++c) fx[c] = pm.col(c) + 0.5f;
     int nc[PPT];
     uint32_t mine = 0;
 #pragma unroll
@@ -330,8 +357,8 @@ __global__ void __launch_bounds__(TS * TS / PPT, bwd_min_blocks<TS * TS / PPT, P
         T[k] = 1.f;
         g0[k] = g1[k] = g2[k] = 0.f;
         nc[k] = 0;
-        if (px < V.W && pm.row(k) < V.H) {
-            const long long pl = (long long)pm.row(k) * V.W + px;
+        if (pm.col(k) < V.W && pm.row(k) < V.H) {
+            const long long pl = (long long)pm.row(k) * V.W + pm.col(k);
             T[k] = T_final[V.pix_off + pl];
             nc[k] = (int)n_contrib[V.pix_off + pl];
             g0[k] = gimg[pl];
@@ -409,10 +436,16 @@ __global__ void __launch_bounds__(TS * TS / PPT, bwd_min_blocks<TS * TS / PPT, P
                 const float4 b = s_b[warp][j];
                 const float4 c = s_c[warp][j];
                 const int rel = __float_as_int(c.z);
-                const float dx = fx - a.x;
-                const float u1 = dx * a.z, u2 = dx * b.x;
+                float dxc[NCOL], u1c[NCOL], u2c[NCOL];
+#pragma unroll
+                for (int c = 0; c < NCOL; ++c) {
+                    dxc[c] = fx[c] - a.x;
+                    u1c[c] = dxc[c] * a.z;
+                    u2c[c] = dxc[c] * b.x;
+                }
 #pragma unroll
                 for (int k = 0; k < PPT; ++k) {
+                    const float dx = dxc[k % NCOL], u1 = u1c[k % NCOL], u2 = u2c[k % NCOL];
                     const float dy = fy[k] - a.y;
                     const float t1 = fmaf(dy, a.w, u1);
                     const float t2 = fmaf(dy, b.y, u2);
@@ -663,7 +696,7 @@ __global__ void __launch_bounds__(TS * TS) k_render_pose_normal(const __grid_con
     const PixelMap<TS, 1> pm(tx, ty, t);
     const int px = pm.px, py = pm.row(0);
     const float fx = px + 0.5f, fy = py + 0.5f;
-    const WarpBox wb = warp_box(px, py, py);
+    const WarpBox wb = warp_box(px, px, py, py);
     const bool inside = px < V.W && py < V.H;
     bool done = !inside;
     float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
