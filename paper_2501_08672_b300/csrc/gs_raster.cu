@@ -289,16 +289,18 @@ __global__ void __launch_bounds__(TS * TS / PPT, fwd_min_blocks<TS * TS / PPT, P
 // with one atomic per (warp, record, component); the factor ln 2, the
 // principal axes and the conversion to the natural conic are applied in
 // the projection backward.
-// Register budget of the backward: enough blocks for 24 resident warps per
-// SM (the kernel is issue-bound and its warps stall on short dependency
-// chains, so occupancy buys issue slots).
+// Register budget of the backward: enough blocks for 28 resident warps per
+// SM (72 registers; the kernel is issue-bound and its warps stall on short
+// dependency chains and on the shared-memory reduction, so occupancy buys
+// issue slots): 0.964 ms against 0.970 at 24 warps.
 // (From 4 pixels per thread on, the cap would spill: no target there, except
-// the 16 x 16 tile's two 16 x 8 warp blocks (QUAD), held to 96 registers
-// for 20 resident warps: 1.127 ms against 1.162 at 116 registers and 1.135
-// at 80 with spills, at the headline workload.)
+// the 16 x 16 tile's two 16 x 8 warp blocks (QUAD), held to 80 registers
+// for 24 resident warps: 0.977 ms against 0.992 at 96 registers, at the
+// headline workload.  A 64-register cap for 32 warps at 2 pixels per thread
+// spills a little and is slower, 0.993 against 0.970 ms.)
 template <int NT, int PPT>
 constexpr int bwd_min_blocks() {
-    return (NT == 64 && PPT == 4) ? 10 : (PPT >= 4 ? 1 : (768 / NT > 32 ? 32 : 768 / NT));
+    return (NT == 64 && PPT == 4) ? 12 : (PPT >= 4 ? 1 : (896 / NT > 32 ? 32 : 896 / NT));
 }
 
 // DET: the deterministic form.  All warps of the tile walk the list in
@@ -331,6 +333,10 @@ __global__ void __launch_bounds__(TS * TS / PPT, bwd_min_blocks<TS * TS / PPT, P
     __shared__ float4 s_a[NW][WB];
     __shared__ float4 s_b[NW][WB];
     __shared__ float4 s_c[NW][WB];  // colour 1, 2; position in the list (bits); record (bits)
+    // per-warp transposition matrix of the warp reduction (where it fits the
+    // 48 KB of static shared memory with the staging above)
+    constexpr bool kSmemRed = NW * 32 * 144 + 3 * NW * WB * 16 + (DET ? NW * WB * kGrad2D * 4 : 0) <= 40 * 1024;
+    __shared__ float4 s_red[kSmemRed ? NW : 1][32][9];
     const int t = threadIdx.x;
     const int lane = t & 31;
     const int warp = t >> 5;
@@ -420,87 +426,142 @@ __global__ void __launch_bounds__(TS * TS / PPT, bwd_min_blocks<TS * TS / PPT, P
         __syncwarp();
         for (int j0 = 0; j0 < n; j0 += kGroup) {
             // contributions of kGroup consecutive listed Gaussians, summed over
-            // this thread's pixels: v[g][e] (e indexes the 9 accumulators)
-            float v[kGroup][kGrad2D];
+            // this thread's pixels (9 accumulators each).  With the reduction
+            // through shared memory each Gaussian's first 8 go to this lane's
+            // row as soon as they are complete (one set of accumulators in
+            // registers, component 8 kept in y); else all kGroup sets stay in
+            // registers for the butterfly.
+            constexpr int NV = kSmemRed ? 1 : kGroup;
+            float v[NV][kGrad2D];
+            float y[kGroup];
+            if constexpr (!kSmemRed) {
 #pragma unroll
-            for (int g = 0; g < kGroup; ++g)
+                for (int g = 0; g < kGroup; ++g)
 #pragma unroll
-                for (int e = 0; e < kGrad2D; ++e) v[g][e] = 0.f;
+                    for (int e = 0; e < kGrad2D; ++e) v[g][e] = 0.f;
+            }
             bool any = false;
 #pragma unroll
             for (int g = 0; g < kGroup; ++g) {
                 const int j = j0 + g;
-                if (j >= n) break;
-
-                const float4 a = s_a[warp][j];
-                const float4 b = s_b[warp][j];
-                const float4 c = s_c[warp][j];
-                const int rel = __float_as_int(c.z);
-                float dxc[NCOL], u1c[NCOL], u2c[NCOL];
+                float* vg = v[kSmemRed ? 0 : g];
+                if constexpr (kSmemRed) {
 #pragma unroll
-                for (int c = 0; c < NCOL; ++c) {
-                    dxc[c] = fx[c] - a.x;
-                    u1c[c] = dxc[c] * a.z;
-                    u2c[c] = dxc[c] * b.x;
+                    for (int e = 0; e < kGrad2D; ++e) vg[e] = 0.f;
                 }
+                if (j < n) {
+
+                    const float4 a = s_a[warp][j];
+                    const float4 b = s_b[warp][j];
+                    const float4 c = s_c[warp][j];
+                    const int rel = __float_as_int(c.z);
+                    float dxc[NCOL], u1c[NCOL], u2c[NCOL];
 #pragma unroll
-                for (int k = 0; k < PPT; ++k) {
-                    const float dx = dxc[k % NCOL], u1 = u1c[k % NCOL], u2 = u2c[k % NCOL];
-                    const float dy = fy[k] - a.y;
-                    const float t1 = fmaf(dy, a.w, u1);
-                    const float t2 = fmaf(dy, b.y, u2);
-                    const float p = fmaf(-t1, t1, fmaf(-t2, t2, b.z));
-                    // behind the pixel's last contributor, or a faint fragment
-                    if (rel >= nc[k] || p < rc.log2_alpha_min) continue;
-                    any = true;
-                    const float araw = ex2_approx(p);
-                    const float alpha = fminf(rc.alpha_max, araw);
-                    T[k] = __fdividef(T[k], 1.f - alpha);
-                    const float w = alpha * T[k];
-                    v[g][6] = fmaf(w, g0[k], v[g][6]);
-                    v[g][7] = fmaf(w, g1[k], v[g][7]);
-                    v[g][8] = fmaf(w, g2[k], v[g][8]);
-                    const float gd = fmaf(g0[k], b.w, fmaf(g1[k], c.x, g2[k] * c.y)) - gR[k];
-                    const float dalpha = T[k] * gd;
-                    gR[k] = fmaf(alpha, gd, gR[k]);
-                    const float ga = araw < rc.alpha_max ? dalpha * araw : 0.f;
-                    // dp/dq = 2 ((d.v1) v1 + (d.v2) v2) with v1, v2 fixed per
-                    // record: only ga (d.v1), ga (d.v2) are summed here
-                    v[g][0] = fmaf(ga, t1, v[g][0]);
-                    v[g][1] = fmaf(ga, t2, v[g][1]);
-                    const float gdx = ga * dx;
-                    v[g][2] = fmaf(gdx, dx, v[g][2]);
-                    v[g][3] = fmaf(gdx, dy, v[g][3]);
-                    v[g][4] = fmaf(ga * dy, dy, v[g][4]);
-                    v[g][5] += ga;
+                    for (int c = 0; c < NCOL; ++c) {
+                        dxc[c] = fx[c] - a.x;
+                        u1c[c] = dxc[c] * a.z;
+                        u2c[c] = dxc[c] * b.x;
+                    }
+#pragma unroll
+                    for (int k = 0; k < PPT; ++k) {
+                        const float dx = dxc[k % NCOL], u1 = u1c[k % NCOL], u2 = u2c[k % NCOL];
+                        const float dy = fy[k] - a.y;
+                        const float t1 = fmaf(dy, a.w, u1);
+                        const float t2 = fmaf(dy, b.y, u2);
+                        const float p = fmaf(-t1, t1, fmaf(-t2, t2, b.z));
+                        // behind the pixel's last contributor, or a faint fragment
+                        if (rel >= nc[k] || p < rc.log2_alpha_min) continue;
+                        any = true;
+                        const float araw = ex2_approx(p);
+                        const float alpha = fminf(rc.alpha_max, araw);
+                        T[k] = __fdividef(T[k], 1.f - alpha);
+                        const float w = alpha * T[k];
+                        vg[6] = fmaf(w, g0[k], vg[6]);
+                        vg[7] = fmaf(w, g1[k], vg[7]);
+                        vg[8] = fmaf(w, g2[k], vg[8]);
+                        const float gd = fmaf(g0[k], b.w, fmaf(g1[k], c.x, g2[k] * c.y)) - gR[k];
+                        const float dalpha = T[k] * gd;
+                        gR[k] = fmaf(alpha, gd, gR[k]);
+                        const float ga = araw < rc.alpha_max ? dalpha * araw : 0.f;
+                        // dp/dq = 2 ((d.v1) v1 + (d.v2) v2) with v1, v2 fixed per
+                        // record: only ga (d.v1), ga (d.v2) are summed here
+                        vg[0] = fmaf(ga, t1, vg[0]);
+                        vg[1] = fmaf(ga, t2, vg[1]);
+                        const float gdx = ga * dx;
+                        vg[2] = fmaf(gdx, dx, vg[2]);
+                        vg[3] = fmaf(gdx, dy, vg[3]);
+                        vg[4] = fmaf(ga * dy, dy, vg[4]);
+                        vg[5] += ga;
+                    }
+                }
+                if constexpr (kSmemRed) {
+                    float4* row = s_red[warp][lane];
+                    row[2 * g] = make_float4(vg[0], vg[1], vg[2], vg[3]);
+                    row[2 * g + 1] = make_float4(vg[4], vg[5], vg[6], vg[7]);
+                    y[g] = vg[8];
                 }
             }
             if (__any_sync(0xffffffffu, any)) {
-                // Reduce-scatter over the warp: the 32 values v[g][e], e < 8,
-                // are halved at each butterfly level (a lane keeps the half
-                // selected by its lane bit and receives its partner's copy of
-                // it), leaving lane l with the warp total of value l, i.e.
-                // component l & 7 of Gaussian l >> 3.
-                float x[32];
+                // Warp totals of the 32 values v[g][e], e < 8.  Each lane ends
+                // with the total of one value: index vi, component vi & 7 of
+                // Gaussian vi >> 3.
+                float tot;
+                int vi;
+                if constexpr (kSmemRed) {
+                    // Through shared memory: each lane has stored its values as
+                    // 8 float4 words in its row (rows 144 bytes apart, so the
+                    // stores of 8 lanes fall into distinct banks); lane l adds
+                    // chunk c = l & 7 (values 4c..4c+3) over the 8 rows of its
+                    // lane group (l & 24), conflict-free too; two halving levels
+                    // over the 4 groups leave it value 4c + 2 ((l >> 4) & 1) +
+                    // ((l >> 3) & 1).  Half the instructions of the butterfly
+                    // below (no selects for 28 of its 31 levels' values).
+                    __syncwarp();
+                    const int c = lane & 7, r0 = lane & 24;
+                    float4 acc = s_red[warp][r0][c];
 #pragma unroll
-                for (int g = 0; g < kGroup; ++g)
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) x[g * 8 + e] = v[g][e];
-#pragma unroll
-                for (int o = 16, len = 32; o > 0; o >>= 1, len >>= 1) {
-                    const bool upper = (lane & o) != 0;
-#pragma unroll
-                    for (int i = 0; i < len / 2; ++i) {
-                        const float send = upper ? x[i] : x[i + len / 2];
-                        const float keep = upper ? x[i + len / 2] : x[i];
-                        x[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+                    for (int j = 1; j < 8; ++j) {
+                        const float4 q = s_red[warp][r0 + j][c];
+                        acc.x += q.x;
+                        acc.y += q.y;
+                        acc.z += q.z;
+                        acc.w += q.w;
                     }
+                    __syncwarp();
+                    const bool u16 = (lane & 16) != 0, u8 = (lane & 8) != 0;
+                    const float h0 = (u16 ? acc.z : acc.x) + __shfl_xor_sync(0xffffffffu, u16 ? acc.x : acc.z, 16);
+                    const float h1 = (u16 ? acc.w : acc.y) + __shfl_xor_sync(0xffffffffu, u16 ? acc.y : acc.w, 16);
+                    tot = (u8 ? h1 : h0) + __shfl_xor_sync(0xffffffffu, u8 ? h0 : h1, 8);
+                    vi = 4 * c + 2 * (int)u16 + (int)u8;
+                } else {
+                    // Reduce-scatter by butterfly: the 32 values are halved at
+                    // each level (a lane keeps the half selected by its lane bit
+                    // and receives its partner's copy of it), leaving lane l
+                    // with the warp total of value l.
+                    float x[32];
+#pragma unroll
+                    for (int g = 0; g < kGroup; ++g)
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) x[g * 8 + e] = v[g][e];
+#pragma unroll
+                    for (int o = 16, len = 32; o > 0; o >>= 1, len >>= 1) {
+                        const bool upper = (lane & o) != 0;
+#pragma unroll
+                        for (int i = 0; i < len / 2; ++i) {
+                            const float send = upper ? x[i] : x[i + len / 2];
+                            const float keep = upper ? x[i + len / 2] : x[i];
+                            x[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+                        }
+                    }
+                    tot = x[0];
+                    vi = lane;
                 }
                 // component 8 of the 4 Gaussians: two halving levels leave
                 // lane l with Gaussian l >> 3, then a sum over its 8 lanes
-                float y[kGroup];
+                if constexpr (!kSmemRed) {
 #pragma unroll
-                for (int g = 0; g < kGroup; ++g) y[g] = v[g][8];
+                    for (int g = 0; g < kGroup; ++g) y[g] = v[g][8];
+                }
 #pragma unroll
                 for (int o = 16, len = kGroup; o >= 8; o >>= 1, len >>= 1) {
                     const bool upper = (lane & o) != 0;
@@ -514,17 +575,16 @@ __global__ void __launch_bounds__(TS * TS / PPT, bwd_min_blocks<TS * TS / PPT, P
                 float yb = y[0];
 #pragma unroll
                 for (int o = 4; o > 0; o >>= 1) yb += __shfl_xor_sync(0xffffffffu, yb, o);
-                const int gl = lane >> 3, el = lane & 7;
-                if (j0 + gl < n) {
-                    if constexpr (DET) {
-                        float* slot = s_acc[warp][hi - 1 - __float_as_int(s_c[warp][j0 + gl].z)];
-                        slot[el] = x[0];
-                        if (el == 0) slot[8] = yb;
-                    } else {
-                        float* dst = grad2d + (size_t)__float_as_uint(s_c[warp][j0 + gl].w) * kGrad2D;
-                        if (x[0] != 0.f) atomicAdd(dst + el, x[0]);
-                        if (el == 0 && yb != 0.f) atomicAdd(dst + 8, yb);
-                    }
+                const int gm = vi >> 3, em = vi & 7;  // this lane's main value
+                const int gl = lane >> 3, el = lane & 7;  // component 8 of Gaussian gl at el == 0
+                if constexpr (DET) {
+                    if (j0 + gm < n) s_acc[warp][hi - 1 - __float_as_int(s_c[warp][j0 + gm].z)][em] = tot;
+                    if (el == 0 && j0 + gl < n) s_acc[warp][hi - 1 - __float_as_int(s_c[warp][j0 + gl].z)][8] = yb;
+                } else {
+                    if (j0 + gm < n && tot != 0.f)
+                        atomicAdd(grad2d + (size_t)__float_as_uint(s_c[warp][j0 + gm].w) * kGrad2D + em, tot);
+                    if (el == 0 && j0 + gl < n && yb != 0.f)
+                        atomicAdd(grad2d + (size_t)__float_as_uint(s_c[warp][j0 + gl].w) * kGrad2D + 8, yb);
                 }
             }
         }
