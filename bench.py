@@ -382,7 +382,8 @@ def run_b300(args, world, rank, local):
     if args.tile_size:
         shape = (args.tile_size, args.ppt, args.batch)
     else:
-        shape, tune_table = autotune(params, views, target, steps=3, device=local, storage=storage)
+        shape, tune_table = autotune(params, views, target, steps=3, device=local, storage=storage,
+                                     deterministic=int(args.deterministic))
     opt = WindowOptimizer(params, views, target, lr=LR, device=local, tile_size=shape[0],
                           ssim_lambda=args.ssim_lambda,
                           pixels_per_thread=shape[1], batch=shape[2], storage=storage,

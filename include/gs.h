@@ -115,7 +115,7 @@ typedef struct gs_config {
      * order, one 9-float partial per (tile, record) pair is written at the
      * pair's place in the tile lists, and each record's partials are added in
      * the order of its tiles; the default adds the totals with float atomics,
-     * whose order varies.  Costs 44 bytes of workspace per pair of capacity
+     * whose order varies.  Costs 56 bytes of workspace per pair of capacity
      * (gs_workspace_query includes them) and some speed. */
     int32_t deterministic;
 } gs_config;

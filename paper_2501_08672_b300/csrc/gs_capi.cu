@@ -215,7 +215,7 @@ int make_layout(gs_ctx* ctx, const gs_config& cfg, const gs_view* views, int n_v
     if (cfg.deterministic) {
         L.pair_rec = take(sizeof(uint32_t) * (size_t)cap);
         L.pair_inv = take(sizeof(uint32_t) * (size_t)cap);
-        L.pair_grad = take(sizeof(float) * kGrad2D * (size_t)cap);
+        L.pair_grad = take(sizeof(float) * kPairGradStride * (size_t)cap);
     }
     W.total = off;
     W.sorted_vals = sorted_buffer((int)T) ? L.pvals1 : W.pair_vals;

@@ -15,6 +15,9 @@ namespace gsb {
 constexpr int kMaxViews = GS_MAX_VIEWS;
 constexpr int kRecFloats = 12;   // projected record: 3 x float4
 constexpr int kGrad2D = 9;       // per-record 2D gradient
+// Row stride of the deterministic backward's per-pair partials: 9 values
+// padded to three 16-byte words.
+constexpr int kPairGradStride = 12;
 constexpr int kSsimRadius = 5;    // 11-tap SSIM window
 constexpr int kPoseTan4 = 12;     // per-record pose tangents: 12 x float4 (see k_pose_tangents)
 constexpr int kNormalVals = 28;   // per-view normal equations: 21 + 6 + 1
@@ -104,7 +107,7 @@ struct WsPtrs {
     // deterministic backward only (nullptr otherwise):
     uint32_t* pair_rec;      // [cap] record of each pair at its emission index
     uint32_t* pair_inv;      // [cap] emission index -> place in the tile lists (~0: listed in no tile)
-    float* pair_grad;        // [cap][9] per-(tile, record) 2D gradient partials, at the place in the tile lists
+    float* pair_grad;        // [cap][kPairGradStride] per-(tile, record) 2D gradient partials (9 used), at the place in the tile lists
     long long cap;
     int scan_blocks;
     float log2_alpha_min;    // -inf in exact mode (every tile of the box is reached)

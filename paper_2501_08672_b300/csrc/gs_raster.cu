@@ -303,11 +303,14 @@ constexpr int bwd_min_blocks() {
     return (NT == 64 && PPT == 4) ? 12 : (PPT >= 4 ? 1 : (896 / NT > 32 ? 32 : 896 / NT));
 }
 
-// DET: the deterministic form.  All warps of the tile walk the list in
-// lockstep batches from the tile's deepest contributor; each warp leaves its
-// per-record totals in shared memory, the block adds them in warp order and
-// writes one 9-float partial per listed record at its place in the tile
-// list (pair_grad), zeros where no pixel of the tile contributes; no atomics.
+// DET: the deterministic form.  All warps of the tile walk the list from the
+// tile's deepest contributor in windows of kDetWindow records (several
+// staging batches, so warps drift within a window and meet at its end); each
+// warp leaves its per-record totals in shared memory, the block adds them in
+// warp order and writes one 9-float partial per listed record at its place in
+// the tile list (pair_grad), zeros where no pixel of the tile contributes; no
+// atomics.
+constexpr int kDetWindow = 64;
 template <int TS, int PPT, int BATCH, bool DET>
 __global__ void __launch_bounds__(TS * TS / PPT, bwd_min_blocks<TS * TS / PPT, PPT>()) k_render_bwd(const __grid_constant__ BatchParam bp,
                                                               RenderConst rc,
@@ -335,7 +338,9 @@ __global__ void __launch_bounds__(TS * TS / PPT, bwd_min_blocks<TS * TS / PPT, P
     __shared__ float4 s_c[NW][WB];  // colour 1, 2; position in the list (bits); record (bits)
     // per-warp transposition matrix of the warp reduction (where it fits the
     // 48 KB of static shared memory with the staging above)
-    constexpr bool kSmemRed = NW * 32 * 144 + 3 * NW * WB * 16 + (DET ? NW * WB * kGrad2D * 4 : 0) <= 40 * 1024;
+    // records per deterministic window (a multiple of the staging batch)
+    constexpr int DW = DET ? (kDetWindow > WB ? kDetWindow : WB) : 1;
+    constexpr bool kSmemRed = NW * 32 * 144 + 3 * NW * WB * 16 + (DET ? NW * DW * kGrad2D * 4 : 0) <= 44 * 1024;
     __shared__ float4 s_red[kSmemRed ? NW : 1][32][9];
     const int t = threadIdx.x;
     const int lane = t & 31;
@@ -377,7 +382,7 @@ __global__ void __launch_bounds__(TS * TS / PPT, bwd_min_blocks<TS * TS / PPT, P
     const int wmax = min((int)__reduce_max_sync(0xffffffffu, mine), (int)(rg.y - rg.x));
     // deterministic form: per-warp totals of the batch's records, and the
     // tile's deepest contributor
-    __shared__ float s_acc[DET ? NW : 1][DET ? WB : 1][kGrad2D];
+    __shared__ float s_acc[DET ? NW : 1][DW][kGrad2D];
     __shared__ int s_wmax[DET ? NW : 1];
     int walk = wmax;
     if constexpr (DET) {
@@ -390,8 +395,12 @@ __global__ void __launch_bounds__(TS * TS / PPT, bwd_min_blocks<TS * TS / PPT, P
 
     for (int hi = walk; hi > 0; hi -= WB) {
         int n = 0;
+        // deterministic form: top of the current window and its last batch
+        const int wtop = walk - ((walk - hi) / DW) * DW;
+        const bool wlast = hi <= WB || wtop - (hi - WB) >= DW;
         if constexpr (DET) {
-            for (int i = lane; i < WB * kGrad2D; i += 32) (&s_acc[warp][0][0])[i] = 0.f;
+            if (hi == wtop)
+                for (int i = lane; i < DW * kGrad2D; i += 32) (&s_acc[warp][0][0])[i] = 0.f;
         }
         // a warp whose pixels all stop before this batch stages nothing
         const bool act = !DET || hi - WB < wmax;
@@ -578,8 +587,8 @@ __global__ void __launch_bounds__(TS * TS / PPT, bwd_min_blocks<TS * TS / PPT, P
                 const int gm = vi >> 3, em = vi & 7;  // this lane's main value
                 const int gl = lane >> 3, el = lane & 7;  // component 8 of Gaussian gl at el == 0
                 if constexpr (DET) {
-                    if (j0 + gm < n) s_acc[warp][hi - 1 - __float_as_int(s_c[warp][j0 + gm].z)][em] = tot;
-                    if (el == 0 && j0 + gl < n) s_acc[warp][hi - 1 - __float_as_int(s_c[warp][j0 + gl].z)][8] = yb;
+                    if (j0 + gm < n) s_acc[warp][wtop - 1 - __float_as_int(s_c[warp][j0 + gm].z)][em] = tot;
+                    if (el == 0 && j0 + gl < n) s_acc[warp][wtop - 1 - __float_as_int(s_c[warp][j0 + gl].z)][8] = yb;
                 } else {
                     if (j0 + gm < n && tot != 0.f)
                         atomicAdd(grad2d + (size_t)__float_as_uint(s_c[warp][j0 + gm].w) * kGrad2D + em, tot);
@@ -590,32 +599,41 @@ __global__ void __launch_bounds__(TS * TS / PPT, bwd_min_blocks<TS * TS / PPT, P
         }
         __syncwarp();
         if constexpr (DET) {
-            // the tile's partial of each record of the batch: warp totals
-            // added in warp order
-            __syncthreads();
-            for (int i = t; i < WB * kGrad2D; i += NT) {
-                const int slot = i / kGrad2D, c = i - slot * kGrad2D;
-                const int rel = hi - 1 - slot;
-                if (rel < 0) continue;
-                float v = 0.f;
+            if (wlast) {
+                // the tile's partial of each record of the window: warp totals
+                // added in warp order
+                __syncthreads();
+                for (int i = t; i < DW * kGrad2D; i += NT) {
+                    const int slot = i / kGrad2D, c = i - slot * kGrad2D;
+                    const int rel = wtop - 1 - slot;
+                    if (rel < 0) continue;
+                    float v = 0.f;
 #pragma unroll
-                for (int w2 = 0; w2 < NW; ++w2) v += s_acc[w2][slot][c];
-                pair_grad[(size_t)(rg.x + (uint32_t)rel) * kGrad2D + c] = v;
+                    for (int w2 = 0; w2 < NW; ++w2) v += s_acc[w2][slot][c];
+                    pair_grad[(size_t)(rg.x + (uint32_t)rel) * kPairGradStride + c] = v;
+                }
+                __syncthreads();
             }
-            __syncthreads();
         }
     }
     if constexpr (DET) {
         // records beyond every pixel's last contributor
-        const size_t end = (size_t)rg.y * kGrad2D;
-        for (size_t i = (size_t)(rg.x + (uint32_t)walk) * kGrad2D + t; i < end; i += NT) pair_grad[i] = 0.f;
+        const size_t end = (size_t)rg.y * kPairGradStride;
+        for (size_t i = (size_t)(rg.x + (uint32_t)walk) * kPairGradStride + t; i < end; i += NT) pair_grad[i] = 0.f;
     }
 }
 
 // Deterministic backward: a record's 2D gradient is the sum of its pairs'
-// partials in the order of its tiles.  Its pairs are contiguous in emission
-// order (records in depth order, k-th record at offsets[k]), and pair_inv
-// gives each one's place in the tile lists.  Every record is written.
+// partials.  Its pairs are contiguous in emission order (records in depth
+// order, k-th record at offsets[k]), and pair_inv gives each one's place in
+// the tile lists.  A warp takes 32 consecutive records; their pairs are one
+// contiguous emission range, which its lanes walk 32 positions at a time
+// (coalesced place reads, one partial row of three 16-byte words per lane),
+// each position's record found by a binary search over the lanes' offsets.
+// A segmented scan across the lanes (a fixed pattern of shuffles) sums each
+// record's positions within the 32, a carry takes a record across rounds,
+// and the lane at a record's last position writes it: the same order on
+// every run.  Records without pairs are written as zero.
 __global__ void __launch_bounds__(256) k_pair_grad_reduce(const uint32_t* __restrict__ order,
                                                           const unsigned long long* __restrict__ offsets,
                                                           const uint32_t* __restrict__ touched,
@@ -625,24 +643,77 @@ __global__ void __launch_bounds__(256) k_pair_grad_reduce(const uint32_t* __rest
                                                           float* __restrict__ grad2d) {
     pdl_wait();
     pdl_trigger();
-    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= M) return;
-    const uint32_t r = order[k];
+    const long long k0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) & ~31ll;
+    if (k0 >= M) return;  // whole warps: M is the same for all lanes
+    const int lane = threadIdx.x & 31;
+    const long long k = k0 + lane;
+    const bool live = k < M;
     unsigned long long n = n_dev[0];
     if (n > (unsigned long long)cap) n = (unsigned long long)cap;
-    const unsigned long long e0 = offsets[k], e1 = e0 + touched[r];
-    float acc[kGrad2D];
+    const uint32_t r = live ? order[k] : 0u;
+    const uint32_t cnt = live ? touched[r] : 0u;
+    const unsigned long long e0 = live ? offsets[k] : 0ull;
+    const unsigned long long wbase = __shfl_sync(0xffffffffu, e0, 0);
+    const uint32_t rel = live ? (uint32_t)(e0 - wbase) : 0xFFFFFFFFu;
+    const uint32_t wtotal = __reduce_max_sync(0xffffffffu, live ? rel + cnt : 0u);
+    if (live && cnt == 0)
+        for (int c = 0; c < kGrad2D; ++c) grad2d[(size_t)r * kGrad2D + c] = 0.f;
+    float carry[kGrad2D];
 #pragma unroll
-    for (int c = 0; c < kGrad2D; ++c) acc[c] = 0.f;
-    for (unsigned long long e = e0; e < e1 && e < n; ++e) {
-        const uint32_t p = pair_inv[e];
-        if (p == 0xFFFFFFFFu) continue;
-        const float* src = pair_grad + (size_t)p * kGrad2D;
+    for (int c = 0; c < kGrad2D; ++c) carry[c] = 0.f;
+    int carry_owner = -1;
+    for (uint32_t p0 = 0; p0 < wtotal; p0 += 32) {
+        const uint32_t pr = p0 + (uint32_t)lane;
+        // owner: the last lane whose first position is at or below pr
+        int o = 0;
 #pragma unroll
-        for (int c = 0; c < kGrad2D; ++c) acc[c] += src[c];
+        for (int st = 16; st >= 1; st >>= 1) {
+            const uint32_t oc = __shfl_sync(0xffffffffu, rel, o + st);
+            if (oc <= pr) o += st;
+        }
+        const bool in = pr < wtotal;
+        float v[kGrad2D];
+#pragma unroll
+        for (int c = 0; c < kGrad2D; ++c) v[c] = 0.f;
+        const unsigned long long e = wbase + pr;
+        if (in && e < n) {
+            const uint32_t p = pair_inv[e];
+            if (p != 0xFFFFFFFFu) {
+                const float4* row = reinterpret_cast<const float4*>(pair_grad + (size_t)p * kPairGradStride);
+                const float4 x = row[0], y = row[1], z = row[2];
+                v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+                v[4] = y.x; v[5] = y.y; v[6] = y.z; v[7] = y.w;
+                v[8] = z.x;
+            }
+        }
+        // segmented inclusive scan over the lanes, segments = owners
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int od = __shfl_up_sync(0xffffffffu, o, d);
+            const bool same = lane >= d && od == o;
+#pragma unroll
+            for (int c = 0; c < kGrad2D; ++c) {
+                const float u = __shfl_up_sync(0xffffffffu, v[c], d);
+                if (same) v[c] += u;
+            }
+        }
+        if (o == carry_owner) {
+#pragma unroll
+            for (int c = 0; c < kGrad2D; ++c) v[c] += carry[c];
+        }
+        // the record of the round's last lane continues into the next round
+        const int last_owner = __shfl_sync(0xffffffffu, o, 31);
+#pragma unroll
+        for (int c = 0; c < kGrad2D; ++c) carry[c] = __shfl_sync(0xffffffffu, v[c], 31);
+        carry_owner = last_owner;
+        const uint32_t ro = __shfl_sync(0xffffffffu, r, o);
+        const uint32_t rel_o = __shfl_sync(0xffffffffu, rel, o);
+        const uint32_t cnt_o = __shfl_sync(0xffffffffu, cnt, o);
+        if (in && pr == rel_o + cnt_o - 1u) {
+#pragma unroll
+            for (int c = 0; c < kGrad2D; ++c) grad2d[(size_t)ro * kGrad2D + c] = v[c];
+        }
     }
-#pragma unroll
-    for (int c = 0; c < kGrad2D; ++c) grad2d[(size_t)r * kGrad2D + c] = acc[c];
 }
 
 constexpr int kL1Threads = 256;

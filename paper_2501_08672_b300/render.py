@@ -641,17 +641,17 @@ RASTER_VARIANTS = [(8, 1, 128), (8, 1, 256), (8, 2, 128), (8, 2, 256),
                    (16, 8, 256), (32, 4, 256), (32, 8, 128), (32, 8, 256)]
 
 
-def autotune(params, views, targets, candidates=None, steps=3, device=0, storage=None, verbose=False):
+def autotune(params, views, targets, candidates=None, steps=3, device=0, storage=None, verbose=False, **cfg):
     """Picks the fastest (tile size, pixels per thread, batch) for this window
     and batch of views by timing whole optimisation iterations (projection to
     Adam, lr = 0 so the parameters do not move) with CUDA events on the
-    launching stream.  Returns (best, table) with table[(ts, ppt, batch)] =
-    ms per iteration."""
+    launching stream; cfg: further configuration (e.g. deterministic=1).
+    Returns (best, table) with table[(ts, ppt, batch)] = ms per iteration."""
     cands = candidates or RASTER_VARIANTS
     table = {}
     for ts, ppt, batch in cands:
         opt = WindowOptimizer(params, views, targets, lr=0.0, device=device, tile_size=ts, storage=storage,
-                              pixels_per_thread=ppt, batch=batch)
+                              pixels_per_thread=ppt, batch=batch, **cfg)
         opt.step(count=True)
         opt.step(count=False)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
