@@ -308,6 +308,51 @@ def test_deterministic_backward_is_bit_reproducible(ts, ppt, batch):
     assert float((outs[0] - outs[2]).norm() / outs[2].norm()) < 1e-5
 
 
+def _det_cases():
+    n = 4000
+    big = scenes.frustum_scene(n, seed=43)
+    big["log_scales"][:6] = np.log(np.array([[1.5, 1.2, 0.4]] * 6, np.float32))
+    big["means"][:6, 2] = np.linspace(3.0, 7.0, 6)
+    big["opacity"][:6] = -1.5
+    yield "huge splats", big, [scenes.identity_view(256, 192, 200.0, 0, n)]
+    p = scenes.frustum_scene(2000, seed=41)
+    away = scenes.lookat_view((0.0, 0.0, 0.0), (0.0, 0.0, -5.0), 48, 40, 40.0, 0, 2000, up=(0, -1, 0))
+    yield "culled view", p, [away, scenes.identity_view(48, 40, 40.0, 0, 2000)]
+    p = scenes.frustum_scene(1500, seed=42)
+    yield "1x17 and 33x2 images", p, [scenes.identity_view(1, 17, 10.5, 0, 1500),
+                                      scenes.identity_view(33, 2, 18.5, 0, 1500)]
+    n = 3000
+    p = scenes.frustum_scene(n, seed=40)
+    views = []
+    for k in range(64):
+        ang = 0.02 * (k - 32)
+        b = (k * 37) % 2000
+        views.append(scenes.lookat_view((2.0 * math.sin(ang), 0.1 * (k % 5), -1.0), (0.0, 0.0, 5.0),
+                                        24 + (k % 7) * 3, 16 + (k % 5) * 4, 30.0, b, b + 1000, up=(0, -1, 0)))
+    yield "64 views", p, views
+
+
+@pytest.mark.parametrize("case", [0, 1, 2, 3])
+def test_deterministic_backward_at_the_limits(case):
+    """The deterministic backward on the edge cases of the parity suite (a
+    few image-wide splats with lists of every tile, a view that culls every
+    Gaussian, 1- and 2-pixel-high images, 64 views): the same gradients as
+    the atomic backward to rounding, bit for bit on a second run."""
+    name, p, views = list(_det_cases())[case]
+    outs = []
+    for det in (1, 1, 0):
+        win, r = gpu_forward(p, views, deterministic=det)
+        w = torch.randn(r.rgb.numel(), device="cuda", generator=torch.Generator(device="cuda").manual_seed(5))
+        win.gflat.fill_(float("nan"))
+        r.backward(win.struct(), w, grads=win.grad_tensors(), want_pose=True)
+        torch.cuda.synchronize()
+        outs.append(torch.cat([win.gflat, r.dL_dpose]).clone())
+    assert torch.equal(outs[0], outs[1]), name
+    assert bool(torch.isfinite(outs[0]).all()), name
+    ref = outs[2].norm()
+    assert float((outs[0] - outs[2]).norm() / ref.clamp_min(1e-30)) < 1e-5, name
+
+
 def test_deterministic_window_iterations_are_bit_reproducible():
     """Whole graph-replayed window iterations (projection, binning, L1 in the
     compositing, backward, Adam) in deterministic mode leave the same
