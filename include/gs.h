@@ -103,10 +103,12 @@ typedef struct gs_config {
     float z_near;      /* Gaussians with camera depth <= z_near are culled, m [0.2] */
     float bg[3];       /* background colour [0, 0, 0] */
     /* Launch shape of the compositing kernels (0 = default).  pixels_per_thread:
-     * 1, 2 for tile 8; 1, 2, 4, 8 for tile 16; 4, 8 for tile 32 [2, 4, 4];
+     * 1, 2 for tile 8; 1, 2, 4, 8 for tile 16; 4, 8 for tile 32 [2, 2, 4];
      * batch: records staged per shared-memory batch, 128 or 256, at least the
-     * threads per tile (tile^2 / pixels_per_thread) [256].  The result does not
-     * depend on them; gs_tune-style autotuning picks the fastest. */
+     * threads per tile (tile^2 / pixels_per_thread) [128 up to 128 threads per
+     * tile, else 256].  The result does not depend on them; the defaults are
+     * the fastest measured at the headline workload, and render.autotune
+     * times the compiled shapes for a given workload. */
     int32_t pixels_per_thread;
     int32_t batch;
     /* 1: gs_render_bwd sums every gradient in a fixed order, so the same
