@@ -56,8 +56,8 @@ FP32_LANES = 128
 # kernel source they were taken on (sha256 prefix of gs_raster.cu up to the L1
 # kernels, which holds both compositing kernels) and the launch shape;
 # otherwise the roofline reports traffic null.
-TRAFFIC = {"raster_fwd": ("db8b113e29680f22", (16, 2, 128), 181.7e6),
-           "raster_bwd": ("db8b113e29680f22", (16, 2, 128), 237.8e6)}
+TRAFFIC = {"raster_fwd": ("c44f4d8f4e06127b", (16, 2, 128), 181.6e6),
+           "raster_bwd": ("c44f4d8f4e06127b", (16, 2, 128), 237.3e6)}
 
 
 def raster_source_hash():
