@@ -309,10 +309,11 @@ GS_API int gs_render_bwd(gs_ctx* ctx, const gs_gaussians* g, const gs_view* view
 
 /* gs_render_bwd, with the parameter gradients added to what grads already
  * holds instead of overwriting it (every entry of every group, zero for
- * Gaussians no view of this call sees), so that the views of one window
- * iteration can be back-propagated in several calls (more views than
- * GS_MAX_VIEWS, or one view per launch sequence) and their gradients summed
- * before one Adam step.  The gradients of the first call's Gaussians must be
+ * Gaussians no view of this call sees).  The window optimisation of
+ * Sec. II-B.2 takes one Adam step on the gradient of a loss summed over the
+ * keyframes (Eq. gaussian_optimization over the window's images); this form
+ * lets that gradient be formed over several calls (more views than
+ * GS_MAX_VIEWS, or one view per launch sequence) before the one Adam step.  The gradients of the first call's Gaussians must be
  * cleared (or written by gs_render_bwd) first.  dL_dpose_dev, when non-NULL,
  * is written per view as in gs_render_bwd.  grads is required.
  * Errors: GS_ERR_INVALID_ARG, GS_ERR_CUDA. */
