@@ -1009,6 +1009,54 @@ def test_odometry_view_pose_gradient_sampled(orc):
     sampled_parity(orc, p, [v], 16, 64, seed=31, check_params=False, pixels_per_thread=2, batch=128)
 
 
+def test_pose_gradient_matches_central_differences_of_the_gpu_render():
+    """Configuration 5's pose-only backward against central differences of
+    the CUDA path's own rendering, T_CW <- Exp(+-h e_k) T_CW, for a smooth
+    loss L = sum w . I in exact mode (alpha_min = 0, alpha_max = 1, T_min = 0:
+    no threshold decision, so the image is smooth in the pose).  FP32
+    rendering bounds the agreement (the loss is summed in FP64 on the host)."""
+    from paper_2501_08672_b300.render import apply_left
+    n = 600
+    p = scenes.frustum_scene(n, seed=52)
+    p["opacity"] = np.clip(p["opacity"], -3, 2).astype(np.float32)
+    v = scenes.lookat_view((0.2, -0.1, -0.3), (0.0, 0.0, 5.0), 96, 72, 80.0, 0, n, up=(0, -1, 0))
+    cfg = dict(alpha_min=0.0, alpha_max=1.0, T_min=0.0)
+    win = GaussianWindow(p, 0)
+    r = Renderer([v], 0, 16, **cfg)
+    g = win.struct()
+    w = torch.randn(3 * 96 * 72, device="cuda", generator=torch.Generator(device="cuda").manual_seed(9))
+
+    def loss(view):
+        r.set_views([view])
+        r.forward(g)
+        torch.cuda.synchronize()
+        return float((r.rgb.double() * w.double()).sum().item())
+
+    loss(v)
+    r.pose_grad(g, w)
+    torch.cuda.synchronize()
+    grad = r.dL_dpose.double().cpu().numpy()
+    def central(h):
+        fd = np.zeros(6)
+        for k in range(6):
+            e = np.zeros(6)
+            e[k] = h
+            fd[k] = (loss(apply_left(v, e)) - loss(apply_left(v, -e))) / (2 * h)
+        return fd
+
+    # Richardson extrapolation of two step sizes removes the h^2 term
+    d1, d2 = central(4e-3), central(2e-3)
+    fd = (4.0 * d2 - d1) / 3.0
+    err = np.linalg.norm(grad - fd) / np.linalg.norm(fd)
+    err_plain = np.linalg.norm(grad - d2) / np.linalg.norm(d2)
+    parity_log.report("pose gradient against central differences of the CUDA render (exact mode)",
+                      ["analytic             %s" % np.array2string(grad, precision=4),
+                       "central, h = 2e-3    %s" % np.array2string(d2, precision=4),
+                       "Richardson (4e-3, 2e-3) %s" % np.array2string(fd, precision=4),
+                       "relative L2 error %.2e (h = 2e-3 alone: %.2e)" % (err, err_plain)])
+    assert err < 5e-3, (grad, fd)
+
+
 def test_adam_device_step_matches_host_step():
     rng = np.random.default_rng(17)
     n = 4099
