@@ -193,7 +193,7 @@ typedef struct gs_ws_layout {
     size_t rects;         /* int32[M][4]: x0|y0<<16, x1|y1<<16, first tile id of the view, tiles_x */
     size_t tiles_touched; /* uint32[M] */
     size_t depth_keys;    /* uint32[M] low words of the 64-bit depth keys, record order (two buffers) */
-    size_t depth_hi;      /* uint32[M] high words of the 64-bit depth keys (sorted in place by gs_bin) */
+    size_t depth_hi;      /* uint32[M] high words of the 64-bit depth keys (overwritten by gs_bin's sort) */
     size_t depth_vals;    /* uint32[M] record indices (two buffers) */
     size_t pair_offsets;  /* uint64[M] */
     size_t pair_keys;     /* uint32[max_pairs] x 2 */
@@ -201,7 +201,7 @@ typedef struct gs_ws_layout {
     size_t sorted_vals;   /* the buffer holding the sorted record index per pair */
     size_t tile_ranges;   /* uint32[T][2] [start, end) into sorted_vals */
     size_t grad2d;        /* float[M][9] per-record 2D gradients */
-    size_t counters;      /* uint64[8]: [0] pairs needed */
+    size_t counters;      /* uint64[8]: [0] pairs needed; [1..3] the projection's depth-key range and its generation */
     size_t total;         /* bytes */
     int64_t n_records;    /* M */
     int32_t n_tiles;      /* T */

@@ -102,7 +102,7 @@ struct WsPtrs {
     uint32_t* okeys[2];      // [T] tile-order keys
     uint32_t* ovals[2];      // [T] tiles, longest list first (buffer 1 after the sort)
     float* grad2d;           // [M][9]
-    unsigned long long* counters; // [8]
+    unsigned long long* counters; // [8]: [0] pairs needed, [1..3] depth-key range (kCtrRange*)
     float* partials;         // reduction scratch
     // deterministic backward only (nullptr otherwise):
     uint32_t* pair_rec;      // [cap] record of each pair at its emission index
@@ -113,6 +113,49 @@ struct WsPtrs {
     float log2_alpha_min;    // -inf in exact mode (every tile of the box is reached)
     int sorted_buf;          // which pvals buffer holds the sorted pairs
 };
+
+// ---- depth-key range ------------------------------------------------------
+//
+// The projection records the range [kmin, kmax] of the valid high depth-key
+// words (culled records carry 0xFFFFFFFF) in counters[kCtrRangeMax] and
+// counters[kCtrRangeMin] by 64-bit atomicMax, with the projection's
+// generation counters[kCtrRangeGen] in the high word (kmax, and ~kmin, in the
+// low word), so no reset is needed: a value of an older generation loses to
+// any of the current one.  Binning advances the generation once its depth
+// sort is done.  The depth sort orders records by the 24-bit map of a key,
+// (key - kmin) >> s with the least s that keeps the range below 0xFFFFFF, and
+// culled keys at 0xFFFFFF; the map is monotone, so equal mapped keys form
+// runs that the fix-up orders by the full key.  When the slots do not carry
+// the current generation (binning again without a new projection, or a
+// workspace never projected into) the map falls back to key >> 8: still
+// monotone, with longer runs.
+constexpr int kCtrRangeMax = 1;
+constexpr int kCtrRangeMin = 2;
+constexpr int kCtrRangeGen = 3;
+
+struct KeyMap {
+    uint32_t kmin;
+    int s;
+};
+
+__device__ __forceinline__ KeyMap load_key_map(const unsigned long long* counters) {
+    const unsigned long long hi = counters[kCtrRangeMax], lo = counters[kCtrRangeMin];
+    const uint32_t gen = (uint32_t)counters[kCtrRangeGen];
+    KeyMap m{0u, 8};
+    if ((uint32_t)(hi >> 32) == gen && (uint32_t)(lo >> 32) == gen) {
+        const uint32_t kmax = (uint32_t)hi, kmin = ~(uint32_t)lo;
+        const uint32_t r = kmax >= kmin ? kmax - kmin : 0u;
+        int s = 0;
+        while ((r >> s) > 0xFFFFFEu) ++s;
+        m.kmin = kmin;
+        m.s = s;
+    }
+    return m;
+}
+
+__device__ __forceinline__ uint32_t map_key(uint32_t k, const KeyMap& m) {
+    return k == 0xFFFFFFFFu ? 0xFFFFFFu : (k - m.kmin) >> m.s;
+}
 
 // ---- small device helpers --------------------------------------------------
 

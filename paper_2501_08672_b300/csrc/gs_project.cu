@@ -244,6 +244,14 @@ __global__ void __launch_bounds__(256) k_project(const __grid_constant__ BatchPa
                                                  RenderConst rc, WsPtrs ws) {
     pdl_wait();
     pdl_trigger();
+    // the block's range of valid high depth-key words, and its warps done
+    __shared__ uint32_t s_kmin, s_kmax, s_warps;
+    if (threadIdx.x == 0) {
+        s_kmin = 0xFFFFFFFFu;
+        s_kmax = 0u;
+        s_warps = 0u;
+    }
+    __syncthreads();
     const ViewParam& V = bp.v[blockIdx.y];
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long cnt = V.g_end - V.g_begin;
@@ -347,7 +355,40 @@ __global__ void __launch_bounds__(256) k_project(const __grid_constant__ BatchPa
     ws.tiles_touched[r] = touched;
     ws.dkeys[0][r] = key_lo;
     ws.dhi[r] = key_hi;
-    ws.dvals[0][r] = (uint32_t)r;
+    ws.dvals[1][r] = (uint32_t)r;  // the depth sort's input values
+
+    // Range of the valid keys: warp minimum and maximum over the warp's live
+    // lanes (those with k < cnt, all of which reach this point), block-wide by
+    // shared atomics; the block's last live warp publishes it with the
+    // current generation (see kCtrRangeGen).
+    const long long wbase = k - (threadIdx.x & 31);
+    const long long nl = cnt - wbase;
+    const uint32_t live = nl >= 32 ? 0xFFFFFFFFu : (1u << nl) - 1u;
+    const bool valid = key_hi != 0xFFFFFFFFu;
+    const uint32_t wmin = __reduce_min_sync(live, valid ? key_hi : 0xFFFFFFFFu);
+    const uint32_t wmax = __reduce_max_sync(live, valid ? key_hi : 0u);
+    if ((threadIdx.x & 31) == 0) {
+        if (wmin <= wmax) {
+            atomicMin(&s_kmin, wmin);
+            atomicMax(&s_kmax, wmax);
+        }
+        __threadfence_block();
+        const long long bl = cnt - (long long)blockIdx.x * blockDim.x;  // live threads of the block
+        const uint32_t nw = (uint32_t)((bl >= (long long)blockDim.x ? (long long)blockDim.x : bl) + 31) / 32;
+        if (atomicAdd(&s_warps, 1u) + 1u == nw) {
+            __threadfence_block();
+            const uint32_t bmin = atomicOr(&s_kmin, 0u), bmax = atomicOr(&s_kmax, 0u);
+            if (bmin <= bmax) {
+                // the slots only grow, so a block whose values do not exceed
+                // what it reads now can skip its atomic
+                const unsigned long long gen = (unsigned long long)(uint32_t)ws.counters[kCtrRangeGen] << 32;
+                const unsigned long long vmax = gen | bmax, vmin = gen | (unsigned long long)(~bmin);
+                volatile const unsigned long long* c = ws.counters;
+                if (c[kCtrRangeMax] < vmax) atomicMax(&ws.counters[kCtrRangeMax], vmax);
+                if (c[kCtrRangeMin] < vmin) atomicMax(&ws.counters[kCtrRangeMin], vmin);
+            }
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------

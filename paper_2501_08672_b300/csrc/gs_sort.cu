@@ -58,15 +58,18 @@ __device__ __forceinline__ uint32_t lane_lt_mask() {
 
 // Also zeroes `nzero` 64-bit words at `zero` (block 0): the look-back flags
 // and ticket of the scan that follows, without a separate memset.
+template <bool MAPPED>
 __global__ void __launch_bounds__(kRadixThreads) k_radix_upsweep(const uint32_t* __restrict__ keys,
                                                                  unsigned long long n_host,
                                                                  const unsigned long long* n_dev,
                                                                  int shift, int bits,
                                                                  uint32_t* __restrict__ hist,
-                                                                 unsigned long long* __restrict__ zero, int nzero) {
+                                                                 unsigned long long* __restrict__ zero, int nzero,
+                                                                 const unsigned long long* __restrict__ key_range) {
     pdl_wait();
     pdl_trigger();
     __shared__ uint32_t wh[kRadixWarps][256];
+    const KeyMap km = MAPPED ? load_key_map(key_range) : KeyMap{0u, 0};
     const int t = threadIdx.x, w = t >> 5;
     if (blockIdx.x == 0)
         for (int i = t; i < nzero; i += kRadixThreads) zero[i] = 0ull;
@@ -81,6 +84,7 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_upsweep(const uint32_t*
     for (int k = 0; k < kRItems; ++k) {
         const unsigned long long i = base + (unsigned long long)k * kRadixThreads + t;
         kk[k] = i < n ? keys[i] : 0u;
+        if (MAPPED) kk[k] = map_key(kk[k], km);
     }
 #pragma unroll
     for (int k = 0; k < kRItems; ++k) {
@@ -102,10 +106,11 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_upsweep(const uint32_t*
 // per digit and over the digits then places every key stably within the
 // tile, the tile is staged digit-sorted in shared memory and written out in
 // runs of consecutive positions.
+template <bool MAPPED>
 __global__ void __launch_bounds__(kRadixThreads, 3) k_radix_downsweep(
     const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
     uint32_t* __restrict__ vout, unsigned long long n_host, const unsigned long long* n_dev, int shift,
-    int bits, const uint32_t* __restrict__ hist) {
+    int bits, const uint32_t* __restrict__ hist, const unsigned long long* __restrict__ key_range) {
     pdl_wait();
     pdl_trigger();
     constexpr int kSlice = kRTile / kRadixWarps;  // 512 keys per warp
@@ -122,6 +127,9 @@ __global__ void __launch_bounds__(kRadixThreads, 3) k_radix_downsweep(
     const int count = (int)(n - base < (unsigned long long)kRTile ? n - base : (unsigned long long)kRTile);
     const uint32_t mask = (1u << bits) - 1u;
     const uint32_t lt = lane_lt_mask();
+    // digits of the mapped key (depth sort) or of the key itself
+    const KeyMap km = MAPPED ? load_key_map(key_range) : KeyMap{0u, 0};
+    auto digit = [&](uint32_t k) { return ((MAPPED ? map_key(k, km) : k) >> shift) & mask; };
 #pragma unroll
     for (int ww = 0; ww < kRadixWarps; ++ww) s_wc[ww][t] = 0u;
     s_gbase[t] = hist[(size_t)t * gridDim.x + blockIdx.x];
@@ -137,7 +145,7 @@ __global__ void __launch_bounds__(kRadixThreads, 3) k_radix_downsweep(
 #pragma unroll
     for (int k = 0; k < kRItems; ++k) {
         const bool valid = w * kSlice + k * 32 + lane < count;
-        const uint32_t d = (key[k] >> shift) & mask;
+        const uint32_t d = digit(key[k]);
         // lanes holding the same digit: one ballot per digit bit (an invalid
         // lane is its own group)
         const uint32_t vm = __ballot_sync(0xffffffffu, valid);
@@ -185,7 +193,7 @@ __global__ void __launch_bounds__(kRadixThreads, 3) k_radix_downsweep(
 #pragma unroll
     for (int k = 0; k < kRItems; ++k) {
         if (w * kSlice + k * 32 + lane < count) {
-            const uint32_t d = (key[k] >> shift) & mask;
+            const uint32_t d = digit(key[k]);
             const uint32_t pos = s_start[d] + s_wc[w][d] + rank[k];
             s_keys[pos] = key[k];
             s_vals[pos] = val[k];
@@ -195,7 +203,7 @@ __global__ void __launch_bounds__(kRadixThreads, 3) k_radix_downsweep(
     // consecutive threads write consecutive positions of each digit run
     for (int i = t; i < count; i += kRadixThreads) {
         const uint32_t k = s_keys[i];
-        const uint32_t d = (k >> shift) & mask;
+        const uint32_t d = digit(k);
         const uint32_t pos = s_gbase[d] + (uint32_t)i - s_start[d];
         if (pos < n) {  // always true for a consistent histogram; guards the write
             kout[pos] = k;
@@ -347,79 +355,97 @@ __global__ void __launch_bounds__(1024) k_u32_scan_single(uint32_t* __restrict__
     }
 }
 
-// Depth order, second step.  The records are sorted stably by the high word
-// of their 64-bit depth key, so records with equal high words sit in runs in
-// record order; each run is put in (low word, record) order here, which is
-// the order of the full 64-bit key with ties by record index.  One thread
-// per run: insertion sort for short runs (the common case: coplanar splats),
-// heapsort beyond kFixupInsertion (a long run only costs time).  Culled
-// records (high word 0xFFFFFFFF, never listed) are left alone.
+// Depth order, second step.  The records are sorted stably by the 24-bit map
+// of the high word of their 64-bit depth key (see KeyMap), so records with
+// equal mapped keys sit in runs in record order; each run is put in (high
+// word, low word, record) order here, which is the order of the full 64-bit
+// key with ties by record index (the map is monotone).  One thread per run:
+// insertion sort for short runs (the common case: a run spans 2^s key values
+// at most), heapsort beyond kFixupInsertion (a long run only costs time).
+// The high words move with the records.  Culled records (mapped key
+// 0xFFFFFF, never listed) are left alone.
 constexpr long long kFixupInsertion = 48;
 
-__device__ __forceinline__ unsigned long long depth_lo_key(const uint32_t* lo, uint32_t v) {
-    return ((unsigned long long)lo[v] << 32) | v;
+struct DepthKey {
+    uint32_t h;
+    unsigned long long l;  // low word, record
+    __device__ __forceinline__ bool operator>(const DepthKey& o) const { return h != o.h ? h > o.h : l > o.l; }
+};
+
+__device__ __forceinline__ DepthKey depth_key(const uint32_t* hi, const uint32_t* a, const uint32_t* lo, long long i) {
+    const uint32_t v = a[i];
+    return DepthKey{hi[i], ((unsigned long long)lo[v] << 32) | v};
 }
 
-__device__ void heap_sift(uint32_t* a, long long root, long long n, const uint32_t* lo) {
-    const uint32_t v = a[root];
-    const unsigned long long kv = depth_lo_key(lo, v);
+__device__ void heap_sift(uint32_t* hi, uint32_t* a, long long root, long long n, const uint32_t* lo) {
+    const uint32_t h = hi[root], v = a[root];
+    const DepthKey kv = depth_key(hi, a, lo, root);
     long long i = root;
     while (true) {
         long long c = 2 * i + 1;
         if (c >= n) break;
-        unsigned long long kc = depth_lo_key(lo, a[c]);
+        DepthKey kc = depth_key(hi, a, lo, c);
         if (c + 1 < n) {
-            const unsigned long long kr = depth_lo_key(lo, a[c + 1]);
+            const DepthKey kr = depth_key(hi, a, lo, c + 1);
             if (kr > kc) {
                 ++c;
                 kc = kr;
             }
         }
-        if (kc <= kv) break;
+        if (!(kc > kv)) break;
+        hi[i] = hi[c];
         a[i] = a[c];
         i = c;
     }
+    hi[i] = h;
     a[i] = v;
 }
 
 // Block 0 also zeroes `nzero` 64-bit words at `zero`: the look-back flags and
 // ticket of the offsets scan that follows.
-__global__ void __launch_bounds__(256) k_depth_fixup(const uint32_t* __restrict__ hi, uint32_t* __restrict__ vals,
+__global__ void __launch_bounds__(256) k_depth_fixup(uint32_t* __restrict__ hi, uint32_t* __restrict__ vals,
                                                      const uint32_t* __restrict__ lo, long long M,
-                                                     unsigned long long* __restrict__ zero, int nzero) {
+                                                     unsigned long long* __restrict__ zero, int nzero,
+                                                     const unsigned long long* __restrict__ key_range) {
     pdl_wait();
     pdl_trigger();
     if (blockIdx.x == 0)
         for (int i = threadIdx.x; i < nzero; i += blockDim.x) zero[i] = 0ull;
     const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= M) return;
-    const uint32_t h = hi[j];
-    if (h == 0xFFFFFFFFu) return;
-    if (j > 0 && hi[j - 1] == h) return;      // not the first of its run
-    if (j + 1 >= M || hi[j + 1] != h) return;  // a run of one
+    const KeyMap km = load_key_map(key_range);
+    const uint32_t h = map_key(hi[j], km);
+    if (h == 0xFFFFFFu) return;
+    if (j > 0 && map_key(hi[j - 1], km) == h) return;      // not the first of its run
+    if (j + 1 >= M || map_key(hi[j + 1], km) != h) return;  // a run of one
     long long e = j + 2;
-    while (e < M && hi[e] == h) ++e;
+    while (e < M && map_key(hi[e], km) == h) ++e;
     uint32_t* a = vals + j;
+    uint32_t* ha = hi + j;
     const long long n = e - j;
     if (n <= kFixupInsertion) {
         for (long long i = 1; i < n; ++i) {
-            const uint32_t v = a[i];
-            const unsigned long long kv = depth_lo_key(lo, v);
+            const uint32_t hv = ha[i], v = a[i];
+            const DepthKey kv = depth_key(ha, a, lo, i);
             long long k = i - 1;
-            while (k >= 0 && depth_lo_key(lo, a[k]) > kv) {
+            while (k >= 0 && depth_key(ha, a, lo, k) > kv) {
+                ha[k + 1] = ha[k];
                 a[k + 1] = a[k];
                 --k;
             }
+            ha[k + 1] = hv;
             a[k + 1] = v;
         }
         return;
     }
-    for (long long r = n / 2 - 1; r >= 0; --r) heap_sift(a, r, n, lo);
+    for (long long r = n / 2 - 1; r >= 0; --r) heap_sift(ha, a, r, n, lo);
     for (long long end = n - 1; end > 0; --end) {
-        const uint32_t t = a[0];
+        const uint32_t th = ha[0], t = a[0];
+        ha[0] = ha[end];
         a[0] = a[end];
+        ha[end] = th;
         a[end] = t;
-        heap_sift(a, 0, end, lo);
+        heap_sift(ha, a, 0, end, lo);
     }
 }
 
@@ -468,6 +494,8 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_offsets(const uint32_t* _
     __shared__ unsigned int s_chunk;
     __shared__ unsigned long long s_prefix;
     const int t = threadIdx.x, lane = t & 31;
+    // the depth sort is done: the next projection opens a new key-range generation
+    if (blockIdx.x == 0 && t == 0) counters[kCtrRangeGen] += 1ull;
     if (t == 0) s_chunk = atomicAdd(reinterpret_cast<unsigned int*>(flags + nchunks), 1u);
     __syncthreads();
     const long long chunk = s_chunk;
@@ -859,11 +887,13 @@ int radix_blocks(unsigned long long n_host) {
     return (int)((n_host + kRTile - 1) / kRTile);
 }
 
-// Sorts (key, value) pairs on the low key_bits bits of the keys, ping-ponging
-// between buffer 0 and 1; *result_buf receives the buffer holding the result.
+// Sorts (key, value) pairs on the low key_bits bits of the keys (of their
+// depth-key map when key_range is set), ping-ponging between buffer 0 and 1;
+// *result_buf receives the buffer holding the result.
 cudaError_t radix_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, const WsPtrs& ws,
                        unsigned long long n_host, const unsigned long long* n_dev, int key_bits,
-                       int* result_buf, unsigned int* status, cudaStream_t s, Prof& pf) {
+                       int* result_buf, unsigned int* status, cudaStream_t s, Prof& pf,
+                       const unsigned long long* key_range = nullptr) {
     const int passes = key_bits <= 0 ? 0 : (key_bits + 7) / 8;
     const int dbits = passes ? (key_bits + passes - 1) / passes : 0;
     const int nblk = radix_blocks(n_host);
@@ -879,8 +909,12 @@ cudaError_t radix_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, c
         // flags of the nparts chunks, then the ticket, zeroed by the upsweep for the look-back scan
         unsigned long long* flags = reinterpret_cast<unsigned long long*>(ws.hist_part);
         const bool single = nh <= kU32SingleScanMax;
-        pdl_launch(k_radix_upsweep, nblk, kRadixThreads, 0, s, kin, n_host, n_dev, shift, bits, ws.hist, flags,
-                                                       single ? 0 : nparts + 1);
+        if (key_range)
+            pdl_launch(k_radix_upsweep<true>, nblk, kRadixThreads, 0, s, kin, n_host, n_dev, shift, bits, ws.hist,
+                       flags, single ? 0 : nparts + 1, key_range);
+        else
+            pdl_launch(k_radix_upsweep<false>, nblk, kRadixThreads, 0, s, kin, n_host, n_dev, shift, bits, ws.hist,
+                       flags, single ? 0 : nparts + 1, key_range);
         if (single) {
             pdl_launch(k_u32_scan_single, 1, 1024, 0, s, ws.hist, nh);
             pf.count(3);
@@ -889,7 +923,12 @@ cudaError_t radix_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, c
             pdl_launch(k_u32_scan_lookback, nparts, 1024, 0, s, ws.hist, nh, flags,
                                                         reinterpret_cast<unsigned int*>(flags + nparts), status);
         }
-        pdl_launch(k_radix_downsweep, nblk, kRadixThreads, 0, s, kin, vin, kout, vout, n_host, n_dev, shift, bits, ws.hist);
+        if (key_range)
+            pdl_launch(k_radix_downsweep<true>, nblk, kRadixThreads, 0, s, kin, vin, kout, vout, n_host, n_dev, shift,
+                       bits, ws.hist, key_range);
+        else
+            pdl_launch(k_radix_downsweep<false>, nblk, kRadixThreads, 0, s, kin, vin, kout, vout, n_host, n_dev, shift,
+                       bits, ws.hist, key_range);
         uint32_t* tk = kin; kin = kout; kout = tk;
         uint32_t* tv = vin; vin = vout; vout = tv;
     }
@@ -905,19 +944,22 @@ cudaError_t launch_bin(const BatchParam& bp, WsPtrs& ws, unsigned int* status,
     cudaError_t e;
     if (M <= 0) return cudaSuccess;
     // 1. front-to-back order of records by the 64-bit double-float depth key:
-    //    a stable radix sort on the high word (4 passes, in place in dhi /
-    //    dvals[0]), then the runs of equal high words by (low word, record)
+    //    a stable radix sort on the 24-bit map of the high word (3 passes from
+    //    dhi / dvals[1], the record indices the projection wrote, to dkeys[1] /
+    //    dvals[0]), then the runs of equal mapped keys by (high word, low
+    //    word, record)
     int pi = pf.begin(GS_KF_DEPTH_SORT, s, 1);  // the fix-up; radix_sort counts its own launches
     int dbuf = 0;
-    e = radix_sort(ws.dhi, ws.dvals[0], ws.dkeys[1], ws.dvals[1], ws, (unsigned long long)M, nullptr, 32, &dbuf,
-                   status, s, pf);
+    const unsigned long long* key_range = ws.counters;
+    e = radix_sort(ws.dhi, ws.dvals[1], ws.dkeys[1], ws.dvals[0], ws, (unsigned long long)M, nullptr, 24, &dbuf,
+                   status, s, pf, key_range);
     if (e != cudaSuccess) return e;
-    uint32_t* sorted_hi = dbuf ? ws.dkeys[1] : ws.dhi;
+    if (dbuf != 1) return cudaErrorInvalidValue;  // three passes end in the second buffers
     const int nb = (int)((M + kScanChunk - 1) / kScanChunk);
-    pdl_launch(k_depth_fixup, (unsigned)((M + 255) / 256), 256, 0, s, sorted_hi, ws.dvals[dbuf], ws.dkeys[0], M,
-               ws.scan_part, nb + 1);
+    pdl_launch(k_depth_fixup, (unsigned)((M + 255) / 256), 256, 0, s, ws.dkeys[1], ws.dvals[0], ws.dkeys[0], M,
+               ws.scan_part, nb + 1, key_range);
     pf.end(pi, s);
-    const uint32_t* order = ws.dvals[dbuf];
+    const uint32_t* order = ws.dvals[0];
     // 2. exclusive scan of tiles-touched in that order (single pass; flags zeroed by the fix-up)
     pi = pf.begin(GS_KF_TILE_SCAN, s, 1);
     pdl_launch(k_scan_offsets, nb, kScanThreads, 0, s, order, ws.tiles_touched, M, ws.scan_part, nb, ws.offsets,
