@@ -477,6 +477,56 @@ def _tie_scene(mu, rng):
                 sh=rng.uniform(-0.5, 1.0, (n, 1, 3)).astype(np.float32), sh_degree=0)
 
 
+def _tile_lists(r, L):
+    torch.cuda.synchronize()
+    T = L.n_tiles
+    ranges = ws_view(r, L.tile_ranges, np.uint32, 2 * T).reshape(T, 2)
+    sv = ws_view(r, L.sorted_vals, np.uint32, int(r.last_pairs))
+    return [sv[a:b].copy() for a, b in ranges]
+
+
+def _set_counters(r, L, first, values):
+    raw = torch.from_numpy(np.array(values, np.uint64).view(np.uint8).copy()).cuda()
+    off = L.counters + 8 * first
+    r.ws[off:off + raw.numel()].copy_(raw)
+
+
+def test_depth_order_survives_stale_key_ranges():
+    """The depth sort orders records by a map of their key's high word
+    through the range the projection recorded under a generation tag.
+    Binning again without a projection (an older generation: the fallback
+    map), garbage in the range slots, and a range wider than the keys under
+    the current generation must all give the same tile lists: the map is
+    monotone in every case and the fix-up orders each run of equal mapped
+    keys by the full key."""
+    p = scenes.frustum_scene(2500, seed=4)
+    views = ragged_views(2500)
+    win, r = gpu_forward(p, views, tile_size=16)
+    L = r.layout()
+    ref = _tile_lists(r, L)
+    assert sum(len(x) for x in ref) == int(r.last_pairs) > 1000
+
+    def same():
+        got = _tile_lists(r, L)
+        for t, (a, b) in enumerate(zip(ref, got)):
+            np.testing.assert_array_equal(a, b, err_msg="tile %d" % t)
+
+    r.ctx.bin(r.views, r.ws_struct)
+    same()
+    rng = np.random.default_rng(7)
+    for _ in range(3):
+        _set_counters(r, L, 1, rng.integers(0, 2**63, 3, dtype=np.uint64) * 2 + 1)
+        r.ctx.project(win.struct(), r.views, r.ws_struct)
+        r.ctx.bin(r.views, r.ws_struct)
+        same()
+    torch.cuda.synchronize()
+    gen = int(ws_view(r, L.counters + 24, np.uint64, 1)[0]) & 0xFFFFFFFF
+    _set_counters(r, L, 1, [(gen << 32) | 0xFFFFFFFE, (gen << 32) | 0xFFFFFFFF])
+    r.ctx.project(win.struct(), r.views, r.ws_struct)
+    r.ctx.bin(r.views, r.ws_struct)
+    same()
+
+
 def test_depth_ties_long_run():
     """3000 Gaussians on the fronto-parallel plane z = 3 seen by the identity
     camera: every depth key is exactly equal (one run of 3000 for the tie
