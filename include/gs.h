@@ -83,7 +83,9 @@ typedef enum gs_status {
     GS_ERR_CAPACITY = -4,    /* more (Gaussian, tile) pairs than the workspace holds */
     GS_ERR_TIMEOUT = -5,     /* a bounded device wait expired (latched, see gs_sync_status) */
     GS_ERR_NONFINITE = -6,   /* a camera or intrinsic value is not finite */
-    GS_ERR_UNSUPPORTED = -7  /* option not built into this library */
+    GS_ERR_UNSUPPORTED = -7, /* option not built into this library */
+    GS_ERR_BOUNDS = -8       /* checked build only: an index read from device memory failed its bounds
+                                check and the access was skipped (latched, see gs_sync_status) */
 } gs_status;
 
 typedef enum gs_dtype { GS_F32 = 0, GS_F16 = 1, GS_BF16 = 2 } gs_dtype;
@@ -457,6 +459,11 @@ GS_API int gs_profile_collect(gs_ctx* ctx, gs_stream stream, gs_profile_entry* o
                               int* n_out);
 /* Number of kernel launches (and memset nodes) this context has issued. */
 GS_API int64_t gs_launch_count(const gs_ctx* ctx);
+/* 1 in the checked build of the library (libgs_b300_checked.so, compiled
+ * with GS_CHECKED: the compositing kernels bounds-check every tile range and
+ * pair record they read and latch GS_ERR_BOUNDS instead of reading out of
+ * bounds), 0 in the normal build.  Same API and results otherwise. */
+GS_API int32_t gs_checked_build(void);
 
 /* ---- pose normal equations of the photometric residual (Sec. II-D) ----
  *

@@ -14,7 +14,10 @@ import numpy as np
 import torch  # noqa: F401  (loads the CUDA runtime the library links against)
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libgs_b300.so")
+# GS_B300_LIB=checked loads the checked build (bounds-checked compositing
+# kernels, `python -m paper_2501_08672_b300.build --checked`).
+LIB_NAME = "libgs_b300_checked.so" if os.environ.get("GS_B300_LIB", "") == "checked" else "libgs_b300.so"
+LIB_PATH = os.path.join(HERE, LIB_NAME)
 
 GS_OK = 0
 GS_ERR_INVALID_ARG = -1
@@ -24,6 +27,7 @@ GS_ERR_CAPACITY = -4
 GS_ERR_TIMEOUT = -5
 GS_ERR_NONFINITE = -6
 GS_ERR_UNSUPPORTED = -7
+GS_ERR_BOUNDS = -8
 GS_F32, GS_F16, GS_BF16 = 0, 1, 2
 GS_MAX_VIEWS = 64
 
@@ -37,7 +41,7 @@ EXPORTED = ["gs_config_default", "gs_version", "gs_context_create", "gs_context_
             "gs_window_scratch_bytes", "gs_window_compact", "gs_window_remove", "gs_window_gather", "gs_window_clear",
             "gs_sh_init_bilinear", "gs_dssim_scratch_floats", "gs_dssim_loss", "gs_adam_step_ranges",
             "gs_selftest_wait_scratch_bytes", "gs_selftest_bounded_wait", "gs_render_fwd_l1",
-            "gs_render_bwd_accumulate"]
+            "gs_render_bwd_accumulate", "gs_checked_build"]
 
 KERNEL_FAMILIES = ["project", "depth_sort", "tile_scan", "emit", "tile_sort", "ranges", "raster_fwd", "l1",
                    "raster_bwd", "project_bwd", "adam", "pose_normal", "window", "ssim"]
@@ -113,12 +117,13 @@ def lib():
     global _lib
     if _lib is None:
         if not os.path.exists(LIB_PATH):
-            raise RuntimeError("libgs_b300.so not found at %s: build it with "
-                               "`python -m paper_2501_08672_b300.build`" % LIB_PATH)
+            raise RuntimeError("%s not found at %s: build it with `python -m paper_2501_08672_b300.build%s`"
+                               % (LIB_NAME, LIB_PATH, " --checked" if "checked" in LIB_NAME else ""))
         L = ctypes.CDLL(LIB_PATH)
         P, I, I64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
         L.gs_config_default.argtypes = [ctypes.POINTER(Config)]
         L.gs_config_default.restype = None
+        L.gs_checked_build.restype = ctypes.c_int32
         L.gs_version.restype = ctypes.c_char_p
         L.gs_context_create.argtypes = [ctypes.POINTER(P), I, ctypes.POINTER(Config)]
         L.gs_context_destroy.argtypes = [P]

@@ -326,6 +326,15 @@ RenderConst make_rc(const gs_config& c) {
     r.z_near = c.z_near;
     r.log2_alpha_min = c.alpha_min > 0.f ? log2f(c.alpha_min) : -INFINITY;
     for (int k = 0; k < 3; ++k) r.bg[k] = c.bg[k];
+    r.status = nullptr;
+    r.cap = 0;
+    return r;
+}
+
+// The context's render constants: its configuration and its status word.
+RenderConst ctx_rc(const gs_ctx* ctx) {
+    RenderConst r = make_rc(ctx->cfg);
+    r.status = ctx->d_status;
     return r;
 }
 
@@ -508,7 +517,7 @@ int gs_project(gs_ctx* ctx, const gs_gaussians* g, const gs_view* views, int n_v
     BatchParam bp;
     make_batch(ctx->cfg, views, n_views, bp);
     const WsPtrs wp = ws_ptrs(ws, L, bp.total_tiles);
-    cudaError_t e = launch_project(bp, gp, make_rc(ctx->cfg), wp, reinterpret_cast<cudaStream_t>(stream), ctx->prof);
+    cudaError_t e = launch_project(bp, gp, ctx_rc(ctx), wp, reinterpret_cast<cudaStream_t>(stream), ctx->prof);
     return e == cudaSuccess ? GS_OK : cuda_fail(ctx, e, "gs_project");
 }
 
@@ -522,7 +531,7 @@ int gs_bin(gs_ctx* ctx, const gs_view* views, int n_views, const gs_workspace* w
     BatchParam bp;
     make_batch(ctx->cfg, views, n_views, bp);
     WsPtrs wp = ws_ptrs(ws, L, bp.total_tiles);
-    wp.log2_alpha_min = make_rc(ctx->cfg).log2_alpha_min;
+    wp.log2_alpha_min = ctx_rc(ctx).log2_alpha_min;
     const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     cudaError_t e = launch_bin(bp, wp, ctx->d_status, ctx->d_pairs, s, ctx->prof);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "gs_bin");
@@ -552,7 +561,7 @@ int gs_render_fwd(gs_ctx* ctx, const gs_view* views, int n_views, const gs_works
     BatchParam bp;
     make_batch(ctx->cfg, views, n_views, bp);
     const WsPtrs wp = ws_ptrs(ws, L, bp.total_tiles);
-    cudaError_t e = launch_render_fwd(bp, make_rc(ctx->cfg), wp, rgb, T_final, n_contrib, n_used, nullptr, nullptr,
+    cudaError_t e = launch_render_fwd(bp, ctx_rc(ctx), wp, rgb, T_final, n_contrib, n_used, nullptr, nullptr,
                                       nullptr, reinterpret_cast<cudaStream_t>(stream), ctx->prof);
     return e == cudaSuccess ? GS_OK : cuda_fail(ctx, e, "gs_render_fwd");
 }
@@ -570,7 +579,7 @@ int gs_render_fwd_l1(gs_ctx* ctx, const gs_view* views, int n_views, const gs_wo
     BatchParam bp;
     make_batch(ctx->cfg, views, n_views, bp);
     const WsPtrs wp = ws_ptrs(ws, L, bp.total_tiles);
-    cudaError_t e = launch_render_fwd(bp, make_rc(ctx->cfg), wp, rgb, T_final, n_contrib, n_used, target, dL_drgb,
+    cudaError_t e = launch_render_fwd(bp, ctx_rc(ctx), wp, rgb, T_final, n_contrib, n_used, target, dL_drgb,
                                       loss_dev, reinterpret_cast<cudaStream_t>(stream), ctx->prof);
     return e == cudaSuccess ? GS_OK : cuda_fail(ctx, e, "gs_render_fwd_l1");
 }
@@ -695,7 +704,7 @@ int render_bwd_impl(gs_ctx* ctx, const gs_gaussians* g, const gs_view* views, in
     BatchParam bp;
     make_batch(ctx->cfg, views, n_views, bp);
     const WsPtrs wp = ws_ptrs(ws, L, bp.total_tiles);
-    const RenderConst rcst = make_rc(ctx->cfg);
+    const RenderConst rcst = ctx_rc(ctx);
     const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     cudaError_t e = launch_render_bwd(bp, rcst, wp, T_final, n_contrib, dL_drgb, s, ctx->prof);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "gs_render_bwd (raster)");
@@ -890,7 +899,7 @@ int gs_pose_normal(gs_ctx* ctx, const gs_gaussians* g, const gs_view* views, int
     BatchParam bp;
     make_batch(ctx->cfg, views, n_views, bp);
     const WsPtrs wp = ws_ptrs(ws, L, bp.total_tiles);
-    const RenderConst rcst = make_rc(ctx->cfg);
+    const RenderConst rcst = ctx_rc(ctx);
     const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     float4* tangents = reinterpret_cast<float4*>(scratch);
     float* partials = scratch + (size_t)4 * kPoseTan4 * (size_t)L.pub.n_records;
@@ -1054,5 +1063,13 @@ int gs_profile_collect(gs_ctx* ctx, gs_stream stream, gs_profile_entry* out, int
 }
 
 int64_t gs_launch_count(const gs_ctx* ctx) { return ctx ? (int64_t)ctx->prof.launches : -1; }
+
+int32_t gs_checked_build(void) {
+#ifdef GS_CHECKED
+    return 1;
+#else
+    return 0;
+#endif
+}
 
 }  // extern "C"

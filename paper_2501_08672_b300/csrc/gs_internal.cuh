@@ -62,7 +62,26 @@ struct RenderConst {
     float alpha_min, alpha_max, T_min, blur, z_near;
     float log2_alpha_min;   // -inf when alpha_min == 0
     float bg[3];
+    unsigned int* status;   // the context's latched status word
+    long long cap;          // pair capacity of the workspace (set by the compositing launches)
 };
+
+// Bounds checks of the checked build (compiled with -DGS_CHECKED): the
+// compositing kernels test every index they read from device memory (a
+// tile's pair range against the capacity, a pair's record against the
+// record count) before using it.  A failed test latches GS_ERR_BOUNDS in the
+// status word (read by gs_sync_status) and the caller skips the access.  In
+// the normal build the test is constant true and compiles away.
+__device__ __forceinline__ bool gs_checked(bool ok, const RenderConst& rc) {
+#ifdef GS_CHECKED
+    if (!ok && rc.status) atomicCAS(rc.status, 0u, (unsigned int)(-GS_ERR_BOUNDS));
+    return ok;
+#else
+    (void)ok;
+    (void)rc;
+    return true;
+#endif
+}
 
 struct GaussPtrs {
     const float* means;

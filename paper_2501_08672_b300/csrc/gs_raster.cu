@@ -155,7 +155,8 @@ __global__ void __launch_bounds__(TS * TS / PPT, fwd_min_blocks<TS * TS / PPT, P
         used[k] = 0;
         thr[k] = (pm.col(k) < V.W && pm.row(k) < V.H) ? rc.log2_alpha_min : kDone;
     }
-    const uint2 rg = ranges[tile];
+    uint2 rg = ranges[tile];
+    if (!gs_checked(rg.x <= rg.y && (long long)rg.y <= rc.cap, rc)) rg.y = rg.x;
 
     for (uint32_t start = rg.x; start < rg.y; start += WB) {
         bool all = true;
@@ -171,10 +172,12 @@ __global__ void __launch_bounds__(TS * TS / PPT, fwd_min_blocks<TS * TS / PPT, P
             float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a, c = a;
             if (idx < rg.y) {
                 r = svals[idx];
-                a = rec[3 * r];
-                c = rec[3 * r + 2];
-                reach = wb.reaches(a.x, a.y, c.w);
-                if (reach) b = rec[3 * r + 1];
+                if (gs_checked(r < (uint32_t)bp.total_recs, rc)) {
+                    a = rec[3 * r];
+                    c = rec[3 * r + 2];
+                    reach = wb.reaches(a.x, a.y, c.w);
+                    if (reach) b = rec[3 * r + 1];
+                }
             }
             const uint32_t m = __ballot_sync(0xffffffffu, reach);
             if (reach) {
@@ -352,7 +355,8 @@ __global__ void __launch_bounds__(TS * TS / PPT, bwd_min_blocks<TS * TS / PPT, P
     const int ty = lt / V.tiles_x, tx = lt - ty * V.tiles_x;
     const PixelMap<TS, PPT> pm(tx, ty, t);
     const WarpBox wb = warp_box(pm.col(0), pm.col(PPT - 1), pm.row(0), pm.row(PPT - 1));
-    const uint2 rg = ranges[tile];
+    uint2 rg = ranges[tile];
+    if (!gs_checked(rg.x <= rg.y && (long long)rg.y <= rc.cap, rc)) rg.y = rg.x;
     const long long hw = (long long)V.W * V.H;
     const float* gimg = dL_drgb + 3 * V.pix_off;
 
@@ -411,8 +415,7 @@ __global__ void __launch_bounds__(TS * TS / PPT, bwd_min_blocks<TS * TS / PPT, P
             bool reach = false;
             uint32_t r = 0;
             float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a, c = a;
-            if (rel >= 0) {
-                r = svals[rg.x + rel];
+            if (rel >= 0 && gs_checked((r = svals[rg.x + rel]) < (uint32_t)bp.total_recs, rc)) {
                 a = rec[3 * r];
                 c = rec[3 * r + 2];
                 reach = wb.reaches(a.x, a.y, c.w);
@@ -837,7 +840,8 @@ __global__ void __launch_bounds__(TS * TS) k_render_pose_normal(const __grid_con
         dT[k] = 0.f;
         dC[0][k] = dC[1][k] = dC[2][k] = 0.f;
     }
-    const uint2 rg = ranges[tile];
+    uint2 rg = ranges[tile];
+    if (!gs_checked(rg.x <= rg.y && (long long)rg.y <= rc.cap, rc)) rg.y = rg.x;
     for (uint32_t start = rg.x; start < rg.y; start += kPNBatch) {
         if (__all_sync(0xffffffffu, done)) break;
         const uint32_t idx = start + lane;
@@ -845,8 +849,7 @@ __global__ void __launch_bounds__(TS * TS) k_render_pose_normal(const __grid_con
         uint32_t r = 0;
         float4 a = make_float4(0.f, 0.f, 0.f, 0.f), c = a;
         float4 b = a;
-        if (lane < kPNBatch && idx < rg.y) {
-            r = svals[idx];
+        if (lane < kPNBatch && idx < rg.y && gs_checked((r = svals[idx]) < (uint32_t)bp.total_recs, rc)) {
             a = rec[3 * r];
             c = rec[3 * r + 2];
             reach = wb.reaches(a.x, a.y, c.w);
@@ -1008,9 +1011,11 @@ bool raster_variant_exists(int ts, int ppt, int batch) {
     return false;
 }
 
-cudaError_t launch_render_fwd(const BatchParam& bp, const RenderConst& rc, const WsPtrs& ws,
+cudaError_t launch_render_fwd(const BatchParam& bp, const RenderConst& rc_in, const WsPtrs& ws,
                               float* rgb, float* T_final, uint32_t* n_contrib, uint32_t* n_used,
                               const float* target, float* dL_drgb, float* loss, cudaStream_t s, Prof& pf) {
+    RenderConst rc = rc_in;
+    rc.cap = ws.cap;
     if (bp.total_tiles <= 0) {
         // no pixels: the loss is 0 (the caller's views are all non-empty, so
         // this is unreachable through the C ABI; kept for safety)
@@ -1039,9 +1044,11 @@ cudaError_t launch_render_fwd(const BatchParam& bp, const RenderConst& rc, const
     return cudaGetLastError();
 }
 
-cudaError_t launch_render_bwd(const BatchParam& bp, const RenderConst& rc, const WsPtrs& ws,
+cudaError_t launch_render_bwd(const BatchParam& bp, const RenderConst& rc_in, const WsPtrs& ws,
                               const float* T_final, const uint32_t* n_contrib,
                               const float* dL_drgb, cudaStream_t s, Prof& pf) {
+    RenderConst rc = rc_in;
+    rc.cap = ws.cap;
     // deterministic form: per-pair partials, then a fixed-order sum per record
     // (which writes every record, so no clearing)
     const bool det = ws.pair_grad != nullptr;
@@ -1211,9 +1218,11 @@ cudaError_t launch_l1_static(const BatchParam& bp, const float* rgb, const float
 
 bool pose_normal_supported(int ts) { return ts == 8 || ts == 16; }
 
-cudaError_t launch_pose_normal(const BatchParam& bp, const RenderConst& rc, const WsPtrs& ws,
+cudaError_t launch_pose_normal(const BatchParam& bp, const RenderConst& rc_in, const WsPtrs& ws,
                                const float4* tangents, const float* target, float* partials, double* normal,
                                float* H_pix, cudaStream_t s, Prof& pf) {
+    RenderConst rc = rc_in;
+    rc.cap = ws.cap;
     if (bp.total_tiles <= 0) return cudaSuccess;
     const uint32_t* svals = ws.pvals[ws.sorted_buf];
     const int pi = pf.begin(GS_KF_POSE_NORMAL, s, 2);
