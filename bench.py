@@ -87,6 +87,8 @@ def parse():
     ap.add_argument("--tile-size", type=int, default=0, help="0: autotune tile size, pixels per thread, batch")
     ap.add_argument("--ppt", type=int, default=0)
     ap.add_argument("--batch", type=int, default=0)
+    ap.add_argument("--bin-tile-size", type=int, default=0,
+                    help="binning tile size with --tile-size (0: the tile size; 2 or 4 times it: bins split per tile)")
     ap.add_argument("--maint-n", default="",
                     help="maintenance workload: comma-separated window sizes (default: the full sweep)")
     ap.add_argument("--compare-forms", dest="compare_forms", action="store_true", default=None,
@@ -380,13 +382,13 @@ def run_b300(args, world, rank, local):
     # launch shape: autotuned over the compiled variants unless given
     tune_table = None
     if args.tile_size:
-        shape = (args.tile_size, args.ppt, args.batch)
+        shape = (args.tile_size, args.ppt, args.batch, args.bin_tile_size)
     else:
         shape, tune_table = autotune(params, views, target, steps=3, device=local, storage=storage,
                                      deterministic=int(args.deterministic))
     opt = WindowOptimizer(params, views, target, lr=LR, device=local, tile_size=shape[0],
                           ssim_lambda=args.ssim_lambda,
-                          pixels_per_thread=shape[1], batch=shape[2], storage=storage,
+                          pixels_per_thread=shape[1], batch=shape[2], bin_tile_size=shape[3], storage=storage,
                           deterministic=int(args.deterministic))
     ctx = opt.r.ctx
     opt.step(count=True)  # sizes the pair workspace
@@ -571,7 +573,8 @@ def run_b300(args, world, rank, local):
                 raise RuntimeError("pair capacity exceeded in a compared form")
             return whole_job_rate(world, K, max_over_ranks([ms], world)[0])
 
-        kw = dict(lr=LR, device=local, tile_size=shape[0], pixels_per_thread=shape[1], batch=shape[2])
+        kw = dict(lr=LR, device=local, tile_size=shape[0], pixels_per_thread=shape[1], batch=shape[2],
+                  bin_tile_size=shape[3])
         if storage:
             o = WindowOptimizer(params, views, target, **kw)
             other_forms["batched_fp32_storage_it_s"] = form_rate(o)
@@ -601,12 +604,13 @@ def run_b300(args, world, rank, local):
                            "image": ([int(views[0]["W"]), int(views[0]["H"])] if len({(v["W"], v["H"]) for v in views}) == 1
                                      else [[int(v["W"]), int(v["H"])] for v in views]),
                            "tile_size": shape[0], "pixels_per_thread": shape[1],
-                           "batch": shape[2], "sh_degree": int(params["sh_degree"]), "lr": LR,
+                           "batch": shape[2], "bin_tile_size": shape[3] or shape[0],
+                           "sh_degree": int(params["sh_degree"]), "lr": LR,
                            "loss": ("L1" if args.ssim_lambda == 0 else
                                     "(1 - %g) L1 + %g (1 - SSIM), 11x11 window" % (args.ssim_lambda, args.ssim_lambda)),
                            "storage": ({k: str(v).replace("torch.", "") for k, v in storage.items()} if storage
                                        else "float32"),
-                           "autotune_ms": ({"%d/%d/%d" % k: round(v, 4) for k, v in tune_table.items()}
+                           "autotune_ms": ({"%d/%d/%d/%d" % k: round(v, 4) for k, v in tune_table.items()}
                                            if tune_table else None),
                            "l2": "flushed between steps (256 MB write outside the timed events)",
                            "pairs_per_step": int(opt.r.last_pairs), "parallelism": "replicas" if world > 1 else "1 GPU",

@@ -122,6 +122,20 @@ typedef struct gs_config {
      * whose order varies.  Costs 56 bytes of workspace per pair of capacity
      * (gs_workspace_query includes them) and some speed. */
     int32_t deterministic;
+    /* Tile size of the binning (a2) [0 = tile_size].  2 or 4 times
+     * tile_size, at most 32: gs_project and gs_bin list and sort the records
+     * per bin of F x F tiles (F = bin_tile_size / tile_size), which has
+     * fewer (bin, record) pairs to sort than (tile, record) pairs, and gs_bin
+     * then splits each bin's front-to-back list, keeping its order, into the
+     * lists of the bin's F^2 tiles, a record going to each tile its
+     * alpha >= alpha_min footprint reaches (the binning's own row-span test
+     * at tile_size, so each tile gets the list that binning at tile_size
+     * gives).  The compositing kernels read those per-tile lists.  Used in
+     * truncated mode (alpha_min > 0) without deterministic only; otherwise the
+     * binning runs at tile_size.  Costs 4 F^2 bytes of workspace per pair of
+     * capacity (max_pairs then counts (bin, record) pairs, and F^2 max_pairs
+     * must stay below 2^32). */
+    int32_t bin_tile_size;
 } gs_config;
 
 GS_API void gs_config_default(gs_config* cfg);
@@ -206,8 +220,18 @@ typedef struct gs_ws_layout {
     size_t counters;      /* uint64[8]: [0] pairs needed; [1..3] the projection's depth-key range and its generation */
     size_t total;         /* bytes */
     int64_t n_records;    /* M */
-    int32_t n_tiles;      /* T */
+    int32_t n_tiles;      /* T (tiles of the compositing) */
     int64_t n_pixels;
+    /* Binning at a larger bin size (gs_config.bin_tile_size): rects,
+     * tiles_touched and the pair arrays count bins; bin_vals holds the sorted
+     * record index per (bin, record) pair, bin_ranges (uint32[n_bins][2])
+     * each bin's [start, end) into it, and sorted_vals / tile_ranges the
+     * per-tile lists split from them.  Otherwise bin_vals = sorted_vals,
+     * bin_ranges = tile_ranges and n_bins = n_tiles. */
+    size_t bin_vals;
+    size_t bin_ranges;
+    int32_t n_bins;
+    int32_t bin_size;     /* pixels per bin side (tile_size when not refined) */
 } gs_ws_layout;
 
 /* Workspace size for `n_views` views and a pair capacity max_pairs.
@@ -230,7 +254,11 @@ GS_API int gs_project(gs_ctx* ctx, const gs_gaussians* g, const gs_view* views, 
  * global tile id, so each tile's list is ordered by (depth, index): the
  * order a radix sort of 64-bit (tile << 32 | depth) keys gives.  Then
  * extracts each tile's [start, end) range.  The tile sort is implied by the
- * 3D-GS rasteriser the paper relies on (Sec. II-C).
+ * 3D-GS rasteriser the paper relies on (Sec. II-C).  With
+ * gs_config.bin_tile_size above the tile size the records are binned and
+ * sorted per bin of F x F tiles, and each bin's list is then split, in
+ * order, into its tiles' lists (the pair count and capacity then count
+ * (bin, record) pairs).
  * pairs_needed: NULL (fully asynchronous) or a host pointer that receives
  * the number of pairs after a stream synchronisation.
  * Errors: GS_ERR_INVALID_ARG, GS_ERR_CUDA; with pairs_needed non-NULL also
@@ -439,7 +467,8 @@ typedef enum gs_kernel_family {
     GS_KF_POSE_NORMAL = 11, /* pose tangents, forward-mode compositing, normal equations */
     GS_KF_WINDOW = 12,      /* sliding-window maintenance and SH0 initialisation */
     GS_KF_SSIM = 13,        /* photometric loss with the D-SSIM term */
-    GS_KF_COUNT = 14
+    GS_KF_REFINE = 14,      /* a2 split of the bin lists into tile lists */
+    GS_KF_COUNT = 15
 } gs_kernel_family;
 
 typedef struct gs_profile_entry {

@@ -44,7 +44,7 @@ EXPORTED = ["gs_config_default", "gs_version", "gs_context_create", "gs_context_
             "gs_render_bwd_accumulate", "gs_checked_build"]
 
 KERNEL_FAMILIES = ["project", "depth_sort", "tile_scan", "emit", "tile_sort", "ranges", "raster_fwd", "l1",
-                   "raster_bwd", "project_bwd", "adam", "pose_normal", "window", "ssim"]
+                   "raster_bwd", "project_bwd", "adam", "pose_normal", "window", "ssim", "refine"]
 
 
 class WindowColumn(ctypes.Structure):
@@ -61,7 +61,7 @@ class Config(ctypes.Structure):
     _fields_ = [("tile_size", ctypes.c_int32), ("alpha_min", ctypes.c_float), ("alpha_max", ctypes.c_float),
                 ("T_min", ctypes.c_float), ("blur", ctypes.c_float), ("z_near", ctypes.c_float),
                 ("bg", ctypes.c_float * 3), ("pixels_per_thread", ctypes.c_int32), ("batch", ctypes.c_int32),
-                ("deterministic", ctypes.c_int32)]
+                ("deterministic", ctypes.c_int32), ("bin_tile_size", ctypes.c_int32)]
 
 
 class View(ctypes.Structure):
@@ -92,7 +92,9 @@ class WsLayout(ctypes.Structure):
                                                "depth_vals",
                                                "pair_offsets", "pair_keys", "pair_vals", "sorted_vals",
                                                "tile_ranges", "grad2d", "counters", "total")] + [
-        ("n_records", ctypes.c_int64), ("n_tiles", ctypes.c_int32), ("n_pixels", ctypes.c_int64)]
+        ("n_records", ctypes.c_int64), ("n_tiles", ctypes.c_int32), ("n_pixels", ctypes.c_int64),
+        ("bin_vals", ctypes.c_size_t), ("bin_ranges", ctypes.c_size_t), ("n_bins", ctypes.c_int32),
+        ("bin_size", ctypes.c_int32)]
 
 
 class ProfileEntry(ctypes.Structure):

@@ -128,9 +128,20 @@ struct Layout {
     gs_ws_layout pub;
     size_t scan_part, dkeys1, dvals1, pkeys1, pvals1, hist, hist_part, partials, okeys0, okeys1, ovals0, ovals1, hitmask;
     size_t pair_rec, pair_inv, pair_grad;  // deterministic backward (0 when off)
+    size_t rvals;                          // per-tile lists split from the bins (0 when the bins are the tiles)
     int scan_blocks;
+    int bin_tiles;                         // bins (== tiles when refine == 1)
+    int refine;                            // bin side / tile side
     long long max_g_end;
 };
+
+// The binning's tile size: gs_config.bin_tile_size where it applies
+// (truncated mode, not deterministic), else the compositing tile size.
+int bin_size_of(const gs_config& c) {
+    if (c.bin_tile_size == 0 || c.bin_tile_size == c.tile_size || c.deterministic || !(c.alpha_min > 0.f))
+        return c.tile_size;
+    return c.bin_tile_size;
+}
 
 int l1_blocks_x(long long max_px) { return (int)((3 * max_px + 1023) / 1024); }
 
@@ -143,7 +154,8 @@ int make_layout(gs_ctx* ctx, const gs_config& cfg, const gs_view* views, int n_v
     if (max_pairs < 0 || max_pairs > 0x7FFFFFFFll)
         return fail(ctx, GS_ERR_INVALID_ARG, "max_pairs=%lld outside [0, 2^31)", (long long)max_pairs);
     const int ts = cfg.tile_size;
-    long long M = 0, P = 0, T = 0, max_px = 0, max_g_end = 0;
+    const int bs = bin_size_of(cfg);
+    long long M = 0, P = 0, T = 0, Tb = 0, max_px = 0, max_g_end = 0;
     for (int v = 0; v < n_views; ++v) {
         const gs_view& V = views[v];
         if (V.width <= 0 || V.height <= 0 || V.width > 32768 || V.height > 32768)
@@ -162,6 +174,7 @@ int make_layout(gs_ctx* ctx, const gs_config& cfg, const gs_view* views, int n_v
         M += V.g_end - V.g_begin;
         const long long tx = (V.width + ts - 1) / ts, ty = (V.height + ts - 1) / ts;
         T += tx * ty;
+        Tb += (long long)((V.width + bs - 1) / bs) * ((V.height + bs - 1) / bs);
         P += (long long)V.width * V.height;
         if ((long long)V.width * V.height > max_px) max_px = (long long)V.width * V.height;
         if (V.g_end > max_g_end) max_g_end = V.g_end;
@@ -170,8 +183,14 @@ int make_layout(gs_ctx* ctx, const gs_config& cfg, const gs_view* views, int n_v
     if (T >= 0x7FFFFFFFll) return fail(ctx, GS_ERR_INVALID_ARG, "too many tiles: %lld", T);
 
     const long long cap = max_pairs;
+    L.refine = bs / ts;
+    L.bin_tiles = (int)Tb;
+    if ((long long)L.refine * L.refine * cap >= 0xFFFFFFFFll)
+        return fail(ctx, GS_ERR_INVALID_ARG, "max_pairs=%lld: %d^2 max_pairs must stay below 2^32 with bins of %d",
+                    (long long)max_pairs, L.refine, bs);
     long long big = M > cap ? M : cap;
     if (T > big) big = T;
+    if (Tb > big) big = Tb;
     const long long radix_tiles = (big + 4095) / 4096;      // tiles of the radix sort passes
     const long long hist_parts = (256 * radix_tiles + 4095) / 4096;
     L.scan_blocks = (int)((M + 4095) / 4096);
@@ -204,6 +223,8 @@ int make_layout(gs_ctx* ctx, const gs_config& cfg, const gs_view* views, int n_v
     L.hist = take(sizeof(uint32_t) * 256 * (size_t)(radix_tiles > 0 ? radix_tiles : 1));
     L.hist_part = take(sizeof(unsigned long long) * (size_t)(hist_parts + 2));  // look-back flags + ticket
     W.tile_ranges = take(sizeof(uint2) * (size_t)T);
+    W.bin_ranges = L.refine > 1 ? take(sizeof(uint2) * (size_t)Tb) : W.tile_ranges;
+    L.rvals = L.refine > 1 ? take(sizeof(uint32_t) * (size_t)(L.refine * L.refine) * (size_t)cap) : 0;
     L.okeys0 = take(sizeof(uint32_t) * (size_t)T);
     L.okeys1 = take(sizeof(uint32_t) * (size_t)T);
     L.ovals0 = take(sizeof(uint32_t) * (size_t)T);
@@ -218,10 +239,13 @@ int make_layout(gs_ctx* ctx, const gs_config& cfg, const gs_view* views, int n_v
         L.pair_grad = take(sizeof(float) * kPairGradStride * (size_t)cap);
     }
     W.total = off;
-    W.sorted_vals = sorted_buffer((int)T) ? L.pvals1 : W.pair_vals;
+    W.bin_vals = sorted_buffer((int)Tb) ? L.pvals1 : W.pair_vals;
+    W.sorted_vals = L.refine > 1 ? L.rvals : W.bin_vals;
     W.n_records = M;
     W.n_tiles = (int32_t)T;
     W.n_pixels = P;
+    W.n_bins = (int32_t)Tb;
+    W.bin_size = bs;
     return GS_OK;
 }
 
@@ -236,7 +260,7 @@ int check_ws(gs_ctx* ctx, const gs_view* views, int n_views, const gs_workspace*
     return GS_OK;
 }
 
-WsPtrs ws_ptrs(const gs_workspace* ws, const Layout& L, int total_tiles) {
+WsPtrs ws_ptrs(const gs_workspace* ws, const Layout& L) {
     char* b = static_cast<char*>(ws->ptr);
     WsPtrs p{};
     p.rec = reinterpret_cast<float4*>(b + L.pub.records);
@@ -257,6 +281,9 @@ WsPtrs ws_ptrs(const gs_workspace* ws, const Layout& L, int total_tiles) {
     p.hist = reinterpret_cast<uint32_t*>(b + L.hist);
     p.hist_part = reinterpret_cast<uint32_t*>(b + L.hist_part);
     p.ranges = reinterpret_cast<uint2*>(b + L.pub.tile_ranges);
+    p.ranges_bin = reinterpret_cast<uint2*>(b + L.pub.bin_ranges);
+    p.rvals = L.rvals ? reinterpret_cast<uint32_t*>(b + L.rvals) : nullptr;
+    p.refine = L.refine;
     p.okeys[0] = reinterpret_cast<uint32_t*>(b + L.okeys0);
     p.okeys[1] = reinterpret_cast<uint32_t*>(b + L.okeys1);
     p.ovals[0] = reinterpret_cast<uint32_t*>(b + L.ovals0);
@@ -269,7 +296,7 @@ WsPtrs ws_ptrs(const gs_workspace* ws, const Layout& L, int total_tiles) {
     p.pair_grad = L.pair_grad ? reinterpret_cast<float*>(b + L.pair_grad) : nullptr;
     p.cap = ws->max_pairs;
     p.scan_blocks = L.scan_blocks;
-    p.sorted_buf = sorted_buffer(total_tiles);
+    p.sorted_buf = sorted_buffer(L.bin_tiles);
     p.log2_alpha_min = -INFINITY;
     return p;
 }
@@ -280,10 +307,13 @@ WsPtrs ws_ptrs(const gs_workspace* ws, const Layout& L, int total_tiles) {
 int default_ppt(int ts) { return ts == 32 ? 4 : 2; }
 int default_batch(int ts, int ppt) { return ts * ts / ppt <= 128 ? 128 : 256; }
 
-void make_batch(const gs_config& cfg, const gs_view* views, int n_views, BatchParam& bp) {
+// The batch with tiles of cfg.tile_size pixels, or of ts pixels (the bins)
+// when ts is nonzero.
+void make_batch(const gs_config& cfg, const gs_view* views, int n_views, BatchParam& bp, int ts = 0) {
     memset(&bp, 0, sizeof(bp));
+    if (ts == 0) ts = cfg.tile_size;
     bp.n_views = n_views;
-    bp.tile_size = cfg.tile_size;
+    bp.tile_size = ts;
     bp.ppt = cfg.pixels_per_thread ? cfg.pixels_per_thread : default_ppt(cfg.tile_size);
     bp.batch = cfg.batch ? cfg.batch : default_batch(cfg.tile_size, bp.ppt);
     long long rec = 0, pix = 0;
@@ -300,8 +330,8 @@ void make_batch(const gs_config& cfg, const gs_view* views, int n_views, BatchPa
             V.campos[k] = (float)c;
         }
         V.W = S.width; V.H = S.height;
-        V.tiles_x = (S.width + cfg.tile_size - 1) / cfg.tile_size;
-        V.tiles_y = (S.height + cfg.tile_size - 1) / cfg.tile_size;
+        V.tiles_x = (S.width + ts - 1) / ts;
+        V.tiles_y = (S.height + ts - 1) / ts;
         V.tile_off = tiles;
         V.g_begin = S.g_begin; V.g_end = S.g_end;
         V.rec_off = rec;
@@ -395,6 +425,15 @@ int check_config(const gs_config& c, char* msg, size_t n) {
         snprintf(msg, n, "deterministic=%d not in {0, 1}", c.deterministic);
         return GS_ERR_INVALID_ARG;
     }
+    if (c.bin_tile_size != 0 && c.bin_tile_size != c.tile_size && c.bin_tile_size != 2 * c.tile_size &&
+        c.bin_tile_size != 4 * c.tile_size) {
+        snprintf(msg, n, "bin_tile_size=%d is not 0 or 1, 2 or 4 times tile_size=%d", c.bin_tile_size, c.tile_size);
+        return GS_ERR_INVALID_ARG;
+    }
+    if (c.bin_tile_size > 32) {
+        snprintf(msg, n, "bin_tile_size=%d above 32", c.bin_tile_size);
+        return GS_ERR_INVALID_ARG;
+    }
     return GS_OK;
 }
 
@@ -414,6 +453,7 @@ void gs_config_default(gs_config* cfg) {
     cfg->pixels_per_thread = 0;
     cfg->batch = 0;
     cfg->deterministic = 0;
+    cfg->bin_tile_size = 0;
 }
 
 const char* gs_version(void) { return "gs_b300 0.1 (sm_103a)"; }
@@ -514,9 +554,9 @@ int gs_project(gs_ctx* ctx, const gs_gaussians* g, const gs_view* views, int n_v
     GaussPtrs gp;
     if ((rc = check_gaussians(ctx, g, views, n_views, gp))) return rc;
     DeviceGuard dg(ctx->device);
-    BatchParam bp;
-    make_batch(ctx->cfg, views, n_views, bp);
-    const WsPtrs wp = ws_ptrs(ws, L, bp.total_tiles);
+    BatchParam bp;  // records are listed per bin
+    make_batch(ctx->cfg, views, n_views, bp, bin_size_of(ctx->cfg));
+    const WsPtrs wp = ws_ptrs(ws, L);
     cudaError_t e = launch_project(bp, gp, ctx_rc(ctx), wp, reinterpret_cast<cudaStream_t>(stream), ctx->prof);
     return e == cudaSuccess ? GS_OK : cuda_fail(ctx, e, "gs_project");
 }
@@ -528,12 +568,30 @@ int gs_bin(gs_ctx* ctx, const gs_view* views, int n_views, const gs_workspace* w
     int rc = check_ws(ctx, views, n_views, ws, L);
     if (rc) return rc;
     DeviceGuard dg(ctx->device);
-    BatchParam bp;
-    make_batch(ctx->cfg, views, n_views, bp);
-    WsPtrs wp = ws_ptrs(ws, L, bp.total_tiles);
+    BatchParam bp;  // at the bin size
+    make_batch(ctx->cfg, views, n_views, bp, bin_size_of(ctx->cfg));
+    WsPtrs wp = ws_ptrs(ws, L);
     wp.log2_alpha_min = ctx_rc(ctx).log2_alpha_min;
     const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    cudaError_t e = launch_bin(bp, wp, ctx->d_status, ctx->d_pairs, s, ctx->prof);
+    RefineGeom geom;
+    int n_tiles = bp.total_tiles;
+    if (wp.refine > 1) {
+        BatchParam bt;  // the compositing tiles
+        make_batch(ctx->cfg, views, n_views, bt);
+        memset(&geom, 0, sizeof(geom));
+        geom.n_views = n_views;
+        geom.ts = bt.tile_size;
+        for (int v = 0; v < n_views; ++v) {
+            geom.bin_off[v] = bp.v[v].tile_off;
+            geom.bins_x[v] = bp.v[v].tiles_x;
+            geom.tile_off[v] = bt.v[v].tile_off;
+            geom.tiles_x[v] = bt.v[v].tiles_x;
+            geom.tiles_y[v] = bt.v[v].tiles_y;
+        }
+        n_tiles = bt.total_tiles;
+    }
+    cudaError_t e = launch_bin(bp, wp, ctx->d_status, ctx->d_pairs, s, ctx->prof, wp.refine > 1 ? &geom : nullptr,
+                               n_tiles);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "gs_bin");
     if (wp.sorted_buf != sorted_buffer(bp.total_tiles))
         return fail(ctx, GS_ERR_CUDA, "gs_bin: sorted buffer parity mismatch");
@@ -560,7 +618,7 @@ int gs_render_fwd(gs_ctx* ctx, const gs_view* views, int n_views, const gs_works
     DeviceGuard dg(ctx->device);
     BatchParam bp;
     make_batch(ctx->cfg, views, n_views, bp);
-    const WsPtrs wp = ws_ptrs(ws, L, bp.total_tiles);
+    const WsPtrs wp = ws_ptrs(ws, L);
     cudaError_t e = launch_render_fwd(bp, ctx_rc(ctx), wp, rgb, T_final, n_contrib, n_used, nullptr, nullptr,
                                       nullptr, reinterpret_cast<cudaStream_t>(stream), ctx->prof);
     return e == cudaSuccess ? GS_OK : cuda_fail(ctx, e, "gs_render_fwd");
@@ -578,7 +636,7 @@ int gs_render_fwd_l1(gs_ctx* ctx, const gs_view* views, int n_views, const gs_wo
     DeviceGuard dg(ctx->device);
     BatchParam bp;
     make_batch(ctx->cfg, views, n_views, bp);
-    const WsPtrs wp = ws_ptrs(ws, L, bp.total_tiles);
+    const WsPtrs wp = ws_ptrs(ws, L);
     cudaError_t e = launch_render_fwd(bp, ctx_rc(ctx), wp, rgb, T_final, n_contrib, n_used, target, dL_drgb,
                                       loss_dev, reinterpret_cast<cudaStream_t>(stream), ctx->prof);
     return e == cudaSuccess ? GS_OK : cuda_fail(ctx, e, "gs_render_fwd_l1");
@@ -594,7 +652,7 @@ int gs_l1_loss(gs_ctx* ctx, const gs_view* views, int n_views, const gs_workspac
     DeviceGuard dg(ctx->device);
     BatchParam bp;
     make_batch(ctx->cfg, views, n_views, bp);
-    const WsPtrs wp = ws_ptrs(ws, L, bp.total_tiles);
+    const WsPtrs wp = ws_ptrs(ws, L);
     cudaError_t e = launch_l1(bp, wp, rgb, target, dL_drgb, loss_dev, reinterpret_cast<cudaStream_t>(stream), ctx->prof);
     return e == cudaSuccess ? GS_OK : cuda_fail(ctx, e, "gs_l1_loss");
 }
@@ -703,7 +761,7 @@ int render_bwd_impl(gs_ctx* ctx, const gs_gaussians* g, const gs_view* views, in
     DeviceGuard dg(ctx->device);
     BatchParam bp;
     make_batch(ctx->cfg, views, n_views, bp);
-    const WsPtrs wp = ws_ptrs(ws, L, bp.total_tiles);
+    const WsPtrs wp = ws_ptrs(ws, L);
     const RenderConst rcst = ctx_rc(ctx);
     const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     cudaError_t e = launch_render_bwd(bp, rcst, wp, T_final, n_contrib, dL_drgb, s, ctx->prof);
@@ -898,7 +956,7 @@ int gs_pose_normal(gs_ctx* ctx, const gs_gaussians* g, const gs_view* views, int
     DeviceGuard dg(ctx->device);
     BatchParam bp;
     make_batch(ctx->cfg, views, n_views, bp);
-    const WsPtrs wp = ws_ptrs(ws, L, bp.total_tiles);
+    const WsPtrs wp = ws_ptrs(ws, L);
     const RenderConst rcst = ctx_rc(ctx);
     const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     float4* tangents = reinterpret_cast<float4*>(scratch);

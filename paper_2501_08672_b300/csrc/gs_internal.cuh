@@ -117,7 +117,9 @@ struct WsPtrs {
     uint32_t* pvals[2];      // [cap]
     uint32_t* hist;          // [256 * radix tiles]
     uint32_t* hist_part;     // look-back scan: [radix scan chunks + 1] 64-bit flags, then the ticket
-    uint2* ranges;           // [T]
+    uint2* ranges;           // [T] per compositing tile, into tile_list_vals()
+    uint2* ranges_bin;       // [bins] per bin, into pvals[sorted_buf] (== ranges when refine == 1)
+    uint32_t* rvals;         // [refine^2 cap] per-tile lists split from the bin lists (refine > 1)
     uint32_t* okeys[2];      // [T] tile-order keys
     uint32_t* ovals[2];      // [T] tiles, longest list first (buffer 1 after the sort)
     float* grad2d;           // [M][9]
@@ -131,6 +133,23 @@ struct WsPtrs {
     int scan_blocks;
     float log2_alpha_min;    // -inf in exact mode (every tile of the box is reached)
     int sorted_buf;          // which pvals buffer holds the sorted pairs
+    int refine;              // bin side / tile side: 1 (bins are the tiles), 2 or 4
+};
+
+// The records of every compositing tile's list: the sorted pairs, or with
+// bins of refine x refine tiles the per-tile lists split from them.
+inline const uint32_t* tile_list_vals(const WsPtrs& ws) {
+    return ws.refine > 1 ? ws.rvals : ws.pvals[ws.sorted_buf];
+}
+// Entries of that buffer (the tile ranges stay below it).
+inline long long tile_list_cap(const WsPtrs& ws) { return ws.cap * ws.refine * ws.refine; }
+
+// Geometry of the split of bin lists into tile lists: per view, its first
+// bin and bins per row, and its first tile and tiles per row and column.
+struct RefineGeom {
+    int n_views, ts;
+    int bin_off[kMaxViews], bins_x[kMaxViews];
+    int tile_off[kMaxViews], tiles_x[kMaxViews], tiles_y[kMaxViews];
 };
 
 // ---- depth-key range ------------------------------------------------------
@@ -298,7 +317,7 @@ __device__ __forceinline__ bool footrows_span(const FootRows& f, int ty, int ts,
     const float xr = __fmul_rn(__fadd_rn(__fmul_rn(-f.B, dR), sR), f.invA);
     const float xl = __fmul_rn(__fadd_rn(__fmul_rn(-f.B, dL), -sL), f.invA);
     // tile tx is reached when tx ts + 0.5 <= qx + xr and tx ts + ts - 0.5 >= qx + xl
-    const float inv_ts = 1.f / (float)ts;
+    const float inv_ts = __int_as_float((128 - __ffs(ts)) << 23);  // 1 / ts, exact (ts a power of two)
     const int ta = max(tx0, (int)ceilf(__fmul_rn(__fadd_rn(__fadd_rn(f.qx, xl), 0.5f), inv_ts) - 1.f));
     const int tb = min(tx1 - 1, (int)floorf(__fmul_rn(__fadd_rn(__fadd_rn(f.qx, xr), -0.5f), inv_ts)));
     if (ta > tb) return false;
@@ -361,8 +380,11 @@ struct Prof {
 
 cudaError_t launch_project(const BatchParam& bp, const GaussPtrs& g, const RenderConst& rc,
                            const WsPtrs& ws, cudaStream_t s, Prof& pf);
+// bp: the batch at the bin size; with ws.refine > 1, geom and n_tiles give
+// the compositing tiles the bin lists are split into.
 cudaError_t launch_bin(const BatchParam& bp, WsPtrs& ws, unsigned int* status,
-                       unsigned long long* status_pairs, cudaStream_t s, Prof& pf);
+                       unsigned long long* status_pairs, cudaStream_t s, Prof& pf,
+                       const RefineGeom* geom = nullptr, int n_tiles = 0);
 bool raster_variant_exists(int ts, int ppt, int batch);
 cudaError_t measure_alu(int sm_count, float* sink, cudaStream_t s, double* ffma_tflops, double* ex2_gops);
 size_t selftest_wait_scratch_bytes();

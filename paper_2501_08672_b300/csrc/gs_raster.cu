@@ -1015,14 +1015,14 @@ cudaError_t launch_render_fwd(const BatchParam& bp, const RenderConst& rc_in, co
                               float* rgb, float* T_final, uint32_t* n_contrib, uint32_t* n_used,
                               const float* target, float* dL_drgb, float* loss, cudaStream_t s, Prof& pf) {
     RenderConst rc = rc_in;
-    rc.cap = ws.cap;
+    rc.cap = tile_list_cap(ws);
     if (bp.total_tiles <= 0) {
         // no pixels: the loss is 0 (the caller's views are all non-empty, so
         // this is unreachable through the C ABI; kept for safety)
         if (target && loss) return cudaMemsetAsync(loss, 0, sizeof(float), s);
         return cudaSuccess;
     }
-    const uint32_t* svals = ws.pvals[ws.sorted_buf];
+    const uint32_t* svals = tile_list_vals(ws);
     float* partials = target ? ws.partials : nullptr;
     const int pi = pf.begin(GS_KF_RASTER_FWD, s);
     bool done = false;
@@ -1048,7 +1048,7 @@ cudaError_t launch_render_bwd(const BatchParam& bp, const RenderConst& rc_in, co
                               const float* T_final, const uint32_t* n_contrib,
                               const float* dL_drgb, cudaStream_t s, Prof& pf) {
     RenderConst rc = rc_in;
-    rc.cap = ws.cap;
+    rc.cap = tile_list_cap(ws);
     // deterministic form: per-pair partials, then a fixed-order sum per record
     // (which writes every record, so no clearing)
     const bool det = ws.pair_grad != nullptr;
@@ -1058,7 +1058,7 @@ cudaError_t launch_render_bwd(const BatchParam& bp, const RenderConst& rc_in, co
         e = cudaMemsetAsync(ws.grad2d, 0, sizeof(float) * kGrad2D * (size_t)bp.total_recs, s);
     }
     if (e != cudaSuccess || bp.total_tiles <= 0) return e;
-    const uint32_t* svals = ws.pvals[ws.sorted_buf];
+    const uint32_t* svals = tile_list_vals(ws);
     const int pi = pf.begin(GS_KF_RASTER_BWD, s, det ? 2 : 1);
     bool done = false;
 #define GS_X(T, P, B)                                                                                      \
@@ -1222,9 +1222,9 @@ cudaError_t launch_pose_normal(const BatchParam& bp, const RenderConst& rc_in, c
                                const float4* tangents, const float* target, float* partials, double* normal,
                                float* H_pix, cudaStream_t s, Prof& pf) {
     RenderConst rc = rc_in;
-    rc.cap = ws.cap;
+    rc.cap = tile_list_cap(ws);
     if (bp.total_tiles <= 0) return cudaSuccess;
-    const uint32_t* svals = ws.pvals[ws.sorted_buf];
+    const uint32_t* svals = tile_list_vals(ws);
     const int pi = pf.begin(GS_KF_POSE_NORMAL, s, 2);
     if (bp.tile_size == 8)
         pdl_launch(k_render_pose_normal<8>, bp.total_tiles, 64, 0, s, bp, rc, ws.rec, ws.ranges, ws.ovals[1], svals,

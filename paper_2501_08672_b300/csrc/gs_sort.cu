@@ -837,6 +837,120 @@ __global__ void __launch_bounds__(256) k_ranges(const uint32_t* __restrict__ key
     }
 }
 
+// Split of the bin lists into tile lists.  A bin is an F x F block of
+// compositing tiles (F = 2 or 4); its list is front to back.  First, one
+// thread per sorted pair finds which of its bin's tiles the record's
+// alpha >= alpha_min footprint reaches (per tile row of the bin, the columns
+// footrows_span gives: the binning's own test at the tile size) and stores
+// that mask over the pair's key (the bin id, no longer needed once the bin
+// ranges are taken).  Then one warp per bin walks the masks in list order
+// and appends each record to the lists of the tiles in its mask (ballot and
+// prefix count per tile), so every tile list stays front to back and holds
+// the records binning at the tile size lists.  Tile s of the bin (row-major)
+// writes its list at F^2 start + s len, where [start, start + len) is the
+// bin's range (room for every record of the bin), and its range goes to
+// ranges[tile]; tiles past the image edge get none.
+__device__ __forceinline__ int refine_view(const RefineGeom& g, int bin) {
+    int lo = 0, hi = g.n_views - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (g.bin_off[mid] <= bin) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <int F>
+__global__ void __launch_bounds__(256) k_refine_mask(const __grid_constant__ RefineGeom g, int n_bins,
+                                                     uint32_t* __restrict__ keys, const uint32_t* __restrict__ vals,
+                                                     const float4* __restrict__ rec, float log2_alpha_min, long long cap,
+                                                     const unsigned long long* __restrict__ n_dev) {
+    pdl_wait();
+    pdl_trigger();
+    const unsigned long long n = clamp_n((unsigned long long)cap, n_dev);
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const uint32_t bin = keys[i];
+        uint32_t hits = 0;
+        if (bin < (uint32_t)n_bins) {
+            const int v = refine_view(g, (int)bin);
+            const int lb = (int)bin - g.bin_off[v];
+            const int by = lb / g.bins_x[v], bx = lb - by * g.bins_x[v];
+            const int tx0 = bx * F, ty0 = by * F;
+            const int tx1 = min(tx0 + F, g.tiles_x[v]), ty1 = min(ty0 + F, g.tiles_y[v]);
+            const uint32_t r = vals[i];
+            const float4 r0 = rec[3 * r], r1 = rec[3 * r + 1];
+            const FootRows fr = make_footrows(r0, r1, r1.z - log2_alpha_min);
+#pragma unroll
+            for (int sy = 0; sy < F; ++sy) {
+                int a, b;
+                if (ty0 + sy < ty1 && footrows_span(fr, ty0 + sy, g.ts, tx0, tx1, &a, &b))
+                    hits |= ((2u << (b - tx0)) - (1u << (a - tx0))) << (sy * F);
+            }
+        }
+        keys[i] = hits;
+    }
+}
+
+// One block per bin with one warp per tile of the bin (F^2 warps).  The
+// bin's list goes through shared memory in rounds of 32 F^2 records (one per
+// thread, the next round's loads in flight while the current one is split);
+// warp t reads the round's masks 32 at a time and appends the records whose
+// bit t is set to its tile's list, in list order (ballot and prefix count).
+template <int F>
+__global__ void __launch_bounds__(32 * F * F) k_refine_split(const __grid_constant__ RefineGeom g,
+                                                             const uint2* __restrict__ bin_ranges,
+                                                             const uint32_t* __restrict__ masks,
+                                                             const uint32_t* __restrict__ vals, long long cap,
+                                                             uint32_t* __restrict__ rvals,
+                                                             uint2* __restrict__ ranges) {
+    pdl_wait();
+    pdl_trigger();
+    constexpr int S = F * F;
+    constexpr int R = 32 * S;  // records per round
+    __shared__ uint32_t s_m[2][R], s_r[2][R];
+    const int lane = threadIdx.x & 31, t = threadIdx.x >> 5;
+    const int bin = blockIdx.x;
+    const int v = refine_view(g, bin);
+    const int lb = bin - g.bin_off[v];
+    const int by = lb / g.bins_x[v], bx = lb - by * g.bins_x[v];
+    const int tx = bx * F + t % F, ty = by * F + t / F;
+    const bool mine = tx < g.tiles_x[v] && ty < g.tiles_y[v];  // warp-uniform; past the image edge: no tile
+    uint2 rg = bin_ranges[bin];
+    if (!(rg.x <= rg.y && (long long)rg.y <= cap)) rg.y = rg.x;
+    const uint32_t len = rg.y - rg.x;
+    const uint32_t* mk = masks + rg.x;
+    const uint32_t* vl = vals + rg.x;
+    const uint32_t q0 = rg.x * (uint32_t)S + (uint32_t)t * len;
+    uint32_t* out = rvals + q0;
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    uint32_t pos = 0;
+    uint32_t nm = 0, nr = 0;  // this thread's record of the next round
+    if ((uint32_t)threadIdx.x < len) {
+        nm = mk[threadIdx.x];
+        nr = vl[threadIdx.x];
+    }
+    int buf = 0;
+    for (uint32_t c0 = 0; c0 < len; c0 += R, buf ^= 1) {
+        s_m[buf][threadIdx.x] = nm;
+        s_r[buf][threadIdx.x] = nr;
+        __syncthreads();
+        const uint32_t i = c0 + R + threadIdx.x;
+        nm = i < len ? mk[i] : 0u;
+        nr = i < len ? vl[i] : 0u;
+        if (mine) {
+#pragma unroll
+            for (int j = 0; j < S; ++j) {
+                const uint32_t m = s_m[buf][32 * j + lane];  // 0 past the end of the list
+                const bool h = (m >> t) & 1u;
+                const uint32_t b = __ballot_sync(0xffffffffu, h);
+                if (h) out[pos + __popc(b & lt_mask)] = s_r[buf][32 * j + lane];
+                pos += __popc(b);
+            }
+        }
+    }
+    if (mine && lane == 0) ranges[g.tile_off[v] + ty * g.tiles_x[v] + tx] = make_uint2(q0, q0 + pos);
+}
+
 // Deterministic backward: after the tile sort the pair values are emission
 // indices.  Each place p of the tile lists gets its pair's record back, and
 // pair_inv records where each emission index went (~0 for a pair listed in
@@ -939,7 +1053,8 @@ cudaError_t radix_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, c
 }  // namespace
 
 cudaError_t launch_bin(const BatchParam& bp, WsPtrs& ws, unsigned int* status,
-                       unsigned long long* status_pairs, cudaStream_t s, Prof& pf) {
+                       unsigned long long* status_pairs, cudaStream_t s, Prof& pf, const RefineGeom* geom,
+                       int n_tiles) {
     const long long M = bp.total_recs;
     cudaError_t e;
     if (M <= 0) return cudaSuccess;
@@ -987,14 +1102,40 @@ cudaError_t launch_bin(const BatchParam& bp, WsPtrs& ws, unsigned int* status,
     pf.end(pi, s);
     if (e != cudaSuccess) return e;
     ws.sorted_buf = pbuf;
-    // 5. per-tile [start, end)
-    pi = pf.begin(GS_KF_RANGES, s, 3);  // memset, ranges, keys
-    e = cudaMemsetAsync(ws.ranges, 0, sizeof(uint2) * (size_t)bp.total_tiles, s);
+    // 5. per-bin [start, end)
+    const bool refine = ws.refine > 1 && geom;
+    if (ws.refine > 1 && !geom) return cudaErrorInvalidValue;
+    if (!refine) n_tiles = bp.total_tiles;
+    uint2* bin_ranges = refine ? ws.ranges_bin : ws.ranges;
+    pi = pf.begin(GS_KF_RANGES, s, 2);  // memset, ranges
+    e = cudaMemsetAsync(bin_ranges, 0, sizeof(uint2) * (size_t)bp.total_tiles, s);
     if (e != cudaSuccess) return e;
-    pdl_launch(k_ranges, 1184, 256, 0, s, ws.pkeys[pbuf], ws.cap, ws.counters, (uint32_t)bp.total_tiles, ws.ranges);
-    pdl_launch(k_tile_keys, (bp.total_tiles + 255) / 256, 256, 0, s, ws.ranges, bp.total_tiles, ws.okeys[0], ws.ovals[0]);
+    pdl_launch(k_ranges, 1184, 256, 0, s, ws.pkeys[pbuf], ws.cap, ws.counters, (uint32_t)bp.total_tiles, bin_ranges);
+    pf.end(pi, s);
+    // 6. bins of F x F tiles: each bin's list split into its tiles' lists
+    //    (every tile's range written, so no clearing)
+    if (refine) {
+        pi = pf.begin(GS_KF_REFINE, s, 2);
+        if (ws.refine == 2) {
+            pdl_launch(k_refine_mask<2>, 1184, 256, 0, s, *geom, bp.total_tiles, ws.pkeys[pbuf], ws.pvals[pbuf],
+                       ws.rec, ws.log2_alpha_min, ws.cap, ws.counters);
+            pdl_launch(k_refine_split<2>, bp.total_tiles, 32 * 4, 0, s, *geom, bin_ranges, ws.pkeys[pbuf],
+                       ws.pvals[pbuf], ws.cap, ws.rvals, ws.ranges);
+        } else if (ws.refine == 4) {
+            pdl_launch(k_refine_mask<4>, 1184, 256, 0, s, *geom, bp.total_tiles, ws.pkeys[pbuf], ws.pvals[pbuf],
+                       ws.rec, ws.log2_alpha_min, ws.cap, ws.counters);
+            pdl_launch(k_refine_split<4>, bp.total_tiles, 32 * 16, 0, s, *geom, bin_ranges, ws.pkeys[pbuf],
+                       ws.pvals[pbuf], ws.cap, ws.rvals, ws.ranges);
+        } else {
+            return cudaErrorInvalidValue;
+        }
+        pf.end(pi, s);
+    }
+    // 7. longest-list-first order of the compositing tiles
+    pi = pf.begin(GS_KF_RANGES, s, 1);  // keys; radix_sort counts its own launches
+    pdl_launch(k_tile_keys, (n_tiles + 255) / 256, 256, 0, s, ws.ranges, n_tiles, ws.okeys[0], ws.ovals[0]);
     int obuf = 0;
-    e = radix_sort(ws.okeys[0], ws.ovals[0], ws.okeys[1], ws.ovals[1], ws, (unsigned long long)bp.total_tiles,
+    e = radix_sort(ws.okeys[0], ws.ovals[0], ws.okeys[1], ws.ovals[1], ws, (unsigned long long)n_tiles,
                    nullptr, 8, &obuf, status, s, pf);
     pf.end(pi, s);
     if (e != cudaSuccess) return e;

@@ -641,17 +641,31 @@ RASTER_VARIANTS = [(8, 1, 128), (8, 1, 256), (8, 2, 128), (8, 2, 256),
                    (16, 8, 256), (32, 4, 256), (32, 8, 128), (32, 8, 256)]
 
 
+def launch_candidates(deterministic=False):
+    """The launch shapes autotune times: every compiled (tile size, pixels
+    per thread, batch) with binning at the tile size (bin 0), and, outside
+    the deterministic mode, with bins of 2 and 4 times the tile size (at most
+    32 pixels) split into per-tile lists."""
+    out = [v + (0,) for v in RASTER_VARIANTS]
+    if not deterministic:
+        out += [v + (b,) for v in RASTER_VARIANTS for b in (2 * v[0], 4 * v[0]) if b <= 32]
+    return out
+
+
 def autotune(params, views, targets, candidates=None, steps=3, device=0, storage=None, verbose=False, **cfg):
-    """Picks the fastest (tile size, pixels per thread, batch) for this window
-    and batch of views by timing whole optimisation iterations (projection to
-    Adam, lr = 0 so the parameters do not move) with CUDA events on the
-    launching stream; cfg: further configuration (e.g. deterministic=1).
-    Returns (best, table) with table[(ts, ppt, batch)] = ms per iteration."""
-    cands = candidates or RASTER_VARIANTS
+    """Picks the fastest (tile size, pixels per thread, batch, bin tile size)
+    for this window and batch of views by timing whole optimisation
+    iterations (projection to Adam, lr = 0 so the parameters do not move)
+    with CUDA events on the launching stream; cfg: further configuration
+    (e.g. deterministic=1).  Returns (best, table) with table[(ts, ppt,
+    batch, bin)] = ms per iteration (bin 0: binning at the tile size)."""
+    cands = candidates or launch_candidates(bool(cfg.get("deterministic", 0)))
     table = {}
-    for ts, ppt, batch in cands:
+    for cand in cands:
+        ts, ppt, batch = cand[:3]
+        bin_ts = cand[3] if len(cand) > 3 else 0
         opt = WindowOptimizer(params, views, targets, lr=0.0, device=device, tile_size=ts, storage=storage,
-                              pixels_per_thread=ppt, batch=batch, **cfg)
+                              pixels_per_thread=ppt, batch=batch, bin_tile_size=bin_ts, **cfg)
         opt.step(count=True)
         opt.step(count=False)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -664,9 +678,10 @@ def autotune(params, views, targets, candidates=None, steps=3, device=0, storage
         rc, _ = opt.r.check_status()
         if rc != B.GS_OK:
             continue
-        table[(ts, ppt, batch)] = a.elapsed_time(b) / steps
+        table[(ts, ppt, batch, bin_ts)] = a.elapsed_time(b) / steps
         if verbose:
-            print("autotune tile %2d ppt %d batch %3d: %.3f ms" % (ts, ppt, batch, table[(ts, ppt, batch)]))
+            print("autotune tile %2d ppt %d batch %3d bin %2d: %.3f ms" % (ts, ppt, batch, bin_ts,
+                                                                       table[(ts, ppt, batch, bin_ts)]))
         del opt
     best = min(table, key=table.get)
     return best, table

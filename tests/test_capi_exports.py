@@ -56,6 +56,27 @@ def test_host_only_calls_work_without_a_gpu(lib):
     assert lib.gs_project(None, None, None, 0, None, None) == B.GS_ERR_INVALID_ARG
 
 
+@pytest.mark.parametrize("ts,bin_ts,ok", [(8, 0, True), (8, 8, True), (8, 16, True), (8, 32, True), (16, 32, True),
+                                          (32, 32, True), (8, 24, False), (16, 8, False), (16, 64, False),
+                                          (32, 64, False), (8, 12, False)])
+def test_bin_tile_size_is_checked_on_the_host(lib, ts, bin_ts, ok):
+    """gs_config.bin_tile_size must be 0 or 1, 2 or 4 times the tile size, at
+    most 32; the check runs before any device call (a valid config then
+    fails only for want of a GPU here)."""
+    from paper_2501_08672_b300 import binding as B
+    c = B.Config()
+    lib.gs_config_default(ctypes.byref(c))
+    assert c.bin_tile_size == 0
+    c.tile_size = ts
+    c.pixels_per_thread = 4 if ts == 32 else 2
+    c.bin_tile_size = bin_ts
+    h = ctypes.c_void_p()
+    rc = lib.gs_context_create(ctypes.byref(h), 0, ctypes.byref(c))
+    if rc == B.GS_OK:
+        lib.gs_context_destroy(h)
+    assert (rc != B.GS_ERR_INVALID_ARG) == ok
+
+
 def header_struct_fields(name):
     text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
     m = re.search(r"typedef struct %s \{(.*?)\} %s;" % (name, name), text, flags=re.S)

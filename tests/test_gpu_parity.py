@@ -394,8 +394,9 @@ def test_autotuner_picks_a_compiled_variant():
     p = scenes.box_room_scene(n, seed=18)
     views = scenes.arc_views(2, 160, 128, 150.0, n_gaussians=n)
     _, rt = gpu_forward(p, views)
-    best, table = autotune(p, views, rt.rgb.clone(), candidates=RASTER_VARIANTS[:4] + RASTER_VARIANTS[7:9], steps=1)
-    assert best in RASTER_VARIANTS and len(table) == 6
+    cands = [v + (0,) for v in RASTER_VARIANTS[:4] + RASTER_VARIANTS[7:9]] + [(8, 2, 128, 32), (16, 2, 128, 32)]
+    best, table = autotune(p, views, rt.rgb.clone(), candidates=cands, steps=1)
+    assert best in cands and len(table) == 8
     assert table[best] == min(table.values())
 
 

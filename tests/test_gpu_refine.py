@@ -1,0 +1,139 @@
+"""Binning at a larger bin size split into per-tile lists (gs_config
+bin_tile_size): the per-tile lists against binning at the tile size
+directly, the images bit for bit, and the whole path against the FP64
+oracle."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from paper_2501_08672_b300 import scenes  # noqa: E402
+from paper_2501_08672_b300.render import GaussianWindow, Renderer  # noqa: E402
+
+from test_gpu_parity import (_footprint_min, compare_images, gpu_forward, l1_parity, l1_target,  # noqa: E402
+                             ragged_views, ws_view)
+
+# (tile size, pixels per thread, bin size): factors 2 and 4
+SPLITS = [(8, 2, 16), (8, 2, 32), (8, 1, 32), (16, 2, 32)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+
+
+def tile_lists(r):
+    torch.cuda.synchronize()
+    L = r.layout()
+    T = L.n_tiles
+    rg = ws_view(r, L.tile_ranges, np.uint32, 2 * T).reshape(T, 2)
+    sv = ws_view(r, L.sorted_vals, np.uint32, int(rg[:, 1].max()) if T else 0)
+    return [sv[a:b].copy() for a, b in rg], L
+
+
+def render(win, views, ts, ppt, bin_ts):
+    r = Renderer(views, 0, ts, pixels_per_thread=ppt, batch=128, bin_tile_size=bin_ts)
+    r.forward(win.struct())
+    torch.cuda.synchronize()
+    return r
+
+
+def _is_subsequence(a, b):
+    it = iter(b.tolist())
+    return all(x in it for x in a.tolist())
+
+
+@pytest.mark.parametrize("ts,ppt,bin_ts", SPLITS)
+def test_split_lists_match_binning_at_the_tile_size(ts, ppt, bin_ts):
+    """Ragged views (sizes not multiples of the bin, so edge bins hold tiles
+    past the image): every per-tile list split from the bins holds the list
+    that binning at the tile size gives, in the same order, plus at most
+    records whose footprint only grazes the tile (within the binning test's
+    margin); the images, T and the loss gradient inputs agree bit for bit."""
+    n = 6000
+    p = scenes.frustum_scene(n, seed=31)
+    views = ragged_views(n)
+    win = GaussianWindow(p, 0)
+    r0 = render(win, views, ts, ppt, 0)
+    r1 = render(win, views, ts, ppt, bin_ts)
+    l0, L0 = tile_lists(r0)
+    l1, L1 = tile_lists(r1)
+    assert L1.bin_size == bin_ts and L1.n_tiles == L0.n_tiles and L1.n_bins < L0.n_tiles
+    assert int(r1.last_pairs) < int(r0.last_pairs)
+    M = L1.n_records
+    rec = ws_view(r1, L1.records, np.float32, 12 * M).reshape(M, 12)
+    log2_amin = math.log2(1.0 / 255.0)
+    tile_xy = []
+    for v in views:
+        tx_n = (v["W"] + ts - 1) // ts
+        ty_n = (v["H"] + ts - 1) // ts
+        tile_xy += [(tx, ty) for ty in range(ty_n) for tx in range(tx_n)]
+    extra = 0
+    for t, (a, b) in enumerate(zip(l0, l1)):
+        assert _is_subsequence(a, b), "tile %d: the direct list is not a subsequence of the split one" % t
+        for i in set(b.tolist()) - set(a.tolist()):
+            tx, ty = tile_xy[t]
+            m = _footprint_min(rec[i], tx * ts + 0.5, tx * ts + ts - 0.5, ty * ts + 0.5, ty * ts + ts - 0.5)
+            Lim = float(rec[i, 6]) - log2_amin
+            assert m > Lim * (1 - 1e-4), "tile %d: record %d clearly reached yet missing from the direct list" % (t, i)
+            assert m <= Lim * 1.01 + 0.01, "tile %d: record %d clearly missed yet listed" % (t, i)
+            extra += 1
+    total = sum(len(a) for a in l0)
+    assert extra <= 1e-3 * total + 3
+    # front to back along every split list
+    depth = rec[:, 10].astype(np.float64)
+    for t, b in enumerate(l1):
+        d = depth[b]
+        assert np.all(d[1:] >= d[:-1] - 1e-6 * np.abs(d[:-1])), "tile %d is not front to back" % t
+    assert torch.equal(r0.rgb, r1.rgb) and torch.equal(r0.T, r1.T)
+
+
+def test_split_applies_only_in_truncated_mode_without_determinism():
+    """Exact mode and the deterministic backward bin at the tile size."""
+    n = 2000
+    p = scenes.frustum_scene(n, seed=32)
+    views = ragged_views(n)
+    for cfg in (dict(alpha_min=0.0, alpha_max=1.0, T_min=0.0), dict(deterministic=1)):
+        _, r = gpu_forward(p, views, tile_size=8, bin_tile_size=32, **cfg)
+        L = r.layout()
+        assert L.bin_size == 8 and L.n_bins == L.n_tiles and L.sorted_vals == L.bin_vals
+
+
+@pytest.mark.parametrize("ts,ppt,bin_ts", [(8, 2, 32), (16, 2, 32)])
+def test_split_path_matches_oracle(orc, ts, ppt, bin_ts):
+    """Forward images and the L1 loss's gradients (every parameter group and
+    the pose) through the split lists against the FP64 oracle."""
+    p = scenes.frustum_scene(1500, seed=33)
+    views = ragged_views(1500)
+    win, r = gpu_forward(p, views, tile_size=ts, pixels_per_thread=ppt, batch=128, bin_tile_size=bin_ts)
+    for v, img, T in zip(views, r.images(), B_unpack_T(r, views)):
+        out = orc.render_view(p, v)
+        compare_images(out, img.cpu().numpy(), T)
+    l1_parity(orc, win, r, p, views, l1_target(p, views))
+
+
+def B_unpack_T(r, views):
+    out, off = [], 0
+    T = r.T.cpu().numpy()
+    for v in views:
+        n = v["W"] * v["H"]
+        out.append(T[off:off + n].reshape(v["H"], v["W"]))
+        off += n
+    return out
+
+
+def test_box_room_window_split_matches_oracle(orc):
+    """The box-room window (SH degree 1) with 8 x 8 tiles from 32 x 32 bins,
+    the headline's launch shape, against the oracle."""
+    n = 20_000
+    p = scenes.box_room_scene(n, seed=34)
+    views = scenes.arc_views(3, 192, 160, 180.0, n_gaussians=n)
+    views[1] = dict(views[1], W=176, H=144, cx=88.0, cy=72.0)
+    win, r = gpu_forward(p, views, tile_size=8, pixels_per_thread=2, batch=128, bin_tile_size=32)
+    assert r.layout().bin_size == 32
+    l1_parity(orc, win, r, p, views, l1_target(p, views))
