@@ -154,7 +154,7 @@ int make_layout(gs_ctx* ctx, const gs_config& cfg, const gs_view* views, int n_v
     if (max_pairs < 0 || max_pairs > 0x7FFFFFFFll)
         return fail(ctx, GS_ERR_INVALID_ARG, "max_pairs=%lld outside [0, 2^31)", (long long)max_pairs);
     const int ts = cfg.tile_size;
-    const int bs = bin_size_of(cfg);
+    int bs = bin_size_of(cfg);
     long long M = 0, P = 0, T = 0, Tb = 0, max_px = 0, max_g_end = 0;
     for (int v = 0; v < n_views; ++v) {
         const gs_view& V = views[v];
@@ -182,6 +182,12 @@ int make_layout(gs_ctx* ctx, const gs_config& cfg, const gs_view* views, int n_v
     if (M >= 0xFFFFFFFFll) return fail(ctx, GS_ERR_INVALID_ARG, "too many (view, Gaussian) records: %lld", M);
     if (T >= 0x7FFFFFFFll) return fail(ctx, GS_ERR_INVALID_ARG, "too many tiles: %lld", T);
 
+    // the pair keys hold a bin id below the F^2-bit tile mask, and the id
+    // 2^(32 - F^2) - 1 marks unlisted pairs: with more bins, bin at the tile size
+    if (bs != ts && Tb >= (1ll << (32 - (bs / ts) * (bs / ts))) - 1) {
+        bs = ts;
+        Tb = T;
+    }
     const long long cap = max_pairs;
     L.refine = bs / ts;
     L.bin_tiles = (int)Tb;
@@ -555,7 +561,7 @@ int gs_project(gs_ctx* ctx, const gs_gaussians* g, const gs_view* views, int n_v
     if ((rc = check_gaussians(ctx, g, views, n_views, gp))) return rc;
     DeviceGuard dg(ctx->device);
     BatchParam bp;  // records are listed per bin
-    make_batch(ctx->cfg, views, n_views, bp, bin_size_of(ctx->cfg));
+    make_batch(ctx->cfg, views, n_views, bp, L.pub.bin_size);
     const WsPtrs wp = ws_ptrs(ws, L);
     cudaError_t e = launch_project(bp, gp, ctx_rc(ctx), wp, reinterpret_cast<cudaStream_t>(stream), ctx->prof);
     return e == cudaSuccess ? GS_OK : cuda_fail(ctx, e, "gs_project");
@@ -569,7 +575,7 @@ int gs_bin(gs_ctx* ctx, const gs_view* views, int n_views, const gs_workspace* w
     if (rc) return rc;
     DeviceGuard dg(ctx->device);
     BatchParam bp;  // at the bin size
-    make_batch(ctx->cfg, views, n_views, bp, bin_size_of(ctx->cfg));
+    make_batch(ctx->cfg, views, n_views, bp, L.pub.bin_size);
     WsPtrs wp = ws_ptrs(ws, L);
     wp.log2_alpha_min = ctx_rc(ctx).log2_alpha_min;
     const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);

@@ -596,6 +596,24 @@ __device__ __forceinline__ uint32_t warp_exclusive_scan(uint32_t v, uint32_t* to
     return x - v;
 }
 
+// F > 1 (bins of F x F compositing tiles, split later): each pair's key
+// also carries, above its bin id (bits from 32 - F^2 up), the mask of the
+// bin's tiles the record's footprint reaches, row-major: per tile row of the
+// bin the columns footrows_span gives at the tile size ts / F (the binning's
+// own test, so the split lists are those of binning at the tile size).
+template <int F>
+__device__ __forceinline__ uint32_t tile_mask(const FootRows& fr, int bx, int by, int tts) {
+    uint32_t m = 0;
+#pragma unroll
+    for (int sy = 0; sy < F; ++sy) {
+        int a, b;
+        if (footrows_span(fr, by * F + sy, tts, bx * F, bx * F + F, &a, &b))
+            m |= ((2u << (b - bx * F)) - (1u << (a - bx * F))) << (sy * F);
+    }
+    return m << (32 - F * F);
+}
+
+template <int F>
 __global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ order,
                                               const uint32_t* __restrict__ touched,
                                               const uint32_t* __restrict__ hitmask,
@@ -651,6 +669,8 @@ __global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ order
         const uint32_t key0 = (uint32_t)rc.z + (uint32_t)ty0 * (uint32_t)rc.w + (uint32_t)tx0;
         // floor(b / w) = (b * ceil(2048 / w)) >> 11 for b < 32, w <= 32
         const uint32_t info = mp ? ((uint32_t)w | ((2048u + (uint32_t)w - 1u) / (uint32_t)w) << 8 | 0x80000000u) : 0u;
+        FootRows mf{};  // the record's footprint rows, for the tile masks of F > 1
+        if (F > 1 && mp) mf = make_footrows(rec[3 * r], rec[3 * r + 1], rec[3 * r + 1].z - log2_alpha_min);
         for (uint32_t p0 = 0; p0 < wtotal; p0 += 32) {
             const uint32_t pr = p0 + (uint32_t)lane;
             int e = 0;
@@ -665,6 +685,20 @@ __global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ order
             const uint32_t se = (uint32_t)__shfl_sync(0xffffffffu, rc.w, e);
             const uint32_t re = __shfl_sync(0xffffffffu, r, e);
             const uint32_t be = __shfl_sync(0xffffffffu, rel, e);
+            FootRows ef{};  // the owner's footprint rows (F > 1)
+            uint32_t rx = 0;
+            if constexpr (F > 1) {
+                ef.qx = __shfl_sync(0xffffffffu, mf.qx, e);
+                ef.qy = __shfl_sync(0xffffffffu, mf.qy, e);
+                ef.A = __shfl_sync(0xffffffffu, mf.A, e);
+                ef.B = __shfl_sync(0xffffffffu, mf.B, e);
+                ef.det = __shfl_sync(0xffffffffu, mf.det, e);
+                ef.invA = __shfl_sync(0xffffffffu, mf.invA, e);
+                ef.ymax = __shfl_sync(0xffffffffu, mf.ymax, e);
+                ef.dyr = __shfl_sync(0xffffffffu, mf.dyr, e);
+                ef.lim = __shfl_sync(0xffffffffu, mf.lim, e);
+                rx = (uint32_t)__shfl_sync(0xffffffffu, rc.x, e);
+            }
             const unsigned long long q = wbase + pr;
             if (pr < wtotal && (ie >> 31) && q < ucap) {
                 // the (pr - be)-th set bit of the mask (0 based), by halving
@@ -681,7 +715,11 @@ __global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ order
                 const bool found = (m & 1u) && jj == 0;  // else the mask holds fewer bits than counted
                 const uint32_t we = ie & 0xFFu, mul = (ie >> 8) & 0xFFFu;
                 const uint32_t row = (bit * mul) >> 11;
-                pkeys[q] = found ? ke + row * se + (bit - row * we) : 0xFFFFFFFFu;
+                uint32_t key = found ? ke + row * se + (bit - row * we) : 0xFFFFFFFFu;
+                if (F > 1 && found)
+                    key |= tile_mask<F>(ef, (int)(rx & 0xFFFFu) + (int)(bit - row * we), (int)(rx >> 16) + (int)row,
+                                        ts / F);
+                pkeys[q] = key;
                 put_val(q, re);
             }
         }
@@ -741,7 +779,9 @@ __global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ order
                 const uint32_t se = __shfl_sync(0xffffffffu, start, e);
                 const unsigned long long q = o + pr;
                 if (pr < total && q < boend && q < ucap) {
-                    pkeys[q] = bz + (uint32_t)(row0 + e) * bwid + (uint32_t)ae + (pr - se);
+                    uint32_t key = bz + (uint32_t)(row0 + e) * bwid + (uint32_t)ae + (pr - se);
+                    if (F > 1) key |= tile_mask<F>(bf, ae + (int)(pr - se), row0 + e, ts / F);
+                    pkeys[q] = key;
                     put_val(q, br);
                 }
             }
@@ -783,7 +823,7 @@ __global__ void k_tile_keys(const uint2* __restrict__ ranges, int n_tiles, uint3
 // 256-byte aligned); the neighbours across threads come by warp shuffles.
 __global__ void __launch_bounds__(256) k_ranges(const uint32_t* __restrict__ keys, long long cap,
                                                 const unsigned long long* __restrict__ n_dev, uint32_t n_tiles,
-                                                uint2* __restrict__ ranges) {
+                                                uint32_t key_bits_mask, uint2* __restrict__ ranges) {
     pdl_wait();
     pdl_trigger();
     const unsigned long long n = clamp_n((unsigned long long)cap, n_dev);
@@ -804,16 +844,17 @@ __global__ void __launch_bounds__(256) k_ranges(const uint32_t* __restrict__ key
             v[c][0] = v[c][1] = v[c][2] = v[c][3] = 0xFFFFFFFFu;
             if (j0 + 3 < n) {
                 const uint4 q = k4[g];
-                v[c][0] = q.x; v[c][1] = q.y; v[c][2] = q.z; v[c][3] = q.w;
+                v[c][0] = q.x & key_bits_mask; v[c][1] = q.y & key_bits_mask;
+                v[c][2] = q.z & key_bits_mask; v[c][3] = q.w & key_bits_mask;
             } else {
 #pragma unroll
                 for (int i = 0; i < 4; ++i)
-                    if (j0 + i < n) v[c][i] = keys[j0 + i];
+                    if (j0 + i < n) v[c][i] = keys[j0 + i] & key_bits_mask;
             }
             pv[c] = 0xFFFFFFFFu;
             nx[c] = 0xFFFFFFFFu;
-            if (lane == 0 && j0 > 0 && j0 - 1 < n) pv[c] = keys[j0 - 1];
-            if (lane == 31 && j0 + 4 < n) nx[c] = keys[j0 + 4];
+            if (lane == 0 && j0 > 0 && j0 - 1 < n) pv[c] = keys[j0 - 1] & key_bits_mask;
+            if (lane == 31 && j0 + 4 < n) nx[c] = keys[j0 + 4] & key_bits_mask;
         }
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
@@ -859,71 +900,38 @@ __device__ __forceinline__ int refine_view(const RefineGeom& g, int bin) {
     return lo;
 }
 
+// One block per bin, each warp taking TW of the bin's F^2 tiles.  The bin's
+// list goes through shared memory in rounds of one record per thread (the
+// next round's loads in flight while the current one is split); a warp reads
+// the round's masks 32 at a time and appends, for each of its tiles, the
+// records whose mask has the tile's bit to the tile's list, in list order
+// (ballot and prefix count).  The masks sit above the bin ids in the keys.
+constexpr int kSplitTilesPerWarp = 1;  // (4 per warp, one load of the masks for four tiles, measured slower)
 template <int F>
-__global__ void __launch_bounds__(256) k_refine_mask(const __grid_constant__ RefineGeom g, int n_bins,
-                                                     uint32_t* __restrict__ keys, const uint32_t* __restrict__ vals,
-                                                     const float4* __restrict__ rec, float log2_alpha_min, long long cap,
-                                                     const unsigned long long* __restrict__ n_dev) {
-    pdl_wait();
-    pdl_trigger();
-    const unsigned long long n = clamp_n((unsigned long long)cap, n_dev);
-    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const uint32_t bin = keys[i];
-        uint32_t hits = 0;
-        if (bin < (uint32_t)n_bins) {
-            const int v = refine_view(g, (int)bin);
-            const int lb = (int)bin - g.bin_off[v];
-            const int by = lb / g.bins_x[v], bx = lb - by * g.bins_x[v];
-            const int tx0 = bx * F, ty0 = by * F;
-            const int tx1 = min(tx0 + F, g.tiles_x[v]), ty1 = min(ty0 + F, g.tiles_y[v]);
-            const uint32_t r = vals[i];
-            const float4 r0 = rec[3 * r], r1 = rec[3 * r + 1];
-            const FootRows fr = make_footrows(r0, r1, r1.z - log2_alpha_min);
-#pragma unroll
-            for (int sy = 0; sy < F; ++sy) {
-                int a, b;
-                if (ty0 + sy < ty1 && footrows_span(fr, ty0 + sy, g.ts, tx0, tx1, &a, &b))
-                    hits |= ((2u << (b - tx0)) - (1u << (a - tx0))) << (sy * F);
-            }
-        }
-        keys[i] = hits;
-    }
-}
-
-// One block per bin with one warp per tile of the bin (F^2 warps).  The
-// bin's list goes through shared memory in rounds of 32 F^2 records (one per
-// thread, the next round's loads in flight while the current one is split);
-// warp t reads the round's masks 32 at a time and appends the records whose
-// bit t is set to its tile's list, in list order (ballot and prefix count).
-template <int F>
-__global__ void __launch_bounds__(32 * F * F) k_refine_split(const __grid_constant__ RefineGeom g,
-                                                             const uint2* __restrict__ bin_ranges,
-                                                             const uint32_t* __restrict__ masks,
-                                                             const uint32_t* __restrict__ vals, long long cap,
-                                                             uint32_t* __restrict__ rvals,
-                                                             uint2* __restrict__ ranges) {
+__global__ void __launch_bounds__(32 * F * F / kSplitTilesPerWarp) k_refine_split(
+    const __grid_constant__ RefineGeom g, const uint2* __restrict__ bin_ranges, const uint32_t* __restrict__ keys,
+    const uint32_t* __restrict__ vals, long long cap, uint32_t* __restrict__ rvals, uint2* __restrict__ ranges) {
     pdl_wait();
     pdl_trigger();
     constexpr int S = F * F;
-    constexpr int R = 32 * S;  // records per round
+    constexpr int TW = kSplitTilesPerWarp < S ? kSplitTilesPerWarp : S;
+    constexpr int NW = S / TW;
+    constexpr int R = 32 * NW;  // records per round
     __shared__ uint32_t s_m[2][R], s_r[2][R];
-    const int lane = threadIdx.x & 31, t = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int bin = blockIdx.x;
     const int v = refine_view(g, bin);
     const int lb = bin - g.bin_off[v];
     const int by = lb / g.bins_x[v], bx = lb - by * g.bins_x[v];
-    const int tx = bx * F + t % F, ty = by * F + t / F;
-    const bool mine = tx < g.tiles_x[v] && ty < g.tiles_y[v];  // warp-uniform; past the image edge: no tile
     uint2 rg = bin_ranges[bin];
     if (!(rg.x <= rg.y && (long long)rg.y <= cap)) rg.y = rg.x;
     const uint32_t len = rg.y - rg.x;
-    const uint32_t* mk = masks + rg.x;
+    const uint32_t* mk = keys + rg.x;
     const uint32_t* vl = vals + rg.x;
-    const uint32_t q0 = rg.x * (uint32_t)S + (uint32_t)t * len;
-    uint32_t* out = rvals + q0;
     const uint32_t lt_mask = (1u << lane) - 1u;
-    uint32_t pos = 0;
+    uint32_t pos[TW];
+#pragma unroll
+    for (int k = 0; k < TW; ++k) pos[k] = 0u;
     uint32_t nm = 0, nr = 0;  // this thread's record of the next round
     if ((uint32_t)threadIdx.x < len) {
         nm = mk[threadIdx.x];
@@ -937,18 +945,29 @@ __global__ void __launch_bounds__(32 * F * F) k_refine_split(const __grid_consta
         const uint32_t i = c0 + R + threadIdx.x;
         nm = i < len ? mk[i] : 0u;
         nr = i < len ? vl[i] : 0u;
-        if (mine) {
 #pragma unroll
-            for (int j = 0; j < S; ++j) {
-                const uint32_t m = s_m[buf][32 * j + lane];  // 0 past the end of the list
-                const bool h = (m >> t) & 1u;
+        for (int j = 0; j < NW; ++j) {
+            const uint32_t m = s_m[buf][32 * j + lane] >> (32 - S + w * TW);  // 0 past the end of the list
+            const uint32_t rr = s_r[buf][32 * j + lane];
+#pragma unroll
+            for (int k = 0; k < TW; ++k) {
+                const bool h = (m >> k) & 1u;
                 const uint32_t b = __ballot_sync(0xffffffffu, h);
-                if (h) out[pos + __popc(b & lt_mask)] = s_r[buf][32 * j + lane];
-                pos += __popc(b);
+                const int t = w * TW + k;
+                if (h) rvals[rg.x * (uint32_t)S + (uint32_t)t * len + pos[k] + __popc(b & lt_mask)] = rr;
+                pos[k] += __popc(b);
             }
         }
     }
-    if (mine && lane == 0) ranges[g.tile_off[v] + ty * g.tiles_x[v] + tx] = make_uint2(q0, q0 + pos);
+#pragma unroll
+    for (int k = 0; k < TW; ++k) {
+        const int t = w * TW + k;
+        const int tx = bx * F + t % F, ty = by * F + t / F;
+        if (lane == 0 && tx < g.tiles_x[v] && ty < g.tiles_y[v]) {  // past the image edge: no tile
+            const uint32_t q0 = rg.x * (uint32_t)S + (uint32_t)t * len;
+            ranges[g.tile_off[v] + ty * g.tiles_x[v] + tx] = make_uint2(q0, q0 + pos[k]);
+        }
+    }
 }
 
 // Deterministic backward: after the tile sort the pair values are emission
@@ -1080,11 +1099,24 @@ cudaError_t launch_bin(const BatchParam& bp, WsPtrs& ws, unsigned int* status,
     pdl_launch(k_scan_offsets, nb, kScanThreads, 0, s, order, ws.tiles_touched, M, ws.scan_part, nb, ws.offsets,
                ws.counters, ws.cap, status, status_pairs);
     pf.end(pi, s);
-    // 3. expand records into (tile, record) pairs
+    // 3. expand records into (tile, record) pairs; with bins of F x F tiles
+    //    the keys also carry the tile masks of the later split
+    if (ws.refine > 1 && !geom) return cudaErrorInvalidValue;
+    const int F = geom ? ws.refine : 1;
+    if (F != 1 && F != 2 && F != 4) return cudaErrorInvalidValue;
     pi = pf.begin(GS_KF_EMIT, s);
-    pdl_launch(k_emit, (unsigned)((M + 255) / 256), 256, 0, s, order, ws.tiles_touched, ws.hitmask, ws.rect, ws.rec, ws.offsets, M,
-                                                       ws.cap, bp.tile_size, ws.log2_alpha_min, ws.pkeys[0],
-                                                       ws.pvals[0], ws.pair_rec);
+    {
+        const unsigned eg = (unsigned)((M + 255) / 256);
+        if (F == 1)
+            pdl_launch(k_emit<1>, eg, 256, 0, s, order, ws.tiles_touched, ws.hitmask, ws.rect, ws.rec, ws.offsets, M,
+                       ws.cap, bp.tile_size, ws.log2_alpha_min, ws.pkeys[0], ws.pvals[0], ws.pair_rec);
+        else if (F == 2)
+            pdl_launch(k_emit<2>, eg, 256, 0, s, order, ws.tiles_touched, ws.hitmask, ws.rect, ws.rec, ws.offsets, M,
+                       ws.cap, bp.tile_size, ws.log2_alpha_min, ws.pkeys[0], ws.pvals[0], ws.pair_rec);
+        else
+            pdl_launch(k_emit<4>, eg, 256, 0, s, order, ws.tiles_touched, ws.hitmask, ws.rect, ws.rec, ws.offsets, M,
+                       ws.cap, bp.tile_size, ws.log2_alpha_min, ws.pkeys[0], ws.pvals[0], ws.pair_rec);
+    }
     pf.end(pi, s);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // 4. stable sort of pairs by global tile id
@@ -1102,33 +1134,25 @@ cudaError_t launch_bin(const BatchParam& bp, WsPtrs& ws, unsigned int* status,
     pf.end(pi, s);
     if (e != cudaSuccess) return e;
     ws.sorted_buf = pbuf;
-    // 5. per-bin [start, end)
-    const bool refine = ws.refine > 1 && geom;
-    if (ws.refine > 1 && !geom) return cudaErrorInvalidValue;
-    if (!refine) n_tiles = bp.total_tiles;
-    uint2* bin_ranges = refine ? ws.ranges_bin : ws.ranges;
+    // 5. per-bin [start, end) (the keys' bin ids below their tile masks)
+    if (F == 1) n_tiles = bp.total_tiles;
+    uint2* bin_ranges = F > 1 ? ws.ranges_bin : ws.ranges;
     pi = pf.begin(GS_KF_RANGES, s, 2);  // memset, ranges
     e = cudaMemsetAsync(bin_ranges, 0, sizeof(uint2) * (size_t)bp.total_tiles, s);
     if (e != cudaSuccess) return e;
-    pdl_launch(k_ranges, 1184, 256, 0, s, ws.pkeys[pbuf], ws.cap, ws.counters, (uint32_t)bp.total_tiles, bin_ranges);
+    pdl_launch(k_ranges, 1184, 256, 0, s, ws.pkeys[pbuf], ws.cap, ws.counters, (uint32_t)bp.total_tiles,
+               F == 1 ? 0xFFFFFFFFu : (1u << (32 - F * F)) - 1u, bin_ranges);
     pf.end(pi, s);
     // 6. bins of F x F tiles: each bin's list split into its tiles' lists
     //    (every tile's range written, so no clearing)
-    if (refine) {
-        pi = pf.begin(GS_KF_REFINE, s, 2);
-        if (ws.refine == 2) {
-            pdl_launch(k_refine_mask<2>, 1184, 256, 0, s, *geom, bp.total_tiles, ws.pkeys[pbuf], ws.pvals[pbuf],
-                       ws.rec, ws.log2_alpha_min, ws.cap, ws.counters);
-            pdl_launch(k_refine_split<2>, bp.total_tiles, 32 * 4, 0, s, *geom, bin_ranges, ws.pkeys[pbuf],
+    if (F > 1) {
+        pi = pf.begin(GS_KF_REFINE, s, 1);
+        if (F == 2)
+            pdl_launch(k_refine_split<2>, bp.total_tiles, 32 * 4 / kSplitTilesPerWarp, 0, s, *geom, bin_ranges, ws.pkeys[pbuf],
                        ws.pvals[pbuf], ws.cap, ws.rvals, ws.ranges);
-        } else if (ws.refine == 4) {
-            pdl_launch(k_refine_mask<4>, 1184, 256, 0, s, *geom, bp.total_tiles, ws.pkeys[pbuf], ws.pvals[pbuf],
-                       ws.rec, ws.log2_alpha_min, ws.cap, ws.counters);
-            pdl_launch(k_refine_split<4>, bp.total_tiles, 32 * 16, 0, s, *geom, bin_ranges, ws.pkeys[pbuf],
+        else
+            pdl_launch(k_refine_split<4>, bp.total_tiles, 32 * 16 / kSplitTilesPerWarp, 0, s, *geom, bin_ranges, ws.pkeys[pbuf],
                        ws.pvals[pbuf], ws.cap, ws.rvals, ws.ranges);
-        } else {
-            return cudaErrorInvalidValue;
-        }
         pf.end(pi, s);
     }
     // 7. longest-list-first order of the compositing tiles
