@@ -56,8 +56,8 @@ FP32_LANES = 128
 # kernel source they were taken on (sha256 prefix of gs_raster.cu up to the L1
 # kernels, which holds both compositing kernels) and the launch shape;
 # otherwise the roofline reports traffic null.
-TRAFFIC = {"raster_fwd": ("c44f4d8f4e06127b", (16, 2, 128), 181.6e6),
-           "raster_bwd": ("c44f4d8f4e06127b", (16, 2, 128), 237.3e6)}
+TRAFFIC = {"raster_fwd": ("488348665ad73821", (8, 2, 128, 32), 198.8e6),
+           "raster_bwd": ("488348665ad73821", (8, 2, 128, 32), 250.5e6)}
 
 
 def raster_source_hash():
@@ -305,7 +305,7 @@ def run_reference(args, world, rank):
 
 
 def kernel_rooflines(kms, n_gauss, n_records, n_pairs, n_tiles, n_params, param_bytes, lowp_elems, visited,
-                     contrib, ffma_tflops, hbm_gbs):
+                     contrib, ffma_tflops, hbm_gbs, n_bins=None, n_list=None):
     """Achieved fraction of its roofline for every kernel family of one
     iteration, from its CUDA-event time per iteration (kms, ms) and its
     algorithmic work: FP32 FLOP per the fragment model for the compositing
@@ -320,7 +320,12 @@ def kernel_rooflines(kms, n_gauss, n_records, n_pairs, n_tiles, n_params, param_
                    written
       emit         per pair: 8 B (tile key, record index) written
       tile_sort    per pair: 8 B read and 8 B written once
-      ranges       per pair: 4 B key read; per tile 8 B range written
+      ranges       per pair: 4 B key read; per bin 8 B range written
+      refine       (bins of several tiles) per pair 8 B (key with its tile
+                   mask, record index) read; per entry of the tiles' lists
+                   (n_list) 4 B written; per tile 8 B range written
+    A pair is a (bin, record) pair; without bins larger than the tiles a bin
+    is a tile (n_bins = n_tiles, n_list = n_pairs, no refine).
       project_bwd  per record 36 B of 2D gradients read; per Gaussian its
                    parameters read and 4 B per parameter written
       adam         per parameter 28 B (p, g, m, v read; p, m, v written),
@@ -331,7 +336,8 @@ def kernel_rooflines(kms, n_gauss, n_records, n_pairs, n_tiles, n_params, param_
         "tile_scan": ("hbm", n_records * 16.0),
         "emit": ("hbm", n_pairs * 8.0),
         "tile_sort": ("hbm", n_pairs * 16.0),
-        "ranges": ("hbm", n_pairs * 4.0 + n_tiles * 8.0),
+        "ranges": ("hbm", n_pairs * 4.0 + (n_bins or n_tiles) * 8.0),
+        "refine": ("hbm", n_pairs * 8.0 + (n_list or 0) * 4.0 + n_tiles * 8.0),
         "raster_fwd": ("alu", FLOP_VISITED * visited + FLOP_CONTRIB["raster_fwd"] * contrib),
         "raster_bwd": ("alu", FLOP_VISITED * visited + FLOP_CONTRIB["raster_bwd"] * contrib),
         "project_bwd": ("hbm", n_records * 36.0 + n_gauss * param_bytes + n_params * 4.0),
@@ -496,8 +502,10 @@ def run_b300(args, world, rank, local):
     lowp_elems = sum(n_gauss * w for k, w in (("log_scales", 3), ("quats", 4), ("opacity", 1), ("sh", 3 * K_sh))
                      if k in st)
     kms = {k: v[1] / n_warm for k, v in prof_all.items()}
+    n_list = opt.r.list_entries()
     by_kernel = kernel_rooflines(kms, n_gauss, int(L.n_records), int(opt.r.last_pairs), int(L.n_tiles), n_params,
-                                 param_bytes, lowp_elems, visited, contrib, ffma_tflops, hbm)
+                                 param_bytes, lowp_elems, visited, contrib, ffma_tflops, hbm, n_bins=int(L.n_bins),
+                                 n_list=n_list)
 
     # end to end through the public API with host buffers: per step the step's
     # input, the keyframe images (targets), goes host->device from pinned
@@ -671,7 +679,11 @@ def run_odometry(args, world, rank, local):
         v["g_begin"], v["g_end"] = 0, n
     win = GaussianWindow(params, local)
     g = win.struct()
-    r = Renderer([true_v[0]], local, 16)
+    # launch shape of both forms: the window's default (8 x 8 tiles split from
+    # 32 x 32 bins) unless given
+    oshape = (args.tile_size, args.ppt, args.batch, args.bin_tile_size) if args.tile_size else (8, 2, 128, 32)
+    r = Renderer([true_v[0]], local, oshape[0], pixels_per_thread=oshape[1], batch=oshape[2],
+                 bin_tile_size=oshape[3])
     targets = []
     most = 0
     for v in true_v:                      # input generation: the camera frames
@@ -788,7 +800,9 @@ def run_odometry(args, world, rank, local):
             "config": {"workload": "odometry: 500k fixed planar Gaussians (SH degree 1), one 1280x1024 view, "
                                    "%d frames on an arc, start poses perturbed by 2 deg and 5 cm, %d iterations "
                                    "per frame" % (n_frames, ODO_ITERS),
-                       "n_gaussians": n, "image": [ODO_W, ODO_H], "tile_size": 16, "frames": n_frames,
+                       "n_gaussians": n, "image": [ODO_W, ODO_H], "tile_size": oshape[0],
+                       "pixels_per_thread": oshape[1], "batch": oshape[2], "bin_tile_size": oshape[3] or oshape[0],
+                       "frames": n_frames,
                        "iterations_per_frame": ODO_ITERS,
                        "timed": "device time per iteration (CUDA events): project + bin + composite with the L1 "
                                 "loss + pose-only backward",

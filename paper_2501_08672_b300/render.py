@@ -64,6 +64,14 @@ class Renderer:
     def layout(self):
         return self.ctx.layout(self.views, self.cap)
 
+    def list_entries(self):
+        """Entries of all tiles' lists after the last binning (the pair count,
+        or with bins larger than the tiles the entries split from them);
+        synchronises."""
+        L = self.layout()
+        rg = self.ws[L.tile_ranges:L.tile_ranges + 8 * L.n_tiles].view(torch.int32).view(-1, 2).long()
+        return int((rg[:, 1] - rg[:, 0]).sum().item())
+
     def forward(self, g, count=None, n_used=None, target=None):
         """project + bin + composite into self.rgb / self.T / self.n_contrib.
         count: True synchronises to read the pair count and grows the workspace

@@ -40,3 +40,15 @@ def test_low_precision_copy_adds_its_bytes():
     a = bench.kernel_rooflines({"adam": 0.02}, 10, 10, 10, 1, 230, 52, 0, 0, 0, 75.0, 6500.0)["adam"]["work"]
     b = bench.kernel_rooflines({"adam": 0.02}, 10, 10, 10, 1, 230, 52, 200, 0, 0, 75.0, 6500.0)["adam"]["work"]
     assert b - a == 200 * 2.0
+
+
+def test_split_bins_count_their_pairs_lists_and_tiles():
+    """Bins of several tiles: the ranges count bins, the split reads each
+    (bin, record) pair's key and record and writes every list entry and
+    tile range."""
+    P, Tb, T, n_list = 4_873_213, 2560, 40_960, 29_290_925
+    out = bench.kernel_rooflines({"ranges": 0.03, "refine": 0.06}, 200_000, 1_600_000, P, T, 4_600_000, 92, 0,
+                                 0, 0, 75.0, 6500.0, n_bins=Tb, n_list=n_list)
+    assert out["ranges"]["work"] == P * 4.0 + Tb * 8.0
+    assert out["refine"]["work"] == P * 8.0 + n_list * 4.0 + T * 8.0
+    assert out["refine"]["frac"] == pytest.approx((P * 8.0 + n_list * 4.0 + T * 8.0) / 0.06e-3 / 1e9 / 6500.0)
