@@ -468,6 +468,16 @@ def run_b300(args, world, rank, local):
     torch.cuda.synchronize()
     visited = float(opt.r.n_contrib.double().sum().item())
     contrib = float(n_used.double().sum().item())
+    # the same count over 16 x 16-tile lists (the 3D-GS tiling), for comparison:
+    # finer lists visit fewer fragments for the same image, so the work of the
+    # kernel's own lists understates what it does against that tiling
+    visited16 = visited
+    if shape[0] != 16 or (shape[3] or 16) != 16:
+        r16 = Renderer(views, local, 16)
+        r16.forward(opt._g, count=True)
+        torch.cuda.synchronize()
+        visited16 = float(r16.n_contrib.double().sum().item())
+        del r16
     if dominant in FLOP_CONTRIB:
         sms = torch.cuda.get_device_properties(local).multi_processor_count
         nominal = sms * FP32_LANES * 2 * MAX_SM_MHZ * 1e6 / 1e12
@@ -484,6 +494,9 @@ def run_b300(args, world, rank, local):
                 "avg_launch_ms": avg_ms,
                 "visited_fragments": visited, "contributing_fragments": contrib,
                 "flop_per_launch": flop,
+                "visited_fragments_16x16_lists": visited16,
+                "frac_16x16_lists": (FLOP_VISITED * visited16 + FLOP_CONTRIB[dominant] * contrib)
+                / (avg_ms / 1e3) / 1e12 / peak,
                 "peak_basis": "measured: FP32 FMA microbenchmark (gs_calibrate_alu, best of 3)",
                 "peak_nominal": nominal,
                 "peak_nominal_basis": "%d SMs x 128 lanes x 2 FLOP x %d MHz (maximum SM clock)" % (sms, MAX_SM_MHZ),
