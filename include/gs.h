@@ -232,6 +232,7 @@ typedef struct gs_ws_layout {
      * each bin's [start, end) into it, and sorted_vals / tile_ranges the
      * per-tile lists split from them.  Otherwise bin_vals = sorted_vals,
      * bin_ranges = tile_ranges and n_bins = n_tiles. */
+    size_t bin_keys;      /* the sorted pair keys (bin id, tile mask above it) */
     size_t bin_vals;
     size_t bin_ranges;
     int32_t n_bins;

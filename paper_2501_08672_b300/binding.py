@@ -93,7 +93,8 @@ class WsLayout(ctypes.Structure):
                                                "pair_offsets", "pair_keys", "pair_vals", "sorted_vals",
                                                "tile_ranges", "grad2d", "counters", "total")] + [
         ("n_records", ctypes.c_int64), ("n_tiles", ctypes.c_int32), ("n_pixels", ctypes.c_int64),
-        ("bin_vals", ctypes.c_size_t), ("bin_ranges", ctypes.c_size_t), ("n_bins", ctypes.c_int32),
+        ("bin_keys", ctypes.c_size_t), ("bin_vals", ctypes.c_size_t), ("bin_ranges", ctypes.c_size_t),
+        ("n_bins", ctypes.c_int32),
         ("bin_size", ctypes.c_int32)]
 
 

@@ -245,6 +245,7 @@ int make_layout(gs_ctx* ctx, const gs_config& cfg, const gs_view* views, int n_v
         L.pair_grad = take(sizeof(float) * kPairGradStride * (size_t)cap);
     }
     W.total = off;
+    W.bin_keys = sorted_buffer((int)Tb) ? L.pkeys1 : W.pair_keys;
     W.bin_vals = sorted_buffer((int)Tb) ? L.pvals1 : W.pair_vals;
     W.sorted_vals = L.refine > 1 ? L.rvals : W.bin_vals;
     W.n_records = M;

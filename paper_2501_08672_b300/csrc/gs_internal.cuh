@@ -326,6 +326,19 @@ __device__ __forceinline__ bool footrows_span(const FootRows& f, int ty, int ts,
     return true;
 }
 
+// Dispatch key of a tile in the longest-first order of the compositing
+// launches: 255 - a log-scale code of its work (16 steps per octave), so one
+// stable 8-bit radix pass puts the heaviest tiles first.
+__device__ __forceinline__ uint32_t tile_order_key(uint32_t len) {
+    uint32_t code = 0;
+    if (len) {
+        const int e = 31 - __clz(len);
+        const uint32_t m = e >= 4 ? (len >> (e - 4)) & 15u : (len << (4 - e)) & 15u;
+        code = min(255u, (uint32_t)e * 16u + m);
+    }
+    return 255u - code;
+}
+
 // ---- programmatic dependent launch ----------------------------------------
 //
 // Every kernel of the library starts with pdl_wait() and pdl_trigger() and is
@@ -382,6 +395,9 @@ cudaError_t launch_project(const BatchParam& bp, const GaussPtrs& g, const Rende
                            const WsPtrs& ws, cudaStream_t s, Prof& pf);
 // bp: the batch at the bin size; with ws.refine > 1, geom and n_tiles give
 // the compositing tiles the bin lists are split into.
+// Reorders the compositing tiles (ws.ovals[1]) by the keys in ws.okeys[0] /
+// ws.ovals[0] (one stable 8-bit radix pass over n_tiles).
+cudaError_t launch_tile_order(const WsPtrs& ws, int n_tiles, unsigned int* status, cudaStream_t s, Prof& pf);
 cudaError_t launch_bin(const BatchParam& bp, WsPtrs& ws, unsigned int* status,
                        unsigned long long* status_pairs, cudaStream_t s, Prof& pf,
                        const RefineGeom* geom = nullptr, int n_tiles = 0);

@@ -112,7 +112,9 @@ __global__ void __launch_bounds__(TS * TS / PPT, fwd_min_blocks<TS * TS / PPT, P
                                                               uint32_t* __restrict__ n_used,
                                                               const float* __restrict__ target,
                                                               float* __restrict__ dL_drgb,
-                                                              float* __restrict__ partials) {
+                                                              float* __restrict__ partials,
+                                                              uint32_t* __restrict__ order_keys,
+                                                              uint32_t* __restrict__ order_vals) {
     pdl_wait();
     pdl_trigger();
     // Each warp walks the tile's list on its own: per step every lane fetches
@@ -261,19 +263,36 @@ __global__ void __launch_bounds__(TS * TS / PPT, fwd_min_blocks<TS * TS / PPT, P
             }
         }
     }
+    // The backward walks each tile back from its deepest contributor: that
+    // depth, the tile's largest n_contrib, keys the tile in the dispatch order
+    // of the backward (heaviest first; sorted after this launch).
+    uint32_t deep = 0;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) deep = max(deep, last[k]);
+    deep = __reduce_max_sync(0xffffffffu, deep);
     if (target) {
         // per-tile partial, summed in a fixed order (indexed by tile, not by
         // launch order, so the loss does not depend on the dispatch order)
         for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
-        __shared__ float s_l[NW];
-        if (lane == 0) s_l[w] = lsum;
-        __syncthreads();
-        if (t == 0) {
-            float tsum = 0.f;
-#pragma unroll
-            for (int i = 0; i < NW; ++i) tsum += s_l[i];
-            partials[tile] = tsum * scale;
+    }
+    __shared__ float s_l[NW];
+    __shared__ uint32_t s_deep[NW];
+    if (NW > 1) {
+        if (lane == 0) {
+            s_l[w] = lsum;
+            s_deep[w] = deep;
         }
+        __syncthreads();
+    }
+    if (t == 0) {
+        float tsum = lsum;
+        for (int i = 1; i < NW; ++i) {
+            tsum += s_l[i];
+            deep = max(deep, s_deep[i]);
+        }
+        if (target) partials[tile] = tsum * scale;
+        order_keys[tile] = tile_order_key(deep);
+        order_vals[tile] = (uint32_t)tile;
     }
 }
 
@@ -1029,7 +1048,7 @@ cudaError_t launch_render_fwd(const BatchParam& bp, const RenderConst& rc_in, co
 #define GS_X(T, P, B)                                                                                  \
     if (!done && bp.tile_size == T && bp.ppt == P && bp.batch == B) {                                  \
         pdl_launch(k_render_fwd<T, P, B>, bp.total_tiles, T * T / P, 0, s, bp, rc, ws.rec, ws.ranges, ws.ovals[1], svals, rgb, \
-                   T_final, n_contrib, n_used, target, dL_drgb, partials);                             \
+                   T_final, n_contrib, n_used, target, dL_drgb, partials, ws.okeys[0], ws.ovals[0]);   \
         done = true;                                                                                   \
     }
     GS_RASTER_VARIANTS(GS_X)
@@ -1041,6 +1060,10 @@ cudaError_t launch_render_fwd(const BatchParam& bp, const RenderConst& rc_in, co
         pdl_launch(k_l1_finish, 1, 1024, 0, s, partials, bp.total_tiles, loss);
         pf.end(pl, s);
     }
+    // the dispatch order of the next compositing launches (the backward):
+    // deepest walk first
+    cudaError_t e = launch_tile_order(ws, bp.total_tiles, rc.status, s, pf);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

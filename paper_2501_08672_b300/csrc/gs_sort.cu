@@ -806,14 +806,7 @@ __global__ void k_tile_keys(const uint2* __restrict__ ranges, int n_tiles, uint3
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_tiles) return;
     const uint2 rg = ranges[i];
-    const uint32_t len = rg.y - rg.x;
-    uint32_t code = 0;
-    if (len) {
-        const int e = 31 - __clz(len);
-        const uint32_t m = e >= 4 ? (len >> (e - 4)) & 15u : (len << (4 - e)) & 15u;
-        code = min(255u, (uint32_t)e * 16u + m);
-    }
-    keys[i] = 255u - code;
+    keys[i] = tile_order_key(rg.y - rg.x);
     vals[i] = (uint32_t)i;
 }
 
@@ -1164,6 +1157,17 @@ cudaError_t launch_bin(const BatchParam& bp, WsPtrs& ws, unsigned int* status,
     pf.end(pi, s);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
+}
+
+cudaError_t launch_tile_order(const WsPtrs& ws, int n_tiles, unsigned int* status, cudaStream_t s, Prof& pf) {
+    if (n_tiles <= 0) return cudaSuccess;
+    const int pi = pf.begin(GS_KF_RANGES, s, 0);  // radix_sort counts its own launches
+    int obuf = 0;
+    cudaError_t e = radix_sort(ws.okeys[0], ws.ovals[0], ws.okeys[1], ws.ovals[1], ws, (unsigned long long)n_tiles,
+                               nullptr, 8, &obuf, status, s, pf);
+    pf.end(pi, s);
+    if (e == cudaSuccess && obuf != 1) return cudaErrorInvalidValue;
+    return e;
 }
 
 }  // namespace gsb

@@ -48,13 +48,42 @@ def _is_subsequence(a, b):
     return all(x in it for x in a.tolist())
 
 
+def split_from_bins(r, ts, views):
+    """Every tile's full list rebuilt on the host from the sorted (bin,
+    record) pairs: the records of the tile's bin, in the bin's order, whose
+    key carries the tile's bit."""
+    torch.cuda.synchronize()
+    L = r.layout()
+    F = L.bin_size // ts
+    rb = ws_view(r, L.bin_ranges, np.uint32, 2 * L.n_bins).reshape(-1, 2)
+    n = int(rb[:, 1].max()) if L.n_bins else 0
+    keys = ws_view(r, L.bin_keys, np.uint32, n)
+    vals = ws_view(r, L.bin_vals, np.uint32, n)
+    out = []
+    bin_off = 0
+    for v in views:
+        tx_n, ty_n = (v["W"] + ts - 1) // ts, (v["H"] + ts - 1) // ts
+        bx_n = (v["W"] + L.bin_size - 1) // L.bin_size
+        by_n = (v["H"] + L.bin_size - 1) // L.bin_size
+        for ty in range(ty_n):
+            for tx in range(tx_n):
+                b = bin_off + (ty // F) * bx_n + tx // F
+                a, e = rb[b]
+                bit = 32 - F * F + (ty % F) * F + tx % F
+                k = keys[a:e]
+                out.append(vals[a:e][((k >> np.uint32(bit)) & np.uint32(1)).astype(bool)].copy())
+        bin_off += bx_n * by_n
+    return out
+
+
 @pytest.mark.parametrize("ts,ppt,bin_ts", SPLITS)
 def test_split_lists_match_binning_at_the_tile_size(ts, ppt, bin_ts):
     """Ragged views (sizes not multiples of the bin, so edge bins hold tiles
-    past the image): every per-tile list split from the bins holds the list
-    that binning at the tile size gives, in the same order, plus at most
-    records whose footprint only grazes the tile (within the binning test's
-    margin); the images, T and the loss gradient inputs agree bit for bit."""
+    past the image): every tile's list split from the bins (rebuilt from the
+    bin lists and the tile masks in their keys) holds the list that binning
+    at the tile size gives, in the same order, plus at most records whose
+    footprint only grazes the tile (within the binning test's margin); the
+    lists gs_bin split out are those; the images and T agree bit for bit."""
     n = 6000
     p = scenes.frustum_scene(n, seed=31)
     views = ragged_views(n)
@@ -62,8 +91,12 @@ def test_split_lists_match_binning_at_the_tile_size(ts, ppt, bin_ts):
     r0 = render(win, views, ts, ppt, 0)
     r1 = render(win, views, ts, ppt, bin_ts)
     l0, L0 = tile_lists(r0)
-    l1, L1 = tile_lists(r1)
+    written, L1 = tile_lists(r1)
+    l1 = split_from_bins(r1, ts, views)
     assert L1.bin_size == bin_ts and L1.n_tiles == L0.n_tiles and L1.n_bins < L0.n_tiles
+    assert len(l1) == len(l0) == len(written)
+    for t, (w, full) in enumerate(zip(written, l1)):
+        assert np.array_equal(w, full), "tile %d: the split list differs from its bin's entries with its bit" % t
     assert int(r1.last_pairs) < int(r0.last_pairs)
     M = L1.n_records
     rec = ws_view(r1, L1.records, np.float32, 12 * M).reshape(M, 12)
@@ -137,3 +170,23 @@ def test_box_room_window_split_matches_oracle(orc):
     win, r = gpu_forward(p, views, tile_size=8, pixels_per_thread=2, batch=128, bin_tile_size=32)
     assert r.layout().bin_size == 32
     l1_parity(orc, win, r, p, views, l1_target(p, views))
+
+
+def test_pose_normal_with_bins_matches_binning_at_the_tile_size():
+    """gs_pose_normal over the lists split from 32 x 32 bins: its per-view
+    normal equations equal those of binning at the tile size (the extra
+    grazing records add nothing)."""
+    n = 4000
+    p = scenes.box_room_scene(n, seed=35)
+    views = scenes.arc_views(2, 176, 144, 160.0, n_gaussians=n)
+    win = GaussianWindow(p, 0)
+    res = []
+    for bin_ts in (0, 32):
+        r = Renderer(views, 0, 8, pixels_per_thread=2, batch=128, bin_tile_size=bin_ts)
+        r.forward(win.struct())
+        target = torch.zeros_like(r.rgb)
+        normal = r.pose_normal(win.struct(), target)
+        torch.cuda.synchronize()
+        res.append(np.asarray(normal.cpu().numpy(), np.float64))
+        assert r.layout().bin_size == (bin_ts or 8)
+    np.testing.assert_allclose(res[1], res[0], rtol=1e-12, atol=0)
