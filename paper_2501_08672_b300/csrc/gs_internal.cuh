@@ -123,7 +123,7 @@ struct WsPtrs {
     uint32_t* okeys[2];      // [T] tile-order keys
     uint32_t* ovals[2];      // [T] tiles, longest list first (buffer 1 after the sort)
     float* grad2d;           // [M][9]
-    unsigned long long* counters; // [8]: [0] pairs needed, [1..3] depth-key range (kCtrRange*)
+    unsigned long long* counters; // [8]: [0] pairs needed, [1..3] depth-key range (kCtrRange*), [4] kCtrOrderTiles
     float* partials;         // reduction scratch
     // deterministic backward only (nullptr otherwise):
     uint32_t* pair_rec;      // [cap] record of each pair at its emission index
@@ -170,6 +170,10 @@ struct RefineGeom {
 constexpr int kCtrRangeMax = 1;
 constexpr int kCtrRangeMin = 2;
 constexpr int kCtrRangeGen = 3;
+// counters[kCtrOrderTiles]: the tile count the dispatch keys in okeys[0] were
+// written for by the last compositing forward (each tile keyed by its walk
+// depth); binning orders the next forward by them when it matches.
+constexpr int kCtrOrderTiles = 4;
 
 struct KeyMap {
     uint32_t kmin;

@@ -114,7 +114,8 @@ __global__ void __launch_bounds__(TS * TS / PPT, fwd_min_blocks<TS * TS / PPT, P
                                                               float* __restrict__ dL_drgb,
                                                               float* __restrict__ partials,
                                                               uint32_t* __restrict__ order_keys,
-                                                              uint32_t* __restrict__ order_vals) {
+                                                              uint32_t* __restrict__ order_vals,
+                                                              unsigned long long* __restrict__ counters) {
     pdl_wait();
     pdl_trigger();
     // Each warp walks the tile's list on its own: per step every lane fetches
@@ -293,6 +294,7 @@ __global__ void __launch_bounds__(TS * TS / PPT, fwd_min_blocks<TS * TS / PPT, P
         if (target) partials[tile] = tsum * scale;
         order_keys[tile] = tile_order_key(deep);
         order_vals[tile] = (uint32_t)tile;
+        if (blockIdx.x == 0) counters[kCtrOrderTiles] = (unsigned long long)bp.total_tiles;
     }
 }
 
@@ -1048,7 +1050,8 @@ cudaError_t launch_render_fwd(const BatchParam& bp, const RenderConst& rc_in, co
 #define GS_X(T, P, B)                                                                                  \
     if (!done && bp.tile_size == T && bp.ppt == P && bp.batch == B) {                                  \
         pdl_launch(k_render_fwd<T, P, B>, bp.total_tiles, T * T / P, 0, s, bp, rc, ws.rec, ws.ranges, ws.ovals[1], svals, rgb, \
-                   T_final, n_contrib, n_used, target, dL_drgb, partials, ws.okeys[0], ws.ovals[0]);   \
+                   T_final, n_contrib, n_used, target, dL_drgb, partials, ws.okeys[0], ws.ovals[0],    \
+                   ws.counters);                                                                       \
         done = true;                                                                                   \
     }
     GS_RASTER_VARIANTS(GS_X)

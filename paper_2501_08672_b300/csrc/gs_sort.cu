@@ -799,14 +799,21 @@ __global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ order
 // (a log-scale code of the list length: 16 steps per octave), one stable
 // 8-bit radix pass, so CTAs of long lists are dispatched first and short ones
 // fill the tail.
+// When the last compositing forward keyed the same number of tiles by their
+// walk depth (counters[kCtrOrderTiles]), those keys stay: the depth a tile's
+// pixels reached in the last iteration predicts its work better than its list
+// length.  Either way every tile gets a key and its index, so the sort yields
+// a permutation of the tiles whatever the keys hold.
 __global__ void k_tile_keys(const uint2* __restrict__ ranges, int n_tiles, uint32_t* __restrict__ keys,
-                            uint32_t* __restrict__ vals) {
+                            uint32_t* __restrict__ vals, const unsigned long long* __restrict__ counters) {
     pdl_wait();
     pdl_trigger();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_tiles) return;
-    const uint2 rg = ranges[i];
-    keys[i] = tile_order_key(rg.y - rg.x);
+    if (counters[kCtrOrderTiles] != (unsigned long long)n_tiles) {
+        const uint2 rg = ranges[i];
+        keys[i] = tile_order_key(rg.y - rg.x);
+    }
     vals[i] = (uint32_t)i;
 }
 
@@ -1150,7 +1157,8 @@ cudaError_t launch_bin(const BatchParam& bp, WsPtrs& ws, unsigned int* status,
     }
     // 7. longest-list-first order of the compositing tiles
     pi = pf.begin(GS_KF_RANGES, s, 1);  // keys; radix_sort counts its own launches
-    pdl_launch(k_tile_keys, (n_tiles + 255) / 256, 256, 0, s, ws.ranges, n_tiles, ws.okeys[0], ws.ovals[0]);
+    pdl_launch(k_tile_keys, (n_tiles + 255) / 256, 256, 0, s, ws.ranges, n_tiles, ws.okeys[0], ws.ovals[0],
+               ws.counters);
     int obuf = 0;
     e = radix_sort(ws.okeys[0], ws.ovals[0], ws.okeys[1], ws.ovals[1], ws, (unsigned long long)n_tiles,
                    nullptr, 8, &obuf, status, s, pf);
