@@ -830,7 +830,10 @@ __global__ void __launch_bounds__(TS * TS) k_render_pose_normal(const __grid_con
                                                                 const float4* __restrict__ tan,
                                                                 const float* __restrict__ target,
                                                                 float* __restrict__ partials,
-                                                                float* __restrict__ H_pix) {
+                                                                float* __restrict__ H_pix,
+                                                                uint32_t* __restrict__ order_keys,
+                                                                uint32_t* __restrict__ order_vals,
+                                                                unsigned long long* __restrict__ counters) {
     pdl_wait();
     pdl_trigger();
     constexpr int NT = TS * TS;
@@ -863,8 +866,10 @@ __global__ void __launch_bounds__(TS * TS) k_render_pose_normal(const __grid_con
     }
     uint2 rg = ranges[tile];
     if (!gs_checked(rg.x <= rg.y && (long long)rg.y <= rc.cap, rc)) rg.y = rg.x;
+    uint32_t walked = 0;  // list entries this warp fetched (its walk depth)
     for (uint32_t start = rg.x; start < rg.y; start += kPNBatch) {
         if (__all_sync(0xffffffffu, done)) break;
+        walked = min(start + kPNBatch, rg.y) - rg.x;
         const uint32_t idx = start + lane;
         bool reach = false;
         uint32_t r = 0;
@@ -972,7 +977,19 @@ __global__ void __launch_bounds__(TS * TS) k_render_pose_normal(const __grid_con
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         if (lane == 0) s_red[w][e] = v;
     }
+    __shared__ uint32_t s_walk[NW];
+    if (lane == 0) s_walk[w] = walked;
     __syncthreads();
+    if (t == 0) {
+        // the tile's walk depth keys it in the next iteration's dispatch
+        // order (binning keeps these keys while the tile count matches)
+        uint32_t deep = 0;
+#pragma unroll
+        for (int ww = 0; ww < NW; ++ww) deep = max(deep, s_walk[ww]);
+        order_keys[tile] = tile_order_key(deep);
+        order_vals[tile] = (uint32_t)tile;
+        if (blockIdx.x == 0) counters[kCtrOrderTiles] = (unsigned long long)bp.total_tiles;
+    }
     if (t < kNormalVals) {
         float v = 0.f;
 #pragma unroll
@@ -1254,10 +1271,10 @@ cudaError_t launch_pose_normal(const BatchParam& bp, const RenderConst& rc_in, c
     const int pi = pf.begin(GS_KF_POSE_NORMAL, s, 2);
     if (bp.tile_size == 8)
         pdl_launch(k_render_pose_normal<8>, bp.total_tiles, 64, 0, s, bp, rc, ws.rec, ws.ranges, ws.ovals[1], svals,
-                                                               tangents, target, partials, H_pix);
+                                                               tangents, target, partials, H_pix, ws.okeys[0], ws.ovals[0], ws.counters);
     else if (bp.tile_size == 16)
         pdl_launch(k_render_pose_normal<16>, bp.total_tiles, 256, 0, s, bp, rc, ws.rec, ws.ranges, ws.ovals[1], svals,
-                                                                 tangents, target, partials, H_pix);
+                                                                 tangents, target, partials, H_pix, ws.okeys[0], ws.ovals[0], ws.counters);
     else
         return cudaErrorInvalidValue;
     pdl_launch(k_pose_normal_finish, bp.n_views, 32 * kPNFinishGroups, 0, s, bp, partials, normal);

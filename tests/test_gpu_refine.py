@@ -190,3 +190,46 @@ def test_pose_normal_with_bins_matches_binning_at_the_tile_size():
         res.append(np.asarray(normal.cpu().numpy(), np.float64))
         assert r.layout().bin_size == (bin_ts or 8)
     np.testing.assert_allclose(res[1], res[0], rtol=1e-12, atol=0)
+
+
+def test_bins_that_would_not_fit_below_the_mask_bin_at_the_tile_size():
+    """4 x 4 tiles per bin leave 16 bits for the bin id: 64 views of
+    1280 x 1024 (81920 bins of 32 x 32) bin at the tile size instead, while
+    2 x 2 tiles per bin (28 bits) still split."""
+    from paper_2501_08672_b300 import binding as B
+    views = [scenes.identity_view(1280, 1024, 1000.0, 0, 10) for _ in range(64)]
+    vc = B.make_views(views)
+    for bin_ts, expect in ((32, 8), (16, 16)):
+        ctx = B.Context(0, tile_size=8, pixels_per_thread=2, batch=128, bin_tile_size=bin_ts)
+        L = ctx.layout(vc, 1024)
+        assert L.bin_size == expect and (L.n_bins == L.n_tiles) == (expect == 8)
+
+
+def test_dispatch_order_by_walk_depth_changes_no_result():
+    """The first forward dispatches tiles by list length, the next ones by the
+    walk depths the previous forward reached: images, T and n_contrib are
+    identical, and the deterministic backward's gradients bit for bit."""
+    n = 8000
+    p = scenes.box_room_scene(n, seed=36)
+    views = scenes.arc_views(3, 192, 160, 180.0, n_gaussians=n)
+    win = GaussianWindow(p, 0)
+    for cfg in (dict(tile_size=8, pixels_per_thread=2, batch=128, bin_tile_size=32),
+                dict(tile_size=16, deterministic=1)):
+        ts = cfg.pop("tile_size")
+        r = Renderer(views, 0, ts, **cfg)
+        outs = []
+        for it in range(3):
+            r.forward(win.struct(), count=(it == 0))
+            torch.cuda.synchronize()
+            order = r.ws[r.layout().counters:r.layout().counters + 64].view(torch.int64).cpu().numpy()
+            g = win.grad_tensors()
+            r.backward(win.struct(), torch.full_like(r.rgb, 1e-3), grads=g)
+            torch.cuda.synchronize()
+            outs.append((r.rgb.clone(), r.T.clone(), r.n_contrib.clone(), win.gflat.clone(), int(order[4])))
+        assert outs[1][4] == outs[2][4] == r.layout().n_tiles  # walk-depth keys in use
+        for o in outs[1:]:
+            assert torch.equal(o[0], outs[0][0]) and torch.equal(o[1], outs[0][1]) and torch.equal(o[2], outs[0][2])
+            if cfg.get("deterministic"):
+                assert torch.equal(o[3], outs[0][3])
+            else:
+                assert float((o[3] - outs[0][3]).norm() / outs[0][3].norm()) < 1e-5
