@@ -365,6 +365,7 @@ RenderConst make_rc(const gs_config& c) {
     for (int k = 0; k < 3; ++k) r.bg[k] = c.bg[k];
     r.status = nullptr;
     r.cap = 0;
+    r.sm_count = 0;
     return r;
 }
 
@@ -372,6 +373,7 @@ RenderConst make_rc(const gs_config& c) {
 RenderConst ctx_rc(const gs_ctx* ctx) {
     RenderConst r = make_rc(ctx->cfg);
     r.status = ctx->d_status;
+    r.sm_count = ctx->sm_count;
     return r;
 }
 

@@ -64,6 +64,7 @@ struct RenderConst {
     float bg[3];
     unsigned int* status;   // the context's latched status word
     long long cap;          // pair capacity of the workspace (set by the compositing launches)
+    int sm_count;           // SMs of the device (0: unknown)
 };
 
 // Bounds checks of the checked build (compiled with -DGS_CHECKED): the

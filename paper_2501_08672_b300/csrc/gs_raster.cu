@@ -1081,9 +1081,12 @@ cudaError_t launch_render_fwd(const BatchParam& bp, const RenderConst& rc_in, co
         pf.end(pl, s);
     }
     // the dispatch order of the next compositing launches (the backward):
-    // deepest walk first
-    cudaError_t e = launch_tile_order(ws, bp.total_tiles, rc.status, s, pf);
-    if (e != cudaSuccess) return e;
+    // deepest walk first; not worth its launches when every tile's block is
+    // resident at once (at most 16 per SM)
+    if (rc.sm_count <= 0 || bp.total_tiles > 16 * rc.sm_count) {
+        cudaError_t e = launch_tile_order(ws, bp.total_tiles, rc.status, s, pf);
+        if (e != cudaSuccess) return e;
+    }
     return cudaGetLastError();
 }
 
