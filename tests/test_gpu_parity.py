@@ -995,15 +995,22 @@ def sampled_parity(orc, params, views, tile_size, per_view, seed, check_params=T
     return r, win, errs
 
 
+# The launch configuration bench.py's autotuner picks for the window workloads:
+# 8 x 8 tiles split from 32 x 32 bins, 2 pixels per thread, 128-record batches.
+BENCH_SHAPE = dict(tile_size=8, pixels_per_thread=2, batch=128, bin_tile_size=32)
+# The edge cases below run in the library's default shape and in that one.
+LIMIT_SHAPES = [dict(), BENCH_SHAPE]
+
+
 def test_full_size_window_sampled(orc):
     """Headline size and launch configuration: 200k box-room Gaussians, 8
-    keyframes 640x512, 16x16 tiles; forward checked on sampled pixels,
-    gradients of a loss supported on those pixels checked in full."""
+    keyframes 640x512, 8x8 tiles from 32x32 bins; forward checked on sampled
+    pixels, gradients of a loss supported on those pixels checked in full."""
     n = 200_000
     p = scenes.box_room_scene(n, seed=0, sh_degree=1)
     views = scenes.arc_views(8, 640, 512, 600.0, n_gaussians=n)
-    r, _, _ = sampled_parity(orc, p, views, 16, 48, seed=21, pixels_per_thread=2, batch=128)
-    assert r.last_pairs > 1_000_000
+    r, _, _ = sampled_parity(orc, p, views, 8, 48, seed=21, pixels_per_thread=2, batch=128, bin_tile_size=32)
+    assert r.last_pairs > 1_000_000 and r.layout().bin_size == 32
 
 
 def test_uneven_window_sampled(orc):
@@ -1012,8 +1019,8 @@ def test_uneven_window_sampled(orc):
     500k), all rendered by one launch per kernel family; forward on sampled
     pixels of every view, full gradients of a loss supported on them."""
     params, views = scenes.uneven_batch(16, 2_000_000, seed=0)
-    r, _, _ = sampled_parity(orc, params, views, 16, 24, seed=51, pixels_per_thread=2, batch=256)
-    assert r.last_pairs > 10_000_000
+    r, _, _ = sampled_parity(orc, params, views, 8, 24, seed=51, pixels_per_thread=2, batch=128, bin_tile_size=32)
+    assert r.last_pairs > 5_000_000 and r.layout().bin_size == 32
     assert len({int(v["W"]) for v in views}) > 4
 
 
@@ -1035,9 +1042,9 @@ def test_mixed_window_sampled(orc):
     storage = dict(log_scales=torch.bfloat16, quats=torch.bfloat16, opacity=torch.float16, sh=torch.float16)
     forms = {}
     for name, st in (("FP16/BF16 storage", storage), ("FP32 storage", None)):
-        win, r = gpu_forward(params, views, 16, storage=st, pixels_per_thread=2, batch=128)
+        win, r = gpu_forward(params, views, 8, storage=st, pixels_per_thread=2, batch=128, bin_tile_size=32)
         forms[name] = (win, r)
-    assert forms["FP32 storage"][1].last_pairs > 100_000_000
+    assert forms["FP32 storage"][1].last_pairs > 50_000_000
     deq = forms["FP16/BF16 storage"][0].numpy(use_render_copy=True)
     pix = sampled_pixels(views, 24, 61)
     inputs = {"dequantised": deq, "FP32 values": params}
@@ -1090,7 +1097,8 @@ def test_odometry_view_pose_gradient_sampled(orc):
     v = scenes.lookat_view((4.0 * math.cos(-1.7), 4.0 * math.sin(-1.7), 2.2), (0.0, 0.0, 0.6), 1280, 1024,
                            1200.0, 0, n)
     v = apply_left(v, np.array([0.02, -0.015, 0.01, 0.03, -0.02, 0.01]))
-    sampled_parity(orc, p, [v], 16, 64, seed=31, check_params=False, pixels_per_thread=2, batch=128)
+    sampled_parity(orc, p, [v], 8, 64, seed=31, check_params=False, pixels_per_thread=2, batch=128,
+                   bin_tile_size=32)
 
 
 def test_pose_gradient_matches_central_differences_of_the_gpu_render():
@@ -1187,7 +1195,8 @@ def test_graph_replay_matches_plain_steps():
 
 # ---------------------------------------------------------------- limits and degenerate inputs
 
-def test_max_views_forward_backward(orc):
+@pytest.mark.parametrize("shape", LIMIT_SHAPES)
+def test_max_views_forward_backward(orc, shape):
     """GS_MAX_VIEWS (64) small views around a scene, each on its own part of
     the window, forward and backward against the oracle."""
     n = 3000
@@ -1199,14 +1208,15 @@ def test_max_views_forward_backward(orc):
         v = scenes.lookat_view((2.0 * math.sin(ang), 0.1 * (k % 5), -1.0), (0.0, 0.0, 5.0),
                                24 + (k % 7) * 3, 16 + (k % 5) * 4, 30.0, b, e, up=(0, -1, 0))
         views.append(v)
-    win, r = gpu_forward(p, views)
+    win, r = gpu_forward(p, views, **shape)
     for v, img, T in zip(views, r.images(), B.unpack_images(r.T, views, 1)):
         compare_images(orc.render_view(p, v), img.cpu().numpy(), T.cpu().numpy())
     tg = l1_target(p, views)
     g, pose, border = l1_parity(orc, win, r, p, views, tg)
 
 
-def test_view_with_every_gaussian_culled(orc):
+@pytest.mark.parametrize("shape", LIMIT_SHAPES)
+def test_view_with_every_gaussian_culled(orc, shape):
     """A camera looking away from the whole window: no pairs, the background
     everywhere, T = 1, and zero gradients (the other view still works)."""
     n = 2000
@@ -1214,7 +1224,7 @@ def test_view_with_every_gaussian_culled(orc):
     away = scenes.lookat_view((0.0, 0.0, 0.0), (0.0, 0.0, -5.0), 48, 40, 40.0, 0, n, up=(0, -1, 0))
     seen = scenes.identity_view(48, 40, 40.0, 0, n)
     cfg = dict(bg=(0.2, 0.4, 0.6))
-    win, r = gpu_forward(p, [away, seen], **cfg)
+    win, r = gpu_forward(p, [away, seen], **cfg, **shape)
     img = r.images()[0].cpu().numpy()
     T = B.unpack_images(r.T, [away, seen], 1)[0].cpu().numpy()
     np.testing.assert_array_equal(T, np.ones_like(T))
@@ -1223,7 +1233,7 @@ def test_view_with_every_gaussian_culled(orc):
     o = orc.render_view(p, seen, dict(orc.DEFAULT_CFG, **cfg))
     compare_images(o, r.images()[1].cpu().numpy(), B.unpack_images(r.T, [away, seen], 1)[1].cpu().numpy())
     # only the culled view in the loss: every Gaussian gradient is zero
-    win2, r2 = gpu_forward(p, [away], **cfg)
+    win2, r2 = gpu_forward(p, [away], **cfg, **shape)
     r2.l1(torch.zeros_like(r2.rgb))
     r2.backward(win2.struct(), r2.dL_drgb, grads=win2.grad_tensors(), want_pose=True)
     torch.cuda.synchronize()
@@ -1232,19 +1242,21 @@ def test_view_with_every_gaussian_culled(orc):
     assert float(r2.dL_dpose.abs().max()) == 0.0
 
 
+@pytest.mark.parametrize("shape", LIMIT_SHAPES)
 @pytest.mark.parametrize("W,H", [(1, 1), (1, 17), (17, 1), (33, 2)])
-def test_degenerate_image_sizes(orc, W, H):
+def test_degenerate_image_sizes(orc, W, H, shape):
     n = 1500
     p = scenes.frustum_scene(n, seed=42)
     views = [scenes.identity_view(W, H, 0.5 * max(W, H) + 2.0, 0, n)]
-    win, r = gpu_forward(p, views)
+    win, r = gpu_forward(p, views, **shape)
     compare_images(orc.render_view(p, views[0]), r.images()[0].cpu().numpy(),
                    B.unpack_images(r.T, views, 1)[0].cpu().numpy())
     tg = l1_target(p, views)
     g, pose, border = l1_parity(orc, win, r, p, views, tg)
 
 
-def test_huge_splats_cover_the_image(orc):
+@pytest.mark.parametrize("shape", LIMIT_SHAPES)
+def test_huge_splats_cover_the_image(orc, shape):
     """A few Gaussians whose footprints span the whole image (hundreds of
     tiles: the warp-cooperative emission path) over many small ones."""
     n = 4000
@@ -1253,7 +1265,7 @@ def test_huge_splats_cover_the_image(orc):
     p["means"][:6, 2] = np.linspace(3.0, 7.0, 6)
     p["opacity"][:6] = -1.5
     views = [scenes.identity_view(256, 192, 200.0, 0, n)]
-    win, r = gpu_forward(p, views)
+    win, r = gpu_forward(p, views, **shape)
     compare_images(orc.render_view(p, views[0]), r.images()[0].cpu().numpy(),
                    B.unpack_images(r.T, views, 1)[0].cpu().numpy())
     tg = l1_target(p, views)
