@@ -48,6 +48,7 @@ def cases():
     yield "ragged", p, [v0, v1], {}
     yield "ragged_det", p, [v0, v1], {"deterministic": 1}
     yield "ragged_t8", p, [v0, v1], {"tile_size": 8}
+    yield "ragged_bins", p, [v0, v1], {"tile_size": 8, "pixels_per_thread": 2, "batch": 128, "bin_tile_size": 32}
     big = scenes.frustum_scene(2000, seed=62)
     big["log_scales"][:6] = np.log(np.array([[1.5, 1.2, 0.4]] * 6, np.float32))
     big["means"][:6, 2] = np.linspace(3.0, 7.0, 6)
@@ -55,6 +56,7 @@ def cases():
     m = scenes.frustum_scene(1500, seed=63)
     views = [scenes.identity_view(40 + 3 * k, 24 + 2 * (k % 5), 30.0, 0, 1500) for k in range(64)]
     yield "64_views", m, views, {"tile_size": 8}
+    yield "64_views_bins", m, views, {"tile_size": 8, "bin_tile_size": 16}
 
 
 for name, p, views, cfg in cases():
@@ -72,7 +74,7 @@ for name, p, views, cfg in cases():
     out[name + "/n_contrib"] = r.n_contrib.cpu().numpy()
     out[name + "/grad"] = win.gflat.cpu().numpy()
     out[name + "/pose"] = r.dL_dpose.cpu().numpy()
-    if name == "ragged":
+    if name in ("ragged", "ragged_bins"):
         target = (r.rgb + 0.05 * w).contiguous()
         H = r.pose_normal(win.struct(), target)
         torch.cuda.synchronize()
@@ -92,6 +94,13 @@ rc, need = r.ctx.sync_status()
 out["overflow_rc"] = np.array([rc])
 rc2, _ = r.ctx.sync_status()
 out["overflow_rc_after"] = np.array([rc2])
+# the same with bins split into tile lists
+r = Renderer(views, 0, 8, capacity=100, pixels_per_thread=2, batch=128, bin_tile_size=32)
+r._counted = True
+r.forward(win.struct())
+torch.cuda.synchronize()
+rc, need = r.ctx.sync_status()
+out["overflow_bins_rc"] = np.array([rc])
 np.savez(os.environ["GS_OUT"], **out)
 """
 
@@ -125,3 +134,4 @@ def test_checked_build_matches_the_normal_build(tmp_path):
             assert rel < 1e-5, (k, rel)
     assert int(b["overflow_rc"][0]) == -4  # GS_ERR_CAPACITY, reported once
     assert int(b["overflow_rc_after"][0]) == 0
+    assert int(b["overflow_bins_rc"][0]) == -4
