@@ -69,7 +69,7 @@ class Renderer:
         or with bins larger than the tiles the entries split from them);
         synchronises."""
         L = self.layout()
-        rg = self.ws[L.tile_ranges:L.tile_ranges + 8 * L.n_tiles].view(torch.int32).view(-1, 2).long()
+        rg = self.ws[L.tile_ranges:L.tile_ranges + 8 * L.n_tiles].view(torch.int32).view(-1, 2).long() & 0xFFFFFFFF
         return int((rg[:, 1] - rg[:, 0]).sum().item())
 
     def forward(self, g, count=None, n_used=None, target=None):
