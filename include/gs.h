@@ -515,7 +515,8 @@ GS_API int32_t gs_checked_build(void);
  * by forward-mode differentiation of Eq. raster through Eqs. q and spat and
  * the view direction of the SH colour; culling and the set of contributing
  * fragments are locally constant, clamped alphas and colours contribute zero
- * derivative.  The per-tile sums are FP32, the per-view sums FP64.
+ * derivative.  The per-tile sums are FP32, the per-view sums FP64 (in a
+ * fixed order: 64 runs of tiles per view, then the runs).
  *
  * Requires gs_project and gs_bin on the same views and workspace (as
  * gs_render_fwd) and a tile size of 8 or 16 (GS_ERR_UNSUPPORTED otherwise).

@@ -944,7 +944,8 @@ int gs_pose_normal_scratch(gs_ctx* ctx, const gs_view* views, int n_views, size_
     Layout L;
     int rc = make_layout(ctx, ctx->cfg, views, n_views, 0, L);
     if (rc) return rc;
-    *floats = (size_t)4 * kPoseTan4 * (size_t)L.pub.n_records + (size_t)kNormalVals * (size_t)L.pub.n_tiles;
+    *floats = (size_t)4 * kPoseTan4 * (size_t)L.pub.n_records + pose_normal_partials_floats(L.pub.n_tiles) +
+              pose_normal_chunk_floats(n_views);
     return GS_OK;
 }
 

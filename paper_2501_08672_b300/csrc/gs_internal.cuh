@@ -428,6 +428,10 @@ cudaError_t launch_sh_init(const ViewParam& V, const float* means, const float* 
 cudaError_t launch_pose_tangents(const BatchParam& bp, const GaussPtrs& g, const RenderConst& rc,
                                  const WsPtrs& ws, float4* tangents, cudaStream_t s, Prof& pf);
 bool pose_normal_supported(int ts);
+// Scratch of the pose normal equations after the per-record tangents: the
+// per-tile partials (an even number of floats), then the FP64 chunk sums.
+size_t pose_normal_partials_floats(long long n_tiles);
+size_t pose_normal_chunk_floats(int n_views);
 cudaError_t launch_pose_normal(const BatchParam& bp, const RenderConst& rc, const WsPtrs& ws,
                                const float4* tangents, const float* target, float* partials, double* normal,
                                float* H_pix, cudaStream_t s, Prof& pf);

@@ -999,38 +999,49 @@ __global__ void __launch_bounds__(TS * TS) k_render_pose_normal(const __grid_con
 }
 
 // Per view: the FP64 sum of its tiles' partials.  grid.x is the view.
-constexpr int kPNFinishGroups = 32;  // warps per view in the final sum
+// Per-view totals of the per-tile partials in FP64, in two fixed-order
+// stages: kPNChunks blocks per view each sum a contiguous run of the view's
+// tiles (warp w of a block takes tiles w, w + 8, ..., lane e value e), then
+// one warp per view adds the chunk sums.  The FP64 rate of one SM is a few
+// operations per clock, so the sums are spread over many SMs.
+constexpr int kPNChunks = 64;
+constexpr int kPNChunkWarps = 8;
 
-__global__ void __launch_bounds__(32 * kPNFinishGroups) k_pose_normal_finish(const __grid_constant__ BatchParam bp,
-                                                                          const float* __restrict__ partials,
-                                                                          double* __restrict__ normal) {
+__global__ void __launch_bounds__(32 * kPNChunkWarps) k_pose_normal_chunks(const __grid_constant__ BatchParam bp,
+                                                                         const float* __restrict__ partials,
+                                                                         double* __restrict__ chunk_sums) {
     pdl_wait();
     pdl_trigger();
-    __shared__ double s_sum[kPNFinishGroups][32];
-    const ViewParam& V = bp.v[blockIdx.x];
-    const int e = threadIdx.x & 31, grp = threadIdx.x >> 5;
+    __shared__ double s_sum[kPNChunkWarps][32];
+    const ViewParam& V = bp.v[blockIdx.y];
+    const int e = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int ntiles = V.tiles_x * ((V.H + bp.tile_size - 1) / bp.tile_size);
+    const int t0 = (int)((long long)ntiles * blockIdx.x / kPNChunks);
+    const int t1 = (int)((long long)ntiles * (blockIdx.x + 1) / kPNChunks);
     const float* src = partials + (size_t)V.tile_off * kNormalVals + e;
     double acc = 0.0;
-    if (e < kNormalVals) {
-        // warp grp sums tiles grp, grp + G, ...; eight loads in flight per lane
-        int tl = grp;
-        for (; tl + 7 * kPNFinishGroups < ntiles; tl += 8 * kPNFinishGroups) {
-            float v[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) v[u] = src[(size_t)(tl + u * kPNFinishGroups) * kNormalVals];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) acc += (double)v[u];
-        }
-        for (; tl < ntiles; tl += kPNFinishGroups) acc += (double)src[(size_t)tl * kNormalVals];
-    }
-    s_sum[grp][e] = acc;
+    if (e < kNormalVals)
+        for (int tl = t0 + w; tl < t1; tl += kPNChunkWarps) acc += (double)src[(size_t)tl * kNormalVals];
+    s_sum[w][e] = acc;
     __syncthreads();
     if (threadIdx.x < kNormalVals) {
         double v = 0.0;
-        for (int g = 0; g < kPNFinishGroups; ++g) v += s_sum[g][threadIdx.x];
-        normal[(size_t)blockIdx.x * kNormalVals + threadIdx.x] = v;
+#pragma unroll
+        for (int g = 0; g < kPNChunkWarps; ++g) v += s_sum[g][threadIdx.x];
+        chunk_sums[((size_t)blockIdx.y * kPNChunks + blockIdx.x) * kNormalVals + threadIdx.x] = v;
     }
+}
+
+__global__ void __launch_bounds__(32) k_pose_normal_finish(const double* __restrict__ chunk_sums,
+                                                           double* __restrict__ normal) {
+    pdl_wait();
+    pdl_trigger();
+    const int e = threadIdx.x;
+    if (e >= kNormalVals) return;
+    const double* src = chunk_sums + (size_t)blockIdx.x * kPNChunks * kNormalVals + e;
+    double v = 0.0;
+    for (int c = 0; c < kPNChunks; ++c) v += src[(size_t)c * kNormalVals];
+    normal[(size_t)blockIdx.x * kNormalVals + e] = v;
 }
 
 }  // namespace
@@ -1264,6 +1275,12 @@ cudaError_t launch_l1_static(const BatchParam& bp, const float* rgb, const float
 
 bool pose_normal_supported(int ts) { return ts == 8 || ts == 16; }
 
+size_t pose_normal_partials_floats(long long n_tiles) {
+    return ((size_t)kNormalVals * (size_t)n_tiles + 1) & ~(size_t)1;  // even: the FP64 chunk sums follow
+}
+
+size_t pose_normal_chunk_floats(int n_views) { return (size_t)2 * kPNChunks * kNormalVals * (size_t)n_views; }
+
 cudaError_t launch_pose_normal(const BatchParam& bp, const RenderConst& rc_in, const WsPtrs& ws,
                                const float4* tangents, const float* target, float* partials, double* normal,
                                float* H_pix, cudaStream_t s, Prof& pf) {
@@ -1271,7 +1288,7 @@ cudaError_t launch_pose_normal(const BatchParam& bp, const RenderConst& rc_in, c
     rc.cap = tile_list_cap(ws);
     if (bp.total_tiles <= 0) return cudaSuccess;
     const uint32_t* svals = tile_list_vals(ws);
-    const int pi = pf.begin(GS_KF_POSE_NORMAL, s, 2);
+    const int pi = pf.begin(GS_KF_POSE_NORMAL, s, 3);
     if (bp.tile_size == 8)
         pdl_launch(k_render_pose_normal<8>, bp.total_tiles, 64, 0, s, bp, rc, ws.rec, ws.ranges, ws.ovals[1], svals,
                                                                tangents, target, partials, H_pix, ws.okeys[0], ws.ovals[0], ws.counters);
@@ -1280,7 +1297,10 @@ cudaError_t launch_pose_normal(const BatchParam& bp, const RenderConst& rc_in, c
                                                                  tangents, target, partials, H_pix, ws.okeys[0], ws.ovals[0], ws.counters);
     else
         return cudaErrorInvalidValue;
-    pdl_launch(k_pose_normal_finish, bp.n_views, 32 * kPNFinishGroups, 0, s, bp, partials, normal);
+    // the chunk sums follow the per-tile partials in the scratch (8-byte aligned)
+    double* chunk_sums = reinterpret_cast<double*>(partials + pose_normal_partials_floats(bp.total_tiles));
+    pdl_launch(k_pose_normal_chunks, dim3(kPNChunks, bp.n_views), 32 * kPNChunkWarps, 0, s, bp, partials, chunk_sums);
+    pdl_launch(k_pose_normal_finish, bp.n_views, 32, 0, s, chunk_sums, normal);
     pf.end(pi, s);
     return cudaGetLastError();
 }
