@@ -99,7 +99,9 @@ constexpr int kGroup = 4;  // Gaussians per warp reduction in the backward
 template <int NT, int PPT>
 constexpr int fwd_min_blocks() { return 0; }
 
-template <int TS, int PPT, int BATCH>
+// CNT: also count each pixel's contributors into n_used (a statistic for the
+// fragment model; the plain forward does without the counter).
+template <int TS, int PPT, int BATCH, bool CNT>
 __global__ void __launch_bounds__(TS * TS / PPT, fwd_min_blocks<TS * TS / PPT, PPT>()) k_render_fwd(const __grid_constant__ BatchParam bp,
                                                               RenderConst rc,
                                                               const float4* __restrict__ rec,
@@ -214,18 +216,19 @@ __global__ void __launch_bounds__(TS * TS / PPT, fwd_min_blocks<TS * TS / PPT, P
                     const float p = fmaf(-t1, t1, fmaf(-t2, t2, b.z));
                     if (p < thr[k]) continue;  // faint fragment, or pixel finished
                     const float alpha = fminf(rc.alpha_max, ex2_approx(p));
-                    const float Tn = T[k] * (1.f - alpha);
+                    // w = alpha T and T (1 - alpha) = T - w
+                    const float wgt = alpha * T[k];
+                    const float Tn = T[k] - wgt;
                     if (Tn < rc.T_min) {
                         thr[k] = kDone;
                         continue;
                     }
-                    const float wgt = alpha * T[k];
                     C0[k] = fmaf(b.w, wgt, C0[k]);
                     C1[k] = fmaf(c.x, wgt, C1[k]);
                     C2[k] = fmaf(c.y, wgt, C2[k]);
                     T[k] = Tn;
                     last[k] = pos1;
-                    ++used[k];
+                    if (CNT) ++used[k];
                 }
             }
         }
@@ -252,7 +255,7 @@ __global__ void __launch_bounds__(TS * TS / PPT, fwd_min_blocks<TS * TS / PPT, P
             }
             T_final[V.pix_off + pl] = T[k];
             n_contrib[V.pix_off + pl] = last[k];
-            if (n_used) n_used[V.pix_off + pl] = used[k];
+            if (CNT) n_used[V.pix_off + pl] = used[k];
             if (target) {
                 const float* y = target + 3 * V.pix_off;
                 float* g = dL_drgb + 3 * V.pix_off;
@@ -512,7 +515,7 @@ __global__ void __launch_bounds__(TS * TS / PPT, bwd_min_blocks<TS * TS / PPT, P
                         vg[6] = fmaf(w, g0[k], vg[6]);
                         vg[7] = fmaf(w, g1[k], vg[7]);
                         vg[8] = fmaf(w, g2[k], vg[8]);
-                        const float gd = fmaf(g0[k], b.w, fmaf(g1[k], c.x, g2[k] * c.y)) - gR[k];
+                        const float gd = fmaf(g0[k], b.w, fmaf(g1[k], c.x, fmaf(g2[k], c.y, -gR[k])));
                         const float dalpha = T[k] * gd;
                         gR[k] = fmaf(alpha, gd, gR[k]);
                         const float ga = araw < rc.alpha_max ? dalpha * araw : 0.f;
@@ -905,12 +908,12 @@ __global__ void __launch_bounds__(TS * TS) k_render_pose_normal(const __grid_con
                 if (p < rc.log2_alpha_min) continue;
                 const float araw = ex2_approx(p);
                 const float alpha = fminf(rc.alpha_max, araw);
-                const float Tn = T * (1.f - alpha);
+                const float wgt = alpha * T;
+                const float Tn = T - wgt;  // as k_render_fwd
                 if (Tn < rc.T_min) {
                     done = true;
                     break;
                 }
-                const float wgt = alpha * T;
                 const float mx = fmaf(t1, ra.z, t2 * rb.x);
                 const float my = fmaf(t1, ra.w, t2 * rb.y);
                 const float sc = araw < rc.alpha_max ? alpha * kLn2 : 0.f;
@@ -1077,9 +1080,14 @@ cudaError_t launch_render_fwd(const BatchParam& bp, const RenderConst& rc_in, co
     bool done = false;
 #define GS_X(T, P, B)                                                                                  \
     if (!done && bp.tile_size == T && bp.ppt == P && bp.batch == B) {                                  \
-        pdl_launch(k_render_fwd<T, P, B>, bp.total_tiles, T * T / P, 0, s, bp, rc, ws.rec, ws.ranges, ws.ovals[1], svals, rgb, \
-                   T_final, n_contrib, n_used, target, dL_drgb, partials, ws.okeys[0], ws.ovals[0],    \
-                   ws.counters);                                                                       \
+        if (n_used)                                                                                    \
+            pdl_launch(k_render_fwd<T, P, B, true>, bp.total_tiles, T * T / P, 0, s, bp, rc, ws.rec, ws.ranges, \
+                       ws.ovals[1], svals, rgb, T_final, n_contrib, n_used, target, dL_drgb, partials,        \
+                       ws.okeys[0], ws.ovals[0], ws.counters);                                            \
+        else                                                                                           \
+            pdl_launch(k_render_fwd<T, P, B, false>, bp.total_tiles, T * T / P, 0, s, bp, rc, ws.rec, ws.ranges, \
+                       ws.ovals[1], svals, rgb, T_final, n_contrib, n_used, target, dL_drgb, partials,        \
+                       ws.okeys[0], ws.ovals[0], ws.counters);                                            \
         done = true;                                                                                   \
     }
     GS_RASTER_VARIANTS(GS_X)
