@@ -209,7 +209,9 @@ typedef struct gs_workspace {
 /* Byte offsets of the workspace arrays, for inspection and tests. */
 typedef struct gs_ws_layout {
     size_t records;       /* float[M][12]: qx, qy, v1x, v1y, v2x, v2y, log2(opacity), r, g, b, depth, 0 */
-    size_t rects;         /* int32[M][4]: x0|y0<<16, x1|y1<<16, first tile id of the view, tiles_x */
+    size_t rects;         /* int32[M][8]: x0|y0<<16, x1|y1<<16, first tile id of the view, tiles_x,
+                           * tiles touched, mask of the listed tiles (row-major over the rectangle when it
+                           * has at most 32 tiles, else 0), 0, 0 */
     size_t tiles_touched; /* uint32[M] */
     size_t depth_keys;    /* uint32[M] low words of the 64-bit depth keys, record order (two buffers) */
     size_t depth_hi;      /* uint32[M] high words of the 64-bit depth keys (overwritten by gs_bin's sort) */

@@ -126,7 +126,7 @@ int sorted_buffer(int total_tiles) {
 
 struct Layout {
     gs_ws_layout pub;
-    size_t scan_part, dkeys1, dvals1, pkeys1, pvals1, hist, hist_part, partials, okeys0, okeys1, ovals0, ovals1, hitmask;
+    size_t scan_part, dkeys1, dvals1, pkeys1, pvals1, hist, hist_part, partials, okeys0, okeys1, ovals0, ovals1;
     size_t pair_rec, pair_inv, pair_grad;  // deterministic backward (0 when off)
     size_t rvals;                          // per-tile lists split from the bins (0 when the bins are the tiles)
     int scan_blocks;
@@ -212,9 +212,8 @@ int make_layout(gs_ctx* ctx, const gs_config& cfg, const gs_view* views, int n_v
     gs_ws_layout& W = L.pub;
     memset(&W, 0, sizeof(W));
     W.records = take(sizeof(float) * kRecFloats * (size_t)M);
-    W.rects = take(sizeof(int4) * (size_t)M);
+    W.rects = take(2 * sizeof(int4) * (size_t)M);
     W.tiles_touched = take(sizeof(uint32_t) * (size_t)M);
-    L.hitmask = take(sizeof(uint32_t) * (size_t)M);
     W.depth_keys = take(sizeof(uint32_t) * (size_t)M);
     L.dkeys1 = take(sizeof(uint32_t) * (size_t)M);
     W.depth_hi = take(sizeof(uint32_t) * (size_t)M);
@@ -273,7 +272,6 @@ WsPtrs ws_ptrs(const gs_workspace* ws, const Layout& L) {
     p.rec = reinterpret_cast<float4*>(b + L.pub.records);
     p.rect = reinterpret_cast<int4*>(b + L.pub.rects);
     p.tiles_touched = reinterpret_cast<uint32_t*>(b + L.pub.tiles_touched);
-    p.hitmask = reinterpret_cast<uint32_t*>(b + L.hitmask);
     p.dkeys[0] = reinterpret_cast<uint32_t*>(b + L.pub.depth_keys);
     p.dkeys[1] = reinterpret_cast<uint32_t*>(b + L.dkeys1);
     p.dvals[0] = reinterpret_cast<uint32_t*>(b + L.pub.depth_vals);

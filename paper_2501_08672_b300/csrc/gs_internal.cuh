@@ -106,9 +106,9 @@ struct GradPtrs {
 // Device-side pointers into the caller's workspace.
 struct WsPtrs {
     float4* rec;             // [M][3]
-    int4* rect;              // [M]
+    int4* rect;              // [2M]: per record (x0|y0<<16, x1|y1<<16, first tile id of the view, tiles_x),
+                             // (tiles touched, listed-tile mask, 0, 0); 32 bytes, one sector per gather
     uint32_t* tiles_touched; // [M]
-    uint32_t* hitmask;       // [M] listed tiles of rectangles of <= 32 tiles, bit = row-major index
     uint32_t* dkeys[2];      // [M] low depth-key words, then scratch
     uint32_t* dvals[2];      // [M]
     uint32_t* dhi;           // [M] high depth-key words

@@ -347,11 +347,13 @@ __global__ void __launch_bounds__(256) k_project(const __grid_constant__ BatchPa
             if (hits == 0) key_hi = key_lo = 0xFFFFFFFFu;
         }
     }
-    ws.hitmask[r] = mask;
     ws.rec[3 * r + 0] = r0;
     ws.rec[3 * r + 1] = r1;
     ws.rec[3 * r + 2] = r2;
-    ws.rect[r] = rect;
+    // the rectangle with its tile count and mask in one 32-byte entry: the
+    // emission gathers it in depth order, one sector per record
+    ws.rect[2 * r] = rect;
+    ws.rect[2 * r + 1] = make_int4((int)touched, (int)mask, 0, 0);
     ws.tiles_touched[r] = touched;
     ws.dkeys[0][r] = key_lo;
     ws.dhi[r] = key_hi;

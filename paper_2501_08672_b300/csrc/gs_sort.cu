@@ -615,8 +615,6 @@ __device__ __forceinline__ uint32_t tile_mask(const FootRows& fr, int bx, int by
 
 template <int F>
 __global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ order,
-                                              const uint32_t* __restrict__ touched,
-                                              const uint32_t* __restrict__ hitmask,
                                               const int4* __restrict__ rects,
                                               const float4* __restrict__ rec,
                                               const unsigned long long* __restrict__ offsets, long long M,
@@ -641,8 +639,11 @@ __global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ order
     if (__all_sync(0xffffffffu, !live)) return;
     const long long j = live ? j0 : 0;
     const uint32_t r = order[j];
-    const uint32_t tt = live ? touched[r] : 0u;
-    const int4 rc = rects[r];
+    // the record's rectangle, then its tile count and listed-tile mask (the
+    // two halves of one 32-byte entry)
+    const int4 rc = rects[2 * r];
+    const int4 rm = rects[2 * r + 1];
+    const uint32_t tt = live ? (uint32_t)rm.x : 0u;
     const int tx0 = rc.x & 0xFFFF, ty0 = (rc.x >> 16) & 0xFFFF;
     const int tx1 = rc.y & 0xFFFF, ty1 = (rc.y >> 16) & 0xFFFF;
     const bool test = log2_alpha_min > -3.0e38f;
@@ -665,7 +666,7 @@ __global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ order
         const unsigned long long wbase = __shfl_sync(0xffffffffu, o0, 0);  // lane 0 is live
         const uint32_t rel = live ? (uint32_t)(o0 - wbase) : 0xFFFFFFFFu;
         const uint32_t wtotal = __reduce_max_sync(0xffffffffu, live ? rel + tt : 0u);
-        const uint32_t mask = mp ? hitmask[r] : 0u;
+        const uint32_t mask = mp ? (uint32_t)rm.y : 0u;
         const uint32_t key0 = (uint32_t)rc.z + (uint32_t)ty0 * (uint32_t)rc.w + (uint32_t)tx0;
         // floor(b / w) = (b * ceil(2048 / w)) >> 11 for b < 32, w <= 32
         const uint32_t info = mp ? ((uint32_t)w | ((2048u + (uint32_t)w - 1u) / (uint32_t)w) << 8 | 0x80000000u) : 0u;
@@ -1108,13 +1109,13 @@ cudaError_t launch_bin(const BatchParam& bp, WsPtrs& ws, unsigned int* status,
     {
         const unsigned eg = (unsigned)((M + 255) / 256);
         if (F == 1)
-            pdl_launch(k_emit<1>, eg, 256, 0, s, order, ws.tiles_touched, ws.hitmask, ws.rect, ws.rec, ws.offsets, M,
+            pdl_launch(k_emit<1>, eg, 256, 0, s, order, ws.rect, ws.rec, ws.offsets, M,
                        ws.cap, bp.tile_size, ws.log2_alpha_min, ws.pkeys[0], ws.pvals[0], ws.pair_rec);
         else if (F == 2)
-            pdl_launch(k_emit<2>, eg, 256, 0, s, order, ws.tiles_touched, ws.hitmask, ws.rect, ws.rec, ws.offsets, M,
+            pdl_launch(k_emit<2>, eg, 256, 0, s, order, ws.rect, ws.rec, ws.offsets, M,
                        ws.cap, bp.tile_size, ws.log2_alpha_min, ws.pkeys[0], ws.pvals[0], ws.pair_rec);
         else
-            pdl_launch(k_emit<4>, eg, 256, 0, s, order, ws.tiles_touched, ws.hitmask, ws.rect, ws.rec, ws.offsets, M,
+            pdl_launch(k_emit<4>, eg, 256, 0, s, order, ws.rect, ws.rec, ws.offsets, M,
                        ws.cap, bp.tile_size, ws.log2_alpha_min, ws.pkeys[0], ws.pvals[0], ws.pair_rec);
     }
     pf.end(pi, s);

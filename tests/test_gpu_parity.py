@@ -432,9 +432,15 @@ def test_bins_are_sorted_and_complete():
     _, r = gpu_forward(p, views, tile_size=ts)
     L = r.layout()
     M, T = L.n_records, L.n_tiles
-    rect = ws_view(r, L.rects, np.int32, 4 * M).reshape(M, 4)
+    rect = ws_view(r, L.rects, np.int32, 8 * M).reshape(M, 8)
     touched = ws_view(r, L.tiles_touched, np.uint32, M)
     rec = ws_view(r, L.records, np.float32, 12 * M).reshape(M, 12)
+    # the rectangle entry repeats the tile count; its mask lists the counted tiles
+    np.testing.assert_array_equal(rect[:, 4].astype(np.uint32), touched)
+    area = ((rect[:, 1] & 0xFFFF) - (rect[:, 0] & 0xFFFF)) * ((rect[:, 1] >> 16) - (rect[:, 0] >> 16))
+    small = (touched > 0) & (area <= 32)
+    bits = np.array([bin(int(m) & 0xFFFFFFFF).count("1") for m in rect[small, 5]])
+    np.testing.assert_array_equal(bits, touched[small].astype(np.int64))
     ranges = ws_view(r, L.tile_ranges, np.uint32, 2 * T).reshape(T, 2)
     npairs = int(r.last_pairs)
     sv = ws_view(r, L.sorted_vals, np.uint32, npairs)
