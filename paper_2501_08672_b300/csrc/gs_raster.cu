@@ -378,7 +378,6 @@ __global__ void __launch_bounds__(TS * TS / PPT, bwd_min_blocks<TS * TS / PPT, P
     const int lt = tile - V.tile_off;
     const int ty = lt / V.tiles_x, tx = lt - ty * V.tiles_x;
     const PixelMap<TS, PPT> pm(tx, ty, t);
-    const WarpBox wb = warp_box(pm.col(0), pm.col(PPT - 1), pm.row(0), pm.row(PPT - 1));
     uint2 rg = ranges[tile];
     if (!gs_checked(rg.x <= rg.y && (long long)rg.y <= rc.cap, rc)) rg.y = rg.x;
     const long long hw = (long long)V.W * V.H;
@@ -432,6 +431,24 @@ __global__ void __launch_bounds__(TS * TS / PPT, bwd_min_blocks<TS * TS / PPT, P
         }
         // a warp whose pixels all stop before this batch stages nothing
         const bool act = !DET || hi - WB < wmax;
+        // Box of the warp's pixels that can take a contribution from this
+        // batch (n_contrib above its first place): a record reaching no such
+        // pixel adds nothing, and deep in the list, where most of the tile's
+        // pixels are already saturated, this box is much smaller than the
+        // warp's (empty, hence reached by nothing, when no pixel is live).
+        WarpBox wb;
+        {
+            int x0 = 1 << 20, x1 = -(1 << 20), y0 = 1 << 20, y1 = -(1 << 20);
+#pragma unroll
+            for (int k = 0; k < PPT; ++k)
+                if (nc[k] > hi - WB) {
+                    x0 = min(x0, pm.col(k));
+                    x1 = max(x1, pm.col(k));
+                    y0 = min(y0, pm.row(k));
+                    y1 = max(y1, pm.row(k));
+                }
+            wb = warp_box(x0, x1, y0, y1);
+        }
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
             if (!act) break;
