@@ -494,8 +494,17 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_offsets(const uint32_t* _
     __shared__ unsigned int s_chunk;
     __shared__ unsigned long long s_prefix;
     const int t = threadIdx.x, lane = t & 31;
-    // the depth sort is done: the next projection opens a new key-range generation
-    if (blockIdx.x == 0 && t == 0) counters[kCtrRangeGen] += 1ull;
+    // The depth sort is done: the next projection opens a new key-range
+    // generation, into cleared slots.  (A slot can start out holding a value
+    // tagged with a later generation, e.g. in a workspace allocated over old
+    // data; the projection's atomicMax would never replace it, and every
+    // binning would fall back to the coarse key map with its long runs of
+    // equal keys.  Cleared here, such a value lasts one binning at most.)
+    if (blockIdx.x == 0 && t == 0) {
+        counters[kCtrRangeGen] += 1ull;
+        counters[kCtrRangeMax] = 0ull;
+        counters[kCtrRangeMin] = 0ull;
+    }
     if (t == 0) s_chunk = atomicAdd(reinterpret_cast<unsigned int*>(flags + nchunks), 1u);
     __syncthreads();
     const long long chunk = s_chunk;

@@ -534,6 +534,34 @@ def test_depth_order_survives_stale_key_ranges():
     same()
 
 
+def test_key_range_slots_recover_from_a_later_generation():
+    """Range slots that start out tagged with a later generation than the
+    workspace's (a workspace allocated over old data) would win every
+    atomicMax of the projection and hold every binning on the coarse
+    fallback map.  The binning clears them once its depth sort is done: the
+    binning over them gives the same tile lists, and the next projection's
+    range carries the current generation again."""
+    p = scenes.frustum_scene(2500, seed=24)
+    views = ragged_views(2500)
+    win, r = gpu_forward(p, views, tile_size=16)
+    L = r.layout()
+    ref = _tile_lists(r, L)
+    torch.cuda.synchronize()
+    gen = int(ws_view(r, L.counters + 24, np.uint64, 1)[0]) & 0xFFFFFFFF
+    later = (gen + 1000) << 32
+    _set_counters(r, L, 1, [later | 0xFFFFFFFF, later | 0xFFFFFFFF])
+    r.ctx.project(win.struct(), r.views, r.ws_struct)
+    r.ctx.bin(r.views, r.ws_struct)
+    got = _tile_lists(r, L)
+    for t, (a, b) in enumerate(zip(ref, got)):
+        np.testing.assert_array_equal(a, b, err_msg="tile %d" % t)
+    r.ctx.project(win.struct(), r.views, r.ws_struct)
+    torch.cuda.synchronize()
+    c = ws_view(r, L.counters, np.uint64, 4)
+    g = int(c[3]) & 0xFFFFFFFF
+    assert int(c[1]) >> 32 == g and int(c[2]) >> 32 == g, [hex(int(x)) for x in c]
+
+
 def test_permuted_gaussians_render_and_backpropagate_identically():
     """Input-permutation invariance away from depth ties: the depth order is
     that of the 64-bit key with ties by index, so permuting the Gaussians of
