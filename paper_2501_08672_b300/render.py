@@ -346,10 +346,11 @@ class WindowOptimizer:
         self.graph = None
         self.step_dev = None
 
-    def step(self, count=None):
-        """One iteration through the C ABI (host-issued launches)."""
+    def step(self, count=None, slot=0):
+        """One iteration through the C ABI (host-issued launches), or, once
+        captured, a replay of the graph of target buffer `slot`."""
         if self.graph is not None:
-            return self.replay()
+            return self.replay(slot)
         w, r = self.win, self.r
         r.forward_loss(self._g, self.targets, self.ssim_lambda, count=count)
         r.backward(self._g, r.dL_drgb, grads=self._grads)
@@ -362,15 +363,8 @@ class WindowOptimizer:
                             w.step_count, self._segs)
         return r.loss
 
-    def capture(self):
-        """Captures one iteration in a CUDA graph (the workspace must already
-        be sized, i.e. after one step).  Later `step()` calls replay it; the
-        Adam step count lives on the device, and a pair-capacity overflow is
-        latched and reported by `r.check_status()`."""
+    def _capture_one(self, targets):
         w, r = self.win, self.r
-        if not r._counted:
-            raise RuntimeError("run one step before capturing (sizes the pair workspace)")
-        self.step_dev = torch.tensor([w.step_count], dtype=torch.int64, device=w.device)
         for attempt in range(3):
             torch.cuda.synchronize()
             g = torch.cuda.CUDAGraph()
@@ -379,7 +373,7 @@ class WindowOptimizer:
                 # the iteration (a tensor or context another part of the
                 # program frees meanwhile) does not invalidate it
                 with torch.cuda.graph(g, capture_error_mode="relaxed"):
-                    r.forward_loss(self._g, self.targets, self.ssim_lambda, count=False)
+                    r.forward_loss(self._g, targets, self.ssim_lambda, count=False)
                     r.backward(self._g, r.dL_drgb, grads=self._grads)
                     if w.capacity > w.n:
                         r.ctx.adam_step_ranges(w.flat, w.gflat, w.m, w.v, w.active_ranges(), self.lr,
@@ -394,11 +388,34 @@ class WindowOptimizer:
                 warnings.warn("graph capture failed (%s); capturing again" % e)
                 torch.cuda.synchronize()
                 continue
-            self.graph = g
             return g
 
-    def replay(self):
-        self.graph.replay()
+    def capture(self, targets=None):
+        """Captures one iteration in a CUDA graph (the workspace must already
+        be sized, i.e. after one step).  Later `step()` calls replay it; the
+        Adam step count lives on the device, and a pair-capacity overflow is
+        latched and reported by `r.check_status()`.
+
+        targets: a list of target buffers (each shaped like the optimiser's
+        targets) to capture one graph per buffer; `step(slot)` then replays
+        the graph that reads targets[slot].  With two buffers the next
+        iteration's keyframe images can be copied into one while the other is
+        in use, and no copy into a fixed buffer is needed."""
+        w, r = self.win, self.r
+        if not r._counted:
+            raise RuntimeError("run one step before capturing (sizes the pair workspace)")
+        bufs = list(targets) if targets is not None else [self.targets]
+        for t in bufs:
+            if t.shape != self.targets.shape or t.dtype != self.targets.dtype or t.device != self.targets.device:
+                raise ValueError("a target buffer differs from the optimiser's targets in shape, dtype or device")
+        self.step_dev = torch.tensor([w.step_count], dtype=torch.int64, device=w.device)
+        self.graphs = [self._capture_one(t) for t in bufs]
+        self.graph = self.graphs[0]
+        self.target_buffers = bufs
+        return self.graph
+
+    def replay(self, slot=0):
+        self.graphs[slot].replay()
         self.win.step_count += 1
         return self.r.loss
 

@@ -1227,6 +1227,41 @@ def test_graph_replay_matches_plain_steps():
     assert abs(float(a.r.loss.item()) - float(b.r.loss.item())) < 1e-5
 
 
+def test_graph_per_target_buffer_follows_host_issued_steps():
+    """capture(targets=[t0, t1]) captures the iteration once per target
+    buffer; replaying slot k % 2 while the next images are copied into the
+    other buffer follows host-issued steps that read the same images in the
+    same order (float atomics differ in order only)."""
+    n = 20_000
+    p = scenes.box_room_scene(n, seed=26)
+    views = scenes.arc_views(3, 160, 128, 150.0, n_gaussians=n)
+    targets = []
+    for seed in (5, 6):
+        _, rt = gpu_forward(scenes.perturbed_copy(p, seed=seed), views)
+        targets.append(rt.rgb.clone())
+    a = WindowOptimizer(p, views, targets[0].clone(), lr=1e-3)
+    b = WindowOptimizer(p, views, targets[0].clone(), lr=1e-3)
+    a.step(count=True)
+    b.step(count=True)
+    bufs = [torch.empty_like(targets[0]) for _ in range(2)]
+    b.capture(targets=bufs)
+    with pytest.raises(ValueError):
+        b.capture(targets=[bufs[0][:10]])
+    losses_a, losses_b = [], []
+    for k in range(4):
+        img = targets[k % 2]
+        a.targets.copy_(img)
+        losses_a.append(float(a.step(count=False).item()))
+        bufs[k % 2].copy_(img)
+        losses_b.append(float(b.step(slot=k % 2).item()))
+    torch.cuda.synchronize()
+    assert b.win.step_count == 5 and int(b.step_dev.item()) == 5
+    assert b.r.check_status()[0] == B.GS_OK
+    assert max(abs(x - y) for x, y in zip(losses_a, losses_b)) < 1e-5
+    assert abs(losses_a[0] - losses_a[1]) > 1e-4  # the two targets do differ
+    assert float((a.win.flat - b.win.flat).norm() / a.win.flat.norm()) < 1e-5
+
+
 # ---------------------------------------------------------------- limits and degenerate inputs
 
 @pytest.mark.parametrize("shape", LIMIT_SHAPES)
