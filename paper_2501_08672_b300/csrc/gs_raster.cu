@@ -141,7 +141,6 @@ __global__ void __launch_bounds__(TS * TS / PPT, fwd_min_blocks<TS * TS / PPT, P
     const int lt = tile - V.tile_off;
     const int ty = lt / V.tiles_x, tx = lt - ty * V.tiles_x;
     const PixelMap<TS, PPT> pm(tx, ty, t);
-    const WarpBox wb = warp_box(pm.col(0), pm.col(PPT - 1), pm.row(0), pm.row(PPT - 1));
     // thr[k]: the exponent a fragment must reach at pixel k; +inf once the
     // pixel is saturated (or outside the image), so one compare both skips
     // faint fragments and finished pixels
@@ -168,6 +167,24 @@ __global__ void __launch_bounds__(TS * TS / PPT, fwd_min_blocks<TS * TS / PPT, P
 #pragma unroll
         for (int k = 0; k < PPT; ++k) all = all && thr[k] == kDone;
         if (__all_sync(0xffffffffu, all)) break;
+        // Box of the warp's pixels still taking contributions: a finished
+        // pixel skips every fragment, so a record reaching none of the live
+        // pixels is not staged.  Past the last contributor of most pixels
+        // (tiles with a few pixels that never saturate walk their whole list)
+        // this box is far smaller than the warp's.
+        WarpBox wb;
+        {
+            int x0 = 1 << 20, x1 = -(1 << 20), y0 = 1 << 20, y1 = -(1 << 20);
+#pragma unroll
+            for (int k = 0; k < PPT; ++k)
+                if (thr[k] != kDone) {
+                    x0 = min(x0, pm.col(k));
+                    x1 = max(x1, pm.col(k));
+                    y0 = min(y0, pm.row(k));
+                    y1 = max(y1, pm.row(k));
+                }
+            wb = warp_box(x0, x1, y0, y1);
+        }
         int n = 0;
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
