@@ -56,8 +56,8 @@ FP32_LANES = 128
 # kernel source they were taken on (sha256 prefix of gs_raster.cu up to the L1
 # kernels, which holds both compositing kernels) and the launch shape;
 # otherwise the roofline reports traffic null.
-TRAFFIC = {"raster_fwd": ("2478bbe003f5cd96", (8, 2, 128, 32), 199.1e6),
-           "raster_bwd": ("2478bbe003f5cd96", (8, 2, 128, 32), 262.7e6)}
+TRAFFIC = {"raster_fwd": ("b545d25b20f69256", (8, 2, 128, 32), 198.9e6),
+           "raster_bwd": ("b545d25b20f69256", (8, 2, 128, 32), 262.8e6)}
 
 
 def raster_source_hash():
