@@ -44,12 +44,12 @@ WORKLOAD = "box-room sliding window: 200k planar Gaussians (SH degree 1), 8 keyf
 # Algorithmic FP32 operations per fragment (FMA = 2; compares, min/max and
 # selects not counted; ex2 and the divide count 1 each):
 #   every visited fragment:  d = x - q (2), t_k = d . v_k (2 x 3), p = l - t1^2 - t2^2 (4)   = 12
-#   forward, contributing:   ex2, 1 - alpha, T (1 - alpha), w = alpha T, C += w c (6)        = 10
+#   forward, contributing:   ex2, w = alpha T, T (1 - alpha) = T - w, C += w c (6)           = 9
 #   backward, contributing:  ex2, 1 - alpha, T / (1 - alpha), w, dL/dc += w g (6), g.c (5),
 #                            g.c - g.R, dL/dalpha, g.R update (2), ga, ga t1, ga t2 (4),
 #                            ga dx, ga dy, ga dx^2, ga dx dy, ga dy^2 (6), sum ga            = 34
 FLOP_VISITED = 12.0
-FLOP_CONTRIB = {"raster_fwd": 10.0, "raster_bwd": 34.0}
+FLOP_CONTRIB = {"raster_fwd": 9.0, "raster_bwd": 34.0}
 FP32_LANES = 128
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # compositing kernels from one ncu capture of this workload, valid only for the
