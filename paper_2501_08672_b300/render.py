@@ -408,6 +408,8 @@ class WindowOptimizer:
         for t in bufs:
             if t.shape != self.targets.shape or t.dtype != self.targets.dtype or t.device != self.targets.device:
                 raise ValueError("a target buffer differs from the optimiser's targets in shape, dtype or device")
+            if not t.is_contiguous():
+                raise ValueError("a target buffer is not contiguous (the kernels read it as one packed array)")
         self.step_dev = torch.tensor([w.step_count], dtype=torch.int64, device=w.device)
         self.graphs = [self._capture_one(t) for t in bufs]
         self.graph = self.graphs[0]

@@ -1247,6 +1247,8 @@ def test_graph_per_target_buffer_follows_host_issued_steps():
     b.capture(targets=bufs)
     with pytest.raises(ValueError):
         b.capture(targets=[bufs[0][:10]])
+    with pytest.raises(ValueError):
+        b.capture(targets=[torch.empty(2 * bufs[0].numel(), device="cuda")[::2]])
     losses_a, losses_b = [], []
     for k in range(4):
         img = targets[k % 2]
