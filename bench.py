@@ -52,12 +52,15 @@ FLOP_VISITED = 12.0
 FLOP_CONTRIB = {"raster_fwd": 9.0, "raster_bwd": 34.0}
 FP32_LANES = 128
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
-# compositing kernels from one ncu capture of this workload, valid only for the
-# kernel source they were taken on (sha256 prefix of gs_raster.cu up to the L1
-# kernels, which holds both compositing kernels) and the launch shape;
-# otherwise the roofline reports traffic null.
-TRAFFIC = {"raster_fwd": ("b545d25b20f69256", (8, 2, 128, 32), 198.9e6),
-           "raster_bwd": ("b545d25b20f69256", (8, 2, 128, 32), 262.8e6)}
+# compositing kernels from ncu captures of this workload, per launch shape
+# (tile size, pixels per thread, batch, bin size: the autotuner's two fastest,
+# within 0.1 % of each other), valid only for the kernel source they were taken
+# on (sha256 prefix of gs_raster.cu up to the L1 kernels, which holds both
+# compositing kernels); otherwise the roofline reports traffic null.
+TRAFFIC = {"raster_fwd": [("b545d25b20f69256", (8, 2, 128, 32), 198.9e6),
+                          ("b545d25b20f69256", (16, 4, 128, 32), 189.7e6)],
+           "raster_bwd": [("b545d25b20f69256", (8, 2, 128, 32), 262.8e6),
+                          ("b545d25b20f69256", (16, 4, 128, 32), 249.3e6)]}
 
 
 def raster_source_hash():
@@ -485,8 +488,7 @@ def run_b300(args, world, rank, local):
         flop = FLOP_VISITED * visited + FLOP_CONTRIB[dominant] * contrib
         achieved = flop / (avg_ms / 1e3) / 1e12
         traffic = None
-        if dominant in TRAFFIC:
-            sha, tshape, tbytes = TRAFFIC[dominant]
+        for sha, tshape, tbytes in TRAFFIC.get(dominant, []):
             if raster_source_hash() == sha and tuple(shape) == tshape and args.workload == "window":
                 traffic = tbytes
         roof = {"bound": "alu", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
