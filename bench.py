@@ -555,6 +555,17 @@ def run_b300(args, world, rank, local):
 
     e_s, e_e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     opt.capture(targets=in_t)  # one graph per target buffer (outside the timed region)
+    # this host link's rate for the step's upload, alone (outside the timed
+    # region): the end-to-end rate cannot exceed it / the bytes per step
+    h_s, h_e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(c_in):
+        in_t[0].copy_(host_target, non_blocking=True)
+        h_s.record(c_in)
+        for _ in range(5):
+            in_t[0].copy_(host_target, non_blocking=True)
+        h_e.record(c_in)
+    torch.cuda.synchronize()
+    h2d_gbs = 5 * host_target.numel() * 4 / (h_s.elapsed_time(h_e) / 1e3) / 1e9
     torch.cuda.synchronize()
     e_s.record(comp)
     for j in range(min(NB - 1, E)):
@@ -650,7 +661,8 @@ def run_b300(args, world, rank, local):
                                "host_issued_it_s": whole_job_rate(world, K, max_plain_ms)}, **other_forms),
                 "cpu_baseline": cpu,
                 "e2e": {"value": 1e3 / e2e_ms, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-                        "d2h_bytes_per_step": int(d2h)},
+                        "d2h_bytes_per_step": int(d2h), "h2d_link_gbs": h2d_gbs,
+                        "upload_only_it_s": h2d_gbs * 1e9 / max(h2d, 1)},
                 "gpu_launches": int(launches), "clocks": clocks}
         print(json.dumps(line), flush=True)
     if world > 1:
